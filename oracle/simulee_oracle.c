@@ -1,0 +1,373 @@
+/*
+ * simulee_oracle.c - CPU ORACLE for the memory-model synchronization check.
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke entry point and the
+ * benchmark's CPU-baseline leg may load this library. The product path never
+ * calls it; it shares no code, header or table with the CUDA library.
+ *
+ * It is deliberately plain and single threaded: records are grouped with
+ * qsort and every group is searched pair by pair, exactly as the definitions
+ * read. It follows the paper (Wu et al., "Characterizing and Detecting CUDA
+ * Program Bugs", arXiv 1905.01833):
+ *   - Memory Model (Sec. 3.2.1): a memory unit holds tuples
+ *     <visit order, thread, action>. Here the barrier epoch of a record plays
+ *     the role of the paper's per-unit visit order (the count of barriers the
+ *     thread has passed), and the record's visit_order field is the serial
+ *     position in the simulated schedule, used only to order accesses.
+ *   - Theorem 1 (Sec. 3.2.3): two tuples of one unit race when they share the
+ *     barrier interval, come from different threads and at least one writes.
+ *     The warp refinements of the theorem are not applied (records carry no
+ *     statement or divergence information); atomics count as writes except
+ *     that two atomics never race; global memory is also checked across
+ *     blocks, where barriers give no order, in any epochs.
+ *   - Algorithm 5 (Sec. 3.2.3): races per unit and visit-order group; a
+ *     barrier is redundant when merging the tuples of the two visit orders it
+ *     separates creates no race.
+ *   - Algorithm 4 and Sec. 2 (barrier divergence): threads of one block that
+ *     reach different numbers of barriers.
+ * Output conventions (one record per group and class, the lowest pair, the
+ * canonical order) are the ones this library defines; see the header of the
+ * Python wrapper for the full statement.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EBADTRACE 2
+#define ORC_ENOMEM 3
+
+#define ACT_R 0u
+#define ACT_W 1u
+#define ACT_A 2u
+
+#define FLAG_UNSORTED 1u
+
+typedef struct {
+    uint8_t space, scope, cls, pad;
+    uint32_t block, epoch, unit, vo_first, vo_second, gtid_first, gtid_second;
+} orc_race;                                               /* 32 bytes */
+
+typedef struct { uint32_t block, min_count, max_count, first_min_tid; } orc_div;
+typedef struct { uint32_t block, barrier; } orc_bar;
+
+typedef struct {
+    int32_t status;
+    uint32_t bad_kind;          /* 0: a record, 1: a barrier count */
+    uint64_t bad_index;
+    orc_race *races; uint64_t n_races;
+    orc_div *divs; uint64_t n_divs;
+    orc_bar *bars; uint64_t n_bars;
+    uint32_t *grid; uint64_t n_grid;
+} orc_result;
+
+typedef struct {                 /* one decoded record */
+    uint32_t unit, vo, block, tid, epoch, act, space, gtid;
+} rec_t;
+
+typedef struct { uint64_t k0, k1, k2, idx; } skey;
+
+static int cmp_skey(const void *a, const void *b) {
+    const skey *x = (const skey *)a, *y = (const skey *)b;
+    if (x->k0 != y->k0) return x->k0 < y->k0 ? -1 : 1;
+    if (x->k1 != y->k1) return x->k1 < y->k1 ? -1 : 1;
+    if (x->k2 != y->k2) return x->k2 < y->k2 ? -1 : 1;
+    if (x->idx != y->idx) return x->idx < y->idx ? -1 : 1;
+    return 0;
+}
+
+/* write or atomic: the actions that modify the unit */
+static int modifies(uint32_t act) { return act == ACT_W || act == ACT_A; }
+
+/* Theorem 1 without warp refinements, plus the atomic rule:
+   different owners, at least one modifying access, not both atomic. */
+static int conflict(const rec_t *p, const rec_t *q, uint32_t id_p, uint32_t id_q) {
+    if (id_p == id_q) return 0;
+    if (!modifies(p->act) && !modifies(q->act)) return 0;
+    if (p->act == ACT_A && q->act == ACT_A) return 0;
+    return 1;
+}
+
+/* class of a conflicting pair: 0 = write&write, 1 = read&write */
+static uint32_t pair_class(const rec_t *p, const rec_t *q) {
+    return (modifies(p->act) && modifies(q->act)) ? 0u : 1u;
+}
+
+static void orc_free_fields(orc_result *r) {
+    free(r->races); free(r->divs); free(r->bars); free(r->grid);
+    r->races = NULL; r->divs = NULL; r->bars = NULL; r->grid = NULL;
+}
+
+void orc_free(orc_result *r) {
+    if (!r) return;
+    orc_free_fields(r);
+    free(r);
+}
+
+/* ---- validation ------------------------------------------------------------ */
+static int validate(const uint32_t *ev, uint64_t n, const uint32_t *counts, uint32_t nb, uint32_t bt,
+                    uint32_t su, uint32_t gu, uint32_t maxb, uint32_t flags,
+                    uint32_t *bad_kind, uint64_t *bad_index) {
+    uint64_t nt = (uint64_t)nb * bt;
+    for (uint64_t i = 0; i < nt; i++) {
+        if (counts[i] > maxb) { *bad_kind = 1; *bad_index = i; return 1; }
+    }
+    for (uint64_t i = 0; i < n; i++) {
+        const uint32_t *w = ev + 4 * i;
+        uint32_t unit = w[0], vo = w[1], block = w[2], w3 = w[3];
+        uint32_t tid = w3 & 0xFFFFu, epoch = (w3 >> 16) & 0xFFFu, act = (w3 >> 28) & 3u;
+        uint32_t space = (w3 >> 30) & 1u, reserved = w3 >> 31;
+        int bad = 0;
+        if (block >= nb || tid >= bt) bad = 1;
+        if (act == 3u || reserved) bad = 1;
+        if (space == 0 && unit >= su) bad = 1;
+        if (space == 1 && unit >= gu) bad = 1;
+        if (!bad && epoch > counts[(uint64_t)block * bt + tid]) bad = 1;
+        if (!(flags & FLAG_UNSORTED) && i > 0 && vo <= ev[4 * (i - 1) + 1]) bad = 1;
+        if (bad) { *bad_kind = 0; *bad_index = i; return 1; }
+    }
+    return 0;
+}
+
+static void decode(const uint32_t *ev, uint64_t n, uint32_t bt, rec_t *r) {
+    for (uint64_t i = 0; i < n; i++) {
+        const uint32_t *w = ev + 4 * i;
+        r[i].unit = w[0];
+        r[i].vo = w[1];
+        r[i].block = w[2];
+        r[i].tid = w[3] & 0xFFFFu;
+        r[i].epoch = (w[3] >> 16) & 0xFFFu;
+        r[i].act = (w[3] >> 28) & 3u;
+        r[i].space = (w[3] >> 30) & 1u;
+        r[i].gtid = w[2] * bt + r[i].tid;
+    }
+}
+
+/* ---- growable output arrays ------------------------------------------------- */
+typedef struct { void *p; uint64_t n, cap; size_t sz; } vec;
+static int vec_push(vec *v, const void *item) {
+    if (v->n == v->cap) {
+        uint64_t nc = v->cap ? v->cap * 2 : 64;
+        void *np_ = realloc(v->p, nc * v->sz);
+        if (!np_) return 0;
+        v->p = np_; v->cap = nc;
+    }
+    memcpy((char *)v->p + v->n * v->sz, item, v->sz);
+    v->n++;
+    return 1;
+}
+
+/*
+ * Lowest conflicting pair of class `cls` in a group whose records are listed
+ * in schedule order (visit order, then record index). "Lowest" means the pair
+ * whose later access comes first; among those, the earliest partner. The
+ * search is the definition itself: scan q in order and, for each q, the
+ * partners before it in order; the first hit is the answer.
+ * inter != 0: owners are blocks, else global thread ids.
+ */
+static int lowest_pair(const rec_t *r, const skey *g, uint64_t m, uint32_t cls, int inter,
+                       uint64_t *pi, uint64_t *qi) {
+    for (uint64_t q = 1; q < m; q++) {
+        const rec_t *rq = &r[g[q].idx];
+        uint32_t idq = inter ? rq->block : rq->gtid;
+        for (uint64_t p = 0; p < q; p++) {
+            const rec_t *rp = &r[g[p].idx];
+            uint32_t idp = inter ? rp->block : rp->gtid;
+            if (conflict(rp, rq, idp, idq) && pair_class(rp, rq) == cls) {
+                *pi = g[p].idx; *qi = g[q].idx;
+                return 1;
+            }
+        }
+    }
+    return 0;
+}
+
+/* a group can only race if it holds a write, or an atomic next to a non-atomic */
+static int may_race(const rec_t *r, const skey *g, uint64_t m) {
+    int has_w = 0, has_a = 0, has_r = 0;
+    for (uint64_t i = 0; i < m; i++) {
+        uint32_t a = r[g[i].idx].act;
+        has_w |= (a == ACT_W); has_a |= (a == ACT_A); has_r |= (a == ACT_R);
+    }
+    return has_w || (has_a && has_r);
+}
+
+static int emit_group(vec *out, const rec_t *r, const skey *g, uint64_t m, int inter) {
+    if (m < 2 || !may_race(r, g, m)) return 1;
+    for (uint32_t cls = 0; cls < 2; cls++) {
+        uint64_t pi, qi;
+        if (!lowest_pair(r, g, m, cls, inter, &pi, &qi)) continue;
+        const rec_t *p = &r[pi], *q = &r[qi];
+        orc_race x;
+        memset(&x, 0, sizeof x);
+        x.space = (uint8_t)q->space;
+        x.scope = (uint8_t)(inter ? 1 : 0);
+        x.cls = (uint8_t)cls;
+        x.block = inter ? 0xFFFFFFFFu : q->block;
+        x.epoch = inter ? 0xFFFFFFFFu : q->epoch;
+        x.unit = q->unit;
+        x.vo_first = p->vo; x.vo_second = q->vo;
+        x.gtid_first = p->gtid; x.gtid_second = q->gtid;
+        if (!vec_push(out, &x)) return 0;
+    }
+    return 1;
+}
+
+/* ---- races: intra-block groups (space, block, epoch, unit), then inter-block
+        groups (global unit); emitted in canonical order ---------------------- */
+static int races(const rec_t *r, uint64_t n, vec *out) {
+    skey *k = (skey *)malloc((n ? n : 1) * sizeof(skey));
+    if (!k) return 0;
+    for (uint64_t i = 0; i < n; i++) {
+        k[i].k0 = ((uint64_t)r[i].space << 32) | r[i].block;
+        k[i].k1 = ((uint64_t)r[i].epoch << 32) | r[i].unit;
+        k[i].k2 = r[i].vo;
+        k[i].idx = i;
+    }
+    qsort(k, n, sizeof(skey), cmp_skey);
+    for (uint64_t s = 0; s < n;) {
+        uint64_t e = s + 1;
+        while (e < n && k[e].k0 == k[s].k0 && k[e].k1 == k[s].k1) e++;
+        if (!emit_group(out, r, k + s, e - s, 0)) { free(k); return 0; }
+        s = e;
+    }
+    /* inter-block: global records grouped by unit only */
+    uint64_t m = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        if (r[i].space != 1) continue;
+        k[m].k0 = r[i].unit; k[m].k1 = 0; k[m].k2 = r[i].vo; k[m].idx = i;
+        m++;
+    }
+    qsort(k, m, sizeof(skey), cmp_skey);
+    for (uint64_t s = 0; s < m;) {
+        uint64_t e = s + 1;
+        while (e < m && k[e].k0 == k[s].k0) e++;
+        if (!emit_group(out, r, k + s, e - s, 1)) { free(k); return 0; }
+        s = e;
+    }
+    free(k);
+    return 1;
+}
+
+/* ---- redundant barriers ------------------------------------------------------
+   Barrier k of block b separates epochs k and k+1. It is NOT redundant iff some
+   unit (either space) of block b has a record p of epoch k and a record q of
+   epoch k+1 that would race if the two epochs were one (owners: threads). */
+static int barriers(const rec_t *r, uint64_t n, const uint32_t *counts, uint32_t nb, uint32_t bt,
+                    uint32_t maxb, vec *bars, vec *grid) {
+    uint64_t ne = (uint64_t)maxb + 1;
+    uint8_t *nonred = (uint8_t *)calloc((uint64_t)nb * ne + 1, 1);
+    uint32_t *maxc = (uint32_t *)calloc((uint64_t)nb + 1, sizeof(uint32_t));
+    skey *k = (skey *)malloc((n ? n : 1) * sizeof(skey));
+    if (!nonred || !maxc || !k) { free(nonred); free(maxc); free(k); return 0; }
+    for (uint32_t b = 0; b < nb; b++)
+        for (uint32_t t = 0; t < bt; t++)
+            if (counts[(uint64_t)b * bt + t] > maxc[b]) maxc[b] = counts[(uint64_t)b * bt + t];
+    for (uint64_t i = 0; i < n; i++) {
+        k[i].k0 = ((uint64_t)r[i].space << 32) | r[i].block;
+        k[i].k1 = ((uint64_t)r[i].unit << 32) | r[i].epoch;
+        k[i].k2 = r[i].vo;
+        k[i].idx = i;
+    }
+    qsort(k, n, sizeof(skey), cmp_skey);
+    for (uint64_t s = 0; s < n;) {           /* one (space, block, unit, epoch) group at a time */
+        uint64_t e = s + 1;
+        while (e < n && k[e].k0 == k[s].k0 && k[e].k1 == k[s].k1) e++;
+        /* the next group: same (space, block, unit), epoch + 1 ? */
+        if (e < n && k[e].k0 == k[s].k0 && (k[e].k1 >> 32) == (k[s].k1 >> 32) &&
+            (k[e].k1 & 0xFFFFFFFFu) == (k[s].k1 & 0xFFFFFFFFu) + 1) {
+            uint64_t f = e + 1;
+            while (f < n && k[f].k0 == k[e].k0 && k[f].k1 == k[e].k1) f++;
+            const rec_t *r0 = &r[k[s].idx];
+            uint64_t slot = (uint64_t)r0->block * ne + r0->epoch;
+            for (uint64_t i = s; i < e && !nonred[slot]; i++)
+                for (uint64_t j = e; j < f; j++) {
+                    const rec_t *p = &r[k[i].idx], *q = &r[k[j].idx];
+                    if (conflict(p, q, p->gtid, q->gtid)) { nonred[slot] = 1; break; }
+                }
+        }
+        s = e;
+    }
+    uint32_t gmax = 0;
+    for (uint32_t b = 0; b < nb; b++) {
+        if (maxc[b] > gmax) gmax = maxc[b];
+        for (uint32_t kk = 0; kk < maxc[b]; kk++)
+            if (!nonred[(uint64_t)b * ne + kk]) {
+                orc_bar x = {b, kk};
+                if (!vec_push(bars, &x)) goto fail;
+            }
+    }
+    /* grid-wide: barrier k is redundant in every block that has it */
+    for (uint32_t kk = 0; kk < gmax; kk++) {
+        int all = 1;
+        for (uint32_t b = 0; b < nb && all; b++)
+            if (maxc[b] > kk && nonred[(uint64_t)b * ne + kk]) all = 0;
+        if (all && !vec_push(grid, &kk)) goto fail;
+    }
+    free(nonred); free(maxc); free(k);
+    return 1;
+fail:
+    free(nonred); free(maxc); free(k);
+    return 0;
+}
+
+/* ---- barrier divergence: a block whose threads reach unequal barrier counts --- */
+static int divergence(const uint32_t *counts, uint32_t nb, uint32_t bt, vec *out) {
+    for (uint32_t b = 0; b < nb; b++) {
+        uint32_t mn = 0xFFFFFFFFu, mx = 0, first = 0;
+        for (uint32_t t = 0; t < bt; t++) {
+            uint32_t c = counts[(uint64_t)b * bt + t];
+            if (c < mn) { mn = c; first = t; }
+            if (c > mx) mx = c;
+        }
+        if (bt > 0 && mn != mx) {
+            orc_div x = {b, mn, mx, first};
+            if (!vec_push(out, &x)) return 0;
+        }
+    }
+    return 1;
+}
+
+/*
+ * Full check. ev: n records of 4 uint32 words; counts: nb*bt per-thread barrier
+ * counts. Returns a heap result (free with orc_free), or NULL when out of memory.
+ */
+orc_result *orc_check(const uint32_t *ev, uint64_t n, const uint32_t *counts, uint32_t nb, uint32_t bt,
+                      uint32_t su, uint32_t gu, uint32_t maxb, uint32_t flags) {
+    orc_result *res = (orc_result *)calloc(1, sizeof(orc_result));
+    if (!res) return NULL;
+    if (validate(ev, n, counts, nb, bt, su, gu, maxb, flags, &res->bad_kind, &res->bad_index)) {
+        res->status = ORC_EBADTRACE;
+        return res;
+    }
+    rec_t *r = (rec_t *)malloc((n ? n : 1) * sizeof(rec_t));
+    if (!r) { free(res); return NULL; }
+    decode(ev, n, bt, r);
+    vec rv = {0, 0, 0, sizeof(orc_race)}, dv = {0, 0, 0, sizeof(orc_div)};
+    vec bv = {0, 0, 0, sizeof(orc_bar)}, gv = {0, 0, 0, sizeof(uint32_t)};
+    int ok = races(r, n, &rv) && divergence(counts, nb, bt, &dv) &&
+             barriers(r, n, counts, nb, bt, maxb, &bv, &gv);
+    free(r);
+    res->races = (orc_race *)rv.p; res->n_races = rv.n;
+    res->divs = (orc_div *)dv.p; res->n_divs = dv.n;
+    res->bars = (orc_bar *)bv.p; res->n_bars = bv.n;
+    res->grid = (uint32_t *)gv.p; res->n_grid = gv.n;
+    if (!ok) { orc_free(res); return NULL; }
+    res->status = ORC_OK;
+    return res;
+}
+
+/* flat accessors for foreign-function callers */
+int32_t orc_status(const orc_result *r) { return r->status; }
+uint32_t orc_bad_kind(const orc_result *r) { return r->bad_kind; }
+uint64_t orc_bad_index(const orc_result *r) { return r->bad_index; }
+uint64_t orc_n_races(const orc_result *r) { return r->n_races; }
+uint64_t orc_n_divs(const orc_result *r) { return r->n_divs; }
+uint64_t orc_n_bars(const orc_result *r) { return r->n_bars; }
+uint64_t orc_n_grid(const orc_result *r) { return r->n_grid; }
+void orc_copy(const orc_result *r, void *races, void *divs, void *bars, void *grid) {
+    if (races && r->n_races) memcpy(races, r->races, r->n_races * sizeof(orc_race));
+    if (divs && r->n_divs) memcpy(divs, r->divs, r->n_divs * sizeof(orc_div));
+    if (bars && r->n_bars) memcpy(bars, r->bars, r->n_bars * sizeof(orc_bar));
+    if (grid && r->n_grid) memcpy(grid, r->grid, r->n_grid * sizeof(uint32_t));
+}

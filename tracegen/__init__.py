@@ -1,0 +1,274 @@
+"""Seeded synthetic access-record traces.
+
+This module only synthesises inputs for the synchronization check: 16-byte
+access records plus per-thread barrier counts. It holds none of the
+detection arithmetic; the CPU oracle and the CUDA path both consume what it
+produces and neither is imported here.
+
+Record layout (four little-endian uint32 words per record):
+    w0 unit, w1 visit_order, w2 block,
+    w3 = tid[0:16] | epoch[16:28] | action[28:30] | space[30] | reserved[31]
+with action 0 read / 1 write / 2 atomic and space 0 shared / 1 global.
+
+The bulk generators are C (``tracegen.c``), compiled on first use with gcc.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+READ, WRITE, ATOMIC = 0, 1, 2
+SHARED, GLOBAL = 0, 1
+UNSORTED = 1  # trace flag: visit orders are not increasing in record order
+
+DEFAULT_SEED = 1905018330
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tracegen.c")
+_SO = os.path.join(_HERE, "libtracegen.so")
+_lock = threading.Lock()
+_lib_handle = None
+
+
+def build(force: bool = False) -> str:
+    """Compile tracegen.c into libtracegen.so (host code, any architecture)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _PatternParams(ctypes.Structure):
+    _fields_ = [
+        ("seed", ctypes.c_uint64),
+        ("n_blocks", ctypes.c_uint32),
+        ("block_threads", ctypes.c_uint32),
+        ("n_epochs", ctypes.c_uint32),
+        ("shared_units", ctypes.c_uint32),
+        ("global_units", ctypes.c_uint32),
+        ("removed_p", ctypes.c_double),
+        ("atomic_p", ctypes.c_double),
+        ("peek_p", ctypes.c_double),
+        ("stray_p", ctypes.c_double),
+    ]
+
+
+def _lib():
+    global _lib_handle
+    with _lock:
+        if _lib_handle is None:
+            lib = ctypes.CDLL(build())
+            vp = ctypes.c_void_p
+            lib.tg_strided.restype = ctypes.c_uint64
+            lib.tg_strided.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                       ctypes.c_uint32, ctypes.c_double, ctypes.c_double, vp, vp]
+            lib.tg_pattern.restype = ctypes.c_uint64
+            lib.tg_pattern.argtypes = [ctypes.POINTER(_PatternParams), vp, vp]
+            lib.tg_barrier.restype = ctypes.c_uint64
+            lib.tg_barrier.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                       ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double,
+                                       ctypes.c_double, vp, vp, vp]
+            _lib_handle = lib
+    return _lib_handle
+
+
+@dataclasses.dataclass
+class Trace:
+    """A trace: records, per-thread barrier counts and the dimensions they live in."""
+    events: np.ndarray            # uint32 (n, 4)
+    barrier_counts: np.ndarray    # uint32 (n_blocks * block_threads,)
+    n_blocks: int
+    block_threads: int
+    shared_units: int
+    global_units: int
+    max_barriers: int
+    flags: int = 0
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def n_events(self) -> int:
+        return int(self.events.shape[0])
+
+
+def pack(unit, vo, block, tid, epoch, action, space):
+    """Pack record fields (scalars or arrays) into an (n, 4) uint32 array."""
+    unit = np.asarray(unit, dtype=np.uint64)
+    w3 = (np.asarray(tid, dtype=np.uint64) & 0xFFFF) | ((np.asarray(epoch, dtype=np.uint64) & 0xFFF) << 16) \
+        | ((np.asarray(action, dtype=np.uint64) & 3) << 28) | ((np.asarray(space, dtype=np.uint64) & 1) << 30)
+    out = np.stack(np.broadcast_arrays(unit, np.asarray(vo, dtype=np.uint64),
+                                       np.asarray(block, dtype=np.uint64), w3), axis=-1)
+    return np.ascontiguousarray(out.astype(np.uint32).reshape(-1, 4))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def strided(seed: int = DEFAULT_SEED, n_threads: int = 256, n_epochs: int = 8, per_thread: int = 16,
+            shared_units: int = 12288, write_p: float = 0.25, redirect_p: float = 0.001) -> Trace:
+    """One block; per epoch a stride s in {1,2,32}; thread t touches (t*s+k) mod units."""
+    lib = _lib()
+    n = lib.tg_strided(seed, n_threads, n_epochs, per_thread, shared_units, write_p, redirect_p, None, None)
+    ev = np.empty((n, 4), dtype=np.uint32)
+    counts = np.empty(n_threads, dtype=np.uint32)
+    lib.tg_strided(seed, n_threads, n_epochs, per_thread, shared_units, write_p, redirect_p, _ptr(ev), _ptr(counts))
+    return Trace(ev, counts, 1, n_threads, shared_units, 0, n_epochs - 1,
+                 meta=dict(kind="strided", seed=seed))
+
+
+def pattern(seed: int = DEFAULT_SEED, n_blocks: int = 1024, block_threads: int = 256, n_epochs: int = 32,
+            shared_units: int = 12288, global_units: int = 1 << 26, removed_p: float = 0.10,
+            atomic_p: float = 0.02, peek_p: float = 0.01, stray_p: float = 0.001) -> Trace:
+    """Grid of tree-reduction / tiled-transpose blocks over shared and global memory."""
+    lib = _lib()
+    pp = _PatternParams(seed, n_blocks, block_threads, n_epochs, shared_units, global_units,
+                        removed_p, atomic_p, peek_p, stray_p)
+    n = lib.tg_pattern(ctypes.byref(pp), None, None)
+    if n == 0:
+        raise ValueError("pattern: dimensions do not fit the access patterns")
+    ev = np.empty((n, 4), dtype=np.uint32)
+    counts = np.empty(n_blocks * block_threads, dtype=np.uint32)
+    lib.tg_pattern(ctypes.byref(pp), _ptr(ev), _ptr(counts))
+    return Trace(ev, counts, n_blocks, block_threads, shared_units, global_units, n_epochs - 1,
+                 meta=dict(kind="pattern", seed=seed))
+
+
+def redundant_set(seed: int, n_barriers: int, count: int) -> int:
+    """Bit mask of `count` distinct barrier indices in [0, n_barriers), seeded."""
+    rng = np.random.default_rng(seed ^ 0x5EED)
+    chosen = rng.choice(n_barriers, size=min(count, n_barriers), replace=False)
+    mask = 0
+    for k in chosen:
+        mask |= 1 << int(k)
+    return mask
+
+
+def barrier(seed: int = DEFAULT_SEED, n_blocks: int = 1024, block_threads: int = 1024, n_epochs: int = 64,
+            shared_units: int = 8192, per_thread: int = 4, redundant_fraction: float = 0.2,
+            redirect_p: float = 1e-5, diverge_p: float = 0.01) -> Trace:
+    """Barrier-analysis family: known redundant set and known divergent blocks."""
+    lib = _lib()
+    nbar = n_epochs - 1
+    mask = redundant_set(seed, nbar, int(round(redundant_fraction * nbar)))
+    args = (seed, n_blocks, block_threads, n_epochs, shared_units, per_thread, mask, redirect_p, diverge_p)
+    n = lib.tg_barrier(*args, None, None, None)
+    if n == 0:
+        raise ValueError("barrier: dimensions do not fit")
+    ev = np.empty((n, 4), dtype=np.uint32)
+    counts = np.empty(n_blocks * block_threads, dtype=np.uint32)
+    div = np.empty(n_blocks, dtype=np.uint8)
+    lib.tg_barrier(*args, _ptr(ev), _ptr(counts), _ptr(div))
+    return Trace(ev, counts, n_blocks, block_threads, shared_units, 0, n_epochs - 1,
+                 meta=dict(kind="barrier", seed=seed, redundant_mask=mask,
+                           divergent_blocks=np.nonzero(div)[0].astype(np.uint32)))
+
+
+# --- the five named workloads --------------------------------------------------
+
+def c1(seed: int = DEFAULT_SEED) -> Trace:
+    """1 block x 256 threads, 8 epochs, 12288 shared units, 16 accesses/thread/epoch (32,768 records)."""
+    return strided(seed, 256, 8, 16, 12288, 0.25, 0.001)
+
+
+def c2(seed: int = DEFAULT_SEED, n_blocks: int = 1024) -> Trace:
+    """1024 blocks x 256 threads, 32 epochs, 12288 shared + 2^26 global units (~6e7 records)."""
+    return pattern(seed, n_blocks, 256, 32, 12288, 1 << 26)
+
+
+def c4(seed: int = DEFAULT_SEED, n_blocks: int = 1024) -> Trace:
+    """1024 blocks x 1024 threads, 64 epochs, 4 accesses/thread/epoch (2^28 records)."""
+    return barrier(seed, n_blocks, 1024, 64, 8192, 4)
+
+
+def c3_sizes(seed: int = DEFAULT_SEED, n_traces: int = 4096, median: float = 1e5, sigma: float = 0.87,
+             lo: float = 1e3, hi: float = 1e7):
+    """Per-trace (target records, block size, epochs) for the batched workload."""
+    rng = np.random.default_rng(seed)
+    n = np.clip(np.exp(np.log(median) + sigma * rng.standard_normal(n_traces)), lo, hi)
+    bs = rng.choice(np.array([64, 128, 256, 1024]), size=n_traces)
+    ep = rng.integers(4, 65, size=n_traces)
+    return n.astype(np.int64), bs.astype(np.int64), ep.astype(np.int64)
+
+
+def c3_trace(i: int, target: int, block_threads: int, n_epochs: int, seed: int = DEFAULT_SEED) -> Trace:
+    """One trace of the batched workload: the grid pattern sized to about `target` records."""
+    nb = max(1, int(np.ceil(target / (block_threads * n_epochs * 8))))
+    gu = 4096 + 2 * 1024 * nb
+    gu = 1 << int(np.ceil(np.log2(gu)))
+    return pattern(seed + 7919 * (i + 1), nb, block_threads, n_epochs, 12288, gu)
+
+
+# --- tiny random traces (for exhaustive pair checks) ---------------------------
+
+def random_tiny(seed: int, n_events: int | None = None, n_blocks: int | None = None,
+                block_threads: int | None = None, max_epochs: int | None = None,
+                units: int | None = None, p_global: float = 0.4, p_atomic: float = 0.15,
+                p_write: float = 0.35, unsorted: bool = False) -> Trace:
+    """A small random trace with valid fields; visit orders increase with random gaps."""
+    rng = np.random.default_rng(seed)
+    nb = n_blocks or int(rng.integers(1, 5))
+    bt = block_threads or int(rng.integers(1, 9))
+    me = max_epochs or int(rng.integers(1, 5))
+    su = units or int(rng.integers(1, 9))
+    gu = units or int(rng.integers(1, 9))
+    n = n_events if n_events is not None else int(rng.integers(0, 120))
+    counts = rng.integers(0, me, size=nb * bt).astype(np.uint32)
+    # most blocks agree on their count; some threads diverge
+    for b in range(nb):
+        if rng.random() < 0.7:
+            counts[b * bt:(b + 1) * bt] = counts[b * bt]
+    block = rng.integers(0, nb, size=n)
+    tid = rng.integers(0, bt, size=n)
+    gt = block * bt + tid
+    epoch = (rng.random(n) * (counts[gt].astype(np.float64) + 1)).astype(np.int64)
+    epoch = np.minimum(epoch, counts[gt])
+    space = (rng.random(n) < p_global).astype(np.int64)
+    r = rng.random(n)
+    act = np.where(r < p_atomic, ATOMIC, np.where(r < p_atomic + p_write, WRITE, READ))
+    unit = np.where(space == 1, rng.integers(0, gu, size=n), rng.integers(0, su, size=n))
+    vo = np.cumsum(rng.integers(1, 4, size=n)) if n else np.zeros(0, dtype=np.int64)
+    flags = 0
+    if unsorted:
+        # shuffle record order and let some visit orders collide
+        vo = rng.integers(0, max(1, n // 2), size=n)
+        flags = UNSORTED
+    ev = pack(unit, vo, block, tid, epoch, act, space)
+    return Trace(ev, counts, nb, bt, su, gu, me - 1 if me > 1 else 0, flags,
+                 meta=dict(kind="random_tiny", seed=seed))
+
+
+class Builder:
+    """Hand-built traces: records are appended in schedule order (visit order = serial)."""
+
+    def __init__(self, n_blocks: int, block_threads: int, shared_units: int, global_units: int = 0):
+        self.nb, self.bt, self.su, self.gu = n_blocks, block_threads, shared_units, global_units
+        self.rows: list[tuple] = []
+        self.counts = np.zeros(n_blocks * block_threads, dtype=np.uint32)
+
+    def access(self, block, tid, epoch, unit, action, space=SHARED):
+        self.rows.append((unit, len(self.rows), block, tid, epoch, action, space))
+        return self
+
+    def set_counts(self, count, block=None, tid=None):
+        if block is None:
+            self.counts[:] = count
+        elif tid is None:
+            self.counts[block * self.bt:(block + 1) * self.bt] = count
+        else:
+            self.counts[block * self.bt + tid] = count
+        return self
+
+    def trace(self, max_barriers=None) -> Trace:
+        if self.rows:
+            cols = list(zip(*self.rows))
+            ev = pack(*cols)
+        else:
+            ev = np.zeros((0, 4), dtype=np.uint32)
+        mb = int(self.counts.max()) if max_barriers is None and self.counts.size else (max_barriers or 0)
+        return Trace(ev, self.counts.copy(), self.nb, self.bt, self.su, self.gu, mb)
