@@ -1,0 +1,216 @@
+/*
+ * simulee.h - C ABI of the GB300 synchronization check over simulated
+ * memory-access records.
+ *
+ * The check is the detection half of the memory-model method of Wu et al.,
+ * "Characterizing and Detecting CUDA Program Bugs" (arXiv 1905.01833), Sec. 3.2:
+ *   - data races          Theorem 1 and Algorithm 5 (Sec. 3.2.3)
+ *   - redundant barriers  Algorithm 5 and the definition in Sec. 2
+ *   - barrier divergence  Algorithm 4 and the definition in Sec. 2
+ * run over a device-resident trace of access records, the Memory Model of
+ * Sec. 3.2.1 flattened to one record per access.
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named "device" must point to device memory of the context's
+ *     GPU. The report may also be page-locked host memory (cudaHostAlloc or a
+ *     pinned torch tensor), which the GPU writes directly.
+ *   - The caller owns every buffer: trace, outputs, report and workspace. The
+ *     library allocates no device memory.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream). The return value reports errors the host can see (bad
+ *     arguments, workspace too small, a failed launch). Errors found on the
+ *     device (a bad record, a wait that gave up, an output cap exceeded) are
+ *     written to report->status when the stream reaches them.
+ *   - Results are deterministic and identical to the CPU definition: the same
+ *     trace gives byte-identical outputs on every run.
+ *   - A workspace may be reused by later calls; two calls that share one
+ *     workspace must not overlap on the GPU.
+ */
+#ifndef SIMULEE_H
+#define SIMULEE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SIMULEE_OK = 0,
+    SIMULEE_EINVAL = 1,      /* bad argument or dimensions out of range (host) */
+    SIMULEE_EBADTRACE = 2,   /* a record or barrier count is invalid (report) */
+    SIMULEE_ENOMEM = 3,      /* workspace smaller than simulee_workspace_size (host) */
+    SIMULEE_ETRUNC = 4,      /* an output held more records than its cap (report) */
+    SIMULEE_ETIMEOUT = 5,    /* a bounded device-side wait gave up; outputs unreliable (report) */
+    SIMULEE_ECUDA = 6        /* a CUDA call failed (host) */
+} simulee_status;
+
+/* actions, spaces, scopes and race classes as stored in records and results */
+enum { SIMULEE_READ = 0, SIMULEE_WRITE = 1, SIMULEE_ATOMIC = 2 };
+enum { SIMULEE_SHARED = 0, SIMULEE_GLOBAL = 1 };
+enum { SIMULEE_INTRA = 0, SIMULEE_INTER = 1 };
+enum { SIMULEE_WW = 0, SIMULEE_RW = 1 };
+
+/* trace flags */
+#define SIMULEE_FLAG_UNSORTED 1u  /* visit orders need not increase with the record index */
+
+/*
+ * One access record (16 bytes, four little-endian words): one tuple
+ * <visit order, thread, action> of a Memory Unit (Sec. 3.2.1), tagged with its
+ * unit, block and barrier epoch.
+ *   w[0] unit         4-byte memory unit; < shared_units or < global_units
+ *   w[1] visit_order  serial position of the access in the simulated schedule
+ *                     (Algorithm 3's round robin); strictly increasing with the
+ *                     record index unless SIMULEE_FLAG_UNSORTED
+ *   w[2] block        linear block id, < n_blocks
+ *   w[3] bits  0..15  tid, linear thread id in the block, < block_threads
+ *        bits 16..27  epoch, number of barriers the thread has passed (the
+ *                     paper's per-unit visit order, Algorithm 4), <= the
+ *                     thread's barrier count
+ *        bits 28..29  action (READ, WRITE, ATOMIC; 3 is invalid)
+ *        bit  30      space (SHARED: per block; GLOBAL: whole grid)
+ *        bit  31      reserved, must be 0
+ */
+typedef struct { uint32_t w[4]; } simulee_event;
+
+/* A trace. All arrays are device memory owned by the caller. */
+typedef struct {
+    const simulee_event *events;     /* device, n_events records */
+    uint64_t n_events;               /* < 2^31 */
+    const uint32_t *barrier_counts;  /* device, n_blocks * block_threads entries: barriers each thread
+                                        passed (block-major, then tid) */
+    uint32_t n_blocks;               /* >= 1; n_blocks * block_threads <= 2^30 */
+    uint32_t block_threads;          /* 1 .. 1024 */
+    uint32_t shared_units;           /* shared-memory units per block */
+    uint32_t global_units;           /* global-memory units of the grid */
+    uint32_t max_barriers;           /* upper bound on every barrier count, <= 4095 */
+    uint32_t flags;                  /* SIMULEE_FLAG_* */
+} simulee_trace;
+
+/*
+ * One data race (32 bytes): the lowest conflicting pair of one group and class.
+ * A pair conflicts (Theorem 1 without its warp conditions) when its owners
+ * differ, at least one access writes or is atomic, and not both are atomic.
+ * Groups: INTRA = one (space, block, epoch, unit), owners are threads;
+ * INTER = one global unit across blocks in any epochs, owners are blocks.
+ * Class WW when both accesses modify the unit, RW when one reads.
+ * The pair is the one whose later access comes first in schedule order
+ * (visit_order, then record index), and among those the earliest partner.
+ * INTER records carry block = epoch = 0xFFFFFFFF.
+ * Canonical order of the list: (space, scope, block, epoch, unit, cls).
+ */
+typedef struct {
+    uint8_t space, scope, cls, pad;
+    uint32_t block, epoch, unit;
+    uint32_t vo_first, vo_second;      /* visit orders of the earlier / later access */
+    uint32_t gtid_first, gtid_second;  /* block * block_threads + tid of each access */
+} simulee_race;
+
+/* A divergent block (Algorithm 4: threads of one block reach different numbers
+   of barriers). Listed by block. */
+typedef struct { uint32_t block, min_count, max_count, first_min_tid; } simulee_divergence;
+
+/* A redundant barrier (Algorithm 5): barrier k of `block` separates epochs k and
+   k+1 and exists when some thread of the block passed it (k < max count). It is
+   redundant when merging its two epochs creates no conflicting pair in any unit
+   of the block. Barriers are judged one at a time. Listed by (block, barrier). */
+typedef struct { uint32_t block, barrier; } simulee_barrier;
+
+/* Output buffers (device). A NULL pointer with cap 0 skips that output's copy
+   but its count is still reported. */
+typedef struct {
+    simulee_race *races;             uint64_t races_cap;
+    simulee_divergence *divergence;  uint64_t divergence_cap;
+    simulee_barrier *redundant;      uint64_t redundant_cap;
+    uint32_t *grid_redundant;        uint64_t grid_redundant_cap;  /* barrier indices redundant in
+                                                                       every block that has them */
+} simulee_outputs;
+
+/*
+ * Per-call report (48 bytes), written by the device. status is OK,
+ * EBADTRACE (bad_kind 0: record bad_index; bad_kind 1: barrier_counts entry
+ * bad_index; counts are checked before records; outputs untouched and counts
+ * 0), ETIMEOUT, or ETRUNC (some count exceeds its cap; the first cap entries
+ * in canonical order were written). n_* are the true counts.
+ */
+typedef struct {
+    int32_t status;
+    uint32_t bad_kind;
+    uint64_t bad_index;
+    uint64_t n_races;
+    uint64_t n_divergence;
+    uint64_t n_redundant;
+    uint64_t n_grid_redundant;
+} simulee_report;
+
+typedef enum {
+    SIMULEE_PATH_AUTO = 0,  /* per trace: the segment-local hash path where it applies, else sorting */
+    SIMULEE_PATH_SORT = 1,  /* always the radix-sort path */
+    SIMULEE_PATH_HASH = 2   /* same as AUTO (the hash path still falls back where it cannot apply) */
+} simulee_path;
+
+typedef struct {
+    uint32_t wait_limit_us;   /* bound on every device-side wait; 0 selects 1,000,000 (1 s) */
+    uint32_t path;            /* simulee_path */
+    uint32_t test_withhold;   /* testing only: 0 = off; t+1 = tile t of the first sort pass never
+                                 publishes its counts, so a later tile's bounded wait gives up */
+    uint32_t reserved[5];
+} simulee_options;
+
+typedef struct simulee_ctx simulee_ctx;
+
+/* Create a context on `device` (host object; no device allocation). opt may be NULL. */
+simulee_status simulee_create(simulee_ctx **ctx, int device, const simulee_options *opt);
+
+/* Destroy a context. Pending work on streams is not waited for. */
+simulee_status simulee_destroy(simulee_ctx *ctx);
+
+/* Workspace bytes needed by simulee_check* for this trace's dimensions and size.
+   Only the dimensions, n_events and flags are read (no device access). */
+simulee_status simulee_workspace_size(simulee_ctx *ctx, const simulee_trace *trace, size_t *bytes);
+
+/*
+ * The whole check in one pass: races (Theorem 1, Algorithm 5), divergence
+ * (Algorithm 4) and redundant barriers (Algorithm 5) over one trace.
+ * ws: device workspace of at least simulee_workspace_size bytes, 256-byte aligned.
+ */
+simulee_status simulee_check(simulee_ctx *ctx, const simulee_trace *trace, const simulee_outputs *out,
+                             simulee_report *report, void *ws, size_t ws_bytes, void *stream);
+
+/* Races only (Theorem 1; Algorithm 5 race part). report->n_races is the true count. */
+simulee_status simulee_check_races(simulee_ctx *ctx, const simulee_trace *trace, simulee_race *out,
+                                   uint64_t cap, simulee_report *report, void *ws, size_t ws_bytes,
+                                   void *stream);
+
+/* Divergent blocks only (Algorithm 4, Sec. 2). Reads barrier_counts and validates the trace. */
+simulee_status simulee_check_divergence(simulee_ctx *ctx, const simulee_trace *trace,
+                                        simulee_divergence *out, uint64_t cap, simulee_report *report,
+                                        void *ws, size_t ws_bytes, void *stream);
+
+/* Redundant barriers only (Algorithm 5 barrier part). grid may be NULL (grid_cap 0). */
+simulee_status simulee_check_redundant_barriers(simulee_ctx *ctx, const simulee_trace *trace,
+                                                simulee_barrier *out, uint64_t cap, uint32_t *grid,
+                                                uint64_t grid_cap, simulee_report *report, void *ws,
+                                                size_t ws_bytes, void *stream);
+
+/*
+ * Batched check: n_traces independent traces checked together, each with its
+ * own outputs and report (reports: device array of n_traces). Results equal
+ * those of checking each trace alone. traces and outs are host arrays read
+ * during the call; the trace data they point to is device memory.
+ */
+simulee_status simulee_batch_workspace_size(simulee_ctx *ctx, const simulee_trace *traces, uint32_t n_traces,
+                                            size_t *bytes);
+simulee_status simulee_check_batch(simulee_ctx *ctx, const simulee_trace *traces, uint32_t n_traces,
+                                   const simulee_outputs *outs, simulee_report *reports, void *ws,
+                                   size_t ws_bytes, void *stream);
+
+/* Static description of a status code. */
+const char *simulee_status_str(simulee_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIMULEE_H */

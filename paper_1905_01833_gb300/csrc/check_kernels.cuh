@@ -1,0 +1,478 @@
+// check_kernels.cuh - ingest, segmented reduction and output kernels of the check.
+#pragma once
+#include "common.cuh"
+
+namespace simk {
+
+// ---------------------------------------------------------------------------
+// Barrier counts: per-block min / max / first thread at the min (Algorithm 4's
+// divergence test is "threads of a block reached different barrier counts"),
+// plus validation of every count. One warp per block.
+// ---------------------------------------------------------------------------
+__global__ void k_block_stats(const uint32_t *__restrict__ counts, Layout L, uint4 *stats, Ctl *ctl) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t b = warp; b < L.nb; b += nwarps) {
+        uint32_t mn = 0xFFFFFFFFu, mx = 0, first = 0xFFFFFFFFu;
+        for (uint32_t t = lane; t < L.bt; t += 32) {
+            const uint32_t c = counts[b * L.bt + t];
+            if (c > L.maxb) atomicMax(&ctl->bad_cnt, ~(unsigned long long)(b * L.bt + t));
+            if (c < mn) { mn = c; first = t; }
+            mx = max(mx, c);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint32_t omn = __shfl_xor_sync(0xFFFFFFFFu, mn, o);
+            const uint32_t ofi = __shfl_xor_sync(0xFFFFFFFFu, first, o);
+            mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+            if (omn < mn || (omn == mn && ofi < first)) { mn = omn; first = ofi; }
+        }
+        if (lane == 0) {
+            stats[b] = make_uint4(mn, mx, first, 0);
+            atomicMax(&ctl->max_count, mx);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t digit_of(uint64_t k, uint32_t p) { return (uint32_t)(k >> (8 * p)) & (RADIX - 1); }
+
+// x << s for s in [0, 64], defined for s == 64
+__device__ __forceinline__ uint64_t shl(uint64_t x, uint32_t s) { return s >= 64 ? 0ull : x << s; }
+
+// Add the digits of every pass of a key to shared histograms; when the whole
+// warp's participating lanes share a digit, one lane adds the warp's count.
+__device__ __forceinline__ void hist_add(uint32_t *sh, uint64_t key, uint32_t npass, bool part, uint32_t pmask) {
+    if (pmask == 0) return;
+    const int leader = __ffs(pmask) - 1;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t p = 0; p < npass; p++) {
+        const uint32_t d = part ? digit_of(key, p) : 0u;
+        const uint32_t dl = __shfl_sync(0xFFFFFFFFu, d, leader);
+        const bool uni = __all_sync(0xFFFFFFFFu, !part || d == dl);
+        if (uni) {
+            if (lane == leader) atomicAdd(&sh[p * RADIX + d], (uint32_t)__popc(pmask));
+        } else if (part) {
+            atomicAdd(&sh[p * RADIX + d], 1u);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Ingest: read every record once (16-byte loads), validate it, and route it:
+// shared records to the intra stream S keyed (block, unit, epoch); global
+// records to the intra stream G keyed (block, unit, epoch) and to the
+// inter-block stream X keyed (unit). Builds the digit histograms of all radix
+// passes. Persistent CTAs over tiles of 2048 records.
+// ---------------------------------------------------------------------------
+constexpr int IN_THREADS = 256;
+constexpr int IN_ITEMS = 8;
+constexpr int IN_TILE = IN_THREADS * IN_ITEMS;
+constexpr int IN_MAXP = 20;   // S + G + X passes histogrammed here
+
+template <class KS, class KG, bool ROUTE>
+__global__ void __launch_bounds__(IN_THREADS)
+k_ingest(const uint4 *__restrict__ ev, const uint32_t *__restrict__ counts, const uint32_t *__restrict__ rank,
+         Layout L, Ctl *ctl, KS *sk, uint64_t *sv, KG *gk, uint64_t *gv, uint32_t *xk, uint64_t *xv,
+         uint32_t *hist) {
+    __shared__ uint32_t sh[IN_MAXP * RADIX];
+    __shared__ uint32_t wtot[IN_THREADS / 32][2];
+    __shared__ uint32_t cbase[2];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint32_t lt = lanemask_lt();
+    const uint32_t np_s = L.np_s, np_g = L.np_g, np_x = L.np_x;
+    uint32_t *hs = sh, *hg = sh + np_s * RADIX, *hx = hg + np_g * RADIX;
+    for (int i = tid; i < IN_MAXP * RADIX; i += IN_THREADS) sh[i] = 0;
+    __syncthreads();
+    const bool sorted = (L.flags & 1u) == 0;
+    const uint64_t ntiles = (L.n + IN_TILE - 1) / IN_TILE;
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        uint32_t cS = 0, cG = 0;
+        uint32_t rS[IN_ITEMS], rG[IN_ITEMS];
+        uint64_t val[IN_ITEMS];
+        KS ks[IN_ITEMS];
+        KG kg[IN_ITEMS];
+        uint32_t unit[IN_ITEMS];
+        uint32_t route = 0;   // bit j: S, bit 8+j: G
+#pragma unroll
+        for (int j = 0; j < IN_ITEMS; j++) {
+            const uint64_t idx = tile * IN_TILE + (uint64_t)j * IN_THREADS + tid;
+            uint4 e = make_uint4(0, 0, 0, 0);
+            const bool in = idx < L.n;
+            if (in) e = ev[idx];
+            uint32_t prev_vo = __shfl_up_sync(0xFFFFFFFFu, e.y, 1);
+            if (lane == 0 && in && idx > 0) prev_vo = ev[idx - 1].y;
+            const uint32_t u = e.x, vo = e.y, blk = e.z, w3 = e.w;
+            const uint32_t t = w3 & 0xFFFFu, ep = (w3 >> 16) & 0xFFFu, act = (w3 >> 28) & 3u;
+            const uint32_t space = (w3 >> 30) & 1u, resv = w3 >> 31;
+            bool ok = in && blk < L.nb && t < L.bt && act != 3u && resv == 0u && (space ? u < L.gu : u < L.su);
+            const uint32_t gtid = blk * L.bt + t;
+            if (ok && ep > counts[gtid]) ok = false;
+            if (in && sorted && idx > 0 && vo <= prev_vo) ok = false;
+            if (in && !ok) atomicMax(&ctl->bad_rec, ~(unsigned long long)idx);
+            const bool isS = ROUTE && ok && space == 0u, isG = ROUTE && ok && space == 1u;
+            const uint32_t bS = __ballot_sync(0xFFFFFFFFu, isS), bG = __ballot_sync(0xFFFFFFFFu, isG);
+            rS[j] = cS + __popc(bS & lt);
+            rG[j] = cG + __popc(bG & lt);
+            cS += __popc(bS);
+            cG += __popc(bG);
+            const uint32_t pos = sorted ? vo : (in ? rank[idx] : 0u);
+            val[j] = make_payload(act, gtid, pos);
+            ks[j] = (KS)(shl(blk, L.bus + L.be) | shl(u, L.be) | ep);
+            kg[j] = (KG)(shl(blk, L.bug + L.be) | shl(u, L.be) | ep);
+            unit[j] = u;
+            route |= (isS ? 1u : 0u) << j;
+            route |= (isG ? 1u : 0u) << (8 + j);
+            hist_add(hs, (uint64_t)ks[j], np_s, isS, bS);
+            hist_add(hg, (uint64_t)kg[j], np_g, isG, bG);
+            hist_add(hx, (uint64_t)u, np_x, isG, bG);
+        }
+        if (lane == 0) { wtot[w][0] = cS; wtot[w][1] = cG; }
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t a = 0, b = 0;
+            for (int i = 0; i < IN_THREADS / 32; i++) {
+                const uint32_t x = wtot[i][0], y = wtot[i][1];
+                wtot[i][0] = a; wtot[i][1] = b;
+                a += x; b += y;
+            }
+            cbase[0] = a ? atomicAdd(&ctl->n_s, a) : 0u;
+            cbase[1] = b ? atomicAdd(&ctl->n_g, b) : 0u;
+        }
+        __syncthreads();
+        const uint32_t oS = cbase[0] + wtot[w][0], oG = cbase[1] + wtot[w][1];
+#pragma unroll
+        for (int j = 0; j < IN_ITEMS; j++) {
+            if (route & (1u << j)) {
+                sk[oS + rS[j]] = ks[j];
+                sv[oS + rS[j]] = val[j];
+            }
+            if (route & (1u << (8 + j))) {
+                gk[oG + rG[j]] = kg[j];
+                gv[oG + rG[j]] = val[j];
+                xk[oG + rG[j]] = unit[j];
+                xv[oG + rG[j]] = val[j];
+            }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    const uint32_t tot = (np_s + np_g + np_x) * RADIX;
+    for (uint32_t i = tid; i < tot; i += IN_THREADS) {
+        const uint32_t c = sh[i];
+        if (c) {
+            const uint32_t p = i / RADIX;
+            const uint32_t gp = p < np_s ? L.p0_s + p : (p < np_s + np_g ? L.p0_g + (p - np_s) : L.p0_x + (p - np_s - np_g));
+            atomicAdd(&hist[gp * RADIX + (i % RADIX)], c);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Race staging: canonical key + payload (vo_first, vo_second, gtid_first, gtid_second).
+// Canonical key bits, low to high: cls(1) unit(bu) epoch(be) block(bb) scope(1) space(1).
+// ---------------------------------------------------------------------------
+struct RaceStage {
+    uint64_t *keys;
+    uint64_t *idx;
+    uint4 *pay;
+    uint64_t cap;
+    const uint32_t *pos_to_vo;   // unsorted traces: schedule position -> visit order (else NULL)
+    uint64_t n_pos;              // entries of pos_to_vo
+};
+
+__device__ __forceinline__ uint64_t race_key(const Layout &L, uint32_t space, uint32_t scope, uint32_t block,
+                                             uint32_t epoch, uint32_t unit, uint32_t cls) {
+    uint64_t k = cls;
+    k |= (uint64_t)unit << 1;
+    k |= (uint64_t)epoch << (1 + L.bu);
+    k |= (uint64_t)block << (1 + L.bu + L.be);
+    k |= (uint64_t)scope << (1 + L.bu + L.be + L.bb);
+    k |= (uint64_t)space << (2 + L.bu + L.be + L.bb);
+    return k;
+}
+
+__device__ __forceinline__ void emit_race(const RaceStage &rs, Ctl *ctl, uint64_t key, uint64_t p, uint64_t q) {
+    const uint32_t slot = atomicAdd(&ctl->n_races, 1u);
+    if (slot < rs.cap) {
+        rs.keys[slot] = key;
+        rs.idx[slot] = slot;
+        uint32_t vp = item_pos(p), vq = item_pos(q);
+        if (rs.pos_to_vo) {
+            vp = vp < rs.n_pos ? rs.pos_to_vo[vp] : 0u;
+            vq = vq < rs.n_pos ? rs.pos_to_vo[vq] : 0u;
+        }
+        rs.pay[slot] = make_uint4(vp, vq, item_gtid(p), item_gtid(q));
+    }
+}
+
+template <class Own>
+__device__ __forceinline__ void emit_group(const Layout &L, const RaceStage &rs, Ctl *ctl, const Top2 &s,
+                                           const Own &own, uint32_t space, uint32_t scope, uint32_t block,
+                                           uint32_t epoch, uint32_t unit) {
+#pragma unroll
+    for (int cls = 0; cls < 2; cls++) {
+        uint64_t p, q;
+        if (lowest_pair(s, cls, own, p, q)) emit_race(rs, ctl, race_key(L, space, scope, block, epoch, unit, cls), p, q);
+    }
+}
+
+// barrier k of block b is needed (not redundant)
+__device__ __forceinline__ void mark_needed(uint32_t *nonred, const Layout &L, uint32_t block, uint32_t k) {
+    if (block < L.nb && (k >> 5) < L.words) atomicOr(&nonred[(uint64_t)block * L.words + (k >> 5)], 1u << (k & 31));
+}
+
+// ---------------------------------------------------------------------------
+// Intra-block reduction over a stream sorted by (block, unit, epoch): one walker
+// per (block, unit) run visits its epochs in order, reduces each epoch group to
+// its top-2 summary, emits the group's races, and tests each pair of
+// consecutive epochs k, k+1 for a conflict (barrier k not redundant).
+// ---------------------------------------------------------------------------
+template <class K>
+__global__ void __launch_bounds__(256)
+k_reduce_intra(const K *__restrict__ keys, const uint64_t *__restrict__ vals, const uint32_t *n_ptr, Layout L,
+               uint32_t space, uint32_t bu, Ctl *ctl, uint32_t *nonred, RaceStage rs) {
+    if (must_stop(ctl)) return;
+    const uint64_t n = *n_ptr;
+    const uint32_t be = L.be;
+    const K emask = (K)((1ull << be) - 1);
+    const uint64_t umask = (1ull << bu) - 1;
+    const OwnThread own;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const K ki = keys[i];
+        const K sk = ki >> be;
+        if (i > 0 && (keys[i - 1] >> be) == sk) continue;   // not the head of a (block, unit) run
+        const uint32_t block = (uint32_t)((uint64_t)sk >> bu), unit = (uint32_t)((uint64_t)sk & umask);
+        Top2 cur, prev;
+        cur.clear();
+        prev.clear();
+        int cur_e = -1, prev_e = -1;
+        for (uint64_t j = i; j < n; j++) {
+            const K kj = keys[j];
+            if ((kj >> be) != sk) break;
+            const int e = (int)(kj & emask);
+            if (e != cur_e) {
+                if (cur_e >= 0) {
+                    emit_group(L, rs, ctl, cur, own, space, 0u, block, (uint32_t)cur_e, unit);
+                    if (prev_e >= 0 && cur_e == prev_e + 1 && any_conflict(prev, cur))
+                        mark_needed(nonred, L, block, (uint32_t)prev_e);
+                    prev = cur;
+                    prev_e = cur_e;
+                }
+                cur.clear();
+                cur_e = e;
+            }
+            const uint64_t v = vals[j];
+            top2_add(cur, payload_act(v), payload_item(v), own);
+        }
+        emit_group(L, rs, ctl, cur, own, space, 0u, block, (uint32_t)cur_e, unit);
+        if (prev_e >= 0 && cur_e == prev_e + 1 && any_conflict(prev, cur))
+            mark_needed(nonred, L, block, (uint32_t)prev_e);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Inter-block reduction over the global stream sorted by unit: one walker per
+// unit reduces all its records to a top-2 summary whose owners are blocks, and
+// emits the unit's inter-block races.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_reduce_inter(const uint32_t *__restrict__ keys, const uint64_t *__restrict__ vals, const uint32_t *n_ptr,
+               Layout L, Ctl *ctl, RaceStage rs) {
+    if (must_stop(ctl)) return;
+    const uint64_t n = *n_ptr;
+    const OwnBlock own{L.bt};
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = keys[i];
+        if (i > 0 && keys[i - 1] == u) continue;
+        Top2 s;
+        s.clear();
+        for (uint64_t j = i; j < n && keys[j] == u; j++) {
+            const uint64_t v = vals[j];
+            top2_add(s, payload_act(v), payload_item(v), own);
+        }
+        emit_group(L, rs, ctl, s, own, 1u, 1u, 0u, 0u, u);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Outputs
+// ---------------------------------------------------------------------------
+__global__ void k_write_races(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ idx,
+                              const uint4 *__restrict__ pay, Layout L, Ctl *ctl, uint8_t *out, uint64_t cap) {
+    if (must_stop(ctl)) return;
+    const uint64_t n = min((uint64_t)ctl->n_races, min(cap, L.race_cap));
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = keys[i];
+        const uint64_t ix = idx[i];
+        if (ix >= L.race_cap) continue;
+        const uint4 p = pay[ix];
+        const uint32_t cls = (uint32_t)(k & 1u);
+        const uint32_t unit = (uint32_t)((k >> 1) & ((1ull << L.bu) - 1));
+        uint32_t epoch = (uint32_t)((k >> (1 + L.bu)) & ((1ull << L.be) - 1));
+        uint32_t block = (uint32_t)((k >> (1 + L.bu + L.be)) & ((1ull << L.bb) - 1));
+        const uint32_t scope = (uint32_t)((k >> (1 + L.bu + L.be + L.bb)) & 1u);
+        const uint32_t space = (uint32_t)((k >> (2 + L.bu + L.be + L.bb)) & 1u);
+        if (scope) { block = 0xFFFFFFFFu; epoch = 0xFFFFFFFFu; }
+        uint4 *o = reinterpret_cast<uint4 *>(out + 32 * i);
+        o[0] = make_uint4(space | (scope << 8) | (cls << 16), block, epoch, unit);
+        o[1] = p;
+    }
+}
+
+// per block: divergence flag and number of redundant barriers
+__global__ void k_block_counts(const uint4 *stats, const uint32_t *nonred, Layout L, Ctl *ctl, uint32_t *cnt_div,
+                               uint32_t *cnt_red) {
+    if (trace_bad(ctl)) return;
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < L.nb; b += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 s = stats[b];
+        cnt_div[b] = s.x != s.y ? 1u : 0u;
+        uint32_t nr = 0;
+        for (uint32_t wd = 0; wd < L.words; wd++) {
+            const uint32_t lo = wd * 32;
+            if (lo >= s.y) break;
+            const uint32_t live = (s.y - lo >= 32) ? 0xFFFFFFFFu : ((1u << (s.y - lo)) - 1u);
+            nr += __popc(~nonred[b * L.words + wd] & live);
+        }
+        cnt_red[b] = nr;
+    }
+}
+
+// Single-CTA exclusive scan (1024 threads) of two count arrays of length m;
+// totals go to *tot_a, *tot_b.
+__global__ void __launch_bounds__(1024) k_scan2(const uint32_t *a, const uint32_t *b, uint64_t m, uint32_t *oa,
+                                                uint32_t *ob, unsigned int *tot_a, unsigned int *tot_b, Ctl *ctl) {
+    __shared__ uint32_t ws[2][32];
+    __shared__ uint32_t carry[2];
+    if (trace_bad(ctl)) return;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) { carry[0] = 0; carry[1] = 0; }
+    __syncthreads();
+    for (uint64_t base = 0; base < m; base += 1024) {
+        const uint64_t i = base + tid;
+        uint32_t x = i < m ? a[i] : 0u, y = i < m ? b[i] : 0u;
+        uint32_t sx = x, sy = y;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t tx = __shfl_up_sync(0xFFFFFFFFu, sx, o), ty = __shfl_up_sync(0xFFFFFFFFu, sy, o);
+            if (lane >= o) { sx += tx; sy += ty; }
+        }
+        if (lane == 31) { ws[0][w] = sx; ws[1][w] = sy; }
+        __syncthreads();
+        if (w == 0) {
+            uint32_t vx = ws[0][lane], vy = ws[1][lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t tx = __shfl_up_sync(0xFFFFFFFFu, vx, o), ty = __shfl_up_sync(0xFFFFFFFFu, vy, o);
+                if (lane >= o) { vx += tx; vy += ty; }
+            }
+            ws[0][lane] = vx;
+            ws[1][lane] = vy;
+        }
+        __syncthreads();
+        const uint32_t px = (w ? ws[0][w - 1] : 0u) + sx - x + carry[0];
+        const uint32_t py = (w ? ws[1][w - 1] : 0u) + sy - y + carry[1];
+        if (i < m) { oa[i] = px; ob[i] = py; }
+        __syncthreads();
+        if (tid == 0) { carry[0] += ws[0][31]; carry[1] += ws[1][31]; }
+        __syncthreads();
+    }
+    if (tid == 0) { *tot_a = carry[0]; *tot_b = carry[1]; }
+}
+
+__global__ void k_block_write(const uint4 *stats, const uint32_t *nonred, Layout L, Ctl *ctl, const uint32_t *ofs_div,
+                              const uint32_t *ofs_red, uint4 *out_div, uint64_t cap_div, uint2 *out_red,
+                              uint64_t cap_red) {
+    if (trace_bad(ctl)) return;
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < L.nb; b += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 s = stats[b];
+        if (s.x != s.y && ofs_div[b] < cap_div) out_div[ofs_div[b]] = make_uint4((uint32_t)b, s.x, s.y, s.z);
+        uint64_t o = ofs_red[b];
+        if (o >= cap_red) continue;
+        for (uint32_t k = 0; k < s.y && o < cap_red; k++)
+            if (!((nonred[b * L.words + (k >> 5)] >> (k & 31)) & 1u)) out_red[o++] = make_uint2((uint32_t)b, k);
+    }
+}
+
+// grid-wide: OR of the non-redundant bits and of "barrier exists" over blocks
+__global__ void k_grid_or(const uint4 *stats, const uint32_t *nonred, Layout L, Ctl *ctl, uint32_t *gnr,
+                          uint32_t *ghas) {
+    if (trace_bad(ctl)) return;
+    const uint64_t tot = (uint64_t)L.nb * L.words;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t b = i / L.words;
+        const uint32_t wd = (uint32_t)(i % L.words), lo = wd * 32, mx = stats[b].y;
+        if (lo >= mx) continue;
+        const uint32_t live = (mx - lo >= 32) ? 0xFFFFFFFFu : ((1u << (mx - lo)) - 1u);
+        const uint32_t nr = nonred[i] & live;
+        if (nr) atomicOr(&gnr[wd], nr);
+        atomicOr(&ghas[wd], live);
+    }
+}
+
+// single CTA: list every barrier k that exists somewhere and is redundant everywhere
+__global__ void __launch_bounds__(1024) k_grid_list(const uint32_t *gnr, const uint32_t *ghas, Layout L, Ctl *ctl,
+                                                    uint32_t *out, uint64_t cap) {
+    __shared__ uint32_t ws[32];
+    __shared__ uint32_t carry;
+    if (trace_bad(ctl)) return;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    const uint32_t nk = L.words * 32;
+    for (uint32_t base = 0; base < nk; base += 1024) {
+        const uint32_t k = base + tid;
+        const bool red = k < nk && ((ghas[k >> 5] >> (k & 31)) & 1u) && !((gnr[k >> 5] >> (k & 31)) & 1u);
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, red);
+        if (lane == 0) ws[w] = __popc(bal);
+        __syncthreads();
+        uint32_t pre = carry;
+        for (int i = 0; i < w; i++) pre += ws[i];
+        pre += __popc(bal & lanemask_lt());
+        if (red && pre < cap) out[pre] = k;
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t s = 0;
+            for (int i = 0; i < 32; i++) s += ws[i];
+            carry += s;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) ctl->n_grid = carry;
+}
+
+// final report: status and true counts
+struct ReportArgs {
+    uint64_t cap_races, cap_div, cap_red, cap_grid;
+    uint32_t want_races, want_div, want_red;
+};
+
+__global__ void k_report(Ctl *ctl, ReportArgs a, uint8_t *report) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    volatile Ctl *c = ctl;
+    int32_t status = 0;
+    uint32_t kind = 0;
+    uint64_t bad = 0, nr = 0, nd = 0, nred = 0, ng = 0;
+    if (c->bad_cnt) {
+        status = 2; kind = 1; bad = ~c->bad_cnt;
+    } else if (c->bad_rec) {
+        status = 2; kind = 0; bad = ~c->bad_rec;
+    } else {
+        if (a.want_races) nr = c->n_races;
+        if (a.want_div) nd = c->n_div;
+        if (a.want_red) { nred = c->n_red; ng = c->n_grid; }
+        if (c->timeout) status = 5;
+        else if (nr > a.cap_races || nd > a.cap_div || nred > a.cap_red || ng > a.cap_grid) status = 4;
+    }
+    int32_t *r32 = reinterpret_cast<int32_t *>(report);
+    uint64_t *r64 = reinterpret_cast<uint64_t *>(report);
+    r32[0] = status;
+    reinterpret_cast<uint32_t *>(report)[1] = kind;
+    r64[1] = bad;
+    r64[2] = nr;
+    r64[3] = nd;
+    r64[4] = nred;
+    r64[5] = ng;
+}
+
+}  // namespace simk

@@ -1,0 +1,203 @@
+// common.cuh - shared device definitions for the synchronization check kernels.
+//
+// Items and the per-group summary
+// -------------------------------
+// An access becomes an item: a 64-bit word (schedule position << 32 | gtid),
+// where the schedule position is the visit order (or, for unsorted traces,
+// the rank of (visit order, record index)). Items of one group compare by
+// schedule position because positions are unique.
+//
+// Per group and per action category c in {read, write, atomic} the kernels
+// keep a "top-2" summary: first[c] = the earliest item, second[c] = the
+// earliest item whose owner differs from first[c]'s owner. The summary of a
+// union is the summary of the union of the summaries, so groups reduce in any
+// order (no stable sort, no ordered scan needed).
+//
+// Why the summary is enough. Let (p, q) be the lowest conflicting pair of a
+// class in a group (q the later access, the pair minimising (q, p)). Suppose q
+// is not in the top-2 of its category. Then first and second of that category
+// are either both earlier than q with distinct owners, or first is earlier and
+// shares q's owner. In both cases some top-2 item c earlier than q has an owner
+// different from p's, lies in q's category, and so conflicts with p in the
+// same class; the pair (p, c) ends before q, contradicting minimality. The
+// same argument applied to p for the fixed q shows p is in the top-2 of its
+// category. So the lowest pair of each class is among the pairs drawn from the
+// at most six summary items, and whether two epochs' groups hold any
+// conflicting pair is likewise decided by their summaries (Theorem 1 and
+// Algorithm 5 of the paper, restated over summaries).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace simk {
+
+constexpr uint32_t ACT_R = 0, ACT_W = 1, ACT_A = 2;
+constexpr uint64_t EMPTY = ~0ull;
+constexpr int RADIX_BITS = 8;
+constexpr int RADIX = 1 << RADIX_BITS;
+constexpr int MAX_PASSES = 40;   // all sort passes of one call
+
+// Device control block at the start of the workspace; zeroed by every call.
+struct Ctl {
+    unsigned long long bad_rec;   // ~index of the first bad record (atomicMax), 0 = none
+    unsigned long long bad_cnt;   // ~index of the first bad barrier count, 0 = none
+    unsigned int timeout;         // a bounded wait gave up
+    unsigned int max_count;       // largest barrier count of the trace
+    unsigned int n_s, n_g;        // shared / global stream sizes (n_x == n_g)
+    unsigned int n_races;         // staged race records
+    unsigned int n_div, n_red, n_grid;
+    unsigned int n_q;                // records in the schedule-rank sort (unsorted traces)
+    unsigned int tiles[MAX_PASSES];  // onesweep tile counters, one per pass
+    unsigned int pad[5];
+};
+
+// Dimensions, bit layouts and workspace offsets of one call (host-computed).
+struct Layout {
+    uint64_t n;                      // records
+    uint32_t nb, bt, su, gu, maxb, flags;
+    uint32_t bb, bus, bug, be, bu;   // bit widths: block, shared unit, global unit, epoch, max(unit)
+    uint32_t bits_s, bits_g, bits_x, bits_r;
+    uint32_t np_s, np_g, np_x, np_r; // radix passes per stream
+    uint32_t p0_s, p0_g, p0_x, p0_r; // first global pass index of each stream
+    uint32_t wide_s, wide_g;         // 64-bit keys
+    uint32_t words;                  // 32-bit words per block in the barrier bitmaps
+    uint64_t race_cap;               // staging capacity for race records
+    uint64_t status_tiles;           // tiles covered by the look-back status array
+    size_t off_ctl, off_stats, off_nonred, off_gridnr, off_gridhas, off_cnt_div, off_cnt_red,
+        off_ofs_div, off_ofs_red, off_hist, off_dbase, off_status;
+    size_t off_sk[2], off_sv[2], off_gk[2], off_gv[2], off_xk[2], off_xv[2];
+    size_t off_rk[2], off_rv[2], off_rp;
+    size_t total;
+};
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ bool trace_bad(const Ctl *ctl) {
+    const volatile Ctl *c = ctl;
+    return c->bad_rec != 0 || c->bad_cnt != 0;
+}
+
+// stop work that depends on sorted data: bad trace, or a wait gave up
+__device__ __forceinline__ bool must_stop(const Ctl *ctl) {
+    const volatile Ctl *c = ctl;
+    return c->bad_rec != 0 || c->bad_cnt != 0 || c->timeout != 0;
+}
+
+// payload of a stream element: (act << 30 | gtid) << 32 | schedule position
+__device__ __forceinline__ uint64_t make_payload(uint32_t act, uint32_t gtid, uint32_t pos) {
+    return ((uint64_t)((act << 30) | gtid) << 32) | pos;
+}
+__device__ __forceinline__ uint32_t payload_act(uint64_t v) { return (uint32_t)(v >> 62); }
+// item = position << 32 | gtid
+__device__ __forceinline__ uint64_t payload_item(uint64_t v) {
+    return ((uint64_t)(uint32_t)v << 32) | ((uint32_t)(v >> 32) & 0x3FFFFFFFu);
+}
+__device__ __forceinline__ uint32_t item_pos(uint64_t x) { return (uint32_t)(x >> 32); }
+__device__ __forceinline__ uint32_t item_gtid(uint64_t x) { return (uint32_t)x; }
+
+// owners: threads (intra-block groups) or blocks (inter-block groups)
+struct OwnThread {
+    __device__ __forceinline__ uint32_t operator()(uint64_t x) const { return (uint32_t)x; }
+};
+struct OwnBlock {
+    uint32_t bt;
+    __device__ __forceinline__ uint32_t operator()(uint64_t x) const { return (uint32_t)x / bt; }
+};
+
+struct Top2 {
+    uint64_t a[3], b[3];   // per category: first, second (EMPTY when absent)
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int c = 0; c < 3; c++) { a[c] = EMPTY; b[c] = EMPTY; }
+    }
+    __device__ __forceinline__ bool empty() const { return a[0] == EMPTY && a[1] == EMPTY && a[2] == EMPTY; }
+};
+
+template <class Own>
+__device__ __forceinline__ void top2_insert(uint64_t &a, uint64_t &b, uint64_t x, const Own &own) {
+    if (x < a) {
+        if (a != EMPTY && own(a) != own(x)) b = a;
+        a = x;
+    } else if (x != a && own(x) != own(a) && x < b) {
+        b = x;
+    }
+}
+
+template <class Own>
+__device__ __forceinline__ void top2_add(Top2 &s, uint32_t act, uint64_t x, const Own &own) {
+    if (act == ACT_R) top2_insert(s.a[0], s.b[0], x, own);
+    else if (act == ACT_W) top2_insert(s.a[1], s.b[1], x, own);
+    else top2_insert(s.a[2], s.b[2], x, own);
+}
+
+template <class Own>
+__device__ __forceinline__ void top2_merge(Top2 &s, const Top2 &o, const Own &own) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        if (o.a[c] != EMPTY) top2_insert(s.a[c], s.b[c], o.a[c], own);
+        if (o.b[c] != EMPTY) top2_insert(s.a[c], s.b[c], o.b[c], own);
+    }
+}
+
+// The lowest pair of class cls (0 WW, 1 RW) among summary items.
+// Returns false when the group holds no conflicting pair of that class.
+template <class Own>
+__device__ __forceinline__ bool lowest_pair(const Top2 &s, int cls, const Own &own, uint64_t &p, uint64_t &q) {
+    uint64_t bq = EMPTY, bp = EMPTY;
+    // candidate list: categories 1 (write) and 2 (atomic) are the modifying ones
+    uint64_t it[6] = {s.a[0], s.b[0], s.a[1], s.b[1], s.a[2], s.b[2]};
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            if (j <= i) continue;
+            const int ci = i >> 1, cj = j >> 1;
+            const uint64_t x = it[i], y = it[j];
+            if (x == EMPTY || y == EMPTY) continue;
+            const bool mi = ci != 0, mj = cj != 0;
+            if (!mi && !mj) continue;                 // read & read
+            if (ci == 2 && cj == 2) continue;         // atomic & atomic
+            const int pc = (mi && mj) ? 0 : 1;
+            if (pc != cls) continue;
+            if (own(x) == own(y)) continue;
+            const uint64_t lo = x < y ? x : y, hi = x < y ? y : x;
+            if (hi < bq || (hi == bq && lo < bp)) { bq = hi; bp = lo; }
+        }
+    }
+    if (bq == EMPTY) return false;
+    p = bp;
+    q = bq;
+    return true;
+}
+
+// Does any item of summary P conflict with any item of summary Q (owners: threads)?
+__device__ __forceinline__ bool any_conflict(const Top2 &P, const Top2 &Q) {
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        const uint64_t x = (i & 1) ? P.b[i >> 1] : P.a[i >> 1];
+        if (x == EMPTY) continue;
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            const uint64_t y = (j & 1) ? Q.b[j >> 1] : Q.a[j >> 1];
+            if (y == EMPTY) continue;
+            const int ci = i >> 1, cj = j >> 1;
+            if (ci == 0 && cj == 0) continue;
+            if (ci == 2 && cj == 2) continue;
+            if ((uint32_t)x == (uint32_t)y) continue;
+            return true;
+        }
+    }
+    return false;
+}
+
+}  // namespace simk

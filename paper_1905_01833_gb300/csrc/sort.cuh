@@ -1,0 +1,194 @@
+// sort.cuh - hand-written onesweep LSD radix sort (one pass per 8-bit digit).
+//
+// Each pass is one persistent kernel. A CTA takes tiles of 4096 elements in
+// the order it claims them (atomic tile counter), ranks its elements per
+// digit (warp match + per-warp counters), publishes its per-digit counts,
+// and finds the counts of all earlier tiles by decoupled look-back over a
+// status array. A status word is (tag:8 | flag:2 | count:54), where the tag
+// is the pass number of the current call, so words left over from an earlier
+// pass are never mistaken for this pass's. Every wait on a predecessor is
+// bounded by wall time (%globaltimer); a wait that gives up sets ctl->timeout,
+// which makes every other waiter stop at once, and the call reports ETIMEOUT.
+// Ranking within a tile is stable, tiles are ordered by claim order, so each
+// pass is stable and the LSD sort is correct.
+#pragma once
+#include "common.cuh"
+
+namespace simk {
+
+constexpr int OS_THREADS = 256;
+constexpr int OS_WARPS = OS_THREADS / 32;
+constexpr int OS_ITEMS = 16;
+constexpr int OS_TILE = OS_THREADS * OS_ITEMS;  // 4096
+
+constexpr uint64_t ST_AGG = 1ull, ST_INC = 2ull;
+__device__ __forceinline__ uint64_t st_make(uint32_t tag, uint64_t flag, uint64_t count) {
+    return ((uint64_t)tag << 56) | (flag << 54) | count;
+}
+__device__ __forceinline__ uint32_t st_tag(uint64_t s) { return (uint32_t)(s >> 56); }
+__device__ __forceinline__ uint64_t st_flag(uint64_t s) { return (s >> 54) & 3ull; }
+__device__ __forceinline__ uint64_t st_count(uint64_t s) { return s & ((1ull << 54) - 1); }
+
+template <class K>
+constexpr size_t onesweep_smem() { return (size_t)OS_TILE * (sizeof(K) + sizeof(uint64_t)); }
+
+// Block-wide exclusive scan of one value per thread (OS_THREADS threads).
+__device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *warp_sums) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    uint32_t add = 0;
+    for (int i = 0; i < w; i++) add += warp_sums[i];
+    __syncthreads();
+    return x - v + add;
+}
+
+template <class K>
+__global__ void __launch_bounds__(OS_THREADS, 2)
+k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__restrict__ kout,
+           uint64_t *__restrict__ vout, const uint32_t *n_ptr, uint64_t n_max, uint32_t shift,
+           const uint32_t *__restrict__ dbase, unsigned long long *status, uint32_t tag, uint32_t *tile_ctr,
+           Ctl *ctl, uint64_t wait_ns, uint32_t withhold) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    K *skeys = reinterpret_cast<K *>(smem);
+    uint64_t *svals = reinterpret_cast<uint64_t *>(smem + (size_t)OS_TILE * sizeof(K));
+    __shared__ uint32_t whist[OS_WARPS][RADIX + 1];
+    __shared__ uint32_t texcl[RADIX];
+    __shared__ uint64_t gbase[RADIX];
+    __shared__ uint32_t wsum[OS_WARPS];
+    __shared__ uint32_t s_tile;
+
+    if (must_stop(ctl)) return;
+    const uint64_t n = min((uint64_t)*n_ptr, n_max);
+    const uint64_t ntiles = (n + OS_TILE - 1) / OS_TILE;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint32_t lt = lanemask_lt();
+
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+        for (int i = tid; i < OS_WARPS * (RADIX + 1); i += OS_THREADS) (&whist[0][0])[i] = 0;
+        __syncthreads();
+        const uint64_t tile = s_tile;
+        if (tile >= ntiles) return;
+        const uint64_t base = tile * OS_TILE;
+        const uint32_t nvalid = (uint32_t)min((uint64_t)OS_TILE, n - base);
+
+        K k[OS_ITEMS];
+        uint32_t rd[OS_ITEMS];   // rank within warp (low 16 bits) | digit << 16
+#pragma unroll
+        for (int j = 0; j < OS_ITEMS; j++) {
+            const uint32_t li = w * (32 * OS_ITEMS) + j * 32 + lane;
+            k[j] = li < nvalid ? kin[base + li] : K(0);
+        }
+#pragma unroll
+        for (int j = 0; j < OS_ITEMS; j++) {
+            const uint32_t li = w * (32 * OS_ITEMS) + j * 32 + lane;
+            const uint32_t d = li < nvalid ? (uint32_t)((k[j] >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+            const uint32_t cnt = whist[w][d];
+            __syncwarp();
+            if ((peers & lt) == 0) whist[w][d] = cnt + __popc(peers);
+            __syncwarp();
+            rd[j] = (cnt + __popc(peers & lt)) | (d << 16);
+        }
+        __syncthreads();
+        // per digit: exclusive offsets of the warps, tile count
+        uint32_t run = 0;
+        {
+            const int d = tid;  // OS_THREADS == RADIX
+#pragma unroll
+            for (int ww = 0; ww < OS_WARPS; ww++) {
+                const uint32_t c = whist[ww][d];
+                whist[ww][d] = run;
+                run += c;
+            }
+        }
+        // publish this tile's counts, then look back over earlier tiles
+        const bool withheld = withhold != 0 && tile == (uint64_t)(withhold - 1);
+        volatile unsigned long long *vst = status;
+        if (!withheld) vst[tile * RADIX + tid] = st_make(tag, tile == 0 ? ST_INC : ST_AGG, run);
+        uint64_t excl = 0;
+        if (tile > 0) {
+            int64_t t = (int64_t)tile - 1;
+            const uint64_t t0 = globaltimer_ns();
+            uint32_t spins = 0;
+            while (t >= 0) {
+                const uint64_t s = vst[(uint64_t)t * RADIX + tid];
+                if (st_tag(s) != tag || st_flag(s) == 0) {
+                    if ((++spins & 63) == 0) {
+                        if (*(volatile unsigned int *)&ctl->timeout) break;
+                        if (globaltimer_ns() - t0 > wait_ns) {
+                            atomicExch(&ctl->timeout, 1u);
+                            break;
+                        }
+                    }
+                    continue;
+                }
+                excl += st_count(s);
+                if (st_flag(s) == ST_INC) break;
+                --t;
+            }
+            if (!withheld) vst[tile * RADIX + tid] = st_make(tag, ST_INC, excl + run);
+        }
+        gbase[tid] = (uint64_t)dbase[tid] + excl;
+        const uint32_t te = block_excl_scan_256(run, wsum);
+        texcl[tid] = te;
+        __syncthreads();
+        // stable scatter into shared memory in digit order
+#pragma unroll
+        for (int j = 0; j < OS_ITEMS; j++) {
+            const uint32_t li = w * (32 * OS_ITEMS) + j * 32 + lane;
+            if (li < nvalid) {
+                const uint32_t d = rd[j] >> 16;
+                const uint32_t pos = texcl[d] + whist[w][d] + (rd[j] & 0xFFFFu);
+                skeys[pos] = k[j];
+                svals[pos] = vin[base + li];
+            }
+        }
+        __syncthreads();
+        for (uint32_t i = tid; i < nvalid; i += OS_THREADS) {
+            const K kk = skeys[i];
+            const uint32_t d = (uint32_t)((kk >> shift) & (RADIX - 1));
+            const uint64_t o = gbase[d] + (i - texcl[d]);
+            if (o < n) {   // always true unless a wait gave up and the offsets are unreliable
+                kout[o] = kk;
+                vout[o] = svals[i];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Exclusive scan of each pass's histogram into its digit bases (one CTA per pass).
+__global__ void k_digit_bases(const uint32_t *hist, uint32_t *dbase, Ctl *ctl) {
+    __shared__ uint32_t wsum[OS_WARPS];
+    const uint32_t p = blockIdx.x;
+    const uint32_t v = hist[p * RADIX + threadIdx.x];
+    const uint32_t e = block_excl_scan_256(v, wsum);
+    dbase[p * RADIX + threadIdx.x] = e;
+}
+
+// Histograms of every digit pass of 64-bit keys (the race records), count from device.
+__global__ void k_hist_u64(const uint64_t *keys, const uint32_t *n_ptr, uint64_t n_max, uint32_t npass,
+                           uint32_t *hist, Ctl *ctl) {
+    __shared__ uint32_t sh[8 * RADIX];
+    if (must_stop(ctl)) return;
+    for (int i = threadIdx.x; i < 8 * RADIX; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const uint64_t n = min((uint64_t)*n_ptr, n_max);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = keys[i];
+        for (uint32_t p = 0; p < npass; p++) atomicAdd(&sh[p * RADIX + ((k >> (8 * p)) & (RADIX - 1))], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < (int)(npass * RADIX); i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+}  // namespace simk

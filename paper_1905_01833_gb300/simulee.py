@@ -1,0 +1,257 @@
+"""Python binding of the C ABI in include/simulee.h (argument marshalling only).
+
+Every step of the check runs in the CUDA library (libsimulee.so). PyTorch
+supplies device memory and the current CUDA stream. If the library is missing
+the calls raise; there is no other implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsimulee.so")
+
+OK, EINVAL, EBADTRACE, ENOMEM, ETRUNC, ETIMEOUT, ECUDA = range(7)
+FLAG_UNSORTED = 1
+PATH_AUTO, PATH_SORT, PATH_HASH = 0, 1, 2
+
+RACE_DTYPE = np.dtype([("space", "u1"), ("scope", "u1"), ("cls", "u1"), ("pad", "u1"),
+                       ("block", "<u4"), ("epoch", "<u4"), ("unit", "<u4"),
+                       ("vo_first", "<u4"), ("vo_second", "<u4"),
+                       ("gtid_first", "<u4"), ("gtid_second", "<u4")])
+DIV_DTYPE = np.dtype([("block", "<u4"), ("min_count", "<u4"), ("max_count", "<u4"), ("first_min_tid", "<u4")])
+BAR_DTYPE = np.dtype([("block", "<u4"), ("barrier", "<u4")])
+
+
+class SimuleeError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: status {status}")
+        self.status = status
+
+
+class Trace(ctypes.Structure):
+    _fields_ = [("events", ctypes.c_void_p), ("n_events", ctypes.c_uint64), ("barrier_counts", ctypes.c_void_p),
+                ("n_blocks", ctypes.c_uint32), ("block_threads", ctypes.c_uint32), ("shared_units", ctypes.c_uint32),
+                ("global_units", ctypes.c_uint32), ("max_barriers", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+class Outputs(ctypes.Structure):
+    _fields_ = [("races", ctypes.c_void_p), ("races_cap", ctypes.c_uint64),
+                ("divergence", ctypes.c_void_p), ("divergence_cap", ctypes.c_uint64),
+                ("redundant", ctypes.c_void_p), ("redundant_cap", ctypes.c_uint64),
+                ("grid_redundant", ctypes.c_void_p), ("grid_redundant_cap", ctypes.c_uint64)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("bad_kind", ctypes.c_uint32), ("bad_index", ctypes.c_uint64),
+                ("n_races", ctypes.c_uint64), ("n_divergence", ctypes.c_uint64), ("n_redundant", ctypes.c_uint64),
+                ("n_grid_redundant", ctypes.c_uint64)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("wait_limit_us", ctypes.c_uint32), ("path", ctypes.c_uint32), ("test_withhold", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 5)]
+
+
+REPORT_BYTES = ctypes.sizeof(Report)
+_lib_handle = None
+
+
+def lib():
+    """Load libsimulee.so; raise if it has not been built."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u32, u64, st = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+        P = ctypes.POINTER
+        sigs = {
+            "simulee_create": [P(vp), ctypes.c_int, P(Options)],
+            "simulee_destroy": [vp],
+            "simulee_workspace_size": [vp, P(Trace), P(ctypes.c_size_t)],
+            "simulee_check": [vp, P(Trace), P(Outputs), vp, vp, ctypes.c_size_t, vp],
+            "simulee_check_races": [vp, P(Trace), vp, u64, vp, vp, ctypes.c_size_t, vp],
+            "simulee_check_divergence": [vp, P(Trace), vp, u64, vp, vp, ctypes.c_size_t, vp],
+            "simulee_check_redundant_barriers": [vp, P(Trace), vp, u64, vp, u64, vp, vp, ctypes.c_size_t, vp],
+            "simulee_batch_workspace_size": [vp, P(Trace), u32, P(ctypes.c_size_t)],
+            "simulee_check_batch": [vp, P(Trace), u32, P(Outputs), vp, vp, ctypes.c_size_t, vp],
+        }
+        for name, args in sigs.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = st
+        L.simulee_status_str.argtypes = [st]
+        L.simulee_status_str.restype = ctypes.c_char_p
+        _lib_handle = L
+    return _lib_handle
+
+
+def status_str(s: int) -> str:
+    return lib().simulee_status_str(s).decode()
+
+
+def _check(s: int, what: str):
+    if s != OK:
+        raise SimuleeError(s, f"{what}: {status_str(s)}")
+
+
+@dataclasses.dataclass
+class DeviceTrace:
+    """A trace whose records and barrier counts live in device memory (torch tensors)."""
+    events: object          # torch.int32 (n, 4) on cuda
+    barrier_counts: object  # torch.int32 (n_blocks * block_threads,) on cuda
+    n_blocks: int
+    block_threads: int
+    shared_units: int
+    global_units: int
+    max_barriers: int
+    flags: int = 0
+
+    @property
+    def n_events(self) -> int:
+        return int(self.events.shape[0])
+
+    def c(self) -> Trace:
+        return Trace(self.events.data_ptr() if self.n_events else None, self.n_events,
+                     self.barrier_counts.data_ptr(), self.n_blocks, self.block_threads, self.shared_units,
+                     self.global_units, self.max_barriers, self.flags)
+
+
+def to_device(trace, device="cuda") -> DeviceTrace:
+    """Copy a host trace (numpy arrays + dimensions) to the GPU."""
+    import torch
+    ev = torch.from_numpy(np.ascontiguousarray(trace.events, dtype=np.uint32).view(np.int32).reshape(-1, 4))
+    cn = torch.from_numpy(np.ascontiguousarray(trace.barrier_counts, dtype=np.uint32).view(np.int32))
+    return DeviceTrace(ev.to(device), cn.to(device), trace.n_blocks, trace.block_threads, trace.shared_units,
+                       trace.global_units, trace.max_barriers, getattr(trace, "flags", 0))
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Checker:
+    """A library context on one GPU plus reusable device buffers."""
+
+    def __init__(self, device: int = 0, wait_limit_us: int = 0, path: int = PATH_AUTO, test_withhold: int = 0):
+        import torch
+        self.device = device
+        self.torch = torch
+        opt = Options(wait_limit_us, path, test_withhold)
+        h = ctypes.c_void_p()
+        _check(lib().simulee_create(ctypes.byref(h), device, ctypes.byref(opt)), "simulee_create")
+        self.h = h
+        self._ws = None
+        self._report = torch.zeros(REPORT_BYTES, dtype=torch.uint8).pin_memory()
+
+    def close(self):
+        if self.h:
+            lib().simulee_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_size(self, dt: DeviceTrace) -> int:
+        n = ctypes.c_size_t()
+        t = dt.c()
+        _check(lib().simulee_workspace_size(self.h, ctypes.byref(t), ctypes.byref(n)), "simulee_workspace_size")
+        return int(n.value)
+
+    def workspace(self, nbytes: int):
+        """A device workspace of at least nbytes, reused across calls (256-byte aligned)."""
+        if self._ws is None or self._ws.numel() < nbytes:
+            self._ws = None
+            self._ws = self.torch.empty(max(nbytes, 256), dtype=self.torch.uint8, device=f"cuda:{self.device}")
+        return self._ws
+
+    def alloc_outputs(self, races_cap: int, div_cap: int, red_cap: int, grid_cap: int):
+        torch = self.torch
+        dev = f"cuda:{self.device}"
+        bufs = dict(races=torch.empty(max(races_cap, 1) * 32, dtype=torch.uint8, device=dev),
+                    divergence=torch.empty(max(div_cap, 1) * 16, dtype=torch.uint8, device=dev),
+                    redundant=torch.empty(max(red_cap, 1) * 8, dtype=torch.uint8, device=dev),
+                    grid=torch.empty(max(grid_cap, 1) * 4, dtype=torch.uint8, device=dev))
+        o = Outputs(bufs["races"].data_ptr(), races_cap, bufs["divergence"].data_ptr(), div_cap,
+                    bufs["redundant"].data_ptr(), red_cap, bufs["grid"].data_ptr(), grid_cap)
+        return o, bufs
+
+    def report(self) -> dict:
+        r = Report.from_buffer_copy(self._report.numpy().tobytes())
+        return dict(status=r.status, bad_kind=r.bad_kind, bad_index=r.bad_index, n_races=r.n_races,
+                    n_divergence=r.n_divergence, n_redundant=r.n_redundant, n_grid_redundant=r.n_grid_redundant)
+
+    def check(self, dt: DeviceTrace, races_cap: int | None = None, div_cap: int | None = None,
+              red_cap: int | None = None, grid_cap: int | None = None, stream=None) -> dict:
+        """Full check; returns the report plus host copies of the (truncated) lists."""
+        torch = self.torch
+        n = dt.n_events
+        races_cap = 2 * n + 2 if races_cap is None else races_cap
+        div_cap = dt.n_blocks if div_cap is None else div_cap
+        red_cap = dt.n_blocks * max(dt.max_barriers, 1) if red_cap is None else red_cap
+        grid_cap = max(dt.max_barriers, 1) if grid_cap is None else grid_cap
+        o, bufs = self.alloc_outputs(races_cap, div_cap, red_cap, grid_cap)
+        ws = self.workspace(self.workspace_size(dt))
+        t = dt.c()
+        _check(lib().simulee_check(self.h, ctypes.byref(t), ctypes.byref(o), ctypes.c_void_p(self._report.data_ptr()),
+                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)), "simulee_check")
+        torch.cuda.synchronize(self.device)
+        rep = self.report()
+        return self._collect(rep, bufs, races_cap, div_cap, red_cap, grid_cap)
+
+    def _collect(self, rep, bufs, races_cap, div_cap, red_cap, grid_cap):
+        def take(buf, cap, count, dtype):
+            k = min(cap, count) if rep["status"] in (OK, ETRUNC) else 0
+            return np.frombuffer(buf[: k * dtype.itemsize].cpu().numpy().tobytes(), dtype=dtype)
+        out = dict(rep)
+        out["races"] = take(bufs["races"], races_cap, rep["n_races"], RACE_DTYPE)
+        out["divergence"] = take(bufs["divergence"], div_cap, rep["n_divergence"], DIV_DTYPE)
+        out["redundant"] = take(bufs["redundant"], red_cap, rep["n_redundant"], BAR_DTYPE)
+        out["grid_redundant"] = take(bufs["grid"], grid_cap, rep["n_grid_redundant"], np.dtype("<u4"))
+        return out
+
+    def check_races(self, dt: DeviceTrace, cap: int | None = None, stream=None) -> dict:
+        cap = 2 * dt.n_events + 2 if cap is None else cap
+        o, bufs = self.alloc_outputs(cap, 0, 0, 0)
+        ws = self.workspace(self.workspace_size(dt))
+        t = dt.c()
+        _check(lib().simulee_check_races(self.h, ctypes.byref(t), ctypes.c_void_p(o.races), cap,
+                                         ctypes.c_void_p(self._report.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                         ws.numel(), _stream_ptr(stream)), "simulee_check_races")
+        self.torch.cuda.synchronize(self.device)
+        return self._collect(self.report(), bufs, cap, 0, 0, 0)
+
+    def check_divergence(self, dt: DeviceTrace, cap: int | None = None, stream=None) -> dict:
+        cap = dt.n_blocks if cap is None else cap
+        o, bufs = self.alloc_outputs(0, cap, 0, 0)
+        ws = self.workspace(self.workspace_size(dt))
+        t = dt.c()
+        _check(lib().simulee_check_divergence(self.h, ctypes.byref(t), ctypes.c_void_p(o.divergence), cap,
+                                              ctypes.c_void_p(self._report.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                              ws.numel(), _stream_ptr(stream)), "simulee_check_divergence")
+        self.torch.cuda.synchronize(self.device)
+        return self._collect(self.report(), bufs, 0, cap, 0, 0)
+
+    def check_redundant_barriers(self, dt: DeviceTrace, cap: int | None = None, grid_cap: int | None = None,
+                                 stream=None) -> dict:
+        cap = dt.n_blocks * max(dt.max_barriers, 1) if cap is None else cap
+        grid_cap = max(dt.max_barriers, 1) if grid_cap is None else grid_cap
+        o, bufs = self.alloc_outputs(0, 0, cap, grid_cap)
+        ws = self.workspace(self.workspace_size(dt))
+        t = dt.c()
+        _check(lib().simulee_check_redundant_barriers(
+            self.h, ctypes.byref(t), ctypes.c_void_p(o.redundant), cap, ctypes.c_void_p(o.grid_redundant), grid_cap,
+            ctypes.c_void_p(self._report.data_ptr()), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+            _stream_ptr(stream)), "simulee_check_redundant_barriers")
+        self.torch.cuda.synchronize(self.device)
+        return self._collect(self.report(), bufs, 0, 0, cap, grid_cap)
