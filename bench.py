@@ -1,0 +1,372 @@
+"""Benchmark of the synchronization check: access records checked per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one full check (all stages: validation and routing, radix sorts,
+segmented reductions with epoch adjacency, canonical race list, divergence and
+redundant-barrier lists) of one synthetic trace of the grid workload: 1024
+blocks x 256 threads, 32 barrier epochs, 12288 shared units per block and 2^26
+global units, tree-reduction and tiled-transpose blocks, ~6e7 records (~1 GB,
+larger than L2, so no flush is needed between steps).
+
+`value` is measured with the trace resident in HBM; `e2e` times the same check
+through the C ABI with the trace in pinned host memory, including the host to
+device copy of the trace and the device to host copy of the report and lists.
+With N > 1 (torchrun) every rank checks its own trace (independent replicas;
+the check has no cross-GPU exchange) and the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "access-events checked/sec"
+UNIT = "Gev/s"
+WORKLOAD = ("grid: 1024 blocks x 256 threads, 32 epochs, 12288 shared units/block + 2^26 global units, "
+            "tree-reduction / 32x32 tiled-transpose blocks, 10% blocks missing one barrier, 2% global atomics")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.lines: list[str] = []
+        self.proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_uuid(torch, dev: int) -> str | None:
+    try:
+        u = torch.cuda.get_device_properties(dev).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else f"GPU-{s}"
+    except Exception:
+        return None
+
+
+def stream_bytes(tr):
+    """Records per stream and key widths, as the library lays them out (for algorithmic bytes)."""
+    def bits(count):
+        b = 0
+        while (1 << b) < count:
+            b += 1
+        return b
+    glob = ((tr.events[:, 3] >> 30) & 1) == 1
+    n_g = int(glob.sum())
+    n_s = tr.n_events - n_g
+    bb, bus, bug, be = bits(tr.n_blocks), bits(tr.shared_units), bits(tr.global_units), bits(tr.max_barriers + 1)
+    ks = 8 if bb + bus + be > 32 else 4
+    kg = 8 if bb + bug + be > 32 else 4
+    np_s, np_g, np_x = -(-(bb + bus + be) // 8), -(-(bb + bug + be) // 8), -(-bug // 8)
+    sort_bytes = 2 * (n_s * np_s * (ks + 8) + n_g * np_g * (kg + 8) + n_g * np_x * (4 + 8))
+    ingest_bytes = 16 * tr.n_events + 4 * tr.barrier_counts.size + n_s * (ks + 8) + n_g * (kg + 8 + 12)
+    reduce_bytes = n_s * (ks + 8) + n_g * (kg + 8) + n_g * 12
+    return dict(n_s=n_s, n_g=n_g, passes=np_s + np_g + np_x, sort=sort_bytes, ingest=ingest_bytes,
+                reduce=reduce_bytes)
+
+
+def kernel_traffic(kernel: str, workload: str):
+    """ncu DRAM bytes per launch recorded under profiles/, if the kernel source is unchanged since."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))[f"{kernel}|{workload}"]
+    except Exception:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec["bytes_per_launch"] if h == rec["source_sha"] else None
+
+
+def run_oracle_sample(tr, n_blocks: int):
+    """Time the CPU oracle on the records of the first n_blocks blocks (a bounded sample)."""
+    import oracle
+    import tracegen
+    sel = tr.events[:, 2] < n_blocks
+    sub = tracegen.Trace(tr.events[sel].copy(), tr.barrier_counts, tr.n_blocks, tr.block_threads, tr.shared_units,
+                         tr.global_units, tr.max_barriers)
+    t0 = time.perf_counter()
+    out = oracle.check(sub)
+    dt = time.perf_counter() - t0
+    assert out["status"] == 0
+    return int(sel.sum()), dt
+
+
+def make_trace(rank: int, n_blocks: int = 1024):
+    import tracegen
+    return tracegen.c2(seed=tracegen.DEFAULT_SEED + rank, n_blocks=n_blocks)
+
+
+def reference_arm(args, rank: int, world: int):
+    """The oracle as the reference: each step checks a bounded sample of the workload on the host."""
+    if rank != 0:
+        return
+    tr = make_trace(0)
+    nb = args.ref_blocks
+    for _ in range(args.warmup):
+        run_oracle_sample(tr, nb)
+    times, n = [], 0
+    for _ in range(args.steps):
+        n, dt = run_oracle_sample(tr, nb)
+        times.append(dt)
+    t = sum(times) / len(times)
+    v = n / t / 1e9
+    sample = f"records of blocks 0..{nb - 1} of the grid workload ({n} records) per step, single thread"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_events_per_step": n},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--path", choices=["auto", "sort"], default="auto")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--oracle-blocks", type=int, default=256)
+    ap.add_argument("--ref-blocks", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--blocks", type=int, default=1024, help="grid blocks (1024 = the benchmark workload; "
+                    "smaller values only for profiling captures)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    from paper_1905_01833_gb300 import simulee
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+
+    tr = make_trace(rank, args.blocks)
+    dt = simulee.to_device(tr, f"cuda:{local}")
+    chk = simulee.Checker(local, path=simulee.PATH_SORT if args.path == "sort" else simulee.PATH_AUTO)
+    ws = chk.workspace(chk.workspace_size(dt))
+    caps = dict(races_cap=4_000_000, div_cap=tr.n_blocks, red_cap=tr.n_blocks * tr.max_barriers,
+                grid_cap=tr.max_barriers)
+    outs, bufs = chk.alloc_outputs(caps["races_cap"], caps["div_cap"], caps["red_cap"], caps["grid_cap"])
+    report_dev = torch.zeros(simulee.REPORT_BYTES, dtype=torch.uint8, device=f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+    L = simulee.lib()
+    ctrace = dt.c()
+    import ctypes
+    sp = ctypes.c_void_p(stream.cuda_stream)
+
+    def step(trace_c, rep_ptr):
+        s = L.simulee_check(chk.h, ctypes.byref(trace_c), ctypes.byref(outs), ctypes.c_void_p(rep_ptr),
+                            ctypes.c_void_p(ws.data_ptr()), ws.numel(), sp)
+        if s != 0:
+            raise RuntimeError(f"simulee_check failed: {simulee.status_str(s)}")
+
+    for _ in range(args.warmup):
+        step(ctrace, report_dev.data_ptr())
+    torch.cuda.synchronize()
+    rep0 = simulee.Report.from_buffer_copy(report_dev.cpu().numpy().tobytes())
+    if rep0.status != 0:
+        raise RuntimeError(f"check reported status {rep0.status}")
+    launches = chk.last_launches()
+
+    # stage events for every timed step
+    nst = len(simulee.STAGES)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * nst)] for _ in range(args.steps)]
+    for row in evs:
+        for e in row:
+            e.record(stream)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(gpu_uuid(torch, local) if world == 1 else None)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        chk.set_stage_events(evs[i])
+        step(ctrace, report_dev.data_ptr())
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    chk.set_stage_events(None)
+    ms = t_start.elapsed_time(t_end) / args.steps
+    stage_ms = {name: sum(evs[i][2 * s].elapsed_time(evs[i][2 * s + 1]) for i in range(args.steps)) / args.steps
+                for s, name in enumerate(simulee.STAGES)}
+    rep = simulee.Report.from_buffer_copy(report_dev.cpu().numpy().tobytes())
+    assert rep.status == 0 and rep.n_races == rep0.n_races and rep.n_redundant == rep0.n_redundant
+
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = tr.n_events * world / (ms * 1e-3) / 1e9
+
+    # end to end through the C ABI: pinned host trace -> device, check, report and lists -> host
+    h_ev = torch.from_numpy(tr.events.view(np.int32)).pin_memory()
+    h_cn = torch.from_numpy(tr.barrier_counts.view(np.int32)).pin_memory()
+    d_ev = torch.empty_like(dt.events)
+    d_cn = torch.empty_like(dt.barrier_counts)
+    etrace = simulee.DeviceTrace(d_ev, d_cn, tr.n_blocks, tr.block_threads, tr.shared_units, tr.global_units,
+                                 tr.max_barriers).c()
+    rep_host = torch.zeros(simulee.REPORT_BYTES, dtype=torch.uint8).pin_memory()
+    h_races = torch.empty(caps["races_cap"] * 32, dtype=torch.uint8).pin_memory()
+    h_red = torch.empty(max(caps["red_cap"], 1) * 8, dtype=torch.uint8).pin_memory()
+    h_div = torch.empty(max(caps["div_cap"], 1) * 16, dtype=torch.uint8).pin_memory()
+    h_grid = torch.empty(max(caps["grid_cap"], 1) * 4, dtype=torch.uint8).pin_memory()
+    d2h = 0
+
+    def e2e_step():
+        nonlocal d2h
+        d_ev.copy_(h_ev, non_blocking=True)
+        d_cn.copy_(h_cn, non_blocking=True)
+        step(etrace, rep_host.data_ptr())
+        stream.synchronize()
+        r = simulee.Report.from_buffer_copy(rep_host.numpy().tobytes())
+        nr, nd, nred, ng = (min(r.n_races, caps["races_cap"]), min(r.n_divergence, caps["div_cap"]),
+                            min(r.n_redundant, caps["red_cap"]), min(r.n_grid_redundant, caps["grid_cap"]))
+        h_races[: nr * 32].copy_(bufs["races"][: nr * 32], non_blocking=True)
+        h_div[: nd * 16].copy_(bufs["divergence"][: nd * 16], non_blocking=True)
+        h_red[: nred * 8].copy_(bufs["redundant"][: nred * 8], non_blocking=True)
+        h_grid[: ng * 4].copy_(bufs["grid"][: ng * 4], non_blocking=True)
+        stream.synchronize()
+        d2h = simulee.REPORT_BYTES + nr * 32 + nd * 16 + nred * 8 + ng * 4
+
+    for _ in range(3):
+        e2e_step()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = tr.events.nbytes + tr.barrier_counts.nbytes
+
+    # roofline of the dominant stage
+    sb = stream_bytes(tr)
+    peak, peak_src = peaks()
+    stage_bytes = {"ingest": sb["ingest"], "sort": sb["sort"], "reduce": sb["reduce"]}
+    dom = max(stage_bytes, key=lambda k: stage_ms[k])
+    kname = {"ingest": "k_ingest", "sort": "k_onesweep", "reduce": "k_reduce_intra+k_reduce_inter"}[dom]
+    nl = sb["passes"] if dom == "sort" else (1 if dom == "ingest" else 3)
+    achieved = stage_bytes[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src,
+                "bytes_per_launch": stage_bytes[dom] / nl, "launch_ms": stage_ms[dom] / nl,
+                "traffic": kernel_traffic(kname, "grid")}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": WORKLOAD if args.blocks == 1024 else WORKLOAD.replace("1024 blocks", f"{args.blocks} blocks"),
+                   "n_events": tr.n_events, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (1 GB trace, 129 MB L2); no flush", "path": args.path},
+        "e2e": {"value": tr.n_events * world / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches * args.steps,
+        "roofline": roofline,
+        "stages_ms": stage_ms,
+        "results": {"n_races": rep.n_races, "n_divergence": rep.n_divergence, "n_redundant": rep.n_redundant,
+                    "n_grid_redundant": rep.n_grid_redundant},
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, secs = run_oracle_sample(tr, args.oracle_blocks)
+        line["cpu_baseline"] = {"value": n / secs / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"records of blocks 0..{args.oracle_blocks - 1} of the same trace "
+                                          f"({n} records, {secs:.1f} s, single thread)",
+                                "host_cores": len(os.sched_getaffinity(0))}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

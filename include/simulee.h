@@ -206,6 +206,26 @@ simulee_status simulee_check_batch(simulee_ctx *ctx, const simulee_trace *traces
                                    const simulee_outputs *outs, simulee_report *reports, void *ws,
                                    size_t ws_bytes, void *stream);
 
+/*
+ * Diagnostics.
+ * simulee_last_launches: kernels launched by the last check call on this context.
+ * simulee_set_stage_events: optional CUDA events (cudaEvent_t, created by the caller
+ * with timing enabled) recorded on the call's stream around each stage of the
+ * next check calls: events[2*s] before stage s and events[2*s+1] after it, for
+ * the stages below (n_events = 2 * SIMULEE_STAGES; NULL / 0 turns recording off).
+ * A stage that does not run in a call still records both of its events, back to back.
+ */
+enum {
+    SIMULEE_STAGE_INGEST = 0,   /* count stats, validation, routing, histograms */
+    SIMULEE_STAGE_SORT = 1,     /* radix passes of the record streams */
+    SIMULEE_STAGE_REDUCE = 2,   /* segmented reductions: races, epoch adjacency */
+    SIMULEE_STAGE_RACES = 3,    /* canonical race sort and copy-out */
+    SIMULEE_STAGE_BLOCKS = 4,   /* divergence, redundant-barrier lists, report */
+    SIMULEE_STAGES = 5
+};
+uint32_t simulee_last_launches(const simulee_ctx *ctx);
+simulee_status simulee_set_stage_events(simulee_ctx *ctx, void *const *events, uint32_t n_events);
+
 /* Static description of a status code. */
 const char *simulee_status_str(simulee_status s);
 

@@ -30,6 +30,9 @@ struct simulee_ctx {
     int sms;
     simulee_options opt;
     bool attrs_set;
+    uint32_t last_launches;
+    cudaEvent_t stage_ev[2 * SIMULEE_STAGES];
+    bool stage_on;
 };
 
 namespace {
@@ -147,8 +150,14 @@ struct Run {
     uint32_t withhold;   // applied to the first sort pass launched
     bool first_pass_done = false;
 
+    uint32_t launches = 0;
+
     template <class T>
     T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
+
+    void mark(int stage, int end) const {
+        if (ctx->stage_on) cudaEventRecord(ctx->stage_ev[2 * stage + end], st);
+    }
 
     int sort_grid(uint64_t n_max) const {
         const uint64_t tiles = (n_max + OS_TILE - 1) / OS_TILE;
@@ -167,6 +176,7 @@ struct Run {
                 at<K>(koff[src]), at<uint64_t>(voff[src]), at<K>(koff[dst]), at<uint64_t>(voff[dst]), n_ptr, n_max,
                 RADIX_BITS * p, at<uint32_t>(L.off_dbase) + (size_t)(p0 + p) * RADIX,
                 at<unsigned long long>(L.off_status), p0 + p + 1, &ctl->tiles[p0 + p], ctl, wait_ns, wh);
+            launches++;
         }
         return (int)(np & 1);
     }
@@ -233,13 +243,17 @@ simulee_status launch_check(simulee_ctx *ctx, const simulee_trace *t, const simu
     cudaMemsetAsync(R.ws + L.off_status, 0, (size_t)L.status_tiles * RADIX * 8, st);
 
     // 2. barrier counts
+    R.mark(SIMULEE_STAGE_INGEST, 0);
     {
         const int grid = (int)std::min<uint64_t>((L.nb + 7) / 8, (uint64_t)sms * 16);
         k_block_stats<<<std::max(grid, 1), 256, 0, st>>>(t->barrier_counts, L, R.at<uint4>(L.off_stats), R.ctl);
+        R.launches++;
     }
 
     const bool route = want.races || want.red;
+    const bool sorting = L.n > 0 && route;
     uint32_t *rank = nullptr, *pos_to_vo = nullptr;
+    uint32_t *hist = R.at<uint32_t>(L.off_hist);
     if (L.n > 0) {
         // 3. unsorted traces: schedule rank of each record = position in (visit order, index) order
         if (L.flags & SIMULEE_FLAG_UNSORTED) {
@@ -249,19 +263,20 @@ simulee_status launch_check(simulee_ctx *ctx, const simulee_trace *t, const simu
             size_t qk[2] = {L.off_rk[0], L.off_rk[1]}, qv[2] = {L.off_rv[0], L.off_rv[1]};
             const int g = (int)std::min<uint64_t>((L.n + 255) / 256, (uint64_t)sms * 8);
             k_rank_init<<<g, 256, 0, st>>>((const uint4 *)t->events, L.n, R.at<uint32_t>(qk[0]),
-                                            R.at<uint64_t>(qv[0]), R.at<uint32_t>(L.off_hist) + (size_t)p0q * RADIX);
-            k_digit_bases<<<4, RADIX, 0, st>>>(R.at<uint32_t>(L.off_hist) + (size_t)p0q * RADIX,
+                                            R.at<uint64_t>(qv[0]), hist + (size_t)p0q * RADIX);
+            k_digit_bases<<<4, RADIX, 0, st>>>(hist + (size_t)p0q * RADIX,
                                                R.at<uint32_t>(L.off_dbase) + (size_t)p0q * RADIX, R.ctl);
             k_set_count<<<1, 1, 0, st>>>(&R.ctl->n_q, (unsigned int)L.n);
+            R.launches += 3;
             const int b = R.sort<uint32_t>(qk, qv, &R.ctl->n_q, L.n, 4, p0q);
             k_rank_scatter<<<g, 256, 0, st>>>(R.at<uint64_t>(qv[b]), L.n, rank, R.ctl);
+            R.launches++;
             cudaMemcpyAsync(pos_to_vo, R.at<uint32_t>(qk[b]), L.n * 4, cudaMemcpyDeviceToDevice, st);
         }
 
         // 4. ingest
         const uint64_t ntiles = (L.n + IN_TILE - 1) / IN_TILE;
         const int gi = (int)std::max<uint64_t>(1, std::min<uint64_t>(ntiles, (uint64_t)sms * 4));
-        uint32_t *hist = R.at<uint32_t>(L.off_hist);
 #define SIM_INGEST(KS, KG, RT)                                                                                     \
     k_ingest<KS, KG, RT><<<gi, IN_THREADS, 0, st>>>((const uint4 *)t->events, t->barrier_counts, rank, L, R.ctl,  \
                                                     R.at<KS>(L.off_sk[0]), R.at<uint64_t>(L.off_sv[0]),             \
@@ -279,64 +294,82 @@ simulee_status launch_check(simulee_ctx *ctx, const simulee_trace *t, const simu
             SIM_INGEST(uint32_t, uint32_t, true);
         }
 #undef SIM_INGEST
+        R.launches++;
+    }
+    R.mark(SIMULEE_STAGE_INGEST, 1);
 
-        if (route) {
-            // 5. sort the three streams
-            if (L.p0_r > 0) k_digit_bases<<<L.p0_r, RADIX, 0, st>>>(hist, R.at<uint32_t>(L.off_dbase), R.ctl);
-            size_t sk[2] = {L.off_sk[0], L.off_sk[1]}, sv[2] = {L.off_sv[0], L.off_sv[1]};
-            size_t gk[2] = {L.off_gk[0], L.off_gk[1]}, gv[2] = {L.off_gv[0], L.off_gv[1]};
-            size_t xk[2] = {L.off_xk[0], L.off_xk[1]}, xv[2] = {L.off_xv[0], L.off_xv[1]};
-            const int bs = L.wide_s ? R.sort<uint64_t>(sk, sv, &R.ctl->n_s, L.n, L.np_s, L.p0_s)
-                                    : R.sort<uint32_t>(sk, sv, &R.ctl->n_s, L.n, L.np_s, L.p0_s);
-            const int bg = L.wide_g ? R.sort<uint64_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g)
-                                    : R.sort<uint32_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g);
-            const int bx = R.sort<uint32_t>(xk, xv, &R.ctl->n_g, L.n, L.np_x, L.p0_x);
+    // 5. sort the three streams
+    R.mark(SIMULEE_STAGE_SORT, 0);
+    int bs = 0, bg = 0, bx = 0;
+    if (sorting) {
+        if (L.p0_r > 0) {
+            k_digit_bases<<<L.p0_r, RADIX, 0, st>>>(hist, R.at<uint32_t>(L.off_dbase), R.ctl);
+            R.launches++;
+        }
+        size_t sk[2] = {L.off_sk[0], L.off_sk[1]}, sv[2] = {L.off_sv[0], L.off_sv[1]};
+        size_t gk[2] = {L.off_gk[0], L.off_gk[1]}, gv[2] = {L.off_gv[0], L.off_gv[1]};
+        size_t xk[2] = {L.off_xk[0], L.off_xk[1]}, xv[2] = {L.off_xv[0], L.off_xv[1]};
+        bs = L.wide_s ? R.sort<uint64_t>(sk, sv, &R.ctl->n_s, L.n, L.np_s, L.p0_s)
+                      : R.sort<uint32_t>(sk, sv, &R.ctl->n_s, L.n, L.np_s, L.p0_s);
+        bg = L.wide_g ? R.sort<uint64_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g)
+                      : R.sort<uint32_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g);
+        bx = R.sort<uint32_t>(xk, xv, &R.ctl->n_g, L.n, L.np_x, L.p0_x);
+    }
+    R.mark(SIMULEE_STAGE_SORT, 1);
 
-            // 6. segmented reductions
-            RaceStage rs;
-            rs.keys = R.at<uint64_t>(L.off_rk[0]);
-            rs.idx = R.at<uint64_t>(L.off_rv[0]);
-            rs.pay = R.at<uint4>(L.off_rp);
-            rs.cap = L.race_cap;
-            rs.pos_to_vo = pos_to_vo;
-            rs.n_pos = L.n;
-            uint32_t *nonred = R.at<uint32_t>(L.off_nonred);
-            const int gr = (int)std::max<uint64_t>(1, std::min<uint64_t>((L.n + 255) / 256, (uint64_t)sms * 8));
-            if (L.wide_s)
-                k_reduce_intra<uint64_t><<<gr, 256, 0, st>>>(R.at<uint64_t>(L.off_sk[bs]), R.at<uint64_t>(L.off_sv[bs]),
-                                                            &R.ctl->n_s, L, 0u, L.bus, R.ctl, nonred, rs);
-            else
-                k_reduce_intra<uint32_t><<<gr, 256, 0, st>>>(R.at<uint32_t>(L.off_sk[bs]), R.at<uint64_t>(L.off_sv[bs]),
-                                                            &R.ctl->n_s, L, 0u, L.bus, R.ctl, nonred, rs);
-            if (L.wide_g)
-                k_reduce_intra<uint64_t><<<gr, 256, 0, st>>>(R.at<uint64_t>(L.off_gk[bg]), R.at<uint64_t>(L.off_gv[bg]),
-                                                            &R.ctl->n_g, L, 1u, L.bug, R.ctl, nonred, rs);
-            else
-                k_reduce_intra<uint32_t><<<gr, 256, 0, st>>>(R.at<uint32_t>(L.off_gk[bg]), R.at<uint64_t>(L.off_gv[bg]),
-                                                            &R.ctl->n_g, L, 1u, L.bug, R.ctl, nonred, rs);
-            k_reduce_inter<<<gr, 256, 0, st>>>(R.at<uint32_t>(L.off_xk[bx]), R.at<uint64_t>(L.off_xv[bx]), &R.ctl->n_g,
-                                               L, R.ctl, rs);
+    // 6. segmented reductions
+    R.mark(SIMULEE_STAGE_REDUCE, 0);
+    RaceStage rs;
+    rs.keys = R.at<uint64_t>(L.off_rk[0]);
+    rs.idx = R.at<uint64_t>(L.off_rv[0]);
+    rs.pay = R.at<uint4>(L.off_rp);
+    rs.cap = L.race_cap;
+    rs.pos_to_vo = pos_to_vo;
+    rs.n_pos = L.n;
+    if (sorting) {
+        uint32_t *nonred = R.at<uint32_t>(L.off_nonred);
+        const int gr = (int)std::max<uint64_t>(1, std::min<uint64_t>((L.n + 255) / 256, (uint64_t)sms * 8));
+        if (L.wide_s)
+            k_reduce_intra<uint64_t><<<gr, 256, 0, st>>>(R.at<uint64_t>(L.off_sk[bs]), R.at<uint64_t>(L.off_sv[bs]),
+                                                        &R.ctl->n_s, L, 0u, L.bus, R.ctl, nonred, rs);
+        else
+            k_reduce_intra<uint32_t><<<gr, 256, 0, st>>>(R.at<uint32_t>(L.off_sk[bs]), R.at<uint64_t>(L.off_sv[bs]),
+                                                        &R.ctl->n_s, L, 0u, L.bus, R.ctl, nonred, rs);
+        if (L.wide_g)
+            k_reduce_intra<uint64_t><<<gr, 256, 0, st>>>(R.at<uint64_t>(L.off_gk[bg]), R.at<uint64_t>(L.off_gv[bg]),
+                                                        &R.ctl->n_g, L, 1u, L.bug, R.ctl, nonred, rs);
+        else
+            k_reduce_intra<uint32_t><<<gr, 256, 0, st>>>(R.at<uint32_t>(L.off_gk[bg]), R.at<uint64_t>(L.off_gv[bg]),
+                                                        &R.ctl->n_g, L, 1u, L.bug, R.ctl, nonred, rs);
+        k_reduce_inter<<<gr, 256, 0, st>>>(R.at<uint32_t>(L.off_xk[bx]), R.at<uint64_t>(L.off_xv[bx]), &R.ctl->n_g,
+                                           L, R.ctl, rs);
+        R.launches += 3;
+    }
+    R.mark(SIMULEE_STAGE_REDUCE, 1);
 
-            // 7. races in canonical order
-            if (want.races) {
-                const int gh = (int)std::max<uint64_t>(1, std::min<uint64_t>((L.race_cap + 255) / 256, (uint64_t)sms * 4));
-                k_hist_u64<<<gh, 256, 0, st>>>(rs.keys, &R.ctl->n_races, L.race_cap, L.np_r,
-                                               hist + (size_t)L.p0_r * RADIX, R.ctl);
-                k_digit_bases<<<L.np_r, RADIX, 0, st>>>(hist + (size_t)L.p0_r * RADIX,
-                                                        R.at<uint32_t>(L.off_dbase) + (size_t)L.p0_r * RADIX, R.ctl);
-                size_t rk[2] = {L.off_rk[0], L.off_rk[1]}, rv[2] = {L.off_rv[0], L.off_rv[1]};
-                const int br = R.sort<uint64_t>(rk, rv, &R.ctl->n_races, L.race_cap, L.np_r, L.p0_r);
-                if (out->races_cap) {
-                    const int gw = (int)std::max<uint64_t>(
-                        1, std::min<uint64_t>((std::min<uint64_t>(out->races_cap, L.race_cap) + 255) / 256, (uint64_t)sms * 8));
-                    k_write_races<<<gw, 256, 0, st>>>(R.at<uint64_t>(rk[br]), R.at<uint64_t>(rv[br]), rs.pay, L, R.ctl,
-                                                      (uint8_t *)out->races, out->races_cap);
-                }
-            }
+    // 7. races in canonical order
+    R.mark(SIMULEE_STAGE_RACES, 0);
+    if (sorting && want.races) {
+        const int gh = (int)std::max<uint64_t>(1, std::min<uint64_t>((L.race_cap + 255) / 256, (uint64_t)sms * 4));
+        k_hist_u64<<<gh, 256, 0, st>>>(rs.keys, &R.ctl->n_races, L.race_cap, L.np_r, hist + (size_t)L.p0_r * RADIX,
+                                       R.ctl);
+        k_digit_bases<<<L.np_r, RADIX, 0, st>>>(hist + (size_t)L.p0_r * RADIX,
+                                                R.at<uint32_t>(L.off_dbase) + (size_t)L.p0_r * RADIX, R.ctl);
+        R.launches += 2;
+        size_t rk[2] = {L.off_rk[0], L.off_rk[1]}, rv[2] = {L.off_rv[0], L.off_rv[1]};
+        const int br = R.sort<uint64_t>(rk, rv, &R.ctl->n_races, L.race_cap, L.np_r, L.p0_r);
+        if (out->races_cap) {
+            const int gw = (int)std::max<uint64_t>(
+                1, std::min<uint64_t>((std::min<uint64_t>(out->races_cap, L.race_cap) + 255) / 256, (uint64_t)sms * 8));
+            k_write_races<<<gw, 256, 0, st>>>(R.at<uint64_t>(rk[br]), R.at<uint64_t>(rv[br]), rs.pay, L, R.ctl,
+                                              (uint8_t *)out->races, out->races_cap);
+            R.launches++;
         }
     }
+    R.mark(SIMULEE_STAGE_RACES, 1);
 
     // 8. per-block outputs
+    R.mark(SIMULEE_STAGE_BLOCKS, 0);
     if (want.div || want.red) {
         const int gb = (int)std::max<uint64_t>(1, std::min<uint64_t>((L.nb + 255) / 256, (uint64_t)sms * 8));
         k_block_counts<<<gb, 256, 0, st>>>(R.at<uint4>(L.off_stats), R.at<uint32_t>(L.off_nonred), L, R.ctl,
@@ -349,12 +382,14 @@ simulee_status launch_check(simulee_ctx *ctx, const simulee_trace *t, const simu
                                           want.div ? (uint4 *)out->divergence : nullptr,
                                           want.div ? out->divergence_cap : 0,
                                           want.red ? (uint2 *)out->redundant : nullptr, want.red ? out->redundant_cap : 0);
+        R.launches += 3;
         if (want.red) {
             const int gg = (int)std::max<uint64_t>(1, std::min<uint64_t>(((uint64_t)L.nb * L.words + 255) / 256, (uint64_t)sms * 8));
             k_grid_or<<<gg, 256, 0, st>>>(R.at<uint4>(L.off_stats), R.at<uint32_t>(L.off_nonred), L, R.ctl,
                                           R.at<uint32_t>(L.off_gridnr), R.at<uint32_t>(L.off_gridhas));
             k_grid_list<<<1, 1024, 0, st>>>(R.at<uint32_t>(L.off_gridnr), R.at<uint32_t>(L.off_gridhas), L, R.ctl,
                                             out->grid_redundant, out->grid_redundant_cap);
+            R.launches += 2;
         }
     }
 
@@ -368,6 +403,9 @@ simulee_status launch_check(simulee_ctx *ctx, const simulee_trace *t, const simu
     ra.want_div = want.div;
     ra.want_red = want.red;
     k_report<<<1, 32, 0, st>>>(R.ctl, ra, (uint8_t *)report);
+    R.launches++;
+    R.mark(SIMULEE_STAGE_BLOCKS, 1);
+    ctx->last_launches = R.launches;
     const cudaError_t e = cudaGetLastError();
     if (prev_dev >= 0 && prev_dev != ctx->device) cudaSetDevice(prev_dev);
     return e == cudaSuccess ? SIMULEE_OK : SIMULEE_ECUDA;
@@ -458,6 +496,23 @@ simulee_status simulee_check_batch(simulee_ctx *ctx, const simulee_trace *traces
                                    void *stream) {
     (void)ctx; (void)traces; (void)n_traces; (void)outs; (void)reports; (void)ws; (void)ws_bytes; (void)stream;
     return SIMULEE_EINVAL;
+}
+
+uint32_t simulee_last_launches(const simulee_ctx *ctx) { return ctx ? ctx->last_launches : 0u; }
+
+simulee_status simulee_set_stage_events(simulee_ctx *ctx, void *const *events, uint32_t n_events) {
+    if (!ctx) return SIMULEE_EINVAL;
+    if (!events || n_events == 0) {
+        ctx->stage_on = false;
+        return SIMULEE_OK;
+    }
+    if (n_events != 2 * SIMULEE_STAGES) return SIMULEE_EINVAL;
+    for (uint32_t i = 0; i < n_events; i++) {
+        if (!events[i]) return SIMULEE_EINVAL;
+        ctx->stage_ev[i] = (cudaEvent_t)events[i];
+    }
+    ctx->stage_on = true;
+    return SIMULEE_OK;
 }
 
 const char *simulee_status_str(simulee_status s) {

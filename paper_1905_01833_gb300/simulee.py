@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libsimulee.so")
 OK, EINVAL, EBADTRACE, ENOMEM, ETRUNC, ETIMEOUT, ECUDA = range(7)
 FLAG_UNSORTED = 1
 PATH_AUTO, PATH_SORT, PATH_HASH = 0, 1, 2
+STAGES = ("ingest", "sort", "reduce", "races", "blocks")
 
 RACE_DTYPE = np.dtype([("space", "u1"), ("scope", "u1"), ("cls", "u1"), ("pad", "u1"),
                        ("block", "<u4"), ("epoch", "<u4"), ("unit", "<u4"),
@@ -81,10 +82,13 @@ def lib():
             "simulee_batch_workspace_size": [vp, P(Trace), u32, P(ctypes.c_size_t)],
             "simulee_check_batch": [vp, P(Trace), u32, P(Outputs), vp, vp, ctypes.c_size_t, vp],
         }
+        sigs["simulee_set_stage_events"] = [vp, P(vp), u32]
         for name, args in sigs.items():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = st
+        L.simulee_last_launches.argtypes = [vp]
+        L.simulee_last_launches.restype = u32
         L.simulee_status_str.argtypes = [st]
         L.simulee_status_str.restype = ctypes.c_char_p
         _lib_handle = L
@@ -161,6 +165,18 @@ class Checker:
             self.close()
         except Exception:
             pass
+
+    def last_launches(self) -> int:
+        """Kernels launched by the last check call."""
+        return int(lib().simulee_last_launches(self.h))
+
+    def set_stage_events(self, events) -> None:
+        """Record the given timing events around the check's stages (2 per stage); None turns it off."""
+        if not events:
+            _check(lib().simulee_set_stage_events(self.h, None, 0), "simulee_set_stage_events")
+            return
+        arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
+        _check(lib().simulee_set_stage_events(self.h, arr, len(events)), "simulee_set_stage_events")
 
     def workspace_size(self, dt: DeviceTrace) -> int:
         n = ctypes.c_size_t()

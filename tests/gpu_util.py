@@ -76,8 +76,9 @@ def sampled_check(tr, got: dict, n_blocks: int = 16, n_units: int = 1500, seed: 
     if not (len(gi) == len(wi) and all(np.array_equal(gi[f], wi[f]) for f in g.dtype.names)):
         bad.append(f"intra races of sampled blocks differ ({len(gi)} vs {len(wi)})")
     gr = got["redundant"][np.isin(got["redundant"]["block"], blocks)]
-    if not np.array_equal(gr, want["redundant"]):
-        bad.append(f"redundant barriers of sampled blocks differ ({len(gr)} vs {len(want['redundant'])})")
+    wr = want["redundant"][np.isin(want["redundant"]["block"], blocks)]
+    if not np.array_equal(gr, wr):
+        bad.append(f"redundant barriers of sampled blocks differ ({len(gr)} vs {len(wr)})")
     # divergence depends on the counts alone
     empty = tracegen.Trace(np.zeros((0, 4), np.uint32), tr.barrier_counts, tr.n_blocks, tr.block_threads,
                            tr.shared_units, tr.global_units, tr.max_barriers)
