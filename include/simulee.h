@@ -195,6 +195,33 @@ simulee_status simulee_check_redundant_barriers(simulee_ctx *ctx, const simulee_
                                                 size_t ws_bytes, void *stream);
 
 /*
+ * simulee_check_noalloc: the full check (as simulee_check) for callers that
+ * cannot allocate device memory: code that runs under a fixed device-memory
+ * plan decided at start-up (a server that reserves all GPU memory up front and
+ * forbids later allocations), or latency-critical loops where the implicit
+ * device synchronisation of cudaMalloc/cudaFree is not acceptable. This entry
+ * point allocates nothing: instead of a caller workspace it uses one fixed
+ * scratch array of SIMULEE_NOALLOC_SCRATCH_BYTES that the library holds in
+ * static device memory; every GPU that loads the library keeps that array until
+ * the process exits. The caller still owns and passes the trace, the outputs
+ * and the report.
+ *   - Size limit: the trace's simulee_workspace_size must not exceed
+ *     SIMULEE_NOALLOC_SCRATCH_BYTES; larger traces are rejected with
+ *     SIMULEE_ENOMEM before any device work is queued.
+ *   - The first call on a device looks up the array's device address (once per
+ *     device, with that device current); make that first call before any
+ *     stream capture is started on that device.
+ *   - All calls in the process share the one array (its contents persist from
+ *     call to call; each call clears what it needs to start from zero). Calls
+ *     that could overlap on the GPU - on different streams, or from different
+ *     threads - race on the array: serialise them, e.g. on one stream.
+ * The paper has no counterpart of this entry point; it is a deployment aid.
+ */
+#define SIMULEE_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+simulee_status simulee_check_noalloc(simulee_ctx *ctx, const simulee_trace *trace, const simulee_outputs *out,
+                                     simulee_report *report, void *stream);
+
+/*
  * Batched check: n_traces independent traces checked together, each with its
  * own outputs and report (reports: device array of n_traces). Results equal
  * those of checking each trace alone. traces and outs are host arrays read

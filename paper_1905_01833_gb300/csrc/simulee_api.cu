@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "../../include/simulee.h"
 #include "check_kernels.cuh"
@@ -529,3 +530,47 @@ const char *simulee_status_str(simulee_status s) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Check without a caller workspace, for callers that cannot allocate device
+// memory. The scratch is this file-scope device array; host code must not use
+// the array's name as an address (on the host it only names the symbol), so the
+// device address is looked up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) uint8_t g_noalloc_scratch[SIMULEE_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoallocMaxDevices];   // device address of the scratch per device, once looked up
+
+// Looks up the scratch address on `device`; the caller has made `device` current.
+simulee_status noalloc_scratch(int device, void **ptr) {
+    if (device < 0 || device >= kNoallocMaxDevices) return SIMULEE_EINVAL;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SIMULEE_ECUDA;
+        g_noalloc_ptr[device] = p;
+    }
+    *ptr = g_noalloc_ptr[device];
+    return SIMULEE_OK;
+}
+}  // namespace
+
+extern "C" simulee_status simulee_check_noalloc(simulee_ctx *ctx, const simulee_trace *trace,
+                                                const simulee_outputs *out, simulee_report *report, void *stream) {
+    if (!ctx || !trace) return SIMULEE_EINVAL;
+    size_t need = 0;
+    simulee_status s = simulee_workspace_size(ctx, trace, &need);
+    if (s != SIMULEE_OK) return s;
+    if (need > (size_t)SIMULEE_NOALLOC_SCRATCH_BYTES) return SIMULEE_ENOMEM;
+    int prev_dev = -1;
+    if (cudaGetDevice(&prev_dev) != cudaSuccess) return SIMULEE_ECUDA;
+    if (prev_dev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return SIMULEE_ECUDA;
+    void *scratch = nullptr;
+    s = noalloc_scratch(ctx->device, &scratch);
+    if (prev_dev != ctx->device) cudaSetDevice(prev_dev);
+    if (s != SIMULEE_OK) return s;
+    return simulee_check(ctx, trace, out, report, scratch, (size_t)SIMULEE_NOALLOC_SCRATCH_BYTES, stream);
+}

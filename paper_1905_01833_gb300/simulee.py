@@ -83,6 +83,7 @@ def lib():
             "simulee_check_batch": [vp, P(Trace), u32, P(Outputs), vp, vp, ctypes.c_size_t, vp],
         }
         sigs["simulee_set_stage_events"] = [vp, P(vp), u32]
+        sigs["simulee_check_noalloc"] = [vp, P(Trace), P(Outputs), vp, vp]
         for name, args in sigs.items():
             f = getattr(L, name)
             f.argtypes = args
