@@ -1,6 +1,7 @@
 // check_kernels.cuh - ingest, segmented reduction and output kernels of the check.
 #pragma once
 #include "common.cuh"
+#include "sort.cuh"
 
 namespace simk {
 
@@ -223,75 +224,181 @@ __device__ __forceinline__ void mark_needed(uint32_t *nonred, const Layout &L, u
 }
 
 // ---------------------------------------------------------------------------
-// Intra-block reduction over a stream sorted by (block, unit, epoch): one walker
-// per (block, unit) run visits its epochs in order, reduces each epoch group to
-// its top-2 summary, emits the group's races, and tests each pair of
-// consecutive epochs k, k+1 for a conflict (barrier k not redundant).
+// Segmented reductions over a sorted stream, one thread per group.
+//
+// A CTA loads a tile of 2048 sorted elements into shared memory, finds the
+// group heads (key changes), and owns the groups whose head lies in its tile;
+// a group that runs past the tile end is finished from global memory by its
+// owner. Each group is reduced to its top-2 summary in registers (groups are a
+// few elements long), emits its races, and leaves a compact adjacency summary
+// in shared memory.
+//
+// Intra streams (key = block, unit, epoch with the epoch in the low bits):
+// group (b, u, e) and the group after it are epochs e and e+1 of the same unit
+// exactly when the next key is key + 1; a conflict between their summaries
+// marks barrier e of block b as needed. The owner of a tile's last group also
+// summarises the group that follows (owned by a later tile) for this test.
+// Inter stream (key = global unit): owners are blocks; no adjacency.
 // ---------------------------------------------------------------------------
-template <class K>
-__global__ void __launch_bounds__(256)
-k_reduce_intra(const K *__restrict__ keys, const uint64_t *__restrict__ vals, const uint32_t *n_ptr, Layout L,
-               uint32_t space, uint32_t bu, Ctl *ctl, uint32_t *nonred, RaceStage rs) {
-    if (must_stop(ctl)) return;
-    const uint64_t n = *n_ptr;
-    const uint32_t be = L.be;
-    const K emask = (K)((1ull << be) - 1);
-    const uint64_t umask = (1ull << bu) - 1;
-    const OwnThread own;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const K ki = keys[i];
-        const K sk = ki >> be;
-        if (i > 0 && (keys[i - 1] >> be) == sk) continue;   // not the head of a (block, unit) run
-        const uint32_t block = (uint32_t)((uint64_t)sk >> bu), unit = (uint32_t)((uint64_t)sk & umask);
-        Top2 cur, prev;
-        cur.clear();
-        prev.clear();
-        int cur_e = -1, prev_e = -1;
-        for (uint64_t j = i; j < n; j++) {
-            const K kj = keys[j];
-            if ((kj >> be) != sk) break;
-            const int e = (int)(kj & emask);
-            if (e != cur_e) {
-                if (cur_e >= 0) {
-                    emit_group(L, rs, ctl, cur, own, space, 0u, block, (uint32_t)cur_e, unit);
-                    if (prev_e >= 0 && cur_e == prev_e + 1 && any_conflict(prev, cur))
-                        mark_needed(nonred, L, block, (uint32_t)prev_e);
-                    prev = cur;
-                    prev_e = cur_e;
-                }
-                cur.clear();
-                cur_e = e;
-            }
-            const uint64_t v = vals[j];
-            top2_add(cur, payload_act(v), payload_item(v), own);
-        }
-        emit_group(L, rs, ctl, cur, own, space, 0u, block, (uint32_t)cur_e, unit);
-        if (prev_e >= 0 && cur_e == prev_e + 1 && any_conflict(prev, cur))
-            mark_needed(nonred, L, block, (uint32_t)prev_e);
+constexpr int RG_THREADS = 256;
+constexpr int RG_ITEMS = 8;
+constexpr int RG_TILE = RG_THREADS * RG_ITEMS;
+
+// compact summary for the cross-epoch conflict test: per category the owner of
+// its earliest item (or none) and whether a second owner exists
+struct Adj {
+    uint32_t own[3];
+    uint32_t multi;   // bit c: category c has two or more owners
+};
+
+__device__ __forceinline__ Adj adj_of(const Top2 &s) {
+    Adj a;
+    a.multi = 0;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        a.own[c] = s.a[c] == EMPTY ? 0xFFFFFFFFu : (uint32_t)s.a[c];
+        if (s.b[c] != EMPTY) a.multi |= 1u << c;
     }
+    return a;
 }
 
-// ---------------------------------------------------------------------------
-// Inter-block reduction over the global stream sorted by unit: one walker per
-// unit reduces all its records to a top-2 summary whose owners are blocks, and
-// emits the unit's inter-block races.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256)
-k_reduce_inter(const uint32_t *__restrict__ keys, const uint64_t *__restrict__ vals, const uint32_t *n_ptr,
-               Layout L, Ctl *ctl, RaceStage rs) {
+__device__ __forceinline__ bool adj_conflict(const Adj &P, const Adj &Q) {
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        if (P.own[i] == 0xFFFFFFFFu) continue;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            if (Q.own[j] == 0xFFFFFFFFu) continue;
+            if ((i == 0 && j == 0) || (i == 2 && j == 2)) continue;   // read/read, atomic/atomic
+            if (((P.multi >> i) & 1u) || ((Q.multi >> j) & 1u) || P.own[i] != Q.own[j]) return true;
+        }
+    }
+    return false;
+}
+
+template <class K, bool INTER>
+constexpr size_t reduce_groups_smem() {
+    return (size_t)RG_TILE * (8 + sizeof(K)) + (INTER ? 0 : (RG_TILE + 1) * sizeof(Adj)) + (RG_TILE + 2) * 2;
+}
+
+template <class K, bool INTER>
+__global__ void __launch_bounds__(RG_THREADS)
+k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, const uint32_t *n_ptr, Layout L,
+                uint32_t space, uint32_t bu, Ctl *ctl, uint32_t *nonred, RaceStage rs) {
+    extern __shared__ __align__(16) uint8_t rg_smem[];
+    uint64_t *sval = reinterpret_cast<uint64_t *>(rg_smem);
+    K *skey = reinterpret_cast<K *>(rg_smem + RG_TILE * 8);
+    Adj *sadj = reinterpret_cast<Adj *>(rg_smem + RG_TILE * (8 + sizeof(K)));
+    uint16_t *shead = reinterpret_cast<uint16_t *>(rg_smem + RG_TILE * (8 + sizeof(K)) + (INTER ? 0 : (RG_TILE + 1) * sizeof(Adj)));
+    __shared__ uint32_t wsum[RG_THREADS / 32];
+    __shared__ K s_next_key;
+    __shared__ uint32_t s_has_next;
     if (must_stop(ctl)) return;
     const uint64_t n = *n_ptr;
-    const OwnBlock own{L.bt};
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t u = keys[i];
-        if (i > 0 && keys[i - 1] == u) continue;
-        Top2 s;
-        s.clear();
-        for (uint64_t j = i; j < n && keys[j] == u; j++) {
-            const uint64_t v = vals[j];
-            top2_add(s, payload_act(v), payload_item(v), own);
+    const uint64_t ntiles = (n + RG_TILE - 1) / RG_TILE;
+    const int tid = threadIdx.x;
+    const uint32_t be = L.be;
+    const uint64_t umask = (bu >= 64) ? ~0ull : ((1ull << bu) - 1);
+    const OwnThread own_t;
+    const OwnBlock own_b{L.bt};
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint64_t t0 = tile * RG_TILE;
+        const uint32_t m = (uint32_t)min((uint64_t)RG_TILE, n - t0);
+        for (uint32_t i = tid; i < m; i += RG_THREADS) {
+            skey[i] = keys[t0 + i];
+            sval[i] = vals[t0 + i];
         }
-        emit_group(L, rs, ctl, s, own, 1u, 1u, 0u, 0u, u);
+        __syncthreads();
+        // heads of the elements [tid*8, tid*8+8)
+        uint32_t hm = 0;
+        const K kprev0 = (t0 > 0) ? keys[t0 - 1] : K(0);
+#pragma unroll
+        for (int j = 0; j < RG_ITEMS; j++) {
+            const uint32_t i = tid * RG_ITEMS + j;
+            if (i < m) {
+                const bool h = (t0 + i == 0) || (i == 0 ? skey[0] != kprev0 : skey[i] != skey[i - 1]);
+                hm |= (h ? 1u : 0u) << j;
+            }
+        }
+        const uint32_t nh = __popc(hm);
+        const uint32_t base = block_excl_scan_256(nh, wsum);
+        {
+            uint32_t o = base;
+#pragma unroll
+            for (int j = 0; j < RG_ITEMS; j++)
+                if ((hm >> j) & 1u) shead[o++] = (uint16_t)(tid * RG_ITEMS + j);
+        }
+        if (tid == RG_THREADS - 1) wsum[0] = base + nh;   // number of groups owned by this tile
+        __syncthreads();
+        const uint32_t G = wsum[0];
+        if (tid == 0) s_has_next = 0;
+        __syncthreads();
+        for (uint32_t g = tid; g < G; g += RG_THREADS) {
+            const uint32_t st = shead[g];
+            const K kg = skey[st];
+            Top2 S;
+            S.clear();
+            uint64_t cnt = 0;
+            uint64_t e;   // element index one past the group (absolute)
+            if (g + 1 < G) {
+                const uint32_t en = shead[g + 1];
+                for (uint32_t j = st; j < en; j++) {
+                    const uint64_t v = sval[j];
+                    if (INTER) top2_add(S, payload_act(v), payload_item(v), own_b);
+                    else top2_add(S, payload_act(v), payload_item(v), own_t);
+                }
+                cnt = en - st;
+                e = t0 + en;
+            } else {
+                uint64_t j = t0 + st;
+                for (; j < n; j++) {
+                    const K kj = (j < t0 + m) ? skey[j - t0] : keys[j];
+                    if (kj != kg) break;
+                    const uint64_t v = (j < t0 + m) ? sval[j - t0] : vals[j];
+                    if (INTER) top2_add(S, payload_act(v), payload_item(v), own_b);
+                    else top2_add(S, payload_act(v), payload_item(v), own_t);
+                }
+                cnt = j - (t0 + st);
+                e = j;
+            }
+            if (INTER) {
+                if (cnt >= 2) emit_group(L, rs, ctl, S, own_b, 1u, 1u, 0u, 0u, (uint32_t)kg);
+            } else {
+                const uint64_t sk = (uint64_t)kg >> be;
+                const uint32_t block = (uint32_t)(sk >> bu), unit = (uint32_t)(sk & umask);
+                const uint32_t epoch = (uint32_t)((uint64_t)kg & ((1ull << be) - 1));
+                if (cnt >= 2) emit_group(L, rs, ctl, S, own_t, space, 0u, block, epoch, unit);
+                sadj[g] = adj_of(S);
+                if (g + 1 == G && e < n) {
+                    // the following group belongs to a later tile: summarise it for the adjacency test
+                    const K kn = keys[e];
+                    Top2 T;
+                    T.clear();
+                    for (uint64_t j = e; j < n && keys[j] == kn; j++) {
+                        const uint64_t v = vals[j];
+                        top2_add(T, payload_act(v), payload_item(v), own_t);
+                    }
+                    sadj[G] = adj_of(T);
+                    s_next_key = kn;
+                    s_has_next = 1;
+                }
+            }
+        }
+        __syncthreads();
+        if (!INTER) {
+            for (uint32_t g = tid; g < G; g += RG_THREADS) {
+                const K kg = skey[shead[g]];
+                bool has = false;
+                K kn = 0;
+                if (g + 1 < G) { has = true; kn = skey[shead[g + 1]]; }
+                else if (s_has_next) { has = true; kn = s_next_key; }
+                if (has && kn == kg + 1 && adj_conflict(sadj[g], sadj[g + 1])) {
+                    const uint64_t sk = (uint64_t)kg >> be;
+                    mark_needed(nonred, L, (uint32_t)(sk >> bu), (uint32_t)((uint64_t)kg & ((1ull << be) - 1)));
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 

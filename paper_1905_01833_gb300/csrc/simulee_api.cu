@@ -141,6 +141,12 @@ void set_sort_attr() {
     cudaFuncSetAttribute(k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem<K>());
 }
 
+template <class K, bool INTER>
+void set_reduce_attr() {
+    cudaFuncSetAttribute(k_reduce_groups<K, INTER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)reduce_groups_smem<K, INTER>());
+}
+
 struct Run {
     simulee_ctx *ctx;
     cudaStream_t st;
@@ -227,6 +233,9 @@ simulee_status launch_check(simulee_ctx *ctx, const simulee_trace *t, const simu
     if (!ctx->attrs_set) {
         set_sort_attr<uint32_t>();
         set_sort_attr<uint64_t>();
+        set_reduce_attr<uint32_t, false>();
+        set_reduce_attr<uint64_t, false>();
+        set_reduce_attr<uint32_t, true>();
         ctx->attrs_set = true;
     }
     R.st = (cudaStream_t)stream;
@@ -329,21 +338,21 @@ simulee_status launch_check(simulee_ctx *ctx, const simulee_trace *t, const simu
     rs.n_pos = L.n;
     if (sorting) {
         uint32_t *nonred = R.at<uint32_t>(L.off_nonred);
-        const int gr = (int)std::max<uint64_t>(1, std::min<uint64_t>((L.n + 255) / 256, (uint64_t)sms * 8));
+        const int gr = (int)std::max<uint64_t>(1, std::min<uint64_t>((L.n + RG_TILE - 1) / RG_TILE, (uint64_t)sms * 3));
         if (L.wide_s)
-            k_reduce_intra<uint64_t><<<gr, 256, 0, st>>>(R.at<uint64_t>(L.off_sk[bs]), R.at<uint64_t>(L.off_sv[bs]),
-                                                        &R.ctl->n_s, L, 0u, L.bus, R.ctl, nonred, rs);
+            k_reduce_groups<uint64_t, false><<<gr, RG_THREADS, reduce_groups_smem<uint64_t, false>(), st>>>(
+                R.at<uint64_t>(L.off_sk[bs]), R.at<uint64_t>(L.off_sv[bs]), &R.ctl->n_s, L, 0u, L.bus, R.ctl, nonred, rs);
         else
-            k_reduce_intra<uint32_t><<<gr, 256, 0, st>>>(R.at<uint32_t>(L.off_sk[bs]), R.at<uint64_t>(L.off_sv[bs]),
-                                                        &R.ctl->n_s, L, 0u, L.bus, R.ctl, nonred, rs);
+            k_reduce_groups<uint32_t, false><<<gr, RG_THREADS, reduce_groups_smem<uint32_t, false>(), st>>>(
+                R.at<uint32_t>(L.off_sk[bs]), R.at<uint64_t>(L.off_sv[bs]), &R.ctl->n_s, L, 0u, L.bus, R.ctl, nonred, rs);
         if (L.wide_g)
-            k_reduce_intra<uint64_t><<<gr, 256, 0, st>>>(R.at<uint64_t>(L.off_gk[bg]), R.at<uint64_t>(L.off_gv[bg]),
-                                                        &R.ctl->n_g, L, 1u, L.bug, R.ctl, nonred, rs);
+            k_reduce_groups<uint64_t, false><<<gr, RG_THREADS, reduce_groups_smem<uint64_t, false>(), st>>>(
+                R.at<uint64_t>(L.off_gk[bg]), R.at<uint64_t>(L.off_gv[bg]), &R.ctl->n_g, L, 1u, L.bug, R.ctl, nonred, rs);
         else
-            k_reduce_intra<uint32_t><<<gr, 256, 0, st>>>(R.at<uint32_t>(L.off_gk[bg]), R.at<uint64_t>(L.off_gv[bg]),
-                                                        &R.ctl->n_g, L, 1u, L.bug, R.ctl, nonred, rs);
-        k_reduce_inter<<<gr, 256, 0, st>>>(R.at<uint32_t>(L.off_xk[bx]), R.at<uint64_t>(L.off_xv[bx]), &R.ctl->n_g,
-                                           L, R.ctl, rs);
+            k_reduce_groups<uint32_t, false><<<gr, RG_THREADS, reduce_groups_smem<uint32_t, false>(), st>>>(
+                R.at<uint32_t>(L.off_gk[bg]), R.at<uint64_t>(L.off_gv[bg]), &R.ctl->n_g, L, 1u, L.bug, R.ctl, nonred, rs);
+        k_reduce_groups<uint32_t, true><<<gr, RG_THREADS, reduce_groups_smem<uint32_t, true>(), st>>>(R.at<uint32_t>(L.off_xk[bx]), R.at<uint64_t>(L.off_xv[bx]),
+                                                                  &R.ctl->n_g, L, 1u, L.bug, R.ctl, nonred, rs);
         R.launches += 3;
     }
     R.mark(SIMULEE_STAGE_REDUCE, 1);
