@@ -1,25 +1,46 @@
 // check_kernels.cuh - ingest, segmented reduction and output kernels of the check.
+//
+// Every kernel works on a batch of traces described by TraceDesc entries; a
+// single-trace call is a batch of one. Blocks are numbered batch-wide (trace
+// t's block b is block_off[t] + b), keys of the intra-block streams carry that
+// batch-wide block, and the inter-block stream's key carries the trace index,
+// so groups never mix traces. Outputs are split back per trace at the end.
 #pragma once
 #include "common.cuh"
 #include "sort.cuh"
 
 namespace simk {
 
+__device__ __forceinline__ uint32_t trace_of_tile(const TraceDesc *td, uint32_t T, uint64_t tile) {
+    return find_trace(T, tile, [&](uint32_t t) { return td[t].tile_off; });
+}
+
+// batch-wide block -> trace
+__global__ void k_block_trace(const TraceDesc *td, Layout L, uint32_t *tob) {
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < L.NB; b += (uint64_t)gridDim.x * blockDim.x)
+        tob[b] = find_trace(L.T, b, [&](uint32_t t) { return (uint64_t)td[t].block_off; });
+}
+
 // ---------------------------------------------------------------------------
 // Barrier counts: per-block min / max / first thread at the min (Algorithm 4's
 // divergence test is "threads of a block reached different barrier counts"),
 // plus validation of every count. One warp per block.
+// stats[b] = (min, min(max, max_barriers), first tid at min, max).
 // ---------------------------------------------------------------------------
-__global__ void k_block_stats(const uint32_t *__restrict__ counts, Layout L, uint4 *stats, Ctl *ctl) {
+__global__ void k_block_stats(const TraceDesc *td, const uint32_t *tob, Layout L, uint4 *stats, TState *ts) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t b = warp; b < L.nb; b += nwarps) {
+    for (uint64_t b = warp; b < L.NB; b += nwarps) {
+        const uint32_t t = tob[b];
+        const TraceDesc &d = td[t];
+        const uint64_t lb = b - d.block_off;
+        const uint32_t *cnt = d.counts + lb * d.bt;
         uint32_t mn = 0xFFFFFFFFu, mx = 0, first = 0xFFFFFFFFu;
-        for (uint32_t t = lane; t < L.bt; t += 32) {
-            const uint32_t c = counts[b * L.bt + t];
-            if (c > L.maxb) atomicMax(&ctl->bad_cnt, ~(unsigned long long)(b * L.bt + t));
-            if (c < mn) { mn = c; first = t; }
+        for (uint32_t i = lane; i < d.bt; i += 32) {
+            const uint32_t c = cnt[i];
+            if (c > d.maxb) atomicMax(&ts[t].bad_cnt, ~(unsigned long long)(lb * d.bt + i));
+            if (c < mn) { mn = c; first = i; }
             mx = max(mx, c);
         }
 #pragma unroll
@@ -29,10 +50,7 @@ __global__ void k_block_stats(const uint32_t *__restrict__ counts, Layout L, uin
             mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
             if (omn < mn || (omn == mn && ofi < first)) { mn = omn; first = ofi; }
         }
-        if (lane == 0) {
-            stats[b] = make_uint4(mn, mx, first, 0);
-            atomicMax(&ctl->max_count, mx);
-        }
+        if (lane == 0) stats[b] = make_uint4(mn, min(mx, L.maxb), first, mx);
     }
 }
 
@@ -63,19 +81,19 @@ __device__ __forceinline__ void hist_add(uint32_t *sh, uint64_t key, uint32_t np
 // Ingest: read every record once (16-byte loads), validate it, and route it:
 // shared records to the intra stream S keyed (block, unit, epoch); global
 // records to the intra stream G keyed (block, unit, epoch) and to the
-// inter-block stream X keyed (unit). Builds the digit histograms of all radix
-// passes. Persistent CTAs over tiles of 2048 records.
+// inter-block stream X keyed (trace, unit). Builds the digit histograms of all
+// radix passes. Persistent CTAs over tiles of 2048 records; a tile never
+// spans two traces.
 // ---------------------------------------------------------------------------
 constexpr int IN_THREADS = 256;
 constexpr int IN_ITEMS = 8;
 constexpr int IN_TILE = IN_THREADS * IN_ITEMS;
-constexpr int IN_MAXP = 20;   // S + G + X passes histogrammed here
+constexpr int IN_MAXP = 24;   // S + G + X passes histogrammed here
 
-template <class KS, class KG, bool ROUTE>
+template <class KS, class KG, class KX, bool ROUTE>
 __global__ void __launch_bounds__(IN_THREADS)
-k_ingest(const uint4 *__restrict__ ev, const uint32_t *__restrict__ counts, const uint32_t *__restrict__ rank,
-         Layout L, Ctl *ctl, KS *sk, uint64_t *sv, KG *gk, uint64_t *gv, uint32_t *xk, uint64_t *xv,
-         uint32_t *hist) {
+k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, Layout L, TState *ts, Ctl *ctl,
+         KS *sk, uint64_t *sv, KG *gk, uint64_t *gv, KX *xk, uint64_t *xv, uint32_t *hist) {
     __shared__ uint32_t sh[IN_MAXP * RADIX];
     __shared__ uint32_t wtot[IN_THREADS / 32][2];
     __shared__ uint32_t cbase[2];
@@ -85,48 +103,54 @@ k_ingest(const uint4 *__restrict__ ev, const uint32_t *__restrict__ counts, cons
     uint32_t *hs = sh, *hg = sh + np_s * RADIX, *hx = hg + np_g * RADIX;
     for (int i = tid; i < IN_MAXP * RADIX; i += IN_THREADS) sh[i] = 0;
     __syncthreads();
-    const bool sorted = (L.flags & 1u) == 0;
-    const uint64_t ntiles = (L.n + IN_TILE - 1) / IN_TILE;
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (uint64_t tile = blockIdx.x; tile < L.ntiles_in; tile += gridDim.x) {
+        const uint32_t t = trace_of_tile(td, L.T, tile);
+        const TraceDesc &d = td[t];
+        const uint4 *ev = d.events;
+        const uint64_t tbase = (tile - d.tile_off) * IN_TILE;
+        const bool sorted = (d.flags & 1u) == 0;
         uint32_t cS = 0, cG = 0;
         uint32_t rS[IN_ITEMS], rG[IN_ITEMS];
         uint64_t val[IN_ITEMS];
         KS ks[IN_ITEMS];
         KG kg[IN_ITEMS];
-        uint32_t unit[IN_ITEMS];
+        KX kx[IN_ITEMS];
         uint32_t route = 0;   // bit j: S, bit 8+j: G
 #pragma unroll
         for (int j = 0; j < IN_ITEMS; j++) {
-            const uint64_t idx = tile * IN_TILE + (uint64_t)j * IN_THREADS + tid;
+            const uint64_t idx = tbase + (uint64_t)j * IN_THREADS + tid;   // record index in the trace
             uint4 e = make_uint4(0, 0, 0, 0);
-            const bool in = idx < L.n;
+            const bool in = idx < d.n;
             if (in) e = ev[idx];
             uint32_t prev_vo = __shfl_up_sync(0xFFFFFFFFu, e.y, 1);
             if (lane == 0 && in && idx > 0) prev_vo = ev[idx - 1].y;
             const uint32_t u = e.x, vo = e.y, blk = e.z, w3 = e.w;
-            const uint32_t t = w3 & 0xFFFFu, ep = (w3 >> 16) & 0xFFFu, act = (w3 >> 28) & 3u;
+            const uint32_t tt = w3 & 0xFFFFu, ep = (w3 >> 16) & 0xFFFu, act = (w3 >> 28) & 3u;
             const uint32_t space = (w3 >> 30) & 1u, resv = w3 >> 31;
-            bool ok = in && blk < L.nb && t < L.bt && act != 3u && resv == 0u && (space ? u < L.gu : u < L.su);
-            const uint32_t gtid = blk * L.bt + t;
-            if (ok && ep > counts[gtid]) ok = false;
+            bool ok = in && blk < d.nb && tt < d.bt && act != 3u && resv == 0u && (space ? u < d.gu : u < d.su);
+            const uint32_t gtid = blk * d.bt + tt;
+            if (ok && ep > d.counts[gtid]) ok = false;
             if (in && sorted && idx > 0 && vo <= prev_vo) ok = false;
-            if (in && !ok) atomicMax(&ctl->bad_rec, ~(unsigned long long)idx);
-            const bool isS = ROUTE && ok && space == 0u, isG = ROUTE && ok && space == 1u;
+            if (in && !ok) atomicMax(&ts[t].bad_rec, ~(unsigned long long)idx);
+            // routed records also keep the epoch inside the key's epoch field
+            const bool route_ok = ROUTE && ok && ep <= d.maxb;
+            const bool isS = route_ok && space == 0u, isG = route_ok && space == 1u;
             const uint32_t bS = __ballot_sync(0xFFFFFFFFu, isS), bG = __ballot_sync(0xFFFFFFFFu, isG);
             rS[j] = cS + __popc(bS & lt);
             rG[j] = cG + __popc(bG & lt);
             cS += __popc(bS);
             cG += __popc(bG);
-            const uint32_t pos = sorted ? vo : (in ? rank[idx] : 0u);
+            const uint32_t pos = sorted ? vo : (in ? rank[d.rec_off + idx] : 0u);
             val[j] = make_payload(act, gtid, pos);
-            ks[j] = (KS)(shl(blk, L.bus + L.be) | shl(u, L.be) | ep);
-            kg[j] = (KG)(shl(blk, L.bug + L.be) | shl(u, L.be) | ep);
-            unit[j] = u;
+            const uint64_t sb = (uint64_t)d.block_off + blk;
+            ks[j] = (KS)(shl(sb, L.bus + L.be) | shl(u, L.be) | ep);
+            kg[j] = (KG)(shl(sb, L.bug + L.be) | shl(u, L.be) | ep);
+            kx[j] = (KX)(shl(t, L.bug) | u);
             route |= (isS ? 1u : 0u) << j;
             route |= (isG ? 1u : 0u) << (8 + j);
             hist_add(hs, (uint64_t)ks[j], np_s, isS, bS);
             hist_add(hg, (uint64_t)kg[j], np_g, isG, bG);
-            hist_add(hx, (uint64_t)u, np_x, isG, bG);
+            hist_add(hx, (uint64_t)kx[j], np_x, isG, bG);
         }
         if (lane == 0) { wtot[w][0] = cS; wtot[w][1] = cG; }
         __syncthreads();
@@ -151,7 +175,7 @@ k_ingest(const uint4 *__restrict__ ev, const uint32_t *__restrict__ counts, cons
             if (route & (1u << (8 + j))) {
                 gk[oG + rG[j]] = kg[j];
                 gv[oG + rG[j]] = val[j];
-                xk[oG + rG[j]] = unit[j];
+                xk[oG + rG[j]] = kx[j];
                 xv[oG + rG[j]] = val[j];
             }
         }
@@ -171,7 +195,9 @@ k_ingest(const uint4 *__restrict__ ev, const uint32_t *__restrict__ counts, cons
 
 // ---------------------------------------------------------------------------
 // Race staging: canonical key + payload (vo_first, vo_second, gtid_first, gtid_second).
-// Canonical key bits, low to high: cls(1) unit(bu) epoch(be) block(bb) scope(1) space(1).
+// Canonical key bits, low to high: cls(1) unit(bu) epoch(be) block(bb) scope(1)
+// space(1) trace(btr); the block field holds the batch-wide block, which orders
+// a trace's blocks like its own block numbers.
 // ---------------------------------------------------------------------------
 struct RaceStage {
     uint64_t *keys;
@@ -180,26 +206,31 @@ struct RaceStage {
     uint64_t cap;
     const uint32_t *pos_to_vo;   // unsorted traces: schedule position -> visit order (else NULL)
     uint64_t n_pos;              // entries of pos_to_vo
+    TState *ts;
+    const TraceDesc *td;
 };
 
-__device__ __forceinline__ uint64_t race_key(const Layout &L, uint32_t space, uint32_t scope, uint32_t block,
-                                             uint32_t epoch, uint32_t unit, uint32_t cls) {
+__device__ __forceinline__ uint64_t race_key(const Layout &L, uint32_t trace, uint32_t space, uint32_t scope,
+                                             uint32_t block, uint32_t epoch, uint32_t unit, uint32_t cls) {
     uint64_t k = cls;
     k |= (uint64_t)unit << 1;
     k |= (uint64_t)epoch << (1 + L.bu);
     k |= (uint64_t)block << (1 + L.bu + L.be);
     k |= (uint64_t)scope << (1 + L.bu + L.be + L.bb);
     k |= (uint64_t)space << (2 + L.bu + L.be + L.bb);
+    k |= shl(trace, 3 + L.bu + L.be + L.bb);
     return k;
 }
 
-__device__ __forceinline__ void emit_race(const RaceStage &rs, Ctl *ctl, uint64_t key, uint64_t p, uint64_t q) {
+__device__ __forceinline__ void emit_race(const RaceStage &rs, Ctl *ctl, uint32_t trace, uint64_t key, uint64_t p,
+                                          uint64_t q) {
     const uint32_t slot = atomicAdd(&ctl->n_races, 1u);
+    atomicAdd(&rs.ts[trace].n_races, 1u);
     if (slot < rs.cap) {
         rs.keys[slot] = key;
         rs.idx[slot] = slot;
         uint32_t vp = item_pos(p), vq = item_pos(q);
-        if (rs.pos_to_vo) {
+        if (rs.pos_to_vo && (rs.td[trace].flags & 1u)) {
             vp = vp < rs.n_pos ? rs.pos_to_vo[vp] : 0u;
             vq = vq < rs.n_pos ? rs.pos_to_vo[vq] : 0u;
         }
@@ -209,18 +240,19 @@ __device__ __forceinline__ void emit_race(const RaceStage &rs, Ctl *ctl, uint64_
 
 template <class Own>
 __device__ __forceinline__ void emit_group(const Layout &L, const RaceStage &rs, Ctl *ctl, const Top2 &s,
-                                           const Own &own, uint32_t space, uint32_t scope, uint32_t block,
-                                           uint32_t epoch, uint32_t unit) {
+                                           const Own &own, uint32_t trace, uint32_t space, uint32_t scope,
+                                           uint32_t block, uint32_t epoch, uint32_t unit) {
 #pragma unroll
     for (int cls = 0; cls < 2; cls++) {
         uint64_t p, q;
-        if (lowest_pair(s, cls, own, p, q)) emit_race(rs, ctl, race_key(L, space, scope, block, epoch, unit, cls), p, q);
+        if (lowest_pair(s, cls, own, p, q))
+            emit_race(rs, ctl, trace, race_key(L, trace, space, scope, block, epoch, unit, cls), p, q);
     }
 }
 
-// barrier k of block b is needed (not redundant)
+// barrier k of batch-wide block b is needed (not redundant)
 __device__ __forceinline__ void mark_needed(uint32_t *nonred, const Layout &L, uint32_t block, uint32_t k) {
-    if (block < L.nb && (k >> 5) < L.words) atomicOr(&nonred[(uint64_t)block * L.words + (k >> 5)], 1u << (k & 31));
+    if (block < L.NB && (k >> 5) < L.words) atomicOr(&nonred[(uint64_t)block * L.words + (k >> 5)], 1u << (k & 31));
 }
 
 // ---------------------------------------------------------------------------
@@ -238,7 +270,7 @@ __device__ __forceinline__ void mark_needed(uint32_t *nonred, const Layout &L, u
 // exactly when the next key is key + 1; a conflict between their summaries
 // marks barrier e of block b as needed. The owner of a tile's last group also
 // summarises the group that follows (owned by a later tile) for this test.
-// Inter stream (key = global unit): owners are blocks; no adjacency.
+// Inter stream (key = trace, global unit): owners are blocks; no adjacency.
 // ---------------------------------------------------------------------------
 constexpr int RG_THREADS = 256;
 constexpr int RG_ITEMS = 8;
@@ -284,12 +316,14 @@ constexpr size_t reduce_groups_smem() {
 template <class K, bool INTER>
 __global__ void __launch_bounds__(RG_THREADS)
 k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, const uint32_t *n_ptr, Layout L,
-                uint32_t space, uint32_t bu, Ctl *ctl, uint32_t *nonred, RaceStage rs) {
+                const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob, uint32_t space, uint32_t bu,
+                Ctl *ctl, uint32_t *nonred, RaceStage rs) {
     extern __shared__ __align__(16) uint8_t rg_smem[];
     uint64_t *sval = reinterpret_cast<uint64_t *>(rg_smem);
     K *skey = reinterpret_cast<K *>(rg_smem + RG_TILE * 8);
     Adj *sadj = reinterpret_cast<Adj *>(rg_smem + RG_TILE * (8 + sizeof(K)));
-    uint16_t *shead = reinterpret_cast<uint16_t *>(rg_smem + RG_TILE * (8 + sizeof(K)) + (INTER ? 0 : (RG_TILE + 1) * sizeof(Adj)));
+    uint16_t *shead = reinterpret_cast<uint16_t *>(rg_smem + RG_TILE * (8 + sizeof(K)) +
+                                                   (INTER ? 0 : (RG_TILE + 1) * sizeof(Adj)));
     __shared__ uint32_t wsum[RG_THREADS / 32];
     __shared__ K s_next_key;
     __shared__ uint32_t s_has_next;
@@ -300,7 +334,6 @@ k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, c
     const uint32_t be = L.be;
     const uint64_t umask = (bu >= 64) ? ~0ull : ((1ull << bu) - 1);
     const OwnThread own_t;
-    const OwnBlock own_b{L.bt};
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint64_t t0 = tile * RG_TILE;
         const uint32_t m = (uint32_t)min((uint64_t)RG_TILE, n - t0);
@@ -309,7 +342,7 @@ k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, c
             sval[i] = vals[t0 + i];
         }
         __syncthreads();
-        // heads of the elements [tid*8, tid*8+8)
+        // heads among the elements [tid*8, tid*8+8)
         uint32_t hm = 0;
         const K kprev0 = (t0 > 0) ? keys[t0 - 1] : K(0);
 #pragma unroll
@@ -336,6 +369,14 @@ k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, c
         for (uint32_t g = tid; g < G; g += RG_THREADS) {
             const uint32_t st = shead[g];
             const K kg = skey[st];
+            uint32_t trace, bt = 1;
+            if (INTER) {
+                trace = (uint32_t)((uint64_t)kg >> L.bug);
+                bt = td[trace].bt;
+            } else {
+                trace = tob[(uint64_t)kg >> (bu + be)];
+            }
+            const OwnBlock own_b{bt};
             Top2 S;
             S.clear();
             uint64_t cnt = 0;
@@ -362,12 +403,13 @@ k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, c
                 e = j;
             }
             if (INTER) {
-                if (cnt >= 2) emit_group(L, rs, ctl, S, own_b, 1u, 1u, 0u, 0u, (uint32_t)kg);
+                if (cnt >= 2)
+                    emit_group(L, rs, ctl, S, own_b, trace, 1u, 1u, 0u, 0u, (uint32_t)((uint64_t)kg & umask));
             } else {
                 const uint64_t sk = (uint64_t)kg >> be;
                 const uint32_t block = (uint32_t)(sk >> bu), unit = (uint32_t)(sk & umask);
                 const uint32_t epoch = (uint32_t)((uint64_t)kg & ((1ull << be) - 1));
-                if (cnt >= 2) emit_group(L, rs, ctl, S, own_t, space, 0u, block, epoch, unit);
+                if (cnt >= 2) emit_group(L, rs, ctl, S, own_t, trace, space, 0u, block, epoch, unit);
                 sadj[g] = adj_of(S);
                 if (g + 1 == G && e < n) {
                     // the following group belongs to a later tile: summarise it for the adjacency test
@@ -405,35 +447,54 @@ k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, c
 // ---------------------------------------------------------------------------
 // Outputs
 // ---------------------------------------------------------------------------
-__global__ void k_write_races(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ idx,
-                              const uint4 *__restrict__ pay, Layout L, Ctl *ctl, uint8_t *out, uint64_t cap) {
+__device__ __forceinline__ uint32_t race_trace(const Layout &L, uint64_t k) {
+    const uint32_t s = 3 + L.bu + L.be + L.bb;
+    return s >= 64 ? 0u : (uint32_t)(k >> s);
+}
+
+// first position of each trace in the sorted race list
+__global__ void k_race_starts(const uint64_t *__restrict__ keys, Layout L, Ctl *ctl, TState *ts) {
     if (must_stop(ctl)) return;
-    const uint64_t n = min((uint64_t)ctl->n_races, min(cap, L.race_cap));
+    const uint64_t n = min((uint64_t)ctl->n_races, L.race_cap);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = race_trace(L, keys[i]);
+        if (t < L.T && (i == 0 || race_trace(L, keys[i - 1]) != t)) ts[t].race_start = (uint32_t)i;
+    }
+}
+
+__global__ void k_write_races(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ idx,
+                              const uint4 *__restrict__ pay, Layout L, const TraceDesc *td, TState *ts, Ctl *ctl) {
+    if (must_stop(ctl)) return;
+    const uint64_t n = min((uint64_t)ctl->n_races, L.race_cap);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t k = keys[i];
+        const uint32_t t = race_trace(L, k);
+        if (t >= L.T || trace_bad(ts[t])) continue;
+        const TraceDesc &d = td[t];
+        const uint64_t rank = i - ts[t].race_start;
+        if (rank >= d.races_cap) continue;
         const uint64_t ix = idx[i];
         if (ix >= L.race_cap) continue;
         const uint4 p = pay[ix];
         const uint32_t cls = (uint32_t)(k & 1u);
         const uint32_t unit = (uint32_t)((k >> 1) & ((1ull << L.bu) - 1));
         uint32_t epoch = (uint32_t)((k >> (1 + L.bu)) & ((1ull << L.be) - 1));
-        uint32_t block = (uint32_t)((k >> (1 + L.bu + L.be)) & ((1ull << L.bb) - 1));
+        uint32_t block = (uint32_t)((k >> (1 + L.bu + L.be)) & ((1ull << L.bb) - 1)) - d.block_off;
         const uint32_t scope = (uint32_t)((k >> (1 + L.bu + L.be + L.bb)) & 1u);
         const uint32_t space = (uint32_t)((k >> (2 + L.bu + L.be + L.bb)) & 1u);
         if (scope) { block = 0xFFFFFFFFu; epoch = 0xFFFFFFFFu; }
-        uint4 *o = reinterpret_cast<uint4 *>(out + 32 * i);
+        uint4 *o = reinterpret_cast<uint4 *>(d.races + 32 * rank);
         o[0] = make_uint4(space | (scope << 8) | (cls << 16), block, epoch, unit);
         o[1] = p;
     }
 }
 
 // per block: divergence flag and number of redundant barriers
-__global__ void k_block_counts(const uint4 *stats, const uint32_t *nonred, Layout L, Ctl *ctl, uint32_t *cnt_div,
+__global__ void k_block_counts(const uint4 *stats, const uint32_t *nonred, Layout L, uint32_t *cnt_div,
                                uint32_t *cnt_red) {
-    if (trace_bad(ctl)) return;
-    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < L.nb; b += (uint64_t)gridDim.x * blockDim.x) {
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < L.NB; b += (uint64_t)gridDim.x * blockDim.x) {
         const uint4 s = stats[b];
-        cnt_div[b] = s.x != s.y ? 1u : 0u;
+        cnt_div[b] = s.x != s.w ? 1u : 0u;
         uint32_t nr = 0;
         for (uint32_t wd = 0; wd < L.words; wd++) {
             const uint32_t lo = wd * 32;
@@ -446,12 +507,11 @@ __global__ void k_block_counts(const uint4 *stats, const uint32_t *nonred, Layou
 }
 
 // Single-CTA exclusive scan (1024 threads) of two count arrays of length m;
-// totals go to *tot_a, *tot_b.
+// oa[m], ob[m] receive the totals.
 __global__ void __launch_bounds__(1024) k_scan2(const uint32_t *a, const uint32_t *b, uint64_t m, uint32_t *oa,
-                                                uint32_t *ob, unsigned int *tot_a, unsigned int *tot_b, Ctl *ctl) {
+                                                uint32_t *ob, Ctl *ctl) {
     __shared__ uint32_t ws[2][32];
     __shared__ uint32_t carry[2];
-    if (trace_bad(ctl)) return;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) { carry[0] = 0; carry[1] = 0; }
     __syncthreads();
@@ -484,59 +544,73 @@ __global__ void __launch_bounds__(1024) k_scan2(const uint32_t *a, const uint32_
         if (tid == 0) { carry[0] += ws[0][31]; carry[1] += ws[1][31]; }
         __syncthreads();
     }
-    if (tid == 0) { *tot_a = carry[0]; *tot_b = carry[1]; }
-}
-
-__global__ void k_block_write(const uint4 *stats, const uint32_t *nonred, Layout L, Ctl *ctl, const uint32_t *ofs_div,
-                              const uint32_t *ofs_red, uint4 *out_div, uint64_t cap_div, uint2 *out_red,
-                              uint64_t cap_red) {
-    if (trace_bad(ctl)) return;
-    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < L.nb; b += (uint64_t)gridDim.x * blockDim.x) {
-        const uint4 s = stats[b];
-        if (s.x != s.y && ofs_div[b] < cap_div) out_div[ofs_div[b]] = make_uint4((uint32_t)b, s.x, s.y, s.z);
-        uint64_t o = ofs_red[b];
-        if (o >= cap_red) continue;
-        for (uint32_t k = 0; k < s.y && o < cap_red; k++)
-            if (!((nonred[b * L.words + (k >> 5)] >> (k & 31)) & 1u)) out_red[o++] = make_uint2((uint32_t)b, k);
+    if (tid == 0) {
+        oa[m] = carry[0];
+        ob[m] = carry[1];
+        ctl->n_div = carry[0];
+        ctl->n_red = carry[1];
     }
 }
 
-// grid-wide: OR of the non-redundant bits and of "barrier exists" over blocks
-__global__ void k_grid_or(const uint4 *stats, const uint32_t *nonred, Layout L, Ctl *ctl, uint32_t *gnr,
+__global__ void k_block_write(const uint4 *stats, const uint32_t *nonred, Layout L, const TraceDesc *td,
+                              const uint32_t *tob, const TState *ts, const uint32_t *ofs_div, const uint32_t *ofs_red,
+                              uint32_t want_div, uint32_t want_red) {
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < L.NB; b += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = tob[b];
+        if (trace_bad(ts[t])) continue;
+        const TraceDesc &d = td[t];
+        const uint4 s = stats[b];
+        const uint64_t lb = b - d.block_off;
+        if (want_div && s.x != s.w) {
+            const uint64_t r = ofs_div[b] - ofs_div[d.block_off];
+            if (r < d.divs_cap) reinterpret_cast<uint4 *>(d.divs)[r] = make_uint4((uint32_t)lb, s.x, s.w, s.z);
+        }
+        if (!want_red) continue;
+        uint64_t o = ofs_red[b] - ofs_red[d.block_off];
+        for (uint32_t k = 0; k < s.y && o < d.reds_cap; k++)
+            if (!((nonred[b * L.words + (k >> 5)] >> (k & 31)) & 1u))
+                reinterpret_cast<uint2 *>(d.reds)[o++] = make_uint2((uint32_t)lb, k);
+    }
+}
+
+// per trace: OR of the non-redundant bits and of "barrier exists" over its blocks
+__global__ void k_grid_or(const uint4 *stats, const uint32_t *nonred, const uint32_t *tob, Layout L, uint32_t *gnr,
                           uint32_t *ghas) {
-    if (trace_bad(ctl)) return;
-    const uint64_t tot = (uint64_t)L.nb * L.words;
+    const uint64_t tot = (uint64_t)L.NB * L.words;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t b = i / L.words;
         const uint32_t wd = (uint32_t)(i % L.words), lo = wd * 32, mx = stats[b].y;
         if (lo >= mx) continue;
         const uint32_t live = (mx - lo >= 32) ? 0xFFFFFFFFu : ((1u << (mx - lo)) - 1u);
+        const uint64_t slot = (uint64_t)tob[b] * L.words + wd;
         const uint32_t nr = nonred[i] & live;
-        if (nr) atomicOr(&gnr[wd], nr);
-        atomicOr(&ghas[wd], live);
+        if (nr) atomicOr(&gnr[slot], nr);
+        atomicOr(&ghas[slot], live);
     }
 }
 
-// single CTA: list every barrier k that exists somewhere and is redundant everywhere
-__global__ void __launch_bounds__(1024) k_grid_list(const uint32_t *gnr, const uint32_t *ghas, Layout L, Ctl *ctl,
-                                                    uint32_t *out, uint64_t cap) {
+// one CTA per trace: list every barrier k that exists in some block and is redundant in all
+__global__ void __launch_bounds__(1024) k_grid_list(const uint32_t *gnr, const uint32_t *ghas, Layout L,
+                                                    const TraceDesc *td, TState *ts) {
     __shared__ uint32_t ws[32];
     __shared__ uint32_t carry;
-    if (trace_bad(ctl)) return;
+    const uint32_t t = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) carry = 0;
     __syncthreads();
     const uint32_t nk = L.words * 32;
+    const uint32_t *nr = gnr + (uint64_t)t * L.words, *hs = ghas + (uint64_t)t * L.words;
+    const uint64_t cap = td[t].grid_cap;
     for (uint32_t base = 0; base < nk; base += 1024) {
         const uint32_t k = base + tid;
-        const bool red = k < nk && ((ghas[k >> 5] >> (k & 31)) & 1u) && !((gnr[k >> 5] >> (k & 31)) & 1u);
+        const bool red = k < nk && ((hs[k >> 5] >> (k & 31)) & 1u) && !((nr[k >> 5] >> (k & 31)) & 1u);
         const uint32_t bal = __ballot_sync(0xFFFFFFFFu, red);
         if (lane == 0) ws[w] = __popc(bal);
         __syncthreads();
         uint32_t pre = carry;
         for (int i = 0; i < w; i++) pre += ws[i];
         pre += __popc(bal & lanemask_lt());
-        if (red && pre < cap) out[pre] = k;
+        if (red && pre < cap && !trace_bad(ts[t])) td[t].grid[pre] = k;
         __syncthreads();
         if (tid == 0) {
             uint32_t s = 0;
@@ -545,41 +619,43 @@ __global__ void __launch_bounds__(1024) k_grid_list(const uint32_t *gnr, const u
         }
         __syncthreads();
     }
-    if (tid == 0) ctl->n_grid = carry;
+    if (tid == 0) ts[t].n_grid = carry;
 }
 
-// final report: status and true counts
+// final report per trace: status and true counts
 struct ReportArgs {
-    uint64_t cap_races, cap_div, cap_red, cap_grid;
     uint32_t want_races, want_div, want_red;
 };
 
-__global__ void k_report(Ctl *ctl, ReportArgs a, uint8_t *report) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    volatile Ctl *c = ctl;
-    int32_t status = 0;
-    uint32_t kind = 0;
-    uint64_t bad = 0, nr = 0, nd = 0, nred = 0, ng = 0;
-    if (c->bad_cnt) {
-        status = 2; kind = 1; bad = ~c->bad_cnt;
-    } else if (c->bad_rec) {
-        status = 2; kind = 0; bad = ~c->bad_rec;
-    } else {
-        if (a.want_races) nr = c->n_races;
-        if (a.want_div) nd = c->n_div;
-        if (a.want_red) { nred = c->n_red; ng = c->n_grid; }
-        if (c->timeout) status = 5;
-        else if (nr > a.cap_races || nd > a.cap_div || nred > a.cap_red || ng > a.cap_grid) status = 4;
+__global__ void k_report(const TraceDesc *td, const TState *ts, const uint32_t *ofs_div, const uint32_t *ofs_red,
+                         Layout L, Ctl *ctl, ReportArgs a) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < L.T; t += gridDim.x * blockDim.x) {
+        const TraceDesc &d = td[t];
+        const volatile TState *v = &ts[t];
+        int32_t status = 0;
+        uint32_t kind = 0;
+        uint64_t bad = 0, nr = 0, nd = 0, nred = 0, ng = 0;
+        if (v->bad_cnt) {
+            status = 2; kind = 1; bad = ~v->bad_cnt;
+        } else if (v->bad_rec) {
+            status = 2; kind = 0; bad = ~v->bad_rec;
+        } else {
+            if (a.want_races) nr = v->n_races;
+            if (a.want_div) nd = ofs_div[d.block_off + d.nb] - ofs_div[d.block_off];
+            if (a.want_red) { nred = ofs_red[d.block_off + d.nb] - ofs_red[d.block_off]; ng = v->n_grid; }
+            if (*(volatile unsigned int *)&ctl->timeout) status = 5;
+            else if (nr > d.races_cap || nd > d.divs_cap || nred > d.reds_cap || ng > d.grid_cap) status = 4;
+        }
+        uint8_t *report = d.report;
+        reinterpret_cast<int32_t *>(report)[0] = status;
+        reinterpret_cast<uint32_t *>(report)[1] = kind;
+        uint64_t *r64 = reinterpret_cast<uint64_t *>(report);
+        r64[1] = bad;
+        r64[2] = nr;
+        r64[3] = nd;
+        r64[4] = nred;
+        r64[5] = ng;
     }
-    int32_t *r32 = reinterpret_cast<int32_t *>(report);
-    uint64_t *r64 = reinterpret_cast<uint64_t *>(report);
-    r32[0] = status;
-    reinterpret_cast<uint32_t *>(report)[1] = kind;
-    r64[1] = bad;
-    r64[2] = nr;
-    r64[3] = nd;
-    r64[4] = nred;
-    r64[5] = ng;
 }
 
 }  // namespace simk

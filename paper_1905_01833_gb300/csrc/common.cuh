@@ -37,36 +37,67 @@ constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;
 constexpr int MAX_PASSES = 40;   // all sort passes of one call
 
-// Device control block at the start of the workspace; zeroed by every call.
-struct Ctl {
-    unsigned long long bad_rec;   // ~index of the first bad record (atomicMax), 0 = none
-    unsigned long long bad_cnt;   // ~index of the first bad barrier count, 0 = none
-    unsigned int timeout;         // a bounded wait gave up
-    unsigned int max_count;       // largest barrier count of the trace
-    unsigned int n_s, n_g;        // shared / global stream sizes (n_x == n_g)
-    unsigned int n_races;         // staged race records
-    unsigned int n_div, n_red, n_grid;
-    unsigned int n_q;                // records in the schedule-rank sort (unsorted traces)
-    unsigned int tiles[MAX_PASSES];  // onesweep tile counters, one per pass
-    unsigned int pad[5];
+// One trace of a call (a single-trace call is a batch of one). Device array
+// in the workspace, written by the host side of the call.
+struct TraceDesc {
+    const uint4 *events;       // records of this trace
+    const uint32_t *counts;    // barrier counts, nb * bt
+    uint64_t n;                // records
+    uint64_t rec_off;          // index of this trace's first record in the batch
+    uint64_t tile_off;         // first ingest tile of this trace
+    uint32_t block_off;        // batch-wide index of this trace's block 0
+    uint32_t nb, bt, su, gu, maxb, flags;
+    uint32_t pad;
+    uint8_t *races;    uint64_t races_cap;    // outputs (device), as in simulee_outputs
+    uint8_t *divs;     uint64_t divs_cap;
+    uint8_t *reds;     uint64_t reds_cap;
+    uint32_t *grid;    uint64_t grid_cap;
+    uint8_t *report;                          // simulee_report of this trace
 };
 
-// Dimensions, bit layouts and workspace offsets of one call (host-computed).
+// Per-trace device state, zeroed by every call.
+struct TState {
+    unsigned long long bad_rec;   // ~index (in the trace) of the first bad record, 0 = none
+    unsigned long long bad_cnt;   // ~index of the first bad barrier count, 0 = none
+    unsigned int n_races;         // race records of the trace
+    unsigned int n_grid;          // grid-redundant barriers of the trace
+    unsigned int race_start;      // position of the trace's first race in the sorted race list
+    unsigned int pad;
+};
+
+// Device control block at the start of the workspace; zeroed by every call.
+struct Ctl {
+    unsigned int timeout;         // a bounded wait gave up
+    unsigned int n_s, n_g;        // shared / global stream sizes (the inter stream has n_g too)
+    unsigned int n_races;         // staged race records (all traces)
+    unsigned int n_div, n_red;    // divergent blocks / redundant barriers (all traces)
+    unsigned int n_q;             // records in the schedule-rank sort (unsorted traces)
+    unsigned int pad0;
+    unsigned int tiles[MAX_PASSES];  // onesweep tile counters, one per pass
+};
+
+// Batch-wide dimensions, bit layouts and workspace offsets of one call (host-computed).
 struct Layout {
-    uint64_t n;                      // records
-    uint32_t nb, bt, su, gu, maxb, flags;
-    uint32_t bb, bus, bug, be, bu;   // bit widths: block, shared unit, global unit, epoch, max(unit)
-    uint32_t bits_s, bits_g, bits_x, bits_r;
-    uint32_t np_s, np_g, np_x, np_r; // radix passes per stream
-    uint32_t p0_s, p0_g, p0_x, p0_r; // first global pass index of each stream
-    uint32_t wide_s, wide_g;         // 64-bit keys
+    uint64_t n;                      // records, all traces
+    uint32_t T;                      // traces
+    uint32_t NB;                     // blocks, all traces
+    uint64_t ntiles_in;              // ingest tiles, all traces
+    uint32_t maxb;                   // largest max_barriers
+    uint32_t any_unsorted;
+    uint32_t bb, bus, bug, be, bu, btr;   // bit widths: batch block, shared unit, global unit, epoch,
+                                           // max(unit), trace index
+    uint32_t bits_s, bits_g, bits_x, bits_r, bits_q;
+    uint32_t np_s, np_g, np_x, np_r, np_q;    // radix passes per stream
+    uint32_t p0_s, p0_g, p0_x, p0_r, p0_q;    // first pass index of each stream
+    uint32_t wide_s, wide_g, wide_x, wide_q;  // 64-bit keys
     uint32_t words;                  // 32-bit words per block in the barrier bitmaps
     uint64_t race_cap;               // staging capacity for race records
     uint64_t status_tiles;           // tiles covered by the look-back status array
-    size_t off_ctl, off_stats, off_nonred, off_gridnr, off_gridhas, off_cnt_div, off_cnt_red,
-        off_ofs_div, off_ofs_red, off_hist, off_dbase, off_status;
+    size_t off_ctl, off_td, off_ts, off_tob, off_stats, off_nonred, off_gridnr, off_gridhas, off_cnt_div,
+        off_cnt_red, off_ofs_div, off_ofs_red, off_hist, off_dbase, off_status, off_rank, off_p2v;
     size_t off_sk[2], off_sv[2], off_gk[2], off_gv[2], off_xk[2], off_xv[2];
     size_t off_rk[2], off_rv[2], off_rp;
+    size_t zero_end;                 // bytes from the start that every call zeroes
     size_t total;
 };
 
@@ -82,15 +113,27 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
-__device__ __forceinline__ bool trace_bad(const Ctl *ctl) {
-    const volatile Ctl *c = ctl;
-    return c->bad_rec != 0 || c->bad_cnt != 0;
-}
-
-// stop work that depends on sorted data: bad trace, or a wait gave up
+// stop work that depends on sorted data: a wait gave up
 __device__ __forceinline__ bool must_stop(const Ctl *ctl) {
     const volatile Ctl *c = ctl;
-    return c->bad_rec != 0 || c->bad_cnt != 0 || c->timeout != 0;
+    return c->timeout != 0;
+}
+
+__device__ __forceinline__ bool trace_bad(const TState &t) {
+    const volatile TState *v = &t;
+    return v->bad_rec != 0 || v->bad_cnt != 0;
+}
+
+// index t with key(t) <= x < key(t+1) over T ascending entries (binary search)
+template <class F>
+__device__ __forceinline__ uint32_t find_trace(uint32_t T, uint64_t x, F key) {
+    uint32_t lo = 0, hi = T;   // invariant: key(lo) <= x, answer in [lo, hi)
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (key(mid) <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
 }
 
 // payload of a stream element: (act << 30 | gtid) << 32 | schedule position

@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "../../include/simulee.h"
 #include "check_kernels.cuh"
@@ -50,6 +51,8 @@ struct Want {
     bool races, div, red;
 };
 
+constexpr uint32_t kMaxTraces = 1u << 20;
+
 simulee_status check_trace_args(const simulee_trace *t) {
     if (!t) return SIMULEE_EINVAL;
     if (t->n_events > 0 && !t->events) return SIMULEE_EINVAL;
@@ -63,77 +66,102 @@ simulee_status check_trace_args(const simulee_trace *t) {
     return SIMULEE_OK;
 }
 
-// Bit layouts, pass counts and workspace offsets for one trace.
-simulee_status make_layout(const simulee_trace *t, Layout &L) {
+// Batch-wide bit layouts, pass counts and workspace offsets (a single trace is a batch of one).
+simulee_status make_layout(const simulee_trace *tr, uint32_t T, Layout &L) {
     memset(&L, 0, sizeof L);
-    L.n = t->n_events;
-    L.nb = t->n_blocks;
-    L.bt = t->block_threads;
-    L.su = t->shared_units;
-    L.gu = t->global_units;
-    L.maxb = t->max_barriers;
-    L.flags = t->flags;
-    L.bb = bits_for(L.nb);
-    L.bus = bits_for(L.su);
-    L.bug = bits_for(L.gu);
-    L.be = bits_for((uint64_t)L.maxb + 1);
+    if (T == 0 || T > kMaxTraces) return SIMULEE_EINVAL;
+    uint64_t n = 0, nb = 0, tiles = 0;
+    uint32_t maxb = 0, su = 0, gu = 0, uns = 0;
+    for (uint32_t i = 0; i < T; i++) {
+        const simulee_trace &t = tr[i];
+        if (t.n_blocks == 0 || t.block_threads == 0 || t.block_threads > 1024 || t.max_barriers > 4095 ||
+            t.n_events >= (1ull << 31) || (uint64_t)t.n_blocks * t.block_threads > (1ull << 30))
+            return SIMULEE_EINVAL;
+        n += t.n_events;
+        nb += t.n_blocks;
+        tiles += (t.n_events + IN_TILE - 1) / IN_TILE;
+        maxb = std::max(maxb, t.max_barriers);
+        su = std::max(su, t.shared_units);
+        gu = std::max(gu, t.global_units);
+        uns |= t.flags & SIMULEE_FLAG_UNSORTED;
+    }
+    if (n >= (1ull << 31) || nb >= (1ull << 31)) return SIMULEE_EINVAL;
+    L.n = n;
+    L.T = T;
+    L.NB = (uint32_t)nb;
+    L.ntiles_in = tiles;
+    L.maxb = maxb;
+    L.any_unsorted = uns;
+    L.bb = bits_for(L.NB);
+    L.bus = bits_for(su);
+    L.bug = bits_for(gu);
+    L.be = bits_for((uint64_t)maxb + 1);
     L.bu = std::max(L.bus, L.bug);
+    L.btr = bits_for(T);
     L.bits_s = L.bb + L.bus + L.be;
     L.bits_g = L.bb + L.bug + L.be;
-    L.bits_x = L.bug;
-    L.bits_r = 3 + L.bb + L.be + L.bu;
-    if (L.bits_s > 64 || L.bits_g > 64 || L.bits_r > 64) return SIMULEE_EINVAL;
+    L.bits_x = L.btr + L.bug;
+    L.bits_r = 3 + L.bb + L.be + L.bu + L.btr;
+    L.bits_q = 32 + L.btr;
+    if (L.bits_s > 64 || L.bits_g > 64 || L.bits_x > 64 || L.bits_r > 64 || L.bits_q > 64) return SIMULEE_EINVAL;
     L.wide_s = L.bits_s > 32;
     L.wide_g = L.bits_g > 32;
+    L.wide_x = L.bits_x > 32;
+    L.wide_q = L.bits_q > 32;
     L.np_s = passes_for(L.bits_s);
     L.np_g = passes_for(L.bits_g);
     L.np_x = passes_for(L.bits_x);
     L.np_r = passes_for(L.bits_r);
+    L.np_q = uns ? passes_for(L.bits_q) : 0;
     L.p0_s = 0;
     L.p0_g = L.p0_s + L.np_s;
     L.p0_x = L.p0_g + L.np_g;
     L.p0_r = L.p0_x + L.np_x;
-    // the unsorted-trace rank sort uses passes p0_r + np_r .. + 3
-    if (L.p0_r + L.np_r + 4 > MAX_PASSES) return SIMULEE_EINVAL;
-    L.words = std::max<uint32_t>(1, (L.maxb + 31) / 32);
+    L.p0_q = L.p0_r + L.np_r;
+    if (L.p0_q + L.np_q > MAX_PASSES || L.np_s + L.np_g + L.np_x > IN_MAXP) return SIMULEE_EINVAL;
+    L.words = std::max<uint32_t>(1, (maxb + 31) / 32);
     L.race_cap = 2 * L.n + 2;
-    const uint64_t n = std::max<uint64_t>(L.n, 1);
-    const uint64_t sort_max = std::max<uint64_t>(n, L.race_cap);
+    const uint64_t n1 = std::max<uint64_t>(L.n, 1);
+    const uint64_t sort_max = std::max<uint64_t>(n1, L.race_cap);
     L.status_tiles = (sort_max + OS_TILE - 1) / OS_TILE;
 
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes); return r; };
+    // zeroed by every call: control block, per-trace state, bitmaps
     L.off_ctl = take(sizeof(Ctl));
-    L.off_stats = take((size_t)L.nb * 16);
-    L.off_nonred = take((size_t)L.nb * L.words * 4);
-    L.off_gridnr = take((size_t)L.words * 4);
-    L.off_gridhas = take((size_t)L.words * 4);
-    L.off_cnt_div = take((size_t)L.nb * 4);
-    L.off_cnt_red = take((size_t)L.nb * 4);
-    L.off_ofs_div = take((size_t)L.nb * 4);
-    L.off_ofs_red = take((size_t)L.nb * 4);
+    L.off_ts = take((size_t)T * sizeof(TState));
+    L.off_nonred = take((size_t)L.NB * L.words * 4);
+    L.off_gridnr = take((size_t)T * L.words * 4);
+    L.off_gridhas = take((size_t)T * L.words * 4);
     L.off_hist = take((size_t)MAX_PASSES * RADIX * 4);
+    L.zero_end = o;
+    L.off_td = take((size_t)T * sizeof(TraceDesc));
+    L.off_tob = take((size_t)L.NB * 4);
+    L.off_stats = take((size_t)L.NB * 16);
+    L.off_cnt_div = take((size_t)L.NB * 4);
+    L.off_cnt_red = take((size_t)L.NB * 4);
+    L.off_ofs_div = take((size_t)(L.NB + 1) * 4);
+    L.off_ofs_red = take((size_t)(L.NB + 1) * 4);
     L.off_dbase = take((size_t)MAX_PASSES * RADIX * 4);
     L.off_status = take((size_t)L.status_tiles * RADIX * 8);
-    const size_t ks = L.wide_s ? 8 : 4, kg = L.wide_g ? 8 : 4;
+    if (uns) {
+        L.off_rank = take(n1 * 4);
+        L.off_p2v = take(n1 * 4);
+    }
+    const size_t ks = L.wide_s ? 8 : 4, kg = L.wide_g ? 8 : 4, kx = L.wide_x ? 8 : 4;
     for (int i = 0; i < 2; i++) {
-        L.off_sk[i] = take(n * ks);
-        L.off_sv[i] = take(n * 8);
-        L.off_gk[i] = take(n * kg);
-        L.off_gv[i] = take(n * 8);
-        L.off_xk[i] = take(n * 4);
-        L.off_xv[i] = take(n * 8);
+        L.off_sk[i] = take(n1 * ks);
+        L.off_sv[i] = take(n1 * 8);
+        L.off_gk[i] = take(n1 * kg);
+        L.off_gv[i] = take(n1 * 8);
+        L.off_xk[i] = take(n1 * kx);
+        L.off_xv[i] = take(n1 * 8);
         L.off_rk[i] = take(L.race_cap * 8);
         L.off_rv[i] = take(L.race_cap * 8);
     }
     L.off_rp = take(L.race_cap * 16);
     L.total = o;
     return SIMULEE_OK;
-}
-
-// extra workspace for unsorted traces: rank[n] and pos_to_vo[n]
-size_t unsorted_extra(const Layout &L) {
-    return (L.flags & SIMULEE_FLAG_UNSORTED) ? 2 * align_up(std::max<uint64_t>(L.n, 1) * 4) : 0;
 }
 
 template <class K>
@@ -156,7 +184,6 @@ struct Run {
     uint64_t wait_ns;
     uint32_t withhold;   // applied to the first sort pass launched
     bool first_pass_done = false;
-
     uint32_t launches = 0;
 
     template <class T>
@@ -187,46 +214,109 @@ struct Run {
         }
         return (int)(np & 1);
     }
+
+    int grid_for(uint64_t items, uint64_t per_cta, uint64_t max_per_sm) const {
+        return (int)std::max<uint64_t>(1, std::min<uint64_t>((items + per_cta - 1) / per_cta, (uint64_t)ctx->sms * max_per_sm));
+    }
 };
 
-__global__ void k_rank_init(const uint4 *ev, uint64_t n, uint32_t *keys, uint64_t *vals, uint32_t *hist) {
-    __shared__ uint32_t sh[4 * RADIX];
-    for (int i = threadIdx.x; i < 4 * RADIX; i += blockDim.x) sh[i] = 0;
+// descriptors reach the device through kernel parameters (no host staging buffer)
+constexpr int kDescChunk = 200;
+struct DescChunk {
+    TraceDesc d[kDescChunk];
+};
+static_assert(sizeof(DescChunk) + 16 < 32000, "descriptor chunk must fit the kernel parameter space");
+
+__global__ void k_set_desc(TraceDesc *dst, DescChunk chunk, uint32_t count) {
+    if (threadIdx.x < count) dst[threadIdx.x] = chunk.d[threadIdx.x];
+}
+
+// schedule-rank sort input: key (trace, visit order), value = batch-wide record index
+template <class KQ>
+__global__ void k_rank_init(const TraceDesc *td, Layout L, KQ *keys, uint64_t *vals, uint32_t *hist) {
+    __shared__ uint32_t sh[8 * RADIX];
+    for (int i = threadIdx.x; i < 8 * RADIX; i += blockDim.x) sh[i] = 0;
     __syncthreads();
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t vo = ev[i].y;
-        keys[i] = vo;
-        vals[i] = i;
-        for (int p = 0; p < 4; p++) atomicAdd(&sh[p * RADIX + ((vo >> (8 * p)) & (RADIX - 1))], 1u);
+    for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < L.n; r += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = find_trace(L.T, r, [&](uint32_t i) { return td[i].rec_off; });
+        const uint32_t vo = td[t].events[r - td[t].rec_off].y;
+        const uint64_t k = shl(t, 32) | vo;
+        keys[r] = (KQ)k;
+        vals[r] = r;
+        for (uint32_t p = 0; p < L.np_q; p++) atomicAdd(&sh[p * RADIX + digit_of(k, p)], 1u);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 4 * RADIX; i += blockDim.x)
+    for (int i = threadIdx.x; i < (int)(L.np_q * RADIX); i += blockDim.x)
         if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
-__global__ void k_rank_scatter(const uint64_t *sorted_idx, uint64_t n, uint32_t *rank, Ctl *ctl) {
+template <class KQ>
+__global__ void k_rank_scatter(const KQ *sorted_keys, const uint64_t *sorted_idx, uint64_t n, uint32_t *rank,
+                               uint32_t *pos_to_vo, Ctl *ctl) {
     if (must_stop(ctl)) return;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         if (sorted_idx[i] < n) rank[sorted_idx[i]] = (uint32_t)i;
+        pos_to_vo[i] = (uint32_t)sorted_keys[i];
+    }
 }
 
 __global__ void k_set_count(unsigned int *dst, unsigned int v) { *dst = v; }
 
-simulee_status launch_check(simulee_ctx *ctx, const simulee_trace *t, const simulee_outputs *out, Want want,
-                            simulee_report *report, void *ws, size_t ws_bytes, void *stream) {
-    if (!ctx || !out || !report || !ws) return SIMULEE_EINVAL;
-    simulee_status s = check_trace_args(t);
-    if (s != SIMULEE_OK) return s;
-    if ((out->races_cap && !out->races) || (out->divergence_cap && !out->divergence) ||
-        (out->redundant_cap && !out->redundant) || (out->grid_redundant_cap && !out->grid_redundant))
-        return SIMULEE_EINVAL;
+// Fill host descriptors for a batch (block, record and tile offsets; outputs).
+void fill_descs(const simulee_trace *tr, const simulee_outputs *outs, uint8_t *const *reports, uint32_t T,
+                std::vector<TraceDesc> &td) {
+    td.resize(T);
+    uint64_t rec = 0, tile = 0;
+    uint32_t blk = 0;
+    for (uint32_t i = 0; i < T; i++) {
+        TraceDesc &d = td[i];
+        memset(&d, 0, sizeof d);
+        d.events = (const uint4 *)tr[i].events;
+        d.counts = tr[i].barrier_counts;
+        d.n = tr[i].n_events;
+        d.rec_off = rec;
+        d.tile_off = tile;
+        d.block_off = blk;
+        d.nb = tr[i].n_blocks;
+        d.bt = tr[i].block_threads;
+        d.su = tr[i].shared_units;
+        d.gu = tr[i].global_units;
+        d.maxb = tr[i].max_barriers;
+        d.flags = tr[i].flags;
+        d.races = (uint8_t *)outs[i].races;
+        d.races_cap = outs[i].races_cap;
+        d.divs = (uint8_t *)outs[i].divergence;
+        d.divs_cap = outs[i].divergence_cap;
+        d.reds = (uint8_t *)outs[i].redundant;
+        d.reds_cap = outs[i].redundant_cap;
+        d.grid = outs[i].grid_redundant;
+        d.grid_cap = outs[i].grid_redundant_cap;
+        d.report = reports[i];
+        rec += d.n;
+        tile += (d.n + IN_TILE - 1) / IN_TILE;
+        blk += d.nb;
+    }
+}
+
+simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t T, const simulee_outputs *outs,
+                         uint8_t *const *reports, Want want, void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx || !traces || !outs || !reports || !ws || T == 0) return SIMULEE_EINVAL;
+    for (uint32_t i = 0; i < T; i++) {
+        const simulee_status s = check_trace_args(&traces[i]);
+        if (s != SIMULEE_OK) return s;
+        const simulee_outputs &o = outs[i];
+        if ((o.races_cap && !o.races) || (o.divergence_cap && !o.divergence) || (o.redundant_cap && !o.redundant) ||
+            (o.grid_redundant_cap && !o.grid_redundant) || !reports[i])
+            return SIMULEE_EINVAL;
+    }
     if (((uintptr_t)ws & 255u) != 0) return SIMULEE_EINVAL;
     Run R;
     R.ctx = ctx;
-    s = make_layout(t, R.L);
+    simulee_status s = make_layout(traces, T, R.L);
     if (s != SIMULEE_OK) return s;
-    const size_t extra = unsorted_extra(R.L);
-    if (ws_bytes < R.L.total + extra) return SIMULEE_ENOMEM;
+    if (ws_bytes < R.L.total) return SIMULEE_ENOMEM;
+    std::vector<TraceDesc> hdesc;
+    fill_descs(traces, outs, reports, T, hdesc);
     int prev_dev = -1;
     cudaGetDevice(&prev_dev);
     if (prev_dev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return SIMULEE_ECUDA;
@@ -236,6 +326,7 @@ simulee_status launch_check(simulee_ctx *ctx, const simulee_trace *t, const simu
         set_reduce_attr<uint32_t, false>();
         set_reduce_attr<uint64_t, false>();
         set_reduce_attr<uint32_t, true>();
+        set_reduce_attr<uint64_t, true>();
         ctx->attrs_set = true;
     }
     R.st = (cudaStream_t)stream;
@@ -244,65 +335,72 @@ simulee_status launch_check(simulee_ctx *ctx, const simulee_trace *t, const simu
     R.wait_ns = (uint64_t)(ctx->opt.wait_limit_us ? ctx->opt.wait_limit_us : 1000000u) * 1000ull;
     R.withhold = ctx->opt.test_withhold;
     const Layout &L = R.L;
-    const int sms = ctx->sms;
     cudaStream_t st = R.st;
+    TraceDesc *td = R.at<TraceDesc>(L.off_td);
+    TState *ts = R.at<TState>(L.off_ts);
+    uint32_t *tob = R.at<uint32_t>(L.off_tob);
+    uint32_t *hist = R.at<uint32_t>(L.off_hist);
 
-    // 1. zero control state
-    cudaMemsetAsync(R.ws, 0, L.off_cnt_div, st);   // ctl, stats, bitmaps
-    cudaMemsetAsync(R.ws + L.off_hist, 0, (size_t)MAX_PASSES * RADIX * 4, st);
-    cudaMemsetAsync(R.ws + L.off_status, 0, (size_t)L.status_tiles * RADIX * 8, st);
-
-    // 2. barrier counts
+    // 1. zero control state, upload descriptors
     R.mark(SIMULEE_STAGE_INGEST, 0);
-    {
-        const int grid = (int)std::min<uint64_t>((L.nb + 7) / 8, (uint64_t)sms * 16);
-        k_block_stats<<<std::max(grid, 1), 256, 0, st>>>(t->barrier_counts, L, R.at<uint4>(L.off_stats), R.ctl);
+    cudaMemsetAsync(R.ws, 0, L.zero_end, st);
+    cudaMemsetAsync(R.ws + L.off_status, 0, (size_t)L.status_tiles * RADIX * 8, st);
+    for (uint32_t i = 0; i < T; i += kDescChunk) {
+        DescChunk c;
+        const uint32_t cnt = std::min<uint32_t>(kDescChunk, T - i);
+        memcpy(c.d, hdesc.data() + i, cnt * sizeof(TraceDesc));
+        k_set_desc<<<1, kDescChunk, 0, st>>>(td + i, c, cnt);
         R.launches++;
     }
+    k_block_trace<<<R.grid_for(L.NB, 256, 8), 256, 0, st>>>(td, L, tob);
+    // 2. barrier counts
+    k_block_stats<<<R.grid_for(L.NB, 8, 16), 256, 0, st>>>(td, tob, L, R.at<uint4>(L.off_stats), ts);
+    R.launches += 2;
 
     const bool route = want.races || want.red;
     const bool sorting = L.n > 0 && route;
     uint32_t *rank = nullptr, *pos_to_vo = nullptr;
-    uint32_t *hist = R.at<uint32_t>(L.off_hist);
     if (L.n > 0) {
-        // 3. unsorted traces: schedule rank of each record = position in (visit order, index) order
-        if (L.flags & SIMULEE_FLAG_UNSORTED) {
-            rank = R.at<uint32_t>(L.total);
-            pos_to_vo = R.at<uint32_t>(L.total + align_up(L.n * 4));
-            const uint32_t p0q = L.p0_r + L.np_r;
+        // 3. unsorted traces: schedule rank of each record = position in (trace, visit order, index) order
+        if (L.any_unsorted) {
+            rank = R.at<uint32_t>(L.off_rank);
+            pos_to_vo = R.at<uint32_t>(L.off_p2v);
             size_t qk[2] = {L.off_rk[0], L.off_rk[1]}, qv[2] = {L.off_rv[0], L.off_rv[1]};
-            const int g = (int)std::min<uint64_t>((L.n + 255) / 256, (uint64_t)sms * 8);
-            k_rank_init<<<g, 256, 0, st>>>((const uint4 *)t->events, L.n, R.at<uint32_t>(qk[0]),
-                                            R.at<uint64_t>(qv[0]), hist + (size_t)p0q * RADIX);
-            k_digit_bases<<<4, RADIX, 0, st>>>(hist + (size_t)p0q * RADIX,
-                                               R.at<uint32_t>(L.off_dbase) + (size_t)p0q * RADIX, R.ctl);
+            const int g = R.grid_for(L.n, 256, 8);
+            uint32_t *hq = hist + (size_t)L.p0_q * RADIX, *dq = R.at<uint32_t>(L.off_dbase) + (size_t)L.p0_q * RADIX;
+            if (L.wide_q) k_rank_init<uint64_t><<<g, 256, 0, st>>>(td, L, R.at<uint64_t>(qk[0]), R.at<uint64_t>(qv[0]), hq);
+            else k_rank_init<uint32_t><<<g, 256, 0, st>>>(td, L, R.at<uint32_t>(qk[0]), R.at<uint64_t>(qv[0]), hq);
+            k_digit_bases<<<L.np_q, RADIX, 0, st>>>(hq, dq, R.ctl);
             k_set_count<<<1, 1, 0, st>>>(&R.ctl->n_q, (unsigned int)L.n);
             R.launches += 3;
-            const int b = R.sort<uint32_t>(qk, qv, &R.ctl->n_q, L.n, 4, p0q);
-            k_rank_scatter<<<g, 256, 0, st>>>(R.at<uint64_t>(qv[b]), L.n, rank, R.ctl);
+            const int b = L.wide_q ? R.sort<uint64_t>(qk, qv, &R.ctl->n_q, L.n, L.np_q, L.p0_q)
+                                   : R.sort<uint32_t>(qk, qv, &R.ctl->n_q, L.n, L.np_q, L.p0_q);
+            if (L.wide_q)
+                k_rank_scatter<uint64_t><<<g, 256, 0, st>>>(R.at<uint64_t>(qk[b]), R.at<uint64_t>(qv[b]), L.n, rank,
+                                                            pos_to_vo, R.ctl);
+            else
+                k_rank_scatter<uint32_t><<<g, 256, 0, st>>>(R.at<uint32_t>(qk[b]), R.at<uint64_t>(qv[b]), L.n, rank,
+                                                            pos_to_vo, R.ctl);
             R.launches++;
-            cudaMemcpyAsync(pos_to_vo, R.at<uint32_t>(qk[b]), L.n * 4, cudaMemcpyDeviceToDevice, st);
         }
 
         // 4. ingest
-        const uint64_t ntiles = (L.n + IN_TILE - 1) / IN_TILE;
-        const int gi = (int)std::max<uint64_t>(1, std::min<uint64_t>(ntiles, (uint64_t)sms * 4));
-#define SIM_INGEST(KS, KG, RT)                                                                                     \
-    k_ingest<KS, KG, RT><<<gi, IN_THREADS, 0, st>>>((const uint4 *)t->events, t->barrier_counts, rank, L, R.ctl,  \
-                                                    R.at<KS>(L.off_sk[0]), R.at<uint64_t>(L.off_sv[0]),             \
-                                                    R.at<KG>(L.off_gk[0]), R.at<uint64_t>(L.off_gv[0]),             \
-                                                    R.at<uint32_t>(L.off_xk[0]), R.at<uint64_t>(L.off_xv[0]), hist)
-        if (!route) {
-            SIM_INGEST(uint32_t, uint32_t, false);
-        } else if (L.wide_s && L.wide_g) {
-            SIM_INGEST(uint64_t, uint64_t, true);
-        } else if (L.wide_s) {
-            SIM_INGEST(uint64_t, uint32_t, true);
-        } else if (L.wide_g) {
-            SIM_INGEST(uint32_t, uint64_t, true);
-        } else {
-            SIM_INGEST(uint32_t, uint32_t, true);
-        }
+        const int gi = R.grid_for(L.ntiles_in, 1, 4);
+#define SIM_INGEST(KS, KG, KX, RT)                                                                                  \
+    k_ingest<KS, KG, KX, RT><<<gi, IN_THREADS, 0, st>>>(td, rank, L, ts, R.ctl, R.at<KS>(L.off_sk[0]),               \
+                                                        R.at<uint64_t>(L.off_sv[0]), R.at<KG>(L.off_gk[0]),          \
+                                                        R.at<uint64_t>(L.off_gv[0]), R.at<KX>(L.off_xk[0]),          \
+                                                        R.at<uint64_t>(L.off_xv[0]), hist)
+        const int wmask = (L.wide_s ? 1 : 0) | (L.wide_g ? 2 : 0) | (L.wide_x ? 4 : 0);
+        if (!route) SIM_INGEST(uint32_t, uint32_t, uint32_t, false);
+        else if (wmask == 0) SIM_INGEST(uint32_t, uint32_t, uint32_t, true);
+        else if (wmask == 1) SIM_INGEST(uint64_t, uint32_t, uint32_t, true);
+        else if (wmask == 2) SIM_INGEST(uint32_t, uint64_t, uint32_t, true);
+        else if (wmask == 3) SIM_INGEST(uint64_t, uint64_t, uint32_t, true);
+        else if (wmask == 4) SIM_INGEST(uint32_t, uint32_t, uint64_t, true);
+        else if (wmask == 5) SIM_INGEST(uint64_t, uint32_t, uint64_t, true);
+        else if (wmask == 6) SIM_INGEST(uint32_t, uint64_t, uint64_t, true);
+        else SIM_INGEST(uint64_t, uint64_t, uint64_t, true);
 #undef SIM_INGEST
         R.launches++;
     }
@@ -323,7 +421,8 @@ simulee_status launch_check(simulee_ctx *ctx, const simulee_trace *t, const simu
                       : R.sort<uint32_t>(sk, sv, &R.ctl->n_s, L.n, L.np_s, L.p0_s);
         bg = L.wide_g ? R.sort<uint64_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g)
                       : R.sort<uint32_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g);
-        bx = R.sort<uint32_t>(xk, xv, &R.ctl->n_g, L.n, L.np_x, L.p0_x);
+        bx = L.wide_x ? R.sort<uint64_t>(xk, xv, &R.ctl->n_g, L.n, L.np_x, L.p0_x)
+                      : R.sort<uint32_t>(xk, xv, &R.ctl->n_g, L.n, L.np_x, L.p0_x);
     }
     R.mark(SIMULEE_STAGE_SORT, 1);
 
@@ -336,89 +435,80 @@ simulee_status launch_check(simulee_ctx *ctx, const simulee_trace *t, const simu
     rs.cap = L.race_cap;
     rs.pos_to_vo = pos_to_vo;
     rs.n_pos = L.n;
+    rs.ts = ts;
+    rs.td = td;
+    uint32_t *nonred = R.at<uint32_t>(L.off_nonred);
     if (sorting) {
-        uint32_t *nonred = R.at<uint32_t>(L.off_nonred);
-        const int gr = (int)std::max<uint64_t>(1, std::min<uint64_t>((L.n + RG_TILE - 1) / RG_TILE, (uint64_t)sms * 3));
-        if (L.wide_s)
-            k_reduce_groups<uint64_t, false><<<gr, RG_THREADS, reduce_groups_smem<uint64_t, false>(), st>>>(
-                R.at<uint64_t>(L.off_sk[bs]), R.at<uint64_t>(L.off_sv[bs]), &R.ctl->n_s, L, 0u, L.bus, R.ctl, nonred, rs);
-        else
-            k_reduce_groups<uint32_t, false><<<gr, RG_THREADS, reduce_groups_smem<uint32_t, false>(), st>>>(
-                R.at<uint32_t>(L.off_sk[bs]), R.at<uint64_t>(L.off_sv[bs]), &R.ctl->n_s, L, 0u, L.bus, R.ctl, nonred, rs);
-        if (L.wide_g)
-            k_reduce_groups<uint64_t, false><<<gr, RG_THREADS, reduce_groups_smem<uint64_t, false>(), st>>>(
-                R.at<uint64_t>(L.off_gk[bg]), R.at<uint64_t>(L.off_gv[bg]), &R.ctl->n_g, L, 1u, L.bug, R.ctl, nonred, rs);
-        else
-            k_reduce_groups<uint32_t, false><<<gr, RG_THREADS, reduce_groups_smem<uint32_t, false>(), st>>>(
-                R.at<uint32_t>(L.off_gk[bg]), R.at<uint64_t>(L.off_gv[bg]), &R.ctl->n_g, L, 1u, L.bug, R.ctl, nonred, rs);
-        k_reduce_groups<uint32_t, true><<<gr, RG_THREADS, reduce_groups_smem<uint32_t, true>(), st>>>(R.at<uint32_t>(L.off_xk[bx]), R.at<uint64_t>(L.off_xv[bx]),
-                                                                  &R.ctl->n_g, L, 1u, L.bug, R.ctl, nonred, rs);
+        const int gr = R.grid_for(L.n, RG_TILE, 3);
+#define SIM_REDUCE(K, INTER, KOFF, VOFF, NPTR, SPACE, BU)                                                             \
+    k_reduce_groups<K, INTER><<<gr, RG_THREADS, reduce_groups_smem<K, INTER>(), st>>>(                                \
+        R.at<K>(KOFF), R.at<uint64_t>(VOFF), NPTR, L, td, tob, SPACE, BU, R.ctl, nonred, rs)
+        if (L.wide_s) SIM_REDUCE(uint64_t, false, L.off_sk[bs], L.off_sv[bs], &R.ctl->n_s, 0u, L.bus);
+        else SIM_REDUCE(uint32_t, false, L.off_sk[bs], L.off_sv[bs], &R.ctl->n_s, 0u, L.bus);
+        if (L.wide_g) SIM_REDUCE(uint64_t, false, L.off_gk[bg], L.off_gv[bg], &R.ctl->n_g, 1u, L.bug);
+        else SIM_REDUCE(uint32_t, false, L.off_gk[bg], L.off_gv[bg], &R.ctl->n_g, 1u, L.bug);
+        if (L.wide_x) SIM_REDUCE(uint64_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_g, 1u, L.bug);
+        else SIM_REDUCE(uint32_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_g, 1u, L.bug);
+#undef SIM_REDUCE
         R.launches += 3;
     }
     R.mark(SIMULEE_STAGE_REDUCE, 1);
 
-    // 7. races in canonical order
+    // 7. races in canonical order, split per trace
     R.mark(SIMULEE_STAGE_RACES, 0);
     if (sorting && want.races) {
-        const int gh = (int)std::max<uint64_t>(1, std::min<uint64_t>((L.race_cap + 255) / 256, (uint64_t)sms * 4));
-        k_hist_u64<<<gh, 256, 0, st>>>(rs.keys, &R.ctl->n_races, L.race_cap, L.np_r, hist + (size_t)L.p0_r * RADIX,
-                                       R.ctl);
+        k_hist_u64<<<R.grid_for(L.race_cap, 256, 4), 256, 0, st>>>(rs.keys, &R.ctl->n_races, L.race_cap, L.np_r,
+                                                                  hist + (size_t)L.p0_r * RADIX, R.ctl);
         k_digit_bases<<<L.np_r, RADIX, 0, st>>>(hist + (size_t)L.p0_r * RADIX,
                                                 R.at<uint32_t>(L.off_dbase) + (size_t)L.p0_r * RADIX, R.ctl);
         R.launches += 2;
         size_t rk[2] = {L.off_rk[0], L.off_rk[1]}, rv[2] = {L.off_rv[0], L.off_rv[1]};
         const int br = R.sort<uint64_t>(rk, rv, &R.ctl->n_races, L.race_cap, L.np_r, L.p0_r);
-        if (out->races_cap) {
-            const int gw = (int)std::max<uint64_t>(
-                1, std::min<uint64_t>((std::min<uint64_t>(out->races_cap, L.race_cap) + 255) / 256, (uint64_t)sms * 8));
-            k_write_races<<<gw, 256, 0, st>>>(R.at<uint64_t>(rk[br]), R.at<uint64_t>(rv[br]), rs.pay, L, R.ctl,
-                                              (uint8_t *)out->races, out->races_cap);
-            R.launches++;
-        }
+        const int gw = R.grid_for(L.race_cap, 256, 8);
+        k_race_starts<<<gw, 256, 0, st>>>(R.at<uint64_t>(rk[br]), L, R.ctl, ts);
+        k_write_races<<<gw, 256, 0, st>>>(R.at<uint64_t>(rk[br]), R.at<uint64_t>(rv[br]), rs.pay, L, td, ts, R.ctl);
+        R.launches += 2;
     }
     R.mark(SIMULEE_STAGE_RACES, 1);
 
-    // 8. per-block outputs
+    // 8. per-block outputs and reports
     R.mark(SIMULEE_STAGE_BLOCKS, 0);
+    uint32_t *ofs_div = R.at<uint32_t>(L.off_ofs_div), *ofs_red = R.at<uint32_t>(L.off_ofs_red);
+    const int gb = R.grid_for(L.NB, 256, 8);
+    k_block_counts<<<gb, 256, 0, st>>>(R.at<uint4>(L.off_stats), nonred, L, R.at<uint32_t>(L.off_cnt_div),
+                                       R.at<uint32_t>(L.off_cnt_red));
+    k_scan2<<<1, 1024, 0, st>>>(R.at<uint32_t>(L.off_cnt_div), R.at<uint32_t>(L.off_cnt_red), L.NB, ofs_div, ofs_red,
+                                R.ctl);
+    R.launches += 2;
     if (want.div || want.red) {
-        const int gb = (int)std::max<uint64_t>(1, std::min<uint64_t>((L.nb + 255) / 256, (uint64_t)sms * 8));
-        k_block_counts<<<gb, 256, 0, st>>>(R.at<uint4>(L.off_stats), R.at<uint32_t>(L.off_nonred), L, R.ctl,
-                                           R.at<uint32_t>(L.off_cnt_div), R.at<uint32_t>(L.off_cnt_red));
-        k_scan2<<<1, 1024, 0, st>>>(R.at<uint32_t>(L.off_cnt_div), R.at<uint32_t>(L.off_cnt_red), L.nb,
-                                    R.at<uint32_t>(L.off_ofs_div), R.at<uint32_t>(L.off_ofs_red), &R.ctl->n_div,
-                                    &R.ctl->n_red, R.ctl);
-        k_block_write<<<gb, 256, 0, st>>>(R.at<uint4>(L.off_stats), R.at<uint32_t>(L.off_nonred), L, R.ctl,
-                                          R.at<uint32_t>(L.off_ofs_div), R.at<uint32_t>(L.off_ofs_red),
-                                          want.div ? (uint4 *)out->divergence : nullptr,
-                                          want.div ? out->divergence_cap : 0,
-                                          want.red ? (uint2 *)out->redundant : nullptr, want.red ? out->redundant_cap : 0);
-        R.launches += 3;
-        if (want.red) {
-            const int gg = (int)std::max<uint64_t>(1, std::min<uint64_t>(((uint64_t)L.nb * L.words + 255) / 256, (uint64_t)sms * 8));
-            k_grid_or<<<gg, 256, 0, st>>>(R.at<uint4>(L.off_stats), R.at<uint32_t>(L.off_nonred), L, R.ctl,
-                                          R.at<uint32_t>(L.off_gridnr), R.at<uint32_t>(L.off_gridhas));
-            k_grid_list<<<1, 1024, 0, st>>>(R.at<uint32_t>(L.off_gridnr), R.at<uint32_t>(L.off_gridhas), L, R.ctl,
-                                            out->grid_redundant, out->grid_redundant_cap);
-            R.launches += 2;
-        }
+        k_block_write<<<gb, 256, 0, st>>>(R.at<uint4>(L.off_stats), nonred, L, td, tob, ts, ofs_div, ofs_red,
+                                          want.div ? 1u : 0u, want.red ? 1u : 0u);
+        R.launches++;
     }
-
-    // 9. report
+    if (want.red) {
+        k_grid_or<<<R.grid_for((uint64_t)L.NB * L.words, 256, 8), 256, 0, st>>>(
+            R.at<uint4>(L.off_stats), nonred, tob, L, R.at<uint32_t>(L.off_gridnr), R.at<uint32_t>(L.off_gridhas));
+        k_grid_list<<<T, 1024, 0, st>>>(R.at<uint32_t>(L.off_gridnr), R.at<uint32_t>(L.off_gridhas), L, td, ts);
+        R.launches += 2;
+    }
     ReportArgs ra;
-    ra.cap_races = out->races_cap;
-    ra.cap_div = out->divergence_cap;
-    ra.cap_red = out->redundant_cap;
-    ra.cap_grid = out->grid_redundant_cap;
     ra.want_races = want.races;
     ra.want_div = want.div;
     ra.want_red = want.red;
-    k_report<<<1, 32, 0, st>>>(R.ctl, ra, (uint8_t *)report);
+    k_report<<<R.grid_for(T, 256, 4), 256, 0, st>>>(td, ts, ofs_div, ofs_red, L, R.ctl, ra);
     R.launches++;
     R.mark(SIMULEE_STAGE_BLOCKS, 1);
     ctx->last_launches = R.launches;
     const cudaError_t e = cudaGetLastError();
     if (prev_dev >= 0 && prev_dev != ctx->device) cudaSetDevice(prev_dev);
     return e == cudaSuccess ? SIMULEE_OK : SIMULEE_ECUDA;
+}
+
+simulee_status launch_check(simulee_ctx *ctx, const simulee_trace *t, const simulee_outputs *out, Want want,
+                            simulee_report *report, void *ws, size_t ws_bytes, void *stream) {
+    if (!out || !report) return SIMULEE_EINVAL;
+    uint8_t *rep = (uint8_t *)report;
+    return run_check(ctx, t, 1, out, &rep, want, ws, ws_bytes, stream);
 }
 
 }  // namespace
@@ -449,13 +539,10 @@ simulee_status simulee_destroy(simulee_ctx *ctx) {
 
 simulee_status simulee_workspace_size(simulee_ctx *ctx, const simulee_trace *trace, size_t *bytes) {
     if (!ctx || !trace || !bytes) return SIMULEE_EINVAL;
-    if (trace->n_blocks == 0 || trace->block_threads == 0 || trace->block_threads > 1024 ||
-        trace->max_barriers > 4095 || trace->n_events >= (1ull << 31))
-        return SIMULEE_EINVAL;
     Layout L;
-    const simulee_status s = make_layout(trace, L);
+    const simulee_status s = make_layout(trace, 1, L);
     if (s != SIMULEE_OK) return s;
-    *bytes = L.total + unsorted_extra(L);
+    *bytes = L.total;
     return SIMULEE_OK;
 }
 
@@ -497,15 +584,21 @@ simulee_status simulee_check_redundant_barriers(simulee_ctx *ctx, const simulee_
 
 simulee_status simulee_batch_workspace_size(simulee_ctx *ctx, const simulee_trace *traces, uint32_t n_traces,
                                             size_t *bytes) {
-    (void)ctx; (void)traces; (void)n_traces; (void)bytes;
-    return SIMULEE_EINVAL;
+    if (!ctx || !traces || !bytes || n_traces == 0) return SIMULEE_EINVAL;
+    Layout L;
+    const simulee_status s = make_layout(traces, n_traces, L);
+    if (s != SIMULEE_OK) return s;
+    *bytes = L.total;
+    return SIMULEE_OK;
 }
 
 simulee_status simulee_check_batch(simulee_ctx *ctx, const simulee_trace *traces, uint32_t n_traces,
                                    const simulee_outputs *outs, simulee_report *reports, void *ws, size_t ws_bytes,
                                    void *stream) {
-    (void)ctx; (void)traces; (void)n_traces; (void)outs; (void)reports; (void)ws; (void)ws_bytes; (void)stream;
-    return SIMULEE_EINVAL;
+    if (!reports || n_traces == 0 || n_traces > kMaxTraces) return SIMULEE_EINVAL;
+    std::vector<uint8_t *> reps(n_traces);
+    for (uint32_t i = 0; i < n_traces; i++) reps[i] = (uint8_t *)(reports + i);
+    return run_check(ctx, traces, n_traces, outs, reps.data(), Want{true, true, true}, ws, ws_bytes, stream);
 }
 
 uint32_t simulee_last_launches(const simulee_ctx *ctx) { return ctx ? ctx->last_launches : 0u; }

@@ -237,6 +237,61 @@ class Checker:
         out["grid_redundant"] = take(bufs["grid"], grid_cap, rep["n_grid_redundant"], np.dtype("<u4"))
         return out
 
+    def batch_workspace_size(self, dts) -> int:
+        arr = (Trace * len(dts))(*[d.c() for d in dts])
+        n = ctypes.c_size_t()
+        _check(lib().simulee_batch_workspace_size(self.h, arr, len(dts), ctypes.byref(n)),
+               "simulee_batch_workspace_size")
+        return int(n.value)
+
+    def check_batch(self, dts, races_caps=None, stream=None) -> list[dict]:
+        """Check independent traces in one batched call; returns one result dict per trace."""
+        torch = self.torch
+        T = len(dts)
+        dev = f"cuda:{self.device}"
+        rc = [2 * d.n_events + 2 for d in dts] if races_caps is None else list(races_caps)
+        dc = [d.n_blocks for d in dts]
+        bc = [d.n_blocks * max(d.max_barriers, 1) for d in dts]
+        gc = [max(d.max_barriers, 1) for d in dts]
+        sizes = {"races": (rc, 32), "divergence": (dc, 16), "redundant": (bc, 8), "grid": (gc, 4)}
+        bufs, offs = {}, {}
+        for k, (caps, w) in sizes.items():
+            o = np.concatenate([[0], np.cumsum([c * w for c in caps])]).astype(np.int64)
+            offs[k] = o
+            bufs[k] = torch.empty(max(int(o[-1]), 16), dtype=torch.uint8, device=dev)
+        outs = (Outputs * T)()
+        for i in range(T):
+            outs[i] = Outputs(bufs["races"].data_ptr() + int(offs["races"][i]), rc[i],
+                              bufs["divergence"].data_ptr() + int(offs["divergence"][i]), dc[i],
+                              bufs["redundant"].data_ptr() + int(offs["redundant"][i]), bc[i],
+                              bufs["grid"].data_ptr() + int(offs["grid"][i]), gc[i])
+        reports = torch.zeros(T * REPORT_BYTES, dtype=torch.uint8, device=dev)
+        arr = (Trace * T)(*[d.c() for d in dts])
+        ws = self.workspace(self.batch_workspace_size(dts))
+        _check(lib().simulee_check_batch(self.h, arr, T, outs, ctypes.c_void_p(reports.data_ptr()),
+                                         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)),
+               "simulee_check_batch")
+        torch.cuda.synchronize(self.device)
+        rep_bytes = reports.cpu().numpy().tobytes()
+        host = {k: v.cpu().numpy() for k, v in bufs.items()}
+        res = []
+        for i in range(T):
+            r = Report.from_buffer_copy(rep_bytes[i * REPORT_BYTES:(i + 1) * REPORT_BYTES])
+            rep = dict(status=r.status, bad_kind=r.bad_kind, bad_index=r.bad_index, n_races=r.n_races,
+                       n_divergence=r.n_divergence, n_redundant=r.n_redundant, n_grid_redundant=r.n_grid_redundant)
+            ok = rep["status"] in (OK, ETRUNC)
+
+            def take(kind, cap, count, dtype):
+                k = min(cap, count) if ok else 0
+                o = int(offs[kind][i])
+                return np.frombuffer(host[kind][o:o + k * dtype.itemsize].tobytes(), dtype=dtype)
+            rep["races"] = take("races", rc[i], rep["n_races"], RACE_DTYPE)
+            rep["divergence"] = take("divergence", dc[i], rep["n_divergence"], DIV_DTYPE)
+            rep["redundant"] = take("redundant", bc[i], rep["n_redundant"], BAR_DTYPE)
+            rep["grid_redundant"] = take("grid", gc[i], rep["n_grid_redundant"], np.dtype("<u4"))
+            res.append(rep)
+        return res
+
     def check_races(self, dt: DeviceTrace, cap: int | None = None, stream=None) -> dict:
         cap = 2 * dt.n_events + 2 if cap is None else cap
         o, bufs = self.alloc_outputs(cap, 0, 0, 0)

@@ -197,11 +197,19 @@ def c3_sizes(seed: int = DEFAULT_SEED, n_traces: int = 4096, median: float = 1e5
 
 
 def c3_trace(i: int, target: int, block_threads: int, n_epochs: int, seed: int = DEFAULT_SEED) -> Trace:
-    """One trace of the batched workload: the grid pattern sized to about `target` records."""
+    """One trace of the batched workload: the grid pattern with enough blocks for
+    `target` records. When even one block holds more records than the target (a
+    1024-thread block over 64 epochs holds ~4.5e5), the trace is cut to its first
+    `target` records in schedule order; barrier counts stay those of the full
+    run, so the cut trace is a valid trace whose later epochs are empty."""
     nb = max(1, int(np.ceil(target / (block_threads * n_epochs * 8))))
     gu = 4096 + 2 * 1024 * nb
     gu = 1 << int(np.ceil(np.log2(gu)))
-    return pattern(seed + 7919 * (i + 1), nb, block_threads, n_epochs, 12288, gu)
+    tr = pattern(seed + 7919 * (i + 1), nb, block_threads, n_epochs, 12288, gu)
+    if tr.n_events > target:
+        tr.events = np.ascontiguousarray(tr.events[:target])
+    tr.meta.update(kind="batch_member", target=int(target))
+    return tr
 
 
 # --- tiny random traces (for exhaustive pair checks) ---------------------------
