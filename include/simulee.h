@@ -248,7 +248,8 @@ enum {
     SIMULEE_STAGE_REDUCE = 2,   /* segmented reductions: races, epoch adjacency */
     SIMULEE_STAGE_RACES = 3,    /* canonical race sort and copy-out */
     SIMULEE_STAGE_BLOCKS = 4,   /* divergence, redundant-barrier lists, report */
-    SIMULEE_STAGES = 5
+    SIMULEE_STAGE_HASH = 5,     /* short-interval hash path (intra-block races, adjacency) */
+    SIMULEE_STAGES = 6
 };
 uint32_t simulee_last_launches(const simulee_ctx *ctx);
 simulee_status simulee_set_stage_events(simulee_ctx *ctx, void *const *events, uint32_t n_events);

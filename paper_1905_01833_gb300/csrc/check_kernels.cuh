@@ -78,94 +78,130 @@ __device__ __forceinline__ void hist_add(uint32_t *sh, uint64_t key, uint32_t np
 }
 
 // ---------------------------------------------------------------------------
-// Ingest: read every record once (16-byte loads), validate it, and route it:
-// shared records to the intra stream S keyed (block, unit, epoch); global
-// records to the intra stream G keyed (block, unit, epoch) and to the
-// inter-block stream X keyed (trace, unit). Builds the digit histograms of all
-// radix passes. Persistent CTAs over tiles of 2048 records; a tile never
-// spans two traces.
+// Ingest, in up to two reads of the records (16-byte loads).
+//
+// First read (IN_FIRST): validate every record; route global records to the
+// inter-block stream X keyed (trace, unit); for traces on the sort path route
+// shared records to stream S and global records to stream G, both keyed
+// (block, unit, epoch); for traces on the hash path record the bounds of every
+// (block, epoch) run and check that runs come in (block, epoch) order. Digit
+// histograms of the radix passes are built on the way.
+// Fallback read (IN_FALLBACK): route S and G for hash-path traces that the
+// device found unsuitable (order or run length).
+// Validate-only read (IN_VALIDATE): validation alone.
+// Persistent CTAs over tiles of 2048 records; a tile never spans two traces.
 // ---------------------------------------------------------------------------
 constexpr int IN_THREADS = 256;
 constexpr int IN_ITEMS = 8;
 constexpr int IN_TILE = IN_THREADS * IN_ITEMS;
 constexpr int IN_MAXP = 24;   // S + G + X passes histogrammed here
+constexpr int IN_FIRST = 0, IN_FALLBACK = 1, IN_VALIDATE = 2;
 
-template <class KS, class KG, class KX, bool ROUTE>
+template <class KS, class KG, class KX, int MODE>
 __global__ void __launch_bounds__(IN_THREADS)
 k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, Layout L, TState *ts, Ctl *ctl,
-         KS *sk, uint64_t *sv, KG *gk, uint64_t *gv, KX *xk, uint64_t *xv, uint32_t *hist) {
+         KS *sk, uint64_t *sv, KG *gk, uint64_t *gv, KX *xk, uint64_t *xv, uint32_t *hist, uint32_t *runs) {
     __shared__ uint32_t sh[IN_MAXP * RADIX];
-    __shared__ uint32_t wtot[IN_THREADS / 32][2];
-    __shared__ uint32_t cbase[2];
+    __shared__ uint32_t wtot[IN_THREADS / 32][3];
+    __shared__ uint32_t cbase[3];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint32_t lt = lanemask_lt();
     const uint32_t np_s = L.np_s, np_g = L.np_g, np_x = L.np_x;
     uint32_t *hs = sh, *hg = sh + np_s * RADIX, *hx = hg + np_g * RADIX;
     for (int i = tid; i < IN_MAXP * RADIX; i += IN_THREADS) sh[i] = 0;
     __syncthreads();
+    const uint64_t ecap = (uint64_t)L.maxb + 1;
     for (uint64_t tile = blockIdx.x; tile < L.ntiles_in; tile += gridDim.x) {
         const uint32_t t = trace_of_tile(td, L.T, tile);
         const TraceDesc &d = td[t];
+        const bool hash_tr = d.hash_ok != 0;
+        if (MODE == IN_FALLBACK && !(hash_tr && *(volatile uint32_t *)&ts[t].inel)) continue;   // uniform per tile
         const uint4 *ev = d.events;
         const uint64_t tbase = (tile - d.tile_off) * IN_TILE;
         const bool sorted = (d.flags & 1u) == 0;
-        uint32_t cS = 0, cG = 0;
-        uint32_t rS[IN_ITEMS], rG[IN_ITEMS];
+        const bool route_sg = (MODE == IN_FIRST && !hash_tr) || MODE == IN_FALLBACK;
+        uint32_t cS = 0, cG = 0, cX = 0;
+        uint32_t rS[IN_ITEMS], rG[IN_ITEMS], rX[IN_ITEMS];
         uint64_t val[IN_ITEMS];
         KS ks[IN_ITEMS];
         KG kg[IN_ITEMS];
         KX kx[IN_ITEMS];
-        uint32_t route = 0;   // bit j: S, bit 8+j: G
+        uint32_t route = 0;   // bit j: S, bit 8+j: G, bit 16+j: X
 #pragma unroll
         for (int j = 0; j < IN_ITEMS; j++) {
             const uint64_t idx = tbase + (uint64_t)j * IN_THREADS + tid;   // record index in the trace
             uint4 e = make_uint4(0, 0, 0, 0);
             const bool in = idx < d.n;
             if (in) e = ev[idx];
-            uint32_t prev_vo = __shfl_up_sync(0xFFFFFFFFu, e.y, 1);
-            if (lane == 0 && in && idx > 0) prev_vo = ev[idx - 1].y;
+            uint4 pe;
+            pe.x = __shfl_up_sync(0xFFFFFFFFu, e.x, 1);
+            pe.y = __shfl_up_sync(0xFFFFFFFFu, e.y, 1);
+            pe.z = __shfl_up_sync(0xFFFFFFFFu, e.z, 1);
+            pe.w = __shfl_up_sync(0xFFFFFFFFu, e.w, 1);
+            if (lane == 0 && in && idx > 0) pe = ev[idx - 1];
             const uint32_t u = e.x, vo = e.y, blk = e.z, w3 = e.w;
             const uint32_t tt = w3 & 0xFFFFu, ep = (w3 >> 16) & 0xFFFu, act = (w3 >> 28) & 3u;
             const uint32_t space = (w3 >> 30) & 1u, resv = w3 >> 31;
             bool ok = in && blk < d.nb && tt < d.bt && act != 3u && resv == 0u && (space ? u < d.gu : u < d.su);
             const uint32_t gtid = blk * d.bt + tt;
             if (ok && ep > d.counts[gtid]) ok = false;
-            if (in && sorted && idx > 0 && vo <= prev_vo) ok = false;
-            if (in && !ok) atomicMax(&ts[t].bad_rec, ~(unsigned long long)idx);
+            if (in && sorted && idx > 0 && vo <= pe.y) ok = false;
+            if (MODE == IN_FIRST || MODE == IN_VALIDATE)
+                if (in && !ok) atomicMax(&ts[t].bad_rec, ~(unsigned long long)idx);
             // routed records also keep the epoch inside the key's epoch field
-            const bool route_ok = ROUTE && ok && ep <= d.maxb;
-            const bool isS = route_ok && space == 0u, isG = route_ok && space == 1u;
+            const bool rok = MODE != IN_VALIDATE && ok && ep <= d.maxb;
+            const bool isS = rok && route_sg && space == 0u, isG = rok && route_sg && space == 1u;
+            const bool isX = MODE == IN_FIRST && rok && space == 1u;
+            if (MODE == IN_FIRST && hash_tr && rok) {
+                // bounds of (block, epoch) runs, and their order
+                const uint64_t cs = ((uint64_t)d.block_off + blk) * ecap + ep;
+                if (idx == 0) {
+                    runs[2 * cs] = 0;
+                } else {
+                    const uint32_t pb = pe.z, pp = (pe.w >> 16) & 0xFFFu;
+                    if (pb != blk || pp != ep) {
+                        if (pb > blk || (pb == blk && pp > ep)) atomicOr(&ts[t].inel, 1u);
+                        runs[2 * cs] = (uint32_t)idx;
+                        if (pb < d.nb && pp <= d.maxb) runs[2 * (((uint64_t)d.block_off + pb) * ecap + pp) + 1] = (uint32_t)idx;
+                    }
+                }
+                if (idx + 1 == d.n) runs[2 * cs + 1] = (uint32_t)d.n;
+            }
             const uint32_t bS = __ballot_sync(0xFFFFFFFFu, isS), bG = __ballot_sync(0xFFFFFFFFu, isG);
+            const uint32_t bX = __ballot_sync(0xFFFFFFFFu, isX);
             rS[j] = cS + __popc(bS & lt);
             rG[j] = cG + __popc(bG & lt);
+            rX[j] = cX + __popc(bX & lt);
             cS += __popc(bS);
             cG += __popc(bG);
+            cX += __popc(bX);
             const uint32_t pos = sorted ? vo : (in ? rank[d.rec_off + idx] : 0u);
             val[j] = make_payload(act, gtid, pos);
             const uint64_t sb = (uint64_t)d.block_off + blk;
             ks[j] = (KS)(shl(sb, L.bus + L.be) | shl(u, L.be) | ep);
             kg[j] = (KG)(shl(sb, L.bug + L.be) | shl(u, L.be) | ep);
             kx[j] = (KX)(shl(t, L.bug) | u);
-            route |= (isS ? 1u : 0u) << j;
-            route |= (isG ? 1u : 0u) << (8 + j);
+            route |= ((isS ? 1u : 0u) << j) | ((isG ? 1u : 0u) << (8 + j)) | ((isX ? 1u : 0u) << (16 + j));
             hist_add(hs, (uint64_t)ks[j], np_s, isS, bS);
             hist_add(hg, (uint64_t)kg[j], np_g, isG, bG);
-            hist_add(hx, (uint64_t)kx[j], np_x, isG, bG);
+            hist_add(hx, (uint64_t)kx[j], np_x, isX, bX);
         }
-        if (lane == 0) { wtot[w][0] = cS; wtot[w][1] = cG; }
+        if (MODE == IN_VALIDATE) continue;
+        if (lane == 0) { wtot[w][0] = cS; wtot[w][1] = cG; wtot[w][2] = cX; }
         __syncthreads();
         if (tid == 0) {
-            uint32_t a = 0, b = 0;
+            uint32_t a = 0, b = 0, c = 0;
             for (int i = 0; i < IN_THREADS / 32; i++) {
-                const uint32_t x = wtot[i][0], y = wtot[i][1];
-                wtot[i][0] = a; wtot[i][1] = b;
-                a += x; b += y;
+                const uint32_t x = wtot[i][0], y = wtot[i][1], z = wtot[i][2];
+                wtot[i][0] = a; wtot[i][1] = b; wtot[i][2] = c;
+                a += x; b += y; c += z;
             }
             cbase[0] = a ? atomicAdd(&ctl->n_s, a) : 0u;
             cbase[1] = b ? atomicAdd(&ctl->n_g, b) : 0u;
+            cbase[2] = c ? atomicAdd(&ctl->n_x, c) : 0u;
         }
         __syncthreads();
-        const uint32_t oS = cbase[0] + wtot[w][0], oG = cbase[1] + wtot[w][1];
+        const uint32_t oS = cbase[0] + wtot[w][0], oG = cbase[1] + wtot[w][1], oX = cbase[2] + wtot[w][2];
 #pragma unroll
         for (int j = 0; j < IN_ITEMS; j++) {
             if (route & (1u << j)) {
@@ -175,13 +211,16 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
             if (route & (1u << (8 + j))) {
                 gk[oG + rG[j]] = kg[j];
                 gv[oG + rG[j]] = val[j];
-                xk[oG + rG[j]] = kx[j];
-                xv[oG + rG[j]] = val[j];
+            }
+            if (route & (1u << (16 + j))) {
+                xk[oX + rX[j]] = kx[j];
+                xv[oX + rX[j]] = val[j];
             }
         }
         __syncthreads();
     }
     __syncthreads();
+    if (MODE == IN_VALIDATE) return;
     const uint32_t tot = (np_s + np_g + np_x) * RADIX;
     for (uint32_t i = tid; i < tot; i += IN_THREADS) {
         const uint32_t c = sh[i];

@@ -47,7 +47,7 @@ struct TraceDesc {
     uint64_t tile_off;         // first ingest tile of this trace
     uint32_t block_off;        // batch-wide index of this trace's block 0
     uint32_t nb, bt, su, gu, maxb, flags;
-    uint32_t pad;
+    uint32_t hash_ok;          // eligible for the short-interval hash path (host decision)
     uint8_t *races;    uint64_t races_cap;    // outputs (device), as in simulee_outputs
     uint8_t *divs;     uint64_t divs_cap;
     uint8_t *reds;     uint64_t reds_cap;
@@ -62,17 +62,16 @@ struct TState {
     unsigned int n_races;         // race records of the trace
     unsigned int n_grid;          // grid-redundant barriers of the trace
     unsigned int race_start;      // position of the trace's first race in the sorted race list
-    unsigned int pad;
+    unsigned int inel;            // hash-path trace found unsuitable on the device (order or run length)
 };
 
 // Device control block at the start of the workspace; zeroed by every call.
 struct Ctl {
     unsigned int timeout;         // a bounded wait gave up
-    unsigned int n_s, n_g;        // shared / global stream sizes (the inter stream has n_g too)
+    unsigned int n_s, n_g, n_x;   // shared-intra, global-intra and global-inter stream sizes
     unsigned int n_races;         // staged race records (all traces)
     unsigned int n_div, n_red;    // divergent blocks / redundant barriers (all traces)
     unsigned int n_q;             // records in the schedule-rank sort (unsorted traces)
-    unsigned int pad0;
     unsigned int tiles[MAX_PASSES];  // onesweep tile counters, one per pass
 };
 
@@ -84,6 +83,7 @@ struct Layout {
     uint64_t ntiles_in;              // ingest tiles, all traces
     uint32_t maxb;                   // largest max_barriers
     uint32_t any_unsorted;
+    uint32_t hash;                   // some trace may take the hash path (run table allocated)
     uint32_t bb, bus, bug, be, bu, btr;   // bit widths: batch block, shared unit, global unit, epoch,
                                            // max(unit), trace index
     uint32_t bits_s, bits_g, bits_x, bits_r, bits_q;
@@ -94,7 +94,7 @@ struct Layout {
     uint64_t race_cap;               // staging capacity for race records
     uint64_t status_tiles;           // tiles covered by the look-back status array
     size_t off_ctl, off_td, off_ts, off_tob, off_stats, off_nonred, off_gridnr, off_gridhas, off_cnt_div,
-        off_cnt_red, off_ofs_div, off_ofs_red, off_hist, off_dbase, off_status, off_rank, off_p2v;
+        off_cnt_red, off_ofs_div, off_ofs_red, off_hist, off_dbase, off_status, off_rank, off_p2v, off_runs;
     size_t off_sk[2], off_sv[2], off_gk[2], off_gv[2], off_xk[2], off_xv[2];
     size_t off_rk[2], off_rv[2], off_rp;
     size_t zero_end;                 // bytes from the start that every call zeroes

@@ -23,6 +23,7 @@
 
 #include "../../include/simulee.h"
 #include "check_kernels.cuh"
+#include "hash_path.cuh"
 #include "sort.cuh"
 
 using namespace simk;
@@ -148,6 +149,10 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, Layout &L) {
         L.off_rank = take(n1 * 4);
         L.off_p2v = take(n1 * 4);
     }
+    // (block, epoch) run bounds for the hash path, when the table stays small
+    const uint64_t run_slots = (uint64_t)L.NB * ((uint64_t)maxb + 1);
+    L.hash = run_slots <= (1ull << 25) ? 1u : 0u;
+    if (L.hash) L.off_runs = take(run_slots * 8);
     const size_t ks = L.wide_s ? 8 : 4, kg = L.wide_g ? 8 : 4, kx = L.wide_x ? 8 : 4;
     for (int i = 0; i < 2; i++) {
         L.off_sk[i] = take(n1 * ks);
@@ -317,6 +322,14 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     if (ws_bytes < R.L.total) return SIMULEE_ENOMEM;
     std::vector<TraceDesc> hdesc;
     fill_descs(traces, outs, reports, T, hdesc);
+    bool any_hash = false;
+    const bool route_any = want.races || want.red;
+    for (uint32_t i = 0; i < T; i++) {
+        TraceDesc &d = hdesc[i];
+        d.hash_ok = (R.L.hash && route_any && ctx->opt.path != SIMULEE_PATH_SORT && !(d.flags & SIMULEE_FLAG_UNSORTED) &&
+                     d.su < 0x7FFFFFFFu && d.gu < 0x7FFFFFFFu && d.n > 0) ? 1u : 0u;
+        any_hash |= d.hash_ok != 0;
+    }
     int prev_dev = -1;
     cudaGetDevice(&prev_dev);
     if (prev_dev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return SIMULEE_ECUDA;
@@ -327,6 +340,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
         set_reduce_attr<uint64_t, false>();
         set_reduce_attr<uint32_t, true>();
         set_reduce_attr<uint64_t, true>();
+        cudaFuncSetAttribute(k_hash_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hash_blocks_smem());
         ctx->attrs_set = true;
     }
     R.st = (cudaStream_t)stream;
@@ -345,6 +359,8 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     R.mark(SIMULEE_STAGE_INGEST, 0);
     cudaMemsetAsync(R.ws, 0, L.zero_end, st);
     cudaMemsetAsync(R.ws + L.off_status, 0, (size_t)L.status_tiles * RADIX * 8, st);
+    uint32_t *runs = any_hash ? R.at<uint32_t>(L.off_runs) : nullptr;
+    if (any_hash) cudaMemsetAsync(runs, 0, (size_t)L.NB * (L.maxb + 1) * 8, st);
     for (uint32_t i = 0; i < T; i += kDescChunk) {
         DescChunk c;
         const uint32_t cnt = std::min<uint32_t>(kDescChunk, T - i);
@@ -384,25 +400,39 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
             R.launches++;
         }
 
-        // 4. ingest
+        // 4. ingest: first read; then, for hash-path traces found unsuitable, a fallback read
         const int gi = R.grid_for(L.ntiles_in, 1, 4);
-#define SIM_INGEST(KS, KG, KX, RT)                                                                                  \
-    k_ingest<KS, KG, KX, RT><<<gi, IN_THREADS, 0, st>>>(td, rank, L, ts, R.ctl, R.at<KS>(L.off_sk[0]),               \
-                                                        R.at<uint64_t>(L.off_sv[0]), R.at<KG>(L.off_gk[0]),          \
-                                                        R.at<uint64_t>(L.off_gv[0]), R.at<KX>(L.off_xk[0]),          \
-                                                        R.at<uint64_t>(L.off_xv[0]), hist)
-        const int wmask = (L.wide_s ? 1 : 0) | (L.wide_g ? 2 : 0) | (L.wide_x ? 4 : 0);
-        if (!route) SIM_INGEST(uint32_t, uint32_t, uint32_t, false);
-        else if (wmask == 0) SIM_INGEST(uint32_t, uint32_t, uint32_t, true);
-        else if (wmask == 1) SIM_INGEST(uint64_t, uint32_t, uint32_t, true);
-        else if (wmask == 2) SIM_INGEST(uint32_t, uint64_t, uint32_t, true);
-        else if (wmask == 3) SIM_INGEST(uint64_t, uint64_t, uint32_t, true);
-        else if (wmask == 4) SIM_INGEST(uint32_t, uint32_t, uint64_t, true);
-        else if (wmask == 5) SIM_INGEST(uint64_t, uint32_t, uint64_t, true);
-        else if (wmask == 6) SIM_INGEST(uint32_t, uint64_t, uint64_t, true);
-        else SIM_INGEST(uint64_t, uint64_t, uint64_t, true);
+#define SIM_INGEST(KS, KG, KX, MODE)                                                                                \
+    k_ingest<KS, KG, KX, MODE><<<gi, IN_THREADS, 0, st>>>(td, rank, L, ts, R.ctl, R.at<KS>(L.off_sk[0]),             \
+                                                          R.at<uint64_t>(L.off_sv[0]), R.at<KG>(L.off_gk[0]),        \
+                                                          R.at<uint64_t>(L.off_gv[0]), R.at<KX>(L.off_xk[0]),        \
+                                                          R.at<uint64_t>(L.off_xv[0]), hist, runs)
+#define SIM_INGEST_W(MODE)                                                                                          \
+    do {                                                                                                            \
+        const int wmask = (L.wide_s ? 1 : 0) | (L.wide_g ? 2 : 0) | (L.wide_x ? 4 : 0);                             \
+        if (wmask == 0) SIM_INGEST(uint32_t, uint32_t, uint32_t, MODE);                                              \
+        else if (wmask == 1) SIM_INGEST(uint64_t, uint32_t, uint32_t, MODE);                                         \
+        else if (wmask == 2) SIM_INGEST(uint32_t, uint64_t, uint32_t, MODE);                                         \
+        else if (wmask == 3) SIM_INGEST(uint64_t, uint64_t, uint32_t, MODE);                                         \
+        else if (wmask == 4) SIM_INGEST(uint32_t, uint32_t, uint64_t, MODE);                                         \
+        else if (wmask == 5) SIM_INGEST(uint64_t, uint32_t, uint64_t, MODE);                                         \
+        else if (wmask == 6) SIM_INGEST(uint32_t, uint64_t, uint64_t, MODE);                                         \
+        else SIM_INGEST(uint64_t, uint64_t, uint64_t, MODE);                                                         \
+        R.launches++;                                                                                               \
+    } while (0)
+        if (!route) {
+            SIM_INGEST(uint32_t, uint32_t, uint32_t, IN_VALIDATE);
+            R.launches++;
+        } else {
+            SIM_INGEST_W(IN_FIRST);
+            if (any_hash) {
+                k_runs_check<<<R.grid_for((uint64_t)L.NB * (L.maxb + 1), 256, 8), 256, 0, st>>>(td, tob, runs, L, ts);
+                R.launches++;
+                SIM_INGEST_W(IN_FALLBACK);
+            }
+        }
+#undef SIM_INGEST_W
 #undef SIM_INGEST
-        R.launches++;
     }
     R.mark(SIMULEE_STAGE_INGEST, 1);
 
@@ -421,8 +451,8 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
                       : R.sort<uint32_t>(sk, sv, &R.ctl->n_s, L.n, L.np_s, L.p0_s);
         bg = L.wide_g ? R.sort<uint64_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g)
                       : R.sort<uint32_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g);
-        bx = L.wide_x ? R.sort<uint64_t>(xk, xv, &R.ctl->n_g, L.n, L.np_x, L.p0_x)
-                      : R.sort<uint32_t>(xk, xv, &R.ctl->n_g, L.n, L.np_x, L.p0_x);
+        bx = L.wide_x ? R.sort<uint64_t>(xk, xv, &R.ctl->n_x, L.n, L.np_x, L.p0_x)
+                      : R.sort<uint32_t>(xk, xv, &R.ctl->n_x, L.n, L.np_x, L.p0_x);
     }
     R.mark(SIMULEE_STAGE_SORT, 1);
 
@@ -447,12 +477,21 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
         else SIM_REDUCE(uint32_t, false, L.off_sk[bs], L.off_sv[bs], &R.ctl->n_s, 0u, L.bus);
         if (L.wide_g) SIM_REDUCE(uint64_t, false, L.off_gk[bg], L.off_gv[bg], &R.ctl->n_g, 1u, L.bug);
         else SIM_REDUCE(uint32_t, false, L.off_gk[bg], L.off_gv[bg], &R.ctl->n_g, 1u, L.bug);
-        if (L.wide_x) SIM_REDUCE(uint64_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_g, 1u, L.bug);
-        else SIM_REDUCE(uint32_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_g, 1u, L.bug);
+        if (L.wide_x) SIM_REDUCE(uint64_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_x, 1u, L.bug);
+        else SIM_REDUCE(uint32_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_x, 1u, L.bug);
 #undef SIM_REDUCE
         R.launches += 3;
     }
     R.mark(SIMULEE_STAGE_REDUCE, 1);
+
+    // 6b. short-interval hash path: intra-block races and adjacency of hash-path traces
+    R.mark(SIMULEE_STAGE_HASH, 0);
+    if (sorting && any_hash) {
+        k_hash_blocks<<<std::max(1, std::min<int>(ctx->sms, (int)L.NB)), HB_THREADS, hash_blocks_smem(), st>>>(
+            td, tob, R.at<uint4>(L.off_stats), runs, L, ts, R.ctl, nonred, rs);
+        R.launches++;
+    }
+    R.mark(SIMULEE_STAGE_HASH, 1);
 
     // 7. races in canonical order, split per trace
     R.mark(SIMULEE_STAGE_RACES, 0);

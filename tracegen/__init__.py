@@ -251,6 +251,20 @@ def random_tiny(seed: int, n_events: int | None = None, n_blocks: int | None = N
                  meta=dict(kind="random_tiny", seed=seed))
 
 
+def random_grouped(seed: int, **kw) -> Trace:
+    """A random tiny trace reordered into simulator order: records sorted by
+    (block, epoch) (stable), visit orders renumbered 0..n-1."""
+    tr = random_tiny(seed, unsorted=False, **kw)
+    ev = tr.events
+    epoch = (ev[:, 3] >> 16) & 0xFFF
+    order = np.lexsort((np.arange(len(ev)), epoch, ev[:, 2]))
+    ev = np.ascontiguousarray(ev[order])
+    ev[:, 1] = np.arange(len(ev), dtype=np.uint32)
+    tr.events = ev
+    tr.meta["kind"] = "random_grouped"
+    return tr
+
+
 class Builder:
     """Hand-built traces: records are appended in schedule order (visit order = serial)."""
 
