@@ -86,8 +86,10 @@ __device__ __forceinline__ void hist_add(uint32_t *sh, uint64_t key, uint32_t np
 // (block, unit, epoch); for traces on the hash path record the bounds of every
 // (block, epoch) run and check that runs come in (block, epoch) order. Digit
 // histograms of the radix passes are built on the way.
-// Fallback read (IN_FALLBACK): route S and G for hash-path traces that the
-// device found unsuitable (order or run length).
+// Fallback read (IN_FALLBACK): route S and G for the blocks of hash-path
+// traces that the device found unsuitable: a block whose epochs are out of
+// order or whose (block, epoch) run is too long, or every block of a trace
+// whose blocks are out of order. Tiles holding no such block are skipped.
 // Validate-only read (IN_VALIDATE): validation alone.
 // Persistent CTAs over tiles of 2048 records; a tile never spans two traces.
 // ---------------------------------------------------------------------------
@@ -100,7 +102,8 @@ constexpr int IN_FIRST = 0, IN_FALLBACK = 1, IN_VALIDATE = 2;
 template <class KS, class KG, class KX, int MODE>
 __global__ void __launch_bounds__(IN_THREADS)
 k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, Layout L, TState *ts, Ctl *ctl,
-         KS *sk, uint64_t *sv, KG *gk, uint64_t *gv, KX *xk, uint64_t *xv, uint32_t *hist, uint32_t *runs) {
+         KS *sk, uint64_t *sv, KG *gk, uint64_t *gv, KX *xk, uint64_t *xv, uint32_t *hist, uint32_t *runs,
+         uint32_t *binel) {
     __shared__ uint32_t sh[IN_MAXP * RADIX];
     __shared__ uint32_t wtot[IN_THREADS / 32][3];
     __shared__ uint32_t cbase[3];
@@ -111,15 +114,34 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
     for (int i = tid; i < IN_MAXP * RADIX; i += IN_THREADS) sh[i] = 0;
     __syncthreads();
     const uint64_t ecap = (uint64_t)L.maxb + 1;
+    __shared__ uint32_t s_fb;   // fallback read: does this tile hold a block that needs the sort path?
     for (uint64_t tile = blockIdx.x; tile < L.ntiles_in; tile += gridDim.x) {
         const uint32_t t = trace_of_tile(td, L.T, tile);
         const TraceDesc &d = td[t];
         const bool hash_tr = d.hash_ok != 0;
-        if (MODE == IN_FALLBACK && !(hash_tr && *(volatile uint32_t *)&ts[t].inel)) continue;   // uniform per tile
         const uint4 *ev = d.events;
         const uint64_t tbase = (tile - d.tile_off) * IN_TILE;
+        bool trace_fb = false;
+        if (MODE == IN_FALLBACK) {
+            if (!hash_tr) continue;   // uniform per tile
+            trace_fb = *(volatile uint32_t *)&ts[t].inel != 0;
+            if (!trace_fb) {
+                // blocks are in record order here: the tile covers blocks first..last
+                if (tid == 0) {
+                    const uint64_t last = min(tbase + IN_TILE, d.n) - 1;
+                    const uint32_t b0 = min(ev[tbase].z, d.nb - 1), b1 = min(ev[last].z, d.nb - 1);
+                    uint32_t any = 0;
+                    for (uint32_t bb = b0; bb <= b1 && !any; bb++) any = binel[(uint64_t)d.block_off + bb];
+                    s_fb = any;
+                }
+                __syncthreads();
+                const uint32_t any = s_fb;
+                __syncthreads();
+                if (!any) continue;
+            }
+        }
         const bool sorted = (d.flags & 1u) == 0;
-        const bool route_sg = (MODE == IN_FIRST && !hash_tr) || MODE == IN_FALLBACK;
+        const bool route_sg_tile = (MODE == IN_FIRST && !hash_tr) || MODE == IN_FALLBACK;
         uint32_t cS = 0, cG = 0, cX = 0;
         uint32_t rS[IN_ITEMS], rG[IN_ITEMS], rX[IN_ITEMS];
         uint64_t val[IN_ITEMS];
@@ -150,6 +172,8 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
                 if (in && !ok) atomicMax(&ts[t].bad_rec, ~(unsigned long long)idx);
             // routed records also keep the epoch inside the key's epoch field
             const bool rok = MODE != IN_VALIDATE && ok && ep <= d.maxb;
+            const bool route_sg = route_sg_tile && (MODE != IN_FALLBACK || trace_fb ||
+                                                    (rok && binel[(uint64_t)d.block_off + blk] != 0));
             const bool isS = rok && route_sg && space == 0u, isG = rok && route_sg && space == 1u;
             const bool isX = MODE == IN_FIRST && rok && space == 1u;
             if (MODE == IN_FIRST && hash_tr && rok) {
@@ -160,7 +184,8 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
                 } else {
                     const uint32_t pb = pe.z, pp = (pe.w >> 16) & 0xFFFu;
                     if (pb != blk || pp != ep) {
-                        if (pb > blk || (pb == blk && pp > ep)) atomicOr(&ts[t].inel, 1u);
+                        if (pb > blk) atomicOr(&ts[t].inel, 1u);                      // blocks out of order
+                        else if (pb == blk && pp > ep) atomicOr(&binel[d.block_off + blk], 1u);   // epochs out of order
                         runs[2 * cs] = (uint32_t)idx;
                         if (pb < d.nb && pp <= d.maxb) runs[2 * (((uint64_t)d.block_off + pb) * ecap + pp) + 1] = (uint32_t)idx;
                     }

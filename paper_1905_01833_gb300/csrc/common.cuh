@@ -62,7 +62,7 @@ struct TState {
     unsigned int n_races;         // race records of the trace
     unsigned int n_grid;          // grid-redundant barriers of the trace
     unsigned int race_start;      // position of the trace's first race in the sorted race list
-    unsigned int inel;            // hash-path trace found unsuitable on the device (order or run length)
+    unsigned int inel;            // hash-path trace whose blocks are not contiguous in record order
 };
 
 // Device control block at the start of the workspace; zeroed by every call.
@@ -93,6 +93,7 @@ struct Layout {
     uint32_t words;                  // 32-bit words per block in the barrier bitmaps
     uint64_t race_cap;               // staging capacity for race records
     uint64_t status_tiles;           // tiles covered by the look-back status array
+    size_t off_binel;                // per batch-wide block: the hash path does not apply to it
     size_t off_ctl, off_td, off_ts, off_tob, off_stats, off_nonred, off_gridnr, off_gridhas, off_cnt_div,
         off_cnt_red, off_ofs_div, off_ofs_red, off_hist, off_dbase, off_status, off_rank, off_p2v, off_runs;
     size_t off_sk[2], off_sv[2], off_gk[2], off_gv[2], off_xk[2], off_xv[2];

@@ -67,7 +67,8 @@ __device__ __forceinline__ uint64_t hb_item64(uint32_t v) {
 
 __global__ void __launch_bounds__(HB_THREADS, 1)
 k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob, const uint4 *__restrict__ stats,
-              const uint32_t *__restrict__ runs, Layout L, TState *ts, Ctl *ctl, uint32_t *nonred, RaceStage rs) {
+              const uint32_t *__restrict__ runs, const uint32_t *__restrict__ binel, Layout L, TState *ts, Ctl *ctl,
+              uint32_t *nonred, RaceStage rs) {
     extern __shared__ __align__(16) uint32_t hb_smem[];
     uint32_t *hkey = hb_smem;                          // [2][HB_SLOTS]
     uint32_t *hfirst = hkey + 2 * HB_SLOTS;            // [3][HB_SLOTS]
@@ -81,7 +82,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         const uint32_t t = tob[b];
         const TraceDesc &d = td[t];
         // uniform over the CTA: only suitable, valid hash-path traces
-        if (!d.hash_ok || *(volatile uint32_t *)&ts[t].inel || trace_bad(ts[t])) continue;
+        if (!d.hash_ok || *(volatile uint32_t *)&ts[t].inel || binel[b] || trace_bad(ts[t])) continue;
         const uint64_t lb = b - d.block_off;
         const uint32_t maxc = min(stats[b].w, L.maxb);
         int cur = 0;
@@ -208,14 +209,15 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
     }
 }
 
-// A hash-path trace whose (block, epoch) runs exceed HB_RUNMAX records goes to the sort path.
-__global__ void k_runs_check(const TraceDesc *td, const uint32_t *tob, const uint32_t *runs, Layout L, TState *ts) {
+// A block with a (block, epoch) run longer than HB_RUNMAX records goes to the sort path.
+__global__ void k_runs_check(const TraceDesc *td, const uint32_t *tob, const uint32_t *runs, Layout L,
+                             uint32_t *binel) {
     const uint64_t tot = (uint64_t)L.NB * (L.maxb + 1);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t t = tob[i / (L.maxb + 1)];
-        if (!td[t].hash_ok) continue;
+        const uint64_t b = i / (L.maxb + 1);
+        if (!td[tob[b]].hash_ok) continue;
         const uint32_t s = runs[2 * i], e = runs[2 * i + 1];
-        if (e < s || e - s > (uint32_t)HB_RUNMAX) atomicOr(&ts[t].inel, 1u);
+        if (e < s || e - s > (uint32_t)HB_RUNMAX) atomicOr(&binel[b], 1u);
     }
 }
 

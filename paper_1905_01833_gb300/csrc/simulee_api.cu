@@ -135,6 +135,7 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, Layout &L) {
     L.off_gridnr = take((size_t)T * L.words * 4);
     L.off_gridhas = take((size_t)T * L.words * 4);
     L.off_hist = take((size_t)MAX_PASSES * RADIX * 4);
+    L.off_binel = take((size_t)L.NB * 4);
     L.zero_end = o;
     L.off_td = take((size_t)T * sizeof(TraceDesc));
     L.off_tob = take((size_t)L.NB * 4);
@@ -360,6 +361,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     cudaMemsetAsync(R.ws, 0, L.zero_end, st);
     cudaMemsetAsync(R.ws + L.off_status, 0, (size_t)L.status_tiles * RADIX * 8, st);
     uint32_t *runs = any_hash ? R.at<uint32_t>(L.off_runs) : nullptr;
+    uint32_t *binel = R.at<uint32_t>(L.off_binel);
     if (any_hash) cudaMemsetAsync(runs, 0, (size_t)L.NB * (L.maxb + 1) * 8, st);
     for (uint32_t i = 0; i < T; i += kDescChunk) {
         DescChunk c;
@@ -406,7 +408,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     k_ingest<KS, KG, KX, MODE><<<gi, IN_THREADS, 0, st>>>(td, rank, L, ts, R.ctl, R.at<KS>(L.off_sk[0]),             \
                                                           R.at<uint64_t>(L.off_sv[0]), R.at<KG>(L.off_gk[0]),        \
                                                           R.at<uint64_t>(L.off_gv[0]), R.at<KX>(L.off_xk[0]),        \
-                                                          R.at<uint64_t>(L.off_xv[0]), hist, runs)
+                                                          R.at<uint64_t>(L.off_xv[0]), hist, runs, binel)
 #define SIM_INGEST_W(MODE)                                                                                          \
     do {                                                                                                            \
         const int wmask = (L.wide_s ? 1 : 0) | (L.wide_g ? 2 : 0) | (L.wide_x ? 4 : 0);                             \
@@ -426,7 +428,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
         } else {
             SIM_INGEST_W(IN_FIRST);
             if (any_hash) {
-                k_runs_check<<<R.grid_for((uint64_t)L.NB * (L.maxb + 1), 256, 8), 256, 0, st>>>(td, tob, runs, L, ts);
+                k_runs_check<<<R.grid_for((uint64_t)L.NB * (L.maxb + 1), 256, 8), 256, 0, st>>>(td, tob, runs, L, binel);
                 R.launches++;
                 SIM_INGEST_W(IN_FALLBACK);
             }
@@ -488,7 +490,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     R.mark(SIMULEE_STAGE_HASH, 0);
     if (sorting && any_hash) {
         k_hash_blocks<<<std::max(1, std::min<int>(ctx->sms, (int)L.NB)), HB_THREADS, hash_blocks_smem(), st>>>(
-            td, tob, R.at<uint4>(L.off_stats), runs, L, ts, R.ctl, nonred, rs);
+            td, tob, R.at<uint4>(L.off_stats), runs, binel, L, ts, R.ctl, nonred, rs);
         R.launches++;
     }
     R.mark(SIMULEE_STAGE_HASH, 1);

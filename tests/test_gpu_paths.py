@@ -56,3 +56,13 @@ def test_batch_mixing_paths():
     got = checker().check_batch([simulee.to_device(t) for t in trs])
     for i, tr in enumerate(trs):
         assert diff(got[i], oracle.check(tr)) == [], f"trace {i}"
+
+
+@pytest.mark.parametrize("path", sorted(PATHS))
+def test_blocks_with_merged_epochs_take_the_sort_path(path):
+    """Half the blocks lose a barrier, so two epochs merge into one run longer
+    than the hash path's limit: those blocks go through the sort path, the
+    rest stay on the hash path, within one trace."""
+    tr = tracegen.pattern(21, n_blocks=16, block_threads=256, n_epochs=20, shared_units=12288,
+                          global_units=1 << 20, removed_p=0.5)
+    assert diff(gpu_check(tr, path=PATHS[path]), oracle.check(tr)) == []
