@@ -109,25 +109,36 @@ def gpu_uuid(torch, dev: int) -> str | None:
         return None
 
 
-def stream_bytes(tr):
-    """Records per stream and key widths, as the library lays them out (for algorithmic bytes)."""
-    def bits(count):
-        b = 0
-        while (1 << b) < count:
-            b += 1
-        return b
-    glob = ((tr.events[:, 3] >> 30) & 1) == 1
-    n_g = int(glob.sum())
-    n_s = tr.n_events - n_g
+def bits(count):
+    b = 0
+    while (1 << b) < count:
+        b += 1
+    return b
+
+
+def stage_bytes(tr, sizes):
+    """Algorithmic DRAM bytes of each stage for the plan that ran (stream sizes from the library).
+
+    ingest: one 16-byte read per record, the barrier counts, the inter-block
+    stream writes (4-byte key + 8-byte payload per global record), the sort-path
+    stream writes, and the re-read of records routed by the fallback read.
+    sort: each radix pass reads and writes key + payload of its stream.
+    reduce: one read of every sorted stream. hash: one 16-byte read of every
+    record the short-interval path checks."""
+    n = tr.n_events
+    n_s, n_g, n_x = sizes["n_s"], sizes["n_g"], sizes["n_x"]
     bb, bus, bug, be = bits(tr.n_blocks), bits(tr.shared_units), bits(tr.global_units), bits(tr.max_barriers + 1)
     ks = 8 if bb + bus + be > 32 else 4
     kg = 8 if bb + bug + be > 32 else 4
+    kx = 8 if bug > 32 else 4
     np_s, np_g, np_x = -(-(bb + bus + be) // 8), -(-(bb + bug + be) // 8), -(-bug // 8)
-    sort_bytes = 2 * (n_s * np_s * (ks + 8) + n_g * np_g * (kg + 8) + n_g * np_x * (4 + 8))
-    ingest_bytes = 16 * tr.n_events + 4 * tr.barrier_counts.size + n_s * (ks + 8) + n_g * (kg + 8 + 12)
-    reduce_bytes = n_s * (ks + 8) + n_g * (kg + 8) + n_g * 12
-    return dict(n_s=n_s, n_g=n_g, passes=np_s + np_g + np_x, sort=sort_bytes, ingest=ingest_bytes,
-                reduce=reduce_bytes)
+    return dict(
+        ingest=16 * n + 4 * tr.barrier_counts.size + n_x * (kx + 8) + n_s * (ks + 8) + n_g * (kg + 8)
+        + 16 * (n_s + n_g),
+        sort=2 * (n_s * np_s * (ks + 8) + n_g * np_g * (kg + 8) + n_x * np_x * (kx + 8)),
+        reduce=n_s * (ks + 8) + n_g * (kg + 8) + n_x * (kx + 8),
+        hash=16 * (n - n_s - n_g),
+        launches=dict(ingest=2, sort=np_s + np_g + np_x, reduce=3, hash=1))
 
 
 def kernel_traffic(kernel: str, workload: str):
@@ -188,6 +199,152 @@ def reference_arm(args, rank: int, world: int):
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def device_pool(torch, trs, dev):
+    """Upload many host traces into one device buffer; DeviceTrace views into it."""
+    from paper_1905_01833_gb300 import simulee
+    n = sum(t.n_events for t in trs)
+    m = sum(t.barrier_counts.size for t in trs)
+    ev = torch.empty((max(n, 1), 4), dtype=torch.int32, device=dev)
+    cn = torch.empty(max(m, 1), dtype=torch.int32, device=dev)
+    out, a, b = [], 0, 0
+    for t in trs:
+        k, c = t.n_events, t.barrier_counts.size
+        if k:
+            ev[a:a + k].copy_(torch.from_numpy(t.events.view(np.int32)))
+        cn[b:b + c].copy_(torch.from_numpy(t.barrier_counts.view(np.int32)))
+        out.append(simulee.DeviceTrace(ev[a:a + k], cn[b:b + c], t.n_blocks, t.block_threads, t.shared_units,
+                                       t.global_units, t.max_barriers, t.flags))
+        a += k
+        b += c
+    return out, (ev, cn)
+
+
+def batch_arm(args):
+    """Batched workload: 4096 independent traces (lognormal sizes, median 1e5 records, block sizes
+    64..1024, 4..64 epochs) checked by one batched call; direct launches and CUDA-graph replay."""
+    import ctypes
+    import torch
+    import tracegen
+    from paper_1905_01833_gb300 import simulee
+    dev = "cuda:0"
+    sizes, bss, eps = tracegen.c3_sizes(n_traces=args.batch_traces)
+    t0 = time.perf_counter()
+    trs = [tracegen.c3_trace(i, int(n), int(bs), int(e)) for i, (n, bs, e) in enumerate(zip(sizes, bss, eps))]
+    gen_s = time.perf_counter() - t0
+    dts, keep = device_pool(torch, trs, dev)
+    del trs
+    chk = simulee.Checker(0)
+    T = len(dts)
+    arr = (simulee.Trace * T)(*[d.c() for d in dts])
+    caps = [(min(2 * d.n_events + 2, 1 << 16), d.n_blocks, d.n_blocks * max(d.max_barriers, 1), max(d.max_barriers, 1))
+            for d in dts]
+    widths = (32, 16, 8, 4)
+    tot = [sum(c[k] * widths[k] for c in caps) for k in range(4)]
+    bufs = [torch.empty(max(x, 16), dtype=torch.uint8, device=dev) for x in tot]
+    outs = (simulee.Outputs * T)()
+    off = [0, 0, 0, 0]
+    for i, c in enumerate(caps):
+        outs[i] = simulee.Outputs(*(v for k in range(4) for v in (bufs[k].data_ptr() + off[k], c[k])))
+        for k in range(4):
+            off[k] += c[k] * widths[k]
+    reports = torch.zeros(T * simulee.REPORT_BYTES, dtype=torch.uint8, device=dev)
+    n = ctypes.c_size_t()
+    simulee._check(simulee.lib().simulee_batch_workspace_size(chk.h, arr, T, ctypes.byref(n)), "batch ws")
+    ws = torch.empty(int(n.value), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    L = simulee.lib()
+
+    def call():
+        s_ = L.simulee_check_batch(chk.h, arr, T, outs, ctypes.c_void_p(reports.data_ptr()),
+                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(stream.cuda_stream))
+        if s_ != 0:
+            raise RuntimeError(simulee.status_str(s_))
+
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    rep = np.frombuffer(reports.cpu().numpy().tobytes(), dtype=np.int32).reshape(T, -1)
+    assert (rep[:, 0] == 0).all() or (np.isin(rep[:, 0], [0, 4])).all(), "batch reported errors"
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the same call captured once in a CUDA graph and replayed
+    g = torch.cuda.CUDAGraph()
+    s2 = torch.cuda.Stream()
+    s2.wait_stream(stream)
+    with torch.cuda.stream(s2):
+        stream = s2
+        with torch.cuda.graph(g, stream=s2):
+            call()
+    stream = torch.cuda.current_stream()
+    g.replay()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_g = e0.elapsed_time(e1) / args.steps
+    n_ev = sum(d.n_events for d in dts)
+    return {"workload": f"batch: {T} traces, lognormal sizes (median 1e5, sigma 0.87, clipped 1e3..1e7), "
+                        f"block sizes 64..1024, 4..64 epochs", "traces": T, "n_events": n_ev,
+            "value": n_ev / (ms * 1e-3) / 1e9, "ms_per_step": ms,
+            "graph_value": n_ev / (ms_g * 1e-3) / 1e9, "graph_ms_per_step": ms_g, "unit": UNIT,
+            "launches_per_step": chk.last_launches(), "workspace_bytes": ws.numel(), "gen_s": gen_s}
+
+
+def serve_arm(args):
+    """Serving workload: Poisson arrivals of check jobs, sizes log-uniform 1e4..1e8 records from the
+    grid and barrier generators, continuous batching under a 120 GB HBM budget, against serial checking."""
+    import torch
+    import tracegen
+    from paper_1905_01833_gb300 import serve
+    rng = np.random.default_rng(7)
+    pool_sizes = np.exp(np.linspace(np.log(1e4), np.log(1e8), args.serve_pool))
+    trs = []
+    for i, sz in enumerate(pool_sizes):
+        if i % 2 == 0:   # grid family: 256-thread blocks, 32 epochs (~2e5 records per block)
+            nb = max(1, int(round(sz / 59600)))
+            tr = tracegen.pattern(100 + i, n_blocks=nb, block_threads=256, n_epochs=32, shared_units=12288,
+                                  global_units=1 << max(20, int(np.ceil(np.log2(4096 + 2 * 1024 * nb)))))
+            if tr.n_events > sz:
+                tr.events = np.ascontiguousarray(tr.events[:int(sz)])
+        else:            # barrier family: 1024-thread blocks, 64 epochs, 4 accesses (262144 records per block)
+            nb = max(1, int(round(sz / 262144)))
+            tr = tracegen.barrier(100 + i, n_blocks=nb, block_threads=1024, n_epochs=64, shared_units=8192)
+            if tr.n_events > sz:
+                tr.events = np.ascontiguousarray(tr.events[:int(sz)])
+        trs.append(tr)
+    dts, keep = device_pool(torch, trs, "cuda:0")
+    del trs
+    draws = np.exp(rng.uniform(np.log(1e4), np.log(1e8), size=args.serve_jobs))
+    pick = np.abs(np.log(draws)[:, None] - np.log(pool_sizes)[None, :]).argmin(axis=1)
+
+    def run(rate, serial):
+        arr = serve.poisson_arrivals(rate, args.serve_jobs, seed=11)
+        jobs = [serve.Job(i, dts[int(pick[i])], float(arr[i])) for i in range(args.serve_jobs)]
+        srv = serve.Server(0, hbm_budget=120 << 30, serial=serial, keep_lists=False)
+        return srv.run(jobs)
+
+    warm = serve.Server(0, keep_lists=False)
+    warm.run([serve.Job(i, dts[i % len(dts)], 0.0) for i in range(len(dts))])
+    res = {"workload": f"serve: Poisson arrivals, {args.serve_jobs} jobs, sizes log-uniform 1e4..1e8 records "
+                       f"(pool of {len(dts)} device-resident traces), 120 GB budget",
+           "unit": UNIT, "rates": {}}
+    for rate in args.serve_rates:
+        a = run(rate, serial=False)
+        b = run(rate, serial=True)
+        res["rates"][str(rate)] = {
+            "batched": {k: a[k] for k in ("p50_ms", "p99_ms", "max_ms", "batches", "max_batch", "max_inflight")}
+            | {"value": a["events_per_s"] / 1e9},
+            "serial": {k: b[k] for k in ("p50_ms", "p99_ms", "max_ms")} | {"value": b["events_per_s"] / 1e9}}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -201,8 +358,20 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--blocks", type=int, default=1024, help="grid blocks (1024 = the benchmark workload; "
                     "smaller values only for profiling captures)")
+    ap.add_argument("--workload", choices=["grid", "batch", "serve"], default="grid",
+                    help="grid: the benchmark line; batch / serve: the batched and served forms (separate lines)")
+    ap.add_argument("--batch-traces", type=int, default=4096)
+    ap.add_argument("--serve-jobs", type=int, default=2000)
+    ap.add_argument("--serve-pool", type=int, default=24)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 1000.0, 4000.0])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload in ("batch", "serve") and args.impl == "ours":
+        import torch
+        torch.cuda.set_device(0)
+        out = batch_arm(args) if args.workload == "batch" else serve_arm(args)
+        print(json.dumps({"metric": METRIC, **out}))
+        return
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -328,17 +497,19 @@ def main():
     h2d = tr.events.nbytes + tr.barrier_counts.nbytes
 
     # roofline of the dominant stage
-    sb = stream_bytes(tr)
+    sizes = chk.stream_sizes()
+    sb = stage_bytes(tr, sizes)
     peak, peak_src = peaks()
-    stage_bytes = {"ingest": sb["ingest"], "sort": sb["sort"], "reduce": sb["reduce"]}
-    dom = max(stage_bytes, key=lambda k: stage_ms[k])
-    kname = {"ingest": "k_ingest", "sort": "k_onesweep", "reduce": "k_reduce_intra+k_reduce_inter"}[dom]
-    nl = sb["passes"] if dom == "sort" else (1 if dom == "ingest" else 3)
-    achieved = stage_bytes[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    cand = [k for k in ("ingest", "sort", "reduce", "hash") if sb[k] > 0]
+    dom = max(cand, key=lambda k: stage_ms[k])
+    kname = {"ingest": "k_ingest", "sort": "k_onesweep", "reduce": "k_reduce_groups", "hash": "k_hash_blocks"}[dom]
+    nl = sb["launches"][dom]
+    achieved = sb[dom] / (stage_ms[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
-                "bytes_per_launch": stage_bytes[dom] / nl, "launch_ms": stage_ms[dom] / nl,
+                "bytes_per_launch": sb[dom] / nl, "launch_ms": stage_ms[dom] / nl,
                 "traffic": kernel_traffic(kname, "grid")}
+    stage_gbs = {k: sb[k] / (stage_ms[k] * 1e-3) / 1e9 for k in cand if stage_ms[k] > 0}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -352,6 +523,8 @@ def main():
         "gpu_launches": launches * args.steps,
         "roofline": roofline,
         "stages_ms": stage_ms,
+        "stages_gbs": stage_gbs,
+        "streams": sizes,
         "results": {"n_races": rep.n_races, "n_divergence": rep.n_divergence, "n_redundant": rep.n_redundant,
                     "n_grid_redundant": rep.n_grid_redundant},
         "clocks": clocks,

@@ -78,7 +78,7 @@ __device__ __forceinline__ void hist_add(uint32_t *sh, uint64_t key, uint32_t np
 }
 
 // ---------------------------------------------------------------------------
-// Ingest, in up to two reads of the records (16-byte loads).
+// Ingest, in up to two reads of the records.
 //
 // First read (IN_FIRST): validate every record; route global records to the
 // inter-block stream X keyed (trace, unit); for traces on the sort path route
@@ -89,21 +89,32 @@ __device__ __forceinline__ void hist_add(uint32_t *sh, uint64_t key, uint32_t np
 // Fallback read (IN_FALLBACK): route S and G for the blocks of hash-path
 // traces that the device found unsuitable: a block whose epochs are out of
 // order or whose (block, epoch) run is too long, or every block of a trace
-// whose blocks are out of order. Tiles holding no such block are skipped.
+// whose blocks are out of order. It visits only the tiles k_fallback_tiles listed.
 // Validate-only read (IN_VALIDATE): validation alone.
-// Persistent CTAs over tiles of 2048 records; a tile never spans two traces.
+//
+// Tiles of 2048 records (a tile never spans two traces) are staged into shared
+// memory by 1-D bulk copies (TMA) on an mbarrier, double-buffered: the copy of
+// the CTA's next-but-one tile is in flight while a tile is processed. Each
+// copy brings the record before the tile as well, for the order checks. A
+// tile is read twice from shared memory: once to validate and count, once to
+// write the routed elements at their stream positions.
 // ---------------------------------------------------------------------------
 constexpr int IN_THREADS = 256;
 constexpr int IN_ITEMS = 8;
 constexpr int IN_TILE = IN_THREADS * IN_ITEMS;
+constexpr int IN_STAGE = IN_TILE + 1;   // records per stage buffer (one before the tile)
 constexpr int IN_MAXP = 24;   // S + G + X passes histogrammed here
 constexpr int IN_FIRST = 0, IN_FALLBACK = 1, IN_VALIDATE = 2;
+
+constexpr size_t ingest_smem() { return 2 * (size_t)IN_STAGE * 16; }
 
 template <class KS, class KG, class KX, int MODE>
 __global__ void __launch_bounds__(IN_THREADS)
 k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, Layout L, TState *ts, Ctl *ctl,
          KS *sk, uint64_t *sv, KG *gk, uint64_t *gv, KX *xk, uint64_t *xv, uint32_t *hist, uint32_t *runs,
-         uint32_t *binel) {
+         uint32_t *binel, const uint32_t *__restrict__ tile_list, uint64_t wait_ns) {
+    extern __shared__ __align__(128) uint4 in_stage[];   // [2][IN_STAGE]
+    __shared__ uint64_t bars[2];
     __shared__ uint32_t sh[IN_MAXP * RADIX];
     __shared__ uint32_t wtot[IN_THREADS / 32][3];
     __shared__ uint32_t cbase[3];
@@ -112,64 +123,71 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
     const uint32_t np_s = L.np_s, np_g = L.np_g, np_x = L.np_x;
     uint32_t *hs = sh, *hg = sh + np_s * RADIX, *hx = hg + np_g * RADIX;
     for (int i = tid; i < IN_MAXP * RADIX; i += IN_THREADS) sh[i] = 0;
+    const uint64_t ntiles = (MODE == IN_FALLBACK) ? (uint64_t)*(volatile unsigned int *)&ctl->n_fb : L.ntiles_in;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
     __syncthreads();
     const uint64_t ecap = (uint64_t)L.maxb + 1;
-    __shared__ uint32_t s_fb;   // fallback read: does this tile hold a block that needs the sort path?
-    for (uint64_t tile = blockIdx.x; tile < L.ntiles_in; tile += gridDim.x) {
+    // thread 0: start the copy of this CTA's k-th tile into stage k & 1
+    auto issue = [&](uint64_t k) {
+        const uint64_t i = blockIdx.x + k * gridDim.x;
+        if (i >= ntiles) return;
+        const uint64_t tile = (MODE == IN_FALLBACK) ? tile_list[i] : i;
+        const TraceDesc &d = td[trace_of_tile(td, L.T, tile)];
+        const uint64_t tbase = (tile - d.tile_off) * IN_TILE;
+        const uint64_t first = tbase > 0 ? tbase - 1 : 0, last = min(tbase + IN_TILE, d.n);
+        const uint32_t bytes = (uint32_t)((last - first) * 16);
+        uint4 *dst = in_stage + (k & 1) * IN_STAGE + (tbase > 0 ? 0 : 1);
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bars[k & 1], bytes);
+        bulk_g2s(dst, d.events + first, bytes, &bars[k & 1]);
+    };
+    if (tid == 0) {
+        issue(0);
+        issue(1);
+    }
+    for (uint64_t k = 0;; k++) {
+        const uint64_t i = blockIdx.x + k * gridDim.x;
+        if (i >= ntiles) break;
+        const bool arrived = __syncthreads_and(mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), wait_ns));
+        if (!arrived) {
+            // bounded: report, give the copies in flight one more bounded wait, and stop
+            if (tid == 0) {
+                atomicExch(&ctl->timeout, 1u);
+                mbar_wait(&bars[k & 1], (uint32_t)((k >> 1) & 1), wait_ns);
+                if (i + gridDim.x < ntiles) mbar_wait(&bars[(k + 1) & 1], (uint32_t)(((k + 1) >> 1) & 1), wait_ns);
+            }
+            return;
+        }
+        const uint64_t tile = (MODE == IN_FALLBACK) ? tile_list[i] : i;
         const uint32_t t = trace_of_tile(td, L.T, tile);
         const TraceDesc &d = td[t];
-        const bool hash_tr = d.hash_ok != 0;
-        const uint4 *ev = d.events;
         const uint64_t tbase = (tile - d.tile_off) * IN_TILE;
-        bool trace_fb = false;
-        if (MODE == IN_FALLBACK) {
-            if (!hash_tr) continue;   // uniform per tile
-            trace_fb = *(volatile uint32_t *)&ts[t].inel != 0;
-            if (!trace_fb) {
-                // blocks are in record order here: the tile covers blocks first..last
-                if (tid == 0) {
-                    const uint64_t last = min(tbase + IN_TILE, d.n) - 1;
-                    const uint32_t b0 = min(ev[tbase].z, d.nb - 1), b1 = min(ev[last].z, d.nb - 1);
-                    uint32_t any = 0;
-                    for (uint32_t bb = b0; bb <= b1 && !any; bb++) any = binel[(uint64_t)d.block_off + bb];
-                    s_fb = any;
-                }
-                __syncthreads();
-                const uint32_t any = s_fb;
-                __syncthreads();
-                if (!any) continue;
-            }
-        }
+        const uint4 *recs = in_stage + (k & 1) * IN_STAGE + 1;   // recs[-1]: the record before the tile
+        const bool hash_tr = d.hash_ok != 0;
+        const bool trace_fb = MODE == IN_FALLBACK && *(volatile uint32_t *)&ts[t].inel != 0;
         const bool sorted = (d.flags & 1u) == 0;
         const bool route_sg_tile = (MODE == IN_FIRST && !hash_tr) || MODE == IN_FALLBACK;
-        uint32_t cS = 0, cG = 0, cX = 0;
-        uint32_t rS[IN_ITEMS], rG[IN_ITEMS], rX[IN_ITEMS];
-        uint64_t val[IN_ITEMS];
-        KS ks[IN_ITEMS];
-        KG kg[IN_ITEMS];
-        KX kx[IN_ITEMS];
         uint32_t route = 0;   // bit j: S, bit 8+j: G, bit 16+j: X
+        uint32_t cS = 0, cG = 0, cX = 0;
+        // pass 1: validate, decide routes, count, run bookkeeping, histograms
 #pragma unroll
         for (int j = 0; j < IN_ITEMS; j++) {
-            const uint64_t idx = tbase + (uint64_t)j * IN_THREADS + tid;   // record index in the trace
-            uint4 e = make_uint4(0, 0, 0, 0);
+            const uint32_t li = j * IN_THREADS + tid;
+            const uint64_t idx = tbase + li;   // record index in the trace
             const bool in = idx < d.n;
-            if (in) e = ev[idx];
-            uint4 pe;
-            pe.x = __shfl_up_sync(0xFFFFFFFFu, e.x, 1);
-            pe.y = __shfl_up_sync(0xFFFFFFFFu, e.y, 1);
-            pe.z = __shfl_up_sync(0xFFFFFFFFu, e.z, 1);
-            pe.w = __shfl_up_sync(0xFFFFFFFFu, e.w, 1);
-            if (lane == 0 && in && idx > 0) pe = ev[idx - 1];
+            const uint4 e = in ? recs[li] : make_uint4(0, 0, 0, 0);
+            const uint4 pe = (in && idx > 0) ? recs[(int)li - 1] : make_uint4(0, 0, 0, 0);
             const uint32_t u = e.x, vo = e.y, blk = e.z, w3 = e.w;
             const uint32_t tt = w3 & 0xFFFFu, ep = (w3 >> 16) & 0xFFFu, act = (w3 >> 28) & 3u;
             const uint32_t space = (w3 >> 30) & 1u, resv = w3 >> 31;
             bool ok = in && blk < d.nb && tt < d.bt && act != 3u && resv == 0u && (space ? u < d.gu : u < d.su);
-            const uint32_t gtid = blk * d.bt + tt;
-            if (ok && ep > d.counts[gtid]) ok = false;
+            if (ok && ep > d.counts[blk * d.bt + tt]) ok = false;
             if (in && sorted && idx > 0 && vo <= pe.y) ok = false;
-            if (MODE == IN_FIRST || MODE == IN_VALIDATE)
-                if (in && !ok) atomicMax(&ts[t].bad_rec, ~(unsigned long long)idx);
+            if (MODE != IN_FALLBACK && in && !ok) atomicMax(&ts[t].bad_rec, ~(unsigned long long)idx);
             // routed records also keep the epoch inside the key's epoch field
             const bool rok = MODE != IN_VALIDATE && ok && ep <= d.maxb;
             const bool route_sg = route_sg_tile && (MODE != IN_FALLBACK || trace_fb ||
@@ -184,7 +202,7 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
                 } else {
                     const uint32_t pb = pe.z, pp = (pe.w >> 16) & 0xFFFu;
                     if (pb != blk || pp != ep) {
-                        if (pb > blk) atomicOr(&ts[t].inel, 1u);                      // blocks out of order
+                        if (pb > blk) atomicOr(&ts[t].inel, 1u);                                   // blocks out of order
                         else if (pb == blk && pp > ep) atomicOr(&binel[d.block_off + blk], 1u);   // epochs out of order
                         runs[2 * cs] = (uint32_t)idx;
                         if (pb < d.nb && pp <= d.maxb) runs[2 * (((uint64_t)d.block_off + pb) * ecap + pp) + 1] = (uint32_t)idx;
@@ -194,55 +212,71 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
             }
             const uint32_t bS = __ballot_sync(0xFFFFFFFFu, isS), bG = __ballot_sync(0xFFFFFFFFu, isG);
             const uint32_t bX = __ballot_sync(0xFFFFFFFFu, isX);
-            rS[j] = cS + __popc(bS & lt);
-            rG[j] = cG + __popc(bG & lt);
-            rX[j] = cX + __popc(bX & lt);
             cS += __popc(bS);
             cG += __popc(bG);
             cX += __popc(bX);
-            const uint32_t pos = sorted ? vo : (in ? rank[d.rec_off + idx] : 0u);
-            val[j] = make_payload(act, gtid, pos);
-            const uint64_t sb = (uint64_t)d.block_off + blk;
-            ks[j] = (KS)(shl(sb, L.bus + L.be) | shl(u, L.be) | ep);
-            kg[j] = (KG)(shl(sb, L.bug + L.be) | shl(u, L.be) | ep);
-            kx[j] = (KX)(shl(t, L.bug) | u);
             route |= ((isS ? 1u : 0u) << j) | ((isG ? 1u : 0u) << (8 + j)) | ((isX ? 1u : 0u) << (16 + j));
-            hist_add(hs, (uint64_t)ks[j], np_s, isS, bS);
-            hist_add(hg, (uint64_t)kg[j], np_g, isG, bG);
-            hist_add(hx, (uint64_t)kx[j], np_x, isX, bX);
-        }
-        if (MODE == IN_VALIDATE) continue;
-        if (lane == 0) { wtot[w][0] = cS; wtot[w][1] = cG; wtot[w][2] = cX; }
-        __syncthreads();
-        if (tid == 0) {
-            uint32_t a = 0, b = 0, c = 0;
-            for (int i = 0; i < IN_THREADS / 32; i++) {
-                const uint32_t x = wtot[i][0], y = wtot[i][1], z = wtot[i][2];
-                wtot[i][0] = a; wtot[i][1] = b; wtot[i][2] = c;
-                a += x; b += y; c += z;
+            if (MODE != IN_VALIDATE) {
+                const uint64_t sb = (uint64_t)d.block_off + blk;
+                hist_add(hs, shl(sb, L.bus + L.be) | shl(u, L.be) | ep, np_s, isS, bS);
+                hist_add(hg, shl(sb, L.bug + L.be) | shl(u, L.be) | ep, np_g, isG, bG);
+                hist_add(hx, shl(t, L.bug) | u, np_x, isX, bX);
             }
-            cbase[0] = a ? atomicAdd(&ctl->n_s, a) : 0u;
-            cbase[1] = b ? atomicAdd(&ctl->n_g, b) : 0u;
-            cbase[2] = c ? atomicAdd(&ctl->n_x, c) : 0u;
         }
-        __syncthreads();
-        const uint32_t oS = cbase[0] + wtot[w][0], oG = cbase[1] + wtot[w][1], oX = cbase[2] + wtot[w][2];
+        if (MODE != IN_VALIDATE) {
+            if (lane == 0) { wtot[w][0] = cS; wtot[w][1] = cG; wtot[w][2] = cX; }
+            __syncthreads();
+            if (tid == 0) {
+                uint32_t a = 0, b = 0, c = 0;
+                for (int q = 0; q < IN_THREADS / 32; q++) {
+                    const uint32_t x = wtot[q][0], y = wtot[q][1], z = wtot[q][2];
+                    wtot[q][0] = a; wtot[q][1] = b; wtot[q][2] = c;
+                    a += x; b += y; c += z;
+                }
+                cbase[0] = a ? atomicAdd(&ctl->n_s, a) : 0u;
+                cbase[1] = b ? atomicAdd(&ctl->n_g, b) : 0u;
+                cbase[2] = c ? atomicAdd(&ctl->n_x, c) : 0u;
+            }
+            __syncthreads();
+            // pass 2: write the routed elements
+            uint32_t oS = cbase[0] + wtot[w][0], oG = cbase[1] + wtot[w][1], oX = cbase[2] + wtot[w][2];
 #pragma unroll
-        for (int j = 0; j < IN_ITEMS; j++) {
-            if (route & (1u << j)) {
-                sk[oS + rS[j]] = ks[j];
-                sv[oS + rS[j]] = val[j];
-            }
-            if (route & (1u << (8 + j))) {
-                gk[oG + rG[j]] = kg[j];
-                gv[oG + rG[j]] = val[j];
-            }
-            if (route & (1u << (16 + j))) {
-                xk[oX + rX[j]] = kx[j];
-                xv[oX + rX[j]] = val[j];
+            for (int j = 0; j < IN_ITEMS; j++) {
+                const bool isS = (route >> j) & 1u, isG = (route >> (8 + j)) & 1u, isX = (route >> (16 + j)) & 1u;
+                const uint32_t bS = __ballot_sync(0xFFFFFFFFu, isS), bG = __ballot_sync(0xFFFFFFFFu, isG);
+                const uint32_t bX = __ballot_sync(0xFFFFFFFFu, isX);
+                if (isS || isG || isX) {
+                    const uint32_t li = j * IN_THREADS + tid;
+                    const uint64_t idx = tbase + li;
+                    const uint4 e = recs[li];
+                    const uint32_t u = e.x, blk = e.z, w3 = e.w;
+                    const uint32_t ep = (w3 >> 16) & 0xFFFu, act = (w3 >> 28) & 3u;
+                    const uint32_t pos = sorted ? e.y : rank[d.rec_off + idx];
+                    const uint64_t val = make_payload(act, blk * d.bt + (w3 & 0xFFFFu), pos);
+                    const uint64_t sb = (uint64_t)d.block_off + blk;
+                    if (isS) {
+                        const uint32_t o = oS + __popc(bS & lt);
+                        sk[o] = (KS)(shl(sb, L.bus + L.be) | shl(u, L.be) | ep);
+                        sv[o] = val;
+                    }
+                    if (isG) {
+                        const uint32_t o = oG + __popc(bG & lt);
+                        gk[o] = (KG)(shl(sb, L.bug + L.be) | shl(u, L.be) | ep);
+                        gv[o] = val;
+                    }
+                    if (isX) {
+                        const uint32_t o = oX + __popc(bX & lt);
+                        xk[o] = (KX)(shl(t, L.bug) | u);
+                        xv[o] = val;
+                    }
+                }
+                oS += __popc(bS);
+                oG += __popc(bG);
+                oX += __popc(bX);
             }
         }
-        __syncthreads();
+        __syncthreads();   // every thread is done with this stage buffer
+        if (tid == 0) issue(k + 2);
     }
     __syncthreads();
     if (MODE == IN_VALIDATE) return;
@@ -254,6 +288,27 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
             const uint32_t gp = p < np_s ? L.p0_s + p : (p < np_s + np_g ? L.p0_g + (p - np_s) : L.p0_x + (p - np_s - np_g));
             atomicAdd(&hist[gp * RADIX + (i % RADIX)], c);
         }
+    }
+}
+
+// Tiles the fallback read must visit: those of hash-path traces holding a block
+// that the hash path does not take (or every tile of a trace whose blocks are
+// out of order). One thread per tile; the list order does not matter.
+__global__ void k_fallback_tiles(const TraceDesc *__restrict__ td, Layout L, const TState *ts,
+                                 const uint32_t *__restrict__ binel, Ctl *ctl, uint32_t *list) {
+    for (uint64_t tile = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; tile < L.ntiles_in;
+         tile += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = trace_of_tile(td, L.T, tile);
+        const TraceDesc &d = td[t];
+        if (!d.hash_ok) continue;
+        bool fb = ts[t].inel != 0;
+        if (!fb) {
+            // blocks are in record order here: the tile covers blocks first..last
+            const uint64_t tbase = (tile - d.tile_off) * IN_TILE, last = min(tbase + IN_TILE, d.n) - 1;
+            const uint32_t b0 = min(d.events[tbase].z, d.nb - 1), b1 = min(d.events[last].z, d.nb - 1);
+            for (uint32_t b = b0; b <= b1 && !fb; b++) fb = binel[(uint64_t)d.block_off + b] != 0;
+        }
+        if (fb) list[atomicAdd(&ctl->n_fb, 1u)] = (uint32_t)tile;
     }
 }
 

@@ -72,6 +72,7 @@ struct Ctl {
     unsigned int n_races;         // staged race records (all traces)
     unsigned int n_div, n_red;    // divergent blocks / redundant barriers (all traces)
     unsigned int n_q;             // records in the schedule-rank sort (unsorted traces)
+    unsigned int n_fb;            // tiles listed for the fallback read
     unsigned int tiles[MAX_PASSES];  // onesweep tile counters, one per pass
 };
 
@@ -94,6 +95,7 @@ struct Layout {
     uint64_t race_cap;               // staging capacity for race records
     uint64_t status_tiles;           // tiles covered by the look-back status array
     size_t off_binel;                // per batch-wide block: the hash path does not apply to it
+    size_t off_fbt;                  // tiles for the fallback read
     size_t off_ctl, off_td, off_ts, off_tob, off_stats, off_nonred, off_gridnr, off_gridhas, off_cnt_div,
         off_cnt_red, off_ofs_div, off_ofs_red, off_hist, off_dbase, off_status, off_rank, off_p2v, off_runs;
     size_t off_sk[2], off_sv[2], off_gk[2], off_gv[2], off_xk[2], off_xv[2];
@@ -112,6 +114,45 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+// ---- 1-D bulk copies (TMA) into shared memory, completed on an mbarrier --------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make barrier initialisation visible to the async proxy
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// order earlier generic-proxy accesses of shared memory before later async-proxy writes
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// wait for phase `parity` of a barrier, giving up after limit_ns of wall time
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t i = 0;; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63) == 63 && globaltimer_ns() - t0 > limit_ns) return false;
+    }
 }
 
 // stop work that depends on sorted data: a wait gave up

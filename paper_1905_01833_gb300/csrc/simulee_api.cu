@@ -16,9 +16,11 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <stddef.h>
 
 #include <algorithm>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "../../include/simulee.h"
@@ -36,6 +38,7 @@ struct simulee_ctx {
     uint32_t last_launches;
     cudaEvent_t stage_ev[2 * SIMULEE_STAGES];
     bool stage_on;
+    std::vector<const void *> attr_fns;   // kernels whose shared-memory attribute is set
 };
 
 namespace {
@@ -137,6 +140,7 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, Layout &L) {
     L.off_hist = take((size_t)MAX_PASSES * RADIX * 4);
     L.off_binel = take((size_t)L.NB * 4);
     L.zero_end = o;
+    L.off_fbt = take((size_t)std::max<uint64_t>(L.ntiles_in, 1) * 4);
     L.off_td = take((size_t)T * sizeof(TraceDesc));
     L.off_tob = take((size_t)L.NB * 4);
     L.off_stats = take((size_t)L.NB * 16);
@@ -181,6 +185,17 @@ void set_reduce_attr() {
                          (int)reduce_groups_smem<K, INTER>());
 }
 
+// one-time opt-in to large dynamic shared memory, per kernel instantiation and context
+template <class F>
+bool attr_done(simulee_ctx *ctx, F *fn) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const void *p : ctx->attr_fns)
+        if (p == (const void *)fn) return true;
+    ctx->attr_fns.push_back((const void *)fn);
+    return false;
+}
+
 struct Run {
     simulee_ctx *ctx;
     cudaStream_t st;
@@ -201,7 +216,7 @@ struct Run {
 
     int sort_grid(uint64_t n_max) const {
         const uint64_t tiles = (n_max + OS_TILE - 1) / OS_TILE;
-        return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)ctx->sms * 2));
+        return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)ctx->sms * 3));
     }
 
     // LSD sort of (key, value) pairs in buffers 0/1; returns the buffer holding the result.
@@ -362,6 +377,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     cudaMemsetAsync(R.ws + L.off_status, 0, (size_t)L.status_tiles * RADIX * 8, st);
     uint32_t *runs = any_hash ? R.at<uint32_t>(L.off_runs) : nullptr;
     uint32_t *binel = R.at<uint32_t>(L.off_binel);
+    uint32_t *fbt = R.at<uint32_t>(L.off_fbt);
     if (any_hash) cudaMemsetAsync(runs, 0, (size_t)L.NB * (L.maxb + 1) * 8, st);
     for (uint32_t i = 0; i < T; i += kDescChunk) {
         DescChunk c;
@@ -403,12 +419,17 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
         }
 
         // 4. ingest: first read; then, for hash-path traces found unsuitable, a fallback read
-        const int gi = R.grid_for(L.ntiles_in, 1, 4);
+        const int gi = R.grid_for(L.ntiles_in, 1, 2);
 #define SIM_INGEST(KS, KG, KX, MODE)                                                                                \
-    k_ingest<KS, KG, KX, MODE><<<gi, IN_THREADS, 0, st>>>(td, rank, L, ts, R.ctl, R.at<KS>(L.off_sk[0]),             \
-                                                          R.at<uint64_t>(L.off_sv[0]), R.at<KG>(L.off_gk[0]),        \
-                                                          R.at<uint64_t>(L.off_gv[0]), R.at<KX>(L.off_xk[0]),        \
-                                                          R.at<uint64_t>(L.off_xv[0]), hist, runs, binel)
+    do {                                                                                                            \
+        if (!attr_done(ctx, k_ingest<KS, KG, KX, MODE>))                                                            \
+            cudaFuncSetAttribute(k_ingest<KS, KG, KX, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,           \
+                                 (int)ingest_smem());                                                               \
+        k_ingest<KS, KG, KX, MODE><<<gi, IN_THREADS, ingest_smem(), st>>>(                                          \
+            td, rank, L, ts, R.ctl, R.at<KS>(L.off_sk[0]), R.at<uint64_t>(L.off_sv[0]), R.at<KG>(L.off_gk[0]),      \
+            R.at<uint64_t>(L.off_gv[0]), R.at<KX>(L.off_xk[0]), R.at<uint64_t>(L.off_xv[0]), hist, runs, binel,     \
+            fbt, R.wait_ns);                                                                                        \
+    } while (0)
 #define SIM_INGEST_W(MODE)                                                                                          \
     do {                                                                                                            \
         const int wmask = (L.wide_s ? 1 : 0) | (L.wide_g ? 2 : 0) | (L.wide_x ? 4 : 0);                             \
@@ -429,7 +450,8 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
             SIM_INGEST_W(IN_FIRST);
             if (any_hash) {
                 k_runs_check<<<R.grid_for((uint64_t)L.NB * (L.maxb + 1), 256, 8), 256, 0, st>>>(td, tob, runs, L, binel);
-                R.launches++;
+                k_fallback_tiles<<<R.grid_for(L.ntiles_in, 256, 8), 256, 0, st>>>(td, L, ts, binel, R.ctl, fbt);
+                R.launches += 2;
                 SIM_INGEST_W(IN_FALLBACK);
             }
         }
@@ -563,7 +585,7 @@ simulee_status simulee_create(simulee_ctx **ctx, int device, const simulee_optio
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SIMULEE_ECUDA;
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return SIMULEE_ECUDA;
-    simulee_ctx *c = (simulee_ctx *)calloc(1, sizeof(simulee_ctx));
+    simulee_ctx *c = new (std::nothrow) simulee_ctx();
     if (!c) return SIMULEE_ENOMEM;
     c->device = device;
     c->sms = prop.multiProcessorCount;
@@ -574,7 +596,7 @@ simulee_status simulee_create(simulee_ctx **ctx, int device, const simulee_optio
 
 simulee_status simulee_destroy(simulee_ctx *ctx) {
     if (!ctx) return SIMULEE_EINVAL;
-    free(ctx);
+    delete ctx;
     return SIMULEE_OK;
 }
 
@@ -643,6 +665,14 @@ simulee_status simulee_check_batch(simulee_ctx *ctx, const simulee_trace *traces
 }
 
 uint32_t simulee_last_launches(const simulee_ctx *ctx) { return ctx ? ctx->last_launches : 0u; }
+
+simulee_status simulee_stream_sizes(simulee_ctx *ctx, const void *ws, uint32_t *dev_out, void *stream) {
+    if (!ctx || !ws || !dev_out) return SIMULEE_EINVAL;
+    static_assert(offsetof(Ctl, n_races) == offsetof(Ctl, n_s) + 12, "stream counters are contiguous");
+    const cudaError_t e = cudaMemcpyAsync(dev_out, (const uint8_t *)ws + offsetof(Ctl, n_s), 16,
+                                          cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIMULEE_OK : SIMULEE_ECUDA;
+}
 
 simulee_status simulee_set_stage_events(simulee_ctx *ctx, void *const *events, uint32_t n_events) {
     if (!ctx) return SIMULEE_EINVAL;

@@ -50,7 +50,7 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *wa
 }
 
 template <class K>
-__global__ void __launch_bounds__(OS_THREADS, 2)
+__global__ void __launch_bounds__(OS_THREADS, 3)
 k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__restrict__ kout,
            uint64_t *__restrict__ vout, const uint32_t *n_ptr, uint64_t n_max, uint32_t shift,
            const uint32_t *__restrict__ dbase, unsigned long long *status, uint32_t tag, uint32_t *tile_ctr,

@@ -84,6 +84,7 @@ def lib():
         }
         sigs["simulee_set_stage_events"] = [vp, P(vp), u32]
         sigs["simulee_check_noalloc"] = [vp, P(Trace), P(Outputs), vp, vp]
+        sigs["simulee_stream_sizes"] = [vp, vp, vp, vp]
         for name, args in sigs.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -178,6 +179,14 @@ class Checker:
             return
         arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
         _check(lib().simulee_set_stage_events(self.h, arr, len(events)), "simulee_set_stage_events")
+
+    def stream_sizes(self, stream=None) -> dict:
+        """Record counts that the last check on this checker's workspace sent through the radix sort."""
+        out = self.torch.zeros(4, dtype=self.torch.int32, device=f"cuda:{self.device}")
+        _check(lib().simulee_stream_sizes(self.h, ctypes.c_void_p(self._ws.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                          _stream_ptr(stream)), "simulee_stream_sizes")
+        v = [int(x) for x in out.cpu().tolist()]
+        return dict(n_s=v[0], n_g=v[1], n_x=v[2], n_races=v[3])
 
     def workspace_size(self, dt: DeviceTrace) -> int:
         n = ctypes.c_size_t()
