@@ -155,7 +155,10 @@ typedef struct {
     uint32_t path;            /* simulee_path */
     uint32_t test_withhold;   /* testing only: 0 = off; t+1 = tile t of the first sort pass never
                                  publishes its counts, so a later tile's bounded wait gives up */
-    uint32_t reserved[5];
+    uint32_t ingest_ctas_per_sm;   /* persistent CTAs per SM of the record reads; 0 = 2 */
+    uint32_t sort_ctas_per_sm;     /* persistent CTAs per SM of each radix pass; 0 = 3 */
+    uint32_t reduce_ctas_per_sm;   /* persistent CTAs per SM of the segmented reductions; 0 = 3 */
+    uint32_t reserved[2];
 } simulee_options;
 
 typedef struct simulee_ctx simulee_ctx;

@@ -99,8 +99,8 @@ __device__ __forceinline__ void hist_add(uint32_t *sh, uint64_t key, uint32_t np
 // tile is read twice from shared memory: once to validate and count, once to
 // write the routed elements at their stream positions.
 // ---------------------------------------------------------------------------
-constexpr int IN_THREADS = 256;
-constexpr int IN_ITEMS = 8;
+constexpr int IN_THREADS = 512;
+constexpr int IN_ITEMS = 4;
 constexpr int IN_TILE = IN_THREADS * IN_ITEMS;
 constexpr int IN_STAGE = IN_TILE + 1;   // records per stage buffer (one before the tile)
 constexpr int IN_MAXP = 24;   // S + G + X passes histogrammed here

@@ -27,8 +27,11 @@ constexpr int HB_PER_THREAD = HB_RUNMAX / HB_THREADS;
 constexpr uint32_t HB_EMPTY = 0xFFFFFFFFu;
 constexpr uint32_t HB_NO_OWNER = 0x7FFu;            // packed owner code: category absent
 
-// shared memory: keys of two epochs, first/second items per category, adjacency summaries
-constexpr size_t hash_blocks_smem() { return (size_t)HB_SLOTS * 4 * (2 + 3 + 3) + (size_t)HB_SLOTS * 8; }
+// shared memory: keys of two epochs, first/second items per category, adjacency summaries,
+// and the staging buffer that receives the next run's records
+constexpr size_t hash_blocks_smem() {
+    return (size_t)HB_SLOTS * 4 * (2 + 3 + 3) + (size_t)HB_SLOTS * 8 + (size_t)HB_RUNMAX * 16;
+}
 
 __device__ __forceinline__ uint32_t hb_hash(uint32_t key) { return (key * 0x9E3779B1u) >> (32 - 12); }
 
@@ -68,15 +71,22 @@ __device__ __forceinline__ uint64_t hb_item64(uint32_t v) {
 __global__ void __launch_bounds__(HB_THREADS, 1)
 k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob, const uint4 *__restrict__ stats,
               const uint32_t *__restrict__ runs, const uint32_t *__restrict__ binel, Layout L, TState *ts, Ctl *ctl,
-              uint32_t *nonred, RaceStage rs) {
-    extern __shared__ __align__(16) uint32_t hb_smem[];
-    uint32_t *hkey = hb_smem;                          // [2][HB_SLOTS]
-    uint32_t *hfirst = hkey + 2 * HB_SLOTS;            // [3][HB_SLOTS]
-    uint32_t *hsecond = hfirst + 3 * HB_SLOTS;         // [3][HB_SLOTS]
-    uint2 *hadj = reinterpret_cast<uint2 *>(hsecond + 3 * HB_SLOTS);   // [HB_SLOTS]
+              uint32_t *nonred, RaceStage rs, uint64_t wait_ns) {
+    extern __shared__ __align__(128) uint32_t hb_smem[];
+    uint4 *hrec = reinterpret_cast<uint4 *>(hb_smem);                      // [HB_RUNMAX] staged records
+    uint32_t *hkey = hb_smem + HB_RUNMAX * 4;                              // [2][HB_SLOTS]
+    uint32_t *hfirst = hkey + 2 * HB_SLOTS;                                // [3][HB_SLOTS]
+    uint32_t *hsecond = hfirst + 3 * HB_SLOTS;                             // [3][HB_SLOTS]
+    uint2 *hadj = reinterpret_cast<uint2 *>(hsecond + 3 * HB_SLOTS);       // [HB_SLOTS]
+    __shared__ uint64_t bar;
     const int tid = threadIdx.x;
-    for (int i = tid; i < 8 * HB_SLOTS; i += HB_THREADS) hb_smem[i] = HB_EMPTY;
+    for (int i = tid; i < 8 * HB_SLOTS; i += HB_THREADS) hkey[i] = HB_EMPTY;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
     __syncthreads();
+    uint32_t phase = 0;   // completed copies into hrec, mod 2 (same value in every thread)
     const OwnThread own;
     for (uint64_t b = blockIdx.x; b < L.NB; b += gridDim.x) {
         const uint32_t t = tob[b];
@@ -90,20 +100,50 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         uint32_t mine_prev[HB_PER_THREAD], mine[HB_PER_THREAD];
 #pragma unroll
         for (int j = 0; j < HB_PER_THREAD; j++) mine_prev[j] = HB_EMPTY;
+        const uint64_t rbase = 2 * (uint64_t)b * (L.maxb + 1);
+        // run bounds of epoch e of this block (empty when out of range)
+        auto run_of = [&](uint32_t e, uint32_t &rs_, uint32_t &m_) {
+            rs_ = 0;
+            m_ = 0;
+            if (e > maxc) return;
+            const uint32_t a = runs[rbase + 2 * e], z = runs[rbase + 2 * e + 1];
+            rs_ = a;
+            m_ = (z > a) ? min(z - a, (uint32_t)HB_RUNMAX) : 0u;
+        };
+        // thread 0: start the copy of a run's records into hrec (hrec is free)
+        auto prefetch = [&](uint32_t rs_, uint32_t m_) {
+            if (m_ == 0) return;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bar, m_ * 16u);
+            bulk_g2s(hrec, d.events + rs_, m_ * 16u, &bar);
+        };
+        uint32_t rs0, m;
+        run_of(0, rs0, m);
+        if (tid == 0) prefetch(rs0, m);
         for (uint32_t e = 0; e <= maxc; e++) {
-            const uint64_t ri = 2 * ((uint64_t)b * (L.maxb + 1) + e);
-            const uint32_t rs0 = runs[ri], re0 = runs[ri + 1];
-            const uint32_t m = (re0 > rs0) ? min(re0 - rs0, (uint32_t)HB_RUNMAX) : 0u;
             uint32_t *key = hkey + cur * HB_SLOTS;
             const uint32_t *pkey = hkey + (cur ^ 1) * HB_SLOTS;
             uint32_t slot[HB_PER_THREAD], item[HB_PER_THREAD], cat[HB_PER_THREAD];
+            if (m > 0) {
+                const bool arrived = __syncthreads_and(mbar_wait(&bar, phase, wait_ns));
+                if (!arrived) {
+                    if (tid == 0) {
+                        atomicExch(&ctl->timeout, 1u);
+                        mbar_wait(&bar, phase, wait_ns);   // bounded: let the copy in flight land
+                    }
+                    return;
+                }
+                phase ^= 1u;
+            }
+            uint32_t rs1, m1;   // the next epoch's run
+            run_of(e + 1, rs1, m1);
             // 1. insert this run's units; remember the slots this thread creates
 #pragma unroll
             for (int j = 0; j < HB_PER_THREAD; j++) {
                 mine[j] = HB_EMPTY;
                 slot[j] = HB_EMPTY;
                 const uint32_t r = tid + j * HB_THREADS;
-                const uint4 ev = r < m ? d.events[rs0 + r] : make_uint4(0, 0, 0, 0x30000000u);
+                const uint4 ev = r < m ? hrec[r] : make_uint4(0, 0, 0, 0x30000000u);
                 const uint32_t sp = (ev.w >> 30) & 1u;
                 // fields were validated by the ingest; the check keeps shared memory safe regardless
                 if (r < m && ((ev.w >> 28) & 3u) != 3u && ev.x < (sp ? d.gu : d.su)) {
@@ -125,6 +165,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                 }
             }
             __syncthreads();
+            if (tid == 0) prefetch(rs1, m1);   // every thread is done with hrec
             // 2. earliest item per slot and category, then the earliest of another thread
 #pragma unroll
             for (int j = 0; j < HB_PER_THREAD; j++)
@@ -200,6 +241,8 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             __syncthreads();
             prev_live = m > 0;
             cur ^= 1;
+            rs0 = rs1;
+            m = m1;
         }
         // release the last epoch's keys before the next block
 #pragma unroll

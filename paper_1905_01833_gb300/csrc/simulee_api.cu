@@ -216,7 +216,8 @@ struct Run {
 
     int sort_grid(uint64_t n_max) const {
         const uint64_t tiles = (n_max + OS_TILE - 1) / OS_TILE;
-        return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)ctx->sms * 3));
+        const uint64_t per_sm = ctx->opt.sort_ctas_per_sm ? ctx->opt.sort_ctas_per_sm : 3u;
+        return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)ctx->sms * per_sm));
     }
 
     // LSD sort of (key, value) pairs in buffers 0/1; returns the buffer holding the result.
@@ -419,7 +420,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
         }
 
         // 4. ingest: first read; then, for hash-path traces found unsuitable, a fallback read
-        const int gi = R.grid_for(L.ntiles_in, 1, 2);
+        const int gi = R.grid_for(L.ntiles_in, 1, ctx->opt.ingest_ctas_per_sm ? ctx->opt.ingest_ctas_per_sm : 2u);
 #define SIM_INGEST(KS, KG, KX, MODE)                                                                                \
     do {                                                                                                            \
         if (!attr_done(ctx, k_ingest<KS, KG, KX, MODE>))                                                            \
@@ -493,7 +494,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     rs.td = td;
     uint32_t *nonred = R.at<uint32_t>(L.off_nonred);
     if (sorting) {
-        const int gr = R.grid_for(L.n, RG_TILE, 3);
+        const int gr = R.grid_for(L.n, RG_TILE, ctx->opt.reduce_ctas_per_sm ? ctx->opt.reduce_ctas_per_sm : 3u);
 #define SIM_REDUCE(K, INTER, KOFF, VOFF, NPTR, SPACE, BU)                                                             \
     k_reduce_groups<K, INTER><<<gr, RG_THREADS, reduce_groups_smem<K, INTER>(), st>>>(                                \
         R.at<K>(KOFF), R.at<uint64_t>(VOFF), NPTR, L, td, tob, SPACE, BU, R.ctl, nonred, rs)
@@ -512,7 +513,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     R.mark(SIMULEE_STAGE_HASH, 0);
     if (sorting && any_hash) {
         k_hash_blocks<<<std::max(1, std::min<int>(ctx->sms, (int)L.NB)), HB_THREADS, hash_blocks_smem(), st>>>(
-            td, tob, R.at<uint4>(L.off_stats), runs, binel, L, ts, R.ctl, nonred, rs);
+            td, tob, R.at<uint4>(L.off_stats), runs, binel, L, ts, R.ctl, nonred, rs, R.wait_ns);
         R.launches++;
     }
     R.mark(SIMULEE_STAGE_HASH, 1);

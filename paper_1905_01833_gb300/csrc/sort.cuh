@@ -89,8 +89,18 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
 #pragma unroll
         for (int j = 0; j < OS_ITEMS; j++) {
             const uint32_t li = w * (32 * OS_ITEMS) + j * 32 + lane;
-            const uint32_t d = li < nvalid ? (uint32_t)((k[j] >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
-            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+            const bool valid = li < nvalid;
+            const uint32_t d = valid ? (uint32_t)((k[j] >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
+            // lanes holding the same digit: one ballot per digit bit (warp multi-split)
+            const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
+            uint32_t peers = vmask;
+#pragma unroll
+            for (int bit = 0; bit < RADIX_BITS; bit++) {
+                const uint32_t on = (d >> bit) & 1u;
+                const uint32_t m = __ballot_sync(0xFFFFFFFFu, on);
+                peers &= on ? m : ~m;
+            }
+            if (!valid) peers = ~vmask;
             const uint32_t cnt = whist[w][d];
             __syncwarp();
             if ((peers & lt) == 0) whist[w][d] = cnt + __popc(peers);

@@ -55,7 +55,8 @@ class Report(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("wait_limit_us", ctypes.c_uint32), ("path", ctypes.c_uint32), ("test_withhold", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32 * 5)]
+                ("ingest_ctas_per_sm", ctypes.c_uint32), ("sort_ctas_per_sm", ctypes.c_uint32),
+                ("reduce_ctas_per_sm", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
 
 
 REPORT_BYTES = ctypes.sizeof(Report)
@@ -146,11 +147,12 @@ def _stream_ptr(stream):
 class Checker:
     """A library context on one GPU plus reusable device buffers."""
 
-    def __init__(self, device: int = 0, wait_limit_us: int = 0, path: int = PATH_AUTO, test_withhold: int = 0):
+    def __init__(self, device: int = 0, wait_limit_us: int = 0, path: int = PATH_AUTO, test_withhold: int = 0,
+                 ingest_ctas_per_sm: int = 0, sort_ctas_per_sm: int = 0, reduce_ctas_per_sm: int = 0):
         import torch
         self.device = device
         self.torch = torch
-        opt = Options(wait_limit_us, path, test_withhold)
+        opt = Options(wait_limit_us, path, test_withhold, ingest_ctas_per_sm, sort_ctas_per_sm, reduce_ctas_per_sm)
         h = ctypes.c_void_p()
         _check(lib().simulee_create(ctypes.byref(h), device, ctypes.byref(opt)), "simulee_create")
         self.h = h
