@@ -116,26 +116,41 @@ def bits(count):
     return b
 
 
+def sig_slots(tr):
+    """Entries of the block-signature table that every check clears (one trace: one per global unit)."""
+    if tr.global_units == 0:
+        return 0
+    if tr.global_units <= (1 << 28):
+        return tr.global_units
+    m = 1 << 16
+    while m < tr.n_events and m < (1 << 28):
+        m <<= 1
+    return m
+
+
 def stage_bytes(tr, sizes):
     """Algorithmic DRAM bytes of each stage for the plan that ran (stream sizes from the library).
 
-    ingest: one 16-byte read per record, the barrier counts, the inter-block
-    stream writes (4-byte key + 8-byte payload per global record), the sort-path
+    ingest: clearing the block-signature table, one 16-byte read per record, the barrier counts, the inter-block
+    stream writes (4-byte key + 8-byte payload per global record) and one
+    read-modify-write of its unit's 4-byte block signature, the sort-path
     stream writes, and the re-read of records routed by the fallback read.
-    sort: each radix pass reads and writes key + payload of its stream.
-    reduce: one read of every sorted stream. hash: one 16-byte read of every
-    record the short-interval path checks."""
+    sort: the inter-block filter (read every inter-block element, write the
+    kept ones), then each radix pass reads and writes key + payload of its
+    stream. reduce: one read of every sorted stream. hash: one 16-byte read of
+    every record the short-interval path checks."""
     n = tr.n_events
-    n_s, n_g, n_x = sizes["n_s"], sizes["n_g"], sizes["n_x"]
+    n_s, n_g, n_x, n_gl = sizes["n_s"], sizes["n_g"], sizes["n_x"], sizes["n_global"]
     bb, bus, bug, be = bits(tr.n_blocks), bits(tr.shared_units), bits(tr.global_units), bits(tr.max_barriers + 1)
     ks = 8 if bb + bus + be > 32 else 4
     kg = 8 if bb + bug + be > 32 else 4
     kx = 8 if bug > 32 else 4
     np_s, np_g, np_x = -(-(bb + bus + be) // 8), -(-(bb + bug + be) // 8), -(-bug // 8)
     return dict(
-        ingest=16 * n + 4 * tr.barrier_counts.size + n_x * (kx + 8) + n_s * (ks + 8) + n_g * (kg + 8)
-        + 16 * (n_s + n_g),
-        sort=2 * (n_s * np_s * (ks + 8) + n_g * np_g * (kg + 8) + n_x * np_x * (kx + 8)),
+        ingest=16 * n + 4 * tr.barrier_counts.size + n_gl * (kx + 8 + 8) + n_s * (ks + 8) + n_g * (kg + 8)
+        + 16 * (n_s + n_g) + 4 * sig_slots(tr),
+        sort=n_gl * (kx + 8) + n_x * (kx + 8)
+        + 2 * (n_s * np_s * (ks + 8) + n_g * np_g * (kg + 8) + n_x * np_x * (kx + 8)),
         reduce=n_s * (ks + 8) + n_g * (kg + 8) + n_x * (kx + 8),
         hash=16 * (n - n_s - n_g),
         launches=dict(ingest=2, sort=np_s + np_g + np_x, reduce=3, hash=1))
@@ -197,6 +212,22 @@ def reference_arm(args, rank: int, world: int):
         "config": {"workload": WORKLOAD, "n_events_per_step": n},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def job_value(events_this_rank: int, ms_this_rank: float, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: all ranks' records over the slowest rank's time.
+
+    Returns (Gev/s, max ms). With torch.distributed initialised (NCCL on the GPU machine, gloo in the
+    CPU tests) the time is the max over ranks and the records are summed over ranks."""
+    ms, total = float(ms_this_rank), float(events_this_rank)
+    if dist is not None and dist.is_initialized():
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        n = torch.tensor([total], dtype=torch.float64, device=device)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        ms, total = float(t.item()), float(n.item())
+    return total / (ms * 1e-3) / 1e9, ms
 
 
 def device_pool(torch, trs, dev):
@@ -445,11 +476,7 @@ def main():
     rep = simulee.Report.from_buffer_copy(report_dev.cpu().numpy().tobytes())
     assert rep.status == 0 and rep.n_races == rep0.n_races and rep.n_redundant == rep0.n_redundant
 
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = tr.n_events * world / (ms * 1e-3) / 1e9
+    value, ms = job_value(tr.n_events, ms, dist, f"cuda:{local}")
 
     # end to end through the C ABI: pinned host trace -> device, check, report and lists -> host
     h_ev = torch.from_numpy(tr.events.view(np.int32)).pin_memory()
@@ -490,10 +517,7 @@ def main():
     for _ in range(args.e2e_steps):
         e2e_step()
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_value, _ = job_value(tr.n_events, e2e_s * 1e3, dist, f"cuda:{local}")
     h2d = tr.events.nbytes + tr.barrier_counts.nbytes
 
     # roofline of the dominant stage
@@ -518,7 +542,7 @@ def main():
         "config": {"workload": WORKLOAD if args.blocks == 1024 else WORKLOAD.replace("1024 blocks", f"{args.blocks} blocks"),
                    "n_events": tr.n_events, "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (1 GB trace, 129 MB L2); no flush", "path": args.path},
-        "e2e": {"value": tr.n_events * world / e2e_s / 1e9, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches * args.steps,
         "roofline": roofline,

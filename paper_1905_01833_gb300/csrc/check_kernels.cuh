@@ -78,6 +78,30 @@ __device__ __forceinline__ void hist_add(uint32_t *sh, uint64_t key, uint32_t np
 }
 
 // ---------------------------------------------------------------------------
+// Block signatures of global units. An inter-block race needs a unit touched
+// by two different blocks. While ingesting, each global record marks its
+// unit's slot with its (batch-wide) block + 1, and with SIG_MULTI when the
+// slot already holds another block. Inter-block records whose slot never got
+// SIG_MULTI touch a unit of one block only and are dropped before sorting.
+// With several traces the slot is a hash of (trace, unit); a collision can
+// only keep extra records, never drop a needed one.
+// ---------------------------------------------------------------------------
+constexpr uint32_t SIG_MULTI = 0x80000000u;
+
+__device__ __forceinline__ uint64_t sig_slot(const Layout &L, uint32_t t, uint32_t unit) {
+    if (L.sig_direct) return unit;
+    return (mix32((t * 0x9E3779B1u) ^ unit) ^ ((uint64_t)t << 7)) & (L.sig_slots - 1);
+}
+
+__device__ __forceinline__ void sig_mark(uint32_t *sig, uint64_t slot, uint32_t block) {
+    const uint32_t me = block + 1u;
+    uint32_t cur = *(volatile uint32_t *)&sig[slot];
+    if (cur == me || (cur & SIG_MULTI)) return;
+    if (cur == 0u) cur = atomicCAS(&sig[slot], 0u, me);
+    if (cur != 0u && cur != me && !(cur & SIG_MULTI)) atomicOr(&sig[slot], SIG_MULTI);
+}
+
+// ---------------------------------------------------------------------------
 // Ingest, in up to two reads of the records.
 //
 // First read (IN_FIRST): validate every record; route global records to the
@@ -112,7 +136,7 @@ template <class KS, class KG, class KX, int MODE>
 __global__ void __launch_bounds__(IN_THREADS)
 k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, Layout L, TState *ts, Ctl *ctl,
          KS *sk, uint64_t *sv, KG *gk, uint64_t *gv, KX *xk, uint64_t *xv, uint32_t *hist, uint32_t *runs,
-         uint32_t *binel, const uint32_t *__restrict__ tile_list, uint64_t wait_ns) {
+         uint32_t *binel, const uint32_t *__restrict__ tile_list, uint32_t *sig, uint64_t wait_ns) {
     extern __shared__ __align__(128) uint4 in_stage[];   // [2][IN_STAGE]
     __shared__ uint64_t bars[2];
     __shared__ uint32_t sh[IN_MAXP * RADIX];
@@ -120,8 +144,8 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
     __shared__ uint32_t cbase[3];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint32_t lt = lanemask_lt();
-    const uint32_t np_s = L.np_s, np_g = L.np_g, np_x = L.np_x;
-    uint32_t *hs = sh, *hg = sh + np_s * RADIX, *hx = hg + np_g * RADIX;
+    const uint32_t np_s = L.np_s, np_g = L.np_g;
+    uint32_t *hs = sh, *hg = sh + np_s * RADIX;
     for (int i = tid; i < IN_MAXP * RADIX; i += IN_THREADS) sh[i] = 0;
     const uint64_t ntiles = (MODE == IN_FALLBACK) ? (uint64_t)*(volatile unsigned int *)&ctl->n_fb : L.ntiles_in;
     if (tid == 0) {
@@ -218,9 +242,9 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
             route |= ((isS ? 1u : 0u) << j) | ((isG ? 1u : 0u) << (8 + j)) | ((isX ? 1u : 0u) << (16 + j));
             if (MODE != IN_VALIDATE) {
                 const uint64_t sb = (uint64_t)d.block_off + blk;
-                hist_add(hs, shl(sb, L.bus + L.be) | shl(u, L.be) | ep, np_s, isS, bS);
-                hist_add(hg, shl(sb, L.bug + L.be) | shl(u, L.be) | ep, np_g, isG, bG);
-                hist_add(hx, shl(t, L.bug) | u, np_x, isX, bX);
+                if (bS) hist_add(hs, shl(sb, L.bus + L.be) | shl(u, L.be) | ep, np_s, isS, bS);
+                if (bG) hist_add(hg, shl(sb, L.bug + L.be) | shl(u, L.be) | ep, np_g, isG, bG);
+                if (isX) sig_mark(sig, sig_slot(L, t, u), (uint32_t)sb);
             }
         }
         if (MODE != IN_VALIDATE) {
@@ -265,9 +289,12 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
                         gv[o] = val;
                     }
                     if (isX) {
+                        // inter-block payload: owner code block << 10 | tid (a shift gives the block)
+                        // when blocks fit 20 bits, else the thread id
+                        const uint32_t xo = d.nb <= (1u << 20) ? ((blk << 10) | (w3 & 0x3FFu)) : blk * d.bt + (w3 & 0xFFFFu);
                         const uint32_t o = oX + __popc(bX & lt);
                         xk[o] = (KX)(shl(t, L.bug) | u);
-                        xv[o] = val;
+                        xv[o] = make_payload(act, xo, pos);
                     }
                 }
                 oS += __popc(bS);
@@ -280,12 +307,12 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
     }
     __syncthreads();
     if (MODE == IN_VALIDATE) return;
-    const uint32_t tot = (np_s + np_g + np_x) * RADIX;
+    const uint32_t tot = (np_s + np_g) * RADIX;   // the inter stream is histogrammed by its filter
     for (uint32_t i = tid; i < tot; i += IN_THREADS) {
         const uint32_t c = sh[i];
         if (c) {
             const uint32_t p = i / RADIX;
-            const uint32_t gp = p < np_s ? L.p0_s + p : (p < np_s + np_g ? L.p0_g + (p - np_s) : L.p0_x + (p - np_s - np_g));
+            const uint32_t gp = p < np_s ? L.p0_s + p : L.p0_g + (p - np_s);
             atomicAdd(&hist[gp * RADIX + (i % RADIX)], c);
         }
     }
@@ -310,6 +337,50 @@ __global__ void k_fallback_tiles(const TraceDesc *__restrict__ td, Layout L, con
         }
         if (fb) list[atomicAdd(&ctl->n_fb, 1u)] = (uint32_t)tile;
     }
+}
+
+// Keep the inter-block records whose unit was touched by two or more blocks;
+// build the digit histograms of the records kept. The order of kept records
+// does not matter (the sort that follows groups them by unit).
+template <class KX>
+__global__ void __launch_bounds__(256)
+k_x_filter(const KX *__restrict__ xk, const uint64_t *__restrict__ xv, KX *yk, uint64_t *yv, const uint32_t *sig,
+           Layout L, Ctl *ctl, uint32_t *hist) {
+    __shared__ uint32_t sh[8 * RADIX];
+    __shared__ uint32_t wsum[8];
+    __shared__ uint32_t s_base;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 8 * RADIX; i += 256) sh[i] = 0;
+    __syncthreads();
+    const uint64_t n = *(volatile unsigned int *)&ctl->n_x;
+    const uint64_t umask = (L.bug >= 64) ? ~0ull : ((1ull << L.bug) - 1);
+    for (uint64_t base = (uint64_t)blockIdx.x * 256; base < n; base += (uint64_t)gridDim.x * 256) {
+        const uint64_t i = base + tid;
+        bool keep = false;
+        KX k = 0;
+        uint64_t v = 0;
+        if (i < n) {
+            k = xk[i];
+            const uint64_t kk = (uint64_t)k;
+            const uint32_t t = (uint32_t)(L.bug >= 64 ? 0 : (kk >> L.bug)), unit = (uint32_t)(kk & umask);
+            keep = (sig[sig_slot(L, t, unit)] & SIG_MULTI) != 0;
+            if (keep) {
+                v = xv[i];
+                for (uint32_t q = 0; q < L.np_x; q++) atomicAdd(&sh[q * RADIX + digit_of(kk, q)], 1u);
+            }
+        }
+        const uint32_t pre = block_excl_scan_256(keep ? 1u : 0u, wsum);
+        if (tid == 255) s_base = atomicAdd(&ctl->n_xf, pre + (keep ? 1u : 0u));
+        __syncthreads();
+        if (keep) {
+            yk[s_base + pre] = k;
+            yv[s_base + pre] = v;
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int i = tid; i < (int)(L.np_x * RADIX); i += 256)
+        if (sh[i]) atomicAdd(&hist[(L.p0_x + i / RADIX) * RADIX + (i % RADIX)], sh[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -489,13 +560,15 @@ k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, c
             const uint32_t st = shead[g];
             const K kg = skey[st];
             uint32_t trace, bt = 1;
+            bool pad = false;
             if (INTER) {
                 trace = (uint32_t)((uint64_t)kg >> L.bug);
                 bt = td[trace].bt;
+                pad = td[trace].nb <= (1u << 20);
             } else {
                 trace = tob[(uint64_t)kg >> (bu + be)];
             }
-            const OwnBlock own_b{bt};
+            const OwnBlock own_b{bt, pad};
             Top2 S;
             S.clear();
             uint64_t cnt = 0;
@@ -522,8 +595,18 @@ k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, c
                 e = j;
             }
             if (INTER) {
-                if (cnt >= 2)
-                    emit_group(L, rs, ctl, S, own_b, trace, 1u, 1u, 0u, 0u, (uint32_t)((uint64_t)kg & umask));
+                if (cnt >= 2) {
+                    const uint32_t unit = (uint32_t)((uint64_t)kg & umask);
+#pragma unroll
+                    for (int cls = 0; cls < 2; cls++) {
+                        uint64_t p, q;
+                        if (!lowest_pair(S, cls, own_b, p, q)) continue;
+                        // owner codes back to block * block_threads + tid
+                        p = (p & ~0xFFFFFFFFull) | own_b.gtid((uint32_t)p);
+                        q = (q & ~0xFFFFFFFFull) | own_b.gtid((uint32_t)q);
+                        emit_race(rs, ctl, trace, race_key(L, trace, 1u, 1u, 0u, 0u, unit, cls), p, q);
+                    }
+                }
             } else {
                 const uint64_t sk = (uint64_t)kg >> be;
                 const uint32_t block = (uint32_t)(sk >> bu), unit = (uint32_t)(sk & umask);

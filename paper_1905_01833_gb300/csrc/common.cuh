@@ -68,8 +68,10 @@ struct TState {
 // Device control block at the start of the workspace; zeroed by every call.
 struct Ctl {
     unsigned int timeout;         // a bounded wait gave up
-    unsigned int n_s, n_g, n_x;   // shared-intra, global-intra and global-inter stream sizes
+    unsigned int n_s, n_g;        // shared-intra and global-intra stream sizes
+    unsigned int n_xf;            // inter-block records left by the block-signature filter
     unsigned int n_races;         // staged race records (all traces)
+    unsigned int n_x;             // inter-block records written by the ingest
     unsigned int n_div, n_red;    // divergent blocks / redundant barriers (all traces)
     unsigned int n_q;             // records in the schedule-rank sort (unsorted traces)
     unsigned int n_fb;            // tiles listed for the fallback read
@@ -96,6 +98,9 @@ struct Layout {
     uint64_t status_tiles;           // tiles covered by the look-back status array
     size_t off_binel;                // per batch-wide block: the hash path does not apply to it
     size_t off_fbt;                  // tiles for the fallback read
+    size_t off_sig;                  // block signature per global unit (or unit hash)
+    uint64_t sig_slots;              // entries of the signature table (0: no global memory)
+    uint32_t sig_direct;             // one trace: the table is indexed by unit itself
     size_t off_ctl, off_td, off_ts, off_tob, off_stats, off_nonred, off_gridnr, off_gridhas, off_cnt_div,
         off_cnt_red, off_ofs_div, off_ofs_red, off_hist, off_dbase, off_status, off_rank, off_p2v, off_runs;
     size_t off_sk[2], off_sv[2], off_gk[2], off_gv[2], off_xk[2], off_xv[2];
@@ -103,6 +108,16 @@ struct Layout {
     size_t zero_end;                 // bytes from the start that every call zeroes
     size_t total;
 };
+
+// 32-bit integer mixer (the finaliser of MurmurHash3)
+__device__ __forceinline__ uint32_t mix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
@@ -194,9 +209,18 @@ __device__ __forceinline__ uint32_t item_gtid(uint64_t x) { return (uint32_t)x; 
 struct OwnThread {
     __device__ __forceinline__ uint32_t operator()(uint64_t x) const { return (uint32_t)x; }
 };
+// Inter-block owners. The inter-block stream codes an access's thread as
+// block << 10 | tid when the trace's blocks fit 20 bits (pad), else as
+// block * block_threads + tid.
 struct OwnBlock {
     uint32_t bt;
-    __device__ __forceinline__ uint32_t operator()(uint64_t x) const { return (uint32_t)x / bt; }
+    bool pad;
+    __device__ __forceinline__ uint32_t operator()(uint64_t x) const {
+        return pad ? ((uint32_t)x >> 10) : (uint32_t)x / bt;
+    }
+    __device__ __forceinline__ uint32_t gtid(uint32_t code) const {
+        return pad ? (code >> 10) * bt + (code & 0x3FFu) : code;
+    }
 };
 
 struct Top2 {

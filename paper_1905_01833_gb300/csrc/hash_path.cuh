@@ -79,6 +79,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
     uint32_t *hsecond = hfirst + 3 * HB_SLOTS;                             // [3][HB_SLOTS]
     uint2 *hadj = reinterpret_cast<uint2 *>(hsecond + 3 * HB_SLOTS);       // [HB_SLOTS]
     __shared__ uint64_t bar;
+    __shared__ uint32_t s_needed;   // barrier e-1 already found needed in this epoch
     const int tid = threadIdx.x;
     for (int i = tid; i < 8 * HB_SLOTS; i += HB_THREADS) hkey[i] = HB_EMPTY;
     if (tid == 0) {
@@ -164,6 +165,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                     slot[j] = s;
                 }
             }
+            if (tid == 0) s_needed = 0u;
             __syncthreads();
             if (tid == 0) prefetch(rs1, m1);   // every thread is done with hrec
             // 2. earliest item per slot and category, then the earliest of another thread
@@ -209,13 +211,16 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                     }
                 }
                 adj[j] = hb_pack(S);
-                if (prev_live && !needed) {
+                if (prev_live && !needed && !*(volatile uint32_t *)&s_needed) {
                     uint32_t ps = hb_hash(k);
                     for (;;) {
                         const uint32_t pk = pkey[ps];
                         if (pk == HB_EMPTY) break;
                         if (pk == k) {
-                            if (hb_conflict(hadj[ps], adj[j])) needed = true;
+                            if (hb_conflict(hadj[ps], adj[j])) {
+                                needed = true;
+                                s_needed = 1u;
+                            }
                             break;
                         }
                         ps = (ps + 1) & (HB_SLOTS - 1);

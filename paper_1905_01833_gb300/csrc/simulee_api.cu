@@ -141,6 +141,19 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, Layout &L) {
     L.off_binel = take((size_t)L.NB * 4);
     L.zero_end = o;
     L.off_fbt = take((size_t)std::max<uint64_t>(L.ntiles_in, 1) * 4);
+    // block signatures of global units: indexed by unit for one trace with a modest global space,
+    // else by a hash of (trace, unit) into a power-of-two table about the size of the trace
+    if (gu > 0) {
+        if (T == 1 && gu <= (1u << 28)) {
+            L.sig_direct = 1;
+            L.sig_slots = gu;
+        } else {
+            uint64_t m = 1u << 16;
+            while (m < L.n && m < (1ull << 28)) m <<= 1;
+            L.sig_slots = m;
+        }
+        L.off_sig = take(L.sig_slots * 4);
+    }
     L.off_td = take((size_t)T * sizeof(TraceDesc));
     L.off_tob = take((size_t)L.NB * 4);
     L.off_stats = take((size_t)L.NB * 16);
@@ -220,12 +233,14 @@ struct Run {
         return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)ctx->sms * per_sm));
     }
 
-    // LSD sort of (key, value) pairs in buffers 0/1; returns the buffer holding the result.
+    // LSD sort of (key, value) pairs that start in buffer `start` of 0/1; returns the buffer
+    // holding the result.
     template <class K>
-    int sort(size_t koff[2], size_t voff[2], const uint32_t *n_ptr, uint64_t n_max, uint32_t np, uint32_t p0) {
+    int sort(size_t koff[2], size_t voff[2], const uint32_t *n_ptr, uint64_t n_max, uint32_t np, uint32_t p0,
+             int start = 0) {
         const int grid = sort_grid(n_max);
         for (uint32_t p = 0; p < np; p++) {
-            const int src = p & 1, dst = src ^ 1;
+            const int src = (start + (int)p) & 1, dst = src ^ 1;
             const uint32_t wh = first_pass_done ? 0u : withhold;
             first_pass_done = true;
             k_onesweep<K><<<grid, OS_THREADS, onesweep_smem<K>(), st>>>(
@@ -234,7 +249,7 @@ struct Run {
                 at<unsigned long long>(L.off_status), p0 + p + 1, &ctl->tiles[p0 + p], ctl, wait_ns, wh);
             launches++;
         }
-        return (int)(np & 1);
+        return (start + (int)np) & 1;
     }
 
     int grid_for(uint64_t items, uint64_t per_cta, uint64_t max_per_sm) const {
@@ -379,6 +394,8 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     uint32_t *runs = any_hash ? R.at<uint32_t>(L.off_runs) : nullptr;
     uint32_t *binel = R.at<uint32_t>(L.off_binel);
     uint32_t *fbt = R.at<uint32_t>(L.off_fbt);
+    uint32_t *sig = L.sig_slots ? R.at<uint32_t>(L.off_sig) : nullptr;
+    if (sig && (want.races || want.red)) cudaMemsetAsync(sig, 0, L.sig_slots * 4, st);
     if (any_hash) cudaMemsetAsync(runs, 0, (size_t)L.NB * (L.maxb + 1) * 8, st);
     for (uint32_t i = 0; i < T; i += kDescChunk) {
         DescChunk c;
@@ -429,7 +446,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
         k_ingest<KS, KG, KX, MODE><<<gi, IN_THREADS, ingest_smem(), st>>>(                                          \
             td, rank, L, ts, R.ctl, R.at<KS>(L.off_sk[0]), R.at<uint64_t>(L.off_sv[0]), R.at<KG>(L.off_gk[0]),      \
             R.at<uint64_t>(L.off_gv[0]), R.at<KX>(L.off_xk[0]), R.at<uint64_t>(L.off_xv[0]), hist, runs, binel,     \
-            fbt, R.wait_ns);                                                                                        \
+            fbt, sig, R.wait_ns);                                                                                   \
     } while (0)
 #define SIM_INGEST_W(MODE)                                                                                          \
     do {                                                                                                            \
@@ -465,19 +482,31 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     R.mark(SIMULEE_STAGE_SORT, 0);
     int bs = 0, bg = 0, bx = 0;
     if (sorting) {
+        size_t sk[2] = {L.off_sk[0], L.off_sk[1]}, sv[2] = {L.off_sv[0], L.off_sv[1]};
+        size_t gk[2] = {L.off_gk[0], L.off_gk[1]}, gv[2] = {L.off_gv[0], L.off_gv[1]};
+        size_t xk[2] = {L.off_xk[0], L.off_xk[1]}, xv[2] = {L.off_xv[0], L.off_xv[1]};
+        // inter-block records of units touched by one block only are dropped before sorting;
+        // the filter also builds the inter stream's digit histograms
+        if (L.sig_slots) {
+            const int gf = R.grid_for(L.n, 256, 8);
+            if (L.wide_x)
+                k_x_filter<uint64_t><<<gf, 256, 0, st>>>(R.at<uint64_t>(xk[0]), R.at<uint64_t>(xv[0]), R.at<uint64_t>(xk[1]),
+                                                         R.at<uint64_t>(xv[1]), sig, L, R.ctl, hist);
+            else
+                k_x_filter<uint32_t><<<gf, 256, 0, st>>>(R.at<uint32_t>(xk[0]), R.at<uint64_t>(xv[0]), R.at<uint32_t>(xk[1]),
+                                                         R.at<uint64_t>(xv[1]), sig, L, R.ctl, hist);
+            R.launches++;
+        }
         if (L.p0_r > 0) {
             k_digit_bases<<<L.p0_r, RADIX, 0, st>>>(hist, R.at<uint32_t>(L.off_dbase), R.ctl);
             R.launches++;
         }
-        size_t sk[2] = {L.off_sk[0], L.off_sk[1]}, sv[2] = {L.off_sv[0], L.off_sv[1]};
-        size_t gk[2] = {L.off_gk[0], L.off_gk[1]}, gv[2] = {L.off_gv[0], L.off_gv[1]};
-        size_t xk[2] = {L.off_xk[0], L.off_xk[1]}, xv[2] = {L.off_xv[0], L.off_xv[1]};
         bs = L.wide_s ? R.sort<uint64_t>(sk, sv, &R.ctl->n_s, L.n, L.np_s, L.p0_s)
                       : R.sort<uint32_t>(sk, sv, &R.ctl->n_s, L.n, L.np_s, L.p0_s);
         bg = L.wide_g ? R.sort<uint64_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g)
                       : R.sort<uint32_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g);
-        bx = L.wide_x ? R.sort<uint64_t>(xk, xv, &R.ctl->n_x, L.n, L.np_x, L.p0_x)
-                      : R.sort<uint32_t>(xk, xv, &R.ctl->n_x, L.n, L.np_x, L.p0_x);
+        bx = L.wide_x ? R.sort<uint64_t>(xk, xv, &R.ctl->n_xf, L.n, L.np_x, L.p0_x, 1)
+                      : R.sort<uint32_t>(xk, xv, &R.ctl->n_xf, L.n, L.np_x, L.p0_x, 1);
     }
     R.mark(SIMULEE_STAGE_SORT, 1);
 
@@ -502,8 +531,8 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
         else SIM_REDUCE(uint32_t, false, L.off_sk[bs], L.off_sv[bs], &R.ctl->n_s, 0u, L.bus);
         if (L.wide_g) SIM_REDUCE(uint64_t, false, L.off_gk[bg], L.off_gv[bg], &R.ctl->n_g, 1u, L.bug);
         else SIM_REDUCE(uint32_t, false, L.off_gk[bg], L.off_gv[bg], &R.ctl->n_g, 1u, L.bug);
-        if (L.wide_x) SIM_REDUCE(uint64_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_x, 1u, L.bug);
-        else SIM_REDUCE(uint32_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_x, 1u, L.bug);
+        if (L.wide_x) SIM_REDUCE(uint64_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_xf, 1u, L.bug);
+        else SIM_REDUCE(uint32_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_xf, 1u, L.bug);
 #undef SIM_REDUCE
         R.launches += 3;
     }
@@ -669,8 +698,8 @@ uint32_t simulee_last_launches(const simulee_ctx *ctx) { return ctx ? ctx->last_
 
 simulee_status simulee_stream_sizes(simulee_ctx *ctx, const void *ws, uint32_t *dev_out, void *stream) {
     if (!ctx || !ws || !dev_out) return SIMULEE_EINVAL;
-    static_assert(offsetof(Ctl, n_races) == offsetof(Ctl, n_s) + 12, "stream counters are contiguous");
-    const cudaError_t e = cudaMemcpyAsync(dev_out, (const uint8_t *)ws + offsetof(Ctl, n_s), 16,
+    static_assert(offsetof(Ctl, n_x) == offsetof(Ctl, n_s) + 16, "stream counters are contiguous");
+    const cudaError_t e = cudaMemcpyAsync(dev_out, (const uint8_t *)ws + offsetof(Ctl, n_s), 20,
                                           cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
     return e == cudaSuccess ? SIMULEE_OK : SIMULEE_ECUDA;
 }

@@ -184,11 +184,11 @@ class Checker:
 
     def stream_sizes(self, stream=None) -> dict:
         """Record counts that the last check on this checker's workspace sent through the radix sort."""
-        out = self.torch.zeros(4, dtype=self.torch.int32, device=f"cuda:{self.device}")
+        out = self.torch.zeros(5, dtype=self.torch.int32, device=f"cuda:{self.device}")
         _check(lib().simulee_stream_sizes(self.h, ctypes.c_void_p(self._ws.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                           _stream_ptr(stream)), "simulee_stream_sizes")
         v = [int(x) for x in out.cpu().tolist()]
-        return dict(n_s=v[0], n_g=v[1], n_x=v[2], n_races=v[3])
+        return dict(n_s=v[0], n_g=v[1], n_x=v[2], n_races=v[3], n_global=v[4])
 
     def workspace_size(self, dt: DeviceTrace) -> int:
         n = ctypes.c_size_t()
