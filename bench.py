@@ -128,17 +128,28 @@ def sig_slots(tr):
     return m
 
 
-def stage_bytes(tr, sizes):
+def distinct_global_units(tr) -> int:
+    """Global units the trace touches (each one's block signature is read and written once)."""
+    ev = tr.events.reshape(-1, 4)
+    g = ev[(ev[:, 3] >> 30) & 1 == 1, 0]
+    return int(np.unique(g).size) if g.size else 0
+
+
+def stage_bytes(tr, sizes, path: str, n_gunits: int):
     """Algorithmic DRAM bytes of each stage for the plan that ran (stream sizes from the library).
 
-    ingest: clearing the block-signature table, one 16-byte read per record, the barrier counts, the inter-block
-    stream writes (4-byte key + 8-byte payload per global record) and one
-    read-modify-write of its unit's 4-byte block signature, the sort-path
-    stream writes, and the re-read of records routed by the fallback read.
-    sort: the inter-block filter (read every inter-block element, write the
-    kept ones), then each radix pass reads and writes key + payload of its
-    stream. reduce: one read of every sorted stream. hash: one 16-byte read of
-    every record the short-interval path checks."""
+    Per record: one 16-byte read. Per global record: the inter-block stream
+    element it produces (key + 8-byte payload). Per touched global unit: one
+    read and one write of its 4-byte block signature; the signature table is
+    cleared once per check. Per routed intra-block element (sort path): its
+    key + 8-byte payload written, then read and written by every radix pass,
+    then read by the reduction, plus the 16-byte re-read of its record by the
+    fallback read (hash path only).
+    ingest: count statistics, the signature clear and, on the sort path, the
+    first read with all routing. hash: the single read of the hash path.
+    fallback: the re-read and routing of what the hash path spilled. sort: the
+    inter-block filter and the radix passes. reduce: one read of every sorted
+    stream."""
     n = tr.n_events
     n_s, n_g, n_x, n_gl = sizes["n_s"], sizes["n_g"], sizes["n_x"], sizes["n_global"]
     bb, bus, bug, be = bits(tr.n_blocks), bits(tr.shared_units), bits(tr.global_units), bits(tr.max_barriers + 1)
@@ -146,14 +157,17 @@ def stage_bytes(tr, sizes):
     kg = 8 if bb + bug + be > 32 else 4
     kx = 8 if bug > 32 else 4
     np_s, np_g, np_x = -(-(bb + bus + be) // 8), -(-(bb + bug + be) // 8), -(-bug // 8)
+    first = 16 * n + n_gl * (kx + 8) + 8 * n_gunits
+    routed = n_s * (ks + 8) + n_g * (kg + 8)
+    hashed = path != "sort"
     return dict(
-        ingest=16 * n + 4 * tr.barrier_counts.size + n_gl * (kx + 8 + 8) + n_s * (ks + 8) + n_g * (kg + 8)
-        + 16 * (n_s + n_g) + 4 * sig_slots(tr),
+        ingest=4 * tr.barrier_counts.size + 4 * sig_slots(tr) + (0 if hashed else first + routed),
+        hash=first if hashed else 0,
+        fallback=(16 * (n_s + n_g) + routed) if hashed else 0,
         sort=n_gl * (kx + 8) + n_x * (kx + 8)
         + 2 * (n_s * np_s * (ks + 8) + n_g * np_g * (kg + 8) + n_x * np_x * (kx + 8)),
         reduce=n_s * (ks + 8) + n_g * (kg + 8) + n_x * (kx + 8),
-        hash=16 * (n - n_s - n_g),
-        launches=dict(ingest=2, sort=np_s + np_g + np_x, reduce=3, hash=1))
+        launches=dict(ingest=1, hash=1, fallback=1, sort=np_s + np_g + np_x + 1, reduce=3))
 
 
 def kernel_traffic(kernel: str, workload: str):
@@ -522,11 +536,12 @@ def main():
 
     # roofline of the dominant stage
     sizes = chk.stream_sizes()
-    sb = stage_bytes(tr, sizes)
+    sb = stage_bytes(tr, sizes, args.path, distinct_global_units(tr))
     peak, peak_src = peaks()
-    cand = [k for k in ("ingest", "sort", "reduce", "hash") if sb[k] > 0]
+    cand = [k for k in ("ingest", "hash", "fallback", "sort", "reduce") if sb[k] > 0]
     dom = max(cand, key=lambda k: stage_ms[k])
-    kname = {"ingest": "k_ingest", "sort": "k_onesweep", "reduce": "k_reduce_groups", "hash": "k_hash_blocks"}[dom]
+    kname = {"ingest": "k_ingest", "hash": "k_hash_blocks", "fallback": "k_ingest", "sort": "k_onesweep",
+             "reduce": "k_reduce_groups"}[dom]
     nl = sb["launches"][dom]
     achieved = sb[dom] / (stage_ms[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",

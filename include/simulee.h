@@ -246,13 +246,15 @@ simulee_status simulee_check_batch(simulee_ctx *ctx, const simulee_trace *traces
  * A stage that does not run in a call still records both of its events, back to back.
  */
 enum {
-    SIMULEE_STAGE_INGEST = 0,   /* count stats, validation, routing, histograms */
-    SIMULEE_STAGE_SORT = 1,     /* radix passes of the record streams */
+    SIMULEE_STAGE_INGEST = 0,   /* count stats; validation and routing of sort-path traces */
+    SIMULEE_STAGE_SORT = 1,     /* inter-block filter, radix passes of the record streams */
     SIMULEE_STAGE_REDUCE = 2,   /* segmented reductions: races, epoch adjacency */
-    SIMULEE_STAGE_RACES = 3,    /* canonical race sort and copy-out */
+    SIMULEE_STAGE_RACES = 3,    /* race filter, canonical race sort and copy-out */
     SIMULEE_STAGE_BLOCKS = 4,   /* divergence, redundant-barrier lists, report */
-    SIMULEE_STAGE_HASH = 5,     /* short-interval hash path (intra-block races, adjacency) */
-    SIMULEE_STAGES = 6
+    SIMULEE_STAGE_HASH = 5,     /* hash path: one read of each block (validation, inter-block stream,
+                                   intra-block races, adjacency) */
+    SIMULEE_STAGE_FALLBACK = 6, /* routing of what the hash path leaves to the sort path */
+    SIMULEE_STAGES = 7
 };
 uint32_t simulee_last_launches(const simulee_ctx *ctx);
 /* Queues on `stream` a copy of five uint32 into dev_out (device memory), for the last check that

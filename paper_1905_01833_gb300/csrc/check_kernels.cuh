@@ -104,16 +104,15 @@ __device__ __forceinline__ void sig_mark(uint32_t *sig, uint64_t slot, uint32_t 
 // ---------------------------------------------------------------------------
 // Ingest, in up to two reads of the records.
 //
-// First read (IN_FIRST): validate every record; route global records to the
-// inter-block stream X keyed (trace, unit); for traces on the sort path route
-// shared records to stream S and global records to stream G, both keyed
-// (block, unit, epoch); for traces on the hash path record the bounds of every
-// (block, epoch) run and check that runs come in (block, epoch) order. Digit
-// histograms of the radix passes are built on the way.
-// Fallback read (IN_FALLBACK): route S and G for the blocks of hash-path
-// traces that the device found unsuitable: a block whose epochs are out of
-// order or whose (block, epoch) run is too long, or every block of a trace
-// whose blocks are out of order. It visits only the tiles k_fallback_tiles listed.
+// First read (IN_FIRST), for traces on the sort path: validate every record;
+// route global records to the inter-block stream X keyed (trace, unit), shared
+// records to stream S and global records to stream G, both keyed (block, unit,
+// epoch). Digit histograms of the radix passes are built on the way. Tiles of
+// hash-path traces are skipped: the hash path reads those records itself.
+// Fallback read (IN_FALLBACK): route S and G for what the hash path left to
+// the sort path: every record of a block it gave up on, of a trace whose
+// blocks are out of order, and of a spilled (block, epoch) run. It visits only
+// the tiles k_fallback_tiles listed.
 // Validate-only read (IN_VALIDATE): validation alone.
 //
 // Tiles of 2048 records (a tile never spans two traces) are staged into shared
@@ -135,8 +134,9 @@ constexpr size_t ingest_smem() { return 2 * (size_t)IN_STAGE * 16; }
 template <class KS, class KG, class KX, int MODE>
 __global__ void __launch_bounds__(IN_THREADS)
 k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, Layout L, TState *ts, Ctl *ctl,
-         KS *sk, uint64_t *sv, KG *gk, uint64_t *gv, KX *xk, uint64_t *xv, uint32_t *hist, uint32_t *runs,
-         uint32_t *binel, const uint32_t *__restrict__ tile_list, uint32_t *sig, uint64_t wait_ns) {
+         KS *sk, uint64_t *sv, KG *gk, uint64_t *gv, KX *xk, uint64_t *xv, uint32_t *hist,
+         const uint32_t *__restrict__ binel, const uint32_t *__restrict__ spill, const uint32_t *__restrict__ tile_list,
+         uint32_t *sig, uint64_t wait_ns) {
     extern __shared__ __align__(128) uint4 in_stage[];   // [2][IN_STAGE]
     __shared__ uint64_t bars[2];
     __shared__ uint32_t sh[IN_MAXP * RADIX];
@@ -154,13 +154,16 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
         fence_mbar_init();
     }
     __syncthreads();
-    const uint64_t ecap = (uint64_t)L.maxb + 1;
     // thread 0: start the copy of this CTA's k-th tile into stage k & 1
     auto issue = [&](uint64_t k) {
         const uint64_t i = blockIdx.x + k * gridDim.x;
         if (i >= ntiles) return;
         const uint64_t tile = (MODE == IN_FALLBACK) ? tile_list[i] : i;
         const TraceDesc &d = td[trace_of_tile(td, L.T, tile)];
+        if (MODE == IN_FIRST && d.hash_ok) {
+            mbar_arrive_expect_tx(&bars[k & 1], 0u);   // nothing to copy: complete the phase
+            return;
+        }
         const uint64_t tbase = (tile - d.tile_off) * IN_TILE;
         const uint64_t first = tbase > 0 ? tbase - 1 : 0, last = min(tbase + IN_TILE, d.n);
         const uint32_t bytes = (uint32_t)((last - first) * 16);
@@ -192,9 +195,10 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
         const uint64_t tbase = (tile - d.tile_off) * IN_TILE;
         const uint4 *recs = in_stage + (k & 1) * IN_STAGE + 1;   // recs[-1]: the record before the tile
         const bool hash_tr = d.hash_ok != 0;
+        if (!(MODE == IN_FIRST && hash_tr)) {   // uniform: a hash-path tile in the first read is skipped
         const bool trace_fb = MODE == IN_FALLBACK && *(volatile uint32_t *)&ts[t].inel != 0;
         const bool sorted = (d.flags & 1u) == 0;
-        const bool route_sg_tile = (MODE == IN_FIRST && !hash_tr) || MODE == IN_FALLBACK;
+        const bool route_sg_tile = MODE == IN_FIRST || MODE == IN_FALLBACK;
         uint32_t route = 0;   // bit j: S, bit 8+j: G, bit 16+j: X
         uint32_t cS = 0, cG = 0, cX = 0;
         // pass 1: validate, decide routes, count, run bookkeeping, histograms
@@ -214,26 +218,13 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
             if (MODE != IN_FALLBACK && in && !ok) atomicMax(&ts[t].bad_rec, ~(unsigned long long)idx);
             // routed records also keep the epoch inside the key's epoch field
             const bool rok = MODE != IN_VALIDATE && ok && ep <= d.maxb;
-            const bool route_sg = route_sg_tile && (MODE != IN_FALLBACK || trace_fb ||
-                                                    (rok && binel[(uint64_t)d.block_off + blk] != 0));
+            bool route_sg = route_sg_tile;
+            if (MODE == IN_FALLBACK && !trace_fb) {
+                const uint64_t sb = (uint64_t)d.block_off + blk;
+                route_sg = rok && (binel[sb] != 0 || ((spill[sb * L.swords + (ep >> 5)] >> (ep & 31)) & 1u));
+            }
             const bool isS = rok && route_sg && space == 0u, isG = rok && route_sg && space == 1u;
             const bool isX = MODE == IN_FIRST && rok && space == 1u;
-            if (MODE == IN_FIRST && hash_tr && rok) {
-                // bounds of (block, epoch) runs, and their order
-                const uint64_t cs = ((uint64_t)d.block_off + blk) * ecap + ep;
-                if (idx == 0) {
-                    runs[2 * cs] = 0;
-                } else {
-                    const uint32_t pb = pe.z, pp = (pe.w >> 16) & 0xFFFu;
-                    if (pb != blk || pp != ep) {
-                        if (pb > blk) atomicOr(&ts[t].inel, 1u);                                   // blocks out of order
-                        else if (pb == blk && pp > ep) atomicOr(&binel[d.block_off + blk], 1u);   // epochs out of order
-                        runs[2 * cs] = (uint32_t)idx;
-                        if (pb < d.nb && pp <= d.maxb) runs[2 * (((uint64_t)d.block_off + pb) * ecap + pp) + 1] = (uint32_t)idx;
-                    }
-                }
-                if (idx + 1 == d.n) runs[2 * cs + 1] = (uint32_t)d.n;
-            }
             const uint32_t bS = __ballot_sync(0xFFFFFFFFu, isS), bG = __ballot_sync(0xFFFFFFFFu, isG);
             const uint32_t bX = __ballot_sync(0xFFFFFFFFu, isX);
             cS += __popc(bS);
@@ -302,6 +293,7 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
                 oX += __popc(bX);
             }
         }
+        }
         __syncthreads();   // every thread is done with this stage buffer
         if (tid == 0) issue(k + 2);
     }
@@ -319,16 +311,18 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
 }
 
 // Tiles the fallback read must visit: those of hash-path traces holding a block
-// that the hash path does not take (or every tile of a trace whose blocks are
-// out of order). One thread per tile; the list order does not matter.
+// that the hash path gave up on or part of a spilled run (or every tile of a
+// trace whose blocks are out of order). One thread per tile; the list order
+// does not matter.
 __global__ void k_fallback_tiles(const TraceDesc *__restrict__ td, Layout L, const TState *ts,
-                                 const uint32_t *__restrict__ binel, Ctl *ctl, uint32_t *list) {
+                                 const uint32_t *__restrict__ binel, const uint32_t *__restrict__ tflag, Ctl *ctl,
+                                 uint32_t *list) {
     for (uint64_t tile = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; tile < L.ntiles_in;
          tile += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t t = trace_of_tile(td, L.T, tile);
         const TraceDesc &d = td[t];
         if (!d.hash_ok) continue;
-        bool fb = ts[t].inel != 0;
+        bool fb = ts[t].inel != 0 || tflag[tile] != 0;
         if (!fb) {
             // blocks are in record order here: the tile covers blocks first..last
             const uint64_t tbase = (tile - d.tile_off) * IN_TILE, last = min(tbase + IN_TILE, d.n) - 1;
@@ -412,13 +406,20 @@ __device__ __forceinline__ uint64_t race_key(const Layout &L, uint32_t trace, ui
     return k;
 }
 
+// Staged races carry their payload index; bit 63 marks a race of the hash
+// path, which the race filter drops when its block fell back to the sort path.
+// Capacity: a group of m >= 2 records yields at most min(2, m - 1) <= 2m/3
+// races, and each record lies in one intra-block group of the hash path, one
+// of the sort path and one inter-block group, so at most 2n races are staged.
+constexpr uint64_t RACE_FROM_HASH = 1ull << 63;
+
 __device__ __forceinline__ void emit_race(const RaceStage &rs, Ctl *ctl, uint32_t trace, uint64_t key, uint64_t p,
-                                          uint64_t q) {
+                                          uint64_t q, bool from_hash = false) {
     const uint32_t slot = atomicAdd(&ctl->n_races, 1u);
     atomicAdd(&rs.ts[trace].n_races, 1u);
     if (slot < rs.cap) {
         rs.keys[slot] = key;
-        rs.idx[slot] = slot;
+        rs.idx[slot] = slot | (from_hash ? RACE_FROM_HASH : 0ull);
         uint32_t vp = item_pos(p), vq = item_pos(q);
         if (rs.pos_to_vo && (rs.td[trace].flags & 1u)) {
             vp = vp < rs.n_pos ? rs.pos_to_vo[vp] : 0u;
@@ -654,10 +655,59 @@ __device__ __forceinline__ uint32_t race_trace(const Layout &L, uint64_t k) {
     return s >= 64 ? 0u : (uint32_t)(k >> s);
 }
 
+// Drop the hash path's races of blocks that fell back to the sort path (which
+// emits them again), keep the rest in any order, and build the digit
+// histograms of the kept keys for the canonical sort.
+__global__ void __launch_bounds__(256)
+k_race_filter(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ idx, uint64_t *okeys, uint64_t *oidx,
+              Layout L, const uint32_t *__restrict__ binel, TState *ts, Ctl *ctl, uint32_t *hist) {
+    __shared__ uint32_t sh[8 * RADIX];
+    __shared__ uint32_t wsum[8];
+    __shared__ uint32_t s_base;
+    const int tid = threadIdx.x;
+    if (must_stop(ctl)) return;
+    for (int i = tid; i < 8 * RADIX; i += 256) sh[i] = 0;
+    __syncthreads();
+    const uint64_t n = min((uint64_t)*(volatile unsigned int *)&ctl->n_races, L.race_cap);
+    const uint64_t bmask = (1ull << L.bb) - 1;
+    for (uint64_t base = (uint64_t)blockIdx.x * 256; base < n; base += (uint64_t)gridDim.x * 256) {
+        const uint64_t i = base + tid;
+        bool keep = false;
+        uint64_t k = 0, ix = 0;
+        if (i < n) {
+            k = keys[i];
+            ix = idx[i];
+            keep = true;
+            if (ix & RACE_FROM_HASH) {
+                ix &= ~RACE_FROM_HASH;
+                const uint32_t t = race_trace(L, k);
+                const uint64_t blk = (k >> (1 + L.bu + L.be)) & bmask;
+                if (t >= L.T || blk >= L.NB || binel[blk] != 0 || *(volatile unsigned int *)&ts[t].inel != 0) {
+                    keep = false;
+                    if (t < L.T) atomicSub(&ts[t].n_races, 1u);
+                }
+            }
+            if (keep)
+                for (uint32_t q = 0; q < L.np_r; q++) atomicAdd(&sh[q * RADIX + digit_of(k, q)], 1u);
+        }
+        const uint32_t pre = block_excl_scan_256(keep ? 1u : 0u, wsum);
+        if (tid == 255) s_base = atomicAdd(&ctl->n_rf, pre + (keep ? 1u : 0u));
+        __syncthreads();
+        if (keep) {
+            okeys[s_base + pre] = k;
+            oidx[s_base + pre] = ix;
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    for (int i = tid; i < (int)(L.np_r * RADIX); i += 256)
+        if (sh[i]) atomicAdd(&hist[(L.p0_r + i / RADIX) * RADIX + (i % RADIX)], sh[i]);
+}
+
 // first position of each trace in the sorted race list
 __global__ void k_race_starts(const uint64_t *__restrict__ keys, Layout L, Ctl *ctl, TState *ts) {
     if (must_stop(ctl)) return;
-    const uint64_t n = min((uint64_t)ctl->n_races, L.race_cap);
+    const uint64_t n = min((uint64_t)ctl->n_rf, L.race_cap);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t t = race_trace(L, keys[i]);
         if (t < L.T && (i == 0 || race_trace(L, keys[i - 1]) != t)) ts[t].race_start = (uint32_t)i;
@@ -667,7 +717,7 @@ __global__ void k_race_starts(const uint64_t *__restrict__ keys, Layout L, Ctl *
 __global__ void k_write_races(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ idx,
                               const uint4 *__restrict__ pay, Layout L, const TraceDesc *td, TState *ts, Ctl *ctl) {
     if (must_stop(ctl)) return;
-    const uint64_t n = min((uint64_t)ctl->n_races, L.race_cap);
+    const uint64_t n = min((uint64_t)ctl->n_rf, L.race_cap);
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t k = keys[i];
         const uint32_t t = race_trace(L, k);

@@ -75,6 +75,8 @@ struct Ctl {
     unsigned int n_div, n_red;    // divergent blocks / redundant barriers (all traces)
     unsigned int n_q;             // records in the schedule-rank sort (unsorted traces)
     unsigned int n_fb;            // tiles listed for the fallback read
+    unsigned int hb_next;         // next block for the hash path's CTAs
+    unsigned int n_rf;            // race records left by the race filter
     unsigned int tiles[MAX_PASSES];  // onesweep tile counters, one per pass
 };
 
@@ -86,7 +88,7 @@ struct Layout {
     uint64_t ntiles_in;              // ingest tiles, all traces
     uint32_t maxb;                   // largest max_barriers
     uint32_t any_unsorted;
-    uint32_t hash;                   // some trace may take the hash path (run table allocated)
+    uint32_t swords;                 // words per block of the spilled-run bitmap (epochs 0..maxb)
     uint32_t bb, bus, bug, be, bu, btr;   // bit widths: batch block, shared unit, global unit, epoch,
                                            // max(unit), trace index
     uint32_t bits_s, bits_g, bits_x, bits_r, bits_q;
@@ -97,12 +99,15 @@ struct Layout {
     uint64_t race_cap;               // staging capacity for race records
     uint64_t status_tiles;           // tiles covered by the look-back status array
     size_t off_binel;                // per batch-wide block: the hash path does not apply to it
+    size_t off_spill;                // per block and epoch: a run the hash path leaves to the sort path
+    size_t off_tflag;                // per ingest tile: holds a spilled run
+    size_t off_bstart;               // per batch-wide block of a hash-path trace: its first record
     size_t off_fbt;                  // tiles for the fallback read
     size_t off_sig;                  // block signature per global unit (or unit hash)
     uint64_t sig_slots;              // entries of the signature table (0: no global memory)
     uint32_t sig_direct;             // one trace: the table is indexed by unit itself
     size_t off_ctl, off_td, off_ts, off_tob, off_stats, off_nonred, off_gridnr, off_gridhas, off_cnt_div,
-        off_cnt_red, off_ofs_div, off_ofs_red, off_hist, off_dbase, off_status, off_rank, off_p2v, off_runs;
+        off_cnt_red, off_ofs_div, off_ofs_red, off_hist, off_dbase, off_status, off_rank, off_p2v;
     size_t off_sk[2], off_sv[2], off_gk[2], off_gv[2], off_xk[2], off_xv[2];
     size_t off_rk[2], off_rv[2], off_rp;
     size_t zero_end;                 // bytes from the start that every call zeroes

@@ -1,271 +1,504 @@
-// hash_path.cuh - short-interval path: intra-block checks without sorting.
+// hash_path.cuh - the single-read path: one CTA per block of a trace whose
+// records come block by block and, inside a block, epoch by epoch (the order
+// Algorithm 3's simulator emits them).
 //
-// Applies to traces whose records come in schedule order block by block and,
-// inside a block, epoch by epoch (the order Algorithm 3's simulator emits),
-// with at most HB_RUNMAX records per (block, epoch) run. One CTA takes a block
-// and walks its epochs in order. The records of a run are grouped by memory
-// unit in a shared-memory hash table (open addressing, Fibonacci hashing);
-// per slot and category {read, write, atomic} two atomicMin passes give the
-// earliest item and the earliest item of another thread (the top-2 summary of
-// common.cuh), from which the slot's lowest conflicting pairs follow. The
-// previous epoch's table keeps its keys and a packed adjacency summary per
-// slot, so each unit of epoch e is tested against the same unit of epoch e-1
-// (barrier e-1 needed or redundant) without a second pass over memory.
+// The CTA finds its block's record range (k_block_ranges), then streams the
+// range once, two records per thread per window, and for every record:
+//   * validates it (the checks of the ingest) and routes a global record to
+//     the inter-block stream X, marking the unit's block signature;
+//   * inserts it into a shared-memory hash table of the current (block, epoch)
+//     run, keyed by (unit, space), whose entry keeps an owner summary per
+//     action category {read, write, atomic}: the OR of the thread ids and the
+//     OR of their complements (10 bits each). A set of threads is one thread
+//     exactly when the two ORs share no bit, and the union of two sets is
+//     one thread exactly when the ORs of the union share no bit, so a single
+//     atomicOr per record keeps everything the conflict tests need.
+// At the end of a run the creator of each entry decides (a) whether the unit
+// holds a conflicting pair inside the run (Theorem 1: owners differ, one
+// access modifies, not both atomic), and (b) whether it conflicts with the
+// same unit in the previous epoch's table (barrier e-1 needed, Algorithm 5's
+// adjacency test). For the few units of (a) the exact lowest pair of each
+// class comes from two atomicMin passes over the run's records into a small
+// pool (the top-2 summary of common.cuh); a run with more racy units than the
+// pool holds is marked for the sort path instead ("spilled"), which then
+// computes its races exactly.
 //
-// The thread that creates a slot (wins the insert) finalises it, and resets it
-// once it is no longer needed, so the work per epoch follows the number of
-// distinct units rather than the table size. Each record is read once.
+// A block falls back to the sort path entirely ("binel") when its records are
+// not in epoch order, a run has more distinct units than the table holds, or a
+// record of another block or an invalid record lies in its range. Adjacency
+// marks the CTA made before that are sound (each comes from a genuine pair of
+// the block's records); its emitted races are dropped by the race filter, and
+// the fallback read routes the block to the sort path.
 #pragma once
 #include "check_kernels.cuh"
 
 namespace simk {
 
 constexpr int HB_THREADS = 1024;
-constexpr int HB_RUNMAX = 2048;                     // records per (block, epoch) run
-constexpr int HB_SLOTS = 4096;                      // load factor <= 1/2
-constexpr int HB_PER_THREAD = HB_RUNMAX / HB_THREADS;
+constexpr int HB_CH = 2 * HB_THREADS;               // records per window
+constexpr int HB_SLOTS = 8192;                      // entries per run table
+constexpr int HB_HASH_SHIFT = 19;                   // 32 - log2(HB_SLOTS)
+constexpr int HB_CAP = 6144;                        // distinct units per run (load <= 3/4)
+constexpr int HB_POOL = 64;                         // racy units resolved in place per run
+constexpr int HB_RSLOTS = 128;                      // racy-unit table (load <= 1/2)
 constexpr uint32_t HB_EMPTY = 0xFFFFFFFFu;
-constexpr uint32_t HB_NO_OWNER = 0x7FFu;            // packed owner code: category absent
+constexpr uint32_t HB_NONE = 0xFFFFFFFFu;           // no epoch
+constexpr uint32_t HB_POS_LIMIT = 1u << 22;         // run positions in a pool item (22 bits)
 
-// shared memory: keys of two epochs, first/second items per category, adjacency summaries,
-// and the staging buffer that receives the next run's records
+// shared memory: owner summaries and keys of two run tables, the creation
+// lists of both, the racy-unit table and its top-2 pool
 constexpr size_t hash_blocks_smem() {
-    return (size_t)HB_SLOTS * 4 * (2 + 3 + 3) + (size_t)HB_SLOTS * 8 + (size_t)HB_RUNMAX * 16;
+    return (size_t)HB_SLOTS * 8 * 2 + (size_t)HB_SLOTS * 4 * 2 + (size_t)HB_CAP * 2 * 2 + (size_t)HB_RSLOTS * 4 +
+           (size_t)HB_RSLOTS * 6 * 4;
 }
 
-__device__ __forceinline__ uint32_t hb_hash(uint32_t key) { return (key * 0x9E3779B1u) >> (32 - 12); }
+// owner summary field of category c: OR(tid) | OR(~tid) << 10
+__device__ __forceinline__ uint64_t hb_own_bits(uint32_t cat, uint32_t tid) {
+    const uint32_t f = (tid & 0x3FFu) | ((~tid & 0x3FFu) << 10);
+    return (uint64_t)f << (20 * cat);
+}
+__device__ __forceinline__ uint32_t hb_field(uint64_t o, int c) { return (uint32_t)(o >> (20 * c)) & 0xFFFFFu; }
+// the union of two owner sets (given by their fields) holds two or more threads
+__device__ __forceinline__ bool hb_two(uint32_t f, uint32_t g) {
+    const uint32_t u = f | g;
+    return (u & (u >> 10) & 0x3FFu) != 0u;
+}
+// Two non-empty sets X, Y have x in X, y in Y with different owners exactly
+// when their union has two owners (if every cross pair shared an owner, X and
+// Y would both be that one owner).
 
-// packed adjacency summary: x = ownR | ownW << 11 | multi << 22, y = ownA (owner = tid, 0x7FF = absent)
-__device__ __forceinline__ uint2 hb_pack(const Top2 &s) {
-    uint32_t own[3], multi = 0;
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-        own[c] = s.a[c] == EMPTY ? HB_NO_OWNER : ((uint32_t)s.a[c] & 0x3FFu);
-        if (s.b[c] != EMPTY) multi |= 1u << c;
-    }
-    return make_uint2(own[0] | (own[1] << 11) | (multi << 22), own[2]);
+// a conflicting pair inside one run's unit
+__device__ __forceinline__ bool hb_racy(uint64_t o) {
+    const uint32_t r = hb_field(o, 0), w = hb_field(o, 1), a = hb_field(o, 2), m = w | a;
+    const bool ww = w && (hb_two(w, w) || (a && hb_two(w, a)));   // write-write, write-atomic
+    const bool rw = r && m && hb_two(r, m);                       // read with write or atomic
+    return ww || rw;
 }
 
-__device__ __forceinline__ bool hb_conflict(uint2 P, uint2 Q) {
-    const uint32_t po[3] = {P.x & 0x7FFu, (P.x >> 11) & 0x7FFu, P.y & 0x7FFu};
-    const uint32_t qo[3] = {Q.x & 0x7FFu, (Q.x >> 11) & 0x7FFu, Q.y & 0x7FFu};
-    const uint32_t pm = (P.x >> 22) & 7u, qm = (Q.x >> 22) & 7u;
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        if (po[i] == HB_NO_OWNER) continue;
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            if (qo[j] == HB_NO_OWNER) continue;
-            if ((i == 0 && j == 0) || (i == 2 && j == 2)) continue;   // read/read, atomic/atomic
-            if (((pm >> i) & 1u) || ((qm >> j) & 1u) || po[i] != qo[j]) return true;
-        }
-    }
-    return false;
+// a conflicting pair between epoch e-1 (P) and epoch e (Q) of a unit:
+// read x modify, modify x read, write x modify, atomic x write (never read x read, atomic x atomic)
+__device__ __forceinline__ bool hb_cross(uint64_t P, uint64_t Q) {
+    const uint32_t pr = hb_field(P, 0), pw = hb_field(P, 1), pa = hb_field(P, 2), pm = pw | pa;
+    const uint32_t qr = hb_field(Q, 0), qw = hb_field(Q, 1), qa = hb_field(Q, 2), qm = qw | qa;
+    return (pr && qm && hb_two(pr, qm)) || (pm && qr && hb_two(pm, qr)) || (pw && qm && hb_two(pw, qm)) ||
+           (pa && qw && hb_two(pa, qw));
 }
 
-// item of the table: run position << 10 | tid  ->  summary item: position << 32 | tid
+__device__ __forceinline__ uint32_t hb_hash(uint32_t key) { return (key * 0x9E3779B1u) >> HB_HASH_SHIFT; }
+__device__ __forceinline__ uint32_t hb_rhash(uint32_t key) { return (key * 0x85EBCA6Bu) >> 25; }
+
+// pool item: run position << 10 | tid  ->  summary item: position << 32 | tid
 __device__ __forceinline__ uint64_t hb_item64(uint32_t v) {
     return v == HB_EMPTY ? EMPTY : (((uint64_t)(v >> 10) << 32) | (v & 0x3FFu));
 }
 
-__global__ void __launch_bounds__(HB_THREADS, 1)
-k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob, const uint4 *__restrict__ stats,
-              const uint32_t *__restrict__ runs, const uint32_t *__restrict__ binel, Layout L, TState *ts, Ctl *ctl,
-              uint32_t *nonred, RaceStage rs, uint64_t wait_ns) {
-    extern __shared__ __align__(128) uint32_t hb_smem[];
-    uint4 *hrec = reinterpret_cast<uint4 *>(hb_smem);                      // [HB_RUNMAX] staged records
-    uint32_t *hkey = hb_smem + HB_RUNMAX * 4;                              // [2][HB_SLOTS]
-    uint32_t *hfirst = hkey + 2 * HB_SLOTS;                                // [3][HB_SLOTS]
-    uint32_t *hsecond = hfirst + 3 * HB_SLOTS;                             // [3][HB_SLOTS]
-    uint2 *hadj = reinterpret_cast<uint2 *>(hsecond + 3 * HB_SLOTS);       // [HB_SLOTS]
-    __shared__ uint64_t bar;
-    __shared__ uint32_t s_needed;   // barrier e-1 already found needed in this epoch
-    const int tid = threadIdx.x;
-    for (int i = tid; i < 8 * HB_SLOTS; i += HB_THREADS) hkey[i] = HB_EMPTY;
-    if (tid == 0) {
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    uint32_t phase = 0;   // completed copies into hrec, mod 2 (same value in every thread)
-    const OwnThread own;
-    for (uint64_t b = blockIdx.x; b < L.NB; b += gridDim.x) {
-        const uint32_t t = tob[b];
-        const TraceDesc &d = td[t];
-        // uniform over the CTA: only suitable, valid hash-path traces
-        if (!d.hash_ok || *(volatile uint32_t *)&ts[t].inel || binel[b] || trace_bad(ts[t])) continue;
-        const uint64_t lb = b - d.block_off;
-        const uint32_t maxc = min(stats[b].w, L.maxb);
-        int cur = 0;
-        bool prev_live = false;
-        uint32_t mine_prev[HB_PER_THREAD], mine[HB_PER_THREAD];
-#pragma unroll
-        for (int j = 0; j < HB_PER_THREAD; j++) mine_prev[j] = HB_EMPTY;
-        const uint64_t rbase = 2 * (uint64_t)b * (L.maxb + 1);
-        // run bounds of epoch e of this block (empty when out of range)
-        auto run_of = [&](uint32_t e, uint32_t &rs_, uint32_t &m_) {
-            rs_ = 0;
-            m_ = 0;
-            if (e > maxc) return;
-            const uint32_t a = runs[rbase + 2 * e], z = runs[rbase + 2 * e + 1];
-            rs_ = a;
-            m_ = (z > a) ? min(z - a, (uint32_t)HB_RUNMAX) : 0u;
-        };
-        // thread 0: start the copy of a run's records into hrec (hrec is free)
-        auto prefetch = [&](uint32_t rs_, uint32_t m_) {
-            if (m_ == 0) return;
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bar, m_ * 16u);
-            bulk_g2s(hrec, d.events + rs_, m_ * 16u, &bar);
-        };
-        uint32_t rs0, m;
-        run_of(0, rs0, m);
-        if (tid == 0) prefetch(rs0, m);
-        for (uint32_t e = 0; e <= maxc; e++) {
-            uint32_t *key = hkey + cur * HB_SLOTS;
-            const uint32_t *pkey = hkey + (cur ^ 1) * HB_SLOTS;
-            uint32_t slot[HB_PER_THREAD], item[HB_PER_THREAD], cat[HB_PER_THREAD];
-            if (m > 0) {
-                const bool arrived = __syncthreads_and(mbar_wait(&bar, phase, wait_ns));
-                if (!arrived) {
-                    if (tid == 0) {
-                        atomicExch(&ctl->timeout, 1u);
-                        mbar_wait(&bar, phase, wait_ns);   // bounded: let the copy in flight land
-                    }
-                    return;
-                }
-                phase ^= 1u;
-            }
-            uint32_t rs1, m1;   // the next epoch's run
-            run_of(e + 1, rs1, m1);
-            // 1. insert this run's units; remember the slots this thread creates
-#pragma unroll
-            for (int j = 0; j < HB_PER_THREAD; j++) {
-                mine[j] = HB_EMPTY;
-                slot[j] = HB_EMPTY;
-                const uint32_t r = tid + j * HB_THREADS;
-                const uint4 ev = r < m ? hrec[r] : make_uint4(0, 0, 0, 0x30000000u);
-                const uint32_t sp = (ev.w >> 30) & 1u;
-                // fields were validated by the ingest; the check keeps shared memory safe regardless
-                if (r < m && ((ev.w >> 28) & 3u) != 3u && ev.x < (sp ? d.gu : d.su)) {
-                    const uint32_t k = (ev.x << 1) | sp;
-                    item[j] = (r << 10) | (ev.w & 0x3FFu);
-                    cat[j] = (ev.w >> 28) & 3u;
-                    uint32_t s = hb_hash(k);
-                    for (;;) {
-                        const uint32_t cur_k = key[s];
-                        if (cur_k == k) break;
-                        if (cur_k == HB_EMPTY) {
-                            const uint32_t old = atomicCAS(&key[s], HB_EMPTY, k);
-                            if (old == HB_EMPTY) { mine[j] = s; break; }
-                            if (old == k) break;
-                        }
-                        s = (s + 1) & (HB_SLOTS - 1);
-                    }
-                    slot[j] = s;
+// ---------------------------------------------------------------------------
+// First record of every block of a hash-path trace: the lower bound of the
+// block id over the records, by a 32-way search per warp. The result is
+// monotone in the block id for any record order, so the ranges partition the
+// trace even when it is not block-contiguous (which the hash kernel detects).
+// ---------------------------------------------------------------------------
+__global__ void k_block_ranges(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob, Layout L,
+                               uint32_t *bstart) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t b = warp; b < L.NB; b += nwarps) {
+        const TraceDesc &d = td[tob[b]];
+        if (!d.hash_ok) continue;
+        const uint32_t lb = (uint32_t)(b - d.block_off);
+        uint64_t lo = 0, hi = d.n;   // the answer lies in [lo, hi]
+        if (lb > 0) {
+            while (hi - lo > 32) {
+                const uint64_t step = (hi - lo + 31) / 32;
+                const uint64_t p = min(lo + (uint64_t)(lane + 1) * step - 1, hi - 1);
+                const bool below = d.events[p].z < lb;
+                const uint32_t m = __ballot_sync(0xFFFFFFFFu, below);
+                const int f = __ffs(~m) - 1;   // first probe not below (-1: all below)
+                if (f < 0) {
+                    lo = hi;
+                } else {
+                    const uint64_t pf = min(lo + (uint64_t)(f + 1) * step - 1, hi - 1);
+                    const uint64_t pl = f > 0 ? min(lo + (uint64_t)f * step - 1, hi - 1) + 1 : lo;
+                    lo = pl;
+                    hi = pf;
                 }
             }
-            if (tid == 0) s_needed = 0u;
-            __syncthreads();
-            if (tid == 0) prefetch(rs1, m1);   // every thread is done with hrec
-            // 2. earliest item per slot and category, then the earliest of another thread
-#pragma unroll
-            for (int j = 0; j < HB_PER_THREAD; j++)
-                if (slot[j] != HB_EMPTY) atomicMin(&hfirst[cat[j] * HB_SLOTS + slot[j]], item[j]);
-            __syncthreads();
-#pragma unroll
-            for (int j = 0; j < HB_PER_THREAD; j++)
-                if (slot[j] != HB_EMPTY) {
-                    const uint32_t f = hfirst[cat[j] * HB_SLOTS + slot[j]];
-                    if ((f & 0x3FFu) != (item[j] & 0x3FFu)) atomicMin(&hsecond[cat[j] * HB_SLOTS + slot[j]], item[j]);
-                }
-            __syncthreads();
-            // 3. creators finalise their slots: races, adjacency with the previous epoch
-            bool needed = false;
-            uint2 adj[HB_PER_THREAD];
-#pragma unroll
-            for (int j = 0; j < HB_PER_THREAD; j++) {
-                const uint32_t s = mine[j];
-                if (s == HB_EMPTY) continue;
-                Top2 S;
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    S.a[c] = hb_item64(hfirst[c * HB_SLOTS + s]);
-                    S.b[c] = hb_item64(hsecond[c * HB_SLOTS + s]);
-                }
-                const uint32_t k = key[s];
-                const uint32_t unit = k >> 1, space = k & 1u;
-                const bool two_owners = S.b[0] != EMPTY || S.b[1] != EMPTY || S.b[2] != EMPTY ||
-                                        (S.a[0] != EMPTY && S.a[1] != EMPTY && (uint32_t)S.a[0] != (uint32_t)S.a[1]) ||
-                                        (S.a[0] != EMPTY && S.a[2] != EMPTY && (uint32_t)S.a[0] != (uint32_t)S.a[2]) ||
-                                        (S.a[1] != EMPTY && S.a[2] != EMPTY && (uint32_t)S.a[1] != (uint32_t)S.a[2]);
-                if (two_owners) {
-#pragma unroll
-                    for (int cls = 0; cls < 2; cls++) {
-                        uint64_t p, q;
-                        if (!lowest_pair(S, cls, own, p, q)) continue;
-                        const uint32_t vp = d.events[rs0 + item_pos(p)].y, vq = d.events[rs0 + item_pos(q)].y;
-                        const uint64_t pp = ((uint64_t)vp << 32) | (uint32_t)(lb * d.bt + item_gtid(p));
-                        const uint64_t qq = ((uint64_t)vq << 32) | (uint32_t)(lb * d.bt + item_gtid(q));
-                        emit_race(rs, ctl, t, race_key(L, t, space, 0u, (uint32_t)b, e, unit, cls), pp, qq);
-                    }
-                }
-                adj[j] = hb_pack(S);
-                if (prev_live && !needed && !*(volatile uint32_t *)&s_needed) {
-                    uint32_t ps = hb_hash(k);
-                    for (;;) {
-                        const uint32_t pk = pkey[ps];
-                        if (pk == HB_EMPTY) break;
-                        if (pk == k) {
-                            if (hb_conflict(hadj[ps], adj[j])) {
-                                needed = true;
-                                s_needed = 1u;
-                            }
-                            break;
-                        }
-                        ps = (ps + 1) & (HB_SLOTS - 1);
-                    }
-                }
-            }
-            if (__syncthreads_or(needed) && tid == 0) mark_needed(nonred, L, (uint32_t)b, e - 1);
-            // 4. publish this epoch's summaries; release the previous epoch's keys and this epoch's items
-#pragma unroll
-            for (int j = 0; j < HB_PER_THREAD; j++) {
-                const uint32_t s = mine[j];
-                if (s != HB_EMPTY) {
-                    hadj[s] = adj[j];
-#pragma unroll
-                    for (int c = 0; c < 3; c++) {
-                        hfirst[c * HB_SLOTS + s] = HB_EMPTY;
-                        hsecond[c * HB_SLOTS + s] = HB_EMPTY;
-                    }
-                }
-                if (mine_prev[j] != HB_EMPTY) hkey[(cur ^ 1) * HB_SLOTS + mine_prev[j]] = HB_EMPTY;
-                mine_prev[j] = mine[j];
-            }
-            __syncthreads();
-            prev_live = m > 0;
-            cur ^= 1;
-            rs0 = rs1;
-            m = m1;
+            const uint64_t p = lo + lane;
+            const bool below = p < hi && d.events[p].z < lb;
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, below);
+            const int f = __ffs(~m) - 1;
+            lo = f < 0 ? lo + 32 : lo + f;
+            lo = min(lo, hi);
         }
-        // release the last epoch's keys before the next block
-#pragma unroll
-        for (int j = 0; j < HB_PER_THREAD; j++)
-            if (mine_prev[j] != HB_EMPTY) hkey[(cur ^ 1) * HB_SLOTS + mine_prev[j]] = HB_EMPTY;
-        __syncthreads();
+        if (lane == 0) bstart[b] = (uint32_t)lo;
     }
 }
 
-// A block with a (block, epoch) run longer than HB_RUNMAX records goes to the sort path.
-__global__ void k_runs_check(const TraceDesc *td, const uint32_t *tob, const uint32_t *runs, Layout L,
-                             uint32_t *binel) {
-    const uint64_t tot = (uint64_t)L.NB * (L.maxb + 1);
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t b = i / (L.maxb + 1);
-        if (!td[tob[b]].hash_ok) continue;
-        const uint32_t s = runs[2 * i], e = runs[2 * i + 1];
-        if (e < s || e - s > (uint32_t)HB_RUNMAX) atomicOr(&binel[b], 1u);
+template <class KX>
+__global__ void __launch_bounds__(HB_THREADS, 1)
+k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob, const uint32_t *__restrict__ bstart,
+              Layout L, TState *ts, Ctl *ctl, uint32_t *nonred, uint32_t *binel, uint32_t *spill, uint32_t *tflag,
+              KX *xk, uint64_t *xv, uint32_t *sig, RaceStage rs) {
+    extern __shared__ __align__(16) uint64_t hb_smem[];
+    uint64_t *own = hb_smem;                                               // [2][HB_SLOTS]
+    uint32_t *key = reinterpret_cast<uint32_t *>(own + 2 * HB_SLOTS);      // [2][HB_SLOTS]
+    uint16_t *list = reinterpret_cast<uint16_t *>(key + 2 * HB_SLOTS);     // [2][HB_CAP]
+    uint32_t *rkey = reinterpret_cast<uint32_t *>(list + 2 * HB_CAP);      // [HB_RSLOTS]
+    uint32_t *pool = rkey + HB_RSLOTS;                                     // [HB_RSLOTS][first 3, second 3]
+    __shared__ uint32_t s_blk, s_cnt[2], s_flag, s_minpend, s_lo, s_hi, s_nracy;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const uint32_t lt = lanemask_lt();
+    for (int i = tid; i < 2 * HB_SLOTS; i += HB_THREADS) {
+        own[i] = 0ull;
+        key[i] = HB_EMPTY;
+    }
+    for (int i = tid; i < HB_RSLOTS * 7; i += HB_THREADS) rkey[i] = HB_EMPTY;   // rkey and pool
+    if (tid == 0) {
+        s_cnt[0] = s_cnt[1] = 0;
+        s_flag = 0;
+        s_minpend = HB_NONE;
+        s_lo = 0xFFFFFFFFu;
+        s_hi = 0;
+        s_nracy = 0;
+    }
+        for (;;) {
+        __syncthreads();
+        if (tid == 0) s_blk = atomicAdd(&ctl->hb_next, 1u);
+        __syncthreads();
+        const uint32_t b = s_blk;
+        if (b >= L.NB) break;
+        const uint32_t t = tob[b];
+        const TraceDesc &d = td[t];
+        // uniform: only hash-path traces whose barrier counts are valid (otherwise nothing is reported)
+        if (!d.hash_ok || *(volatile unsigned long long *)&ts[t].bad_cnt) continue;
+        const uint32_t lb = b - d.block_off;
+        const uint64_t s0 = bstart[b], s1 = (lb + 1 < d.nb) ? (uint64_t)bstart[b + 1] : d.n;
+        if (s0 >= s1) continue;   // a block without records: no runs
+        const uint4 *ev = d.events;
+        const bool pad = d.nb <= (1u << 20);
+
+        // ---- window: records wbase + j * HB_THREADS + tid, j = 0, 1 --------------------------
+        uint64_t wbase = s0;
+        uint4 cur[2], nxt[2];
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+            const uint64_t i0 = s0 + j * HB_THREADS + tid, i1 = i0 + HB_CH;
+            cur[j] = i0 < s1 ? ev[i0] : make_uint4(0, 0, 0, 0);
+            nxt[j] = i1 < s1 ? ev[i1] : make_uint4(0, 0, 0, 0);
+        }
+        // validate the window's records, route global ones to X; returns the records to hash
+        auto activate = [&]() -> uint32_t {
+            uint32_t pb = 0;
+            bool stopme = false, isx[2];
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                const uint64_t idx = wbase + j * HB_THREADS + tid;
+                const bool in = idx < s1;
+                const uint4 e = cur[j];
+                const uint32_t u = e.x, vo = e.y, blk = e.z, w3 = e.w;
+                const uint32_t tt = w3 & 0xFFFFu, ep = (w3 >> 16) & 0xFFFu, act = (w3 >> 28) & 3u;
+                const uint32_t sp = (w3 >> 30) & 1u, resv = w3 >> 31;
+                uint32_t pvo = __shfl_up_sync(0xFFFFFFFFu, vo, 1);
+                if (lane == 0) pvo = (in && idx > 0) ? ev[idx - 1].y : 0u;
+                bool ok = in && blk < d.nb && tt < d.bt && act != 3u && resv == 0u && (sp ? u < d.gu : u < d.su);
+                if (ok && ep > d.counts[(uint64_t)blk * d.bt + tt]) ok = false;
+                if (in && idx > 0 && vo <= pvo) ok = false;
+                if (in && !ok) atomicMax(&ts[t].bad_rec, ~(unsigned long long)idx);
+                if (ok && blk != lb) atomicOr(&ts[t].inel, 1u);   // the trace is not block-contiguous
+                if (in && (!ok || blk != lb)) stopme = true;
+                if (ok && blk == lb) pb |= 1u << j;
+                isx[j] = ok && sp == 1u && ep <= d.maxb;
+            }
+            const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, isx[0]), b1 = __ballot_sync(0xFFFFFFFFu, isx[1]);
+            const uint32_t tot = __popc(b0) + __popc(b1);
+            uint32_t xb = 0;
+            if (lane == 0 && tot) xb = atomicAdd(&ctl->n_x, tot);
+            xb = __shfl_sync(0xFFFFFFFFu, xb, 0);
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                if (!isx[j]) continue;
+                const uint4 e = cur[j];
+                const uint32_t o = xb + (j ? __popc(b0) + __popc(b1 & lt) : __popc(b0 & lt));
+                const uint32_t blk = e.z, w3 = e.w, act = (w3 >> 28) & 3u;
+                const uint32_t xo = pad ? ((blk << 10) | (w3 & 0x3FFu)) : blk * d.bt + (w3 & 0xFFFFu);
+                xk[o] = (KX)(shl(t, L.bug) | e.x);
+                xv[o] = make_payload(act, xo, e.y);
+                sig_mark(sig, sig_slot(L, t, e.x), d.block_off + blk);
+            }
+            if (stopme) s_flag = 1u;
+            return pb;
+        };
+        auto advance = [&]() {
+            wbase += HB_CH;
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                cur[j] = nxt[j];
+                const uint64_t i1 = wbase + HB_CH + j * HB_THREADS + tid;
+                nxt[j] = i1 < s1 ? ev[i1] : make_uint4(0, 0, 0, 0);
+            }
+        };
+        uint32_t pend = activate();
+
+        uint32_t e = (ev[s0].w >> 16) & 0xFFFu;   // epoch of the block's first record
+        uint32_t prev_e = HB_NONE, par = 0, cnt_prev = 0;
+        bool hashing = true, full_reset = false;
+        for (;;) {
+            // ---- 1. insert run e: its records in this window and, while it continues, the next
+            for (;;) {
+                uint32_t lo = 0xFFFFFFFFu, hi = 0, mp = HB_NONE;
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    const uint4 r = cur[j];
+                    const uint32_t ep = (r.w >> 16) & 0xFFFu;
+                    const bool mine = ((pend >> j) & 1u) && ep == e;
+                    uint32_t s = HB_EMPTY;
+                    bool created = false;
+                    if (mine) {
+                        const uint32_t k = (r.x << 1) | ((r.w >> 30) & 1u);
+                        uint32_t h = hb_hash(k);
+                        for (int probe = 0; probe < HB_SLOTS; probe++) {
+                            const uint32_t c = key[par * HB_SLOTS + h];
+                            if (c == k) { s = h; break; }
+                            if (c == HB_EMPTY) {
+                                const uint32_t old = atomicCAS(&key[par * HB_SLOTS + h], HB_EMPTY, k);
+                                if (old == HB_EMPTY) { s = h; created = true; break; }
+                                if (old == k) { s = h; break; }
+                            }
+                            h = (h + 1) & (HB_SLOTS - 1);
+                        }
+                        if (s == HB_EMPTY) {
+                            s_flag = 2u;   // table full
+                        } else {
+                            atomicOr(reinterpret_cast<unsigned long long *>(&own[par * HB_SLOTS + s]),
+                                     (unsigned long long)hb_own_bits((r.w >> 28) & 3u, r.w & 0x3FFu));
+                        }
+                        const uint32_t idx = (uint32_t)(wbase + j * HB_THREADS + tid);
+                        lo = min(lo, idx);
+                        hi = max(hi, idx);
+                        pend &= ~(1u << j);
+                    } else if ((pend >> j) & 1u) {
+                        mp = min(mp, ep);
+                    }
+                    const uint32_t cm = __ballot_sync(0xFFFFFFFFu, created);
+                    if (cm) {
+                        uint32_t base = 0;
+                        if (lane == __ffs(cm) - 1) base = atomicAdd(&s_cnt[par], (uint32_t)__popc(cm));
+                        base = __shfl_sync(0xFFFFFFFFu, base, __ffs(cm) - 1);
+                        if (created) {
+                            const uint32_t pos = base + __popc(cm & lt);
+                            if (pos < HB_CAP) list[par * HB_CAP + pos] = (uint16_t)s;
+                            else s_flag = 2u;   // more distinct units than listed entries
+                        }
+                    }
+                }
+                lo = __reduce_min_sync(0xFFFFFFFFu, lo);
+                hi = __reduce_max_sync(0xFFFFFFFFu, hi);
+                mp = __reduce_min_sync(0xFFFFFFFFu, mp);
+                if (lane == 0) {
+                    if (lo != 0xFFFFFFFFu) {
+                        atomicMin(&s_lo, lo);
+                        atomicMax(&s_hi, hi);
+                    }
+                    if (mp != HB_NONE) atomicMin(&s_minpend, mp);
+                }
+                // the run continues into the next window when that window exists and this one
+                // ends with a record of the run
+                const uint64_t wend = min(wbase + HB_CH, s1);
+                if (wend < s1) {
+                    const uint4 last = ev[wend - 1];
+                    if (last.z == lb && ((last.w >> 16) & 0xFFFu) == e) {
+                        if (pend) s_flag = 3u;   // a record of this window was left behind: not in epoch order
+                        advance();
+                        pend = activate();
+                        continue;
+                    }
+                }
+                break;
+            }
+
+            // ---- 2. finalise run e
+            __syncthreads();   // A: the run's inserts are complete
+            const uint32_t flag = s_flag, next = s_minpend;
+            const uint32_t cnt = min(s_cnt[par], (uint32_t)HB_CAP);
+            const uint32_t lo = s_lo, hi = s_hi;
+            const bool stop = flag != 0u || (next != HB_NONE && next <= e);
+            bool needed = false;
+            uint32_t rmask = 0;   // bit m: this thread's list entry tid + m * HB_THREADS went to the racy table
+            uint64_t rq = 0;      // their racy-table slots, 7 bits each
+            if (!stop) {
+                const bool adj = prev_e != HB_NONE && prev_e + 1 == e;
+                const uint32_t pp = par ^ 1u;
+#pragma unroll 1
+                for (uint32_t i = tid, m = 0; i < cnt; i += HB_THREADS, m++) {
+                    const uint32_t s = list[par * HB_CAP + i];
+                    const uint64_t o = own[par * HB_SLOTS + s];
+                    const uint32_t k = key[par * HB_SLOTS + s];
+                    if (hb_racy(o)) {
+                        const uint32_t r = atomicAdd(&s_nracy, 1u);
+                        if (r < HB_POOL) {
+                            uint32_t q = hb_rhash(k);
+                            bool in = false;
+                            for (int probe = 0; probe < HB_RSLOTS && !in; probe++) {
+                                in = atomicCAS(&rkey[q], HB_EMPTY, k) == HB_EMPTY;
+                                if (!in) q = (q + 1) & (HB_RSLOTS - 1);
+                            }
+                            if (in) {
+                                rmask |= 1u << m;
+                                rq |= (uint64_t)q << (7 * m);
+                            } else {
+                                atomicOr(&s_nracy, 0x40000000u);   // cannot happen (load <= 1/2); spill the run
+                            }
+                        }
+                    }
+                    if (adj && !needed) {
+                        uint32_t h = hb_hash(k);
+                        for (int probe = 0; probe < HB_SLOTS; probe++) {
+                            const uint32_t c = key[pp * HB_SLOTS + h];
+                            if (c == HB_EMPTY) break;
+                            if (c == k) {
+                                needed = hb_cross(own[pp * HB_SLOTS + h], o);
+                                break;
+                            }
+                            h = (h + 1) & (HB_SLOTS - 1);
+                        }
+                    }
+                }
+            }
+            if (__syncthreads_or(needed) && tid == 0) mark_needed(nonred, L, b, e - 1);   // B
+            const uint32_t nracy = s_nracy;
+            if (!stop && nracy > 0) {
+                if (nracy > HB_POOL || hi - lo >= HB_POS_LIMIT) {
+                    // too many racy units: the sort path computes this run's races
+                    if (tid == 0) {
+                        atomicOr(&spill[(uint64_t)b * L.swords + (e >> 5)], 1u << (e & 31));
+                        for (uint64_t tl = lo / IN_TILE; tl <= hi / IN_TILE; tl++) tflag[d.tile_off + tl] = 1u;
+                    }
+                } else {
+                    // exact lowest pairs of the racy units: first, then first of another thread, per category
+#pragma unroll 1
+                    for (int pass = 0; pass < 2; pass++) {
+                        for (uint64_t i = lo + tid; i <= hi; i += HB_THREADS) {
+                            const uint4 r = ev[i];
+                            if (r.z != lb || ((r.w >> 16) & 0xFFFu) != e) continue;
+                            const uint32_t k = (r.x << 1) | ((r.w >> 30) & 1u);
+                            const uint32_t c = (r.w >> 28) & 3u, tt = r.w & 0x3FFu;
+                            if (c == 3u) continue;
+                            const uint32_t item = ((uint32_t)(i - lo) << 10) | tt;
+                            uint32_t q = hb_rhash(k);
+                            for (int probe = 0; probe < HB_RSLOTS; probe++) {
+                                const uint32_t rk = rkey[q];
+                                if (rk == HB_EMPTY) break;
+                                if (rk == k) {
+                                    uint32_t *pe = pool + q * 6;
+                                    if (pass == 0) atomicMin(&pe[c], item);
+                                    else if ((pe[c] & 0x3FFu) != tt) atomicMin(&pe[3 + c], item);
+                                    break;
+                                }
+                                q = (q + 1) & (HB_RSLOTS - 1);
+                            }
+                        }
+                        __syncthreads();   // C, D
+                    }
+                    const OwnThread ownt;
+                    for (uint32_t m = 0; rmask >> m; m++) {
+                        if (!((rmask >> m) & 1u)) continue;
+                        const uint32_t q = (uint32_t)(rq >> (7 * m)) & 0x7Fu;
+                        const uint32_t k = rkey[q];
+                        Top2 S;
+#pragma unroll
+                        for (int c = 0; c < 3; c++) {
+                            S.a[c] = hb_item64(pool[q * 6 + c]);
+                            S.b[c] = hb_item64(pool[q * 6 + 3 + c]);
+                        }
+#pragma unroll
+                        for (int cls = 0; cls < 2; cls++) {
+                            uint64_t p, q2;
+                            if (!lowest_pair(S, cls, ownt, p, q2)) continue;
+                            const uint32_t vp = ev[lo + item_pos(p)].y, vq = ev[lo + item_pos(q2)].y;
+                            const uint64_t pi = ((uint64_t)vp << 32) | (uint32_t)((uint64_t)lb * d.bt + item_gtid(p));
+                            const uint64_t qi = ((uint64_t)vq << 32) | (uint32_t)((uint64_t)lb * d.bt + item_gtid(q2));
+                            emit_race(rs, ctl, t, race_key(L, t, k & 1u, 0u, b, e, k >> 1, cls), pi, qi, true);
+                        }
+                    }
+                }
+            }
+            // release racy-table entries; release the previous run's table
+            for (uint32_t m = 0; rmask >> m; m++) {
+                if (!((rmask >> m) & 1u)) continue;
+                const uint32_t q = (uint32_t)(rq >> (7 * m)) & 0x7Fu;
+                rkey[q] = HB_EMPTY;
+#pragma unroll
+                for (int c = 0; c < 6; c++) pool[q * 6 + c] = HB_EMPTY;
+            }
+            if (!stop) {
+                const uint32_t pp = par ^ 1u;
+                for (uint32_t i = tid; i < cnt_prev; i += HB_THREADS) {
+                    const uint32_t s = list[pp * HB_CAP + i];
+                    key[pp * HB_SLOTS + s] = HB_EMPTY;
+                    own[pp * HB_SLOTS + s] = 0ull;
+                }
+            }
+            if (tid == 0) {
+                s_cnt[par ^ 1u] = 0;
+                s_minpend = HB_NONE;
+                s_lo = 0xFFFFFFFFu;
+                s_hi = 0;
+            }
+            __syncthreads();   // E
+            if (tid == 0) s_nracy = 0;
+            if (stop) {
+                // the block goes to the sort path; its tables are cleared in full below
+                if (tid == 0) atomicOr(&binel[b], 1u);
+                hashing = false;
+                full_reset = true;
+                break;
+            }
+            prev_e = e;
+            cnt_prev = cnt;
+            par ^= 1u;
+            if (next == HB_NONE) {
+                // every record of the window is in; a record range that goes on means the block's
+                // records are not in run order
+                if (min(wbase + HB_CH, s1) < s1) {
+                    if (tid == 0) atomicOr(&binel[b], 1u);
+                    hashing = false;
+                    full_reset = true;
+                }
+                break;
+            }
+            e = next;
+        }
+        // records of the range not yet read (the block left the hash path early): validate and route
+        while (wbase + HB_CH < s1) {
+            advance();
+            activate();
+        }
+        // clean tables for the next block
+        if (full_reset) {
+            __syncthreads();
+            for (int i = tid; i < 2 * HB_SLOTS; i += HB_THREADS) {
+                own[i] = 0ull;
+                key[i] = HB_EMPTY;
+            }
+            if (tid == 0) {
+                s_cnt[0] = s_cnt[1] = 0;
+                s_flag = 0;
+            }
+        } else if (hashing) {
+            const uint32_t pp = par ^ 1u;   // the last run's table
+            for (uint32_t i = tid; i < cnt_prev; i += HB_THREADS) {
+                const uint32_t s = list[pp * HB_CAP + i];
+                key[pp * HB_SLOTS + s] = HB_EMPTY;
+                own[pp * HB_SLOTS + s] = 0ull;
+            }
+            if (tid == 0) s_cnt[pp] = 0;
+        }
+        if (tid == 0) {
+            s_minpend = HB_NONE;
+            s_lo = 0xFFFFFFFFu;
+            s_hi = 0;
+        }
     }
 }
 

@@ -139,7 +139,11 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, Layout &L) {
     L.off_gridhas = take((size_t)T * L.words * 4);
     L.off_hist = take((size_t)MAX_PASSES * RADIX * 4);
     L.off_binel = take((size_t)L.NB * 4);
+    L.swords = maxb / 32 + 1;
+    L.off_spill = take((size_t)L.NB * L.swords * 4);
+    L.off_tflag = take((size_t)std::max<uint64_t>(L.ntiles_in, 1) * 4);
     L.zero_end = o;
+    L.off_bstart = take((size_t)L.NB * 4);
     L.off_fbt = take((size_t)std::max<uint64_t>(L.ntiles_in, 1) * 4);
     // block signatures of global units: indexed by unit for one trace with a modest global space,
     // else by a hash of (trace, unit) into a power-of-two table about the size of the trace
@@ -167,10 +171,6 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, Layout &L) {
         L.off_rank = take(n1 * 4);
         L.off_p2v = take(n1 * 4);
     }
-    // (block, epoch) run bounds for the hash path, when the table stays small
-    const uint64_t run_slots = (uint64_t)L.NB * ((uint64_t)maxb + 1);
-    L.hash = run_slots <= (1ull << 25) ? 1u : 0u;
-    if (L.hash) L.off_runs = take(run_slots * 8);
     const size_t ks = L.wide_s ? 8 : 4, kg = L.wide_g ? 8 : 4, kx = L.wide_x ? 8 : 4;
     for (int i = 0; i < 2; i++) {
         L.off_sk[i] = take(n1 * ks);
@@ -358,7 +358,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     const bool route_any = want.races || want.red;
     for (uint32_t i = 0; i < T; i++) {
         TraceDesc &d = hdesc[i];
-        d.hash_ok = (R.L.hash && route_any && ctx->opt.path != SIMULEE_PATH_SORT && !(d.flags & SIMULEE_FLAG_UNSORTED) &&
+        d.hash_ok = (route_any && ctx->opt.path != SIMULEE_PATH_SORT && !(d.flags & SIMULEE_FLAG_UNSORTED) &&
                      d.su < 0x7FFFFFFFu && d.gu < 0x7FFFFFFFu && d.n > 0) ? 1u : 0u;
         any_hash |= d.hash_ok != 0;
     }
@@ -372,7 +372,8 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
         set_reduce_attr<uint64_t, false>();
         set_reduce_attr<uint32_t, true>();
         set_reduce_attr<uint64_t, true>();
-        cudaFuncSetAttribute(k_hash_blocks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hash_blocks_smem());
+        cudaFuncSetAttribute(k_hash_blocks<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hash_blocks_smem());
+        cudaFuncSetAttribute(k_hash_blocks<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hash_blocks_smem());
         ctx->attrs_set = true;
     }
     R.st = (cudaStream_t)stream;
@@ -391,12 +392,12 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     R.mark(SIMULEE_STAGE_INGEST, 0);
     cudaMemsetAsync(R.ws, 0, L.zero_end, st);
     cudaMemsetAsync(R.ws + L.off_status, 0, (size_t)L.status_tiles * RADIX * 8, st);
-    uint32_t *runs = any_hash ? R.at<uint32_t>(L.off_runs) : nullptr;
     uint32_t *binel = R.at<uint32_t>(L.off_binel);
+    uint32_t *spill = R.at<uint32_t>(L.off_spill);
+    uint32_t *tflag = R.at<uint32_t>(L.off_tflag);
     uint32_t *fbt = R.at<uint32_t>(L.off_fbt);
     uint32_t *sig = L.sig_slots ? R.at<uint32_t>(L.off_sig) : nullptr;
     if (sig && (want.races || want.red)) cudaMemsetAsync(sig, 0, L.sig_slots * 4, st);
-    if (any_hash) cudaMemsetAsync(runs, 0, (size_t)L.NB * (L.maxb + 1) * 8, st);
     for (uint32_t i = 0; i < T; i += kDescChunk) {
         DescChunk c;
         const uint32_t cnt = std::min<uint32_t>(kDescChunk, T - i);
@@ -411,12 +412,26 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
 
     const bool route = want.races || want.red;
     const bool sorting = L.n > 0 && route;
+    bool any_sort = false;   // a trace on the sort path from the start
+    for (uint32_t i = 0; i < T; i++) any_sort |= hdesc[i].hash_ok == 0 && hdesc[i].n > 0;
     uint32_t *rank = nullptr, *pos_to_vo = nullptr;
+    if (L.any_unsorted) {
+        rank = R.at<uint32_t>(L.off_rank);
+        pos_to_vo = R.at<uint32_t>(L.off_p2v);
+    }
+    RaceStage rs;
+    rs.keys = R.at<uint64_t>(L.off_rk[0]);
+    rs.idx = R.at<uint64_t>(L.off_rv[0]);
+    rs.pay = R.at<uint4>(L.off_rp);
+    rs.cap = L.race_cap;
+    rs.pos_to_vo = pos_to_vo;
+    rs.n_pos = L.n;
+    rs.ts = ts;
+    rs.td = td;
+    uint32_t *nonred = R.at<uint32_t>(L.off_nonred);
     if (L.n > 0) {
         // 3. unsorted traces: schedule rank of each record = position in (trace, visit order, index) order
         if (L.any_unsorted) {
-            rank = R.at<uint32_t>(L.off_rank);
-            pos_to_vo = R.at<uint32_t>(L.off_p2v);
             size_t qk[2] = {L.off_rk[0], L.off_rk[1]}, qv[2] = {L.off_rv[0], L.off_rv[1]};
             const int g = R.grid_for(L.n, 256, 8);
             uint32_t *hq = hist + (size_t)L.p0_q * RADIX, *dq = R.at<uint32_t>(L.off_dbase) + (size_t)L.p0_q * RADIX;
@@ -436,7 +451,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
             R.launches++;
         }
 
-        // 4. ingest: first read; then, for hash-path traces found unsuitable, a fallback read
+        // 4. ingest: validation-only read, or the first read of sort-path traces
         const int gi = R.grid_for(L.ntiles_in, 1, ctx->opt.ingest_ctas_per_sm ? ctx->opt.ingest_ctas_per_sm : 2u);
 #define SIM_INGEST(KS, KG, KX, MODE)                                                                                \
     do {                                                                                                            \
@@ -445,7 +460,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
                                  (int)ingest_smem());                                                               \
         k_ingest<KS, KG, KX, MODE><<<gi, IN_THREADS, ingest_smem(), st>>>(                                          \
             td, rank, L, ts, R.ctl, R.at<KS>(L.off_sk[0]), R.at<uint64_t>(L.off_sv[0]), R.at<KG>(L.off_gk[0]),      \
-            R.at<uint64_t>(L.off_gv[0]), R.at<KX>(L.off_xk[0]), R.at<uint64_t>(L.off_xv[0]), hist, runs, binel,     \
+            R.at<uint64_t>(L.off_gv[0]), R.at<KX>(L.off_xk[0]), R.at<uint64_t>(L.off_xv[0]), hist, binel, spill,    \
             fbt, sig, R.wait_ns);                                                                                   \
     } while (0)
 #define SIM_INGEST_W(MODE)                                                                                          \
@@ -464,21 +479,49 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
         if (!route) {
             SIM_INGEST(uint32_t, uint32_t, uint32_t, IN_VALIDATE);
             R.launches++;
-        } else {
+        } else if (any_sort) {
             SIM_INGEST_W(IN_FIRST);
-            if (any_hash) {
-                k_runs_check<<<R.grid_for((uint64_t)L.NB * (L.maxb + 1), 256, 8), 256, 0, st>>>(td, tob, runs, L, binel);
-                k_fallback_tiles<<<R.grid_for(L.ntiles_in, 256, 8), 256, 0, st>>>(td, L, ts, binel, R.ctl, fbt);
-                R.launches += 2;
-                SIM_INGEST_W(IN_FALLBACK);
-            }
+        }
+        R.mark(SIMULEE_STAGE_INGEST, 1);
+
+        // 5. hash-path traces: one read of each block's records (validation, inter-block stream,
+        //    intra-block checks), then the fallback read of what the hash path left to the sort path
+        R.mark(SIMULEE_STAGE_HASH, 0);
+        if (route && any_hash) {
+            uint32_t *bstart = R.at<uint32_t>(L.off_bstart);
+            k_block_ranges<<<R.grid_for(L.NB, 8, 16), 256, 0, st>>>(td, tob, L, bstart);
+            const int gh = std::max(1, std::min<int>(ctx->sms, (int)L.NB));
+            if (L.wide_x)
+                k_hash_blocks<uint64_t><<<gh, HB_THREADS, hash_blocks_smem(), st>>>(
+                    td, tob, bstart, L, ts, R.ctl, nonred, binel, spill, tflag, R.at<uint64_t>(L.off_xk[0]),
+                    R.at<uint64_t>(L.off_xv[0]), sig, rs);
+            else
+                k_hash_blocks<uint32_t><<<gh, HB_THREADS, hash_blocks_smem(), st>>>(
+                    td, tob, bstart, L, ts, R.ctl, nonred, binel, spill, tflag, R.at<uint32_t>(L.off_xk[0]),
+                    R.at<uint64_t>(L.off_xv[0]), sig, rs);
+            R.launches += 2;
+            R.mark(SIMULEE_STAGE_HASH, 1);
+            R.mark(SIMULEE_STAGE_FALLBACK, 0);
+            k_fallback_tiles<<<R.grid_for(L.ntiles_in, 256, 8), 256, 0, st>>>(td, L, ts, binel, tflag, R.ctl, fbt);
+            R.launches++;
+            SIM_INGEST_W(IN_FALLBACK);
+            R.mark(SIMULEE_STAGE_FALLBACK, 1);
+        } else {
+            R.mark(SIMULEE_STAGE_HASH, 1);
+            R.mark(SIMULEE_STAGE_FALLBACK, 0);
+            R.mark(SIMULEE_STAGE_FALLBACK, 1);
         }
 #undef SIM_INGEST_W
 #undef SIM_INGEST
+    } else {
+        R.mark(SIMULEE_STAGE_INGEST, 1);
+        R.mark(SIMULEE_STAGE_HASH, 0);
+        R.mark(SIMULEE_STAGE_HASH, 1);
+        R.mark(SIMULEE_STAGE_FALLBACK, 0);
+        R.mark(SIMULEE_STAGE_FALLBACK, 1);
     }
-    R.mark(SIMULEE_STAGE_INGEST, 1);
 
-    // 5. sort the three streams
+    // 6. sort the three streams
     R.mark(SIMULEE_STAGE_SORT, 0);
     int bs = 0, bg = 0, bx = 0;
     if (sorting) {
@@ -510,18 +553,8 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     }
     R.mark(SIMULEE_STAGE_SORT, 1);
 
-    // 6. segmented reductions
+    // 7. segmented reductions
     R.mark(SIMULEE_STAGE_REDUCE, 0);
-    RaceStage rs;
-    rs.keys = R.at<uint64_t>(L.off_rk[0]);
-    rs.idx = R.at<uint64_t>(L.off_rv[0]);
-    rs.pay = R.at<uint4>(L.off_rp);
-    rs.cap = L.race_cap;
-    rs.pos_to_vo = pos_to_vo;
-    rs.n_pos = L.n;
-    rs.ts = ts;
-    rs.td = td;
-    uint32_t *nonred = R.at<uint32_t>(L.off_nonred);
     if (sorting) {
         const int gr = R.grid_for(L.n, RG_TILE, ctx->opt.reduce_ctas_per_sm ? ctx->opt.reduce_ctas_per_sm : 3u);
 #define SIM_REDUCE(K, INTER, KOFF, VOFF, NPTR, SPACE, BU)                                                             \
@@ -538,25 +571,16 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     }
     R.mark(SIMULEE_STAGE_REDUCE, 1);
 
-    // 6b. short-interval hash path: intra-block races and adjacency of hash-path traces
-    R.mark(SIMULEE_STAGE_HASH, 0);
-    if (sorting && any_hash) {
-        k_hash_blocks<<<std::max(1, std::min<int>(ctx->sms, (int)L.NB)), HB_THREADS, hash_blocks_smem(), st>>>(
-            td, tob, R.at<uint4>(L.off_stats), runs, binel, L, ts, R.ctl, nonred, rs, R.wait_ns);
-        R.launches++;
-    }
-    R.mark(SIMULEE_STAGE_HASH, 1);
-
-    // 7. races in canonical order, split per trace
+    // 8. races in canonical order, split per trace
     R.mark(SIMULEE_STAGE_RACES, 0);
     if (sorting && want.races) {
-        k_hist_u64<<<R.grid_for(L.race_cap, 256, 4), 256, 0, st>>>(rs.keys, &R.ctl->n_races, L.race_cap, L.np_r,
-                                                                  hist + (size_t)L.p0_r * RADIX, R.ctl);
+        k_race_filter<<<R.grid_for(L.race_cap, 256, 4), 256, 0, st>>>(
+            rs.keys, rs.idx, R.at<uint64_t>(L.off_rk[1]), R.at<uint64_t>(L.off_rv[1]), L, binel, ts, R.ctl, hist);
         k_digit_bases<<<L.np_r, RADIX, 0, st>>>(hist + (size_t)L.p0_r * RADIX,
                                                 R.at<uint32_t>(L.off_dbase) + (size_t)L.p0_r * RADIX, R.ctl);
         R.launches += 2;
         size_t rk[2] = {L.off_rk[0], L.off_rk[1]}, rv[2] = {L.off_rv[0], L.off_rv[1]};
-        const int br = R.sort<uint64_t>(rk, rv, &R.ctl->n_races, L.race_cap, L.np_r, L.p0_r);
+        const int br = R.sort<uint64_t>(rk, rv, &R.ctl->n_rf, L.race_cap, L.np_r, L.p0_r, 1);
         const int gw = R.grid_for(L.race_cap, 256, 8);
         k_race_starts<<<gw, 256, 0, st>>>(R.at<uint64_t>(rk[br]), L, R.ctl, ts);
         k_write_races<<<gw, 256, 0, st>>>(R.at<uint64_t>(rk[br]), R.at<uint64_t>(rv[br]), rs.pay, L, td, ts, R.ctl);
@@ -564,7 +588,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     }
     R.mark(SIMULEE_STAGE_RACES, 1);
 
-    // 8. per-block outputs and reports
+    // 9. per-block outputs and reports
     R.mark(SIMULEE_STAGE_BLOCKS, 0);
     uint32_t *ofs_div = R.at<uint32_t>(L.off_ofs_div), *ofs_red = R.at<uint32_t>(L.off_ofs_red);
     const int gb = R.grid_for(L.NB, 256, 8);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libsimulee.so")
 OK, EINVAL, EBADTRACE, ENOMEM, ETRUNC, ETIMEOUT, ECUDA = range(7)
 FLAG_UNSORTED = 1
 PATH_AUTO, PATH_SORT, PATH_HASH = 0, 1, 2
-STAGES = ("ingest", "sort", "reduce", "races", "blocks", "hash")
+STAGES = ("ingest", "sort", "reduce", "races", "blocks", "hash", "fallback")
 
 RACE_DTYPE = np.dtype([("space", "u1"), ("scope", "u1"), ("cls", "u1"), ("pad", "u1"),
                        ("block", "<u4"), ("epoch", "<u4"), ("unit", "<u4"),

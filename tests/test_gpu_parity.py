@@ -157,7 +157,7 @@ def test_bounded_wait_reports_timeout_and_context_survives():
     bounded, the call reports ETIMEOUT, and the next call on the GPU is fine."""
     from paper_1905_01833_gb300 import simulee
     tr = tracegen.pattern(2, n_blocks=16, block_threads=256, n_epochs=16, shared_units=12288, global_units=1 << 20)
-    stalled = simulee.Checker(0, wait_limit_us=20000, test_withhold=3)
+    stalled = simulee.Checker(0, wait_limit_us=20000, test_withhold=3, path=1)   # sort path: long radix passes
     got = stalled.check(simulee.to_device(tr))
     assert got["status"] == simulee.ETIMEOUT
     stalled.close()

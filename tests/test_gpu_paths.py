@@ -1,6 +1,12 @@
-"""Both device paths against the oracle: the short-interval hash path (traces
-in simulator order, short (block, epoch) runs) and the radix-sort path (forced,
-or taken when a trace does not qualify)."""
+"""Both device paths against the oracle: the hash path (traces in simulator
+order: blocks one after another, epochs in order inside a block) and the
+radix-sort path (forced, or taken when a trace or block does not qualify).
+
+The hash path has its own limits and hand-offs, each exercised here: racy
+units resolved in place (up to 64 per run) or the run spilled to the sort
+path (more), a run with more distinct units than its table holds (the block
+falls back), epochs out of order, blocks interleaved, blocks and epochs
+without records, and runs that span several 2048-record windows."""
 import numpy as np
 import pytest
 
@@ -39,7 +45,7 @@ def test_grid_family_both_paths(path, nb, bt, ep):
 
 
 def test_long_runs_and_out_of_order_epochs_fall_back():
-    # 4096-record runs (single block, 256 threads x 16 accesses) exceed the hash path's run limit
+    # 4096-record runs (single block, 256 threads x 16 accesses) span two windows of the hash path
     tr = tracegen.c1()
     assert diff(gpu_check(tr, path=0), oracle.check(tr)) == []
     # a diverged thread's accesses carry a lower epoch inside later runs: not in (block, epoch) order
@@ -60,9 +66,91 @@ def test_batch_mixing_paths():
 
 @pytest.mark.parametrize("path", sorted(PATHS))
 def test_blocks_with_merged_epochs_take_the_sort_path(path):
-    """Half the blocks lose a barrier, so two epochs merge into one run longer
-    than the hash path's limit: those blocks go through the sort path, the
-    rest stay on the hash path, within one trace."""
+    """Half the blocks lose a barrier, so two epochs merge into one run of two
+    windows with many racy units (spilled to the sort path)."""
     tr = tracegen.pattern(21, n_blocks=16, block_threads=256, n_epochs=20, shared_units=12288,
                           global_units=1 << 20, removed_p=0.5)
     assert diff(gpu_check(tr, path=PATHS[path]), oracle.check(tr)) == []
+
+
+def _racy_units_trace(k: int, n_blocks: int = 2):
+    """Epoch 0: thread 0 writes units 0..k-1, thread 1 reads them (k racy units);
+    epoch 1: thread 2 writes units 0..k-1 (barrier 0 needed)."""
+    b = tracegen.Builder(n_blocks, 32, 4096)
+    for blk in range(n_blocks):
+        for u in range(k):
+            b.access(blk, 0, 0, u, tracegen.WRITE)
+        for u in range(k):
+            b.access(blk, 1, 0, u, tracegen.READ)
+        for u in range(k):
+            b.access(blk, 2, 1, u, tracegen.WRITE)
+    return b.set_counts(1).trace()
+
+
+@pytest.mark.parametrize("k", [1, 63, 64, 65, 300, 2500])
+def test_racy_units_in_place_and_spilled(k):
+    tr = _racy_units_trace(k)
+    want = oracle.check(tr)
+    assert len(want["races"]) == 2 * k
+    assert diff(gpu_check(tr, path=0), want) == []
+
+
+def test_run_with_more_distinct_units_than_the_table():
+    """One epoch of 1024 threads x 7 distinct units (7168 > 6144): the block
+    leaves the hash path; a second block stays on it."""
+    rng = np.random.default_rng(4)
+    b = tracegen.Builder(2, 1024, 1 << 14)
+    for e in range(2):
+        for k in range(7):
+            for t in range(1024):
+                b.access(0, t, e, (t * 7 + k + e) % (1 << 14), tracegen.WRITE if rng.random() < 0.3 else tracegen.READ)
+        for t in range(1024):
+            b.access(1, t, e, (t + 5 * e) % 2048, tracegen.WRITE)
+    tr = b.set_counts(1).trace()
+    assert diff(gpu_check(tr, path=0), oracle.check(tr)) == []
+
+
+def test_epoch_gaps_and_blocks_without_records():
+    """Block 0 has records in epochs 0, 2, 5 only; block 1 has none; block 2 has
+    one record; adjacency is only tested between consecutive epochs."""
+    b = tracegen.Builder(3, 4, 64)
+    for e in (0, 2, 5):
+        for t in range(4):
+            b.access(0, t, e, t if e != 2 else (t + 1) % 4, tracegen.WRITE)
+    b.access(2, 3, 4, 9, tracegen.READ)
+    tr = b.set_counts(6).trace()
+    assert diff(gpu_check(tr, path=0), oracle.check(tr)) == []
+
+
+def test_interleaved_blocks_and_late_epochs():
+    """Records of two blocks alternate (the trace is not block-contiguous), and
+    in a third trace one block's epochs go back (not in run order)."""
+    b = tracegen.Builder(2, 8, 32)
+    for i in range(64):
+        b.access(i % 2, i % 8, (i // 16) % 3, i % 5, i % 3 if i % 3 != 2 else tracegen.ATOMIC)
+    tr = b.set_counts(2).trace()
+    assert diff(gpu_check(tr, path=0), oracle.check(tr)) == []
+    b = tracegen.Builder(2, 8, 32)
+    for e in (0, 1, 0, 2):
+        for t in range(8):
+            b.access(0, t, e, (t + e) % 8, tracegen.WRITE if t % 2 else tracegen.READ)
+    for t in range(8):
+        b.access(1, t, 0, t, tracegen.WRITE)
+    tr = b.set_counts(2).trace()
+    assert diff(gpu_check(tr, path=0), oracle.check(tr)) == []
+
+
+@pytest.mark.parametrize("where", [0, 2047, 2048, 5000, -1])
+def test_bad_record_inside_block_ranges(where):
+    """Validation happens inside the hash path's block ranges: the first bad
+    index is reported wherever it lies (window edges included)."""
+    tr = tracegen.pattern(31, n_blocks=3, block_threads=256, n_epochs=6, shared_units=12288, global_units=1 << 16)
+    ev = tr.events.copy()
+    i = where % len(ev)
+    ev[i, 3] |= np.uint32(3 << 28)   # action 3 is invalid
+    ev[-1, 0] = np.uint32(1 << 20) | (ev[-1, 0] & np.uint32(0xFF))   # a later bad unit as well
+    bad = tracegen.Trace(ev, tr.barrier_counts, tr.n_blocks, tr.block_threads, tr.shared_units, tr.global_units,
+                         tr.max_barriers)
+    got, want = gpu_check(bad, path=0), oracle.check(bad)
+    assert diff(got, want) == []
+    assert got["bad_index"] == i
