@@ -128,14 +128,15 @@ def sig_slots(tr):
     return m
 
 
-def distinct_global_units(tr) -> int:
-    """Global units the trace touches (each one's block signature is read and written once)."""
+def global_counts(tr) -> tuple[int, int]:
+    """Global records of the trace, and the global units they touch (each unit's block signature is read and
+    written once)."""
     ev = tr.events.reshape(-1, 4)
-    g = ev[(ev[:, 3] >> 30) & 1 == 1, 0]
-    return int(np.unique(g).size) if g.size else 0
+    g = ev[((ev[:, 3] >> 30) & 1) == 1, 0]
+    return int(g.size), (int(np.unique(g).size) if g.size else 0)
 
 
-def stage_bytes(tr, sizes, path: str, n_gunits: int):
+def stage_bytes(tr, sizes, path: str, n_gl: int, n_gunits: int):
     """Algorithmic DRAM bytes of each stage for the plan that ran (stream sizes from the library).
 
     Per record: one 16-byte read. Per global record: the inter-block stream
@@ -151,7 +152,7 @@ def stage_bytes(tr, sizes, path: str, n_gunits: int):
     inter-block filter and the radix passes. reduce: one read of every sorted
     stream."""
     n = tr.n_events
-    n_s, n_g, n_x, n_gl = sizes["n_s"], sizes["n_g"], sizes["n_x"], sizes["n_global"]
+    n_s, n_g, n_x, n_xs = sizes["n_s"], sizes["n_g"], sizes["n_x"], sizes["x_slots"]
     bb, bus, bug, be = bits(tr.n_blocks), bits(tr.shared_units), bits(tr.global_units), bits(tr.max_barriers + 1)
     ks = 8 if bb + bus + be > 32 else 4
     kg = 8 if bb + bug + be > 32 else 4
@@ -164,7 +165,7 @@ def stage_bytes(tr, sizes, path: str, n_gunits: int):
         ingest=4 * tr.barrier_counts.size + 4 * sig_slots(tr) + (0 if hashed else first + routed),
         hash=first if hashed else 0,
         fallback=(16 * (n_s + n_g) + routed) if hashed else 0,
-        sort=n_gl * (kx + 8) + n_x * (kx + 8)
+        sort=n_xs * (kx + 8) + n_x * (kx + 8)
         + 2 * (n_s * np_s * (ks + 8) + n_g * np_g * (kg + 8) + n_x * np_x * (kx + 8)),
         reduce=n_s * (ks + 8) + n_g * (kg + 8) + n_x * (kx + 8),
         launches=dict(ingest=1, hash=1, fallback=1, sort=np_s + np_g + np_x + 1, reduce=3))
@@ -536,7 +537,7 @@ def main():
 
     # roofline of the dominant stage
     sizes = chk.stream_sizes()
-    sb = stage_bytes(tr, sizes, args.path, distinct_global_units(tr))
+    sb = stage_bytes(tr, sizes, args.path, *global_counts(tr))
     peak, peak_src = peaks()
     cand = [k for k in ("ingest", "hash", "fallback", "sort", "reduce") if sb[k] > 0]
     dom = max(cand, key=lambda k: stage_ms[k])

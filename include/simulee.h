@@ -259,9 +259,9 @@ enum {
 uint32_t simulee_last_launches(const simulee_ctx *ctx);
 /* Queues on `stream` a copy of five uint32 into dev_out (device memory), for the last check that
    used workspace `ws`: the record counts of the shared-intra, global-intra and global-inter streams
-   that went through the radix sort, the number of race records, and the number of global records
-   before the inter-block filter dropped those of units touched by one block only (records checked
-   by the short-interval hash path are the rest). For measuring algorithmic bytes. */
+   that went through the radix sort, the number of staged race records, and the number of
+   inter-block stream slots written before the inter-block filter (every global record, plus slots
+   the hash path reserved and left unused). For measuring algorithmic bytes. */
 simulee_status simulee_stream_sizes(simulee_ctx *ctx, const void *ws, uint32_t *dev_out, void *stream);
 simulee_status simulee_set_stage_events(simulee_ctx *ctx, void *const *events, uint32_t n_events);
 

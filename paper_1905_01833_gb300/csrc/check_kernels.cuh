@@ -79,10 +79,13 @@ __device__ __forceinline__ void hist_add(uint32_t *sh, uint64_t key, uint32_t np
 
 // ---------------------------------------------------------------------------
 // Block signatures of global units. An inter-block race needs a unit touched
-// by two different blocks. While ingesting, each global record marks its
-// unit's slot with its (batch-wide) block + 1, and with SIG_MULTI when the
-// slot already holds another block. Inter-block records whose slot never got
-// SIG_MULTI touch a unit of one block only and are dropped before sorting.
+// by two different blocks. Each global record marks its unit's slot; records
+// whose slot shows a single block are dropped before the inter-block sort.
+// When every trace has at most 2^15 blocks the slot is the OR of
+// (b | ~b << 15) over the trace-local blocks b that touched it: it shows two
+// or more blocks exactly when its two 15-bit halves share a bit, and a mark is
+// one atomicOr whose result nobody waits for. Otherwise the slot holds the
+// batch-wide block + 1, and SIG_MULTI once another block touches it.
 // With several traces the slot is a hash of (trace, unit); a collision can
 // only keep extra records, never drop a needed one.
 // ---------------------------------------------------------------------------
@@ -93,12 +96,21 @@ __device__ __forceinline__ uint64_t sig_slot(const Layout &L, uint32_t t, uint32
     return (mix32((t * 0x9E3779B1u) ^ unit) ^ ((uint64_t)t << 7)) & (L.sig_slots - 1);
 }
 
-__device__ __forceinline__ void sig_mark(uint32_t *sig, uint64_t slot, uint32_t block) {
+__device__ __forceinline__ void sig_mark(const Layout &L, uint32_t *sig, uint64_t slot, uint32_t local_block,
+                                         uint32_t block) {
+    if (L.sig_or) {
+        atomicOr(&sig[slot], (local_block & 0x7FFFu) | ((~local_block & 0x7FFFu) << 15));
+        return;
+    }
     const uint32_t me = block + 1u;
     uint32_t cur = *(volatile uint32_t *)&sig[slot];
     if (cur == me || (cur & SIG_MULTI)) return;
     if (cur == 0u) cur = atomicCAS(&sig[slot], 0u, me);
     if (cur != 0u && cur != me && !(cur & SIG_MULTI)) atomicOr(&sig[slot], SIG_MULTI);
+}
+
+__device__ __forceinline__ bool sig_multi(const Layout &L, uint32_t v) {
+    return L.sig_or ? ((v & (v >> 15) & 0x7FFFu) != 0u) : (v & SIG_MULTI) != 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -235,7 +247,7 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
                 const uint64_t sb = (uint64_t)d.block_off + blk;
                 if (bS) hist_add(hs, shl(sb, L.bus + L.be) | shl(u, L.be) | ep, np_s, isS, bS);
                 if (bG) hist_add(hg, shl(sb, L.bug + L.be) | shl(u, L.be) | ep, np_g, isG, bG);
-                if (isX) sig_mark(sig, sig_slot(L, t, u), (uint32_t)sb);
+                if (isX) sig_mark(L, sig, sig_slot(L, t, u), blk, (uint32_t)sb);
             }
         }
         if (MODE != IN_VALIDATE) {
@@ -335,7 +347,8 @@ __global__ void k_fallback_tiles(const TraceDesc *__restrict__ td, Layout L, con
 
 // Keep the inter-block records whose unit was touched by two or more blocks;
 // build the digit histograms of the records kept. The order of kept records
-// does not matter (the sort that follows groups them by unit).
+// does not matter (the sort that follows groups them by unit). Slots the hash
+// path reserved but did not use carry an invalid action and are dropped.
 template <class KX>
 __global__ void __launch_bounds__(256)
 k_x_filter(const KX *__restrict__ xk, const uint64_t *__restrict__ xv, KX *yk, uint64_t *yv, const uint32_t *sig,
@@ -346,7 +359,7 @@ k_x_filter(const KX *__restrict__ xk, const uint64_t *__restrict__ xv, KX *yk, u
     const int tid = threadIdx.x;
     for (int i = tid; i < 8 * RADIX; i += 256) sh[i] = 0;
     __syncthreads();
-    const uint64_t n = *(volatile unsigned int *)&ctl->n_x;
+    const uint64_t n = min((uint64_t)*(volatile unsigned int *)&ctl->n_x, L.x_cap);
     const uint64_t umask = (L.bug >= 64) ? ~0ull : ((1ull << L.bug) - 1);
     for (uint64_t base = (uint64_t)blockIdx.x * 256; base < n; base += (uint64_t)gridDim.x * 256) {
         const uint64_t i = base + tid;
@@ -357,9 +370,12 @@ k_x_filter(const KX *__restrict__ xk, const uint64_t *__restrict__ xv, KX *yk, u
             k = xk[i];
             const uint64_t kk = (uint64_t)k;
             const uint32_t t = (uint32_t)(L.bug >= 64 ? 0 : (kk >> L.bug)), unit = (uint32_t)(kk & umask);
-            keep = (sig[sig_slot(L, t, unit)] & SIG_MULTI) != 0;
+            keep = sig_multi(L, sig[sig_slot(L, t, unit)]);
             if (keep) {
                 v = xv[i];
+                keep = payload_act(v) != 3u;
+            }
+            if (keep) {
                 for (uint32_t q = 0; q < L.np_x; q++) atomicAdd(&sh[q * RADIX + digit_of(kk, q)], 1u);
             }
         }

@@ -106,6 +106,8 @@ struct Layout {
     size_t off_sig;                  // block signature per global unit (or unit hash)
     uint64_t sig_slots;              // entries of the signature table (0: no global memory)
     uint32_t sig_direct;             // one trace: the table is indexed by unit itself
+    uint32_t sig_or;                 // signatures are ORs of (block | ~block << 15)
+    uint64_t x_cap;                  // elements of each inter-block stream buffer
     size_t off_ctl, off_td, off_ts, off_tob, off_stats, off_nonred, off_gridnr, off_gridhas, off_cnt_div,
         off_cnt_red, off_ofs_div, off_ofs_red, off_hist, off_dbase, off_status, off_rank, off_p2v;
     size_t off_sk[2], off_sv[2], off_gk[2], off_gv[2], off_xk[2], off_xv[2];

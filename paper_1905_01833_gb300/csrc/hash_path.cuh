@@ -44,6 +44,7 @@ constexpr int HB_RSLOTS = 128;                      // racy-unit table (load <= 
 constexpr uint32_t HB_EMPTY = 0xFFFFFFFFu;
 constexpr uint32_t HB_NONE = 0xFFFFFFFFu;           // no epoch
 constexpr uint32_t HB_POS_LIMIT = 1u << 22;         // run positions in a pool item (22 bits)
+constexpr uint32_t HB_XCH = 256;                    // inter-block slots a warp reserves at a time
 
 // shared memory: owner summaries and keys of two run tables, the creation
 // lists of both, the racy-unit table and its top-2 pool
@@ -135,6 +136,16 @@ __global__ void k_block_ranges(const TraceDesc *__restrict__ td, const uint32_t 
     }
 }
 
+// one unused inter-block slot: key 0 with an invalid action, dropped by the filter
+template <class KX>
+__device__ __forceinline__ void hb_x_fill(KX *xk, uint64_t *xv, uint32_t from, uint32_t to, uint64_t cap, int lane) {
+    for (uint32_t o = from + lane; o < to; o += 32)
+        if (o < cap) {
+            xk[o] = (KX)0;
+            xv[o] = ~0ull;
+        }
+}
+
 template <class KX>
 __global__ void __launch_bounds__(HB_THREADS, 1)
 k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob, const uint32_t *__restrict__ bstart,
@@ -146,7 +157,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
     uint16_t *list = reinterpret_cast<uint16_t *>(key + 2 * HB_SLOTS);     // [2][HB_CAP]
     uint32_t *rkey = reinterpret_cast<uint32_t *>(list + 2 * HB_CAP);      // [HB_RSLOTS]
     uint32_t *pool = rkey + HB_RSLOTS;                                     // [HB_RSLOTS][first 3, second 3]
-    __shared__ uint32_t s_blk, s_cnt[2], s_flag, s_minpend, s_lo, s_hi, s_nracy;
+    __shared__ uint32_t s_blk, s_cnt[2], s_flag, s_minpend, s_hi, s_nracy, s_needed;
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t lt = lanemask_lt();
     for (int i = tid; i < 2 * HB_SLOTS; i += HB_THREADS) {
@@ -158,11 +169,13 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         s_cnt[0] = s_cnt[1] = 0;
         s_flag = 0;
         s_minpend = HB_NONE;
-        s_lo = 0xFFFFFFFFu;
         s_hi = 0;
         s_nracy = 0;
+        s_needed = 0;
     }
-        for (;;) {
+    const uint64_t xcap = L.x_cap;
+    uint32_t xpos = 0, xend = 0;   // this warp's reserved inter-block slots [xpos, xend)
+    for (;;) {
         __syncthreads();
         if (tid == 0) s_blk = atomicAdd(&ctl->hb_next, 1u);
         __syncthreads();
@@ -173,17 +186,19 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         // uniform: only hash-path traces whose barrier counts are valid (otherwise nothing is reported)
         if (!d.hash_ok || *(volatile unsigned long long *)&ts[t].bad_cnt) continue;
         const uint32_t lb = b - d.block_off;
-        const uint64_t s0 = bstart[b], s1 = (lb + 1 < d.nb) ? (uint64_t)bstart[b + 1] : d.n;
+        const uint32_t s0 = bstart[b], s1 = (lb + 1 < d.nb) ? bstart[b + 1] : (uint32_t)d.n;
         if (s0 >= s1) continue;   // a block without records: no runs
         const uint4 *ev = d.events;
-        const bool pad = d.nb <= (1u << 20);
+        const uint32_t *cnts = d.counts;
+        const uint32_t nb = d.nb, bt = d.bt, su = d.su, gu = d.gu, maxb = d.maxb;
+        const bool pad = nb <= (1u << 20);
 
         // ---- window: records wbase + j * HB_THREADS + tid, j = 0, 1 --------------------------
-        uint64_t wbase = s0;
+        uint32_t wbase = s0;
         uint4 cur[2], nxt[2];
 #pragma unroll
         for (int j = 0; j < 2; j++) {
-            const uint64_t i0 = s0 + j * HB_THREADS + tid, i1 = i0 + HB_CH;
+            const uint32_t i0 = s0 + j * HB_THREADS + tid, i1 = i0 + HB_CH;
             cur[j] = i0 < s1 ? ev[i0] : make_uint4(0, 0, 0, 0);
             nxt[j] = i1 < s1 ? ev[i1] : make_uint4(0, 0, 0, 0);
         }
@@ -193,38 +208,56 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             bool stopme = false, isx[2];
 #pragma unroll
             for (int j = 0; j < 2; j++) {
-                const uint64_t idx = wbase + j * HB_THREADS + tid;
+                const uint32_t idx = wbase + j * HB_THREADS + tid;
                 const bool in = idx < s1;
                 const uint4 e = cur[j];
                 const uint32_t u = e.x, vo = e.y, blk = e.z, w3 = e.w;
                 const uint32_t tt = w3 & 0xFFFFu, ep = (w3 >> 16) & 0xFFFu, act = (w3 >> 28) & 3u;
                 const uint32_t sp = (w3 >> 30) & 1u, resv = w3 >> 31;
-                uint32_t pvo = __shfl_up_sync(0xFFFFFFFFu, vo, 1);
-                if (lane == 0) pvo = (in && idx > 0) ? ev[idx - 1].y : 0u;
-                bool ok = in && blk < d.nb && tt < d.bt && act != 3u && resv == 0u && (sp ? u < d.gu : u < d.su);
-                if (ok && ep > d.counts[(uint64_t)blk * d.bt + tt]) ok = false;
+                // the record before: its visit order (strictly increasing) and, in the same block, its epoch
+                uint32_t pvo = __shfl_up_sync(0xFFFFFFFFu, vo, 1), pw = __shfl_up_sync(0xFFFFFFFFu, w3, 1);
+                uint32_t pz = __shfl_up_sync(0xFFFFFFFFu, blk, 1);
+                if (lane == 0) {
+                    const uint4 p = (in && idx > 0) ? ev[idx - 1] : make_uint4(0, 0, 0xFFFFFFFFu, 0);
+                    pvo = p.y;
+                    pw = p.w;
+                    pz = p.z;
+                }
+                bool ok = in && blk < nb && tt < bt && act != 3u && resv == 0u && (sp ? u < gu : u < su);
+                if (ok && ep > cnts[blk * bt + tt]) ok = false;
                 if (in && idx > 0 && vo <= pvo) ok = false;
                 if (in && !ok) atomicMax(&ts[t].bad_rec, ~(unsigned long long)idx);
                 if (ok && blk != lb) atomicOr(&ts[t].inel, 1u);   // the trace is not block-contiguous
                 if (in && (!ok || blk != lb)) stopme = true;
+                if (ok && pz == blk && ((pw >> 16) & 0xFFFu) > ep) stopme = true;   // epochs go back
                 if (ok && blk == lb) pb |= 1u << j;
-                isx[j] = ok && sp == 1u && ep <= d.maxb;
+                isx[j] = ok && sp == 1u && ep <= maxb;
             }
             const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, isx[0]), b1 = __ballot_sync(0xFFFFFFFFu, isx[1]);
             const uint32_t tot = __popc(b0) + __popc(b1);
-            uint32_t xb = 0;
-            if (lane == 0 && tot) xb = atomicAdd(&ctl->n_x, tot);
-            xb = __shfl_sync(0xFFFFFFFFu, xb, 0);
+            if (tot) {
+                if (xpos + tot > xend) {   // warp-uniform: a fresh chunk of slots for this warp
+                    hb_x_fill(xk, xv, xpos, xend, xcap, lane);
+                    uint32_t nbase = 0;
+                    if (lane == 0) nbase = atomicAdd(&ctl->n_x, (uint32_t)HB_XCH);
+                    nbase = __shfl_sync(0xFFFFFFFFu, nbase, 0);
+                    xpos = nbase;
+                    xend = nbase + HB_XCH;
+                }
 #pragma unroll
-            for (int j = 0; j < 2; j++) {
-                if (!isx[j]) continue;
-                const uint4 e = cur[j];
-                const uint32_t o = xb + (j ? __popc(b0) + __popc(b1 & lt) : __popc(b0 & lt));
-                const uint32_t blk = e.z, w3 = e.w, act = (w3 >> 28) & 3u;
-                const uint32_t xo = pad ? ((blk << 10) | (w3 & 0x3FFu)) : blk * d.bt + (w3 & 0xFFFFu);
-                xk[o] = (KX)(shl(t, L.bug) | e.x);
-                xv[o] = make_payload(act, xo, e.y);
-                sig_mark(sig, sig_slot(L, t, e.x), d.block_off + blk);
+                for (int j = 0; j < 2; j++) {
+                    if (!isx[j]) continue;
+                    const uint4 e = cur[j];
+                    const uint32_t o = xpos + (j ? __popc(b0) + __popc(b1 & lt) : __popc(b0 & lt));
+                    const uint32_t blk = e.z, w3 = e.w, act = (w3 >> 28) & 3u;
+                    const uint32_t xo = pad ? ((blk << 10) | (w3 & 0x3FFu)) : blk * bt + (w3 & 0xFFFFu);
+                    if (o < xcap) {
+                        xk[o] = (KX)(shl(t, L.bug) | e.x);
+                        xv[o] = make_payload(act, xo, e.y);
+                    }
+                    sig_mark(L, sig, sig_slot(L, t, e.x), blk, d.block_off + blk);
+                }
+                xpos += tot;
             }
             if (stopme) s_flag = 1u;
             return pb;
@@ -234,19 +267,21 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
 #pragma unroll
             for (int j = 0; j < 2; j++) {
                 cur[j] = nxt[j];
-                const uint64_t i1 = wbase + HB_CH + j * HB_THREADS + tid;
+                const uint32_t i1 = wbase + HB_CH + j * HB_THREADS + tid;
                 nxt[j] = i1 < s1 ? ev[i1] : make_uint4(0, 0, 0, 0);
             }
         };
         uint32_t pend = activate();
 
         uint32_t e = (ev[s0].w >> 16) & 0xFFFu;   // epoch of the block's first record
-        uint32_t prev_e = HB_NONE, par = 0, cnt_prev = 0;
+        uint32_t prev_e = HB_NONE, par = 0, cnt_prev = 0, run_start = s0;
         bool hashing = true, full_reset = false;
         for (;;) {
+            uint32_t *kt = key + par * HB_SLOTS;
+            uint64_t *ot = own + par * HB_SLOTS;
             // ---- 1. insert run e: its records in this window and, while it continues, the next
             for (;;) {
-                uint32_t lo = 0xFFFFFFFFu, hi = 0, mp = HB_NONE;
+                uint32_t hi = 0, mp = HB_NONE;
 #pragma unroll
                 for (int j = 0; j < 2; j++) {
                     const uint4 r = cur[j];
@@ -258,10 +293,10 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                         const uint32_t k = (r.x << 1) | ((r.w >> 30) & 1u);
                         uint32_t h = hb_hash(k);
                         for (int probe = 0; probe < HB_SLOTS; probe++) {
-                            const uint32_t c = key[par * HB_SLOTS + h];
+                            const uint32_t c = kt[h];
                             if (c == k) { s = h; break; }
                             if (c == HB_EMPTY) {
-                                const uint32_t old = atomicCAS(&key[par * HB_SLOTS + h], HB_EMPTY, k);
+                                const uint32_t old = atomicCAS(&kt[h], HB_EMPTY, k);
                                 if (old == HB_EMPTY) { s = h; created = true; break; }
                                 if (old == k) { s = h; break; }
                             }
@@ -270,21 +305,20 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                         if (s == HB_EMPTY) {
                             s_flag = 2u;   // table full
                         } else {
-                            atomicOr(reinterpret_cast<unsigned long long *>(&own[par * HB_SLOTS + s]),
+                            atomicOr(reinterpret_cast<unsigned long long *>(&ot[s]),
                                      (unsigned long long)hb_own_bits((r.w >> 28) & 3u, r.w & 0x3FFu));
                         }
-                        const uint32_t idx = (uint32_t)(wbase + j * HB_THREADS + tid);
-                        lo = min(lo, idx);
-                        hi = max(hi, idx);
+                        hi = wbase + j * HB_THREADS + tid;
                         pend &= ~(1u << j);
                     } else if ((pend >> j) & 1u) {
                         mp = min(mp, ep);
                     }
                     const uint32_t cm = __ballot_sync(0xFFFFFFFFu, created);
                     if (cm) {
+                        const int leader = __ffs(cm) - 1;
                         uint32_t base = 0;
-                        if (lane == __ffs(cm) - 1) base = atomicAdd(&s_cnt[par], (uint32_t)__popc(cm));
-                        base = __shfl_sync(0xFFFFFFFFu, base, __ffs(cm) - 1);
+                        if (lane == leader) base = atomicAdd(&s_cnt[par], (uint32_t)__popc(cm));
+                        base = __shfl_sync(0xFFFFFFFFu, base, leader);
                         if (created) {
                             const uint32_t pos = base + __popc(cm & lt);
                             if (pos < HB_CAP) list[par * HB_CAP + pos] = (uint16_t)s;
@@ -292,19 +326,15 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                         }
                     }
                 }
-                lo = __reduce_min_sync(0xFFFFFFFFu, lo);
                 hi = __reduce_max_sync(0xFFFFFFFFu, hi);
                 mp = __reduce_min_sync(0xFFFFFFFFu, mp);
                 if (lane == 0) {
-                    if (lo != 0xFFFFFFFFu) {
-                        atomicMin(&s_lo, lo);
-                        atomicMax(&s_hi, hi);
-                    }
+                    if (hi) atomicMax(&s_hi, hi);
                     if (mp != HB_NONE) atomicMin(&s_minpend, mp);
                 }
                 // the run continues into the next window when that window exists and this one
                 // ends with a record of the run
-                const uint64_t wend = min(wbase + HB_CH, s1);
+                const uint32_t wend = min(wbase + (uint32_t)HB_CH, s1);
                 if (wend < s1) {
                     const uint4 last = ev[wend - 1];
                     if (last.z == lb && ((last.w >> 16) & 0xFFFu) == e) {
@@ -321,19 +351,20 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             __syncthreads();   // A: the run's inserts are complete
             const uint32_t flag = s_flag, next = s_minpend;
             const uint32_t cnt = min(s_cnt[par], (uint32_t)HB_CAP);
-            const uint32_t lo = s_lo, hi = s_hi;
+            const uint32_t lo = run_start, hi = max(s_hi, run_start);
             const bool stop = flag != 0u || (next != HB_NONE && next <= e);
             bool needed = false;
             uint32_t rmask = 0;   // bit m: this thread's list entry tid + m * HB_THREADS went to the racy table
             uint64_t rq = 0;      // their racy-table slots, 7 bits each
             if (!stop) {
                 const bool adj = prev_e != HB_NONE && prev_e + 1 == e;
-                const uint32_t pp = par ^ 1u;
+                const uint32_t *pkt = key + (par ^ 1u) * HB_SLOTS;
+                const uint64_t *pot = own + (par ^ 1u) * HB_SLOTS;
 #pragma unroll 1
                 for (uint32_t i = tid, m = 0; i < cnt; i += HB_THREADS, m++) {
                     const uint32_t s = list[par * HB_CAP + i];
-                    const uint64_t o = own[par * HB_SLOTS + s];
-                    const uint32_t k = key[par * HB_SLOTS + s];
+                    const uint64_t o = ot[s];
+                    const uint32_t k = kt[s];
                     if (hb_racy(o)) {
                         const uint32_t r = atomicAdd(&s_nracy, 1u);
                         if (r < HB_POOL) {
@@ -351,17 +382,19 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                             }
                         }
                     }
-                    if (adj && !needed) {
+                    // adjacency: until some thread has found barrier e-1 needed
+                    if (adj && !needed && !*(volatile uint32_t *)&s_needed) {
                         uint32_t h = hb_hash(k);
                         for (int probe = 0; probe < HB_SLOTS; probe++) {
-                            const uint32_t c = key[pp * HB_SLOTS + h];
+                            const uint32_t c = pkt[h];
                             if (c == HB_EMPTY) break;
                             if (c == k) {
-                                needed = hb_cross(own[pp * HB_SLOTS + h], o);
+                                needed = hb_cross(pot[h], o);
                                 break;
                             }
                             h = (h + 1) & (HB_SLOTS - 1);
                         }
+                        if (needed) s_needed = 1u;
                     }
                 }
             }
@@ -372,19 +405,19 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                     // too many racy units: the sort path computes this run's races
                     if (tid == 0) {
                         atomicOr(&spill[(uint64_t)b * L.swords + (e >> 5)], 1u << (e & 31));
-                        for (uint64_t tl = lo / IN_TILE; tl <= hi / IN_TILE; tl++) tflag[d.tile_off + tl] = 1u;
+                        for (uint32_t tl = lo / IN_TILE; tl <= hi / IN_TILE; tl++) tflag[d.tile_off + tl] = 1u;
                     }
                 } else {
                     // exact lowest pairs of the racy units: first, then first of another thread, per category
 #pragma unroll 1
                     for (int pass = 0; pass < 2; pass++) {
-                        for (uint64_t i = lo + tid; i <= hi; i += HB_THREADS) {
+                        for (uint32_t i = lo + tid; i <= hi; i += HB_THREADS) {
                             const uint4 r = ev[i];
                             if (r.z != lb || ((r.w >> 16) & 0xFFFu) != e) continue;
                             const uint32_t k = (r.x << 1) | ((r.w >> 30) & 1u);
                             const uint32_t c = (r.w >> 28) & 3u, tt = r.w & 0x3FFu;
                             if (c == 3u) continue;
-                            const uint32_t item = ((uint32_t)(i - lo) << 10) | tt;
+                            const uint32_t item = ((i - lo) << 10) | tt;
                             uint32_t q = hb_rhash(k);
                             for (int probe = 0; probe < HB_RSLOTS; probe++) {
                                 const uint32_t rk = rkey[q];
@@ -416,8 +449,8 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                             uint64_t p, q2;
                             if (!lowest_pair(S, cls, ownt, p, q2)) continue;
                             const uint32_t vp = ev[lo + item_pos(p)].y, vq = ev[lo + item_pos(q2)].y;
-                            const uint64_t pi = ((uint64_t)vp << 32) | (uint32_t)((uint64_t)lb * d.bt + item_gtid(p));
-                            const uint64_t qi = ((uint64_t)vq << 32) | (uint32_t)((uint64_t)lb * d.bt + item_gtid(q2));
+                            const uint64_t pi = ((uint64_t)vp << 32) | (lb * bt + item_gtid(p));
+                            const uint64_t qi = ((uint64_t)vq << 32) | (lb * bt + item_gtid(q2));
                             emit_race(rs, ctl, t, race_key(L, t, k & 1u, 0u, b, e, k >> 1, cls), pi, qi, true);
                         }
                     }
@@ -442,8 +475,8 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             if (tid == 0) {
                 s_cnt[par ^ 1u] = 0;
                 s_minpend = HB_NONE;
-                s_lo = 0xFFFFFFFFu;
                 s_hi = 0;
+                s_needed = 0;
             }
             __syncthreads();   // E
             if (tid == 0) s_nracy = 0;
@@ -457,10 +490,11 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             prev_e = e;
             cnt_prev = cnt;
             par ^= 1u;
+            run_start = hi + 1;
             if (next == HB_NONE) {
                 // every record of the window is in; a record range that goes on means the block's
                 // records are not in run order
-                if (min(wbase + HB_CH, s1) < s1) {
+                if (min(wbase + (uint32_t)HB_CH, s1) < s1) {
                     if (tid == 0) atomicOr(&binel[b], 1u);
                     hashing = false;
                     full_reset = true;
@@ -496,10 +530,10 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         }
         if (tid == 0) {
             s_minpend = HB_NONE;
-            s_lo = 0xFFFFFFFFu;
             s_hi = 0;
         }
     }
+    hb_x_fill(xk, xv, xpos, xend, xcap, lane);   // the unused tail of this warp's last chunk
 }
 
 }  // namespace simk

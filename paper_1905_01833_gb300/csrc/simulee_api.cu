@@ -71,11 +71,11 @@ simulee_status check_trace_args(const simulee_trace *t) {
 }
 
 // Batch-wide bit layouts, pass counts and workspace offsets (a single trace is a batch of one).
-simulee_status make_layout(const simulee_trace *tr, uint32_t T, Layout &L) {
+simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout &L) {
     memset(&L, 0, sizeof L);
     if (T == 0 || T > kMaxTraces) return SIMULEE_EINVAL;
     uint64_t n = 0, nb = 0, tiles = 0;
-    uint32_t maxb = 0, su = 0, gu = 0, uns = 0;
+    uint32_t maxb = 0, su = 0, gu = 0, uns = 0, maxnb = 0;
     for (uint32_t i = 0; i < T; i++) {
         const simulee_trace &t = tr[i];
         if (t.n_blocks == 0 || t.block_threads == 0 || t.block_threads > 1024 || t.max_barriers > 4095 ||
@@ -85,6 +85,7 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, Layout &L) {
         nb += t.n_blocks;
         tiles += (t.n_events + IN_TILE - 1) / IN_TILE;
         maxb = std::max(maxb, t.max_barriers);
+        maxnb = std::max(maxnb, t.n_blocks);
         su = std::max(su, t.shared_units);
         gu = std::max(gu, t.global_units);
         uns |= t.flags & SIMULEE_FLAG_UNSORTED;
@@ -156,6 +157,7 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, Layout &L) {
             while (m < L.n && m < (1ull << 28)) m <<= 1;
             L.sig_slots = m;
         }
+        L.sig_or = maxnb <= (1u << 15) ? 1u : 0u;
         L.off_sig = take(L.sig_slots * 4);
     }
     L.off_td = take((size_t)T * sizeof(TraceDesc));
@@ -172,13 +174,18 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, Layout &L) {
         L.off_p2v = take(n1 * 4);
     }
     const size_t ks = L.wide_s ? 8 : 4, kg = L.wide_g ? 8 : 4, kx = L.wide_x ? 8 : 4;
+    // inter-block stream: every global record, plus the unused tails of the chunks of slots
+    // the hash path's warps reserve (one partial chunk per warp that reserved any)
+    const uint64_t hash_warps = (uint64_t)std::max(1, std::min<int>(sms, (int)std::max<uint32_t>(L.NB, 1))) *
+                                (HB_THREADS / 32);
+    L.x_cap = n1 + std::min<uint64_t>(hash_warps, n1) * HB_XCH;
     for (int i = 0; i < 2; i++) {
         L.off_sk[i] = take(n1 * ks);
         L.off_sv[i] = take(n1 * 8);
         L.off_gk[i] = take(n1 * kg);
         L.off_gv[i] = take(n1 * 8);
-        L.off_xk[i] = take(n1 * kx);
-        L.off_xv[i] = take(n1 * 8);
+        L.off_xk[i] = take(L.x_cap * kx);
+        L.off_xv[i] = take(L.x_cap * 8);
         L.off_rk[i] = take(L.race_cap * 8);
         L.off_rv[i] = take(L.race_cap * 8);
     }
@@ -349,7 +356,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     if (((uintptr_t)ws & 255u) != 0) return SIMULEE_EINVAL;
     Run R;
     R.ctx = ctx;
-    simulee_status s = make_layout(traces, T, R.L);
+    simulee_status s = make_layout(traces, T, ctx->sms, R.L);
     if (s != SIMULEE_OK) return s;
     if (ws_bytes < R.L.total) return SIMULEE_ENOMEM;
     std::vector<TraceDesc> hdesc;
@@ -657,7 +664,7 @@ simulee_status simulee_destroy(simulee_ctx *ctx) {
 simulee_status simulee_workspace_size(simulee_ctx *ctx, const simulee_trace *trace, size_t *bytes) {
     if (!ctx || !trace || !bytes) return SIMULEE_EINVAL;
     Layout L;
-    const simulee_status s = make_layout(trace, 1, L);
+    const simulee_status s = make_layout(trace, 1, ctx->sms, L);
     if (s != SIMULEE_OK) return s;
     *bytes = L.total;
     return SIMULEE_OK;
@@ -703,7 +710,7 @@ simulee_status simulee_batch_workspace_size(simulee_ctx *ctx, const simulee_trac
                                             size_t *bytes) {
     if (!ctx || !traces || !bytes || n_traces == 0) return SIMULEE_EINVAL;
     Layout L;
-    const simulee_status s = make_layout(traces, n_traces, L);
+    const simulee_status s = make_layout(traces, n_traces, ctx->sms, L);
     if (s != SIMULEE_OK) return s;
     *bytes = L.total;
     return SIMULEE_OK;

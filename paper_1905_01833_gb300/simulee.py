@@ -188,7 +188,8 @@ class Checker:
         _check(lib().simulee_stream_sizes(self.h, ctypes.c_void_p(self._ws.data_ptr()), ctypes.c_void_p(out.data_ptr()),
                                           _stream_ptr(stream)), "simulee_stream_sizes")
         v = [int(x) for x in out.cpu().tolist()]
-        return dict(n_s=v[0], n_g=v[1], n_x=v[2], n_races=v[3], n_global=v[4])
+        # x_slots: inter-block stream slots written (global records, plus unused reserved slots on the hash path)
+        return dict(n_s=v[0], n_g=v[1], n_x=v[2], n_races=v[3], x_slots=v[4])
 
     def workspace_size(self, dt: DeviceTrace) -> int:
         n = ctypes.c_size_t()
