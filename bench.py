@@ -398,6 +398,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--path", choices=["auto", "sort"], default="auto")
+    ap.add_argument("--hash-shape", type=int, choices=[0, 1, 2], default=0,
+                    help="hash path CTAs: 0 chosen per call, 1 one 1024-thread CTA per SM, 2 two 512-thread CTAs")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--oracle-blocks", type=int, default=256)
     ap.add_argument("--ref-blocks", type=int, default=32)
@@ -436,7 +438,8 @@ def main():
 
     tr = make_trace(rank, args.blocks)
     dt = simulee.to_device(tr, f"cuda:{local}")
-    chk = simulee.Checker(local, path=simulee.PATH_SORT if args.path == "sort" else simulee.PATH_AUTO)
+    chk = simulee.Checker(local, path=simulee.PATH_SORT if args.path == "sort" else simulee.PATH_AUTO,
+                          hash_shape=args.hash_shape)
     ws = chk.workspace(chk.workspace_size(dt))
     caps = dict(races_cap=4_000_000, div_cap=tr.n_blocks, red_cap=tr.n_blocks * tr.max_barriers,
                 grid_cap=tr.max_barriers)

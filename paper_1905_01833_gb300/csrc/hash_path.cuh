@@ -17,11 +17,12 @@
 // holds a conflicting pair inside the run (Theorem 1: owners differ, one
 // access modifies, not both atomic), and (b) whether it conflicts with the
 // same unit in the previous epoch's table (barrier e-1 needed, Algorithm 5's
-// adjacency test). For the few units of (a) the exact lowest pair of each
-// class comes from two atomicMin passes over the run's records into a small
-// pool (the top-2 summary of common.cuh); a run with more racy units than the
-// pool holds is marked for the sort path instead ("spilled"), which then
-// computes its races exactly.
+// adjacency test). For the units of (a) the exact lowest pair of each class
+// comes from two atomicMin passes over the run's records into a pool of top-2
+// summaries (common.cuh) laid over the previous run's table, which is free
+// once the adjacency test is done; a run with more racy units than that pool
+// holds (a third of the table's entries) is marked for the sort path instead
+// ("spilled"), which then computes its races exactly.
 //
 // A block falls back to the sort path entirely ("binel") when its records are
 // not in epoch order, a run has more distinct units than the table holds, or a
@@ -34,23 +35,34 @@
 
 namespace simk {
 
-constexpr int HB_THREADS = 1024;
-constexpr int HB_CH = 2 * HB_THREADS;               // records per window
-constexpr int HB_SLOTS = 8192;                      // entries per run table
-constexpr int HB_HASH_SHIFT = 19;                   // 32 - log2(HB_SLOTS)
-constexpr int HB_CAP = 6144;                        // distinct units per run (load <= 3/4)
-constexpr int HB_POOL = 64;                         // racy units resolved in place per run
-constexpr int HB_RSLOTS = 128;                      // racy-unit table (load <= 1/2)
+// Two shapes: one CTA of 1024 threads per SM with 8192-entry run tables, or
+// two CTAs of 512 threads per SM with 4096-entry tables (so that one CTA's
+// barriers overlap the other's work). A run may hold up to 3/4 of a table's
+// entries in distinct units.
+template <int THREADS, int SLOTS>
+struct HbShape {
+    static constexpr int threads = THREADS;
+    static constexpr int slots = SLOTS;
+    static constexpr int ctas_per_sm = 1024 / THREADS;
+    static constexpr int window = 2 * THREADS;        // records per window (two per thread)
+    static constexpr int cap = SLOTS / 4 * 3;         // distinct units per run
+    static constexpr int shift = SLOTS == 8192 ? 19 : 20;   // 32 - log2(SLOTS)
+    static constexpr int pool = SLOTS / 3;            // racy units per run (24-byte summaries in 8-byte entries)
+};
+using HbLarge = HbShape<1024, 8192>;
+using HbSmall = HbShape<512, 4096>;
+static_assert((HbLarge::cap + HbLarge::threads - 1) / HbLarge::threads <= 32, "list entries per thread");
+static_assert((HbSmall::cap + HbSmall::threads - 1) / HbSmall::threads <= 32, "list entries per thread");
+
 constexpr uint32_t HB_EMPTY = 0xFFFFFFFFu;
 constexpr uint32_t HB_NONE = 0xFFFFFFFFu;           // no epoch
 constexpr uint32_t HB_POS_LIMIT = 1u << 22;         // run positions in a pool item (22 bits)
 constexpr uint32_t HB_XCH = 256;                    // inter-block slots a warp reserves at a time
 
-// shared memory: owner summaries and keys of two run tables, the creation
-// lists of both, the racy-unit table and its top-2 pool
+// shared memory: owner summaries and keys of two run tables and the creation lists of both
+template <class SH>
 constexpr size_t hash_blocks_smem() {
-    return (size_t)HB_SLOTS * 8 * 2 + (size_t)HB_SLOTS * 4 * 2 + (size_t)HB_CAP * 2 * 2 + (size_t)HB_RSLOTS * 4 +
-           (size_t)HB_RSLOTS * 6 * 4;
+    return (size_t)SH::slots * 8 * 2 + (size_t)SH::slots * 4 * 2 + (size_t)SH::cap * 2 * 2;
 }
 
 // owner summary field of category c: OR(tid) | OR(~tid) << 10
@@ -85,8 +97,8 @@ __device__ __forceinline__ bool hb_cross(uint64_t P, uint64_t Q) {
            (pa && qw && hb_two(pa, qw));
 }
 
-__device__ __forceinline__ uint32_t hb_hash(uint32_t key) { return (key * 0x9E3779B1u) >> HB_HASH_SHIFT; }
-__device__ __forceinline__ uint32_t hb_rhash(uint32_t key) { return (key * 0x85EBCA6Bu) >> 25; }
+template <class SH>
+__device__ __forceinline__ uint32_t hb_hash(uint32_t key) { return (key * 0x9E3779B1u) >> SH::shift; }
 
 // pool item: run position << 10 | tid  ->  summary item: position << 32 | tid
 __device__ __forceinline__ uint64_t hb_item64(uint32_t v) {
@@ -146,25 +158,22 @@ __device__ __forceinline__ void hb_x_fill(KX *xk, uint64_t *xv, uint32_t from, u
         }
 }
 
-template <class KX>
-__global__ void __launch_bounds__(HB_THREADS, 1)
+template <class KX, class SH>
+__global__ void __launch_bounds__(SH::threads, SH::ctas_per_sm)
 k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob, const uint32_t *__restrict__ bstart,
               Layout L, TState *ts, Ctl *ctl, uint32_t *nonred, uint32_t *binel, uint32_t *spill, uint32_t *tflag,
               KX *xk, uint64_t *xv, uint32_t *sig, RaceStage rs) {
     extern __shared__ __align__(16) uint64_t hb_smem[];
-    uint64_t *own = hb_smem;                                               // [2][HB_SLOTS]
-    uint32_t *key = reinterpret_cast<uint32_t *>(own + 2 * HB_SLOTS);      // [2][HB_SLOTS]
-    uint16_t *list = reinterpret_cast<uint16_t *>(key + 2 * HB_SLOTS);     // [2][HB_CAP]
-    uint32_t *rkey = reinterpret_cast<uint32_t *>(list + 2 * HB_CAP);      // [HB_RSLOTS]
-    uint32_t *pool = rkey + HB_RSLOTS;                                     // [HB_RSLOTS][first 3, second 3]
-    __shared__ uint32_t s_blk, s_cnt[2], s_flag, s_minpend, s_hi, s_nracy, s_needed;
+    uint64_t *own = hb_smem;                                               // [2][SH::slots]
+    uint32_t *key = reinterpret_cast<uint32_t *>(own + 2 * SH::slots);      // [2][SH::slots]
+    uint16_t *list = reinterpret_cast<uint16_t *>(key + 2 * SH::slots);     // [2][SH::cap]
+    __shared__ uint32_t s_blk, s_cnt[2], s_flag, s_minpend, s_hi, s_nracy, s_needed, s_ridx;
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t lt = lanemask_lt();
-    for (int i = tid; i < 2 * HB_SLOTS; i += HB_THREADS) {
+    for (int i = tid; i < 2 * SH::slots; i += SH::threads) {
         own[i] = 0ull;
         key[i] = HB_EMPTY;
     }
-    for (int i = tid; i < HB_RSLOTS * 7; i += HB_THREADS) rkey[i] = HB_EMPTY;   // rkey and pool
     if (tid == 0) {
         s_cnt[0] = s_cnt[1] = 0;
         s_flag = 0;
@@ -172,6 +181,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         s_hi = 0;
         s_nracy = 0;
         s_needed = 0;
+        s_ridx = 0;
     }
     const uint64_t xcap = L.x_cap;
     uint32_t xpos = 0, xend = 0;   // this warp's reserved inter-block slots [xpos, xend)
@@ -193,12 +203,12 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         const uint32_t nb = d.nb, bt = d.bt, su = d.su, gu = d.gu, maxb = d.maxb;
         const bool pad = nb <= (1u << 20);
 
-        // ---- window: records wbase + j * HB_THREADS + tid, j = 0, 1 --------------------------
+        // ---- window: records wbase + j * SH::threads + tid, j = 0, 1 --------------------------
         uint32_t wbase = s0;
         uint4 cur[2], nxt[2];
 #pragma unroll
         for (int j = 0; j < 2; j++) {
-            const uint32_t i0 = s0 + j * HB_THREADS + tid, i1 = i0 + HB_CH;
+            const uint32_t i0 = s0 + j * SH::threads + tid, i1 = i0 + SH::window;
             cur[j] = i0 < s1 ? ev[i0] : make_uint4(0, 0, 0, 0);
             nxt[j] = i1 < s1 ? ev[i1] : make_uint4(0, 0, 0, 0);
         }
@@ -208,7 +218,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             bool stopme = false, isx[2];
 #pragma unroll
             for (int j = 0; j < 2; j++) {
-                const uint32_t idx = wbase + j * HB_THREADS + tid;
+                const uint32_t idx = wbase + j * SH::threads + tid;
                 const bool in = idx < s1;
                 const uint4 e = cur[j];
                 const uint32_t u = e.x, vo = e.y, blk = e.z, w3 = e.w;
@@ -263,11 +273,11 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             return pb;
         };
         auto advance = [&]() {
-            wbase += HB_CH;
+            wbase += SH::window;
 #pragma unroll
             for (int j = 0; j < 2; j++) {
                 cur[j] = nxt[j];
-                const uint32_t i1 = wbase + HB_CH + j * HB_THREADS + tid;
+                const uint32_t i1 = wbase + SH::window + j * SH::threads + tid;
                 nxt[j] = i1 < s1 ? ev[i1] : make_uint4(0, 0, 0, 0);
             }
         };
@@ -277,8 +287,8 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         uint32_t prev_e = HB_NONE, par = 0, cnt_prev = 0, run_start = s0;
         bool hashing = true, full_reset = false;
         for (;;) {
-            uint32_t *kt = key + par * HB_SLOTS;
-            uint64_t *ot = own + par * HB_SLOTS;
+            uint32_t *kt = key + par * SH::slots;
+            uint64_t *ot = own + par * SH::slots;
             // ---- 1. insert run e: its records in this window and, while it continues, the next
             for (;;) {
                 uint32_t hi = 0, mp = HB_NONE;
@@ -291,8 +301,8 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                     bool created = false;
                     if (mine) {
                         const uint32_t k = (r.x << 1) | ((r.w >> 30) & 1u);
-                        uint32_t h = hb_hash(k);
-                        for (int probe = 0; probe < HB_SLOTS; probe++) {
+                        uint32_t h = hb_hash<SH>(k);
+                        for (int probe = 0; probe < SH::slots; probe++) {
                             const uint32_t c = kt[h];
                             if (c == k) { s = h; break; }
                             if (c == HB_EMPTY) {
@@ -300,7 +310,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                                 if (old == HB_EMPTY) { s = h; created = true; break; }
                                 if (old == k) { s = h; break; }
                             }
-                            h = (h + 1) & (HB_SLOTS - 1);
+                            h = (h + 1) & (SH::slots - 1);
                         }
                         if (s == HB_EMPTY) {
                             s_flag = 2u;   // table full
@@ -308,7 +318,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                             atomicOr(reinterpret_cast<unsigned long long *>(&ot[s]),
                                      (unsigned long long)hb_own_bits((r.w >> 28) & 3u, r.w & 0x3FFu));
                         }
-                        hi = wbase + j * HB_THREADS + tid;
+                        hi = wbase + j * SH::threads + tid;
                         pend &= ~(1u << j);
                     } else if ((pend >> j) & 1u) {
                         mp = min(mp, ep);
@@ -321,7 +331,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                         base = __shfl_sync(0xFFFFFFFFu, base, leader);
                         if (created) {
                             const uint32_t pos = base + __popc(cm & lt);
-                            if (pos < HB_CAP) list[par * HB_CAP + pos] = (uint16_t)s;
+                            if (pos < SH::cap) list[par * SH::cap + pos] = (uint16_t)s;
                             else s_flag = 2u;   // more distinct units than listed entries
                         }
                     }
@@ -334,7 +344,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                 }
                 // the run continues into the next window when that window exists and this one
                 // ends with a record of the run
-                const uint32_t wend = min(wbase + (uint32_t)HB_CH, s1);
+                const uint32_t wend = min(wbase + (uint32_t)SH::window, s1);
                 if (wend < s1) {
                     const uint4 last = ev[wend - 1];
                     if (last.z == lb && ((last.w >> 16) & 0xFFFu) == e) {
@@ -350,49 +360,35 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             // ---- 2. finalise run e
             __syncthreads();   // A: the run's inserts are complete
             const uint32_t flag = s_flag, next = s_minpend;
-            const uint32_t cnt = min(s_cnt[par], (uint32_t)HB_CAP);
+            const uint32_t cnt = min(s_cnt[par], (uint32_t)SH::cap);
             const uint32_t lo = run_start, hi = max(s_hi, run_start);
             const bool stop = flag != 0u || (next != HB_NONE && next <= e);
             bool needed = false;
-            uint32_t rmask = 0;   // bit m: this thread's list entry tid + m * HB_THREADS went to the racy table
-            uint64_t rq = 0;      // their racy-table slots, 7 bits each
+            uint32_t rmask = 0;   // bit m: this thread's list entry tid + m * SH::threads is racy
             if (!stop) {
                 const bool adj = prev_e != HB_NONE && prev_e + 1 == e;
-                const uint32_t *pkt = key + (par ^ 1u) * HB_SLOTS;
-                const uint64_t *pot = own + (par ^ 1u) * HB_SLOTS;
+                const uint32_t *pkt = key + (par ^ 1u) * SH::slots;
+                const uint64_t *pot = own + (par ^ 1u) * SH::slots;
 #pragma unroll 1
-                for (uint32_t i = tid, m = 0; i < cnt; i += HB_THREADS, m++) {
-                    const uint32_t s = list[par * HB_CAP + i];
+                for (uint32_t i = tid, m = 0; i < cnt; i += SH::threads, m++) {
+                    const uint32_t s = list[par * SH::cap + i];
                     const uint64_t o = ot[s];
                     const uint32_t k = kt[s];
                     if (hb_racy(o)) {
-                        const uint32_t r = atomicAdd(&s_nracy, 1u);
-                        if (r < HB_POOL) {
-                            uint32_t q = hb_rhash(k);
-                            bool in = false;
-                            for (int probe = 0; probe < HB_RSLOTS && !in; probe++) {
-                                in = atomicCAS(&rkey[q], HB_EMPTY, k) == HB_EMPTY;
-                                if (!in) q = (q + 1) & (HB_RSLOTS - 1);
-                            }
-                            if (in) {
-                                rmask |= 1u << m;
-                                rq |= (uint64_t)q << (7 * m);
-                            } else {
-                                atomicOr(&s_nracy, 0x40000000u);   // cannot happen (load <= 1/2); spill the run
-                            }
-                        }
+                        rmask |= 1u << m;
+                        atomicAdd(&s_nracy, 1u);
                     }
                     // adjacency: until some thread has found barrier e-1 needed
                     if (adj && !needed && !*(volatile uint32_t *)&s_needed) {
-                        uint32_t h = hb_hash(k);
-                        for (int probe = 0; probe < HB_SLOTS; probe++) {
+                        uint32_t h = hb_hash<SH>(k);
+                        for (int probe = 0; probe < SH::slots; probe++) {
                             const uint32_t c = pkt[h];
                             if (c == HB_EMPTY) break;
                             if (c == k) {
                                 needed = hb_cross(pot[h], o);
                                 break;
                             }
-                            h = (h + 1) & (HB_SLOTS - 1);
+                            h = (h + 1) & (SH::slots - 1);
                         }
                         if (needed) s_needed = 1u;
                     }
@@ -400,49 +396,63 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             }
             if (__syncthreads_or(needed) && tid == 0) mark_needed(nonred, L, b, e - 1);   // B
             const uint32_t nracy = s_nracy;
+            bool prev_overlaid = false;   // the previous run's table holds the racy pool
             if (!stop && nracy > 0) {
-                if (nracy > HB_POOL || hi - lo >= HB_POS_LIMIT) {
+                if (nracy > (uint32_t)SH::pool || hi - lo >= HB_POS_LIMIT) {
                     // too many racy units: the sort path computes this run's races
                     if (tid == 0) {
                         atomicOr(&spill[(uint64_t)b * L.swords + (e >> 5)], 1u << (e & 31));
                         for (uint32_t tl = lo / IN_TILE; tl <= hi / IN_TILE; tl++) tflag[d.tile_off + tl] = 1u;
                     }
                 } else {
-                    // exact lowest pairs of the racy units: first, then first of another thread, per category
+                    // exact lowest pairs of the racy units: per category the first item, then the first
+                    // item of another thread. The previous run's table is free now: its keys become a
+                    // map slot -> racy index, its owner summaries the pool of 6 items per racy unit.
+                    prev_overlaid = true;
+                    uint16_t *rmap = reinterpret_cast<uint16_t *>(key + (par ^ 1u) * SH::slots);
+                    uint32_t *pool = reinterpret_cast<uint32_t *>(own + (par ^ 1u) * SH::slots);
+                    for (uint32_t i = tid; i < SH::slots / 2; i += SH::threads)
+                        reinterpret_cast<uint32_t *>(rmap)[i] = 0xFFFFFFFFu;
+                    for (uint32_t i = tid; i < nracy * 6; i += SH::threads) pool[i] = HB_EMPTY;
+                    __syncthreads();
+                    for (uint32_t m = 0; rmask >> m; m++)
+                        if ((rmask >> m) & 1u) rmap[list[par * SH::cap + tid + m * SH::threads]] = (uint16_t)atomicAdd(&s_ridx, 1u);
+                    __syncthreads();
 #pragma unroll 1
                     for (int pass = 0; pass < 2; pass++) {
-                        for (uint32_t i = lo + tid; i <= hi; i += HB_THREADS) {
+                        for (uint32_t i = lo + tid; i <= hi; i += SH::threads) {
                             const uint4 r = ev[i];
                             if (r.z != lb || ((r.w >> 16) & 0xFFFu) != e) continue;
                             const uint32_t k = (r.x << 1) | ((r.w >> 30) & 1u);
                             const uint32_t c = (r.w >> 28) & 3u, tt = r.w & 0x3FFu;
                             if (c == 3u) continue;
-                            const uint32_t item = ((i - lo) << 10) | tt;
-                            uint32_t q = hb_rhash(k);
-                            for (int probe = 0; probe < HB_RSLOTS; probe++) {
-                                const uint32_t rk = rkey[q];
-                                if (rk == HB_EMPTY) break;
-                                if (rk == k) {
-                                    uint32_t *pe = pool + q * 6;
-                                    if (pass == 0) atomicMin(&pe[c], item);
-                                    else if ((pe[c] & 0x3FFu) != tt) atomicMin(&pe[3 + c], item);
-                                    break;
-                                }
-                                q = (q + 1) & (HB_RSLOTS - 1);
+                            uint32_t h = hb_hash<SH>(k);
+                            for (int probe = 0; probe < SH::slots; probe++) {
+                                const uint32_t kk = kt[h];
+                                if (kk == k || kk == HB_EMPTY) break;
+                                h = (h + 1) & (SH::slots - 1);
                             }
+                            if (kt[h] != k) continue;
+                            const uint32_t ri = rmap[h];
+                            if (ri == 0xFFFFu) continue;
+                            const uint32_t item = ((i - lo) << 10) | tt;
+                            uint32_t *pe = pool + ri * 6;
+                            if (pass == 0) atomicMin(&pe[c], item);
+                            else if ((pe[c] & 0x3FFu) != tt) atomicMin(&pe[3 + c], item);
                         }
-                        __syncthreads();   // C, D
+                        __syncthreads();
                     }
                     const OwnThread ownt;
                     for (uint32_t m = 0; rmask >> m; m++) {
                         if (!((rmask >> m) & 1u)) continue;
-                        const uint32_t q = (uint32_t)(rq >> (7 * m)) & 0x7Fu;
-                        const uint32_t k = rkey[q];
+                        const uint32_t sl = list[par * SH::cap + tid + m * SH::threads];
+                        const uint32_t k = kt[sl];
+                        const uint32_t *pe = pool + rmap[sl] * 6;
                         Top2 S;
 #pragma unroll
                         for (int c = 0; c < 3; c++) {
-                            S.a[c] = hb_item64(pool[q * 6 + c]);
-                            S.b[c] = hb_item64(pool[q * 6 + 3 + c]);
+                            S.a[c] = hb_item64(pe[c]);
+                            S.b[c] = hb_item64(pe[3 + c]);
                         }
 #pragma unroll
                         for (int cls = 0; cls < 2; cls++) {
@@ -454,22 +464,23 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                             emit_race(rs, ctl, t, race_key(L, t, k & 1u, 0u, b, e, k >> 1, cls), pi, qi, true);
                         }
                     }
+                    if (tid == 0) s_ridx = 0;
+                    __syncthreads();   // every emission has read the pool
                 }
             }
-            // release racy-table entries; release the previous run's table
-            for (uint32_t m = 0; rmask >> m; m++) {
-                if (!((rmask >> m) & 1u)) continue;
-                const uint32_t q = (uint32_t)(rq >> (7 * m)) & 0x7Fu;
-                rkey[q] = HB_EMPTY;
-#pragma unroll
-                for (int c = 0; c < 6; c++) pool[q * 6 + c] = HB_EMPTY;
-            }
-            if (!stop) {
+            // release the previous run's table (all of it when it held the racy pool)
+            if (prev_overlaid) {
                 const uint32_t pp = par ^ 1u;
-                for (uint32_t i = tid; i < cnt_prev; i += HB_THREADS) {
-                    const uint32_t s = list[pp * HB_CAP + i];
-                    key[pp * HB_SLOTS + s] = HB_EMPTY;
-                    own[pp * HB_SLOTS + s] = 0ull;
+                for (uint32_t i = tid; i < SH::slots; i += SH::threads) {
+                    key[pp * SH::slots + i] = HB_EMPTY;
+                    own[pp * SH::slots + i] = 0ull;
+                }
+            } else if (!stop) {
+                const uint32_t pp = par ^ 1u;
+                for (uint32_t i = tid; i < cnt_prev; i += SH::threads) {
+                    const uint32_t s = list[pp * SH::cap + i];
+                    key[pp * SH::slots + s] = HB_EMPTY;
+                    own[pp * SH::slots + s] = 0ull;
                 }
             }
             if (tid == 0) {
@@ -494,7 +505,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             if (next == HB_NONE) {
                 // every record of the window is in; a record range that goes on means the block's
                 // records are not in run order
-                if (min(wbase + (uint32_t)HB_CH, s1) < s1) {
+                if (min(wbase + (uint32_t)SH::window, s1) < s1) {
                     if (tid == 0) atomicOr(&binel[b], 1u);
                     hashing = false;
                     full_reset = true;
@@ -504,14 +515,14 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             e = next;
         }
         // records of the range not yet read (the block left the hash path early): validate and route
-        while (wbase + HB_CH < s1) {
+        while (wbase + SH::window < s1) {
             advance();
             activate();
         }
         // clean tables for the next block
         if (full_reset) {
             __syncthreads();
-            for (int i = tid; i < 2 * HB_SLOTS; i += HB_THREADS) {
+            for (int i = tid; i < 2 * SH::slots; i += SH::threads) {
                 own[i] = 0ull;
                 key[i] = HB_EMPTY;
             }
@@ -521,10 +532,10 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             }
         } else if (hashing) {
             const uint32_t pp = par ^ 1u;   // the last run's table
-            for (uint32_t i = tid; i < cnt_prev; i += HB_THREADS) {
-                const uint32_t s = list[pp * HB_CAP + i];
-                key[pp * HB_SLOTS + s] = HB_EMPTY;
-                own[pp * HB_SLOTS + s] = 0ull;
+            for (uint32_t i = tid; i < cnt_prev; i += SH::threads) {
+                const uint32_t s = list[pp * SH::cap + i];
+                key[pp * SH::slots + s] = HB_EMPTY;
+                own[pp * SH::slots + s] = 0ull;
             }
             if (tid == 0) s_cnt[pp] = 0;
         }

@@ -176,8 +176,8 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout 
     const size_t ks = L.wide_s ? 8 : 4, kg = L.wide_g ? 8 : 4, kx = L.wide_x ? 8 : 4;
     // inter-block stream: every global record, plus the unused tails of the chunks of slots
     // the hash path's warps reserve (one partial chunk per warp that reserved any)
-    const uint64_t hash_warps = (uint64_t)std::max(1, std::min<int>(sms, (int)std::max<uint32_t>(L.NB, 1))) *
-                                (HB_THREADS / 32);
+    // (32 warps per SM in either CTA shape, at most one SM's worth per block)
+    const uint64_t hash_warps = (uint64_t)std::max(1, std::min<int>(sms, (int)std::max<uint32_t>(L.NB, 1))) * 32;
     L.x_cap = n1 + std::min<uint64_t>(hash_warps, n1) * HB_XCH;
     for (int i = 0; i < 2; i++) {
         L.off_sk[i] = take(n1 * ks);
@@ -197,6 +197,11 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout 
 template <class K>
 void set_sort_attr() {
     cudaFuncSetAttribute(k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem<K>());
+}
+
+template <class KX, class SH>
+void set_hash_attr() {
+    cudaFuncSetAttribute(k_hash_blocks<KX, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hash_blocks_smem<SH>());
 }
 
 template <class K, bool INTER>
@@ -379,8 +384,10 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
         set_reduce_attr<uint64_t, false>();
         set_reduce_attr<uint32_t, true>();
         set_reduce_attr<uint64_t, true>();
-        cudaFuncSetAttribute(k_hash_blocks<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hash_blocks_smem());
-        cudaFuncSetAttribute(k_hash_blocks<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hash_blocks_smem());
+        set_hash_attr<uint32_t, HbLarge>();
+        set_hash_attr<uint64_t, HbLarge>();
+        set_hash_attr<uint32_t, HbSmall>();
+        set_hash_attr<uint64_t, HbSmall>();
         ctx->attrs_set = true;
     }
     R.st = (cudaStream_t)stream;
@@ -497,15 +504,25 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
         if (route && any_hash) {
             uint32_t *bstart = R.at<uint32_t>(L.off_bstart);
             k_block_ranges<<<R.grid_for(L.NB, 8, 16), 256, 0, st>>>(td, tob, L, bstart);
-            const int gh = std::max(1, std::min<int>(ctx->sms, (int)L.NB));
-            if (L.wide_x)
-                k_hash_blocks<uint64_t><<<gh, HB_THREADS, hash_blocks_smem(), st>>>(
-                    td, tob, bstart, L, ts, R.ctl, nonred, binel, spill, tflag, R.at<uint64_t>(L.off_xk[0]),
-                    R.at<uint64_t>(L.off_xv[0]), sig, rs);
-            else
-                k_hash_blocks<uint32_t><<<gh, HB_THREADS, hash_blocks_smem(), st>>>(
-                    td, tob, bstart, L, ts, R.ctl, nonred, binel, spill, tflag, R.at<uint32_t>(L.off_xk[0]),
-                    R.at<uint64_t>(L.off_xv[0]), sig, rs);
+            // CTA shape: two smaller CTAs per SM unless a hash-path trace has blocks of more than
+            // 256 threads (whose runs may hold more distinct units than the smaller table)
+            uint32_t max_bt = 0;
+            for (uint32_t i = 0; i < T; i++)
+                if (hdesc[i].hash_ok) max_bt = std::max(max_bt, hdesc[i].bt);
+            const bool small = ctx->opt.hash_shape == 2 || (ctx->opt.hash_shape == 0 && max_bt <= 256);
+#define SIM_HASH(KX, SH)                                                                                            \
+    k_hash_blocks<KX, SH><<<std::max(1, std::min<int>(ctx->sms * SH::ctas_per_sm, (int)L.NB)), SH::threads,        \
+                            hash_blocks_smem<SH>(), st>>>(td, tob, bstart, L, ts, R.ctl, nonred, binel, spill,      \
+                                                          tflag, R.at<KX>(L.off_xk[0]), R.at<uint64_t>(L.off_xv[0]), \
+                                                          sig, rs)
+            if (L.wide_x) {
+                if (small) SIM_HASH(uint64_t, HbSmall);
+                else SIM_HASH(uint64_t, HbLarge);
+            } else {
+                if (small) SIM_HASH(uint32_t, HbSmall);
+                else SIM_HASH(uint32_t, HbLarge);
+            }
+#undef SIM_HASH
             R.launches += 2;
             R.mark(SIMULEE_STAGE_HASH, 1);
             R.mark(SIMULEE_STAGE_FALLBACK, 0);

@@ -56,7 +56,7 @@ class Report(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("wait_limit_us", ctypes.c_uint32), ("path", ctypes.c_uint32), ("test_withhold", ctypes.c_uint32),
                 ("ingest_ctas_per_sm", ctypes.c_uint32), ("sort_ctas_per_sm", ctypes.c_uint32),
-                ("reduce_ctas_per_sm", ctypes.c_uint32), ("reserved", ctypes.c_uint32 * 2)]
+                ("reduce_ctas_per_sm", ctypes.c_uint32), ("hash_shape", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 REPORT_BYTES = ctypes.sizeof(Report)
@@ -148,11 +148,13 @@ class Checker:
     """A library context on one GPU plus reusable device buffers."""
 
     def __init__(self, device: int = 0, wait_limit_us: int = 0, path: int = PATH_AUTO, test_withhold: int = 0,
-                 ingest_ctas_per_sm: int = 0, sort_ctas_per_sm: int = 0, reduce_ctas_per_sm: int = 0):
+                 ingest_ctas_per_sm: int = 0, sort_ctas_per_sm: int = 0, reduce_ctas_per_sm: int = 0,
+                 hash_shape: int = 0):
         import torch
         self.device = device
         self.torch = torch
-        opt = Options(wait_limit_us, path, test_withhold, ingest_ctas_per_sm, sort_ctas_per_sm, reduce_ctas_per_sm)
+        opt = Options(wait_limit_us, path, test_withhold, ingest_ctas_per_sm, sort_ctas_per_sm, reduce_ctas_per_sm,
+                      hash_shape)
         h = ctypes.c_void_p()
         _check(lib().simulee_create(ctypes.byref(h), device, ctypes.byref(opt)), "simulee_create")
         self.h = h

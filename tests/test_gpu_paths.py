@@ -3,8 +3,9 @@ order: blocks one after another, epochs in order inside a block) and the
 radix-sort path (forced, or taken when a trace or block does not qualify).
 
 The hash path has its own limits and hand-offs, each exercised here: racy
-units resolved in place (up to 64 per run) or the run spilled to the sort
-path (more), a run with more distinct units than its table holds (the block
+units resolved in place (up to a third of a run table's entries: 2730 with
+the 8192-entry table, 1365 with the 4096-entry one) or the run spilled to the
+sort path (more), a run with more distinct units than its table holds (the block
 falls back), epochs out of order, blocks interleaved, blocks and epochs
 without records, and runs that span several 2048-record windows."""
 import numpy as np
@@ -17,6 +18,7 @@ from gpu_util import diff, gpu_check
 pytestmark = pytest.mark.gpu
 
 PATHS = {"auto": 0, "sort": 1}
+SHAPES = [1, 2]   # hash path: one 1024-thread CTA per SM (8192-entry tables), two 512-thread CTAs (4096)
 
 
 @pytest.mark.parametrize("path", sorted(PATHS))
@@ -24,6 +26,14 @@ def test_grouped_random_traces(path):
     for seed in range(200):
         tr = tracegen.random_grouped(seed)
         d = diff(gpu_check(tr, path=PATHS[path]), oracle.check(tr))
+        assert d == [], f"seed {seed}: {d}"
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_grouped_random_traces_both_shapes(shape):
+    for seed in range(200, 320):
+        tr = tracegen.random_grouped(seed)
+        d = diff(gpu_check(tr, path=0, hash_shape=shape), oracle.check(tr))
         assert d == [], f"seed {seed}: {d}"
 
 
@@ -42,6 +52,14 @@ def test_grid_family_both_paths(path, nb, bt, ep):
     tr = tracegen.pattern(nb * 7 + ep, n_blocks=nb, block_threads=bt, n_epochs=ep, shared_units=12288,
                           global_units=1 << 20)
     assert diff(gpu_check(tr, path=PATHS[path]), oracle.check(tr)) == []
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("nb,bt,ep,removed", [(12, 256, 32, 0.5), (3, 1024, 6, 0.3), (40, 64, 12, 0.1)])
+def test_grid_family_both_shapes(shape, nb, bt, ep, removed):
+    tr = tracegen.pattern(nb * 3 + ep, n_blocks=nb, block_threads=bt, n_epochs=ep, shared_units=12288,
+                          global_units=1 << 20, removed_p=removed)
+    assert diff(gpu_check(tr, path=0, hash_shape=shape), oracle.check(tr)) == []
 
 
 def test_long_runs_and_out_of_order_epochs_fall_back():
@@ -87,17 +105,20 @@ def _racy_units_trace(k: int, n_blocks: int = 2):
     return b.set_counts(1).trace()
 
 
-@pytest.mark.parametrize("k", [1, 63, 64, 65, 300, 2500])
-def test_racy_units_in_place_and_spilled(k):
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("k", [1, 2, 64, 300, 1365, 1366, 2730, 2731])
+def test_racy_units_in_place_and_spilled(k, shape):
     tr = _racy_units_trace(k)
     want = oracle.check(tr)
     assert len(want["races"]) == 2 * k
-    assert diff(gpu_check(tr, path=0), want) == []
+    assert diff(gpu_check(tr, path=0, hash_shape=shape), want) == []
 
 
-def test_run_with_more_distinct_units_than_the_table():
-    """One epoch of 1024 threads x 7 distinct units (7168 > 6144): the block
-    leaves the hash path; a second block stays on it."""
+@pytest.mark.parametrize("shape", SHAPES)
+def test_run_with_more_distinct_units_than_the_table(shape):
+    """One epoch of 1024 threads x 7 distinct units (7168, more than either
+    table holds): the block leaves the hash path; a second block (2048
+    distinct units) stays on it with the larger table."""
     rng = np.random.default_rng(4)
     b = tracegen.Builder(2, 1024, 1 << 14)
     for e in range(2):
@@ -107,7 +128,7 @@ def test_run_with_more_distinct_units_than_the_table():
         for t in range(1024):
             b.access(1, t, e, (t + 5 * e) % 2048, tracegen.WRITE)
     tr = b.set_counts(1).trace()
-    assert diff(gpu_check(tr, path=0), oracle.check(tr)) == []
+    assert diff(gpu_check(tr, path=0, hash_shape=shape), oracle.check(tr)) == []
 
 
 def test_epoch_gaps_and_blocks_without_records():
