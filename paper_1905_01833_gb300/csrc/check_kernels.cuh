@@ -349,47 +349,92 @@ __global__ void k_fallback_tiles(const TraceDesc *__restrict__ td, Layout L, con
 // build the digit histograms of the records kept. The order of kept records
 // does not matter (the sort that follows groups them by unit). Slots the hash
 // path reserved but did not use carry an invalid action and are dropped.
+// A CTA takes tiles of 4096 elements (8 per thread); kept elements are
+// compacted with warp ballots and one atomicAdd per tile.
+constexpr int XF_THREADS = 512;
+constexpr int XF_ITEMS = 8;
+constexpr int XF_TILE = XF_THREADS * XF_ITEMS;
+
 template <class KX>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(XF_THREADS)
 k_x_filter(const KX *__restrict__ xk, const uint64_t *__restrict__ xv, KX *yk, uint64_t *yv, const uint32_t *sig,
            Layout L, Ctl *ctl, uint32_t *hist) {
     __shared__ uint32_t sh[8 * RADIX];
-    __shared__ uint32_t wsum[8];
-    __shared__ uint32_t s_base;
-    const int tid = threadIdx.x;
-    for (int i = tid; i < 8 * RADIX; i += 256) sh[i] = 0;
+    __shared__ uint32_t wtot[XF_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const uint32_t lt = lanemask_lt();
+    for (int i = tid; i < 8 * RADIX; i += XF_THREADS) sh[i] = 0;
     __syncthreads();
     const uint64_t n = min((uint64_t)*(volatile unsigned int *)&ctl->n_x, L.x_cap);
     const uint64_t umask = (L.bug >= 64) ? ~0ull : ((1ull << L.bug) - 1);
-    for (uint64_t base = (uint64_t)blockIdx.x * 256; base < n; base += (uint64_t)gridDim.x * 256) {
-        const uint64_t i = base + tid;
-        bool keep = false;
-        KX k = 0;
-        uint64_t v = 0;
-        if (i < n) {
-            k = xk[i];
-            const uint64_t kk = (uint64_t)k;
+    for (uint64_t base = (uint64_t)blockIdx.x * XF_TILE; base < n; base += (uint64_t)gridDim.x * XF_TILE) {
+        KX k[XF_ITEMS];
+        uint32_t sv[XF_ITEMS];
+#pragma unroll
+        for (int j = 0; j < XF_ITEMS; j++) {
+            const uint64_t i = base + j * XF_THREADS + tid;
+            k[j] = i < n ? xk[i] : (KX)0;
+        }
+#pragma unroll
+        for (int j = 0; j < XF_ITEMS; j++) {
+            const uint64_t i = base + j * XF_THREADS + tid;
+            const uint64_t kk = (uint64_t)k[j];
             const uint32_t t = (uint32_t)(L.bug >= 64 ? 0 : (kk >> L.bug)), unit = (uint32_t)(kk & umask);
-            keep = sig_multi(L, sig[sig_slot(L, t, unit)]);
-            if (keep) {
-                v = xv[i];
-                keep = payload_act(v) != 3u;
-            }
-            if (keep) {
-                for (uint32_t q = 0; q < L.np_x; q++) atomicAdd(&sh[q * RADIX + digit_of(kk, q)], 1u);
+            sv[j] = i < n ? sig[sig_slot(L, t, unit)] : 0u;
+        }
+        uint64_t v[XF_ITEMS];
+        uint32_t keep = 0;
+#pragma unroll
+        for (int j = 0; j < XF_ITEMS; j++) {
+            const uint64_t i = base + j * XF_THREADS + tid;
+            v[j] = 0;
+            if (i < n && sig_multi(L, sv[j])) {
+                v[j] = xv[i];
+                if (payload_act(v[j]) != 3u) keep |= 1u << j;
             }
         }
-        const uint32_t pre = block_excl_scan_256(keep ? 1u : 0u, wsum);
-        if (tid == 255) s_base = atomicAdd(&ctl->n_xf, pre + (keep ? 1u : 0u));
+        // positions: warp ballots per item, warp totals, one atomicAdd per tile
+        uint32_t wcount = 0, bal[XF_ITEMS];
+#pragma unroll
+        for (int j = 0; j < XF_ITEMS; j++) {
+            bal[j] = __ballot_sync(0xFFFFFFFFu, (keep >> j) & 1u);
+            wcount += __popc(bal[j]);
+        }
+        if (lane == 0) wtot[w] = wcount;
+        __syncthreads();
+        if (w == 0) {
+            const uint32_t x = lane < XF_THREADS / 32 ? wtot[lane] : 0u;
+            uint32_t incl = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            uint32_t b0 = 0;
+            if (lane == 0 && total) b0 = atomicAdd(&ctl->n_xf, total);
+            b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
+            if (lane < XF_THREADS / 32) wtot[lane] = b0 + incl - x;
+        }
         __syncthreads();
         if (keep) {
-            yk[s_base + pre] = k;
-            yv[s_base + pre] = v;
+            uint32_t o = wtot[w];
+#pragma unroll
+            for (int j = 0; j < XF_ITEMS; j++) {
+                if ((keep >> j) & 1u) {
+                    const uint32_t pos = o + __popc(bal[j] & lt);
+                    yk[pos] = k[j];
+                    yv[pos] = v[j];
+                    const uint64_t kk = (uint64_t)k[j];
+                    for (uint32_t q = 0; q < L.np_x; q++) atomicAdd(&sh[q * RADIX + digit_of(kk, q)], 1u);
+                }
+                o += __popc(bal[j]);
+            }
         }
-        __syncthreads();
+        __syncthreads();   // wtot is rewritten by the next tile
     }
     __syncthreads();
-    for (int i = tid; i < (int)(L.np_x * RADIX); i += 256)
+    for (int i = tid; i < (int)(L.np_x * RADIX); i += XF_THREADS)
         if (sh[i]) atomicAdd(&hist[(L.p0_x + i / RADIX) * RADIX + (i % RADIX)], sh[i]);
 }
 

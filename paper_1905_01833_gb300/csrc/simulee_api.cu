@@ -555,12 +555,12 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
         // inter-block records of units touched by one block only are dropped before sorting;
         // the filter also builds the inter stream's digit histograms
         if (L.sig_slots) {
-            const int gf = R.grid_for(L.n, 256, 8);
+            const int gf = R.grid_for(L.x_cap, XF_TILE, 2);
             if (L.wide_x)
-                k_x_filter<uint64_t><<<gf, 256, 0, st>>>(R.at<uint64_t>(xk[0]), R.at<uint64_t>(xv[0]), R.at<uint64_t>(xk[1]),
+                k_x_filter<uint64_t><<<gf, XF_THREADS, 0, st>>>(R.at<uint64_t>(xk[0]), R.at<uint64_t>(xv[0]), R.at<uint64_t>(xk[1]),
                                                          R.at<uint64_t>(xv[1]), sig, L, R.ctl, hist);
             else
-                k_x_filter<uint32_t><<<gf, 256, 0, st>>>(R.at<uint32_t>(xk[0]), R.at<uint64_t>(xv[0]), R.at<uint32_t>(xk[1]),
+                k_x_filter<uint32_t><<<gf, XF_THREADS, 0, st>>>(R.at<uint32_t>(xk[0]), R.at<uint64_t>(xv[0]), R.at<uint32_t>(xk[1]),
                                                          R.at<uint64_t>(xv[1]), sig, L, R.ctl, hist);
             R.launches++;
         }
@@ -606,9 +606,12 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
         size_t rk[2] = {L.off_rk[0], L.off_rk[1]}, rv[2] = {L.off_rv[0], L.off_rv[1]};
         const int br = R.sort<uint64_t>(rk, rv, &R.ctl->n_rf, L.race_cap, L.np_r, L.p0_r, 1);
         const int gw = R.grid_for(L.race_cap, 256, 8);
-        k_race_starts<<<gw, 256, 0, st>>>(R.at<uint64_t>(rk[br]), L, R.ctl, ts);
+        if (T > 1) {   // one trace: its races start at 0 (the per-trace state is zeroed)
+            k_race_starts<<<gw, 256, 0, st>>>(R.at<uint64_t>(rk[br]), L, R.ctl, ts);
+            R.launches++;
+        }
         k_write_races<<<gw, 256, 0, st>>>(R.at<uint64_t>(rk[br]), R.at<uint64_t>(rv[br]), rs.pay, L, td, ts, R.ctl);
-        R.launches += 2;
+        R.launches++;
     }
     R.mark(SIMULEE_STAGE_RACES, 1);
 
