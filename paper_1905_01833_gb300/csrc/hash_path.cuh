@@ -167,7 +167,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
     uint64_t *own = hb_smem;                                               // [2][SH::slots]
     uint32_t *key = reinterpret_cast<uint32_t *>(own + 2 * SH::slots);      // [2][SH::slots]
     uint16_t *list = reinterpret_cast<uint16_t *>(key + 2 * SH::slots);     // [2][SH::cap]
-    __shared__ uint32_t s_blk, s_cnt[2], s_flag, s_minpend, s_hi, s_nracy, s_needed, s_ridx;
+    __shared__ uint32_t s_blk, s_cnt[2], s_flag, s_first, s_nracy, s_needed, s_ridx;
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t lt = lanemask_lt();
     for (int i = tid; i < 2 * SH::slots; i += SH::threads) {
@@ -177,8 +177,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
     if (tid == 0) {
         s_cnt[0] = s_cnt[1] = 0;
         s_flag = 0;
-        s_minpend = HB_NONE;
-        s_hi = 0;
+        s_first = HB_NONE;
         s_nracy = 0;
         s_needed = 0;
         s_ridx = 0;
@@ -203,23 +202,27 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         const uint32_t nb = d.nb, bt = d.bt, su = d.su, gu = d.gu, maxb = d.maxb;
         const bool pad = nb <= (1u << 20);
 
-        // ---- window: records wbase + j * SH::threads + tid, j = 0, 1 --------------------------
-        uint32_t wbase = s0;
+        // ---- windows: records wbase + j * SH::threads + tid, j = 0, 1. A run's first window
+        //      starts at the run's first record; records below vmark are already validated and
+        //      routed (a window that starts inside the previous one re-reads them from cache).
+        uint32_t wbase = s0, vmark = s0;
         uint4 cur[2], nxt[2];
+        auto load = [&](uint4 (&w)[2], uint32_t base) {
 #pragma unroll
-        for (int j = 0; j < 2; j++) {
-            const uint32_t i0 = s0 + j * SH::threads + tid, i1 = i0 + SH::window;
-            cur[j] = i0 < s1 ? ev[i0] : make_uint4(0, 0, 0, 0);
-            nxt[j] = i1 < s1 ? ev[i1] : make_uint4(0, 0, 0, 0);
-        }
-        // validate the window's records, route global ones to X; returns the records to hash
+            for (int j = 0; j < 2; j++) {
+                const uint32_t i = base + j * SH::threads + tid;
+                w[j] = i < s1 ? ev[i] : make_uint4(0, 0, 0, 0);
+            }
+        };
+        // validate the window's new records, route global ones to X; returns the window's
+        // records of this block (those to hash)
         auto activate = [&]() -> uint32_t {
             uint32_t pb = 0;
             bool stopme = false, isx[2];
 #pragma unroll
             for (int j = 0; j < 2; j++) {
                 const uint32_t idx = wbase + j * SH::threads + tid;
-                const bool in = idx < s1;
+                const bool in = idx < s1, fresh = in && idx >= vmark;
                 const uint4 e = cur[j];
                 const uint32_t u = e.x, vo = e.y, blk = e.z, w3 = e.w;
                 const uint32_t tt = w3 & 0xFFFFu, ep = (w3 >> 16) & 0xFFFu, act = (w3 >> 28) & 3u;
@@ -228,19 +231,19 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                 uint32_t pvo = __shfl_up_sync(0xFFFFFFFFu, vo, 1), pw = __shfl_up_sync(0xFFFFFFFFu, w3, 1);
                 uint32_t pz = __shfl_up_sync(0xFFFFFFFFu, blk, 1);
                 if (lane == 0) {
-                    const uint4 p = (in && idx > 0) ? ev[idx - 1] : make_uint4(0, 0, 0xFFFFFFFFu, 0);
+                    const uint4 p = (fresh && idx > 0) ? ev[idx - 1] : make_uint4(0, 0, 0xFFFFFFFFu, 0);
                     pvo = p.y;
                     pw = p.w;
                     pz = p.z;
                 }
-                bool ok = in && blk < nb && tt < bt && act != 3u && resv == 0u && (sp ? u < gu : u < su);
+                bool ok = fresh && blk < nb && tt < bt && act != 3u && resv == 0u && (sp ? u < gu : u < su);
                 if (ok && ep > cnts[blk * bt + tt]) ok = false;
-                if (in && idx > 0 && vo <= pvo) ok = false;
-                if (in && !ok) atomicMax(&ts[t].bad_rec, ~(unsigned long long)idx);
+                if (fresh && idx > 0 && vo <= pvo) ok = false;
+                if (fresh && !ok) atomicMax(&ts[t].bad_rec, ~(unsigned long long)idx);
                 if (ok && blk != lb) atomicOr(&ts[t].inel, 1u);   // the trace is not block-contiguous
-                if (in && (!ok || blk != lb)) stopme = true;
+                if (fresh && (!ok || blk != lb)) stopme = true;
                 if (ok && pz == blk && ((pw >> 16) & 0xFFFu) > ep) stopme = true;   // epochs go back
-                if (ok && blk == lb) pb |= 1u << j;
+                if (in && blk == lb && (ok || !fresh)) pb |= 1u << j;
                 isx[j] = ok && sp == 1u && ep <= maxb;
             }
             const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, isx[0]), b1 = __ballot_sync(0xFFFFFFFFu, isx[1]);
@@ -270,17 +273,10 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                 xpos += tot;
             }
             if (stopme) s_flag = 1u;
+            vmark = max(vmark, min(wbase + (uint32_t)SH::window, s1));
             return pb;
         };
-        auto advance = [&]() {
-            wbase += SH::window;
-#pragma unroll
-            for (int j = 0; j < 2; j++) {
-                cur[j] = nxt[j];
-                const uint32_t i1 = wbase + SH::window + j * SH::threads + tid;
-                nxt[j] = i1 < s1 ? ev[i1] : make_uint4(0, 0, 0, 0);
-            }
-        };
+        load(cur, s0);
         uint32_t pend = activate();
 
         uint32_t e = (ev[s0].w >> 16) & 0xFFFu;   // epoch of the block's first record
@@ -289,12 +285,20 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         for (;;) {
             uint32_t *kt = key + par * SH::slots;
             uint64_t *ot = own + par * SH::slots;
-            // ---- 1. insert run e: its records in this window and, while it continues, the next
+            // ---- 1. insert run e: its records in this window and, while it goes on, the next windows
             for (;;) {
-                uint32_t hi = 0, mp = HB_NONE;
+                const uint32_t wend = min(wbase + (uint32_t)SH::window, s1);
+                bool more = false;   // the run goes on past this window: fetch the next one now
+                if (wend < s1) {
+                    const uint4 last = ev[wend - 1];
+                    more = last.z == lb && ((last.w >> 16) & 0xFFFu) == e;
+                }
+                if (more) load(nxt, wend);
+                uint32_t first = HB_NONE;   // the window's first record after the run
 #pragma unroll
                 for (int j = 0; j < 2; j++) {
                     const uint4 r = cur[j];
+                    const uint32_t idx = wbase + j * SH::threads + tid;
                     const uint32_t ep = (r.w >> 16) & 0xFFFu;
                     const bool mine = ((pend >> j) & 1u) && ep == e;
                     uint32_t s = HB_EMPTY;
@@ -318,10 +322,8 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                             atomicOr(reinterpret_cast<unsigned long long *>(&ot[s]),
                                      (unsigned long long)hb_own_bits((r.w >> 28) & 3u, r.w & 0x3FFu));
                         }
-                        hi = wbase + j * SH::threads + tid;
-                        pend &= ~(1u << j);
-                    } else if ((pend >> j) & 1u) {
-                        mp = min(mp, ep);
+                    } else if (idx < s1) {
+                        first = min(first, idx);
                     }
                     const uint32_t cm = __ballot_sync(0xFFFFFFFFu, created);
                     if (cm) {
@@ -336,33 +338,31 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                         }
                     }
                 }
-                hi = __reduce_max_sync(0xFFFFFFFFu, hi);
-                mp = __reduce_min_sync(0xFFFFFFFFu, mp);
-                if (lane == 0) {
-                    if (hi) atomicMax(&s_hi, hi);
-                    if (mp != HB_NONE) atomicMin(&s_minpend, mp);
-                }
-                // the run continues into the next window when that window exists and this one
-                // ends with a record of the run
-                const uint32_t wend = min(wbase + (uint32_t)SH::window, s1);
-                if (wend < s1) {
-                    const uint4 last = ev[wend - 1];
-                    if (last.z == lb && ((last.w >> 16) & 0xFFFu) == e) {
-                        if (pend) s_flag = 3u;   // a record of this window was left behind: not in epoch order
-                        advance();
-                        pend = activate();
-                        continue;
-                    }
+                first = __reduce_min_sync(0xFFFFFFFFu, first);
+                if (lane == 0 && first != HB_NONE) atomicMin(&s_first, first);
+                if (more) {
+                    wbase = wend;
+                    cur[0] = nxt[0];
+                    cur[1] = nxt[1];
+                    pend = activate();
+                    continue;
                 }
                 break;
             }
 
             // ---- 2. finalise run e
             __syncthreads();   // A: the run's inserts are complete
-            const uint32_t flag = s_flag, next = s_minpend;
+            const uint32_t flag = s_flag, first = s_first;
             const uint32_t cnt = min(s_cnt[par], (uint32_t)SH::cap);
-            const uint32_t lo = run_start, hi = max(s_hi, run_start);
-            const bool stop = flag != 0u || (next != HB_NONE && next <= e);
+            const uint32_t lo = run_start, hi = (first != HB_NONE ? first : min(wbase + (uint32_t)SH::window, s1)) - 1;
+            const uint32_t next_start = hi + 1;
+            const bool stop = flag != 0u;
+            // the next run's first window: fetched now, it arrives while this run is finalised
+            uint32_t next_e = HB_NONE;
+            if (!stop && next_start < s1) {
+                load(cur, next_start);
+                next_e = (ev[next_start].w >> 16) & 0xFFFu;
+            }
             bool needed = false;
             uint32_t rmask = 0;   // bit m: this thread's list entry tid + m * SH::threads is racy
             if (!stop) {
@@ -416,7 +416,8 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                     for (uint32_t i = tid; i < nracy * 6; i += SH::threads) pool[i] = HB_EMPTY;
                     __syncthreads();
                     for (uint32_t m = 0; rmask >> m; m++)
-                        if ((rmask >> m) & 1u) rmap[list[par * SH::cap + tid + m * SH::threads]] = (uint16_t)atomicAdd(&s_ridx, 1u);
+                        if ((rmask >> m) & 1u)
+                            rmap[list[par * SH::cap + tid + m * SH::threads]] = (uint16_t)atomicAdd(&s_ridx, 1u);
                     __syncthreads();
 #pragma unroll 1
                     for (int pass = 0; pass < 2; pass++) {
@@ -485,8 +486,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             }
             if (tid == 0) {
                 s_cnt[par ^ 1u] = 0;
-                s_minpend = HB_NONE;
-                s_hi = 0;
+                s_first = HB_NONE;
                 s_needed = 0;
             }
             __syncthreads();   // E
@@ -501,22 +501,16 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             prev_e = e;
             cnt_prev = cnt;
             par ^= 1u;
-            run_start = hi + 1;
-            if (next == HB_NONE) {
-                // every record of the window is in; a record range that goes on means the block's
-                // records are not in run order
-                if (min(wbase + (uint32_t)SH::window, s1) < s1) {
-                    if (tid == 0) atomicOr(&binel[b], 1u);
-                    hashing = false;
-                    full_reset = true;
-                }
-                break;
-            }
-            e = next;
+            run_start = next_start;
+            if (next_start >= s1) break;   // the block's last run
+            wbase = next_start;
+            pend = activate();
+            e = next_e;
         }
         // records of the range not yet read (the block left the hash path early): validate and route
-        while (wbase + SH::window < s1) {
-            advance();
+        while (vmark < s1) {
+            wbase = vmark;
+            load(cur, wbase);
             activate();
         }
         // clean tables for the next block
@@ -539,10 +533,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             }
             if (tid == 0) s_cnt[pp] = 0;
         }
-        if (tid == 0) {
-            s_minpend = HB_NONE;
-            s_hi = 0;
-        }
+        if (tid == 0) s_first = HB_NONE;
     }
     hb_x_fill(xk, xv, xpos, xend, xcap, lane);   // the unused tail of this warp's last chunk
 }
