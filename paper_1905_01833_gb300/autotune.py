@@ -1,10 +1,12 @@
 """Autotuner for the check's launch choices, with a persistent JSON cache.
 
 Tuned per GPU model and trace-shape bucket (log2 of the record count, of the
-block count and of the epoch count): the path (short-interval hash path where
-it applies, or the radix-sort path for everything) and the persistent CTAs per
-SM of the record reads, the radix passes and the segmented reductions. Tile
-sizes and the 8-bit radix are fixed at compile time. Each candidate is timed
+block count and of the epoch count): the path (hash path where it applies, or
+the radix-sort path for everything), the hash path's CTA shape (one 1024-thread
+CTA per SM with 8192-entry run tables, or two 512-thread CTAs with 4096-entry
+tables), and the persistent CTAs per SM of the record reads, the radix passes
+and the segmented reductions. Tile sizes and the 8-bit radix are fixed at
+compile time. Each candidate is timed
 with CUDA events on the caller's trace; the fastest is cached and reused for
 traces in the same bucket.
 """
@@ -19,9 +21,10 @@ import statistics
 
 from . import simulee
 
-KNOBS = ("path", "ingest_ctas_per_sm", "sort_ctas_per_sm", "reduce_ctas_per_sm")
-CANDIDATES = [dict(zip(KNOBS, v)) for v in itertools.product((simulee.PATH_AUTO, simulee.PATH_SORT), (1, 2),
-                                                              (2, 3), (2, 3, 4))]
+KNOBS = ("path", "hash_shape", "ingest_ctas_per_sm", "sort_ctas_per_sm", "reduce_ctas_per_sm")
+# the hash path's shape only matters on the auto path
+CANDIDATES = [dict(zip(KNOBS, v)) for v in itertools.product((simulee.PATH_AUTO,), (1, 2), (1, 2), (2, 3), (2, 3, 4))] + \
+             [dict(zip(KNOBS, v)) for v in itertools.product((simulee.PATH_SORT,), (0,), (1, 2), (2, 3), (2, 3, 4))]
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "simulee_gb300", "autotune.json")
 
 

@@ -12,7 +12,7 @@ def test_bucket_and_candidates():
     class T:
         n_events, n_blocks, max_barriers = 61_000_000, 1024, 31
     assert autotune.bucket(T) == "n26-b10-e5"
-    assert len(autotune.CANDIDATES) == 24
+    assert len(autotune.CANDIDATES) == 36
     assert all(set(c) == set(autotune.KNOBS) for c in autotune.CANDIDATES)
 
 
