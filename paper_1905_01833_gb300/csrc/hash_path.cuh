@@ -83,6 +83,7 @@ __device__ __forceinline__ bool hb_two(uint32_t f, uint32_t g) {
 // a conflicting pair inside one run's unit
 __device__ __forceinline__ bool hb_racy(uint64_t o) {
     const uint32_t r = hb_field(o, 0), w = hb_field(o, 1), a = hb_field(o, 2), m = w | a;
+    if (!hb_two(r | m, r | m)) return false;                      // one thread only (the usual case)
     const bool ww = w && (hb_two(w, w) || (a && hb_two(w, a)));   // write-write, write-atomic
     const bool rw = r && m && hb_two(r, m);                       // read with write or atomic
     return ww || rw;
@@ -93,6 +94,7 @@ __device__ __forceinline__ bool hb_racy(uint64_t o) {
 __device__ __forceinline__ bool hb_cross(uint64_t P, uint64_t Q) {
     const uint32_t pr = hb_field(P, 0), pw = hb_field(P, 1), pa = hb_field(P, 2), pm = pw | pa;
     const uint32_t qr = hb_field(Q, 0), qw = hb_field(Q, 1), qa = hb_field(Q, 2), qm = qw | qa;
+    if (!hb_two(pr | pm, qr | qm)) return false;                  // one thread only (the usual case)
     return (pr && qm && hb_two(pr, qm)) || (pm && qr && hb_two(pm, qr)) || (pw && qm && hb_two(pw, qm)) ||
            (pa && qw && hb_two(pa, qw));
 }
