@@ -90,6 +90,9 @@ def _bind(lib):
     lib.orc_copy.argtypes = [vp, vp, vp, vp, vp]
     lib.orc_free.restype = None
     lib.orc_free.argtypes = [vp]
+    if hasattr(lib, "orc_fitness"):
+        lib.orc_fitness.restype = ctypes.c_int32
+        lib.orc_fitness.argtypes = [vp, u64, vp, u32, u32, u32, u32, u32, u32, vp, vp, vp, vp, vp]
     return lib
 
 
@@ -138,3 +141,32 @@ def check(trace, lib=None) -> dict:
     return check_arrays(trace.events, trace.barrier_counts, trace.n_blocks, trace.block_threads,
                         trace.shared_units, trace.global_units, trace.max_barriers, getattr(trace, "flags", 0),
                         lib=lib)
+
+
+def fitness_arrays(events, barrier_counts, n_blocks, block_threads, shared_units, global_units,
+                   max_barriers, flags=0, lib=None) -> dict:
+    """Eq. 1 of the paper on raw arrays: sum g (addresses accessed), sum f (distinct (address, thread)
+    pairs) and the accessed unit range of each space; validation as for check()."""
+    lib = lib or _lib()
+    ev = np.ascontiguousarray(events, dtype=np.uint32).reshape(-1, 4)
+    cn = np.ascontiguousarray(barrier_counts, dtype=np.uint32)
+    if cn.size != n_blocks * block_threads:
+        raise ValueError("barrier_counts must hold n_blocks * block_threads entries")
+    kind, idx = ctypes.c_uint32(), ctypes.c_uint64()
+    na, npairs = ctypes.c_uint64(), ctypes.c_uint64()
+    rng = (ctypes.c_uint32 * 4)()
+    st = lib.orc_fitness(ev.ctypes.data_as(ctypes.c_void_p), ev.shape[0], cn.ctypes.data_as(ctypes.c_void_p),
+                         n_blocks, block_threads, shared_units, global_units, max_barriers, flags,
+                         ctypes.byref(kind), ctypes.byref(idx), ctypes.byref(na), ctypes.byref(npairs), rng)
+    if st == ENOMEM:
+        raise MemoryError("oracle ran out of host memory")
+    return dict(status=int(st), bad_kind=int(kind.value), bad_index=int(idx.value), n_addresses=int(na.value),
+                n_pairs=int(npairs.value), shared_lo=int(rng[0]), shared_hi=int(rng[1]), global_lo=int(rng[2]),
+                global_hi=int(rng[3]))
+
+
+def fitness(trace, lib=None) -> dict:
+    """fitness_arrays() on a trace object."""
+    return fitness_arrays(trace.events, trace.barrier_counts, trace.n_blocks, trace.block_threads,
+                          trace.shared_units, trace.global_units, trace.max_barriers, getattr(trace, "flags", 0),
+                          lib=lib)

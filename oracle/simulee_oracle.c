@@ -357,6 +357,64 @@ orc_result *orc_check(const uint32_t *ev, uint64_t n, const uint32_t *counts, ui
     return res;
 }
 
+/* ---- fitness (Sec. 3.3.1, Eq. 1) --------------------------------------------
+ * For memory address i: f(i) = the number of distinct threads that access i,
+ * g(i) = 1 when some thread accesses i. Eq. 1's fitness is sum g / sum f. An
+ * address is a global unit (one for the whole grid) or a shared unit of one
+ * block; a thread is its global id block * block_threads + tid; all epochs and
+ * actions count. Also returned: the accessed unit range [lo, hi] of each space
+ * (the secondary fitness R = end - start; lo = 0xFFFFFFFF, hi = 0 when the
+ * space is not accessed). The trace is validated exactly as by orc_check.
+ * Written out directly: sort the (space, block or 0, unit, gtid) tuples, count
+ * distinct tuples and distinct (space, block or 0, unit) prefixes. */
+typedef struct { uint32_t space, block, unit, gtid; } ftuple;
+
+static int cmp_ftuple(const void *a, const void *b) {
+    const ftuple *x = (const ftuple *)a, *y = (const ftuple *)b;
+    if (x->space != y->space) return x->space < y->space ? -1 : 1;
+    if (x->block != y->block) return x->block < y->block ? -1 : 1;
+    if (x->unit != y->unit) return x->unit < y->unit ? -1 : 1;
+    if (x->gtid != y->gtid) return x->gtid < y->gtid ? -1 : 1;
+    return 0;
+}
+
+/* Returns ORC_OK, ORC_EBADTRACE (bad_kind / bad_index set) or ORC_ENOMEM.
+ * out6 = {n_addresses, n_pairs} as uint64; range4 = {shared lo, shared hi, global lo, global hi}. */
+int32_t orc_fitness(const uint32_t *ev, uint64_t n, const uint32_t *counts, uint32_t nb, uint32_t bt,
+                    uint32_t su, uint32_t gu, uint32_t maxb, uint32_t flags, uint32_t *bad_kind,
+                    uint64_t *bad_index, uint64_t *n_addresses, uint64_t *n_pairs, uint32_t *range4) {
+    *bad_kind = 0;
+    *bad_index = 0;
+    *n_addresses = 0;
+    *n_pairs = 0;
+    range4[0] = range4[2] = 0xFFFFFFFFu;
+    range4[1] = range4[3] = 0;
+    if (validate(ev, n, counts, nb, bt, su, gu, maxb, flags, bad_kind, bad_index)) return ORC_EBADTRACE;
+    ftuple *t = (ftuple *)malloc((n ? n : 1) * sizeof(ftuple));
+    if (!t) return ORC_ENOMEM;
+    for (uint64_t i = 0; i < n; i++) {
+        const uint32_t *w = ev + 4 * i;
+        const uint32_t space = (w[3] >> 30) & 1u, unit = w[0], block = w[2], tid = w[3] & 0xFFFFu;
+        t[i].space = space;
+        t[i].block = space ? 0u : block;
+        t[i].unit = unit;
+        t[i].gtid = block * bt + tid;
+        uint32_t *lo = &range4[2 * space], *hi = &range4[2 * space + 1];
+        if (unit < *lo) *lo = unit;
+        if (unit > *hi) *hi = unit;
+    }
+    qsort(t, n, sizeof(ftuple), cmp_ftuple);
+    for (uint64_t i = 0; i < n; i++) {
+        const int new_pair = i == 0 || cmp_ftuple(&t[i - 1], &t[i]) != 0;
+        const int new_addr = i == 0 || t[i - 1].space != t[i].space || t[i - 1].block != t[i].block ||
+                             t[i - 1].unit != t[i].unit;
+        *n_pairs += (uint64_t)new_pair;
+        *n_addresses += (uint64_t)new_addr;
+    }
+    free(t);
+    return ORC_OK;
+}
+
 /* flat accessors for foreign-function callers */
 int32_t orc_status(const orc_result *r) { return r->status; }
 uint32_t orc_bad_kind(const orc_result *r) { return r->bad_kind; }
