@@ -343,6 +343,70 @@ def batch_arm(args):
             "launches_per_step": chk.last_launches(), "workspace_bytes": ws.numel(), "gen_s": gen_s}
 
 
+def fitness_arm(args):
+    """Fitness of Eq. 1 (distinct addresses / distinct address-thread pairs) over the grid workload: records
+    per second through simulee_fitness_batch, with the radix plan's algorithmic bytes against the HBM peak."""
+    import ctypes
+    import torch
+    import tracegen
+    from paper_1905_01833_gb300 import simulee
+    tr = make_trace(0, args.blocks)
+    dt = simulee.to_device(tr)
+    chk = simulee.Checker(0)
+    arr = (simulee.Trace * 1)(dt.c())
+    ws = chk.workspace(chk.fitness_workspace_size([dt]))
+    out = torch.zeros(simulee.FITNESS_BYTES, dtype=torch.uint8, device="cuda:0")
+    stream = torch.cuda.current_stream()
+    L = simulee.lib()
+
+    def step():
+        st = L.simulee_fitness_batch(chk.h, arr, 1, ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(ws.data_ptr()),
+                                     ws.numel(), ctypes.c_void_p(stream.cuda_stream))
+        if st != simulee.OK:
+            raise RuntimeError(f"simulee_fitness_batch failed: {simulee.status_str(st)}")
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches = chk.last_launches()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(1, min(args.steps, 50))
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    f = simulee.Fitness.from_buffer_copy(out.cpu().numpy().tobytes())
+    assert f.status == 0
+    # key bits: gtid + unit + block + space (one trace): radix passes of 8 bits, 8-byte keys when wider than 32 bits
+    kb = bits(tr.n_blocks * tr.block_threads) + bits(max(tr.shared_units, tr.global_units)) + bits(tr.n_blocks) + 1
+    npass, kw = -(-kb // 8), (8 if kb > 32 else 4)
+    n = tr.n_events
+    algo = n * (16 + kw + 2 * npass * kw + kw) + 4 * tr.barrier_counts.size   # read, key write, passes, count
+    peak, peak_src = peaks()
+    line = {"workload": f"fitness (Eq. 1) over the grid workload ({tr.n_blocks} blocks, {n} records)",
+            "unit": UNIT, "value": n / (ms * 1e-3) / 1e9, "ms_per_step": ms, "steps": steps,
+            "launches_per_step": launches, "key_bits": kb, "radix_passes": npass,
+            "result": {"n_addresses": f.n_addresses, "n_pairs": f.n_pairs, "F": f.n_addresses / max(f.n_pairs, 1),
+                       "shared_range": [f.shared_lo, f.shared_hi], "global_range": [f.global_lo, f.global_hi]},
+            "roofline": {"bound": "hbm", "achieved": algo / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": algo / (ms * 1e-3) / 1e9 / peak, "peak_source": peak_src,
+                         "bytes_per_step": algo}}
+    if not args.no_cpu_baseline:
+        import oracle
+        sel = tr.events[:, 2] < args.oracle_blocks
+        sub = tracegen.Trace(tr.events[sel].copy(), tr.barrier_counts, tr.n_blocks, tr.block_threads,
+                             tr.shared_units, tr.global_units, tr.max_barriers)
+        t0 = time.perf_counter()
+        o = oracle.fitness(sub)
+        secs = time.perf_counter() - t0
+        assert o["status"] == 0
+        line["cpu_baseline"] = {"value": int(sel.sum()) / secs / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"records of blocks 0..{args.oracle_blocks - 1} ({int(sel.sum())} records, "
+                                          f"{secs:.1f} s, single thread)"}
+    return line
+
+
 def serve_arm(args):
     """Serving workload: Poisson arrivals of check jobs, sizes log-uniform 1e4..1e8 records from the
     grid and barrier generators, continuous batching under a 120 GB HBM budget, against serial checking."""
@@ -406,18 +470,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--blocks", type=int, default=1024, help="grid blocks (1024 = the benchmark workload; "
                     "smaller values only for profiling captures)")
-    ap.add_argument("--workload", choices=["grid", "batch", "serve"], default="grid",
-                    help="grid: the benchmark line; batch / serve: the batched and served forms (separate lines)")
+    ap.add_argument("--workload", choices=["grid", "batch", "serve", "fitness"], default="grid",
+                    help="grid: the benchmark line; batch / serve: the batched and served forms; fitness: Eq. 1 "
+                         "over the grid workload (separate lines)")
     ap.add_argument("--batch-traces", type=int, default=4096)
     ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--serve-pool", type=int, default=24)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 1000.0, 4000.0])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    if args.workload in ("batch", "serve") and args.impl == "ours":
+    if args.workload in ("batch", "serve", "fitness") and args.impl == "ours":
         import torch
         torch.cuda.set_device(0)
-        out = batch_arm(args) if args.workload == "batch" else serve_arm(args)
+        out = {"batch": batch_arm, "serve": serve_arm, "fitness": fitness_arm}[args.workload](args)
         print(json.dumps({"metric": METRIC, **out}))
         return
 

@@ -240,6 +240,42 @@ simulee_status simulee_check_batch(simulee_ctx *ctx, const simulee_trace *traces
                                    size_t ws_bytes, void *stream);
 
 /*
+ * Fitness of a batch of traces: Eq. 1 of the paper (Sec. 3.3.1, "Intuition")
+ * and its secondary fitness R = end - start (Sec. 3.3.2, "Fitness Function"),
+ * the scores that guide the evolutionary input generation (Algorithm 1).
+ * For memory address i, f(i) = number of distinct threads that access i and
+ * g(i) = 1 when i is accessed; F = sum g / sum f (1 when no two threads share
+ * an address). An address is a global unit or a shared unit of one block; a
+ * thread is block * block_threads + tid; every epoch and action counts.
+ * Per trace (out: device array of n_traces, 48 bytes each):
+ *   status / bad_kind / bad_index: as in simulee_report (the trace is
+ *     validated exactly as by the check; a bad trace reports zero sums);
+ *   n_addresses = sum g, n_pairs = sum f (F = n_addresses / n_pairs; a trace
+ *     without records has both 0);
+ *   shared_lo..hi, global_lo..hi: the accessed unit range of each space
+ *     (lo = 0xFFFFFFFF, hi = 0 when the space is not accessed), from which
+ *     R = hi - lo of the range the caller's kernel model uses.
+ * Limits beyond the check's: the key (trace index, space, block, unit, global
+ * thread id) must fit 64 bits (SIMULEE_EINVAL otherwise). traces is a host
+ * array read during the call; ws: caller-owned device workspace of at least
+ * simulee_fitness_workspace_size bytes, 256-byte aligned. Asynchronous on
+ * `stream`.
+ */
+typedef struct {
+    int32_t status;
+    uint32_t bad_kind;
+    uint64_t bad_index;
+    uint64_t n_addresses;
+    uint64_t n_pairs;
+    uint32_t shared_lo, shared_hi;
+    uint32_t global_lo, global_hi;
+} simulee_fitness;
+simulee_status simulee_fitness_workspace_size(simulee_ctx *ctx, const simulee_trace *traces, uint32_t n_traces,
+                                              size_t *bytes);
+simulee_status simulee_fitness_batch(simulee_ctx *ctx, const simulee_trace *traces, uint32_t n_traces,
+                                     simulee_fitness *out, void *ws, size_t ws_bytes, void *stream);
+
+/*
  * Diagnostics.
  * simulee_last_launches: kernels launched by the last check call on this context.
  * simulee_set_stage_events: optional CUDA events (cudaEvent_t, created by the caller

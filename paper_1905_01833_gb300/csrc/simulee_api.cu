@@ -26,6 +26,7 @@
 #include "../../include/simulee.h"
 #include "check_kernels.cuh"
 #include "hash_path.cuh"
+#include "fitness.cuh"
 #include "sort.cuh"
 
 using namespace simk;
@@ -648,6 +649,158 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     return e == cudaSuccess ? SIMULEE_OK : SIMULEE_ECUDA;
 }
 
+// ---- fitness (Eq. 1) -------------------------------------------------------------------------
+static_assert(sizeof(simulee_fitness) == FIT_OUT_BYTES, "simulee_fitness layout");
+struct FitPlan {
+    Layout L;       // the fields the validation kernels read (n, T, NB, ntiles_in, maxb)
+    FitKeys fk;
+    bool wide;
+    uint64_t status_tiles;
+    size_t off_ctl, off_ts, off_acc, off_hist, off_td, off_tob, off_stats, off_dbase, off_status, off_k[2];
+    size_t zero_end, total;
+};
+
+simulee_status fit_plan(const simulee_trace *tr, uint32_t T, FitPlan &P) {
+    memset(&P, 0, sizeof P);
+    if (!tr || T == 0 || T > kMaxTraces) return SIMULEE_EINVAL;
+    uint64_t n = 0, nb = 0, tiles = 0, maxthreads = 0;
+    uint32_t maxb = 0, maxnb = 0, units = 0;
+    for (uint32_t i = 0; i < T; i++) {
+        const simulee_status s = check_trace_args(&tr[i]);
+        if (s != SIMULEE_OK) return s;
+        n += tr[i].n_events;
+        nb += tr[i].n_blocks;
+        tiles += (tr[i].n_events + IN_TILE - 1) / IN_TILE;
+        maxb = std::max(maxb, tr[i].max_barriers);
+        maxnb = std::max(maxnb, tr[i].n_blocks);
+        units = std::max(units, std::max(tr[i].shared_units, tr[i].global_units));
+        maxthreads = std::max<uint64_t>(maxthreads, (uint64_t)tr[i].n_blocks * tr[i].block_threads);
+    }
+    if (n >= (1ull << 31) || nb >= (1ull << 31)) return SIMULEE_EINVAL;
+    Layout &L = P.L;
+    L.n = n;
+    L.T = T;
+    L.NB = (uint32_t)nb;
+    L.ntiles_in = tiles;
+    L.maxb = maxb;
+    FitKeys &f = P.fk;
+    f.bg = bits_for(maxthreads);
+    f.bu = bits_for(units);
+    f.bbl = bits_for(maxnb);
+    f.btr = bits_for(T);
+    f.bits = f.bg + f.bu + f.bbl + 1 + f.btr;
+    if (f.bits > 64) return SIMULEE_EINVAL;
+    f.np = passes_for(f.bits);
+    if (f.np > 8) return SIMULEE_EINVAL;
+    P.wide = f.bits > 32;
+    const uint64_t n1 = std::max<uint64_t>(n, 1);
+    P.status_tiles = (n1 + OS_TILE - 1) / OS_TILE;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes); return r; };
+    P.off_ctl = take(sizeof(Ctl));
+    P.off_ts = take((size_t)T * sizeof(TState));
+    P.off_hist = take((size_t)8 * RADIX * 4);
+    P.zero_end = o;
+    P.off_acc = take((size_t)T * sizeof(FitAcc));
+    P.off_td = take((size_t)T * sizeof(TraceDesc));
+    P.off_tob = take((size_t)nb * 4);
+    P.off_stats = take((size_t)nb * 16);
+    P.off_dbase = take((size_t)8 * RADIX * 4);
+    P.off_status = take((size_t)P.status_tiles * RADIX * 8);
+    for (int i = 0; i < 2; i++) P.off_k[i] = take(n1 * (P.wide ? 8 : 4));
+    P.total = o;
+    return SIMULEE_OK;
+}
+
+simulee_status run_fitness(simulee_ctx *ctx, const simulee_trace *traces, uint32_t T, simulee_fitness *out, void *ws,
+                           size_t ws_bytes, void *stream) {
+    if (!ctx || !traces || !out || !ws || T == 0) return SIMULEE_EINVAL;
+    if (((uintptr_t)ws & 255u) != 0) return SIMULEE_EINVAL;
+    FitPlan P;
+    simulee_status s = fit_plan(traces, T, P);
+    if (s != SIMULEE_OK) return s;
+    if (ws_bytes < P.total) return SIMULEE_ENOMEM;
+    int prev_dev = -1;
+    cudaGetDevice(&prev_dev);
+    if (prev_dev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return SIMULEE_ECUDA;
+    const Layout &L = P.L;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint8_t *w = (uint8_t *)ws;
+    Ctl *ctl = reinterpret_cast<Ctl *>(w + P.off_ctl);
+    TState *ts = reinterpret_cast<TState *>(w + P.off_ts);
+    FitAcc *acc = reinterpret_cast<FitAcc *>(w + P.off_acc);
+    TraceDesc *td = reinterpret_cast<TraceDesc *>(w + P.off_td);
+    uint32_t *tob = reinterpret_cast<uint32_t *>(w + P.off_tob);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(w + P.off_hist);
+    uint32_t *dbase = reinterpret_cast<uint32_t *>(w + P.off_dbase);
+    const uint64_t wait_ns = (uint64_t)(ctx->opt.wait_limit_us ? ctx->opt.wait_limit_us : 1000000u) * 1000ull;
+    uint32_t launches = 0;
+    auto grid_for = [&](uint64_t items, uint64_t per_cta, uint64_t per_sm) {
+        return (int)std::max<uint64_t>(1, std::min<uint64_t>((items + per_cta - 1) / per_cta, (uint64_t)ctx->sms * per_sm));
+    };
+    cudaMemsetAsync(w, 0, P.zero_end, st);
+    cudaMemsetAsync(w + P.off_status, 0, (size_t)P.status_tiles * RADIX * 8, st);
+    // descriptors: the check's, without outputs
+    std::vector<simulee_outputs> no_out(T);
+    memset(no_out.data(), 0, T * sizeof(simulee_outputs));
+    std::vector<uint8_t *> no_rep(T, nullptr);
+    std::vector<TraceDesc> hdesc;
+    fill_descs(traces, no_out.data(), no_rep.data(), T, hdesc);
+    for (uint32_t i = 0; i < T; i += kDescChunk) {
+        DescChunk c;
+        const uint32_t cnt = std::min<uint32_t>(kDescChunk, T - i);
+        memcpy(c.d, hdesc.data() + i, cnt * sizeof(TraceDesc));
+        k_set_desc<<<1, kDescChunk, 0, st>>>(td + i, c, cnt);
+        launches++;
+    }
+    k_fit_init<<<grid_for(T, 256, 1), 256, 0, st>>>(acc, T);
+    k_block_trace<<<grid_for(L.NB, 256, 8), 256, 0, st>>>(td, L, tob);
+    k_block_stats<<<grid_for(L.NB, 8, 16), 256, 0, st>>>(td, tob, L, reinterpret_cast<uint4 *>(w + P.off_stats), ts);
+    launches += 3;
+    if (L.n > 0) {
+        // validation: the check's record read, validation only
+        if (!attr_done(ctx, k_ingest<uint32_t, uint32_t, uint32_t, IN_VALIDATE>))
+            cudaFuncSetAttribute(k_ingest<uint32_t, uint32_t, uint32_t, IN_VALIDATE>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ingest_smem());
+        const int gi = grid_for(L.ntiles_in, 1, 2);
+        k_ingest<uint32_t, uint32_t, uint32_t, IN_VALIDATE><<<gi, IN_THREADS, ingest_smem(), st>>>(
+            td, nullptr, L, ts, ctl, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, hist, nullptr, nullptr,
+            nullptr, nullptr, wait_ns);
+        k_set_count<<<1, 1, 0, st>>>(&ctl->n_q, (unsigned int)L.n);
+        const int gk = grid_for(L.ntiles_in, 1, 8);
+        const int gs = grid_for(L.n, OS_TILE, 3);
+        launches += 2;
+#define SIM_FIT(K)                                                                                                 \
+    do {                                                                                                           \
+        if (!attr_done(ctx, k_onesweep<K>))                                                                        \
+            cudaFuncSetAttribute(k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem<K>()); \
+        K *k0 = reinterpret_cast<K *>(w + P.off_k[0]), *k1 = reinterpret_cast<K *>(w + P.off_k[1]);                 \
+        k_fit_keys<K><<<gk, FK_THREADS, 0, st>>>(td, L, P.fk, k0, hist, acc);                                      \
+        k_digit_bases<<<P.fk.np, RADIX, 0, st>>>(hist, dbase, ctl);                                                \
+        launches += 2;                                                                                             \
+        K *bufs[2] = {k0, k1};                                                                                     \
+        for (uint32_t p = 0; p < P.fk.np; p++) {                                                                   \
+            k_onesweep<K><<<gs, OS_THREADS, onesweep_smem<K>(), st>>>(                                             \
+                bufs[p & 1], nullptr, bufs[(p & 1) ^ 1], nullptr, &ctl->n_q, L.n, RADIX_BITS * p,                  \
+                dbase + (size_t)p * RADIX, reinterpret_cast<unsigned long long *>(w + P.off_status), p + 1,        \
+                &ctl->tiles[p], ctl, wait_ns, 0u);                                                                 \
+            launches++;                                                                                            \
+        }                                                                                                          \
+        k_fit_count<K><<<grid_for(L.n, 256, 8), 256, 0, st>>>(bufs[P.fk.np & 1], &ctl->n_q, P.fk, T, acc, ctl);    \
+        launches++;                                                                                                \
+    } while (0)
+        if (P.wide) SIM_FIT(uint64_t);
+        else SIM_FIT(uint32_t);
+#undef SIM_FIT
+    }
+    k_fit_report<<<grid_for(T, 256, 1), 256, 0, st>>>(ts, acc, T, ctl, reinterpret_cast<uint8_t *>(out));
+    launches++;
+    ctx->last_launches = launches;
+    const cudaError_t e = cudaGetLastError();
+    if (prev_dev >= 0 && prev_dev != ctx->device) cudaSetDevice(prev_dev);
+    return e == cudaSuccess ? SIMULEE_OK : SIMULEE_ECUDA;
+}
+
 simulee_status launch_check(simulee_ctx *ctx, const simulee_trace *t, const simulee_outputs *out, Want want,
                             simulee_report *report, void *ws, size_t ws_bytes, void *stream) {
     if (!out || !report) return SIMULEE_EINVAL;
@@ -743,6 +896,21 @@ simulee_status simulee_check_batch(simulee_ctx *ctx, const simulee_trace *traces
     std::vector<uint8_t *> reps(n_traces);
     for (uint32_t i = 0; i < n_traces; i++) reps[i] = (uint8_t *)(reports + i);
     return run_check(ctx, traces, n_traces, outs, reps.data(), Want{true, true, true}, ws, ws_bytes, stream);
+}
+
+simulee_status simulee_fitness_workspace_size(simulee_ctx *ctx, const simulee_trace *traces, uint32_t n_traces,
+                                              size_t *bytes) {
+    if (!ctx || !traces || !bytes) return SIMULEE_EINVAL;
+    FitPlan P;
+    const simulee_status s = fit_plan(traces, n_traces, P);
+    if (s != SIMULEE_OK) return s;
+    *bytes = P.total;
+    return SIMULEE_OK;
+}
+
+simulee_status simulee_fitness_batch(simulee_ctx *ctx, const simulee_trace *traces, uint32_t n_traces,
+                                     simulee_fitness *out, void *ws, size_t ws_bytes, void *stream) {
+    return run_fitness(ctx, traces, n_traces, out, ws, ws_bytes, stream);
 }
 
 uint32_t simulee_last_launches(const simulee_ctx *ctx) { return ctx ? ctx->last_launches : 0u; }

@@ -10,7 +10,8 @@
 // bounded by wall time (%globaltimer); a wait that gives up sets ctl->timeout,
 // which makes every other waiter stop at once, and the call reports ETIMEOUT.
 // Ranking within a tile is stable, tiles are ordered by claim order, so each
-// pass is stable and the LSD sort is correct.
+// pass is stable and the LSD sort is correct. With vin == vout == NULL the
+// pass moves keys only.
 #pragma once
 #include "common.cuh"
 
@@ -158,7 +159,7 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
                 const uint32_t d = rd[j] >> 16;
                 const uint32_t pos = texcl[d] + whist[w][d] + (rd[j] & 0xFFFFu);
                 skeys[pos] = k[j];
-                svals[pos] = vin[base + li];
+                if (vin) svals[pos] = vin[base + li];
             }
         }
         __syncthreads();
@@ -168,7 +169,7 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
             const uint64_t o = gbase[d] + (i - texcl[d]);
             if (o < n) {   // always true unless a wait gave up and the offsets are unreliable
                 kout[o] = kk;
-                vout[o] = svals[i];
+                if (vout) vout[o] = svals[i];
             }
         }
         __syncthreads();

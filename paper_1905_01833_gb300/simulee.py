@@ -59,7 +59,15 @@ class Options(ctypes.Structure):
                 ("reduce_ctas_per_sm", ctypes.c_uint32), ("hash_shape", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
+class Fitness(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("bad_kind", ctypes.c_uint32), ("bad_index", ctypes.c_uint64),
+                ("n_addresses", ctypes.c_uint64), ("n_pairs", ctypes.c_uint64),
+                ("shared_lo", ctypes.c_uint32), ("shared_hi", ctypes.c_uint32),
+                ("global_lo", ctypes.c_uint32), ("global_hi", ctypes.c_uint32)]
+
+
 REPORT_BYTES = ctypes.sizeof(Report)
+FITNESS_BYTES = ctypes.sizeof(Fitness)
 _lib_handle = None
 
 
@@ -86,6 +94,8 @@ def lib():
         sigs["simulee_set_stage_events"] = [vp, P(vp), u32]
         sigs["simulee_check_noalloc"] = [vp, P(Trace), P(Outputs), vp, vp]
         sigs["simulee_stream_sizes"] = [vp, vp, vp, vp]
+        sigs["simulee_fitness_workspace_size"] = [vp, P(Trace), u32, P(ctypes.c_size_t)]
+        sigs["simulee_fitness_batch"] = [vp, P(Trace), u32, vp, vp, ctypes.c_size_t, vp]
         for name, args in sigs.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -257,6 +267,31 @@ class Checker:
         _check(lib().simulee_batch_workspace_size(self.h, arr, len(dts), ctypes.byref(n)),
                "simulee_batch_workspace_size")
         return int(n.value)
+
+    def fitness_workspace_size(self, dts) -> int:
+        T = len(dts)
+        arr = (Trace * T)(*[d.c() for d in dts])
+        n = ctypes.c_size_t()
+        _check(lib().simulee_fitness_workspace_size(self.h, arr, T, ctypes.byref(n)), "simulee_fitness_workspace_size")
+        return int(n.value)
+
+    def fitness_batch(self, dts, stream=None) -> list[dict]:
+        """Eq. 1 fitness of each trace: sum g, sum f (F = n_addresses / n_pairs) and the unit ranges."""
+        torch = self.torch
+        T = len(dts)
+        out = torch.zeros(T * FITNESS_BYTES, dtype=torch.uint8, device=f"cuda:{self.device}")
+        arr = (Trace * T)(*[d.c() for d in dts])
+        ws = self.workspace(self.fitness_workspace_size(dts))
+        _check(lib().simulee_fitness_batch(self.h, arr, T, ctypes.c_void_p(out.data_ptr()),
+                                           ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)),
+               "simulee_fitness_batch")
+        torch.cuda.synchronize(self.device)
+        raw = out.cpu().numpy().tobytes()
+        res = []
+        for i in range(T):
+            f = Fitness.from_buffer_copy(raw[i * FITNESS_BYTES:(i + 1) * FITNESS_BYTES])
+            res.append({name: int(getattr(f, name)) for name, _ in Fitness._fields_})
+        return res
 
     def check_batch(self, dts, races_caps=None, stream=None) -> list[dict]:
         """Check independent traces in one batched call; returns one result dict per trace."""

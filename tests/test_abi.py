@@ -53,8 +53,9 @@ def test_binding_structs_match_header(tmp_path):
 #include <stddef.h>
 #include "simulee.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(simulee_trace), sizeof(simulee_outputs), sizeof(simulee_report),
-         sizeof(simulee_options), sizeof(simulee_race), sizeof(simulee_divergence), sizeof(simulee_barrier));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(simulee_trace), sizeof(simulee_outputs), sizeof(simulee_report),
+         sizeof(simulee_options), sizeof(simulee_race), sizeof(simulee_divergence), sizeof(simulee_barrier),
+         sizeof(simulee_fitness));
   printf("%zu %zu %zu %zu\\n", offsetof(simulee_trace, barrier_counts), offsetof(simulee_trace, flags),
          offsetof(simulee_report, n_grid_redundant), offsetof(simulee_race, gtid_second));
   return 0;
@@ -66,7 +67,8 @@ int main(void) {
     sizes = [int(x) for x in a.split()]
     offs = [int(x) for x in b.split()]
     assert sizes == [ctypes.sizeof(S.Trace), ctypes.sizeof(S.Outputs), ctypes.sizeof(S.Report),
-                     ctypes.sizeof(S.Options), S.RACE_DTYPE.itemsize, S.DIV_DTYPE.itemsize, S.BAR_DTYPE.itemsize]
+                     ctypes.sizeof(S.Options), S.RACE_DTYPE.itemsize, S.DIV_DTYPE.itemsize, S.BAR_DTYPE.itemsize,
+                     ctypes.sizeof(S.Fitness)]
     assert offs == [S.Trace.barrier_counts.offset, S.Trace.flags.offset, S.Report.n_grid_redundant.offset,
                     S.RACE_DTYPE.fields["gtid_second"][1]]
 
