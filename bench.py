@@ -407,6 +407,53 @@ def fitness_arm(args):
     return line
 
 
+def evolve_arm(args):
+    """Evolutionary search (Algorithms 1 and 2: population 50, 3 generations, acceptable F < 0.3) over the
+    copy2d and stencil model kernels at full dimension limits: every generation's children are generated on
+    the device and scored by one batched fitness call; the best launch is then checked."""
+    import torch
+    from paper_1905_01833_gb300 import evolve, simulee
+    chk = simulee.Checker(0)
+    scorer = evolve.DeviceScorer(chk)
+    out = {"workload": "evolve: population 50, 3 generations, copy2d (grid <= 16x16, block <= 32x32) and stencil "
+                       "(grid <= 64, block <= 1024)", "unit": "candidates/s", "models": {}}
+    for name, model in (("copy2d", simulee.MODEL_COPY2D), ("stencil", simulee.MODEL_STENCIL)):
+        ev = evolve.Evolution(model, scorer, population=50, generations=3, seed=args.steps)
+        calls = {"n": 0, "records": 0, "secs": 0.0}
+
+        def timed(sols, _inner=scorer):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = _inner(sols)
+            torch.cuda.synchronize()
+            calls["secs"] += time.perf_counter() - t0
+            calls["n"] += len(sols)
+            calls["records"] += sum(tracegen_events(s) for s in sols)
+            return res
+        ev.scorer = timed
+        timed([ev.initial() for _ in range(4)])   # warm-up
+        calls.update(n=0, records=0, secs=0.0)
+        t0 = time.perf_counter()
+        r = ev.run()
+        wall = time.perf_counter() - t0
+        rep = evolve.detect(chk, r["best"])
+        b = r["best"]
+        out["models"][name] = {
+            "candidates": calls["n"], "records": calls["records"], "scoring_s": calls["secs"], "wall_s": wall,
+            "value": calls["n"] / calls["secs"], "records_per_s": calls["records"] / calls["secs"],
+            "generations": r["generations"], "accepted": r["accepted"], "best_F": b.F, "best_R": b.R,
+            "best_launch": {"grid": b.dims[:2], "block": b.dims[2:], "args": [int(a) for a in b.args]},
+            "check": {"status": rep["status"], "races": len(rep["races"]), "redundant": len(rep["redundant"]),
+                      "divergence": len(rep["divergence"])}}
+    return out
+
+
+def tracegen_events(sol) -> int:
+    import tracegen
+    model, grid, block, _ = sol.launch()
+    return tracegen.model_events(model, grid, block)
+
+
 def serve_arm(args):
     """Serving workload: Poisson arrivals of check jobs, sizes log-uniform 1e4..1e8 records from the
     grid and barrier generators, continuous batching under a 120 GB HBM budget, against serial checking."""
@@ -470,7 +517,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--blocks", type=int, default=1024, help="grid blocks (1024 = the benchmark workload; "
                     "smaller values only for profiling captures)")
-    ap.add_argument("--workload", choices=["grid", "batch", "serve", "fitness"], default="grid",
+    ap.add_argument("--workload", choices=["grid", "batch", "serve", "fitness", "evolve"], default="grid",
                     help="grid: the benchmark line; batch / serve: the batched and served forms; fitness: Eq. 1 "
                          "over the grid workload (separate lines)")
     ap.add_argument("--batch-traces", type=int, default=4096)
@@ -479,10 +526,10 @@ def main():
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 1000.0, 4000.0])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    if args.workload in ("batch", "serve", "fitness") and args.impl == "ours":
+    if args.workload in ("batch", "serve", "fitness", "evolve") and args.impl == "ours":
         import torch
         torch.cuda.set_device(0)
-        out = {"batch": batch_arm, "serve": serve_arm, "fitness": fitness_arm}[args.workload](args)
+        out = {"batch": batch_arm, "serve": serve_arm, "fitness": fitness_arm, "evolve": evolve_arm}[args.workload](args)
         print(json.dumps({"metric": METRIC, **out}))
         return
 

@@ -276,6 +276,42 @@ simulee_status simulee_fitness_batch(simulee_ctx *ctx, const simulee_trace *trac
                                      simulee_fitness *out, void *ws, size_t ws_bytes, void *stream);
 
 /*
+ * Parametric model kernels: the inputs of the evolutionary search for
+ * error-inducing launch configurations (Algorithms 1 and 2). Each model
+ * stands for a small CUDA kernel; simulee_model_traces writes, for a batch
+ * of launch configurations, the traces their simulated executions record
+ * (schedule order block, epoch, slot, thread; visit order = serial position
+ * within the launch), ready for simulee_fitness_batch and simulee_check.
+ *   SIMULEE_MODEL_COPY2D (kaldi's _copy_from_mat of Sec. 2): thread (x, y) of
+ *     block (bx, by), X = bx * block_x + x, Y = by * block_y + y, reads global
+ *     unit (Y * arg1 + X) mod 2^19 and writes global unit
+ *     2^19 + (Y * arg0 + X) mod 2^19; no barrier (barrier counts 0).
+ *   SIMULEE_MODEL_STENCIL: 1-D blocks (block_y must be 1); thread t writes
+ *     shared unit (t * arg1) mod 4096, passes one barrier, reads shared unit
+ *     (t * arg1 + arg0) mod 4096 and writes global unit
+ *     (block * block_x + t) mod 2^20 (barrier counts 1).
+ * Negative arguments count as 0. Traces use shared_units = 4096 and
+ * global_units = 2^20, n_blocks = grid_x * grid_y, block_threads =
+ * block_x * block_y (<= 1024). models: device array of n_models, sorted by
+ * events_off and by counts_off; launch i writes records
+ * [events_off, events_off + threads * (2 or 3)) of events and barrier counts
+ * [counts_off, counts_off + threads) of counts (device, caller-owned;
+ * n_events / n_counts: their lengths). Asynchronous on `stream`.
+ */
+enum { SIMULEE_MODEL_COPY2D = 0, SIMULEE_MODEL_STENCIL = 1 };
+typedef struct {
+    uint32_t model;
+    uint32_t grid_x, grid_y, block_x, block_y;
+    int32_t arg0, arg1;
+    uint32_t reserved;
+    uint64_t events_off;
+    uint64_t counts_off;
+} simulee_model;
+simulee_status simulee_model_traces(simulee_ctx *ctx, const simulee_model *models, uint32_t n_models,
+                                    simulee_event *events, uint64_t n_events, uint32_t *counts, uint64_t n_counts,
+                                    void *stream);
+
+/*
  * Diagnostics.
  * simulee_last_launches: kernels launched by the last check call on this context.
  * simulee_set_stage_events: optional CUDA events (cudaEvent_t, created by the caller

@@ -27,6 +27,7 @@
 #include "check_kernels.cuh"
 #include "hash_path.cuh"
 #include "fitness.cuh"
+#include "models.cuh"
 #include "sort.cuh"
 
 using namespace simk;
@@ -911,6 +912,24 @@ simulee_status simulee_fitness_workspace_size(simulee_ctx *ctx, const simulee_tr
 simulee_status simulee_fitness_batch(simulee_ctx *ctx, const simulee_trace *traces, uint32_t n_traces,
                                      simulee_fitness *out, void *ws, size_t ws_bytes, void *stream) {
     return run_fitness(ctx, traces, n_traces, out, ws, ws_bytes, stream);
+}
+
+simulee_status simulee_model_traces(simulee_ctx *ctx, const simulee_model *models, uint32_t n_models,
+                                    simulee_event *events, uint64_t n_events, uint32_t *counts, uint64_t n_counts,
+                                    void *stream) {
+    if (!ctx || !models || n_models == 0 || (n_events && !events) || (n_counts && !counts)) return SIMULEE_EINVAL;
+    if (((uintptr_t)events & 15u) != 0) return SIMULEE_EINVAL;
+    int prev_dev = -1;
+    cudaGetDevice(&prev_dev);
+    if (prev_dev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return SIMULEE_ECUDA;
+    const uint64_t work = std::max(n_events, n_counts);
+    const int g = (int)std::max<uint64_t>(1, std::min<uint64_t>((work + 255) / 256, (uint64_t)ctx->sms * 8));
+    k_model_traces<<<g, 256, 0, (cudaStream_t)stream>>>(models, n_models, n_events, reinterpret_cast<uint4 *>(events),
+                                                       n_counts, counts);
+    ctx->last_launches = 1;
+    const cudaError_t e = cudaGetLastError();
+    if (prev_dev >= 0 && prev_dev != ctx->device) cudaSetDevice(prev_dev);
+    return e == cudaSuccess ? SIMULEE_OK : SIMULEE_ECUDA;
 }
 
 uint32_t simulee_last_launches(const simulee_ctx *ctx) { return ctx ? ctx->last_launches : 0u; }

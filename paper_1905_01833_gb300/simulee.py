@@ -66,6 +66,16 @@ class Fitness(ctypes.Structure):
                 ("global_lo", ctypes.c_uint32), ("global_hi", ctypes.c_uint32)]
 
 
+class Model(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_uint32), ("grid_x", ctypes.c_uint32), ("grid_y", ctypes.c_uint32),
+                ("block_x", ctypes.c_uint32), ("block_y", ctypes.c_uint32), ("arg0", ctypes.c_int32),
+                ("arg1", ctypes.c_int32), ("reserved", ctypes.c_uint32), ("events_off", ctypes.c_uint64),
+                ("counts_off", ctypes.c_uint64)]
+
+
+MODEL_COPY2D, MODEL_STENCIL = 0, 1
+MODEL_SHARED_UNITS, MODEL_GLOBAL_UNITS = 4096, 1 << 20
+
 REPORT_BYTES = ctypes.sizeof(Report)
 FITNESS_BYTES = ctypes.sizeof(Fitness)
 _lib_handle = None
@@ -96,6 +106,7 @@ def lib():
         sigs["simulee_stream_sizes"] = [vp, vp, vp, vp]
         sigs["simulee_fitness_workspace_size"] = [vp, P(Trace), u32, P(ctypes.c_size_t)]
         sigs["simulee_fitness_batch"] = [vp, P(Trace), u32, vp, vp, ctypes.c_size_t, vp]
+        sigs["simulee_model_traces"] = [vp, vp, u32, vp, u64, vp, u64, vp]
         for name, args in sigs.items():
             f = getattr(L, name)
             f.argtypes = args
@@ -267,6 +278,37 @@ class Checker:
         _check(lib().simulee_batch_workspace_size(self.h, arr, len(dts), ctypes.byref(n)),
                "simulee_batch_workspace_size")
         return int(n.value)
+
+    def model_traces(self, launches, stream=None) -> list:
+        """Traces of model-kernel launches, generated on the device.
+
+        launches: sequence of (model, (grid_x, grid_y), (block_x, block_y), (arg0, arg1)) with integer
+        arguments. Returns DeviceTrace views into two shared device buffers."""
+        torch = self.torch
+        T = len(launches)
+        ms = (Model * T)()
+        ev_off = ct_off = 0
+        dims = []
+        for i, (model, grid, block, args) in enumerate(launches):
+            nb, bt = grid[0] * grid[1], block[0] * block[1]
+            ne = nb * bt * (2 if model == MODEL_COPY2D else 3)
+            ms[i] = Model(model, grid[0], grid[1], block[0], block[1], int(args[0]), int(args[1]), 0, ev_off, ct_off)
+            dims.append((ev_off, ne, ct_off, nb, bt, model))
+            ev_off += ne
+            ct_off += nb * bt
+        dev = f"cuda:{self.device}"
+        m_dev = torch.from_numpy(np.frombuffer(bytes(ms), dtype=np.uint8).copy()).to(dev)
+        ev = torch.empty((max(ev_off, 1), 4), dtype=torch.int32, device=dev)
+        cn = torch.empty(max(ct_off, 1), dtype=torch.int32, device=dev)
+        _check(lib().simulee_model_traces(self.h, ctypes.c_void_p(m_dev.data_ptr()), T, ctypes.c_void_p(ev.data_ptr()),
+                                          ev_off, ctypes.c_void_p(cn.data_ptr()), ct_off, _stream_ptr(stream)),
+               "simulee_model_traces")
+        out = []
+        for (eo, ne, co, nb, bt, model) in dims:
+            out.append(DeviceTrace(ev[eo:eo + ne], cn[co:co + nb * bt], nb, bt, MODEL_SHARED_UNITS,
+                                   MODEL_GLOBAL_UNITS, 0 if model == MODEL_COPY2D else 1))
+        self._model_bufs = (m_dev, ev, cn)   # keep the buffers alive with the views
+        return out
 
     def fitness_workspace_size(self, dts) -> int:
         T = len(dts)

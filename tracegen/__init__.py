@@ -294,3 +294,70 @@ class Builder:
             ev = np.zeros((0, 4), dtype=np.uint32)
         mb = int(self.counts.max()) if max_barriers is None and self.counts.size else (max_barriers or 0)
         return Trace(ev, self.counts.copy(), self.nb, self.bt, self.su, self.gu, mb)
+
+
+# --- parametric model kernels (inputs of the evolutionary search) -----------------
+#
+# Each model stands for a small CUDA kernel with grid and block dimensions and
+# integer arguments; a trace is what simulating one launch records (Algorithm 3's
+# schedule: block, epoch, slot, thread; visit order = serial position).
+#
+# copy2d (kaldi's _copy_from_mat, Sec. 2): 2-D blocks; thread (x, y) of block
+#   (bx, by) has column X = bx * block_x + x and row Y = by * block_y + y; it reads
+#   src[Y * a1 + X] and writes dst[Y * a0 + X] (global memory, no barrier). src is
+#   units [0, 2^19), dst units [2^19, 2^20), indices taken mod 2^19.
+# stencil: 1-D blocks of block_x threads (block_y = 1); thread t writes shared
+#   sh[(t * a1) mod 4096], passes one barrier, reads sh[(t * a1 + a0) mod 4096] and
+#   writes global out[(block * block_x + t) mod 2^20].
+# Arguments are integers (negative ones count as 0).
+MODEL_COPY2D, MODEL_STENCIL = 0, 1
+MODEL_GLOBAL_UNITS = 1 << 20
+MODEL_SHARED_UNITS = 4096
+_HALF = 1 << 19
+
+
+def model_events(model: int, grid: tuple, block: tuple) -> int:
+    """Records of one launch of a model kernel."""
+    threads = grid[0] * grid[1] * block[0] * block[1]
+    return threads * (2 if model == MODEL_COPY2D else 3)
+
+
+def model_trace(model: int, grid: tuple, block: tuple, args: tuple) -> Trace:
+    """Host reference of a model kernel's trace (plain loops over the schedule)."""
+    gx, gy = grid
+    bxd, byd = block
+    a0, a1 = max(0, int(args[0])), max(0, int(args[1]))   # negative arguments count as 0
+    nb, bt = gx * gy, bxd * byd
+    rows = []
+    if model == MODEL_COPY2D:
+        for b in range(nb):
+            bx, by = b % gx, b // gx
+            for slot in range(2):
+                for t in range(bt):
+                    x, y = t % bxd, t // bxd
+                    X, Y = bx * bxd + x, by * byd + y
+                    if slot == 0:
+                        rows.append(((Y * a1 + X) % _HALF, b, t, 0, READ, GLOBAL))
+                    else:
+                        rows.append((_HALF + (Y * a0 + X) % _HALF, b, t, 0, WRITE, GLOBAL))
+        counts = np.zeros(nb * bt, dtype=np.uint32)
+        maxb = 0
+    else:
+        for b in range(nb):
+            for t in range(bt):
+                rows.append(((t * a1) % MODEL_SHARED_UNITS, b, t, 0, WRITE, SHARED))
+            for slot in range(2):
+                for t in range(bt):
+                    if slot == 0:
+                        rows.append(((t * a1 + a0) % MODEL_SHARED_UNITS, b, t, 1, READ, SHARED))
+                    else:
+                        rows.append(((b * bxd + t) % MODEL_GLOBAL_UNITS, b, t, 1, WRITE, GLOBAL))
+        counts = np.ones(nb * bt, dtype=np.uint32)
+        maxb = 1
+    if rows:
+        unit, blk, tid, ep, act, sp = (np.array(c, dtype=np.int64) for c in zip(*rows))
+        ev = pack(unit, np.arange(len(rows)), blk, tid, ep, act, sp)
+    else:
+        ev = np.zeros((0, 4), dtype=np.uint32)
+    return Trace(ev, counts, nb, bt, MODEL_SHARED_UNITS, MODEL_GLOBAL_UNITS, maxb,
+                 meta=dict(kind="model", model=model, grid=(gx, gy), block=(bxd, byd), args=(a0, a1)))
