@@ -274,6 +274,7 @@ def batch_arm(args):
     from paper_1905_01833_gb300 import simulee
     dev = "cuda:0"
     sizes, bss, eps = tracegen.c3_sizes(n_traces=args.batch_traces)
+    base = None if args.no_cpu_baseline else batch_oracle_baseline(sizes, bss, eps)
     t0 = time.perf_counter()
     trs = [tracegen.c3_trace(i, int(n), int(bs), int(e)) for i, (n, bs, e) in enumerate(zip(sizes, bss, eps))]
     gen_s = time.perf_counter() - t0
@@ -340,7 +341,88 @@ def batch_arm(args):
                         f"block sizes 64..1024, 4..64 epochs", "traces": T, "n_events": n_ev,
             "value": n_ev / (ms * 1e-3) / 1e9, "ms_per_step": ms,
             "graph_value": n_ev / (ms_g * 1e-3) / 1e9, "graph_ms_per_step": ms_g, "unit": UNIT,
-            "launches_per_step": chk.last_launches(), "workspace_bytes": ws.numel(), "gen_s": gen_s}
+            "launches_per_step": chk.last_launches(), "workspace_bytes": ws.numel(), "gen_s": gen_s,
+            **({"cpu_baseline": base} if base else {})}
+
+
+def _oracle_trace_worker(job):
+    """One batch member checked by the oracle (runs in a spawned process; generation not timed)."""
+    import oracle
+    import tracegen
+    i, n, bs, ep = job
+    tr = tracegen.c3_trace(i, n, bs, ep)
+    t0 = time.perf_counter()
+    out = oracle.check(tr)
+    assert out["status"] == 0
+    return tr.n_events, time.perf_counter() - t0
+
+
+def batch_oracle_baseline(sizes, bss, eps, stride: int = 32) -> dict:
+    """The oracle over every stride-th batch member, one process per host core (spawned before any GPU work)."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0))
+    jobs = [(i, int(sizes[i]), int(bss[i]), int(eps[i])) for i in range(0, len(sizes), stride)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_trace_worker, jobs[:cores])        # warm-up: load the oracle in every worker
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_trace_worker, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+    n = sum(r[0] for r in res)
+    return {"value": n / wall / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"every {stride}th batch member ({len(jobs)} traces, {n} records), one process per core, "
+                      f"{wall:.1f} s wall"}
+
+
+def single_trace_arm(args):
+    """One more single-trace configuration: 'strided' (1 block x 256 threads, 8 epochs, 32768 records) or
+    'barrier' (1024 blocks x 1024 threads, 64 epochs, 2^28 records). Device time of simulee_check with the
+    trace resident, and the oracle on a sample."""
+    import torch
+    import tracegen
+    from paper_1905_01833_gb300 import simulee
+    if args.workload == "strided":
+        tr, name, sample_blocks = tracegen.c1(), "strided: 1 block x 256 threads, 8 epochs, 12288 shared units", 1
+    else:
+        tr, name = tracegen.c4(), "barrier: 1024 blocks x 1024 threads, 64 epochs, 4 accesses per thread per epoch"
+        sample_blocks = 8
+    dt = simulee.to_device(tr)
+    chk = simulee.Checker(0)
+    races_cap = min(2 * tr.n_events + 2, 1 << 22)
+    ws = chk.workspace(chk.workspace_size(dt))
+    outs, bufs = chk.alloc_outputs(races_cap, tr.n_blocks, tr.n_blocks * max(tr.max_barriers, 1),
+                                   max(tr.max_barriers, 1))
+    rep = torch.zeros(simulee.REPORT_BYTES, dtype=torch.uint8, device="cuda:0")
+    t = dt.c()
+    stream = torch.cuda.current_stream()
+    import ctypes
+    L = simulee.lib()
+
+    def step():
+        st = L.simulee_check(chk.h, ctypes.byref(t), ctypes.byref(outs), ctypes.c_void_p(rep.data_ptr()),
+                             ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(stream.cuda_stream))
+        if st != simulee.OK:
+            raise RuntimeError(simulee.status_str(st))
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 50 if args.workload == "barrier" else 500))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    r = simulee.Report.from_buffer_copy(rep.cpu().numpy().tobytes())
+    line = {"workload": name, "n_events": tr.n_events, "value": tr.n_events / (ms * 1e-3) / 1e9, "unit": UNIT,
+            "ms_per_step": ms, "steps": steps, "launches_per_step": chk.last_launches(),
+            "results": {"status": r.status, "n_races": r.n_races, "n_divergence": r.n_divergence,
+                        "n_redundant": r.n_redundant, "n_grid_redundant": r.n_grid_redundant}}
+    if not args.no_cpu_baseline:
+        n, secs = run_oracle_sample(tr, sample_blocks)
+        line["cpu_baseline"] = {"value": n / secs / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"records of blocks 0..{sample_blocks - 1} ({n} records, {secs:.2f} s)"}
+    return line
 
 
 def fitness_arm(args):
@@ -517,7 +599,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--blocks", type=int, default=1024, help="grid blocks (1024 = the benchmark workload; "
                     "smaller values only for profiling captures)")
-    ap.add_argument("--workload", choices=["grid", "batch", "serve", "fitness", "evolve"], default="grid",
+    ap.add_argument("--workload", choices=["grid", "batch", "serve", "fitness", "evolve", "strided", "barrier"],
+                    default="grid",
                     help="grid: the benchmark line; batch / serve: the batched and served forms; fitness: Eq. 1 "
                          "over the grid workload (separate lines)")
     ap.add_argument("--batch-traces", type=int, default=4096)
@@ -526,10 +609,11 @@ def main():
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 1000.0, 4000.0])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    if args.workload in ("batch", "serve", "fitness", "evolve") and args.impl == "ours":
+    if args.workload != "grid" and args.impl == "ours":
         import torch
         torch.cuda.set_device(0)
-        out = {"batch": batch_arm, "serve": serve_arm, "fitness": fitness_arm, "evolve": evolve_arm}[args.workload](args)
+        out = {"batch": batch_arm, "serve": serve_arm, "fitness": fitness_arm, "evolve": evolve_arm,
+               "strided": single_trace_arm, "barrier": single_trace_arm}[args.workload](args)
         print(json.dumps({"metric": METRIC, **out}))
         return
 

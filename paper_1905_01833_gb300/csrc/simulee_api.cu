@@ -506,12 +506,14 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
         if (route && any_hash) {
             uint32_t *bstart = R.at<uint32_t>(L.off_bstart);
             k_block_ranges<<<R.grid_for(L.NB, 8, 16), 256, 0, st>>>(td, tob, L, bstart);
-            // CTA shape: two smaller CTAs per SM unless a hash-path trace has blocks of more than
-            // 256 threads (whose runs may hold more distinct units than the smaller table)
+            // CTA shape: two smaller CTAs per SM when there are blocks enough to fill them and no
+            // hash-path trace has blocks of more than 256 threads (whose runs may hold more distinct
+            // units than the smaller table); otherwise one CTA per SM with the larger table
             uint32_t max_bt = 0;
             for (uint32_t i = 0; i < T; i++)
                 if (hdesc[i].hash_ok) max_bt = std::max(max_bt, hdesc[i].bt);
-            const bool small = ctx->opt.hash_shape == 2 || (ctx->opt.hash_shape == 0 && max_bt <= 256);
+            const bool small = ctx->opt.hash_shape == 2 ||
+                               (ctx->opt.hash_shape == 0 && max_bt <= 256 && L.NB >= 2u * (uint32_t)ctx->sms);
 #define SIM_HASH(KX, SH)                                                                                            \
     k_hash_blocks<KX, SH><<<std::max(1, std::min<int>(ctx->sms * SH::ctas_per_sm, (int)L.NB)), SH::threads,        \
                             hash_blocks_smem<SH>(), st>>>(td, tob, bstart, L, ts, R.ctl, nonred, binel, spill,      \
