@@ -169,7 +169,9 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
     uint64_t *own = hb_smem;                                               // [2][SH::slots]
     uint32_t *key = reinterpret_cast<uint32_t *>(own + 2 * SH::slots);      // [2][SH::slots]
     uint16_t *list = reinterpret_cast<uint16_t *>(key + 2 * SH::slots);     // [2][SH::cap]
-    __shared__ uint32_t s_blk, s_cnt[2], s_flag, s_first, s_nracy, s_needed, s_ridx;
+    // per-run scalars are indexed by the run's table parity: the finalisation of one run clears the
+    // next run's set, so a run needs no barrier between its finalisation and the next run's inserts
+    __shared__ uint32_t s_blk, s_flag, s_ridx, s_cnt[2], s_first[2], s_nracy[2], s_needed[2];
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t lt = lanemask_lt();
     for (int i = tid; i < 2 * SH::slots; i += SH::threads) {
@@ -177,12 +179,14 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         key[i] = HB_EMPTY;
     }
     if (tid == 0) {
-        s_cnt[0] = s_cnt[1] = 0;
         s_flag = 0;
-        s_first = HB_NONE;
-        s_nracy = 0;
-        s_needed = 0;
         s_ridx = 0;
+        for (int q = 0; q < 2; q++) {
+            s_cnt[q] = 0;
+            s_first[q] = HB_NONE;
+            s_nracy[q] = 0;
+            s_needed[q] = 0;
+        }
     }
     const uint64_t xcap = L.x_cap;
     uint32_t xpos = 0, xend = 0;   // this warp's reserved inter-block slots [xpos, xend)
@@ -287,7 +291,14 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         for (;;) {
             uint32_t *kt = key + par * SH::slots;
             uint64_t *ot = own + par * SH::slots;
-            // ---- 1. insert run e: its records in this window and, while it goes on, the next windows
+            const uint32_t *pkt = key + (par ^ 1u) * SH::slots;   // the previous run's table
+            const uint64_t *pot = own + (par ^ 1u) * SH::slots;
+            const bool adj = prev_e != HB_NONE && prev_e + 1 == e;
+            volatile uint32_t *needed_flag = &s_needed[par];
+            // ---- 1. insert run e: its records in this window and, while it goes on, the next windows.
+            //      Adjacency (barrier e-1 needed) is tested record by record against the previous run's
+            //      table: a conflict between epoch e-1 and the epoch-e records exists exactly when one
+            //      record conflicts with it; the test stops once some thread has found one.
             for (;;) {
                 const uint32_t wend = min(wbase + (uint32_t)SH::window, s1);
                 bool more = false;   // the run goes on past this window: fetch the next one now
@@ -318,11 +329,23 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                             }
                             h = (h + 1) & (SH::slots - 1);
                         }
+                        const uint64_t qb = hb_own_bits((r.w >> 28) & 3u, r.w & 0x3FFu);
                         if (s == HB_EMPTY) {
                             s_flag = 2u;   // table full
                         } else {
-                            atomicOr(reinterpret_cast<unsigned long long *>(&ot[s]),
-                                     (unsigned long long)hb_own_bits((r.w >> 28) & 3u, r.w & 0x3FFu));
+                            atomicOr(reinterpret_cast<unsigned long long *>(&ot[s]), (unsigned long long)qb);
+                        }
+                        if (adj && !*needed_flag) {
+                            uint32_t ph = hb_hash<SH>(k);
+                            for (int probe = 0; probe < SH::slots; probe++) {
+                                const uint32_t c = pkt[ph];
+                                if (c == HB_EMPTY) break;
+                                if (c == k) {
+                                    if (hb_cross(pot[ph], qb)) *needed_flag = 1u;
+                                    break;
+                                }
+                                ph = (ph + 1) & (SH::slots - 1);
+                            }
                         }
                     } else if (idx < s1) {
                         first = min(first, idx);
@@ -341,7 +364,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                     }
                 }
                 first = __reduce_min_sync(0xFFFFFFFFu, first);
-                if (lane == 0 && first != HB_NONE) atomicMin(&s_first, first);
+                if (lane == 0 && first != HB_NONE) atomicMin(&s_first[par], first);
                 if (more) {
                     wbase = wend;
                     cur[0] = nxt[0];
@@ -354,7 +377,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
 
             // ---- 2. finalise run e
             __syncthreads();   // A: the run's inserts are complete
-            const uint32_t flag = s_flag, first = s_first;
+            const uint32_t flag = s_flag, first = s_first[par];
             const uint32_t cnt = min(s_cnt[par], (uint32_t)SH::cap);
             const uint32_t lo = run_start, hi = (first != HB_NONE ? first : min(wbase + (uint32_t)SH::window, s1)) - 1;
             const uint32_t next_start = hi + 1;
@@ -365,40 +388,32 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                 load(cur, next_start);
                 next_e = (ev[next_start].w >> 16) & 0xFFFu;
             }
-            bool needed = false;
+            if (!stop && tid == 0 && *needed_flag) mark_needed(nonred, L, b, e - 1);
             uint32_t rmask = 0;   // bit m: this thread's list entry tid + m * SH::threads is racy
             if (!stop) {
-                const bool adj = prev_e != HB_NONE && prev_e + 1 == e;
-                const uint32_t *pkt = key + (par ^ 1u) * SH::slots;
-                const uint64_t *pot = own + (par ^ 1u) * SH::slots;
 #pragma unroll 1
                 for (uint32_t i = tid, m = 0; i < cnt; i += SH::threads, m++) {
-                    const uint32_t s = list[par * SH::cap + i];
-                    const uint64_t o = ot[s];
-                    const uint32_t k = kt[s];
-                    if (hb_racy(o)) {
+                    if (hb_racy(ot[list[par * SH::cap + i]])) {
                         rmask |= 1u << m;
-                        atomicAdd(&s_nracy, 1u);
-                    }
-                    // adjacency: until some thread has found barrier e-1 needed
-                    if (adj && !needed && !*(volatile uint32_t *)&s_needed) {
-                        uint32_t h = hb_hash<SH>(k);
-                        for (int probe = 0; probe < SH::slots; probe++) {
-                            const uint32_t c = pkt[h];
-                            if (c == HB_EMPTY) break;
-                            if (c == k) {
-                                needed = hb_cross(pot[h], o);
-                                break;
-                            }
-                            h = (h + 1) & (SH::slots - 1);
-                        }
-                        if (needed) s_needed = 1u;
+                        atomicAdd(&s_nracy[par], 1u);
                     }
                 }
+                // the previous run's table is no longer read: release it for the next run
+                const uint32_t pp = par ^ 1u;
+                for (uint32_t i = tid; i < cnt_prev; i += SH::threads) {
+                    const uint32_t sl = list[pp * SH::cap + i];
+                    key[pp * SH::slots + sl] = HB_EMPTY;
+                    own[pp * SH::slots + sl] = 0ull;
+                }
             }
-            if (__syncthreads_or(needed) && tid == 0) mark_needed(nonred, L, b, e - 1);   // B
-            const uint32_t nracy = s_nracy;
-            bool prev_overlaid = false;   // the previous run's table holds the racy pool
+            if (tid == 0) {   // the next run's scalars
+                s_cnt[par ^ 1u] = 0;
+                s_first[par ^ 1u] = HB_NONE;
+                s_nracy[par ^ 1u] = 0;
+                s_needed[par ^ 1u] = 0;
+            }
+            __syncthreads();   // B
+            const uint32_t nracy = s_nracy[par];
             if (!stop && nracy > 0) {
                 if (nracy > (uint32_t)SH::pool || hi - lo >= HB_POS_LIMIT) {
                     // too many racy units: the sort path computes this run's races
@@ -410,7 +425,6 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                     // exact lowest pairs of the racy units: per category the first item, then the first
                     // item of another thread. The previous run's table is free now: its keys become a
                     // map slot -> racy index, its owner summaries the pool of 6 items per racy unit.
-                    prev_overlaid = true;
                     uint16_t *rmap = reinterpret_cast<uint16_t *>(key + (par ^ 1u) * SH::slots);
                     uint32_t *pool = reinterpret_cast<uint32_t *>(own + (par ^ 1u) * SH::slots);
                     for (uint32_t i = tid; i < SH::slots / 2; i += SH::threads)
@@ -468,31 +482,14 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                         }
                     }
                     if (tid == 0) s_ridx = 0;
-                    __syncthreads();   // every emission has read the pool
+                    __syncthreads();   // every emission has read the pool: clear it for the next run
+                    for (uint32_t i = tid; i < SH::slots; i += SH::threads) {
+                        key[(par ^ 1u) * SH::slots + i] = HB_EMPTY;
+                        own[(par ^ 1u) * SH::slots + i] = 0ull;
+                    }
+                    __syncthreads();
                 }
             }
-            // release the previous run's table (all of it when it held the racy pool)
-            if (prev_overlaid) {
-                const uint32_t pp = par ^ 1u;
-                for (uint32_t i = tid; i < SH::slots; i += SH::threads) {
-                    key[pp * SH::slots + i] = HB_EMPTY;
-                    own[pp * SH::slots + i] = 0ull;
-                }
-            } else if (!stop) {
-                const uint32_t pp = par ^ 1u;
-                for (uint32_t i = tid; i < cnt_prev; i += SH::threads) {
-                    const uint32_t s = list[pp * SH::cap + i];
-                    key[pp * SH::slots + s] = HB_EMPTY;
-                    own[pp * SH::slots + s] = 0ull;
-                }
-            }
-            if (tid == 0) {
-                s_cnt[par ^ 1u] = 0;
-                s_first = HB_NONE;
-                s_needed = 0;
-            }
-            __syncthreads();   // E
-            if (tid == 0) s_nracy = 0;
             if (stop) {
                 // the block goes to the sort path; its tables are cleared in full below
                 if (tid == 0) atomicOr(&binel[b], 1u);
@@ -522,20 +519,22 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                 own[i] = 0ull;
                 key[i] = HB_EMPTY;
             }
-            if (tid == 0) {
-                s_cnt[0] = s_cnt[1] = 0;
-                s_flag = 0;
-            }
+            if (tid == 0) s_flag = 0;
         } else if (hashing) {
             const uint32_t pp = par ^ 1u;   // the last run's table
             for (uint32_t i = tid; i < cnt_prev; i += SH::threads) {
-                const uint32_t s = list[pp * SH::cap + i];
-                key[pp * SH::slots + s] = HB_EMPTY;
-                own[pp * SH::slots + s] = 0ull;
+                const uint32_t sl = list[pp * SH::cap + i];
+                key[pp * SH::slots + sl] = HB_EMPTY;
+                own[pp * SH::slots + sl] = 0ull;
             }
-            if (tid == 0) s_cnt[pp] = 0;
         }
-        if (tid == 0) s_first = HB_NONE;
+        if (tid == 0)
+            for (int q = 0; q < 2; q++) {
+                s_cnt[q] = 0;
+                s_first[q] = HB_NONE;
+                s_nracy[q] = 0;
+                s_needed[q] = 0;
+            }
     }
     hb_x_fill(xk, xv, xpos, xend, xcap, lane);   // the unused tail of this warp's last chunk
 }
