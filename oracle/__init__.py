@@ -82,6 +82,9 @@ def _bind(lib):
     vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
     lib.orc_check.restype = vp
     lib.orc_check.argtypes = [vp, u64, vp, u32, u32, u32, u32, u32, u32]
+    if hasattr(lib, "orc_check2"):
+        lib.orc_check2.restype = vp
+        lib.orc_check2.argtypes = [vp, u64, vp, u32, u32, u32, u32, u32, u32, vp]
     for name, rt in [("orc_status", ctypes.c_int32), ("orc_bad_kind", u32), ("orc_bad_index", u64),
                      ("orc_n_races", u64), ("orc_n_divs", u64), ("orc_n_bars", u64), ("orc_n_grid", u64)]:
         getattr(lib, name).restype = rt
@@ -109,16 +112,29 @@ def load(path: str):
     return _bind(ctypes.CDLL(path))
 
 
+WARP_AWARE = 2     # trace flag: records carry statement words (Theorem 1's warp refinements apply)
+DIVERGED = 0x80000000
+
+
 def check_arrays(events, barrier_counts, n_blocks, block_threads, shared_units, global_units,
-                 max_barriers, flags=0, lib=None) -> dict:
-    """Run the oracle on raw arrays; returns status, bad_kind, bad_index and the four lists."""
+                 max_barriers, flags=0, lib=None, stmt=None) -> dict:
+    """Run the oracle on raw arrays; returns status, bad_kind, bad_index and the four lists.
+    stmt (with flag WARP_AWARE): per record, statement id | DIVERGED."""
     lib = lib or _lib()
     ev = np.ascontiguousarray(events, dtype=np.uint32).reshape(-1, 4)
     cn = np.ascontiguousarray(barrier_counts, dtype=np.uint32)
     if cn.size != n_blocks * block_threads:
         raise ValueError("barrier_counts must hold n_blocks * block_threads entries")
-    h = lib.orc_check(ev.ctypes.data_as(ctypes.c_void_p), ev.shape[0], cn.ctypes.data_as(ctypes.c_void_p),
-                      n_blocks, block_threads, shared_units, global_units, max_barriers, flags)
+    if flags & WARP_AWARE:
+        st = np.ascontiguousarray(stmt, dtype=np.uint32)
+        if st.size != ev.shape[0]:
+            raise ValueError("a warp-aware trace needs one statement word per record")
+        h = lib.orc_check2(ev.ctypes.data_as(ctypes.c_void_p), ev.shape[0], cn.ctypes.data_as(ctypes.c_void_p),
+                           n_blocks, block_threads, shared_units, global_units, max_barriers, flags,
+                           st.ctypes.data_as(ctypes.c_void_p))
+    else:
+        h = lib.orc_check(ev.ctypes.data_as(ctypes.c_void_p), ev.shape[0], cn.ctypes.data_as(ctypes.c_void_p),
+                          n_blocks, block_threads, shared_units, global_units, max_barriers, flags)
     if not h:
         raise MemoryError("oracle ran out of host memory")
     try:
@@ -140,7 +156,7 @@ def check(trace, lib=None) -> dict:
     """Run the oracle on any object with the trace attributes (events, barrier_counts, dims, flags)."""
     return check_arrays(trace.events, trace.barrier_counts, trace.n_blocks, trace.block_threads,
                         trace.shared_units, trace.global_units, trace.max_barriers, getattr(trace, "flags", 0),
-                        lib=lib)
+                        lib=lib, stmt=getattr(trace, "stmt", None))
 
 
 def fitness_arrays(events, barrier_counts, n_blocks, block_threads, shared_units, global_units,

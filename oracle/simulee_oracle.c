@@ -16,10 +16,13 @@
  *     position in the simulated schedule, used only to order accesses.
  *   - Theorem 1 (Sec. 3.2.3): two tuples of one unit race when they share the
  *     barrier interval, come from different threads and at least one writes.
- *     The warp refinements of the theorem are not applied (records carry no
- *     statement or divergence information); atomics count as writes except
- *     that two atomics never race; global memory is also checked across
- *     blocks, where barriers give no order, in any epochs.
+ *     The warp refinements of the theorem apply only to traces that carry a
+ *     statement word per record (flag WARP_AWARE, orc_check2): two accesses
+ *     of threads in the same warp then race only when both are plain writes
+ *     of the same statement, or when either was made after the warp's
+ *     threads diverged. Otherwise they are not applied. Atomics count as
+ *     writes except that two atomics never race; global memory is also
+ *     checked across blocks, where barriers give no order, in any epochs.
  *   - Algorithm 5 (Sec. 3.2.3): races per unit and visit-order group; a
  *     barrier is redundant when merging the tuples of the two visit orders it
  *     separates creates no race.
@@ -42,6 +45,8 @@
 #define ACT_A 2u
 
 #define FLAG_UNSORTED 1u
+#define FLAG_WARP_AWARE 2u
+#define STMT_DIVERGED 0x80000000u
 
 typedef struct {
     uint8_t space, scope, cls, pad;
@@ -63,6 +68,8 @@ typedef struct {
 
 typedef struct {                 /* one decoded record */
     uint32_t unit, vo, block, tid, epoch, act, space, gtid;
+    uint32_t stmt;               /* statement id | STMT_DIVERGED (warp-aware traces) */
+    uint32_t wa;                 /* the trace is warp-aware */
 } rec_t;
 
 typedef struct { uint64_t k0, k1, k2, idx; } skey;
@@ -79,12 +86,23 @@ static int cmp_skey(const void *a, const void *b) {
 /* write or atomic: the actions that modify the unit */
 static int modifies(uint32_t act) { return act == ACT_W || act == ACT_A; }
 
-/* Theorem 1 without warp refinements, plus the atomic rule:
-   different owners, at least one modifying access, not both atomic. */
+/* Theorem 1 plus the atomic rule: different owners, at least one modifying
+   access, not both atomic. For warp-aware traces, two threads of one warp
+   (same block, same tid / 32) race only when both plainly write by the same
+   statement, or when either access came after the warp diverged. */
+static int same_warp(const rec_t *p, const rec_t *q) {
+    return p->block == q->block && (p->tid >> 5) == (q->tid >> 5);
+}
 static int conflict(const rec_t *p, const rec_t *q, uint32_t id_p, uint32_t id_q) {
     if (id_p == id_q) return 0;
     if (!modifies(p->act) && !modifies(q->act)) return 0;
     if (p->act == ACT_A && q->act == ACT_A) return 0;
+    if (p->wa && same_warp(p, q)) {
+        const int same_statement_writes = p->act == ACT_W && q->act == ACT_W &&
+                                          (p->stmt & ~STMT_DIVERGED) == (q->stmt & ~STMT_DIVERGED);
+        const int diverged = (p->stmt & STMT_DIVERGED) || (q->stmt & STMT_DIVERGED);
+        if (!same_statement_writes && !diverged) return 0;
+    }
     return 1;
 }
 
@@ -129,8 +147,10 @@ static int validate(const uint32_t *ev, uint64_t n, const uint32_t *counts, uint
     return 0;
 }
 
-static void decode(const uint32_t *ev, uint64_t n, uint32_t bt, rec_t *r) {
+static void decode(const uint32_t *ev, uint64_t n, uint32_t bt, const uint32_t *stmt, rec_t *r) {
     for (uint64_t i = 0; i < n; i++) {
+        r[i].stmt = stmt ? stmt[i] : 0u;
+        r[i].wa = stmt ? 1u : 0u;
         const uint32_t *w = ev + 4 * i;
         r[i].unit = w[0];
         r[i].vo = w[1];
@@ -332,8 +352,8 @@ static int divergence(const uint32_t *counts, uint32_t nb, uint32_t bt, vec *out
  * Full check. ev: n records of 4 uint32 words; counts: nb*bt per-thread barrier
  * counts. Returns a heap result (free with orc_free), or NULL when out of memory.
  */
-orc_result *orc_check(const uint32_t *ev, uint64_t n, const uint32_t *counts, uint32_t nb, uint32_t bt,
-                      uint32_t su, uint32_t gu, uint32_t maxb, uint32_t flags) {
+orc_result *orc_check2(const uint32_t *ev, uint64_t n, const uint32_t *counts, uint32_t nb, uint32_t bt,
+                       uint32_t su, uint32_t gu, uint32_t maxb, uint32_t flags, const uint32_t *stmt) {
     orc_result *res = (orc_result *)calloc(1, sizeof(orc_result));
     if (!res) return NULL;
     if (validate(ev, n, counts, nb, bt, su, gu, maxb, flags, &res->bad_kind, &res->bad_index)) {
@@ -342,7 +362,7 @@ orc_result *orc_check(const uint32_t *ev, uint64_t n, const uint32_t *counts, ui
     }
     rec_t *r = (rec_t *)malloc((n ? n : 1) * sizeof(rec_t));
     if (!r) { free(res); return NULL; }
-    decode(ev, n, bt, r);
+    decode(ev, n, bt, (flags & FLAG_WARP_AWARE) ? stmt : NULL, r);
     vec rv = {0, 0, 0, sizeof(orc_race)}, dv = {0, 0, 0, sizeof(orc_div)};
     vec bv = {0, 0, 0, sizeof(orc_bar)}, gv = {0, 0, 0, sizeof(uint32_t)};
     int ok = races(r, n, &rv) && divergence(counts, nb, bt, &dv) &&
@@ -413,6 +433,12 @@ int32_t orc_fitness(const uint32_t *ev, uint64_t n, const uint32_t *counts, uint
     }
     free(t);
     return ORC_OK;
+}
+
+/* The check without statement words (warp refinements off). */
+orc_result *orc_check(const uint32_t *ev, uint64_t n, const uint32_t *counts, uint32_t nb, uint32_t bt,
+                      uint32_t su, uint32_t gu, uint32_t maxb, uint32_t flags) {
+    return orc_check2(ev, n, counts, nb, bt, su, gu, maxb, flags & ~FLAG_WARP_AWARE, NULL);
 }
 
 /* flat accessors for foreign-function callers */

@@ -25,6 +25,8 @@ import numpy as np
 READ, WRITE, ATOMIC = 0, 1, 2
 SHARED, GLOBAL = 0, 1
 UNSORTED = 1  # trace flag: visit orders are not increasing in record order
+WARP_AWARE = 2  # trace flag: records carry statement words (Theorem 1's warp refinements apply)
+DIVERGED = 0x80000000  # statement-word bit: the access came after the thread's warp diverged
 
 DEFAULT_SEED = 1905018330
 
@@ -90,6 +92,7 @@ class Trace:
     max_barriers: int
     flags: int = 0
     meta: dict = dataclasses.field(default_factory=dict)
+    stmt: np.ndarray | None = None   # warp-aware traces: per record, statement id | DIVERGED
 
     @property
     def n_events(self) -> int:
@@ -361,3 +364,34 @@ def model_trace(model: int, grid: tuple, block: tuple, args: tuple) -> Trace:
         ev = np.zeros((0, 4), dtype=np.uint32)
     return Trace(ev, counts, nb, bt, MODEL_SHARED_UNITS, MODEL_GLOBAL_UNITS, maxb,
                  meta=dict(kind="model", model=model, grid=(gx, gy), block=(bxd, byd), args=(a0, a1)))
+
+
+def with_statements(tr: Trace, seed: int = DEFAULT_SEED, diverge_p: float = 0.05) -> Trace:
+    """The same records with statement words: the statement of a record is its position among its
+    thread's accesses of its epoch (threads of a warp run the same program point in lockstep), plus
+    64 * epoch; every record of a (block, warp, epoch) that diverges (probability diverge_p, hashed
+    from the seed) carries DIVERGED."""
+    ev = tr.events
+    n = ev.shape[0]
+    epoch = (ev[:, 3] >> 16) & 0xFFF
+    gt = ev[:, 2].astype(np.int64) * tr.block_threads + (ev[:, 3] & 0xFFFF)
+    key = gt * 4096 + epoch
+    order = np.argsort(key, kind="stable")
+    sk = key[order]
+    start = np.ones(n, dtype=bool)
+    start[1:] = sk[1:] != sk[:-1]
+    grp = np.cumsum(start) - 1
+    first = np.flatnonzero(start)
+    slot = np.empty(n, dtype=np.int64)
+    slot[order] = np.arange(n) - first[grp]
+    stmt = (epoch.astype(np.int64) * 64 + np.minimum(slot, 63)).astype(np.uint32)
+    warp = ev[:, 2].astype(np.uint64) * 64 + ((ev[:, 3] & 0xFFFF) >> 5).astype(np.uint64)
+    h = (np.uint64(seed) ^ (warp * np.uint64(0x9E3779B97F4A7C15)) ^ (epoch.astype(np.uint64) << np.uint64(40)))
+    h ^= h >> np.uint64(31)
+    h *= np.uint64(0xBF58476D1CE4E5B9)
+    h ^= h >> np.uint64(29)
+    div = (h % np.uint64(1 << 20)).astype(np.float64) / float(1 << 20) < diverge_p
+    stmt = stmt | np.where(div, np.uint32(DIVERGED), np.uint32(0))
+    out = dataclasses.replace(tr, flags=tr.flags | WARP_AWARE, stmt=stmt.astype(np.uint32),
+                              meta=dict(tr.meta, statements=True, diverge_p=diverge_p))
+    return out
