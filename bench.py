@@ -191,8 +191,9 @@ def run_oracle_sample(tr, n_blocks: int):
     import oracle
     import tracegen
     sel = tr.events[:, 2] < n_blocks
+    st = getattr(tr, "stmt", None)
     sub = tracegen.Trace(tr.events[sel].copy(), tr.barrier_counts, tr.n_blocks, tr.block_threads, tr.shared_units,
-                         tr.global_units, tr.max_barriers)
+                         tr.global_units, tr.max_barriers, tr.flags, stmt=None if st is None else st[sel].copy())
     t0 = time.perf_counter()
     out = oracle.check(sub)
     dt = time.perf_counter() - t0
@@ -382,6 +383,11 @@ def single_trace_arm(args):
     from paper_1905_01833_gb300 import simulee
     if args.workload == "strided":
         tr, name, sample_blocks = tracegen.c1(), "strided: 1 block x 256 threads, 8 epochs, 12288 shared units", 1
+    elif args.workload == "warp":
+        tr = tracegen.with_statements(make_trace(0, args.blocks), diverge_p=0.05)
+        name = ("warp-aware (Theorem 1 with its warp conditions): the grid workload with a statement word per "
+                "record, 5% of (block, warp, epoch) diverged; radix-sort path, pairwise group search")
+        sample_blocks = 16
     else:
         tr, name = tracegen.c4(), "barrier: 1024 blocks x 1024 threads, 64 epochs, 4 accesses per thread per epoch"
         sample_blocks = 8
@@ -599,7 +605,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--blocks", type=int, default=1024, help="grid blocks (1024 = the benchmark workload; "
                     "smaller values only for profiling captures)")
-    ap.add_argument("--workload", choices=["grid", "batch", "serve", "fitness", "evolve", "strided", "barrier"],
+    ap.add_argument("--workload", choices=["grid", "batch", "serve", "fitness", "evolve", "strided", "barrier", "warp"],
                     default="grid",
                     help="grid: the benchmark line; batch / serve: the batched and served forms; fitness: Eq. 1 "
                          "over the grid workload (separate lines)")
@@ -613,7 +619,7 @@ def main():
         import torch
         torch.cuda.set_device(0)
         out = {"batch": batch_arm, "serve": serve_arm, "fitness": fitness_arm, "evolve": evolve_arm,
-               "strided": single_trace_arm, "barrier": single_trace_arm}[args.workload](args)
+               "strided": single_trace_arm, "barrier": single_trace_arm, "warp": single_trace_arm}[args.workload](args)
         print(json.dumps({"metric": METRIC, **out}))
         return
 
@@ -749,6 +755,11 @@ def main():
                 "bytes_per_launch": sb[dom] / nl, "launch_ms": stage_ms[dom] / nl,
                 "traffic": kernel_traffic(kname, "grid")}
     stage_gbs = {k: sb[k] / (stage_ms[k] * 1e-3) / 1e9 for k in cand if stage_ms[k] > 0}
+    # the whole plan: algorithmic bytes per record over every stage, and the single-read floor (16 B per record)
+    b_plan = sum(sb[k] for k in ("ingest", "hash", "fallback", "sort", "reduce")) / tr.n_events
+    roofline["plan"] = {"bytes_per_record": b_plan, "frac": value * 1e9 * b_plan / (peak * 1e9),
+                        "floor_frac": value * 1e9 * 16 / (peak * 1e9),
+                        "radix_passes": sb["launches"]["sort"] - 1}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -54,6 +54,12 @@ enum { SIMULEE_WW = 0, SIMULEE_RW = 1 };
 
 /* trace flags */
 #define SIMULEE_FLAG_UNSORTED 1u  /* visit orders need not increase with the record index */
+/* Theorem 1's warp refinements (Sec. 3.2.3): the trace carries one statement word per record
+   (simulee_trace.stmt), and two accesses of threads in the same warp (same block, same
+   tid / 32) race only when both are plain writes of the same statement, or when either was made
+   after the warp's threads diverged. Not combinable with SIMULEE_FLAG_UNSORTED. */
+#define SIMULEE_FLAG_WARP_AWARE 2u
+#define SIMULEE_STMT_DIVERGED 0x80000000u  /* statement-word bit: the access came after divergence */
 
 /*
  * One access record (16 bytes, four little-endian words): one tuple
@@ -86,12 +92,15 @@ typedef struct {
     uint32_t global_units;           /* global-memory units of the grid */
     uint32_t max_barriers;           /* upper bound on every barrier count, <= 4095 */
     uint32_t flags;                  /* SIMULEE_FLAG_* */
+    const uint32_t *stmt;            /* with SIMULEE_FLAG_WARP_AWARE: device, n_events statement words
+                                        (statement id in bits 0..30 | SIMULEE_STMT_DIVERGED); else NULL */
 } simulee_trace;
 
 /*
  * One data race (32 bytes): the lowest conflicting pair of one group and class.
- * A pair conflicts (Theorem 1 without its warp conditions) when its owners
- * differ, at least one access writes or is atomic, and not both are atomic.
+ * A pair conflicts (Theorem 1; its warp conditions only for traces flagged
+ * SIMULEE_FLAG_WARP_AWARE) when its owners differ, at least one access writes
+ * or is atomic, and not both are atomic.
  * Groups: INTRA = one (space, block, epoch, unit), owners are threads;
  * INTER = one global unit across blocks in any epochs, owners are blocks.
  * Class WW when both accesses modify the unit, RW when one reads.

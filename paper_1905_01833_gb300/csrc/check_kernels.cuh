@@ -279,7 +279,9 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
                     const uint32_t u = e.x, blk = e.z, w3 = e.w;
                     const uint32_t ep = (w3 >> 16) & 0xFFFu, act = (w3 >> 28) & 3u;
                     const uint32_t pos = sorted ? e.y : rank[d.rec_off + idx];
-                    const uint64_t val = make_payload(act, blk * d.bt + (w3 & 0xFFFFu), pos);
+                    // warp-aware traces: intra-block elements carry the record index (for the statement word)
+                    const uint32_t ipos = (d.flags & TF_WARP_AWARE) ? (uint32_t)idx : pos;
+                    const uint64_t val = make_payload(act, blk * d.bt + (w3 & 0xFFFFu), ipos);
                     const uint64_t sb = (uint64_t)d.block_off + blk;
                     if (isS) {
                         const uint32_t o = oS + __popc(bS & lt);
@@ -560,6 +562,68 @@ __device__ __forceinline__ bool adj_conflict(const Adj &P, const Adj &Q) {
     return false;
 }
 
+// Warp-aware traces (Theorem 1 with its warp conditions): a pair of one warp conflicts only when both
+// are plain writes of the same statement or either came after divergence. The top-2 summary does not
+// carry warps and statements, so these groups are searched pair by pair, as the definition reads.
+__device__ __forceinline__ bool wa_conflict(uint32_t ap, uint32_t gp, uint32_t sp, uint32_t aq, uint32_t gq,
+                                            uint32_t sq, uint32_t bt) {
+    if (gp == gq) return false;
+    const bool mp = ap != ACT_R, mq = aq != ACT_R;
+    if (!mp && !mq) return false;
+    if (ap == ACT_A && aq == ACT_A) return false;
+    if (gp / bt == gq / bt && ((gp % bt) >> 5) == ((gq % bt) >> 5)) {
+        const bool same_statement_writes = ap == ACT_W && aq == ACT_W && (sp & ~STMT_DIVERGED) == (sq & ~STMT_DIVERGED);
+        if (!same_statement_writes && !(sp & STMT_DIVERGED) && !(sq & STMT_DIVERGED)) return false;
+    }
+    return true;
+}
+
+// one element of a warp-aware group: action, thread (block * bt + tid), statement word, visit order
+struct WaItem {
+    uint32_t act, gtid, stmt, vo;
+};
+__device__ __forceinline__ WaItem wa_item(const TraceDesc &d, uint64_t v) {
+    const uint32_t idx = (uint32_t)v;   // the record index (warp-aware elements)
+    return WaItem{payload_act(v), (uint32_t)(v >> 32) & 0x3FFFFFFFu, d.stmt[idx], d.events[idx].y};
+}
+
+// races of group [gs, ge) and the adjacency test against the group of the next epoch, if present
+template <class K>
+__device__ void warp_group(const K *__restrict__ keys, const uint64_t *__restrict__ vals, uint64_t gs, uint64_t ge,
+                           uint64_t n, K kg, const TraceDesc &d, const Layout &L, const RaceStage &rs, Ctl *ctl,
+                           uint32_t *nonred, uint32_t trace, uint32_t space, uint32_t block, uint32_t epoch,
+                           uint32_t unit) {
+    // lowest pair per class: elements are in schedule order (the sort is stable over record order)
+#pragma unroll 1
+    for (int cls = 0; cls < 2; cls++) {
+        bool found = false;
+        for (uint64_t qi = gs + 1; qi < ge && !found; qi++) {
+            const WaItem q = wa_item(d, vals[qi]);
+            for (uint64_t pi = gs; pi < qi; pi++) {
+                const WaItem p = wa_item(d, vals[pi]);
+                if (!wa_conflict(p.act, p.gtid, p.stmt, q.act, q.gtid, q.stmt, d.bt)) continue;
+                if (((p.act != ACT_R && q.act != ACT_R) ? 0 : 1) != cls) continue;
+                emit_race(rs, ctl, trace, race_key(L, trace, space, 0u, block, epoch, unit, (uint32_t)cls),
+                          ((uint64_t)p.vo << 32) | p.gtid, ((uint64_t)q.vo << 32) | q.gtid);
+                found = true;
+                break;
+            }
+        }
+    }
+    // barrier `epoch` is needed when a pair across this group and the next epoch's group conflicts
+    if (ge < n && keys[ge] == kg + 1) {
+        bool needed = false;
+        for (uint64_t qi = ge; qi < n && keys[qi] == kg + 1 && !needed; qi++) {
+            const WaItem q = wa_item(d, vals[qi]);
+            for (uint64_t pi = gs; pi < ge && !needed; pi++) {
+                const WaItem p = wa_item(d, vals[pi]);
+                needed = wa_conflict(p.act, p.gtid, p.stmt, q.act, q.gtid, q.stmt, d.bt);
+            }
+        }
+        if (needed) mark_needed(nonred, L, block, epoch);
+    }
+}
+
 template <class K, bool INTER>
 constexpr size_t reduce_groups_smem() {
     return (size_t)RG_TILE * (8 + sizeof(K)) + (INTER ? 0 : (RG_TILE + 1) * sizeof(Adj)) + (RG_TILE + 2) * 2;
@@ -673,8 +737,16 @@ k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, c
                 const uint64_t sk = (uint64_t)kg >> be;
                 const uint32_t block = (uint32_t)(sk >> bu), unit = (uint32_t)(sk & umask);
                 const uint32_t epoch = (uint32_t)((uint64_t)kg & ((1ull << be) - 1));
-                if (cnt >= 2) emit_group(L, rs, ctl, S, own_t, trace, space, 0u, block, epoch, unit);
-                sadj[g] = adj_of(S);
+                const TraceDesc &d = td[trace];
+                if (d.flags & TF_WARP_AWARE) {
+                    warp_group(keys, vals, e - cnt, e, n, kg, d, L, rs, ctl, nonred, trace, space, block, epoch, unit);
+                    Top2 none;
+                    none.clear();
+                    sadj[g] = adj_of(none);   // adjacency already decided pair by pair
+                } else {
+                    if (cnt >= 2) emit_group(L, rs, ctl, S, own_t, trace, space, 0u, block, epoch, unit);
+                    sadj[g] = adj_of(S);
+                }
                 if (g + 1 == G && e < n) {
                     // the following group belongs to a later tile: summarise it for the adjacency test
                     const K kn = keys[e];

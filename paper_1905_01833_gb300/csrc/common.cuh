@@ -32,6 +32,8 @@
 namespace simk {
 
 constexpr uint32_t ACT_R = 0, ACT_W = 1, ACT_A = 2;
+constexpr uint32_t TF_UNSORTED = 1, TF_WARP_AWARE = 2;     // trace flags
+constexpr uint32_t STMT_DIVERGED = 0x80000000u;
 constexpr uint64_t EMPTY = ~0ull;
 constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;
@@ -48,6 +50,7 @@ struct TraceDesc {
     uint32_t block_off;        // batch-wide index of this trace's block 0
     uint32_t nb, bt, su, gu, maxb, flags;
     uint32_t hash_ok;          // eligible for the short-interval hash path (host decision)
+    const uint32_t *stmt;      // warp-aware traces: statement word per record
     uint8_t *races;    uint64_t races_cap;    // outputs (device), as in simulee_outputs
     uint8_t *divs;     uint64_t divs_cap;
     uint8_t *reds;     uint64_t reds_cap;

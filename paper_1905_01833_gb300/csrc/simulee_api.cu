@@ -67,7 +67,11 @@ simulee_status check_trace_args(const simulee_trace *t) {
     if (t->n_blocks == 0 || t->block_threads == 0 || t->block_threads > 1024) return SIMULEE_EINVAL;
     if ((uint64_t)t->n_blocks * t->block_threads > (1ull << 30)) return SIMULEE_EINVAL;
     if (t->max_barriers > 4095) return SIMULEE_EINVAL;
-    if (t->flags & ~SIMULEE_FLAG_UNSORTED) return SIMULEE_EINVAL;
+    if (t->flags & ~(SIMULEE_FLAG_UNSORTED | SIMULEE_FLAG_WARP_AWARE)) return SIMULEE_EINVAL;
+    if (t->flags & SIMULEE_FLAG_WARP_AWARE) {
+        if (t->flags & SIMULEE_FLAG_UNSORTED) return SIMULEE_EINVAL;
+        if (t->n_events > 0 && (!t->stmt || ((uintptr_t)t->stmt & 3u) != 0)) return SIMULEE_EINVAL;
+    }
     if (((uintptr_t)t->events & 15u) != 0 || ((uintptr_t)t->barrier_counts & 3u) != 0) return SIMULEE_EINVAL;
     return SIMULEE_OK;
 }
@@ -334,6 +338,7 @@ void fill_descs(const simulee_trace *tr, const simulee_outputs *outs, uint8_t *c
         d.gu = tr[i].global_units;
         d.maxb = tr[i].max_barriers;
         d.flags = tr[i].flags;
+        d.stmt = (tr[i].flags & SIMULEE_FLAG_WARP_AWARE) ? tr[i].stmt : nullptr;
         d.races = (uint8_t *)outs[i].races;
         d.races_cap = outs[i].races_cap;
         d.divs = (uint8_t *)outs[i].divergence;
@@ -372,7 +377,8 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     const bool route_any = want.races || want.red;
     for (uint32_t i = 0; i < T; i++) {
         TraceDesc &d = hdesc[i];
-        d.hash_ok = (route_any && ctx->opt.path != SIMULEE_PATH_SORT && !(d.flags & SIMULEE_FLAG_UNSORTED) &&
+        d.hash_ok = (route_any && ctx->opt.path != SIMULEE_PATH_SORT &&
+                     !(d.flags & (SIMULEE_FLAG_UNSORTED | SIMULEE_FLAG_WARP_AWARE)) &&
                      d.su < 0x7FFFFFFFu && d.gu < 0x7FFFFFFFu && d.n > 0) ? 1u : 0u;
         any_hash |= d.hash_ok != 0;
     }

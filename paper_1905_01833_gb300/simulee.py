@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libsimulee.so")
 
 OK, EINVAL, EBADTRACE, ENOMEM, ETRUNC, ETIMEOUT, ECUDA = range(7)
 FLAG_UNSORTED = 1
+FLAG_WARP_AWARE = 2
+STMT_DIVERGED = 0x80000000
 PATH_AUTO, PATH_SORT, PATH_HASH = 0, 1, 2
 STAGES = ("ingest", "sort", "reduce", "races", "blocks", "hash", "fallback")
 
@@ -37,7 +39,8 @@ class SimuleeError(RuntimeError):
 class Trace(ctypes.Structure):
     _fields_ = [("events", ctypes.c_void_p), ("n_events", ctypes.c_uint64), ("barrier_counts", ctypes.c_void_p),
                 ("n_blocks", ctypes.c_uint32), ("block_threads", ctypes.c_uint32), ("shared_units", ctypes.c_uint32),
-                ("global_units", ctypes.c_uint32), ("max_barriers", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+                ("global_units", ctypes.c_uint32), ("max_barriers", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("stmt", ctypes.c_void_p)]
 
 
 class Outputs(ctypes.Structure):
@@ -139,15 +142,17 @@ class DeviceTrace:
     global_units: int
     max_barriers: int
     flags: int = 0
+    stmt: object = None     # torch.int32 (n,) on cuda: statement words of a warp-aware trace
 
     @property
     def n_events(self) -> int:
         return int(self.events.shape[0])
 
     def c(self) -> Trace:
+        st = self.stmt.data_ptr() if (self.stmt is not None and self.n_events) else None
         return Trace(self.events.data_ptr() if self.n_events else None, self.n_events,
                      self.barrier_counts.data_ptr(), self.n_blocks, self.block_threads, self.shared_units,
-                     self.global_units, self.max_barriers, self.flags)
+                     self.global_units, self.max_barriers, self.flags, st)
 
 
 def to_device(trace, device="cuda") -> DeviceTrace:
@@ -155,8 +160,10 @@ def to_device(trace, device="cuda") -> DeviceTrace:
     import torch
     ev = torch.from_numpy(np.ascontiguousarray(trace.events, dtype=np.uint32).view(np.int32).reshape(-1, 4))
     cn = torch.from_numpy(np.ascontiguousarray(trace.barrier_counts, dtype=np.uint32).view(np.int32))
+    st = getattr(trace, "stmt", None)
+    st = None if st is None else torch.from_numpy(np.ascontiguousarray(st, dtype=np.uint32).view(np.int32)).to(device)
     return DeviceTrace(ev.to(device), cn.to(device), trace.n_blocks, trace.block_threads, trace.shared_units,
-                       trace.global_units, trace.max_barriers, getattr(trace, "flags", 0))
+                       trace.global_units, trace.max_barriers, getattr(trace, "flags", 0), st)
 
 
 def _stream_ptr(stream):
