@@ -58,6 +58,7 @@ constexpr uint32_t HB_EMPTY = 0xFFFFFFFFu;
 constexpr uint32_t HB_NONE = 0xFFFFFFFFu;           // no epoch
 constexpr uint32_t HB_POS_LIMIT = 1u << 22;         // run positions in a pool item (22 bits)
 constexpr uint32_t HB_XCH = 256;                    // inter-block slots a warp reserves at a time
+constexpr int HB_RM = 4;                            // run records per thread held across the two pool passes
 
 // shared memory: owner summaries and keys of two run tables and the creation lists of both
 template <class SH>
@@ -423,54 +424,95 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                     }
                 } else {
                     // exact lowest pairs of the racy units: per category the first item, then the first
-                    // item of another thread. The previous run's table is free now: its keys become a
-                    // map slot -> racy index, its owner summaries the pool of 6 items per racy unit.
+                    // item of another thread. The previous run's table was released before barrier B, so
+                    // its keys are all HB_EMPTY (every 16-bit half 0xFFFF) and its owner summaries all 0:
+                    // the keys become a map slot -> racy index, the summaries the pool of 6 items per
+                    // racy unit, and only what the racy units used is put back afterwards.
                     uint16_t *rmap = reinterpret_cast<uint16_t *>(key + (par ^ 1u) * SH::slots);
                     uint32_t *pool = reinterpret_cast<uint32_t *>(own + (par ^ 1u) * SH::slots);
-                    for (uint32_t i = tid; i < SH::slots / 2; i += SH::threads)
-                        reinterpret_cast<uint32_t *>(rmap)[i] = 0xFFFFFFFFu;
                     for (uint32_t i = tid; i < nracy * 6; i += SH::threads) pool[i] = HB_EMPTY;
-                    __syncthreads();
                     for (uint32_t m = 0; rmask >> m; m++)
                         if ((rmask >> m) & 1u)
                             rmap[list[par * SH::cap + tid + m * SH::threads]] = (uint16_t)atomicAdd(&s_ridx, 1u);
                     __syncthreads();
-#pragma unroll 1
-                    for (int pass = 0; pass < 2; pass++) {
-                        for (uint32_t i = lo + tid; i <= hi; i += SH::threads) {
-                            const uint4 r = ev[i];
-                            if (r.z != lb || ((r.w >> 16) & 0xFFFu) != e) continue;
-                            const uint32_t k = (r.x << 1) | ((r.w >> 30) & 1u);
-                            const uint32_t c = (r.w >> 28) & 3u, tt = r.w & 0x3FFu;
-                            if (c == 3u) continue;
-                            uint32_t h = hb_hash<SH>(k);
-                            for (int probe = 0; probe < SH::slots; probe++) {
-                                const uint32_t kk = kt[h];
-                                if (kk == k || kk == HB_EMPTY) break;
-                                h = (h + 1) & (SH::slots - 1);
-                            }
-                            if (kt[h] != k) continue;
-                            const uint32_t ri = rmap[h];
-                            if (ri == 0xFFFFu) continue;
-                            const uint32_t item = ((i - lo) << 10) | tt;
-                            uint32_t *pe = pool + ri * 6;
-                            if (pass == 0) atomicMin(&pe[c], item);
-                            else if ((pe[c] & 0x3FFu) != tt) atomicMin(&pe[3 + c], item);
+                    // a record of a racy unit of this run: racy index | category << 16 in the high word,
+                    // run position << 10 | tid in the low word; ~0 for any other record
+                    auto racy_item = [&](const uint4 &r, uint32_t i) -> uint64_t {
+                        if (r.z != lb || ((r.w >> 16) & 0xFFFu) != e) return ~0ull;
+                        const uint32_t c = (r.w >> 28) & 3u;
+                        if (c == 3u) return ~0ull;
+                        const uint32_t k = (r.x << 1) | ((r.w >> 30) & 1u);
+                        uint32_t h = hb_hash<SH>(k);
+                        bool found = false;
+                        for (int probe = 0; probe < SH::slots; probe++) {
+                            const uint32_t kk = kt[h];
+                            if (kk == k) { found = true; break; }
+                            if (kk == HB_EMPTY) break;
+                            h = (h + 1) & (SH::slots - 1);
+                        }
+                        if (!found) return ~0ull;
+                        const uint32_t ri = rmap[h];
+                        if (ri == 0xFFFFu) return ~0ull;
+                        return ((uint64_t)(ri | (c << 16)) << 32) | (((i - lo) << 10) | (r.w & 0x3FFu));
+                    };
+                    auto first_pass = [&](uint64_t x) {
+                        if (x == ~0ull) return;
+                        const uint32_t hw = (uint32_t)(x >> 32);
+                        atomicMin(&pool[(hw & 0xFFFFu) * 6 + (hw >> 16)], (uint32_t)x);
+                    };
+                    auto second_pass = [&](uint64_t x) {
+                        if (x == ~0ull) return;
+                        const uint32_t hw = (uint32_t)(x >> 32), item = (uint32_t)x;
+                        uint32_t *pe = pool + (hw & 0xFFFFu) * 6;
+                        if ((pe[hw >> 16] & 0x3FFu) != (item & 0x3FFu)) atomicMin(&pe[3 + (hw >> 16)], item);
+                    };
+                    const uint32_t nrec = hi - lo + 1;
+                    if (nrec <= (uint32_t)(SH::threads * HB_RM)) {
+                        // the run's records, HB_RM per thread, looked up once: both passes use the items
+                        uint4 rr[HB_RM];
+#pragma unroll
+                        for (int m = 0; m < HB_RM; m++) {
+                            const uint32_t i = lo + tid + m * SH::threads;
+                            rr[m] = i <= hi ? ev[i] : make_uint4(0, 0, 0xFFFFFFFFu, 0);
+                        }
+                        uint64_t it[HB_RM];
+#pragma unroll
+                        for (int m = 0; m < HB_RM; m++) {
+                            it[m] = racy_item(rr[m], lo + tid + m * SH::threads);
+                            first_pass(it[m]);
                         }
                         __syncthreads();
+#pragma unroll
+                        for (int m = 0; m < HB_RM; m++) second_pass(it[m]);
+                        __syncthreads();
+                    } else {
+#pragma unroll 1
+                        for (int pass = 0; pass < 2; pass++) {
+                            for (uint32_t i = lo + tid; i <= hi; i += SH::threads) {
+                                const uint64_t x = racy_item(ev[i], i);
+                                if (pass == 0) first_pass(x);
+                                else second_pass(x);
+                            }
+                            __syncthreads();
+                        }
                     }
+                    // emission; each racy unit's map entry and pool items are read by its own thread only,
+                    // which then puts them back (map entry HB_EMPTY's half, items 0)
                     const OwnThread ownt;
                     for (uint32_t m = 0; rmask >> m; m++) {
                         if (!((rmask >> m) & 1u)) continue;
                         const uint32_t sl = list[par * SH::cap + tid + m * SH::threads];
                         const uint32_t k = kt[sl];
-                        const uint32_t *pe = pool + rmap[sl] * 6;
+                        uint32_t *pe = pool + rmap[sl] * 6;
                         Top2 S;
 #pragma unroll
                         for (int c = 0; c < 3; c++) {
                             S.a[c] = hb_item64(pe[c]);
                             S.b[c] = hb_item64(pe[3 + c]);
                         }
+                        rmap[sl] = 0xFFFFu;
+#pragma unroll
+                        for (int c = 0; c < 6; c++) pe[c] = 0u;
 #pragma unroll
                         for (int cls = 0; cls < 2; cls++) {
                             uint64_t p, q2;
@@ -482,12 +524,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                         }
                     }
                     if (tid == 0) s_ridx = 0;
-                    __syncthreads();   // every emission has read the pool: clear it for the next run
-                    for (uint32_t i = tid; i < SH::slots; i += SH::threads) {
-                        key[(par ^ 1u) * SH::slots + i] = HB_EMPTY;
-                        own[(par ^ 1u) * SH::slots + i] = 0ull;
-                    }
-                    __syncthreads();
+                    __syncthreads();   // the map and the pool are clean again before the next run inserts there
                 }
             }
             if (stop) {

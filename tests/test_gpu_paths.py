@@ -115,6 +115,28 @@ def test_racy_units_in_place_and_spilled(k, shape):
 
 
 @pytest.mark.parametrize("shape", SHAPES)
+def test_racy_units_in_consecutive_runs(shape):
+    """Racy units in every epoch, over units that overlap from run to run: each
+    run resolves its racy units in the previous run's table and must leave it
+    empty for the next. Run sizes (2k records) fall on both sides of the
+    records held per thread (4 per thread: 2048 or 4096) and of the racy-unit
+    pool (1365 or 2730)."""
+    ks = [3, 700, 1, 1200, 50, 2100, 9, 1024, 1500, 2]
+    b = tracegen.Builder(3, 64, 8192)
+    for blk in range(3):
+        for e, k in enumerate(ks):
+            base = (e * 37 + blk * 11) % 4096
+            for u in range(k):
+                b.access(blk, (e + blk) % 5, e, base + u, tracegen.WRITE)
+            for u in range(k):
+                b.access(blk, 5 + (u % 3), e, base + u, tracegen.READ)
+    tr = b.set_counts(len(ks) - 1).trace()
+    want = oracle.check(tr)
+    assert len(want["races"]) == 3 * sum(ks)
+    assert diff(gpu_check(tr, path=0, hash_shape=shape), want) == []
+
+
+@pytest.mark.parametrize("shape", SHAPES)
 def test_run_with_more_distinct_units_than_the_table(shape):
     """One epoch of 1024 threads x 7 distinct units (7168, more than either
     table holds): the block leaves the hash path; a second block (2048
