@@ -358,7 +358,7 @@ constexpr int XF_ITEMS = 8;
 constexpr int XF_TILE = XF_THREADS * XF_ITEMS;
 
 template <class KX>
-__global__ void __launch_bounds__(XF_THREADS)
+__global__ void __launch_bounds__(XF_THREADS, sizeof(KX) == 4 ? 3 : 2)
 k_x_filter(const KX *__restrict__ xk, const uint64_t *__restrict__ xv, KX *yk, uint64_t *yv, const uint32_t *sig,
            Layout L, Ctl *ctl, uint32_t *hist) {
     __shared__ uint32_t sh[8 * RADIX];

@@ -565,7 +565,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
         // inter-block records of units touched by one block only are dropped before sorting;
         // the filter also builds the inter stream's digit histograms
         if (L.sig_slots) {
-            const int gf = R.grid_for(L.x_cap, XF_TILE, 2);
+            const int gf = R.grid_for(L.x_cap, XF_TILE, L.wide_x ? 2 : 3);   // resident CTAs per SM
             if (L.wide_x)
                 k_x_filter<uint64_t><<<gf, XF_THREADS, 0, st>>>(R.at<uint64_t>(xk[0]), R.at<uint64_t>(xv[0]), R.at<uint64_t>(xk[1]),
                                                          R.at<uint64_t>(xv[1]), sig, L, R.ctl, hist);

@@ -67,7 +67,16 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
 
     if (must_stop(ctl)) return;
     const uint64_t n = min((uint64_t)*n_ptr, n_max);
-    const uint64_t ntiles = (n + OS_TILE - 1) / OS_TILE;
+    // tile size: 4096 elements, or, when the grid has more CTAs than 4096-element tiles, the
+    // smallest multiple of the CTA's threads that gives every CTA at most one tile (the count is
+    // known on the device only; every CTA computes the same size)
+    uint32_t ipt = OS_ITEMS;
+    if (n < (uint64_t)gridDim.x * OS_TILE) {
+        const uint64_t per = (uint64_t)gridDim.x * OS_THREADS;
+        ipt = n > per ? (uint32_t)((n + per - 1) / per) : 1u;
+    }
+    const uint32_t tile_n = ipt * OS_THREADS;
+    const uint64_t ntiles = (n + tile_n - 1) / tile_n;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint32_t lt = lanemask_lt();
 
@@ -77,19 +86,22 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
         __syncthreads();
         const uint64_t tile = s_tile;
         if (tile >= ntiles) return;
-        const uint64_t base = tile * OS_TILE;
-        const uint32_t nvalid = (uint32_t)min((uint64_t)OS_TILE, n - base);
+        const uint64_t base = tile * tile_n;
+        const uint32_t nvalid = (uint32_t)min((uint64_t)tile_n, n - base);
 
+        // element li of the tile: warp w holds li in [w * 32 * ipt, (w + 1) * 32 * ipt), item j of
+        // lane l is li = w * 32 * ipt + j * 32 + l (items j >= ipt are unused)
         K k[OS_ITEMS];
         uint32_t rd[OS_ITEMS];   // rank within warp (low 16 bits) | digit << 16
 #pragma unroll
         for (int j = 0; j < OS_ITEMS; j++) {
-            const uint32_t li = w * (32 * OS_ITEMS) + j * 32 + lane;
-            k[j] = li < nvalid ? kin[base + li] : K(0);
+            const uint32_t li = w * (32 * ipt) + j * 32 + lane;
+            k[j] = ((uint32_t)j < ipt && li < nvalid) ? kin[base + li] : K(0);
         }
 #pragma unroll
         for (int j = 0; j < OS_ITEMS; j++) {
-            const uint32_t li = w * (32 * OS_ITEMS) + j * 32 + lane;
+            if ((uint32_t)j >= ipt) break;
+            const uint32_t li = w * (32 * ipt) + j * 32 + lane;
             const bool valid = li < nvalid;
             const uint32_t d = valid ? (uint32_t)((k[j] >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
             // lanes holding the same digit: one ballot per digit bit (warp multi-split)
@@ -154,7 +166,8 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
         // stable scatter into shared memory in digit order
 #pragma unroll
         for (int j = 0; j < OS_ITEMS; j++) {
-            const uint32_t li = w * (32 * OS_ITEMS) + j * 32 + lane;
+            if ((uint32_t)j >= ipt) break;
+            const uint32_t li = w * (32 * ipt) + j * 32 + lane;
             if (li < nvalid) {
                 const uint32_t d = rd[j] >> 16;
                 const uint32_t pos = texcl[d] + whist[w][d] + (rd[j] & 0xFFFFu);
