@@ -684,15 +684,44 @@ def main():
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
     for i in range(args.steps):
-        chk.set_stage_events(evs[i])
         step(ctrace, report_dev.data_ptr())
     t_end.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    chk.set_stage_events(None)
     ms = t_start.elapsed_time(t_end) / args.steps
+    # per-stage times from a second run of the same steps with stage events (not the timed steps above,
+    # so the events add nothing to their time)
+    for i in range(args.steps):
+        chk.set_stage_events(evs[i])
+        step(ctrace, report_dev.data_ptr())
+    torch.cuda.synchronize()
+    chk.set_stage_events(None)
     stage_ms = {name: sum(evs[i][2 * s].elapsed_time(evs[i][2 * s + 1]) for i in range(args.steps)) / args.steps
                 for s, name in enumerate(simulee.STAGES)}
+    # the same steps with graph replay off: every call issues its kernels one by one
+    direct = None
+    if world == 1:
+        chk_d = simulee.Checker(local, path=simulee.PATH_SORT if args.path == "sort" else simulee.PATH_AUTO,
+                                hash_shape=args.hash_shape, graph_replay=simulee.GRAPH_OFF)
+
+        def step_d():
+            s = L.simulee_check(chk_d.h, ctypes.byref(ctrace), ctypes.byref(outs), ctypes.c_void_p(report_dev.data_ptr()),
+                                ctypes.c_void_p(ws.data_ptr()), ws.numel(), sp)
+            if s != 0:
+                raise RuntimeError(f"simulee_check failed: {simulee.status_str(s)}")
+        for _ in range(3):
+            step_d()
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            step_d()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        ms_d = g0.elapsed_time(g1) / args.steps
+        direct = {"value": tr.n_events / (ms_d * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_d,
+                  "launches_per_step": chk_d.last_launches()}
+        chk_d.close()
     rep = simulee.Report.from_buffer_copy(report_dev.cpu().numpy().tobytes())
     assert rep.status == 0 and rep.n_races == rep0.n_races and rep.n_redundant == rep0.n_redundant
 
@@ -771,6 +800,9 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches * args.steps,
+        "launch": "repeated identical calls replayed by the library as one CUDA graph (graph_replay auto); "
+                  "'direct' times the same steps with every kernel launched by the call",
+        "direct": direct,
         "roofline": roofline,
         "stages_ms": stage_ms,
         "stages_gbs": stage_gbs,

@@ -171,8 +171,21 @@ typedef struct {
                                  most 256 threads and there are at least two blocks per SM), 1 = one 1024-thread CTA per SM with
                                  8192-entry run tables (up to 6144 distinct units per run), 2 = two
                                  512-thread CTAs per SM with 4096-entry tables (up to 3072) */
-    uint32_t reserved;
+    uint32_t graph_replay;    /* simulee_graph_replay */
 } simulee_options;
+
+/* Repeated calls. With SIMULEE_GRAPH_AUTO, a check call (simulee_check*, simulee_check_batch,
+   simulee_check_noalloc) whose arguments are byte-for-byte those of the previous check call on the
+   same context (trace and output descriptors, report, workspace, options; not the device data they
+   point to) is issued as one CUDA graph launch: the second such call captures the launch sequence
+   (the context keeps one graph) and every later one replays it. The graph reads and writes device
+   memory at run time exactly as the direct launches do, so new trace contents in the same buffers
+   give new results. Calls on a stream that is being captured, and calls with stage events set, are
+   always launched directly. */
+typedef enum {
+    SIMULEE_GRAPH_AUTO = 0,
+    SIMULEE_GRAPH_OFF = 1
+} simulee_graph_replay;
 
 typedef struct simulee_ctx simulee_ctx;
 

@@ -320,14 +320,12 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                     if (mine) {
                         const uint32_t k = (r.x << 1) | ((r.w >> 30) & 1u);
                         uint32_t h = hb_hash<SH>(k);
+                        // linear probing; each probe is a claim attempt (most records bring a new unit,
+                        // so the compare-and-swap replaces a plain read rather than following one)
                         for (int probe = 0; probe < SH::slots; probe++) {
-                            const uint32_t c = kt[h];
-                            if (c == k) { s = h; break; }
-                            if (c == HB_EMPTY) {
-                                const uint32_t old = atomicCAS(&kt[h], HB_EMPTY, k);
-                                if (old == HB_EMPTY) { s = h; created = true; break; }
-                                if (old == k) { s = h; break; }
-                            }
+                            const uint32_t old = atomicCAS(&kt[h], HB_EMPTY, k);
+                            if (old == HB_EMPTY) { s = h; created = true; break; }
+                            if (old == k) { s = h; break; }
                             h = (h + 1) & (SH::slots - 1);
                         }
                         const uint64_t qb = hb_own_bits((r.w >> 28) & 3u, r.w & 0x3FFu);

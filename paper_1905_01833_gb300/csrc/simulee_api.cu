@@ -41,6 +41,16 @@ struct simulee_ctx {
     cudaEvent_t stage_ev[2 * SIMULEE_STAGES];
     bool stage_on;
     std::vector<const void *> attr_fns;   // kernels whose shared-memory attribute is set
+    // replay of repeated identical calls: the arguments of the last call launched directly (seen_key),
+    // and the launch sequence of a call seen twice in a row captured as a CUDA graph (graph_key)
+    std::vector<uint8_t> seen_key, graph_key;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    uint32_t graph_launches = 0;
+    ~simulee_ctx() {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
 };
 
 namespace {
@@ -354,8 +364,8 @@ void fill_descs(const simulee_trace *tr, const simulee_outputs *outs, uint8_t *c
     }
 }
 
-simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t T, const simulee_outputs *outs,
-                         uint8_t *const *reports, Want want, void *ws, size_t ws_bytes, void *stream) {
+simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t T, const simulee_outputs *outs,
+                           uint8_t *const *reports, Want want, void *ws, size_t ws_bytes, void *stream) {
     if (!ctx || !traces || !outs || !reports || !ws || T == 0) return SIMULEE_EINVAL;
     for (uint32_t i = 0; i < T; i++) {
         const simulee_status s = check_trace_args(&traces[i]);
@@ -655,6 +665,97 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     ctx->last_launches = R.launches;
     const cudaError_t e = cudaGetLastError();
     if (prev_dev >= 0 && prev_dev != ctx->device) cudaSetDevice(prev_dev);
+    return e == cudaSuccess ? SIMULEE_OK : SIMULEE_ECUDA;
+}
+
+// Every argument a check's launch sequence depends on, as bytes: two calls with equal keys issue the
+// same kernels with the same parameters (the device data they read may differ).
+std::vector<uint8_t> call_key(const simulee_ctx *ctx, const simulee_trace *traces, uint32_t T,
+                              const simulee_outputs *outs, uint8_t *const *reports, Want want, void *ws,
+                              size_t ws_bytes) {
+    std::vector<uint8_t> k;
+    auto put = [&k](const void *p, size_t n) {
+        const uint8_t *b = (const uint8_t *)p;
+        k.insert(k.end(), b, b + n);
+    };
+    put(&ctx->opt, sizeof ctx->opt);
+    put(&T, sizeof T);
+    const uint8_t w[3] = {want.races, want.div, want.red};
+    put(w, 3);
+    put(&ws, sizeof ws);
+    put(&ws_bytes, sizeof ws_bytes);
+    for (uint32_t i = 0; i < T; i++) {
+        put(&traces[i], sizeof traces[i]);
+        put(&outs[i], sizeof outs[i]);
+        put(&reports[i], sizeof reports[i]);
+    }
+    return k;
+}
+
+// A check. A call whose arguments equal those of the call just before it on this context is issued
+// as a CUDA graph: the second such call captures the launch sequence (on a private stream, without
+// running it) and launches the graph on the caller's stream; later equal calls launch it again. The
+// graph's kernels read the trace, write the outputs and use the workspace at run time, exactly as
+// the direct launches do. Direct launches are used when graph replay is off in the options, when
+// stage events are on, and when the caller's stream is itself being captured.
+simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t T, const simulee_outputs *outs,
+                         uint8_t *const *reports, Want want, void *ws, size_t ws_bytes, void *stream) {
+    if (!ctx || !traces || !outs || !reports || !ws || T == 0) return SIMULEE_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (ctx->opt.graph_replay == SIMULEE_GRAPH_OFF || ctx->stage_on || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusNone)
+        return issue_check(ctx, traces, T, outs, reports, want, ws, ws_bytes, stream);
+    std::vector<uint8_t> key = call_key(ctx, traces, T, outs, reports, want, ws, ws_bytes);
+    int prev_dev = -1;
+    cudaGetDevice(&prev_dev);
+    auto restore = [&]() {
+        if (prev_dev >= 0 && prev_dev != ctx->device) cudaSetDevice(prev_dev);
+    };
+    if (prev_dev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return SIMULEE_ECUDA;
+    if (ctx->graph_exec && key == ctx->graph_key) {
+        const cudaError_t e = cudaGraphLaunch(ctx->graph_exec, st);
+        ctx->last_launches = ctx->graph_launches;
+        restore();
+        return e == cudaSuccess ? SIMULEE_OK : SIMULEE_ECUDA;
+    }
+    if (key != ctx->seen_key) {   // first sighting: direct launches
+        restore();
+        const simulee_status s = issue_check(ctx, traces, T, outs, reports, want, ws, ws_bytes, stream);
+        ctx->seen_key = s == SIMULEE_OK ? std::move(key) : std::vector<uint8_t>();
+        return s;
+    }
+    // the same arguments twice in a row: capture, instantiate, launch
+    if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        ctx->cap_stream = nullptr;
+        restore();
+        return issue_check(ctx, traces, T, outs, reports, want, ws, ws_bytes, stream);
+    }
+    if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        restore();
+        return issue_check(ctx, traces, T, outs, reports, want, ws, ws_bytes, stream);
+    }
+    const simulee_status s = issue_check(ctx, traces, T, outs, reports, want, ws, ws_bytes, ctx->cap_stream);
+    cudaSetDevice(ctx->device);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(ctx->cap_stream, &g);
+    cudaGraphExec_t ex = nullptr;
+    const bool ok = s == SIMULEE_OK && ec == cudaSuccess && g && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        cudaGetLastError();
+        if (ex) cudaGraphExecDestroy(ex);
+        restore();
+        if (s != SIMULEE_OK) return s;
+        return issue_check(ctx, traces, T, outs, reports, want, ws, ws_bytes, stream);
+    }
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    ctx->graph_exec = ex;
+    ctx->graph_key = std::move(key);
+    ctx->graph_launches = ctx->last_launches;
+    const cudaError_t e = cudaGraphLaunch(ex, st);
+    restore();
     return e == cudaSuccess ? SIMULEE_OK : SIMULEE_ECUDA;
 }
 

@@ -20,6 +20,7 @@ FLAG_UNSORTED = 1
 FLAG_WARP_AWARE = 2
 STMT_DIVERGED = 0x80000000
 PATH_AUTO, PATH_SORT, PATH_HASH = 0, 1, 2
+GRAPH_AUTO, GRAPH_OFF = 0, 1   # repeated identical check calls replayed as one CUDA graph, or always direct
 STAGES = ("ingest", "sort", "reduce", "races", "blocks", "hash", "fallback")
 
 RACE_DTYPE = np.dtype([("space", "u1"), ("scope", "u1"), ("cls", "u1"), ("pad", "u1"),
@@ -59,7 +60,7 @@ class Report(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("wait_limit_us", ctypes.c_uint32), ("path", ctypes.c_uint32), ("test_withhold", ctypes.c_uint32),
                 ("ingest_ctas_per_sm", ctypes.c_uint32), ("sort_ctas_per_sm", ctypes.c_uint32),
-                ("reduce_ctas_per_sm", ctypes.c_uint32), ("hash_shape", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("reduce_ctas_per_sm", ctypes.c_uint32), ("hash_shape", ctypes.c_uint32), ("graph_replay", ctypes.c_uint32)]
 
 
 class Fitness(ctypes.Structure):
@@ -177,12 +178,12 @@ class Checker:
 
     def __init__(self, device: int = 0, wait_limit_us: int = 0, path: int = PATH_AUTO, test_withhold: int = 0,
                  ingest_ctas_per_sm: int = 0, sort_ctas_per_sm: int = 0, reduce_ctas_per_sm: int = 0,
-                 hash_shape: int = 0):
+                 hash_shape: int = 0, graph_replay: int = GRAPH_AUTO):
         import torch
         self.device = device
         self.torch = torch
         opt = Options(wait_limit_us, path, test_withhold, ingest_ctas_per_sm, sort_ctas_per_sm, reduce_ctas_per_sm,
-                      hash_shape)
+                      hash_shape, graph_replay)
         h = ctypes.c_void_p()
         _check(lib().simulee_create(ctypes.byref(h), device, ctypes.byref(opt)), "simulee_create")
         self.h = h

@@ -197,3 +197,38 @@ def test_bad_record_inside_block_ranges(where):
     got, want = gpu_check(bad, path=0), oracle.check(bad)
     assert diff(got, want) == []
     assert got["bad_index"] == i
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_order_checks_at_warp_and_window_edges(shape):
+    """The comparison of each record with the record before it (visit order
+    strictly increasing; epochs not going back inside a block) at every kind
+    of position: warp starts of a run's windows (64 records apart), lanes
+    either side of them, and the start of a run's second window. Runs hold
+    2816 records (256 threads x 11 units), more than one window of either
+    shape and fewer distinct units than the smaller table holds."""
+    b = tracegen.Builder(2, 256, 4096)
+    for blk in range(2):
+        for e in range(4):
+            for k in range(11):
+                for t in range(256):
+                    b.access(blk, t, e, t * 11 + k, tracegen.WRITE if (t + k + e) % 5 == 0 else tracegen.READ)
+    tr = b.set_counts(3).trace()
+    ev0 = tr.events
+    s = 2816 * 6   # first record of run (block 1, epoch 2)
+    assert ev0[s, 2] == 1 and (ev0[s, 3] >> 16) & 0xFFF == 2 and (ev0[s - 1, 3] >> 16) & 0xFFF == 1
+    window = 2048 if shape == 1 else 1024
+    offs = [0, 1, 2, 31, 32, 33, 63, 64, 65, 95, 96, 127, 128, 129, 511, 512, 513]
+    for p in sorted({s + o for o in offs} | {s + window + o for o in offs}):
+        ev = ev0.copy()
+        ev[p, 1] = ev[p - 1, 1]   # visit order repeats: the trace is invalid at p
+        bad = tracegen.Trace(ev, tr.barrier_counts, tr.n_blocks, tr.block_threads, tr.shared_units,
+                             tr.global_units, tr.max_barriers)
+        got = gpu_check(bad, path=0, hash_shape=shape)
+        assert (got["status"], got["bad_kind"], got["bad_index"]) == (2, 0, p), p
+        if p > s:   # epoch 1 inside run 2: a valid trace whose epochs go back
+            ev = ev0.copy()
+            ev[p, 3] = (ev[p, 3] & ~np.uint32(0xFFF << 16)) | np.uint32(1 << 16)
+            back = tracegen.Trace(ev, tr.barrier_counts, tr.n_blocks, tr.block_threads, tr.shared_units,
+                                  tr.global_units, tr.max_barriers)
+            assert diff(gpu_check(back, path=0, hash_shape=shape), oracle.check(back)) == [], p
