@@ -113,6 +113,7 @@ def load(path: str):
 
 
 WARP_AWARE = 2     # trace flag: records carry statement words (Theorem 1's warp refinements apply)
+PAPER_ORDER = 4    # trace flag: the paper's visit-order counters (Algorithm 3) group the tuples
 DIVERGED = 0x80000000
 
 

@@ -28,6 +28,16 @@
  *     separates creates no race.
  *   - Algorithm 4 and Sec. 2 (barrier divergence): threads of one block that
  *     reach different numbers of barriers.
+ *   - Paper visit orders (flag PAPER_ORDER): Algorithm 3 keeps one visit-order
+ *     counter per memory address, set to 0 for every block (for global memory
+ *     too), and a barrier bumps an address's counter only if the address was
+ *     visited since its last bump. An access's visit order is then the number
+ *     of earlier epochs in which its block touched its unit (the unit's
+ *     non-empty epochs, counted). Algorithm 5 groups a unit's tuples by visit
+ *     order: inside a block that is the same as grouping by epoch, but the
+ *     tuples of a global unit from different blocks now meet only at equal
+ *     visit orders, and a barrier's adjacent groups are a unit's accesses
+ *     before it and at the unit's next non-empty epoch of the block.
  * Output conventions (one record per group and class, the lowest pair, the
  * canonical order) are the ones this library defines; see the header of the
  * Python wrapper for the full statement.
@@ -46,6 +56,7 @@
 
 #define FLAG_UNSORTED 1u
 #define FLAG_WARP_AWARE 2u
+#define FLAG_PAPER_ORDER 4u
 #define STMT_DIVERGED 0x80000000u
 
 typedef struct {
@@ -70,6 +81,7 @@ typedef struct {                 /* one decoded record */
     uint32_t unit, vo, block, tid, epoch, act, space, gtid;
     uint32_t stmt;               /* statement id | STMT_DIVERGED (warp-aware traces) */
     uint32_t wa;                 /* the trace is warp-aware */
+    uint32_t rank;               /* PAPER_ORDER: earlier non-empty epochs of (space, block, unit) */
 } rec_t;
 
 typedef struct { uint64_t k0, k1, k2, idx; } skey;
@@ -151,6 +163,7 @@ static void decode(const uint32_t *ev, uint64_t n, uint32_t bt, const uint32_t *
     for (uint64_t i = 0; i < n; i++) {
         r[i].stmt = stmt ? stmt[i] : 0u;
         r[i].wa = stmt ? 1u : 0u;
+        r[i].rank = 0;
         const uint32_t *w = ev + 4 * i;
         r[i].unit = w[0];
         r[i].vo = w[1];
@@ -212,7 +225,7 @@ static int may_race(const rec_t *r, const skey *g, uint64_t m) {
     return has_w || (has_a && has_r);
 }
 
-static int emit_group(vec *out, const rec_t *r, const skey *g, uint64_t m, int inter) {
+static int emit_group(vec *out, const rec_t *r, const skey *g, uint64_t m, int inter, int paper) {
     if (m < 2 || !may_race(r, g, m)) return 1;
     for (uint32_t cls = 0; cls < 2; cls++) {
         uint64_t pi, qi;
@@ -224,7 +237,7 @@ static int emit_group(vec *out, const rec_t *r, const skey *g, uint64_t m, int i
         x.scope = (uint8_t)(inter ? 1 : 0);
         x.cls = (uint8_t)cls;
         x.block = inter ? 0xFFFFFFFFu : q->block;
-        x.epoch = inter ? 0xFFFFFFFFu : q->epoch;
+        x.epoch = inter ? (paper ? q->rank : 0xFFFFFFFFu) : q->epoch;
         x.unit = q->unit;
         x.vo_first = p->vo; x.vo_second = q->vo;
         x.gtid_first = p->gtid; x.gtid_second = q->gtid;
@@ -233,9 +246,30 @@ static int emit_group(vec *out, const rec_t *r, const skey *g, uint64_t m, int i
     return 1;
 }
 
+/* ---- paper visit orders: per (space, block, unit), the number of distinct earlier epochs --- */
+static int paper_ranks(rec_t *r, uint64_t n) {
+    skey *k = (skey *)malloc((n ? n : 1) * sizeof(skey));
+    if (!k) return 0;
+    for (uint64_t i = 0; i < n; i++) {
+        k[i].k0 = ((uint64_t)r[i].space << 32) | r[i].block;
+        k[i].k1 = ((uint64_t)r[i].unit << 32) | r[i].epoch;
+        k[i].k2 = 0;
+        k[i].idx = i;
+    }
+    qsort(k, n, sizeof(skey), cmp_skey);
+    uint32_t rank = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        if (i == 0 || k[i].k0 != k[i - 1].k0 || (k[i].k1 >> 32) != (k[i - 1].k1 >> 32)) rank = 0;
+        else if (k[i].k1 != k[i - 1].k1) rank++;
+        r[k[i].idx].rank = rank;
+    }
+    free(k);
+    return 1;
+}
+
 /* ---- races: intra-block groups (space, block, epoch, unit), then inter-block
         groups (global unit); emitted in canonical order ---------------------- */
-static int races(const rec_t *r, uint64_t n, vec *out) {
+static int races(const rec_t *r, uint64_t n, int paper, vec *out) {
     skey *k = (skey *)malloc((n ? n : 1) * sizeof(skey));
     if (!k) return 0;
     for (uint64_t i = 0; i < n; i++) {
@@ -248,21 +282,22 @@ static int races(const rec_t *r, uint64_t n, vec *out) {
     for (uint64_t s = 0; s < n;) {
         uint64_t e = s + 1;
         while (e < n && k[e].k0 == k[s].k0 && k[e].k1 == k[s].k1) e++;
-        if (!emit_group(out, r, k + s, e - s, 0)) { free(k); return 0; }
+        if (!emit_group(out, r, k + s, e - s, 0, paper)) { free(k); return 0; }
         s = e;
     }
-    /* inter-block: global records grouped by unit only */
+    /* inter-block: global records grouped by unit only (paper visit orders: by visit order, then unit,
+       which is also the canonical order of the records emitted) */
     uint64_t m = 0;
     for (uint64_t i = 0; i < n; i++) {
         if (r[i].space != 1) continue;
-        k[m].k0 = r[i].unit; k[m].k1 = 0; k[m].k2 = r[i].vo; k[m].idx = i;
+        k[m].k0 = paper ? r[i].rank : r[i].unit; k[m].k1 = paper ? r[i].unit : 0; k[m].k2 = r[i].vo; k[m].idx = i;
         m++;
     }
     qsort(k, m, sizeof(skey), cmp_skey);
     for (uint64_t s = 0; s < m;) {
         uint64_t e = s + 1;
-        while (e < m && k[e].k0 == k[s].k0) e++;
-        if (!emit_group(out, r, k + s, e - s, 1)) { free(k); return 0; }
+        while (e < m && k[e].k0 == k[s].k0 && k[e].k1 == k[s].k1) e++;
+        if (!emit_group(out, r, k + s, e - s, 1, paper)) { free(k); return 0; }
         s = e;
     }
     free(k);
@@ -272,9 +307,11 @@ static int races(const rec_t *r, uint64_t n, vec *out) {
 /* ---- redundant barriers ------------------------------------------------------
    Barrier k of block b separates epochs k and k+1. It is NOT redundant iff some
    unit (either space) of block b has a record p of epoch k and a record q of
-   epoch k+1 that would race if the two epochs were one (owners: threads). */
+   epoch k+1 that would race if the two epochs were one (owners: threads).
+   Paper visit orders: q is in the unit's next non-empty epoch of block b after
+   k (the group of the next visit order), whichever epoch that is. */
 static int barriers(const rec_t *r, uint64_t n, const uint32_t *counts, uint32_t nb, uint32_t bt,
-                    uint32_t maxb, vec *bars, vec *grid) {
+                    uint32_t maxb, int paper, vec *bars, vec *grid) {
     uint64_t ne = (uint64_t)maxb + 1;
     uint8_t *nonred = (uint8_t *)calloc((uint64_t)nb * ne + 1, 1);
     uint32_t *maxc = (uint32_t *)calloc((uint64_t)nb + 1, sizeof(uint32_t));
@@ -293,9 +330,9 @@ static int barriers(const rec_t *r, uint64_t n, const uint32_t *counts, uint32_t
     for (uint64_t s = 0; s < n;) {           /* one (space, block, unit, epoch) group at a time */
         uint64_t e = s + 1;
         while (e < n && k[e].k0 == k[s].k0 && k[e].k1 == k[s].k1) e++;
-        /* the next group: same (space, block, unit), epoch + 1 ? */
+        /* the next group: same (space, block, unit), epoch + 1 (paper visit orders: any later epoch) ? */
         if (e < n && k[e].k0 == k[s].k0 && (k[e].k1 >> 32) == (k[s].k1 >> 32) &&
-            (k[e].k1 & 0xFFFFFFFFu) == (k[s].k1 & 0xFFFFFFFFu) + 1) {
+            (paper || (k[e].k1 & 0xFFFFFFFFu) == (k[s].k1 & 0xFFFFFFFFu) + 1)) {
             uint64_t f = e + 1;
             while (f < n && k[f].k0 == k[e].k0 && k[f].k1 == k[e].k1) f++;
             const rec_t *r0 = &r[k[s].idx];
@@ -363,10 +400,11 @@ orc_result *orc_check2(const uint32_t *ev, uint64_t n, const uint32_t *counts, u
     rec_t *r = (rec_t *)malloc((n ? n : 1) * sizeof(rec_t));
     if (!r) { free(res); return NULL; }
     decode(ev, n, bt, (flags & FLAG_WARP_AWARE) ? stmt : NULL, r);
+    const int paper = (flags & FLAG_PAPER_ORDER) != 0;
     vec rv = {0, 0, 0, sizeof(orc_race)}, dv = {0, 0, 0, sizeof(orc_div)};
     vec bv = {0, 0, 0, sizeof(orc_bar)}, gv = {0, 0, 0, sizeof(uint32_t)};
-    int ok = races(r, n, &rv) && divergence(counts, nb, bt, &dv) &&
-             barriers(r, n, counts, nb, bt, maxb, &bv, &gv);
+    int ok = (!paper || paper_ranks(r, n)) && races(r, n, paper, &rv) && divergence(counts, nb, bt, &dv) &&
+             barriers(r, n, counts, nb, bt, maxb, paper, &bv, &gv);
     free(r);
     res->races = (orc_race *)rv.p; res->n_races = rv.n;
     res->divs = (orc_div *)dv.p; res->n_divs = dv.n;

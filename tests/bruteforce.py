@@ -5,6 +5,14 @@ looks at every pair of records and applies the definitions directly
 (Theorem 1 without warp refinements, the atomic rule, the inter-block rule for
 global memory, the one-barrier-at-a-time redundancy test of Algorithm 5 and the
 barrier-count divergence rule of Algorithm 4).
+
+With flag PAPER_ORDER it replays Algorithm 3's visit-order counters instead of
+using epochs: per (space, block, unit) a counter starts at 0, an access takes
+the counter's value, and the barrier at the end of an epoch bumps the counter
+when the unit was accessed in that epoch. Pairs of one block then race at
+equal counter values, pairs of different blocks on a global unit as well, and
+two accesses at consecutive counter values make the barrier that bumped the
+counter between them needed.
 """
 from __future__ import annotations
 
@@ -57,6 +65,22 @@ def brute(trace) -> dict:
     def order(r):
         return (r["vo"], r["i"])
 
+    paper = bool(getattr(trace, "flags", 0) & 4)
+    if paper:   # Algorithm 3: replay the counters epoch by epoch
+        touched = {}
+        for r in recs:
+            touched.setdefault((r["space"], r["block"], r["unit"]), set()).add(r["epoch"])
+        counter_at = {}
+        for key, eps in touched.items():
+            c, vals = 0, {}
+            for e in range(max(eps) + 1):
+                vals[e] = c
+                if e in eps:      # the barrier ending epoch e bumps a unit accessed in epoch e
+                    c += 1
+            counter_at[key] = vals
+        for r in recs:
+            r["pvo"] = counter_at[(r["space"], r["block"], r["unit"])][r["epoch"]]
+
     best = {}
     nonred = set()
     for a in recs:
@@ -75,10 +99,14 @@ def brute(trace) -> dict:
                     if key not in best or cand[:2] < best[key][:2]:
                         best[key] = cand
                 lo, hi = (p, q) if p["epoch"] < q["epoch"] else (q, p)
-                if hi["epoch"] == lo["epoch"] + 1 and _conflict(lo, hi, gp, gq):
+                if paper:
+                    # consecutive counter values: the barrier ending lo's epoch made the step
+                    if hi["pvo"] == lo["pvo"] + 1 and _conflict(lo, hi, gp, gq):
+                        nonred.add((p["block"], lo["epoch"]))
+                elif hi["epoch"] == lo["epoch"] + 1 and _conflict(lo, hi, gp, gq):
                     nonred.add((p["block"], lo["epoch"]))
-            elif p["space"] == 1 and _conflict(p, q, p["block"], q["block"]):
-                key = (1, 1, 0xFFFFFFFF, 0xFFFFFFFF, p["unit"], cls)
+            elif p["space"] == 1 and (not paper or p["pvo"] == q["pvo"]) and _conflict(p, q, p["block"], q["block"]):
+                key = (1, 1, 0xFFFFFFFF, q["pvo"] if paper else 0xFFFFFFFF, p["unit"], cls)
                 cand = (order(q), order(p), p, q)
                 if key not in best or cand[:2] < best[key][:2]:
                     best[key] = cand

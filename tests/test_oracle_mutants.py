@@ -30,8 +30,8 @@ MUTANTS = {
     "pair_order_swapped": ("x.vo_first = p->vo; x.vo_second = q->vo;", "x.vo_first = q->vo; x.vo_second = p->vo;"),
     "inter_includes_shared": ("        if (r[i].space != 1) continue;\n", ""),
     "intra_ignores_epoch": ("k[i].k1 = ((uint64_t)r[i].epoch << 32) | r[i].unit;", "k[i].k1 = r[i].unit;"),
-    "redundancy_ignores_space": ("k[i].k0 = ((uint64_t)r[i].space << 32) | r[i].block;\n        k[i].k1 = ((uint64_t)r[i].unit << 32)",
-                                 "k[i].k0 = r[i].block;\n        k[i].k1 = ((uint64_t)r[i].unit << 32)"),
+    "redundancy_ignores_space": ("k[i].k0 = ((uint64_t)r[i].space << 32) | r[i].block;\n        k[i].k1 = ((uint64_t)r[i].unit << 32) | r[i].epoch;\n        k[i].k2 = r[i].vo;",
+                                 "k[i].k0 = r[i].block;\n        k[i].k1 = ((uint64_t)r[i].unit << 32) | r[i].epoch;\n        k[i].k2 = r[i].vo;"),
     "vo_check_allows_equal": ("vo <= ev[4 * (i - 1) + 1]", "vo < ev[4 * (i - 1) + 1]"),
     "read_read_conflicts": ("    if (!modifies(p->act) && !modifies(q->act)) return 0;\n", ""),
 }

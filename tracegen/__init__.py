@@ -26,6 +26,7 @@ READ, WRITE, ATOMIC = 0, 1, 2
 SHARED, GLOBAL = 0, 1
 UNSORTED = 1  # trace flag: visit orders are not increasing in record order
 WARP_AWARE = 2  # trace flag: records carry statement words (Theorem 1's warp refinements apply)
+PAPER_ORDER = 4  # trace flag: the paper's visit-order counters (Algorithm 3) group the tuples
 DIVERGED = 0x80000000  # statement-word bit: the access came after the thread's warp diverged
 
 DEFAULT_SEED = 1905018330
