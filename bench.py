@@ -388,6 +388,12 @@ def single_trace_arm(args):
         name = ("warp-aware (Theorem 1 with its warp conditions): the grid workload with a statement word per "
                 "record, 5% of (block, warp, epoch) diverged; radix-sort path, pairwise group search")
         sample_blocks = 16
+    elif args.workload == "paper":
+        tr = make_trace(0, args.blocks)
+        tr.flags |= tracegen.PAPER_ORDER
+        name = ("paper visit orders (Algorithm 3's counters): the grid workload with flag PAPER_ORDER; radix-sort "
+                "path, visit orders of global records by a segmented scan, inter-block groups per visit order")
+        sample_blocks = 16
     else:
         tr, name = tracegen.c4(), "barrier: 1024 blocks x 1024 threads, 64 epochs, 4 accesses per thread per epoch"
         sample_blocks = 8
@@ -599,13 +605,16 @@ def main():
     ap.add_argument("--path", choices=["auto", "sort"], default="auto")
     ap.add_argument("--hash-shape", type=int, choices=[0, 1, 2], default=0,
                     help="hash path CTAs: 0 chosen per call, 1 one 1024-thread CTA per SM, 2 two 512-thread CTAs")
+    ap.add_argument("--graph-replay", choices=["auto", "off"], default="auto",
+                    help="auto: repeated identical calls replayed by the library as one CUDA graph; off: direct launches")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--oracle-blocks", type=int, default=256)
     ap.add_argument("--ref-blocks", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--blocks", type=int, default=1024, help="grid blocks (1024 = the benchmark workload; "
                     "smaller values only for profiling captures)")
-    ap.add_argument("--workload", choices=["grid", "batch", "serve", "fitness", "evolve", "strided", "barrier", "warp"],
+    ap.add_argument("--workload", choices=["grid", "batch", "serve", "fitness", "evolve", "strided", "barrier", "warp",
+                                           "paper"],
                     default="grid",
                     help="grid: the benchmark line; batch / serve: the batched and served forms; fitness: Eq. 1 "
                          "over the grid workload (separate lines)")
@@ -619,7 +628,8 @@ def main():
         import torch
         torch.cuda.set_device(0)
         out = {"batch": batch_arm, "serve": serve_arm, "fitness": fitness_arm, "evolve": evolve_arm,
-               "strided": single_trace_arm, "barrier": single_trace_arm, "warp": single_trace_arm}[args.workload](args)
+               "strided": single_trace_arm, "barrier": single_trace_arm, "warp": single_trace_arm,
+               "paper": single_trace_arm}[args.workload](args)
         print(json.dumps({"metric": METRIC, **out}))
         return
 
@@ -641,7 +651,8 @@ def main():
     tr = make_trace(rank, args.blocks)
     dt = simulee.to_device(tr, f"cuda:{local}")
     chk = simulee.Checker(local, path=simulee.PATH_SORT if args.path == "sort" else simulee.PATH_AUTO,
-                          hash_shape=args.hash_shape)
+                          hash_shape=args.hash_shape,
+                          graph_replay=simulee.GRAPH_OFF if args.graph_replay == "off" else simulee.GRAPH_AUTO)
     ws = chk.workspace(chk.workspace_size(dt))
     caps = dict(races_cap=4_000_000, div_cap=tr.n_blocks, red_cap=tr.n_blocks * tr.max_barriers,
                 grid_cap=tr.max_barriers)

@@ -60,6 +60,16 @@ enum { SIMULEE_WW = 0, SIMULEE_RW = 1 };
    after the warp's threads diverged. Not combinable with SIMULEE_FLAG_UNSORTED. */
 #define SIMULEE_FLAG_WARP_AWARE 2u
 #define SIMULEE_STMT_DIVERGED 0x80000000u  /* statement-word bit: the access came after divergence */
+/* The paper's visit-order counters (Algorithm 3, Sec. 3.2.2): a counter per memory address,
+   restarted at 0 for every block (global memory included), bumped by a barrier only when the
+   address was visited since its last bump. An access's visit order is then the number of earlier
+   epochs in which its block touched its unit, and Algorithm 5 groups by it: intra-block groups are
+   unchanged; a barrier k is needed when a unit's accesses in epoch k conflict with its accesses in
+   the block's next epoch that touches the unit (empty epochs skipped); global accesses of different
+   blocks conflict only at equal visit orders, and such an INTER race record carries that visit
+   order in its epoch field. Such traces take the radix-sort path. Not combinable with
+   SIMULEE_FLAG_WARP_AWARE. */
+#define SIMULEE_FLAG_PAPER_ORDER 4u
 
 /*
  * One access record (16 bytes, four little-endian words): one tuple
@@ -102,7 +112,8 @@ typedef struct {
  * SIMULEE_FLAG_WARP_AWARE) when its owners differ, at least one access writes
  * or is atomic, and not both are atomic.
  * Groups: INTRA = one (space, block, epoch, unit), owners are threads;
- * INTER = one global unit across blocks in any epochs, owners are blocks.
+ * INTER = one global unit across blocks in any epochs, owners are blocks (with
+ * SIMULEE_FLAG_PAPER_ORDER: one global unit and one visit order).
  * Class WW when both accesses modify the unit, RW when one reads.
  * The pair is the one whose later access comes first in schedule order
  * (visit_order, then record index), and among those the earliest partner.

@@ -236,7 +236,11 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
                 route_sg = rok && (binel[sb] != 0 || ((spill[sb * L.swords + (ep >> 5)] >> (ep & 31)) & 1u));
             }
             const bool isS = rok && route_sg && space == 0u, isG = rok && route_sg && space == 1u;
-            const bool isX = MODE == IN_FIRST && rok && space == 1u;
+            // inter-block stream: global records (a trace with the paper's visit-order counters gets its
+            // elements from the sorted intra-block stream instead, once the counters are known; its units
+            // are marked here all the same)
+            const bool markX = MODE == IN_FIRST && rok && space == 1u;
+            const bool isX = markX && !(d.flags & TF_PAPER_ORDER);
             const uint32_t bS = __ballot_sync(0xFFFFFFFFu, isS), bG = __ballot_sync(0xFFFFFFFFu, isG);
             const uint32_t bX = __ballot_sync(0xFFFFFFFFu, isX);
             cS += __popc(bS);
@@ -247,7 +251,7 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
                 const uint64_t sb = (uint64_t)d.block_off + blk;
                 if (bS) hist_add(hs, shl(sb, L.bus + L.be) | shl(u, L.be) | ep, np_s, isS, bS);
                 if (bG) hist_add(hg, shl(sb, L.bug + L.be) | shl(u, L.be) | ep, np_g, isG, bG);
-                if (isX) sig_mark(L, sig, sig_slot(L, t, u), blk, (uint32_t)sb);
+                if (markX) sig_mark(L, sig, sig_slot(L, t, u), blk, (uint32_t)sb);
             }
         }
         if (MODE != IN_VALIDATE) {
@@ -298,7 +302,7 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
                         // when blocks fit 20 bits, else the thread id
                         const uint32_t xo = d.nb <= (1u << 20) ? ((blk << 10) | (w3 & 0x3FFu)) : blk * d.bt + (w3 & 0xFFFFu);
                         const uint32_t o = oX + __popc(bX & lt);
-                        xk[o] = (KX)(shl(t, L.bug) | u);
+                        xk[o] = (KX)(shl(t, L.bug + L.bxr) | u);
                         xv[o] = make_payload(act, xo, pos);
                     }
                 }
@@ -381,7 +385,7 @@ k_x_filter(const KX *__restrict__ xk, const uint64_t *__restrict__ xv, KX *yk, u
         for (int j = 0; j < XF_ITEMS; j++) {
             const uint64_t i = base + j * XF_THREADS + tid;
             const uint64_t kk = (uint64_t)k[j];
-            const uint32_t t = (uint32_t)(L.bug >= 64 ? 0 : (kk >> L.bug)), unit = (uint32_t)(kk & umask);
+            const uint32_t t = (uint32_t)(L.bug + L.bxr >= 64 ? 0 : (kk >> (L.bug + L.bxr))), unit = (uint32_t)(kk & umask);
             sv[j] = i < n ? sig[sig_slot(L, t, unit)] : 0u;
         }
         uint64_t v[XF_ITEMS];
@@ -688,7 +692,7 @@ k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, c
             uint32_t trace, bt = 1;
             bool pad = false;
             if (INTER) {
-                trace = (uint32_t)((uint64_t)kg >> L.bug);
+                trace = (uint32_t)((uint64_t)kg >> (L.bug + L.bxr));
                 bt = td[trace].bt;
                 pad = td[trace].nb <= (1u << 20);
             } else {
@@ -723,6 +727,8 @@ k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, c
             if (INTER) {
                 if (cnt >= 2) {
                     const uint32_t unit = (uint32_t)((uint64_t)kg & umask);
+                    // the visit order of a paper-counter trace's group (0 for other traces)
+                    const uint32_t vord = (uint32_t)(((uint64_t)kg >> L.bug) & ((1ull << L.bxr) - 1));
 #pragma unroll
                     for (int cls = 0; cls < 2; cls++) {
                         uint64_t p, q;
@@ -730,7 +736,7 @@ k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, c
                         // owner codes back to block * block_threads + tid
                         p = (p & ~0xFFFFFFFFull) | own_b.gtid((uint32_t)p);
                         q = (q & ~0xFFFFFFFFull) | own_b.gtid((uint32_t)q);
-                        emit_race(rs, ctl, trace, race_key(L, trace, 1u, 1u, 0u, 0u, unit, cls), p, q);
+                        emit_race(rs, ctl, trace, race_key(L, trace, 1u, 1u, 0u, vord, unit, cls), p, q);
                     }
                 }
             } else {
@@ -770,7 +776,12 @@ k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, c
                 K kn = 0;
                 if (g + 1 < G) { has = true; kn = skey[shead[g + 1]]; }
                 else if (s_has_next) { has = true; kn = s_next_key; }
-                if (has && kn == kg + 1 && adj_conflict(sadj[g], sadj[g + 1])) {
+                // the next group of the same (block, unit): epoch + 1, or, with the paper's counters, the
+                // next epoch that touches the unit
+                bool next = kn == kg + 1;
+                if (has && !next && ((uint64_t)kn >> be) == ((uint64_t)kg >> be))
+                    next = (td[tob[(uint64_t)kg >> (bu + be)]].flags & TF_PAPER_ORDER) != 0;
+                if (has && next && adj_conflict(sadj[g], sadj[g + 1])) {
                     const uint64_t sk = (uint64_t)kg >> be;
                     mark_needed(nonred, L, (uint32_t)(sk >> bu), (uint32_t)((uint64_t)kg & ((1ull << be) - 1)));
                 }
@@ -867,7 +878,10 @@ __global__ void k_write_races(const uint64_t *__restrict__ keys, const uint64_t 
         uint32_t block = (uint32_t)((k >> (1 + L.bu + L.be)) & ((1ull << L.bb) - 1)) - d.block_off;
         const uint32_t scope = (uint32_t)((k >> (1 + L.bu + L.be + L.bb)) & 1u);
         const uint32_t space = (uint32_t)((k >> (2 + L.bu + L.be + L.bb)) & 1u);
-        if (scope) { block = 0xFFFFFFFFu; epoch = 0xFFFFFFFFu; }
+        if (scope) {   // inter-block: no block; the visit order of a paper-counter trace, else no epoch
+            block = 0xFFFFFFFFu;
+            if (!(d.flags & TF_PAPER_ORDER)) epoch = 0xFFFFFFFFu;
+        }
         uint4 *o = reinterpret_cast<uint4 *>(d.races + 32 * rank);
         o[0] = make_uint4(space | (scope << 8) | (cls << 16), block, epoch, unit);
         o[1] = p;

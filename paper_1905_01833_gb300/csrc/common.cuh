@@ -32,7 +32,7 @@
 namespace simk {
 
 constexpr uint32_t ACT_R = 0, ACT_W = 1, ACT_A = 2;
-constexpr uint32_t TF_UNSORTED = 1, TF_WARP_AWARE = 2;     // trace flags
+constexpr uint32_t TF_UNSORTED = 1, TF_WARP_AWARE = 2, TF_PAPER_ORDER = 4;     // trace flags
 constexpr uint32_t STMT_DIVERGED = 0x80000000u;
 constexpr uint64_t EMPTY = ~0ull;
 constexpr int RADIX_BITS = 8;
@@ -80,6 +80,7 @@ struct Ctl {
     unsigned int n_fb;            // tiles listed for the fallback read
     unsigned int hb_next;         // next block for the hash path's CTAs
     unsigned int n_rf;            // race records left by the race filter
+    unsigned int px_tile;         // next tile of the visit-order scan
     unsigned int tiles[MAX_PASSES];  // onesweep tile counters, one per pass
 };
 
@@ -95,6 +96,8 @@ struct Layout {
     uint32_t bb, bus, bug, be, bu, btr;   // bit widths: batch block, shared unit, global unit, epoch,
                                            // max(unit), trace index
     uint32_t bits_s, bits_g, bits_x, bits_r, bits_q;
+    uint32_t any_paper;              // a trace has the paper's visit-order counters
+    uint32_t bxr;                    // bits of the visit-order field of inter-block keys (0 without such a trace)
     uint32_t np_s, np_g, np_x, np_r, np_q;    // radix passes per stream
     uint32_t p0_s, p0_g, p0_x, p0_r, p0_q;    // first pass index of each stream
     uint32_t wide_s, wide_g, wide_x, wide_q;  // 64-bit keys

@@ -272,7 +272,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                     const uint32_t blk = e.z, w3 = e.w, act = (w3 >> 28) & 3u;
                     const uint32_t xo = pad ? ((blk << 10) | (w3 & 0x3FFu)) : blk * bt + (w3 & 0xFFFFu);
                     if (o < xcap) {
-                        xk[o] = (KX)(shl(t, L.bug) | e.x);
+                        xk[o] = (KX)(shl(t, L.bug + L.bxr) | e.x);
                         xv[o] = make_payload(act, xo, e.y);
                     }
                     sig_mark(L, sig, sig_slot(L, t, e.x), blk, d.block_off + blk);

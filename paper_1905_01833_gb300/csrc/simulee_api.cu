@@ -28,6 +28,7 @@
 #include "hash_path.cuh"
 #include "fitness.cuh"
 #include "models.cuh"
+#include "paper_order.cuh"
 #include "sort.cuh"
 
 using namespace simk;
@@ -77,7 +78,8 @@ simulee_status check_trace_args(const simulee_trace *t) {
     if (t->n_blocks == 0 || t->block_threads == 0 || t->block_threads > 1024) return SIMULEE_EINVAL;
     if ((uint64_t)t->n_blocks * t->block_threads > (1ull << 30)) return SIMULEE_EINVAL;
     if (t->max_barriers > 4095) return SIMULEE_EINVAL;
-    if (t->flags & ~(SIMULEE_FLAG_UNSORTED | SIMULEE_FLAG_WARP_AWARE)) return SIMULEE_EINVAL;
+    if (t->flags & ~(SIMULEE_FLAG_UNSORTED | SIMULEE_FLAG_WARP_AWARE | SIMULEE_FLAG_PAPER_ORDER)) return SIMULEE_EINVAL;
+    if ((t->flags & SIMULEE_FLAG_WARP_AWARE) && (t->flags & SIMULEE_FLAG_PAPER_ORDER)) return SIMULEE_EINVAL;
     if (t->flags & SIMULEE_FLAG_WARP_AWARE) {
         if (t->flags & SIMULEE_FLAG_UNSORTED) return SIMULEE_EINVAL;
         if (t->n_events > 0 && (!t->stmt || ((uintptr_t)t->stmt & 3u) != 0)) return SIMULEE_EINVAL;
@@ -91,7 +93,7 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout 
     memset(&L, 0, sizeof L);
     if (T == 0 || T > kMaxTraces) return SIMULEE_EINVAL;
     uint64_t n = 0, nb = 0, tiles = 0;
-    uint32_t maxb = 0, su = 0, gu = 0, uns = 0, maxnb = 0;
+    uint32_t maxb = 0, su = 0, gu = 0, uns = 0, maxnb = 0, paper = 0;
     for (uint32_t i = 0; i < T; i++) {
         const simulee_trace &t = tr[i];
         if (t.n_blocks == 0 || t.block_threads == 0 || t.block_threads > 1024 || t.max_barriers > 4095 ||
@@ -105,6 +107,7 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout 
         su = std::max(su, t.shared_units);
         gu = std::max(gu, t.global_units);
         uns |= t.flags & SIMULEE_FLAG_UNSORTED;
+        paper |= (t.flags & SIMULEE_FLAG_PAPER_ORDER) ? 1u : 0u;
     }
     if (n >= (1ull << 31) || nb >= (1ull << 31)) return SIMULEE_EINVAL;
     L.n = n;
@@ -121,7 +124,10 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout 
     L.btr = bits_for(T);
     L.bits_s = L.bb + L.bus + L.be;
     L.bits_g = L.bb + L.bug + L.be;
-    L.bits_x = L.btr + L.bug;
+    // inter-block keys: trace | visit order (paper counters only) | unit
+    L.any_paper = paper;
+    L.bxr = paper ? L.be : 0;
+    L.bits_x = L.btr + L.bxr + L.bug;
     L.bits_r = 3 + L.bb + L.be + L.bu + L.btr;
     L.bits_q = 32 + L.btr;
     if (L.bits_s > 64 || L.bits_g > 64 || L.bits_x > 64 || L.bits_r > 64 || L.bits_q > 64) return SIMULEE_EINVAL;
@@ -388,7 +394,7 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
     for (uint32_t i = 0; i < T; i++) {
         TraceDesc &d = hdesc[i];
         d.hash_ok = (route_any && ctx->opt.path != SIMULEE_PATH_SORT &&
-                     !(d.flags & (SIMULEE_FLAG_UNSORTED | SIMULEE_FLAG_WARP_AWARE)) &&
+                     !(d.flags & (SIMULEE_FLAG_UNSORTED | SIMULEE_FLAG_WARP_AWARE | SIMULEE_FLAG_PAPER_ORDER)) &&
                      d.su < 0x7FFFFFFFu && d.gu < 0x7FFFFFFFu && d.n > 0) ? 1u : 0u;
         any_hash |= d.hash_ok != 0;
     }
@@ -572,6 +578,52 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
         size_t sk[2] = {L.off_sk[0], L.off_sk[1]}, sv[2] = {L.off_sv[0], L.off_sv[1]};
         size_t gk[2] = {L.off_gk[0], L.off_gk[1]}, gv[2] = {L.off_gv[0], L.off_gv[1]};
         size_t xk[2] = {L.off_xk[0], L.off_xk[1]}, xv[2] = {L.off_xv[0], L.off_xv[1]};
+        if (L.any_paper) {
+            // the intra-block streams first (their digit bases come from the record reads); the inter-block
+            // elements of traces with the paper's visit-order counters come from the sorted global stream
+            uint32_t *dbase = R.at<uint32_t>(L.off_dbase);
+            if (L.p0_x > 0) {
+                k_digit_bases<<<L.p0_x, RADIX, 0, st>>>(hist, dbase, R.ctl);
+                R.launches++;
+            }
+            bs = L.wide_s ? R.sort<uint64_t>(sk, sv, &R.ctl->n_s, L.n, L.np_s, L.p0_s)
+                          : R.sort<uint32_t>(sk, sv, &R.ctl->n_s, L.n, L.np_s, L.p0_s);
+            bg = L.wide_g ? R.sort<uint64_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g)
+                          : R.sort<uint32_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g);
+            const int gp = R.grid_for(L.n, PX_TILE, 4);
+            unsigned long long *stw = R.at<unsigned long long>(L.off_status);
+#define SIM_PX(KG, KX)                                                                                            \
+    k_paper_x<KG, KX><<<gp, PX_THREADS, 0, st>>>(R.at<KG>(gk[bg]), R.at<uint64_t>(gv[bg]), &R.ctl->n_g, L, td, tob, \
+                                                stw, R.ctl, R.at<KX>(xk[0]), R.at<uint64_t>(xv[0]), R.wait_ns)
+            if (L.wide_g) {
+                if (L.wide_x) SIM_PX(uint64_t, uint64_t);
+                else SIM_PX(uint64_t, uint32_t);
+            } else {
+                if (L.wide_x) SIM_PX(uint32_t, uint64_t);
+                else SIM_PX(uint32_t, uint32_t);
+            }
+#undef SIM_PX
+            R.launches++;
+            if (L.sig_slots) {
+                const int gf = R.grid_for(L.x_cap, XF_TILE, L.wide_x ? 2 : 3);
+                if (L.wide_x)
+                    k_x_filter<uint64_t><<<gf, XF_THREADS, 0, st>>>(R.at<uint64_t>(xk[0]), R.at<uint64_t>(xv[0]),
+                                                                 R.at<uint64_t>(xk[1]), R.at<uint64_t>(xv[1]), sig, L,
+                                                                 R.ctl, hist);
+                else
+                    k_x_filter<uint32_t><<<gf, XF_THREADS, 0, st>>>(R.at<uint32_t>(xk[0]), R.at<uint64_t>(xv[0]),
+                                                                 R.at<uint32_t>(xk[1]), R.at<uint64_t>(xv[1]), sig, L,
+                                                                 R.ctl, hist);
+                R.launches++;
+            }
+            if (L.np_x > 0) {
+                k_digit_bases<<<L.np_x, RADIX, 0, st>>>(hist + (size_t)L.p0_x * RADIX, dbase + (size_t)L.p0_x * RADIX,
+                                                        R.ctl);
+                R.launches++;
+            }
+            bx = L.wide_x ? R.sort<uint64_t>(xk, xv, &R.ctl->n_xf, L.n, L.np_x, L.p0_x, 1)
+                          : R.sort<uint32_t>(xk, xv, &R.ctl->n_xf, L.n, L.np_x, L.p0_x, 1);
+        } else {
         // inter-block records of units touched by one block only are dropped before sorting;
         // the filter also builds the inter stream's digit histograms
         if (L.sig_slots) {
@@ -594,6 +646,7 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
                       : R.sort<uint32_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g);
         bx = L.wide_x ? R.sort<uint64_t>(xk, xv, &R.ctl->n_xf, L.n, L.np_x, L.p0_x, 1)
                       : R.sort<uint32_t>(xk, xv, &R.ctl->n_xf, L.n, L.np_x, L.p0_x, 1);
+        }
     }
     R.mark(SIMULEE_STAGE_SORT, 1);
 

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libsimulee.so")
 OK, EINVAL, EBADTRACE, ENOMEM, ETRUNC, ETIMEOUT, ECUDA = range(7)
 FLAG_UNSORTED = 1
 FLAG_WARP_AWARE = 2
+FLAG_PAPER_ORDER = 4   # the paper's visit-order counters (Algorithm 3) group the tuples
 STMT_DIVERGED = 0x80000000
 PATH_AUTO, PATH_SORT, PATH_HASH = 0, 1, 2
 GRAPH_AUTO, GRAPH_OFF = 0, 1   # repeated identical check calls replayed as one CUDA graph, or always direct
