@@ -320,6 +320,19 @@ def batch_arm(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    # per-stage times from further calls with the library's stage events (not part of the timed steps)
+    nst = len(simulee.STAGES)
+    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * nst)] for _ in range(3)]
+    for row in sev:
+        for e in row:
+            e.record(stream)
+    for row in sev:
+        chk.set_stage_events(row)
+        call()
+    torch.cuda.synchronize()
+    chk.set_stage_events(None)
+    stage_ms = {name: sum(r[2 * k].elapsed_time(r[2 * k + 1]) for r in sev) / len(sev)
+                for k, name in enumerate(simulee.STAGES)}
     # the same call captured once in a CUDA graph and replayed
     g = torch.cuda.CUDAGraph()
     s2 = torch.cuda.Stream()
@@ -342,6 +355,7 @@ def batch_arm(args):
                         f"block sizes 64..1024, 4..64 epochs", "traces": T, "n_events": n_ev,
             "value": n_ev / (ms * 1e-3) / 1e9, "ms_per_step": ms,
             "graph_value": n_ev / (ms_g * 1e-3) / 1e9, "graph_ms_per_step": ms_g, "unit": UNIT,
+            "stages_ms": stage_ms,
             "launches_per_step": chk.last_launches(), "workspace_bytes": ws.numel(), "gen_s": gen_s,
             **({"cpu_baseline": base} if base else {})}
 

@@ -91,8 +91,8 @@ __device__ __forceinline__ void hist_add(uint32_t *sh, uint64_t key, uint32_t np
 // ---------------------------------------------------------------------------
 constexpr uint32_t SIG_MULTI = 0x80000000u;
 
-__device__ __forceinline__ uint64_t sig_slot(const Layout &L, uint32_t t, uint32_t unit) {
-    if (L.sig_direct) return unit;
+__device__ __forceinline__ uint64_t sig_slot(const Layout &L, uint64_t sig_off, uint32_t t, uint32_t unit) {
+    if (L.sig_direct) return sig_off + unit;
     return (mix32((t * 0x9E3779B1u) ^ unit) ^ ((uint64_t)t << 7)) & (L.sig_slots - 1);
 }
 
@@ -251,7 +251,7 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
                 const uint64_t sb = (uint64_t)d.block_off + blk;
                 if (bS) hist_add(hs, shl(sb, L.bus + L.be) | shl(u, L.be) | ep, np_s, isS, bS);
                 if (bG) hist_add(hg, shl(sb, L.bug + L.be) | shl(u, L.be) | ep, np_g, isG, bG);
-                if (markX) sig_mark(L, sig, sig_slot(L, t, u), blk, (uint32_t)sb);
+                if (markX) sig_mark(L, sig, sig_slot(L, d.sig_off, t, u), blk, (uint32_t)sb);
             }
         }
         if (MODE != IN_VALIDATE) {
@@ -364,7 +364,7 @@ constexpr int XF_TILE = XF_THREADS * XF_ITEMS;
 template <class KX>
 __global__ void __launch_bounds__(XF_THREADS, sizeof(KX) == 4 ? 3 : 2)
 k_x_filter(const KX *__restrict__ xk, const uint64_t *__restrict__ xv, KX *yk, uint64_t *yv, const uint32_t *sig,
-           Layout L, Ctl *ctl, uint32_t *hist) {
+           const TraceDesc *__restrict__ td, Layout L, Ctl *ctl, uint32_t *hist) {
     __shared__ uint32_t sh[8 * RADIX];
     __shared__ uint32_t wtot[XF_THREADS / 32];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -386,7 +386,8 @@ k_x_filter(const KX *__restrict__ xk, const uint64_t *__restrict__ xv, KX *yk, u
             const uint64_t i = base + j * XF_THREADS + tid;
             const uint64_t kk = (uint64_t)k[j];
             const uint32_t t = (uint32_t)(L.bug + L.bxr >= 64 ? 0 : (kk >> (L.bug + L.bxr))), unit = (uint32_t)(kk & umask);
-            sv[j] = i < n ? sig[sig_slot(L, t, unit)] : 0u;
+            const uint64_t off = (L.sig_direct && L.T > 1 && i < n && t < L.T) ? td[t].sig_off : 0ull;
+            sv[j] = i < n ? sig[sig_slot(L, off, t, unit)] : 0u;
         }
         uint64_t v[XF_ITEMS];
         uint32_t keep = 0;

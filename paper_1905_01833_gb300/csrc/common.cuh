@@ -50,6 +50,8 @@ struct TraceDesc {
     uint32_t block_off;        // batch-wide index of this trace's block 0
     uint32_t nb, bt, su, gu, maxb, flags;
     uint32_t hash_ok;          // eligible for the short-interval hash path (host decision)
+    uint32_t hlist;            // hash-path traces: position of block 0 in the hash-path block list
+    uint64_t sig_off;          // direct signature table: the slot of this trace's unit 0
     const uint32_t *stmt;      // warp-aware traces: statement word per record
     uint8_t *races;    uint64_t races_cap;    // outputs (device), as in simulee_outputs
     uint8_t *divs;     uint64_t divs_cap;
@@ -78,7 +80,7 @@ struct Ctl {
     unsigned int n_div, n_red;    // divergent blocks / redundant barriers (all traces)
     unsigned int n_q;             // records in the schedule-rank sort (unsorted traces)
     unsigned int n_fb;            // tiles listed for the fallback read
-    unsigned int hb_next;         // next block for the hash path's CTAs
+    unsigned int hb_next[2];      // next list entry for the hash path's CTAs, per launch
     unsigned int n_rf;            // race records left by the race filter
     unsigned int px_tile;         // next tile of the visit-order scan
     unsigned int tiles[MAX_PASSES];  // onesweep tile counters, one per pass
@@ -108,10 +110,11 @@ struct Layout {
     size_t off_spill;                // per block and epoch: a run the hash path leaves to the sort path
     size_t off_tflag;                // per ingest tile: holds a spilled run
     size_t off_bstart;               // per batch-wide block of a hash-path trace: its first record
+    size_t off_blist;                // hash-path blocks, grouped by the CTA shape that takes them
     size_t off_fbt;                  // tiles for the fallback read
     size_t off_sig;                  // block signature per global unit (or unit hash)
     uint64_t sig_slots;              // entries of the signature table (0: no global memory)
-    uint32_t sig_direct;             // one trace: the table is indexed by unit itself
+    uint32_t sig_direct;             // the table is indexed by the trace's offset plus the unit
     uint32_t sig_or;                 // signatures are ORs of (block | ~block << 15)
     uint64_t x_cap;                  // elements of each inter-block stream buffer
     size_t off_ctl, off_td, off_ts, off_tob, off_stats, off_nonred, off_gridnr, off_gridhas, off_cnt_div,

@@ -115,7 +115,7 @@ __device__ __forceinline__ uint64_t hb_item64(uint32_t v) {
 // trace even when it is not block-contiguous (which the hash kernel detects).
 // ---------------------------------------------------------------------------
 __global__ void k_block_ranges(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob, Layout L,
-                               uint32_t *bstart) {
+                               uint32_t *bstart, uint32_t *blist) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -147,7 +147,10 @@ __global__ void k_block_ranges(const TraceDesc *__restrict__ td, const uint32_t 
             lo = f < 0 ? lo + 32 : lo + f;
             lo = min(lo, hi);
         }
-        if (lane == 0) bstart[b] = (uint32_t)lo;
+        if (lane == 0) {
+            bstart[b] = (uint32_t)lo;
+            blist[d.hlist + lb] = (uint32_t)b;   // the block's entry in the hash path's list
+        }
     }
 }
 
@@ -164,7 +167,7 @@ __device__ __forceinline__ void hb_x_fill(KX *xk, uint64_t *xv, uint32_t from, u
 template <class KX, class SH>
 __global__ void __launch_bounds__(SH::threads, SH::ctas_per_sm)
 k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob, const uint32_t *__restrict__ bstart,
-              Layout L, TState *ts, Ctl *ctl, uint32_t *nonred, uint32_t *binel, uint32_t *spill, uint32_t *tflag,
+              const uint32_t *__restrict__ blist, uint32_t lbeg, uint32_t lcnt, unsigned int *queue, Layout L, TState *ts, Ctl *ctl, uint32_t *nonred, uint32_t *binel, uint32_t *spill, uint32_t *tflag,
               KX *xk, uint64_t *xv, uint32_t *sig, RaceStage rs) {
     extern __shared__ __align__(16) uint64_t hb_smem[];
     uint64_t *own = hb_smem;                                               // [2][SH::slots]
@@ -193,10 +196,10 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
     uint32_t xpos = 0, xend = 0;   // this warp's reserved inter-block slots [xpos, xend)
     for (;;) {
         __syncthreads();
-        if (tid == 0) s_blk = atomicAdd(&ctl->hb_next, 1u);
+        if (tid == 0) s_blk = atomicAdd(queue, 1u);
         __syncthreads();
-        const uint32_t b = s_blk;
-        if (b >= L.NB) break;
+        if (s_blk >= lcnt) break;
+        const uint32_t b = blist[lbeg + s_blk];   // this launch's blocks: list entries lbeg .. lbeg + lcnt - 1
         const uint32_t t = tob[b];
         const TraceDesc &d = td[t];
         // uniform: only hash-path traces whose barrier counts are valid (otherwise nothing is reported)
@@ -275,7 +278,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                         xk[o] = (KX)(shl(t, L.bug + L.bxr) | e.x);
                         xv[o] = make_payload(act, xo, e.y);
                     }
-                    sig_mark(L, sig, sig_slot(L, t, e.x), blk, d.block_off + blk);
+                    sig_mark(L, sig, sig_slot(L, d.sig_off, t, e.x), blk, d.block_off + blk);
                 }
                 xpos += tot;
             }

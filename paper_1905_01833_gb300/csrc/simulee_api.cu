@@ -167,13 +167,18 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout 
     L.off_tflag = take((size_t)std::max<uint64_t>(L.ntiles_in, 1) * 4);
     L.zero_end = o;
     L.off_bstart = take((size_t)L.NB * 4);
+    L.off_blist = take((size_t)L.NB * 4);
     L.off_fbt = take((size_t)std::max<uint64_t>(L.ntiles_in, 1) * 4);
-    // block signatures of global units: indexed by unit for one trace with a modest global space,
-    // else by a hash of (trace, unit) into a power-of-two table about the size of the trace
+    // block signatures of global units: indexed directly (each trace's units after the previous
+    // traces' ones) when all traces' global units together fit 2^28 slots, else by a hash of
+    // (trace, unit) into a power-of-two table about the size of the batch (a collision only keeps
+    // records that a direct table would have dropped)
     if (gu > 0) {
-        if (T == 1 && gu <= (1u << 28)) {
+        uint64_t sum_gu = 0;
+        for (uint32_t i = 0; i < T; i++) sum_gu += tr[i].global_units;
+        if (sum_gu <= (1ull << 28)) {
             L.sig_direct = 1;
-            L.sig_slots = gu;
+            L.sig_slots = sum_gu;
         } else {
             uint64_t m = 1u << 16;
             while (m < L.n && m < (1ull << 28)) m <<= 1;
@@ -199,7 +204,8 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout 
     // inter-block stream: every global record, plus the unused tails of the chunks of slots
     // the hash path's warps reserve (one partial chunk per warp that reserved any)
     // (32 warps per SM in either CTA shape, at most one SM's worth per block)
-    const uint64_t hash_warps = (uint64_t)std::max(1, std::min<int>(sms, (int)std::max<uint32_t>(L.NB, 1))) * 32;
+    // (two launches at most, one per CTA shape)
+    const uint64_t hash_warps = (uint64_t)std::max(1, std::min<int>(sms, (int)std::max<uint32_t>(L.NB, 1))) * 32 * 2;
     L.x_cap = n1 + std::min<uint64_t>(hash_warps, n1) * HB_XCH;
     for (int i = 0; i < 2; i++) {
         L.off_sk[i] = take(n1 * ks);
@@ -292,7 +298,7 @@ struct Run {
 };
 
 // descriptors reach the device through kernel parameters (no host staging buffer)
-constexpr int kDescChunk = 200;
+constexpr int kDescChunk = 180;
 struct DescChunk {
     TraceDesc d[kDescChunk];
 };
@@ -337,7 +343,7 @@ __global__ void k_set_count(unsigned int *dst, unsigned int v) { *dst = v; }
 void fill_descs(const simulee_trace *tr, const simulee_outputs *outs, uint8_t *const *reports, uint32_t T,
                 std::vector<TraceDesc> &td) {
     td.resize(T);
-    uint64_t rec = 0, tile = 0;
+    uint64_t rec = 0, tile = 0, sig = 0;
     uint32_t blk = 0;
     for (uint32_t i = 0; i < T; i++) {
         TraceDesc &d = td[i];
@@ -354,6 +360,8 @@ void fill_descs(const simulee_trace *tr, const simulee_outputs *outs, uint8_t *c
         d.gu = tr[i].global_units;
         d.maxb = tr[i].max_barriers;
         d.flags = tr[i].flags;
+        d.sig_off = sig;
+        sig += tr[i].global_units;
         d.stmt = (tr[i].flags & SIMULEE_FLAG_WARP_AWARE) ? tr[i].stmt : nullptr;
         d.races = (uint8_t *)outs[i].races;
         d.races_cap = outs[i].races_cap;
@@ -398,6 +406,38 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
                      d.su < 0x7FFFFFFFu && d.gu < 0x7FFFFFFFu && d.n > 0) ? 1u : 0u;
         any_hash |= d.hash_ok != 0;
     }
+    // hash-path CTA shapes: blocks of at most 256 threads go to two 512-thread CTAs per SM with
+    // 4096-entry tables when there are at least two such blocks per SM (their runs hold fewer distinct
+    // units than that table; one CTA's barriers overlap the other's work), the others to one
+    // 1024-thread CTA per SM with 8192-entry tables. The block list holds the first group, then the
+    // second; each group is one launch.
+    uint32_t nb_small = 0, nb_large = 0;
+    for (uint32_t i = 0; i < T; i++)
+        if (hdesc[i].hash_ok) (hdesc[i].bt <= 256 ? nb_small : nb_large) += hdesc[i].nb;
+    bool split_small;
+    if (ctx->opt.hash_shape == 1) split_small = false;
+    else if (ctx->opt.hash_shape == 2) split_small = true;
+    else split_small = nb_small >= 2u * (uint32_t)ctx->sms;
+    // with a forced shape every block goes to its group
+    const bool all_one = ctx->opt.hash_shape != 0 || !split_small;
+    uint32_t n_first = 0, n_second = 0;
+    {
+        uint32_t o_first = 0, o_second = 0;
+        for (uint32_t i = 0; i < T; i++) {
+            TraceDesc &d = hdesc[i];
+            if (!d.hash_ok) continue;
+            const bool first = all_one || d.bt <= 256;
+            if (first) { d.hlist = o_first; o_first += d.nb; }
+            else { d.hlist = o_second; o_second += d.nb; }
+        }
+        n_first = o_first;
+        n_second = o_second;
+        for (uint32_t i = 0; i < T; i++)
+            if (hdesc[i].hash_ok && !(all_one || hdesc[i].bt <= 256)) hdesc[i].hlist += n_first;
+    }
+    // the first group's shape: small when split (or forced small), else large; the second is large
+    const bool first_small = all_one ? (ctx->opt.hash_shape == 2 || (ctx->opt.hash_shape == 0 && split_small))
+                                     : true;
     int prev_dev = -1;
     cudaGetDevice(&prev_dev);
     if (prev_dev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return SIMULEE_ECUDA;
@@ -526,30 +566,29 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
         //    intra-block checks), then the fallback read of what the hash path left to the sort path
         R.mark(SIMULEE_STAGE_HASH, 0);
         if (route && any_hash) {
-            uint32_t *bstart = R.at<uint32_t>(L.off_bstart);
-            k_block_ranges<<<R.grid_for(L.NB, 8, 16), 256, 0, st>>>(td, tob, L, bstart);
-            // CTA shape: two smaller CTAs per SM when there are blocks enough to fill them and no
-            // hash-path trace has blocks of more than 256 threads (whose runs may hold more distinct
-            // units than the smaller table); otherwise one CTA per SM with the larger table
-            uint32_t max_bt = 0;
-            for (uint32_t i = 0; i < T; i++)
-                if (hdesc[i].hash_ok) max_bt = std::max(max_bt, hdesc[i].bt);
-            const bool small = ctx->opt.hash_shape == 2 ||
-                               (ctx->opt.hash_shape == 0 && max_bt <= 256 && L.NB >= 2u * (uint32_t)ctx->sms);
-#define SIM_HASH(KX, SH)                                                                                            \
-    k_hash_blocks<KX, SH><<<std::max(1, std::min<int>(ctx->sms * SH::ctas_per_sm, (int)L.NB)), SH::threads,        \
-                            hash_blocks_smem<SH>(), st>>>(td, tob, bstart, L, ts, R.ctl, nonred, binel, spill,      \
-                                                          tflag, R.at<KX>(L.off_xk[0]), R.at<uint64_t>(L.off_xv[0]), \
-                                                          sig, rs)
-            if (L.wide_x) {
-                if (small) SIM_HASH(uint64_t, HbSmall);
-                else SIM_HASH(uint64_t, HbLarge);
-            } else {
-                if (small) SIM_HASH(uint32_t, HbSmall);
-                else SIM_HASH(uint32_t, HbLarge);
+            uint32_t *bstart = R.at<uint32_t>(L.off_bstart), *blist = R.at<uint32_t>(L.off_blist);
+            k_block_ranges<<<R.grid_for(L.NB, 8, 16), 256, 0, st>>>(td, tob, L, bstart, blist);
+            R.launches++;
+#define SIM_HASH(KX, SH, BEG, CNT, Q)                                                                               \
+    k_hash_blocks<KX, SH><<<std::max(1, std::min<int>(ctx->sms * SH::ctas_per_sm, (int)(CNT))), SH::threads,       \
+                            hash_blocks_smem<SH>(), st>>>(td, tob, bstart, blist, BEG, CNT, &R.ctl->hb_next[Q], L,  \
+                                                          ts, R.ctl, nonred, binel, spill, tflag,                   \
+                                                          R.at<KX>(L.off_xk[0]), R.at<uint64_t>(L.off_xv[0]), sig, rs)
+            // the first group (small CTAs when split or forced), then the second group (large CTAs)
+            for (int q = 0; q < 2; q++) {
+                const uint32_t beg = q == 0 ? 0u : n_first, cnt = q == 0 ? n_first : n_second;
+                if (cnt == 0) continue;
+                const bool small = q == 0 && first_small;
+                if (L.wide_x) {
+                    if (small) SIM_HASH(uint64_t, HbSmall, beg, cnt, q);
+                    else SIM_HASH(uint64_t, HbLarge, beg, cnt, q);
+                } else {
+                    if (small) SIM_HASH(uint32_t, HbSmall, beg, cnt, q);
+                    else SIM_HASH(uint32_t, HbLarge, beg, cnt, q);
+                }
+                R.launches++;
             }
 #undef SIM_HASH
-            R.launches += 2;
             R.mark(SIMULEE_STAGE_HASH, 1);
             R.mark(SIMULEE_STAGE_FALLBACK, 0);
             k_fallback_tiles<<<R.grid_for(L.ntiles_in, 256, 8), 256, 0, st>>>(td, L, ts, binel, tflag, R.ctl, fbt);
@@ -608,11 +647,11 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
                 const int gf = R.grid_for(L.x_cap, XF_TILE, L.wide_x ? 2 : 3);
                 if (L.wide_x)
                     k_x_filter<uint64_t><<<gf, XF_THREADS, 0, st>>>(R.at<uint64_t>(xk[0]), R.at<uint64_t>(xv[0]),
-                                                                 R.at<uint64_t>(xk[1]), R.at<uint64_t>(xv[1]), sig, L,
+                                                                 R.at<uint64_t>(xk[1]), R.at<uint64_t>(xv[1]), sig, td, L,
                                                                  R.ctl, hist);
                 else
                     k_x_filter<uint32_t><<<gf, XF_THREADS, 0, st>>>(R.at<uint32_t>(xk[0]), R.at<uint64_t>(xv[0]),
-                                                                 R.at<uint32_t>(xk[1]), R.at<uint64_t>(xv[1]), sig, L,
+                                                                 R.at<uint32_t>(xk[1]), R.at<uint64_t>(xv[1]), sig, td, L,
                                                                  R.ctl, hist);
                 R.launches++;
             }
@@ -630,10 +669,10 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
             const int gf = R.grid_for(L.x_cap, XF_TILE, L.wide_x ? 2 : 3);   // resident CTAs per SM
             if (L.wide_x)
                 k_x_filter<uint64_t><<<gf, XF_THREADS, 0, st>>>(R.at<uint64_t>(xk[0]), R.at<uint64_t>(xv[0]), R.at<uint64_t>(xk[1]),
-                                                         R.at<uint64_t>(xv[1]), sig, L, R.ctl, hist);
+                                                         R.at<uint64_t>(xv[1]), sig, td, L, R.ctl, hist);
             else
                 k_x_filter<uint32_t><<<gf, XF_THREADS, 0, st>>>(R.at<uint32_t>(xk[0]), R.at<uint64_t>(xv[0]), R.at<uint32_t>(xk[1]),
-                                                         R.at<uint64_t>(xv[1]), sig, L, R.ctl, hist);
+                                                         R.at<uint64_t>(xv[1]), sig, td, L, R.ctl, hist);
             R.launches++;
         }
         if (L.p0_r > 0) {

@@ -76,7 +76,11 @@ class _Batch:
         n = ctypes.c_size_t()
         simulee._check(simulee.lib().simulee_batch_workspace_size(server.chk.h, arr, T, ctypes.byref(n)),
                        "simulee_batch_workspace_size")
-        self.ws = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=dev)
+        try:
+            self.ws = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=dev)
+        except torch.OutOfMemoryError:   # cached blocks of finished batches: hand them back, then retry once
+            torch.cuda.empty_cache()
+            self.ws = torch.empty(max(int(n.value), 256), dtype=torch.uint8, device=dev)
         self.bytes = self.ws.numel() + sum(b.numel() for b in self.bufs) + self.reports.numel()
         with torch.cuda.stream(stream):
             simulee._check(simulee.lib().simulee_check_batch(
@@ -137,6 +141,19 @@ class Server:
         c = _caps(dt, job.races_cap)
         return int(n.value) + 32 * c[0] + 16 * c[1] + 8 * c[2] + 4 * c[3]
 
+    def _batch_need(self, batch: list[Job]) -> int:
+        """Working memory of a batch as one call: its workspace (the batch's key widths and
+        signature table, which can exceed the sum of its jobs' own) and outputs."""
+        arr = (simulee.Trace * len(batch))(*[j.trace.c() for j in batch])
+        n = ctypes.c_size_t()
+        simulee._check(simulee.lib().simulee_batch_workspace_size(self.chk.h, arr, len(batch), ctypes.byref(n)),
+                       "simulee_batch_workspace_size")
+        out = 0
+        for j in batch:
+            c = _caps(j.trace, j.races_cap)
+            out += 32 * c[0] + 16 * c[1] + 8 * c[2] + 4 * c[3]
+        return int(n.value) + out
+
     def run(self, jobs: list[Job], clock=time.perf_counter) -> dict:
         """Serve jobs at their arrival times (seconds after start); returns latency and throughput figures."""
         torch = self.torch
@@ -181,6 +198,15 @@ class Server:
                     j = pending.popleft()
                     reserve += need[j.jid]
                     batch.append(j)
+                if batch:
+                    # the batch as one call may need more than its jobs' sum: give jobs back until it fits
+                    reserve = self._batch_need(batch)
+                    while len(batch) > 1 and used + reserve > self.budget:
+                        pending.appendleft(batch.pop())
+                        reserve = self._batch_need(batch)
+                    if used + reserve > self.budget and inflight:
+                        pending.extendleft(reversed(batch))   # wait for memory to come back
+                        batch = []
                 if batch:
                     t_adm = clock() - t0
                     for j in batch:

@@ -82,6 +82,38 @@ def test_batch_mixing_paths():
         assert diff(got[i], oracle.check(tr)) == [], f"trace {i}"
 
 
+def test_batch_split_between_cta_shapes():
+    """A batch with at least two blocks of at most 256 threads per SM and some 1024-thread blocks:
+    the first go to the two-CTA shape, the others to the one-CTA shape, in two launches over one
+    block list; every trace equals checking it alone."""
+    from paper_1905_01833_gb300 import simulee
+    from gpu_util import checker
+    trs = [tracegen.pattern(51, n_blocks=200, block_threads=64, n_epochs=6, shared_units=4096, global_units=1 << 20),
+           tracegen.pattern(52, n_blocks=2, block_threads=1024, n_epochs=5, shared_units=12288, global_units=1 << 20),
+           tracegen.pattern(53, n_blocks=130, block_threads=128, n_epochs=5, shared_units=4096, global_units=1 << 20),
+           tracegen.pattern(54, n_blocks=3, block_threads=1024, n_epochs=4, shared_units=12288, global_units=1 << 20)]
+    assert sum(t.n_blocks for t in trs if t.block_threads <= 256) >= 2 * 152
+    got = checker().check_batch([simulee.to_device(t) for t in trs])
+    for i, tr in enumerate(trs):
+        assert diff(got[i], oracle.check(tr)) == [], f"trace {i}"
+
+
+def test_batch_signature_tables_direct_and_hashed():
+    """Block signatures: each trace's units in its own stretch of one direct table while all
+    traces' global units together fit 2^28 slots, else a hashed (trace, unit) table (collisions
+    only keep records). The same traces, declared with small and with large global spaces."""
+    from paper_1905_01833_gb300 import simulee
+    from gpu_util import checker
+    base = [tracegen.random_grouped(900 + i, n_events=4000, n_blocks=6) for i in range(3)] + \
+           [tracegen.pattern(61, n_blocks=6, block_threads=64, n_epochs=5, shared_units=4096, global_units=1 << 16)]
+    for gu in (None, (1 << 27) + 5):
+        trs = [t if gu is None else tracegen.Trace(t.events, t.barrier_counts, t.n_blocks, t.block_threads,
+                                                   t.shared_units, gu, t.max_barriers, t.flags) for t in base]
+        got = checker().check_batch([simulee.to_device(t) for t in trs])
+        for i, tr in enumerate(trs):
+            assert diff(got[i], oracle.check(tr)) == [], (gu, i)
+
+
 @pytest.mark.parametrize("path", sorted(PATHS))
 def test_blocks_with_merged_epochs_take_the_sort_path(path):
     """Half the blocks lose a barrier, so two epochs merge into one run of two
