@@ -361,7 +361,8 @@ constexpr int XF_THREADS = 512;
 constexpr int XF_ITEMS = 8;
 constexpr int XF_TILE = XF_THREADS * XF_ITEMS;
 
-template <class KX>
+// OFFS: a direct signature table of several traces (each trace's units after the previous traces')
+template <class KX, bool OFFS>
 __global__ void __launch_bounds__(XF_THREADS, sizeof(KX) == 4 ? 3 : 2)
 k_x_filter(const KX *__restrict__ xk, const uint64_t *__restrict__ xv, KX *yk, uint64_t *yv, const uint32_t *sig,
            const TraceDesc *__restrict__ td, Layout L, Ctl *ctl, uint32_t *hist) {
@@ -386,7 +387,7 @@ k_x_filter(const KX *__restrict__ xk, const uint64_t *__restrict__ xv, KX *yk, u
             const uint64_t i = base + j * XF_THREADS + tid;
             const uint64_t kk = (uint64_t)k[j];
             const uint32_t t = (uint32_t)(L.bug + L.bxr >= 64 ? 0 : (kk >> (L.bug + L.bxr))), unit = (uint32_t)(kk & umask);
-            const uint64_t off = (L.sig_direct && L.T > 1 && i < n && t < L.T) ? td[t].sig_off : 0ull;
+            const uint64_t off = (OFFS && i < n && t < L.T) ? td[t].sig_off : 0ull;
             sv[j] = i < n ? sig[sig_slot(L, off, t, unit)] : 0u;
         }
         uint64_t v[XF_ITEMS];

@@ -211,6 +211,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         const uint32_t *cnts = d.counts;
         const uint32_t nb = d.nb, bt = d.bt, su = d.su, gu = d.gu, maxb = d.maxb;
         const bool pad = nb <= (1u << 20);
+        uint32_t *const sig_t = L.sig_direct ? sig + d.sig_off : sig;   // this trace's stretch of a direct table
 
         // ---- windows: records wbase + j * SH::threads + tid, j = 0, 1. A run's first window
         //      starts at the run's first record; records below vmark are already validated and
@@ -278,7 +279,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                         xk[o] = (KX)(shl(t, L.bug + L.bxr) | e.x);
                         xv[o] = make_payload(act, xo, e.y);
                     }
-                    sig_mark(L, sig, sig_slot(L, d.sig_off, t, e.x), blk, d.block_off + blk);
+                    sig_mark(L, sig_t, sig_slot(L, 0ull, t, e.x), blk, d.block_off + blk);
                 }
                 xpos += tot;
             }

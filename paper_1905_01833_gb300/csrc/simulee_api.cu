@@ -378,6 +378,26 @@ void fill_descs(const simulee_trace *tr, const simulee_outputs *outs, uint8_t *c
     }
 }
 
+// the inter-block filter, instantiated for the key width and for the signature table's indexing
+// (several traces in one direct table read each trace's offset; one trace or a hashed table does not)
+void launch_x_filter(Run &R, const size_t xk[2], const size_t xv[2], uint32_t *sig, const TraceDesc *td,
+                     uint32_t *hist) {
+    const Layout &L = R.L;
+    const int gf = R.grid_for(L.x_cap, XF_TILE, L.wide_x ? 2 : 3);   // resident CTAs per SM
+    const bool offs = L.sig_direct && L.T > 1;
+#define SIM_XF(KX, OFFS)                                                                                            \
+    k_x_filter<KX, OFFS><<<gf, XF_THREADS, 0, R.st>>>(R.at<KX>(xk[0]), R.at<uint64_t>(xv[0]), R.at<KX>(xk[1]),        \
+                                                   R.at<uint64_t>(xv[1]), sig, td, L, R.ctl, hist)
+    if (L.wide_x) {
+        if (offs) SIM_XF(uint64_t, true);
+        else SIM_XF(uint64_t, false);
+    } else {
+        if (offs) SIM_XF(uint32_t, true);
+        else SIM_XF(uint32_t, false);
+    }
+#undef SIM_XF
+}
+
 simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t T, const simulee_outputs *outs,
                            uint8_t *const *reports, Want want, void *ws, size_t ws_bytes, void *stream) {
     if (!ctx || !traces || !outs || !reports || !ws || T == 0) return SIMULEE_EINVAL;
@@ -644,15 +664,7 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
 #undef SIM_PX
             R.launches++;
             if (L.sig_slots) {
-                const int gf = R.grid_for(L.x_cap, XF_TILE, L.wide_x ? 2 : 3);
-                if (L.wide_x)
-                    k_x_filter<uint64_t><<<gf, XF_THREADS, 0, st>>>(R.at<uint64_t>(xk[0]), R.at<uint64_t>(xv[0]),
-                                                                 R.at<uint64_t>(xk[1]), R.at<uint64_t>(xv[1]), sig, td, L,
-                                                                 R.ctl, hist);
-                else
-                    k_x_filter<uint32_t><<<gf, XF_THREADS, 0, st>>>(R.at<uint32_t>(xk[0]), R.at<uint64_t>(xv[0]),
-                                                                 R.at<uint32_t>(xk[1]), R.at<uint64_t>(xv[1]), sig, td, L,
-                                                                 R.ctl, hist);
+                launch_x_filter(R, xk, xv, sig, td, hist);
                 R.launches++;
             }
             if (L.np_x > 0) {
@@ -666,13 +678,7 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
         // inter-block records of units touched by one block only are dropped before sorting;
         // the filter also builds the inter stream's digit histograms
         if (L.sig_slots) {
-            const int gf = R.grid_for(L.x_cap, XF_TILE, L.wide_x ? 2 : 3);   // resident CTAs per SM
-            if (L.wide_x)
-                k_x_filter<uint64_t><<<gf, XF_THREADS, 0, st>>>(R.at<uint64_t>(xk[0]), R.at<uint64_t>(xv[0]), R.at<uint64_t>(xk[1]),
-                                                         R.at<uint64_t>(xv[1]), sig, td, L, R.ctl, hist);
-            else
-                k_x_filter<uint32_t><<<gf, XF_THREADS, 0, st>>>(R.at<uint32_t>(xk[0]), R.at<uint64_t>(xv[0]), R.at<uint32_t>(xk[1]),
-                                                         R.at<uint64_t>(xv[1]), sig, td, L, R.ctl, hist);
+            launch_x_filter(R, xk, xv, sig, td, hist);
             R.launches++;
         }
         if (L.p0_r > 0) {
