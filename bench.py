@@ -752,13 +752,22 @@ def main():
 
     value, ms = job_value(tr.n_events, ms, dist, f"cuda:{local}")
 
-    # end to end through the C ABI: pinned host trace -> device, check, report and lists -> host
+    # end to end through the C ABI: pinned host trace -> device, check, report and lists -> host, every
+    # step. Two device trace buffers: the next step's records go up on a copy stream while this step
+    # is checked (one context per buffer, so that each keeps its own replay graph); the same steps
+    # one after another give e2e_serial.
     h_ev = torch.from_numpy(tr.events.view(np.int32)).pin_memory()
     h_cn = torch.from_numpy(tr.barrier_counts.view(np.int32)).pin_memory()
-    d_ev = torch.empty_like(dt.events)
-    d_cn = torch.empty_like(dt.barrier_counts)
-    etrace = simulee.DeviceTrace(d_ev, d_cn, tr.n_blocks, tr.block_threads, tr.shared_units, tr.global_units,
-                                 tr.max_barriers).c()
+    d_ev = [torch.empty_like(dt.events) for _ in range(2)]
+    d_cn = [torch.empty_like(dt.barrier_counts) for _ in range(2)]
+    etr = [simulee.DeviceTrace(d_ev[q], d_cn[q], tr.n_blocks, tr.block_threads, tr.shared_units, tr.global_units,
+                               tr.max_barriers).c() for q in range(2)]
+    chks = [chk, simulee.Checker(local, path=simulee.PATH_SORT if args.path == "sort" else simulee.PATH_AUTO,
+                                 hash_shape=args.hash_shape,
+                                 graph_replay=simulee.GRAPH_OFF if args.graph_replay == "off" else simulee.GRAPH_AUTO)]
+    copy_s = torch.cuda.Stream(device=f"cuda:{local}")
+    copied = [torch.cuda.Event() for _ in range(2)]
+    freed = [torch.cuda.Event() for _ in range(2)]
     rep_host = torch.zeros(simulee.REPORT_BYTES, dtype=torch.uint8).pin_memory()
     h_races = torch.empty(caps["races_cap"] * 32, dtype=torch.uint8).pin_memory()
     h_red = torch.empty(max(caps["red_cap"], 1) * 8, dtype=torch.uint8).pin_memory()
@@ -766,11 +775,24 @@ def main():
     h_grid = torch.empty(max(caps["grid_cap"], 1) * 4, dtype=torch.uint8).pin_memory()
     d2h = 0
 
-    def e2e_step():
+    def issue_copy(i):
+        q = i % 2
+        if i >= 2:
+            copy_s.wait_event(freed[q])   # the check of step i - 2 has read this buffer
+        with torch.cuda.stream(copy_s):
+            d_ev[q].copy_(h_ev, non_blocking=True)
+            d_cn[q].copy_(h_cn, non_blocking=True)
+        copied[q].record(copy_s)
+
+    def finish_step(i):
         nonlocal d2h
-        d_ev.copy_(h_ev, non_blocking=True)
-        d_cn.copy_(h_cn, non_blocking=True)
-        step(etrace, rep_host.data_ptr())
+        q = i % 2
+        stream.wait_event(copied[q])
+        s_ = L.simulee_check(chks[q].h, ctypes.byref(etr[q]), ctypes.byref(outs), ctypes.c_void_p(rep_host.data_ptr()),
+                             ctypes.c_void_p(ws.data_ptr()), ws.numel(), sp)
+        if s_ != 0:
+            raise RuntimeError(f"simulee_check failed: {simulee.status_str(s_)}")
+        freed[q].record(stream)
         stream.synchronize()
         r = simulee.Report.from_buffer_copy(rep_host.numpy().tobytes())
         nr, nd, nred, ng = (min(r.n_races, caps["races_cap"]), min(r.n_divergence, caps["div_cap"]),
@@ -781,17 +803,32 @@ def main():
         h_grid[: ng * 4].copy_(bufs["grid"][: ng * 4], non_blocking=True)
         stream.synchronize()
         d2h = simulee.REPORT_BYTES + nr * 32 + nd * 16 + nred * 8 + ng * 4
+        if r.status != 0 or r.n_races != rep0.n_races:
+            raise RuntimeError("end-to-end check result differs from the resident-trace check")
 
-    for _ in range(3):
-        e2e_step()
+    def run_e2e(k, overlap):
+        issue_copy(0)
+        for i in range(k):
+            if overlap and i + 1 < k:
+                issue_copy(i + 1)
+            finish_step(i)
+            if not overlap and i + 1 < k:
+                issue_copy(i + 1)
+
+    run_e2e(4, True)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        e2e_step()
+    run_e2e(args.e2e_steps, True)
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     e2e_value, _ = job_value(tr.n_events, e2e_s * 1e3, dist, f"cuda:{local}")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run_e2e(max(2, args.e2e_steps // 2), False)
+    e2e_serial_s = (time.perf_counter() - t0) / max(2, args.e2e_steps // 2)
+    e2e_serial, _ = job_value(tr.n_events, e2e_serial_s * 1e3, dist, f"cuda:{local}")
+    chks[1].close()
     h2d = tr.events.nbytes + tr.barrier_counts.nbytes
 
     # roofline of the dominant stage
@@ -823,7 +860,10 @@ def main():
                    "n_events": tr.n_events, "parallelism": f"replicas{world}",
                    "l2": "inputs larger than L2 (1 GB trace, 129 MB L2); no flush", "path": args.path},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "serial_value": e2e_serial,
+                "overlap": "two device trace buffers: the next step's host-to-device copy runs on a copy "
+                           "stream while the current step is checked; serial_value = copy, check and "
+                           "read-back one after another"},
         "gpu_launches": launches * args.steps,
         "launch": "repeated identical calls replayed by the library as one CUDA graph (graph_replay auto); "
                   "'direct' times the same steps with every kernel launched by the call",
