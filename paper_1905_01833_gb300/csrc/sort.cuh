@@ -67,6 +67,7 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
 
     if (must_stop(ctl)) return;
     const uint64_t n = min((uint64_t)*n_ptr, n_max);
+    if (n == 0) return;   // an empty stream (e.g. nothing left the hash path): no tile, no look-back
     // tile size: 4096 elements, or, when the grid has more CTAs than 4096-element tiles, the
     // smallest multiple of the CTA's threads that gives every CTA at most one tile (the count is
     // known on the device only; every CTA computes the same size)
