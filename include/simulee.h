@@ -200,7 +200,10 @@ typedef enum {
 
 typedef struct simulee_ctx simulee_ctx;
 
-/* Create a context on `device` (host object; no device allocation). opt may be NULL. */
+/* Create a context on `device` (host object; no device allocation). opt may be NULL. A context
+   keeps host state between calls (which kernels are configured, the replay graph of a repeated
+   call), so calls on one context must not overlap from several host threads; use one context
+   per thread. */
 simulee_status simulee_create(simulee_ctx **ctx, int device, const simulee_options *opt);
 
 /* Destroy a context. Pending work on streams is not waited for. */
