@@ -277,7 +277,7 @@ struct Run {
     // holding the result.
     template <class K>
     int sort(size_t koff[2], size_t voff[2], const uint32_t *n_ptr, uint64_t n_max, uint32_t np, uint32_t p0,
-             int start = 0) {
+             int start = 0, uint32_t tile_cap = 0) {
         const int grid = sort_grid(n_max);
         for (uint32_t p = 0; p < np; p++) {
             const int src = (start + (int)p) & 1, dst = src ^ 1;
@@ -286,7 +286,7 @@ struct Run {
             k_onesweep<K><<<grid, OS_THREADS, onesweep_smem<K>(), st>>>(
                 at<K>(koff[src]), at<uint64_t>(voff[src]), at<K>(koff[dst]), at<uint64_t>(voff[dst]), n_ptr, n_max,
                 RADIX_BITS * p, at<uint32_t>(L.off_dbase) + (size_t)(p0 + p) * RADIX,
-                at<unsigned long long>(L.off_status), p0 + p + 1, &ctl->tiles[p0 + p], ctl, wait_ns, wh);
+                at<unsigned long long>(L.off_status), p0 + p + 1, &ctl->tiles[p0 + p], ctl, wait_ns, wh, tile_cap);
             launches++;
         }
         return (start + (int)np) & 1;
@@ -722,7 +722,8 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
                                                 R.at<uint32_t>(L.off_dbase) + (size_t)L.p0_r * RADIX, R.ctl);
         R.launches += 2;
         size_t rk[2] = {L.off_rk[0], L.off_rk[1]}, rv[2] = {L.off_rv[0], L.off_rv[1]};
-        const int br = R.sort<uint64_t>(rk, rv, &R.ctl->n_rf, L.race_cap, L.np_r, L.p0_r, 1);
+        // race records are few next to the record streams: at most 128 tiles keeps their look-back short
+        const int br = R.sort<uint64_t>(rk, rv, &R.ctl->n_rf, L.race_cap, L.np_r, L.p0_r, 1, 128u);
         const int gw = R.grid_for(L.race_cap, 256, 8);
         if (T > 1) {   // one trace: its races start at 0 (the per-trace state is zeroed)
             k_race_starts<<<gw, 256, 0, st>>>(R.at<uint64_t>(rk[br]), L, R.ctl, ts);
@@ -991,7 +992,7 @@ simulee_status run_fitness(simulee_ctx *ctx, const simulee_trace *traces, uint32
             k_onesweep<K><<<gs, OS_THREADS, onesweep_smem<K>(), st>>>(                                             \
                 bufs[p & 1], nullptr, bufs[(p & 1) ^ 1], nullptr, &ctl->n_q, L.n, RADIX_BITS * p,                  \
                 dbase + (size_t)p * RADIX, reinterpret_cast<unsigned long long *>(w + P.off_status), p + 1,        \
-                &ctl->tiles[p], ctl, wait_ns, 0u);                                                                 \
+                &ctl->tiles[p], ctl, wait_ns, 0u, 0u);                                                             \
             launches++;                                                                                            \
         }                                                                                                          \
         k_fit_count<K><<<grid_for(L.n, 256, 8), 256, 0, st>>>(bufs[P.fk.np & 1], &ctl->n_q, P.fk, T, acc, ctl);    \

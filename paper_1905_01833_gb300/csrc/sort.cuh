@@ -21,6 +21,7 @@ constexpr int OS_THREADS = 256;
 constexpr int OS_WARPS = OS_THREADS / 32;
 constexpr int OS_ITEMS = 16;
 constexpr int OS_TILE = OS_THREADS * OS_ITEMS;  // 4096
+constexpr int OS_LOOKBACK = 4;                  // predecessor tiles read per look-back step
 
 constexpr uint64_t ST_AGG = 1ull, ST_INC = 2ull;
 __device__ __forceinline__ uint64_t st_make(uint32_t tag, uint64_t flag, uint64_t count) {
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(OS_THREADS, 3)
 k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__restrict__ kout,
            uint64_t *__restrict__ vout, const uint32_t *n_ptr, uint64_t n_max, uint32_t shift,
            const uint32_t *__restrict__ dbase, unsigned long long *status, uint32_t tag, uint32_t *tile_ctr,
-           Ctl *ctl, uint64_t wait_ns, uint32_t withhold) {
+           Ctl *ctl, uint64_t wait_ns, uint32_t withhold, uint32_t tile_cap) {
     extern __shared__ __align__(16) uint8_t smem[];
     K *skeys = reinterpret_cast<K *>(smem);
     uint64_t *svals = reinterpret_cast<uint64_t *>(smem + (size_t)OS_TILE * sizeof(K));
@@ -68,12 +69,14 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
     if (must_stop(ctl)) return;
     const uint64_t n = min((uint64_t)*n_ptr, n_max);
     if (n == 0) return;   // an empty stream (e.g. nothing left the hash path): no tile, no look-back
-    // tile size: 4096 elements, or, when the grid has more CTAs than 4096-element tiles, the
-    // smallest multiple of the CTA's threads that gives every CTA at most one tile (the count is
-    // known on the device only; every CTA computes the same size)
+    // tile size: 4096 elements, or, when there would be fewer tiles than mt (the grid's CTAs, at most
+    // tile_cap when given), the smallest multiple of the CTA's threads that makes at most mt tiles
+    // (the count is known on the device only; every CTA computes the same size). More, smaller tiles
+    // mean less work per tile but longer look-back chains.
     uint32_t ipt = OS_ITEMS;
-    if (n < (uint64_t)gridDim.x * OS_TILE) {
-        const uint64_t per = (uint64_t)gridDim.x * OS_THREADS;
+    const uint64_t mt = tile_cap ? min((uint64_t)gridDim.x, (uint64_t)tile_cap) : (uint64_t)gridDim.x;
+    if (n < mt * OS_TILE) {
+        const uint64_t per = mt * OS_THREADS;
         ipt = n > per ? (uint32_t)((n + per - 1) / per) : 1u;
     }
     const uint32_t tile_n = ipt * OS_THREADS;
@@ -143,20 +146,34 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
             const uint64_t t0 = globaltimer_ns();
             uint32_t spins = 0;
             while (t >= 0) {
-                const uint64_t s = vst[(uint64_t)t * RADIX + tid];
-                if (st_tag(s) != tag || st_flag(s) == 0) {
-                    if ((++spins & 63) == 0) {
-                        if (*(volatile unsigned int *)&ctl->timeout) break;
-                        if (globaltimer_ns() - t0 > wait_ns) {
-                            atomicExch(&ctl->timeout, 1u);
-                            break;
-                        }
+                // four predecessors per step, their loads in flight together; consume them in order up
+                // to the first inclusive count, or up to a word not yet published (then read again)
+                uint64_t s4[OS_LOOKBACK];
+#pragma unroll
+                for (int q = 0; q < OS_LOOKBACK; q++) s4[q] = t - q >= 0 ? vst[(uint64_t)(t - q) * RADIX + tid] : 0ull;
+                int used = 0;
+                bool inc = false, blocked = false;
+#pragma unroll
+                for (int q = 0; q < OS_LOOKBACK; q++) {
+                    if (inc || blocked || t - q < 0) continue;
+                    const uint64_t s = s4[q];
+                    if (st_tag(s) != tag || st_flag(s) == 0) {
+                        blocked = true;
+                        continue;
                     }
-                    continue;
+                    excl += st_count(s);
+                    used = q + 1;
+                    if (st_flag(s) == ST_INC) inc = true;
                 }
-                excl += st_count(s);
-                if (st_flag(s) == ST_INC) break;
-                --t;
+                if (inc) break;
+                t -= used;
+                if (blocked && (++spins & 63) == 0) {
+                    if (*(volatile unsigned int *)&ctl->timeout) break;
+                    if (globaltimer_ns() - t0 > wait_ns) {
+                        atomicExch(&ctl->timeout, 1u);
+                        break;
+                    }
+                }
             }
             if (!withheld) vst[tile * RADIX + tid] = st_make(tag, ST_INC, excl + run);
         }
