@@ -367,12 +367,15 @@ __global__ void __launch_bounds__(XF_THREADS, sizeof(KX) == 4 ? 3 : 2)
 k_x_filter(const KX *__restrict__ xk, const uint64_t *__restrict__ xv, KX *yk, uint64_t *yv, const uint32_t *sig,
            const TraceDesc *__restrict__ td, Layout L, Ctl *ctl, uint32_t *hist) {
     __shared__ uint32_t sh[8 * RADIX];
-    __shared__ uint32_t wtot[XF_THREADS / 32];
+    // warp counts, then offsets, of a tile; two sets used in turn, so that a tile's set is only
+    // rewritten two tiles later, after every warp has passed the next tile's first barrier
+    __shared__ uint32_t wtot[2][XF_THREADS / 32];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint32_t lt = lanemask_lt();
     for (int i = tid; i < 8 * RADIX; i += XF_THREADS) sh[i] = 0;
     __syncthreads();
     const uint64_t n = min((uint64_t)*(volatile unsigned int *)&ctl->n_x, L.x_cap);
+    uint32_t par = 0;
     const uint64_t umask = (L.bug >= 64) ? ~0ull : ((1ull << L.bug) - 1);
     for (uint64_t base = (uint64_t)blockIdx.x * XF_TILE; base < n; base += (uint64_t)gridDim.x * XF_TILE) {
         KX k[XF_ITEMS];
@@ -408,10 +411,10 @@ k_x_filter(const KX *__restrict__ xk, const uint64_t *__restrict__ xv, KX *yk, u
             bal[j] = __ballot_sync(0xFFFFFFFFu, (keep >> j) & 1u);
             wcount += __popc(bal[j]);
         }
-        if (lane == 0) wtot[w] = wcount;
+        if (lane == 0) wtot[par][w] = wcount;
         __syncthreads();
         if (w == 0) {
-            const uint32_t x = lane < XF_THREADS / 32 ? wtot[lane] : 0u;
+            const uint32_t x = lane < XF_THREADS / 32 ? wtot[par][lane] : 0u;
             uint32_t incl = x;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -422,11 +425,11 @@ k_x_filter(const KX *__restrict__ xk, const uint64_t *__restrict__ xv, KX *yk, u
             uint32_t b0 = 0;
             if (lane == 0 && total) b0 = atomicAdd(&ctl->n_xf, total);
             b0 = __shfl_sync(0xFFFFFFFFu, b0, 0);
-            if (lane < XF_THREADS / 32) wtot[lane] = b0 + incl - x;
+            if (lane < XF_THREADS / 32) wtot[par][lane] = b0 + incl - x;
         }
         __syncthreads();
         if (keep) {
-            uint32_t o = wtot[w];
+            uint32_t o = wtot[par][w];
 #pragma unroll
             for (int j = 0; j < XF_ITEMS; j++) {
                 if ((keep >> j) & 1u) {
@@ -439,7 +442,7 @@ k_x_filter(const KX *__restrict__ xk, const uint64_t *__restrict__ xv, KX *yk, u
                 o += __popc(bal[j]);
             }
         }
-        __syncthreads();   // wtot is rewritten by the next tile
+        par ^= 1u;
     }
     __syncthreads();
     for (int i = tid; i < (int)(L.np_x * RADIX); i += XF_THREADS)
