@@ -102,3 +102,60 @@ def test_batch_calls_replayed():
         for i, t in enumerate(src):
             assert diff(got[i], oracle.check(t)) == [], (rnd, i)
     chk.close()
+
+
+def test_single_output_entry_points_replayed():
+    """simulee_check_races / _divergence / _redundant_barriers called again and again on fixed buffers
+    (each call's arguments equal the previous call's, so the second captures and the rest replay),
+    with new trace contents before every call."""
+    import torch
+    from paper_1905_01833_gb300 import simulee
+    L = simulee.lib()
+    chk = simulee.Checker(0)
+    a = tracegen.pattern(23, n_blocks=12, block_threads=128, n_epochs=10, shared_units=4096, global_units=1 << 18)
+    traces = [a, _variant(a, 3), _variant(a, 4)]
+    wants = [oracle.check(t) for t in traces]
+    assert len({w["races"].tobytes() for w in wants}) == 3 and len({w["redundant"].tobytes() for w in wants}) == 3
+    dt = simulee.to_device(a)
+    t = dt.c()
+    ws = torch.empty(chk.workspace_size(dt), dtype=torch.uint8, device="cuda:0")
+    rep = torch.zeros(simulee.REPORT_BYTES, dtype=torch.uint8, device="cuda:0")
+    rcap, dcap, bcap, gcap = 2 * a.n_events + 2, a.n_blocks, a.n_blocks * max(a.max_barriers, 1), max(a.max_barriers, 1)
+    races = torch.empty(rcap * 32, dtype=torch.uint8, device="cuda:0")
+    divs = torch.empty(dcap * 16, dtype=torch.uint8, device="cuda:0")
+    bars = torch.empty(bcap * 8, dtype=torch.uint8, device="cuda:0")
+    grid = torch.empty(gcap * 4, dtype=torch.uint8, device="cuda:0")
+    sp = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    wsp, repp = ctypes.c_void_p(ws.data_ptr()), ctypes.c_void_p(rep.data_ptr())
+
+    def report():
+        torch.cuda.synchronize()
+        r = simulee.Report.from_buffer_copy(rep.cpu().numpy().tobytes())
+        assert r.status == 0
+        return r
+
+    def take(buf, n, dtype):
+        return np.frombuffer(buf[: n * dtype.itemsize].cpu().numpy().tobytes(), dtype=dtype)
+
+    for name in ("races", "divergence", "redundant"):
+        for i in [0, 1, 2, 0, 1, 2]:
+            dt.events.copy_(torch.from_numpy(traces[i].events.view(np.int32).reshape(-1, 4)))
+            w = wants[i]
+            if name == "races":
+                assert L.simulee_check_races(chk.h, ctypes.byref(t), ctypes.c_void_p(races.data_ptr()), rcap, repp,
+                                             wsp, ws.numel(), sp) == simulee.OK
+                r = report()
+                assert take(races, r.n_races, simulee.RACE_DTYPE).tobytes() == w["races"].tobytes(), (name, i)
+            elif name == "divergence":
+                assert L.simulee_check_divergence(chk.h, ctypes.byref(t), ctypes.c_void_p(divs.data_ptr()), dcap,
+                                                  repp, wsp, ws.numel(), sp) == simulee.OK
+                r = report()
+                assert take(divs, r.n_divergence, simulee.DIV_DTYPE).tobytes() == w["divergence"].tobytes(), (name, i)
+            else:
+                assert L.simulee_check_redundant_barriers(chk.h, ctypes.byref(t), ctypes.c_void_p(bars.data_ptr()),
+                                                          bcap, ctypes.c_void_p(grid.data_ptr()), gcap, repp, wsp,
+                                                          ws.numel(), sp) == simulee.OK
+                r = report()
+                assert take(bars, r.n_redundant, simulee.BAR_DTYPE).tobytes() == w["redundant"].tobytes(), (name, i)
+                assert take(grid, r.n_grid_redundant, np.dtype("<u4")).tobytes() == w["grid_redundant"].tobytes()
+    chk.close()
