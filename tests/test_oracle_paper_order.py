@@ -132,6 +132,23 @@ def test_oracle_equals_all_pairs(chunk):
         assert as_tuples(oracle.check(tr)) == brute(tr), seed
 
 
+def test_oracle_equals_all_pairs_hypothesis():
+    """Random shapes, sizes, spaces and action mixes (more epochs than units, so units skip epochs)."""
+    hyp = pytest.importorskip("hypothesis")
+    st = hyp.strategies
+
+    @hyp.settings(max_examples=150, deadline=None, derandomize=True)
+    @hyp.given(seed=st.integers(0, 2**31), n=st.integers(0, 60), nb=st.integers(1, 3), bt=st.integers(1, 6),
+               me=st.integers(1, 6), units=st.integers(1, 5), pg=st.floats(0, 1), pa=st.floats(0, 0.5),
+               unsorted=st.booleans())
+    def prop(seed, n, nb, bt, me, units, pg, pa, unsorted):
+        tr = tracegen.random_tiny(seed, n, nb, bt, me, units, p_global=pg, p_atomic=pa, unsorted=unsorted)
+        tr.flags |= tracegen.PAPER_ORDER
+        assert as_tuples(oracle.check(tr)) == brute(tr)
+
+    prop()
+
+
 def test_against_epoch_grouping():
     """Intra-block races are the same records; the variant only adds needed barriers (a unit's
     next non-empty epoch after k is k + 1 whenever epoch k + 1 touches it)."""
