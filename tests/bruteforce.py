@@ -6,6 +6,11 @@ looks at every pair of records and applies the definitions directly
 global memory, the one-barrier-at-a-time redundancy test of Algorithm 5 and the
 barrier-count divergence rule of Algorithm 4).
 
+With flag WARP_AWARE (a statement word per record) it applies Theorem 1's
+warp clauses: two accesses of one warp (same block, same tid / 32) race only
+when both are plain writes with the same statement id, or when either carries
+the diverged bit.
+
 With flag PAPER_ORDER it replays Algorithm 3's visit-order counters instead of
 using epochs: per (space, block, unit) a counter starts at 0, an access takes
 the counter's value, and the barrier at the end of an epoch bumps the counter
@@ -21,12 +26,16 @@ import numpy as np
 R, W, A = 0, 1, 2
 
 
-def _decode(ev):
+DIVERGED = 0x80000000
+
+
+def _decode(ev, stmt=None):
     out = []
     for i, w in enumerate(np.asarray(ev, dtype=np.uint64).reshape(-1, 4)):
         w = [int(x) for x in w]
         out.append(dict(i=i, unit=w[0], vo=w[1], block=w[2], tid=w[3] & 0xFFFF, epoch=(w[3] >> 16) & 0xFFF,
-                        act=(w[3] >> 28) & 3, space=(w[3] >> 30) & 1, reserved=w[3] >> 31))
+                        act=(w[3] >> 28) & 3, space=(w[3] >> 30) & 1, reserved=w[3] >> 31,
+                        stmt=None if stmt is None else int(stmt[i])))
     return out
 
 
@@ -38,13 +47,20 @@ def _conflict(p, q, idp, idq):
         return False
     if p["act"] == A and q["act"] == A:
         return False
+    if p["stmt"] is not None and p["block"] == q["block"] and p["tid"] // 32 == q["tid"] // 32:
+        same_statement_writes = (p["act"] == W and q["act"] == W and
+                                 (p["stmt"] & ~DIVERGED) == (q["stmt"] & ~DIVERGED))
+        diverged = bool(p["stmt"] & DIVERGED) or bool(q["stmt"] & DIVERGED)
+        if not (same_statement_writes or diverged):
+            return False
     return True
 
 
 def brute(trace) -> dict:
     nb, bt = trace.n_blocks, trace.block_threads
     counts = [int(c) for c in trace.barrier_counts]
-    recs = _decode(trace.events)
+    warp_aware = bool(getattr(trace, "flags", 0) & 2)
+    recs = _decode(trace.events, getattr(trace, "stmt", None) if warp_aware else None)
     unsorted = bool(getattr(trace, "flags", 0) & 1)
     res = dict(status=0, bad_kind=0, bad_index=0, races=[], divergence=[], redundant=[], grid_redundant=[])
     for t, c in enumerate(counts):

@@ -167,3 +167,13 @@ def test_warp_mutant_is_caught(name, src, tmp_path):
     lib = oracle.load(so)
     assert _pins_fail(lib) is not None, f"mutant {name} passed every pin"
     os.remove(so)
+
+
+@pytest.mark.parametrize("chunk", range(3))
+def test_oracle_equals_all_pairs_with_statement_words(chunk):
+    """The all-pairs brute force with Theorem 1's warp clauses, written separately, on random traces
+    with statement words (tiny blocks: every same-block pair shares a warp)."""
+    from bruteforce import as_tuples, brute
+    for seed in range(chunk * 80, chunk * 80 + 80):
+        tr = tracegen.with_statements(tracegen.random_tiny(seed), seed=seed, diverge_p=0.3)
+        assert as_tuples(oracle.check(tr)) == brute(tr), seed
