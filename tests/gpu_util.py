@@ -1,4 +1,4 @@
-"""Helpers shared by the GPU tests: run the CUDA path, compare with the oracle, sample big traces."""
+"""Helpers shared by the GPU tests: run the CUDA path, compare with the oracle, digest big results."""
 from __future__ import annotations
 
 import numpy as np
@@ -56,47 +56,51 @@ def sub_trace(tr, mask: np.ndarray):
                           tr.shared_units, tr.global_units, tr.max_barriers, tr.flags)
 
 
-def sampled_check(tr, got: dict, n_blocks: int = 16, n_units: int = 1500, seed: int = 0) -> list[str]:
-    """Check a full-size GPU result on samples the oracle computes one by one.
+def result_digest(res: dict, races_cap: int) -> str:
+    """Digest of a result: status, counts and list bytes, the race list up to races_cap (what an output of
+    that capacity holds; a truncated GPU list compares as its prefix plus the true count)."""
+    import hashlib
+    nr = int(res["n_races"]) if "n_races" in res else len(res["races"])
+    status = int(res["status"])
+    if status == 4 and nr > races_cap:
+        status = 0
+    h = hashlib.sha256()
+    h.update(np.array([status, int(res["bad_kind"]), int(res["bad_index"]), nr, len(res["divergence"]),
+                       len(res["redundant"]), len(res["grid_redundant"])], dtype=np.int64).tobytes())
+    h.update(np.ascontiguousarray(res["races"][:races_cap]).tobytes())
+    for k in ("divergence", "redundant", "grid_redundant"):
+        h.update(np.ascontiguousarray(res[k]).tobytes())
+    return h.hexdigest()
 
-    Intra-block races and redundant barriers of a block depend only on that
-    block's records; inter-block races of a global unit only on the records of
-    that unit; the divergence list only on the barrier counts."""
-    rng = np.random.default_rng(seed)
-    bad = []
-    ev = tr.events
-    blocks = rng.choice(tr.n_blocks, size=min(n_blocks, tr.n_blocks), replace=False)
-    bsel = np.isin(ev[:, 2], blocks)
-    want = oracle.check(sub_trace(tr, bsel))
-    if want["status"] != 0:
-        return [f"oracle status {want['status']}"]
-    g = got["races"]
-    gi = g[(g["scope"] == 0) & np.isin(g["block"], blocks)]
-    wi = want["races"][want["races"]["scope"] == 0]
-    if not (len(gi) == len(wi) and all(np.array_equal(gi[f], wi[f]) for f in g.dtype.names)):
-        bad.append(f"intra races of sampled blocks differ ({len(gi)} vs {len(wi)})")
-    gr = got["redundant"][np.isin(got["redundant"]["block"], blocks)]
-    wr = want["redundant"][np.isin(want["redundant"]["block"], blocks)]
-    if not np.array_equal(gr, wr):
-        bad.append(f"redundant barriers of sampled blocks differ ({len(gr)} vs {len(wr)})")
-    # divergence depends on the counts alone
-    empty = tracegen.Trace(np.zeros((0, 4), np.uint32), tr.barrier_counts, tr.n_blocks, tr.block_threads,
-                           tr.shared_units, tr.global_units, tr.max_barriers)
-    if not np.array_equal(got["divergence"], oracle.check(empty)["divergence"]):
-        bad.append("divergence list differs")
-    # inter-block races on sampled global units (half of them units that do race)
-    glob = ((ev[:, 3] >> 30) & 1) == 1
-    if glob.any():
-        inter = g[g["scope"] == 1]
-        racing = inter["unit"]
-        gunits = np.unique(ev[glob, 0])
-        pick = rng.choice(gunits, size=min(n_units, len(gunits)), replace=False)
-        if len(racing):
-            pick = np.union1d(pick, rng.choice(racing, size=min(n_units, len(racing)), replace=False))
-        usel = glob & np.isin(ev[:, 0], pick)
-        w2 = oracle.check(sub_trace(tr, usel))
-        wx = w2["races"][w2["races"]["scope"] == 1]
-        gx = inter[np.isin(inter["unit"], pick)]
-        if not (len(gx) == len(wx) and all(np.array_equal(gx[f], wx[f]) for f in g.dtype.names)):
-            bad.append(f"inter races of sampled units differ ({len(gx)} vs {len(wx)})")
-    return bad
+
+def make_trace(recipe):
+    """A trace from a recipe tuple: ("c2",), ("c4",), ("c3", i, n, block_threads, epochs, seed) or
+    ("c5", i, size)."""
+    kind = recipe[0]
+    if kind == "c2":
+        return tracegen.c2()
+    if kind == "c4":
+        return tracegen.c4()
+    if kind == "c3":
+        _, i, n, bs, ep, seed = recipe
+        return tracegen.c3_trace(i, n, bs, ep, seed=seed)
+    if kind == "c5":
+        return tracegen.c5_member(recipe[1], recipe[2])
+    raise ValueError(recipe)
+
+
+def oracle_digest(job):
+    """(key, records, digest) of the oracle's result on a recipe's trace; runs in a spawned process."""
+    key, recipe, races_cap = job
+    tr = make_trace(recipe)
+    res = oracle.check(tr)
+    return key, tr.n_events, result_digest(res, races_cap)
+
+
+def oracle_digests_async(jobs, processes=None):
+    """Start the oracle on many recipes in spawned processes (largest first); returns (pool, async result)."""
+    import multiprocessing as mp
+    import os
+    procs = processes or len(os.sched_getaffinity(0))
+    pool = mp.get_context("spawn").Pool(min(procs, max(1, len(jobs))))
+    return pool, pool.map_async(oracle_digest, jobs, chunksize=1)

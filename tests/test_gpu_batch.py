@@ -25,7 +25,7 @@ def test_batch_of_tiny_random_traces_equals_oracle():
 
 def test_batch_mixed_shapes_equals_single_checks():
     from gpu_util import gpu_check
-    sizes, bss, eps = tracegen.c3_sizes(seed=5, n_traces=24, median=4e3, lo=300, hi=3e4)
+    sizes, bss, eps = tracegen.c3_sizes(seed=5, n_traces=24, median=4e3, sigma=0.87, lo=300, hi=3e4)
     trs = [tracegen.c3_trace(i, int(n), int(b), int(e), seed=5) for i, (n, b, e) in enumerate(zip(sizes, bss, eps))]
     trs.append(tracegen.c1())
     trs.append(tracegen.barrier(seed=2, n_blocks=6, block_threads=64, n_epochs=12, shared_units=512, diverge_p=0.3))

@@ -190,9 +190,37 @@ def c4(seed: int = DEFAULT_SEED, n_blocks: int = 1024) -> Trace:
     return barrier(seed, n_blocks, 1024, 64, 8192, 4)
 
 
-def c3_sizes(seed: int = DEFAULT_SEED, n_traces: int = 4096, median: float = 1e5, sigma: float = 0.87,
-             lo: float = 1e3, hi: float = 1e7):
-    """Per-trace (target records, block size, epochs) for the batched workload."""
+C3_RECORDS = 600_000_000   # records of the batched workload, all traces together
+
+
+def c3_sigma(seed: int = DEFAULT_SEED, n_traces: int = 4096, median: float = 1e5, lo: float = 1e3,
+             hi: float = 1e7, total: int = C3_RECORDS) -> float:
+    """The lognormal sigma whose seeded, clipped size draws sum to `total` records (bisection).
+
+    The draws are exp(ln(median) + sigma * z_i) with the seeded standard normals z_i of c3_sizes,
+    clipped to [lo, hi] and truncated to integers; their sum increases with sigma over the bracket."""
+    z = np.random.default_rng(seed).standard_normal(n_traces)
+
+    def tot(s):
+        return int(np.clip(np.exp(np.log(median) + s * z), lo, hi).astype(np.int64).sum())
+    a, b = 0.3, 3.0
+    if not (tot(a) <= total <= tot(b)):
+        raise ValueError("c3_sigma: total out of reach")
+    for _ in range(64):
+        m = 0.5 * (a + b)
+        if tot(m) < total:
+            a = m
+        else:
+            b = m
+    return b
+
+
+def c3_sizes(seed: int = DEFAULT_SEED, n_traces: int = 4096, median: float = 1e5, sigma: float | None = None,
+             lo: float = 1e3, hi: float = 1e7, total: int = C3_RECORDS):
+    """Per-trace (records, block size, epochs) for the batched workload. Without an explicit sigma,
+    sigma is fitted so that the sizes sum to `total` (c3_sigma)."""
+    if sigma is None:
+        sigma = c3_sigma(seed, n_traces, median, lo, hi, total)
     rng = np.random.default_rng(seed)
     n = np.clip(np.exp(np.log(median) + sigma * rng.standard_normal(n_traces)), lo, hi)
     bs = rng.choice(np.array([64, 128, 256, 1024]), size=n_traces)
@@ -202,17 +230,46 @@ def c3_sizes(seed: int = DEFAULT_SEED, n_traces: int = 4096, median: float = 1e5
 
 def c3_trace(i: int, target: int, block_threads: int, n_epochs: int, seed: int = DEFAULT_SEED) -> Trace:
     """One trace of the batched workload: the grid pattern with enough blocks for
-    `target` records. When even one block holds more records than the target (a
-    1024-thread block over 64 epochs holds ~4.5e5), the trace is cut to its first
-    `target` records in schedule order; barrier counts stay those of the full
-    run, so the cut trace is a valid trace whose later epochs are empty."""
+    `target` records, cut to its first `target` records in schedule order. The
+    block count starts from 8 records per thread per epoch and grows (from the
+    records per block of the last attempt) until the pattern holds the target.
+    Barrier counts stay those of the full run, so the cut trace is a valid trace
+    whose last block ends early (its later epochs are empty)."""
     nb = max(1, int(np.ceil(target / (block_threads * n_epochs * 8))))
-    gu = 4096 + 2 * 1024 * nb
-    gu = 1 << int(np.ceil(np.log2(gu)))
-    tr = pattern(seed + 7919 * (i + 1), nb, block_threads, n_epochs, 12288, gu)
+    for _ in range(8):
+        gu = 1 << int(np.ceil(np.log2(4096 + 2 * 1024 * nb)))
+        tr = pattern(seed + 7919 * (i + 1), nb, block_threads, n_epochs, 12288, gu)
+        if tr.n_events >= target:
+            break
+        nb = max(nb + 1, int(np.ceil(1.05 * target * nb / max(tr.n_events, 1))))
     if tr.n_events > target:
         tr.events = np.ascontiguousarray(tr.events[:target])
     tr.meta.update(kind="batch_member", target=int(target))
+    return tr
+
+
+C5_SIZES = (1e4, 1e8)   # record range of the served workload's jobs (log-uniform)
+
+
+def c5_pool_sizes(n_pool: int = 24) -> np.ndarray:
+    """Sizes of the served workload's pool of traces: log-spaced over C5_SIZES."""
+    return np.exp(np.linspace(np.log(C5_SIZES[0]), np.log(C5_SIZES[1]), n_pool))
+
+
+def c5_member(i: int, size: float) -> Trace:
+    """Pool trace i of the served workload: even i the grid family (256-thread blocks, 32 epochs,
+    about 6e4 records per block), odd i the barrier family (1024-thread blocks, 64 epochs, 4 accesses
+    per thread per epoch, 262144 records per block); cut to `size` records in schedule order."""
+    if i % 2 == 0:
+        nb = max(1, int(round(size / 59600)))
+        tr = pattern(100 + i, n_blocks=nb, block_threads=256, n_epochs=32, shared_units=12288,
+                     global_units=1 << max(20, int(np.ceil(np.log2(4096 + 2 * 1024 * nb)))))
+    else:
+        nb = max(1, int(round(size / 262144)))
+        tr = barrier(100 + i, n_blocks=nb, block_threads=1024, n_epochs=64, shared_units=8192)
+    if tr.n_events > size:
+        tr.events = np.ascontiguousarray(tr.events[:int(size)])
+    tr.meta.update(kind="serve_member", index=i)
     return tr
 
 
