@@ -40,7 +40,8 @@ typedef enum {
     SIMULEE_OK = 0,
     SIMULEE_EINVAL = 1,      /* bad argument or dimensions out of range (host) */
     SIMULEE_EBADTRACE = 2,   /* a record or barrier count is invalid (report) */
-    SIMULEE_ENOMEM = 3,      /* workspace smaller than simulee_workspace_size (host) */
+    SIMULEE_ENOMEM = 3,      /* workspace too small: below the compact size (host), or a workspace
+                                below simulee_workspace_size ran out of stream capacity (report) */
     SIMULEE_ETRUNC = 4,      /* an output held more records than its cap (report) */
     SIMULEE_ETIMEOUT = 5,    /* a bounded device-side wait gave up; outputs unreliable (report) */
     SIMULEE_ECUDA = 6        /* a CUDA call failed (host) */
@@ -151,8 +152,12 @@ typedef struct {
  * Per-call report (48 bytes), written by the device. status is OK,
  * EBADTRACE (bad_kind 0: record bad_index; bad_kind 1: barrier_counts entry
  * bad_index; counts are checked before records; outputs untouched and counts
- * 0), ETIMEOUT, or ETRUNC (some count exceeds its cap; the first cap entries
- * in canonical order were written). n_* are the true counts.
+ * 0), ETIMEOUT, ENOMEM (the call's workspace was smaller than
+ * simulee_workspace_size and more records needed the radix-sort streams, or
+ * more races were staged, than its capacities held; outputs unreliable: call
+ * again with simulee_workspace_size bytes), or ETRUNC (some count exceeds its
+ * cap; the first cap entries in canonical order were written). n_* are the
+ * true counts.
  */
 typedef struct {
     int32_t status;
@@ -209,14 +214,29 @@ simulee_status simulee_create(simulee_ctx **ctx, int device, const simulee_optio
 /* Destroy a context. Pending work on streams is not waited for. */
 simulee_status simulee_destroy(simulee_ctx *ctx);
 
-/* Workspace bytes needed by simulee_check* for this trace's dimensions and size.
+/* Workspace bytes with which simulee_check* never runs out of room for this trace's dimensions and
+   size (the worst case: every record through the radix-sort streams, two races per record).
    Only the dimensions, n_events and flags are read (no device access). */
 simulee_status simulee_workspace_size(simulee_ctx *ctx, const simulee_trace *trace, size_t *bytes);
+
+/* Compact workspace bytes for a call over n_traces traces (1 for the single-trace entry points).
+   The check lays its streams out in whatever workspace it is given: with simulee_workspace_size
+   bytes (simulee_batch_workspace_size for a batch) or more it cannot run out of room; with less,
+   down to this compact size, its radix-sort streams and race staging get what the workspace holds
+   beyond the fixed part. Traces in simulator order take the hash path, which needs those streams
+   only for runs it hands over and for the races it finds, so the compact size gives them the
+   records of traces that start on the sort path (flags UNSORTED, WARP_AWARE, PAPER_ORDER, or the
+   sort path forced in the options) plus max(n/16, 65536) elements. A call that needs more reports
+   SIMULEE_ENOMEM in its reports (its outputs are then unreliable) and is repeated with the full
+   size. Below this size a call returns SIMULEE_ENOMEM at once (host). No device access. */
+simulee_status simulee_compact_workspace_size(simulee_ctx *ctx, const simulee_trace *traces, uint32_t n_traces,
+                                              size_t *bytes);
 
 /*
  * The whole check in one pass: races (Theorem 1, Algorithm 5), divergence
  * (Algorithm 4) and redundant barriers (Algorithm 5) over one trace.
- * ws: device workspace of at least simulee_workspace_size bytes, 256-byte aligned.
+ * ws: device workspace of at least simulee_compact_workspace_size bytes (simulee_workspace_size
+ * bytes never run out of room; see there), 256-byte aligned.
  */
 simulee_status simulee_check(simulee_ctx *ctx, const simulee_trace *trace, const simulee_outputs *out,
                              simulee_report *report, void *ws, size_t ws_bytes, void *stream);
@@ -252,8 +272,13 @@ simulee_status simulee_check_redundant_barriers(simulee_ctx *ctx, const simulee_
  *     SIMULEE_NOALLOC_SCRATCH_BYTES; larger traces are rejected with
  *     SIMULEE_ENOMEM before any device work is queued.
  *   - The first call on a device looks up the array's device address (once per
- *     device, with that device current); make that first call before any
- *     stream capture is started on that device.
+ *     device, with that device current, in the device's primary context); make
+ *     that first call before any stream capture is started on that device. A
+ *     first call made while `stream` is being captured returns SIMULEE_EINVAL
+ *     and queues nothing. If the device's primary context is destroyed and
+ *     created again (cudaDeviceReset), the library sees the new context on the
+ *     next call and looks the address up again, so that call is again a first
+ *     call.
  *   - All calls in the process share the one array (its contents persist from
  *     call to call; each call clears what it needs to start from zero). Calls
  *     that could overlap on the GPU - on different streams, or from different
@@ -369,6 +394,9 @@ enum {
     SIMULEE_STAGES = 7
 };
 uint32_t simulee_last_launches(const simulee_ctx *ctx);
+/* 1 when the last check call on this context was issued as one CUDA graph launch (its arguments
+   equal the previous call's, graph replay on), 0 when its kernels were launched one by one. */
+uint32_t simulee_last_replayed(const simulee_ctx *ctx);
 /* Queues on `stream` a copy of five uint32 into dev_out (device memory), for the last check that
    used workspace `ws`: the record counts of the shared-intra, global-intra and global-inter streams
    that went through the radix sort, the number of staged race records, and the number of

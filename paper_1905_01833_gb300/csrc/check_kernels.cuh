@@ -289,21 +289,27 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
                     const uint64_t sb = (uint64_t)d.block_off + blk;
                     if (isS) {
                         const uint32_t o = oS + __popc(bS & lt);
-                        sk[o] = (KS)(shl(sb, L.bus + L.be) | shl(u, L.be) | ep);
-                        sv[o] = val;
+                        if (o < L.cap_s) {   // beyond the capacity: the call reports ENOMEM
+                            sk[o] = (KS)(shl(sb, L.bus + L.be) | shl(u, L.be) | ep);
+                            sv[o] = val;
+                        }
                     }
                     if (isG) {
                         const uint32_t o = oG + __popc(bG & lt);
-                        gk[o] = (KG)(shl(sb, L.bug + L.be) | shl(u, L.be) | ep);
-                        gv[o] = val;
+                        if (o < L.cap_s) {
+                            gk[o] = (KG)(shl(sb, L.bug + L.be) | shl(u, L.be) | ep);
+                            gv[o] = val;
+                        }
                     }
                     if (isX) {
                         // inter-block payload: owner code block << 10 | tid (a shift gives the block)
                         // when blocks fit 20 bits, else the thread id
                         const uint32_t xo = d.nb <= (1u << 20) ? ((blk << 10) | (w3 & 0x3FFu)) : blk * d.bt + (w3 & 0xFFFFu);
                         const uint32_t o = oX + __popc(bX & lt);
-                        xk[o] = (KX)(shl(t, L.bug + L.bxr) | u);
-                        xv[o] = make_payload(act, xo, pos);
+                        if (o < L.x_cap) {
+                            xk[o] = (KX)(shl(t, L.bug + L.bxr) | u);
+                            xv[o] = make_payload(act, xo, pos);
+                        }
                     }
                 }
                 oS += __popc(bS);
@@ -434,8 +440,10 @@ k_x_filter(const KX *__restrict__ xk, const uint64_t *__restrict__ xv, KX *yk, u
             for (int j = 0; j < XF_ITEMS; j++) {
                 if ((keep >> j) & 1u) {
                     const uint32_t pos = o + __popc(bal[j] & lt);
-                    yk[pos] = k[j];
-                    yv[pos] = v[j];
+                    if (pos < L.cap_x1) {   // beyond the capacity: the call reports ENOMEM
+                        yk[pos] = k[j];
+                        yv[pos] = v[j];
+                    }
                     const uint64_t kk = (uint64_t)k[j];
                     for (uint32_t q = 0; q < L.np_x; q++) atomicAdd(&sh[q * RADIX + digit_of(kk, q)], 1u);
                 }
@@ -640,9 +648,9 @@ constexpr size_t reduce_groups_smem() {
 
 template <class K, bool INTER>
 __global__ void __launch_bounds__(RG_THREADS)
-k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, const uint32_t *n_ptr, Layout L,
-                const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob, uint32_t space, uint32_t bu,
-                Ctl *ctl, uint32_t *nonred, RaceStage rs) {
+k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, const uint32_t *n_ptr, uint64_t n_max,
+                Layout L, const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob, uint32_t space,
+                uint32_t bu, Ctl *ctl, uint32_t *nonred, RaceStage rs) {
     extern __shared__ __align__(16) uint8_t rg_smem[];
     uint64_t *sval = reinterpret_cast<uint64_t *>(rg_smem);
     K *skey = reinterpret_cast<K *>(rg_smem + RG_TILE * 8);
@@ -653,7 +661,7 @@ k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, c
     __shared__ K s_next_key;
     __shared__ uint32_t s_has_next;
     if (must_stop(ctl)) return;
-    const uint64_t n = *n_ptr;
+    const uint64_t n = min((uint64_t)*n_ptr, n_max);
     const uint64_t ntiles = (n + RG_TILE - 1) / RG_TILE;
     const int tid = threadIdx.x;
     const uint32_t be = L.be;
@@ -1031,6 +1039,13 @@ struct ReportArgs {
     uint32_t want_races, want_div, want_red;
 };
 
+// A workspace below the worst case: some stream or the race staging received more elements than its
+// capacity (the elements beyond it were dropped, so the results are incomplete).
+__device__ __forceinline__ bool stream_overflow(const Ctl *ctl, const Layout &L) {
+    const volatile Ctl *c = ctl;
+    return c->n_s > L.cap_s || c->n_g > L.cap_s || c->n_xf > L.cap_x1 || c->n_x > L.x_cap || c->n_races > L.race_cap;
+}
+
 __global__ void k_report(const TraceDesc *td, const TState *ts, const uint32_t *ofs_div, const uint32_t *ofs_red,
                          Layout L, Ctl *ctl, ReportArgs a) {
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < L.T; t += gridDim.x * blockDim.x) {
@@ -1048,6 +1063,7 @@ __global__ void k_report(const TraceDesc *td, const TState *ts, const uint32_t *
             if (a.want_div) nd = ofs_div[d.block_off + d.nb] - ofs_div[d.block_off];
             if (a.want_red) { nred = ofs_red[d.block_off + d.nb] - ofs_red[d.block_off]; ng = v->n_grid; }
             if (*(volatile unsigned int *)&ctl->timeout) status = 5;
+            else if (L.compact && stream_overflow(ctl, L)) status = 3;
             else if (nr > d.races_cap || nd > d.divs_cap || nred > d.reds_cap || ng > d.grid_cap) status = 4;
         }
         uint8_t *report = d.report;

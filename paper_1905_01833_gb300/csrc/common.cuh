@@ -116,7 +116,10 @@ struct Layout {
     uint64_t sig_slots;              // entries of the signature table (0: no global memory)
     uint32_t sig_direct;             // the table is indexed by the trace's offset plus the unit
     uint32_t sig_or;                 // signatures are ORs of (block | ~block << 15)
-    uint64_t x_cap;                  // elements of each inter-block stream buffer
+    uint64_t x_cap;                  // elements of the first inter-block stream buffer (every global record)
+    uint64_t cap_s;                  // elements of each intra-block stream buffer (S and G)
+    uint64_t cap_x1;                 // elements of the second inter-block buffer (kept by the filter)
+    uint32_t compact;                // some capacity is below the worst case: counts are checked against them
     size_t off_ctl, off_td, off_ts, off_tob, off_stats, off_nonred, off_gridnr, off_gridhas, off_cnt_div,
         off_cnt_red, off_ofs_div, off_ofs_red, off_hist, off_dbase, off_status, off_rank, off_p2v;
     size_t off_sk[2], off_sv[2], off_gk[2], off_gv[2], off_xk[2], off_xv[2];

@@ -49,7 +49,7 @@ k_paper_x(const KG *__restrict__ gk, const uint64_t *__restrict__ gv, const uint
     __shared__ SegCount s_warp[PX_THREADS / 32];
     __shared__ SegCount s_prefix;
     if (must_stop(ctl)) return;
-    const uint64_t n = min((uint64_t)*n_ptr, L.n);
+    const uint64_t n = min((uint64_t)*n_ptr, L.cap_s);
     const uint64_t ntiles = (n + PX_TILE - 1) / PX_TILE;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const uint32_t lt = lanemask_lt();

@@ -12,6 +12,7 @@
 //   7. race sort          radix sort of race records by canonical key, then copy out
 //   8. block outputs      divergence and redundant-barrier lists by prefix sums
 //   9. k_report           status and counts
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -48,6 +49,7 @@ struct simulee_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     uint32_t graph_launches = 0;
+    uint32_t last_replayed = 0;   // the last check call was one graph launch
     ~simulee_ctx() {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -88,8 +90,19 @@ simulee_status check_trace_args(const simulee_trace *t) {
     return SIMULEE_OK;
 }
 
+// How make_layout sizes the record streams and the race staging.
+//   FULL:    for the worst case (every record on the sort path, every group racing): never overflows.
+//   COMPACT: the query of a compact workspace: streams hold the records of traces that take the sort
+//            path from the start plus a slack of max(n / 16, 65536) elements (all of n at most).
+//   FIT:     the layout of a call: FULL when the caller's workspace holds it, else the largest slack
+//            that fits the caller's workspace; a count beyond a capacity reports SIMULEE_ENOMEM.
+enum class Sizing { FULL, COMPACT, FIT };
+
 // Batch-wide bit layouts, pass counts and workspace offsets (a single trace is a batch of one).
-simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout &L) {
+// sort_all: every trace takes the sort path (the options force it). avail: the caller's workspace
+// bytes (Sizing::FIT).
+simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout &L, Sizing sizing = Sizing::FULL,
+                           bool sort_all = false, size_t avail = 0) {
     memset(&L, 0, sizeof L);
     if (T == 0 || T > kMaxTraces) return SIMULEE_EINVAL;
     uint64_t n = 0, nb = 0, tiles = 0;
@@ -147,10 +160,7 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout 
     L.p0_q = L.p0_r + L.np_r;
     if (L.p0_q + L.np_q > MAX_PASSES || L.np_s + L.np_g + L.np_x > IN_MAXP) return SIMULEE_EINVAL;
     L.words = std::max<uint32_t>(1, (maxb + 31) / 32);
-    L.race_cap = 2 * L.n + 2;
     const uint64_t n1 = std::max<uint64_t>(L.n, 1);
-    const uint64_t sort_max = std::max<uint64_t>(n1, L.race_cap);
-    L.status_tiles = (sort_max + OS_TILE - 1) / OS_TILE;
 
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes); return r; };
@@ -195,7 +205,6 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout 
     L.off_ofs_div = take((size_t)(L.NB + 1) * 4);
     L.off_ofs_red = take((size_t)(L.NB + 1) * 4);
     L.off_dbase = take((size_t)MAX_PASSES * RADIX * 4);
-    L.off_status = take((size_t)L.status_tiles * RADIX * 8);
     if (uns) {
         L.off_rank = take(n1 * 4);
         L.off_p2v = take(n1 * 4);
@@ -207,18 +216,74 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout 
     // (two launches at most, one per CTA shape)
     const uint64_t hash_warps = (uint64_t)std::max(1, std::min<int>(sms, (int)std::max<uint32_t>(L.NB, 1))) * 32 * 2;
     L.x_cap = n1 + std::min<uint64_t>(hash_warps, n1) * HB_XCH;
-    for (int i = 0; i < 2; i++) {
-        L.off_sk[i] = take(n1 * ks);
-        L.off_sv[i] = take(n1 * 8);
-        L.off_gk[i] = take(n1 * kg);
-        L.off_gv[i] = take(n1 * 8);
-        L.off_xk[i] = take(L.x_cap * kx);
-        L.off_xv[i] = take(L.x_cap * 8);
-        L.off_rk[i] = take(L.race_cap * 8);
-        L.off_rv[i] = take(L.race_cap * 8);
+    // The rest scales with three capacities (elements): cs for each intra-block stream S and G, cx for
+    // the inter-block elements kept by the filter, cr for the race staging. The first inter-block
+    // buffer always holds x_cap slots (the record read writes every global record there).
+    const size_t fixed = o;
+    auto lay = [&](uint64_t cs, uint64_t cx, uint64_t cr, Layout &M) -> size_t {
+        size_t p = fixed;
+        auto tk = [&](size_t bytes) { size_t r = p; p = align_up(p + bytes); return r; };
+        M.cap_s = cs;
+        M.cap_x1 = cx;
+        M.race_cap = cr;
+        const uint64_t sort_max = std::max<uint64_t>(std::max<uint64_t>(cs, cx), std::max<uint64_t>(cr, uns ? n1 : 0));
+        M.status_tiles = (sort_max + OS_TILE - 1) / OS_TILE;
+        M.off_status = tk((size_t)M.status_tiles * RADIX * 8);
+        for (int i = 0; i < 2; i++) {
+            M.off_sk[i] = tk(cs * ks);
+            M.off_sv[i] = tk(cs * 8);
+            M.off_gk[i] = tk(cs * kg);
+            M.off_gv[i] = tk(cs * 8);
+            M.off_xk[i] = tk((i == 0 ? M.x_cap : cx) * kx);
+            M.off_xv[i] = tk((i == 0 ? M.x_cap : cx) * 8);
+            M.off_rk[i] = tk(cr * 8);
+            M.off_rv[i] = tk(cr * 8);
+        }
+        M.off_rp = tk(cr * 16);
+        return p;
+    };
+    // full capacities: every record in S or G, every global record kept, two races per record
+    const uint64_t full_r = 2 * L.n + 2;
+    // records of traces that take the sort path from the start: the streams hold all of them
+    uint64_t n_sort = 0;
+    for (uint32_t i = 0; i < T; i++)
+        if (sort_all || (tr[i].flags & (SIMULEE_FLAG_UNSORTED | SIMULEE_FLAG_WARP_AWARE | SIMULEE_FLAG_PAPER_ORDER)))
+            n_sort += tr[i].n_events;
+    // the unsorted traces' schedule-rank sort runs in the race buffers over all records
+    auto caps = [&](uint64_t slack, uint64_t &cs, uint64_t &cx, uint64_t &cr) {
+        cs = std::min<uint64_t>(n1, n_sort + slack);
+        cx = std::min<uint64_t>(L.x_cap, n_sort + slack);
+        cr = std::min<uint64_t>(full_r, std::max<uint64_t>(2 * n_sort + slack + 2, uns ? n1 : 0));
+    };
+    Layout F = L;
+    const size_t full_total = lay(n1, L.x_cap, full_r, F);
+    uint64_t slack = n1;
+    if (sizing == Sizing::COMPACT) {
+        slack = std::min<uint64_t>(n1, std::max<uint64_t>(n1 / 16, 65536));
+    } else if (sizing == Sizing::FIT && avail < full_total) {
+        uint64_t cs, cx, cr;
+        caps(0, cs, cx, cr);
+        Layout M = L;
+        if (lay(cs, cx, cr, M) > avail) return SIMULEE_ENOMEM;
+        uint64_t lo = 0, hi = n1;   // the largest slack whose layout fits `avail`
+        while (lo < hi) {
+            const uint64_t mid = lo + (hi - lo + 1) / 2;
+            caps(mid, cs, cx, cr);
+            if (lay(cs, cx, cr, M) <= avail) lo = mid;
+            else hi = mid - 1;
+        }
+        slack = lo;
     }
-    L.off_rp = take(L.race_cap * 16);
-    L.total = o;
+    if (slack >= n1) {
+        L = F;
+        L.total = full_total;
+        L.compact = 0;
+    } else {
+        uint64_t cs, cx, cr;
+        caps(slack, cs, cx, cr);
+        L.total = lay(cs, cx, cr, L);
+        L.compact = (cs < n1 || cx < L.x_cap || cr < full_r) ? 1u : 0u;
+    }
     return SIMULEE_OK;
 }
 
@@ -412,7 +477,7 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
     if (((uintptr_t)ws & 255u) != 0) return SIMULEE_EINVAL;
     Run R;
     R.ctx = ctx;
-    simulee_status s = make_layout(traces, T, ctx->sms, R.L);
+    simulee_status s = make_layout(traces, T, ctx->sms, R.L, Sizing::FIT, ctx->opt.path == SIMULEE_PATH_SORT, ws_bytes);
     if (s != SIMULEE_OK) return s;
     if (ws_bytes < R.L.total) return SIMULEE_ENOMEM;
     std::vector<TraceDesc> hdesc;
@@ -645,10 +710,10 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
                 k_digit_bases<<<L.p0_x, RADIX, 0, st>>>(hist, dbase, R.ctl);
                 R.launches++;
             }
-            bs = L.wide_s ? R.sort<uint64_t>(sk, sv, &R.ctl->n_s, L.n, L.np_s, L.p0_s)
-                          : R.sort<uint32_t>(sk, sv, &R.ctl->n_s, L.n, L.np_s, L.p0_s);
-            bg = L.wide_g ? R.sort<uint64_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g)
-                          : R.sort<uint32_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g);
+            bs = L.wide_s ? R.sort<uint64_t>(sk, sv, &R.ctl->n_s, L.cap_s, L.np_s, L.p0_s)
+                          : R.sort<uint32_t>(sk, sv, &R.ctl->n_s, L.cap_s, L.np_s, L.p0_s);
+            bg = L.wide_g ? R.sort<uint64_t>(gk, gv, &R.ctl->n_g, L.cap_s, L.np_g, L.p0_g)
+                          : R.sort<uint32_t>(gk, gv, &R.ctl->n_g, L.cap_s, L.np_g, L.p0_g);
             const int gp = R.grid_for(L.n, PX_TILE, 4);
             unsigned long long *stw = R.at<unsigned long long>(L.off_status);
 #define SIM_PX(KG, KX)                                                                                            \
@@ -672,8 +737,8 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
                                                         R.ctl);
                 R.launches++;
             }
-            bx = L.wide_x ? R.sort<uint64_t>(xk, xv, &R.ctl->n_xf, L.n, L.np_x, L.p0_x, 1)
-                          : R.sort<uint32_t>(xk, xv, &R.ctl->n_xf, L.n, L.np_x, L.p0_x, 1);
+            bx = L.wide_x ? R.sort<uint64_t>(xk, xv, &R.ctl->n_xf, L.cap_x1, L.np_x, L.p0_x, 1)
+                          : R.sort<uint32_t>(xk, xv, &R.ctl->n_xf, L.cap_x1, L.np_x, L.p0_x, 1);
         } else {
         // inter-block records of units touched by one block only are dropped before sorting;
         // the filter also builds the inter stream's digit histograms
@@ -685,12 +750,12 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
             k_digit_bases<<<L.p0_r, RADIX, 0, st>>>(hist, R.at<uint32_t>(L.off_dbase), R.ctl);
             R.launches++;
         }
-        bs = L.wide_s ? R.sort<uint64_t>(sk, sv, &R.ctl->n_s, L.n, L.np_s, L.p0_s)
-                      : R.sort<uint32_t>(sk, sv, &R.ctl->n_s, L.n, L.np_s, L.p0_s);
-        bg = L.wide_g ? R.sort<uint64_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g)
-                      : R.sort<uint32_t>(gk, gv, &R.ctl->n_g, L.n, L.np_g, L.p0_g);
-        bx = L.wide_x ? R.sort<uint64_t>(xk, xv, &R.ctl->n_xf, L.n, L.np_x, L.p0_x, 1)
-                      : R.sort<uint32_t>(xk, xv, &R.ctl->n_xf, L.n, L.np_x, L.p0_x, 1);
+        bs = L.wide_s ? R.sort<uint64_t>(sk, sv, &R.ctl->n_s, L.cap_s, L.np_s, L.p0_s)
+                      : R.sort<uint32_t>(sk, sv, &R.ctl->n_s, L.cap_s, L.np_s, L.p0_s);
+        bg = L.wide_g ? R.sort<uint64_t>(gk, gv, &R.ctl->n_g, L.cap_s, L.np_g, L.p0_g)
+                      : R.sort<uint32_t>(gk, gv, &R.ctl->n_g, L.cap_s, L.np_g, L.p0_g);
+        bx = L.wide_x ? R.sort<uint64_t>(xk, xv, &R.ctl->n_xf, L.cap_x1, L.np_x, L.p0_x, 1)
+                      : R.sort<uint32_t>(xk, xv, &R.ctl->n_xf, L.cap_x1, L.np_x, L.p0_x, 1);
         }
     }
     R.mark(SIMULEE_STAGE_SORT, 1);
@@ -699,15 +764,15 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
     R.mark(SIMULEE_STAGE_REDUCE, 0);
     if (sorting) {
         const int gr = R.grid_for(L.n, RG_TILE, ctx->opt.reduce_ctas_per_sm ? ctx->opt.reduce_ctas_per_sm : 3u);
-#define SIM_REDUCE(K, INTER, KOFF, VOFF, NPTR, SPACE, BU)                                                             \
+#define SIM_REDUCE(K, INTER, KOFF, VOFF, NPTR, NMAX, SPACE, BU)                                                       \
     k_reduce_groups<K, INTER><<<gr, RG_THREADS, reduce_groups_smem<K, INTER>(), st>>>(                                \
-        R.at<K>(KOFF), R.at<uint64_t>(VOFF), NPTR, L, td, tob, SPACE, BU, R.ctl, nonred, rs)
-        if (L.wide_s) SIM_REDUCE(uint64_t, false, L.off_sk[bs], L.off_sv[bs], &R.ctl->n_s, 0u, L.bus);
-        else SIM_REDUCE(uint32_t, false, L.off_sk[bs], L.off_sv[bs], &R.ctl->n_s, 0u, L.bus);
-        if (L.wide_g) SIM_REDUCE(uint64_t, false, L.off_gk[bg], L.off_gv[bg], &R.ctl->n_g, 1u, L.bug);
-        else SIM_REDUCE(uint32_t, false, L.off_gk[bg], L.off_gv[bg], &R.ctl->n_g, 1u, L.bug);
-        if (L.wide_x) SIM_REDUCE(uint64_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_xf, 1u, L.bug);
-        else SIM_REDUCE(uint32_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_xf, 1u, L.bug);
+        R.at<K>(KOFF), R.at<uint64_t>(VOFF), NPTR, NMAX, L, td, tob, SPACE, BU, R.ctl, nonred, rs)
+        if (L.wide_s) SIM_REDUCE(uint64_t, false, L.off_sk[bs], L.off_sv[bs], &R.ctl->n_s, L.cap_s, 0u, L.bus);
+        else SIM_REDUCE(uint32_t, false, L.off_sk[bs], L.off_sv[bs], &R.ctl->n_s, L.cap_s, 0u, L.bus);
+        if (L.wide_g) SIM_REDUCE(uint64_t, false, L.off_gk[bg], L.off_gv[bg], &R.ctl->n_g, L.cap_s, 1u, L.bug);
+        else SIM_REDUCE(uint32_t, false, L.off_gk[bg], L.off_gv[bg], &R.ctl->n_g, L.cap_s, 1u, L.bug);
+        if (L.wide_x) SIM_REDUCE(uint64_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_xf, L.cap_x1, 1u, L.bug);
+        else SIM_REDUCE(uint32_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_xf, L.cap_x1, 1u, L.bug);
 #undef SIM_REDUCE
         R.launches += 3;
     }
@@ -802,6 +867,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     if (!ctx || !traces || !outs || !reports || !ws || T == 0) return SIMULEE_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    ctx->last_replayed = 0;
     if (ctx->opt.graph_replay == SIMULEE_GRAPH_OFF || ctx->stage_on || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
         cs != cudaStreamCaptureStatusNone)
         return issue_check(ctx, traces, T, outs, reports, want, ws, ws_bytes, stream);
@@ -815,6 +881,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     if (ctx->graph_exec && key == ctx->graph_key) {
         const cudaError_t e = cudaGraphLaunch(ctx->graph_exec, st);
         ctx->last_launches = ctx->graph_launches;
+        ctx->last_replayed = e == cudaSuccess ? 1u : 0u;
         restore();
         return e == cudaSuccess ? SIMULEE_OK : SIMULEE_ECUDA;
     }
@@ -854,6 +921,7 @@ simulee_status run_check(simulee_ctx *ctx, const simulee_trace *traces, uint32_t
     ctx->graph_key = std::move(key);
     ctx->graph_launches = ctx->last_launches;
     const cudaError_t e = cudaGraphLaunch(ex, st);
+    ctx->last_replayed = e == cudaSuccess ? 1u : 0u;
     restore();
     return e == cudaSuccess ? SIMULEE_OK : SIMULEE_ECUDA;
 }
@@ -1052,6 +1120,17 @@ simulee_status simulee_workspace_size(simulee_ctx *ctx, const simulee_trace *tra
     return SIMULEE_OK;
 }
 
+simulee_status simulee_compact_workspace_size(simulee_ctx *ctx, const simulee_trace *traces, uint32_t n_traces,
+                                              size_t *bytes) {
+    if (!ctx || !traces || !bytes || n_traces == 0) return SIMULEE_EINVAL;
+    Layout L;
+    const simulee_status s =
+        make_layout(traces, n_traces, ctx->sms, L, Sizing::COMPACT, ctx->opt.path == SIMULEE_PATH_SORT);
+    if (s != SIMULEE_OK) return s;
+    *bytes = L.total;
+    return SIMULEE_OK;
+}
+
 simulee_status simulee_check(simulee_ctx *ctx, const simulee_trace *trace, const simulee_outputs *out,
                              simulee_report *report, void *ws, size_t ws_bytes, void *stream) {
     return launch_check(ctx, trace, out, Want{true, true, true}, report, ws, ws_bytes, stream);
@@ -1142,6 +1221,8 @@ simulee_status simulee_model_traces(simulee_ctx *ctx, const simulee_model *model
 
 uint32_t simulee_last_launches(const simulee_ctx *ctx) { return ctx ? ctx->last_launches : 0u; }
 
+uint32_t simulee_last_replayed(const simulee_ctx *ctx) { return ctx ? ctx->last_replayed : 0u; }
+
 simulee_status simulee_stream_sizes(simulee_ctx *ctx, const void *ws, uint32_t *dev_out, void *stream) {
     if (!ctx || !ws || !dev_out) return SIMULEE_EINVAL;
     static_assert(offsetof(Ctl, n_x) == offsetof(Ctl, n_s) + 16, "stream counters are contiguous");
@@ -1170,7 +1251,7 @@ const char *simulee_status_str(simulee_status s) {
         case SIMULEE_OK: return "ok";
         case SIMULEE_EINVAL: return "invalid argument or dimensions out of range";
         case SIMULEE_EBADTRACE: return "invalid record or barrier count in the trace";
-        case SIMULEE_ENOMEM: return "workspace too small";
+        case SIMULEE_ENOMEM: return "workspace too small (for the call, or for the records and races it met)";
         case SIMULEE_ETRUNC: return "an output held more records than its capacity";
         case SIMULEE_ETIMEOUT: return "a bounded device-side wait gave up";
         case SIMULEE_ECUDA: return "a CUDA call failed";
@@ -1184,25 +1265,61 @@ const char *simulee_status_str(simulee_status s) {
 // Check without a caller workspace, for callers that cannot allocate device
 // memory. The scratch is this file-scope device array; host code must not use
 // the array's name as an address (on the host it only names the symbol), so the
-// device address is looked up once per device with cudaGetSymbolAddress.
+// device address is looked up with cudaGetSymbolAddress, once per device and
+// primary context: the address is cached with the context it was found in, and
+// looked up again when the device's current context is another one (the
+// primary context was destroyed and created again, and the module with it).
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) uint8_t g_noalloc_scratch[SIMULEE_NOALLOC_SCRATCH_BYTES];
 
 namespace {
 constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[kNoallocMaxDevices];   // device address of the scratch per device, once looked up
+struct NoallocEntry {
+    void *context;   // the context the address was looked up in (nullptr: none yet)
+    void *ptr;       // device address of the scratch array in that context
+};
+NoallocEntry g_noalloc[kNoallocMaxDevices];
 
-// Looks up the scratch address on `device`; the caller has made `device` current.
-simulee_status noalloc_scratch(int device, void **ptr) {
+// The calling thread's current driver context (cuCtxGetCurrent, reached through the runtime so that
+// the library needs no link against the driver library), or nullptr when it cannot be told.
+void *current_context() {
+    using GetCurrent = CUresult (*)(CUcontext *);
+    static std::once_flag once;
+    static GetCurrent fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<GetCurrent>(f);
+    });
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return (void *)c;
+}
+
+// The scratch address on `device`; the caller has made `device` current. A lookup that is needed
+// while `stream` is being captured is refused (EINVAL): the lookup may load the module, which a
+// capture does not allow.
+simulee_status noalloc_scratch(int device, cudaStream_t stream, void **ptr) {
     if (device < 0 || device >= kNoallocMaxDevices) return SIMULEE_EINVAL;
+    void *context = current_context();
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[device]) {
+    NoallocEntry &e = g_noalloc[device];
+    if (!e.ptr || !context || e.context != context) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) return SIMULEE_ECUDA;
+        if (cs != cudaStreamCaptureStatusNone) return SIMULEE_EINVAL;
         void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SIMULEE_ECUDA;
-        g_noalloc_ptr[device] = p;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return SIMULEE_ECUDA;
+        }
+        e.context = context;
+        e.ptr = p;
     }
-    *ptr = g_noalloc_ptr[device];
+    *ptr = e.ptr;
     return SIMULEE_OK;
 }
 }  // namespace
@@ -1216,9 +1333,10 @@ extern "C" simulee_status simulee_check_noalloc(simulee_ctx *ctx, const simulee_
     if (need > (size_t)SIMULEE_NOALLOC_SCRATCH_BYTES) return SIMULEE_ENOMEM;
     int prev_dev = -1;
     if (cudaGetDevice(&prev_dev) != cudaSuccess) return SIMULEE_ECUDA;
-    if (prev_dev != ctx->device && cudaSetDevice(ctx->device) != cudaSuccess) return SIMULEE_ECUDA;
+    // made current even when it already is: the device's primary context is then current too
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return SIMULEE_ECUDA;
     void *scratch = nullptr;
-    s = noalloc_scratch(ctx->device, &scratch);
+    s = noalloc_scratch(ctx->device, (cudaStream_t)stream, &scratch);
     if (prev_dev != ctx->device) cudaSetDevice(prev_dev);
     if (s != SIMULEE_OK) return s;
     return simulee_check(ctx, trace, out, report, scratch, (size_t)SIMULEE_NOALLOC_SCRATCH_BYTES, stream);

@@ -107,6 +107,7 @@ def lib():
             "simulee_check_batch": [vp, P(Trace), u32, P(Outputs), vp, vp, ctypes.c_size_t, vp],
         }
         sigs["simulee_set_stage_events"] = [vp, P(vp), u32]
+        sigs["simulee_compact_workspace_size"] = [vp, P(Trace), u32, P(ctypes.c_size_t)]
         sigs["simulee_check_noalloc"] = [vp, P(Trace), P(Outputs), vp, vp]
         sigs["simulee_stream_sizes"] = [vp, vp, vp, vp]
         sigs["simulee_fitness_workspace_size"] = [vp, P(Trace), u32, P(ctypes.c_size_t)]
@@ -118,6 +119,8 @@ def lib():
             f.restype = st
         L.simulee_last_launches.argtypes = [vp]
         L.simulee_last_launches.restype = u32
+        L.simulee_last_replayed.argtypes = [vp]
+        L.simulee_last_replayed.restype = u32
         L.simulee_status_str.argtypes = [st]
         L.simulee_status_str.restype = ctypes.c_char_p
         _lib_handle = L
@@ -206,6 +209,10 @@ class Checker:
         """Kernels launched by the last check call."""
         return int(lib().simulee_last_launches(self.h))
 
+    def last_replayed(self) -> bool:
+        """The last check call was issued as one CUDA graph launch (graph replay)."""
+        return bool(lib().simulee_last_replayed(self.h))
+
     def set_stage_events(self, events) -> None:
         """Record the given timing events around the check's stages (2 per stage); None turns it off."""
         if not events:
@@ -227,6 +234,14 @@ class Checker:
         n = ctypes.c_size_t()
         t = dt.c()
         _check(lib().simulee_workspace_size(self.h, ctypes.byref(t), ctypes.byref(n)), "simulee_workspace_size")
+        return int(n.value)
+
+    def compact_workspace_size(self, dts) -> int:
+        """Compact workspace bytes for a call over these traces (a list; one trace for the single-trace calls)."""
+        arr = (Trace * len(dts))(*[d.c() for d in dts])
+        n = ctypes.c_size_t()
+        _check(lib().simulee_compact_workspace_size(self.h, arr, len(dts), ctypes.byref(n)),
+               "simulee_compact_workspace_size")
         return int(n.value)
 
     def workspace(self, nbytes: int):
@@ -253,8 +268,9 @@ class Checker:
                     n_divergence=r.n_divergence, n_redundant=r.n_redundant, n_grid_redundant=r.n_grid_redundant)
 
     def check(self, dt: DeviceTrace, races_cap: int | None = None, div_cap: int | None = None,
-              red_cap: int | None = None, grid_cap: int | None = None, stream=None) -> dict:
-        """Full check; returns the report plus host copies of the (truncated) lists."""
+              red_cap: int | None = None, grid_cap: int | None = None, stream=None, compact: bool = False) -> dict:
+        """Full check; returns the report plus host copies of the (truncated) lists. compact: a workspace of
+        simulee_compact_workspace_size bytes (the report says ENOMEM if the call needed more)."""
         torch = self.torch
         n = dt.n_events
         races_cap = 2 * n + 2 if races_cap is None else races_cap
@@ -262,10 +278,11 @@ class Checker:
         red_cap = dt.n_blocks * max(dt.max_barriers, 1) if red_cap is None else red_cap
         grid_cap = max(dt.max_barriers, 1) if grid_cap is None else grid_cap
         o, bufs = self.alloc_outputs(races_cap, div_cap, red_cap, grid_cap)
-        ws = self.workspace(self.workspace_size(dt))
+        need = self.compact_workspace_size([dt]) if compact else self.workspace_size(dt)
+        ws = self.workspace(need)
         t = dt.c()
         _check(lib().simulee_check(self.h, ctypes.byref(t), ctypes.byref(o), ctypes.c_void_p(self._report.data_ptr()),
-                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)), "simulee_check")
+                                   ctypes.c_void_p(ws.data_ptr()), need, _stream_ptr(stream)), "simulee_check")
         torch.cuda.synchronize(self.device)
         rep = self.report()
         return self._collect(rep, bufs, races_cap, div_cap, red_cap, grid_cap)
@@ -344,8 +361,9 @@ class Checker:
             res.append({name: int(getattr(f, name)) for name, _ in Fitness._fields_})
         return res
 
-    def check_batch(self, dts, races_caps=None, stream=None) -> list[dict]:
-        """Check independent traces in one batched call; returns one result dict per trace."""
+    def check_batch(self, dts, races_caps=None, stream=None, compact: bool = False) -> list[dict]:
+        """Check independent traces in one batched call; returns one result dict per trace. compact: a
+        workspace of simulee_compact_workspace_size bytes."""
         torch = self.torch
         T = len(dts)
         dev = f"cuda:{self.device}"
@@ -367,9 +385,10 @@ class Checker:
                               bufs["grid"].data_ptr() + int(offs["grid"][i]), gc[i])
         reports = torch.zeros(T * REPORT_BYTES, dtype=torch.uint8, device=dev)
         arr = (Trace * T)(*[d.c() for d in dts])
-        ws = self.workspace(self.batch_workspace_size(dts))
+        need = self.compact_workspace_size(dts) if compact else self.batch_workspace_size(dts)
+        ws = self.workspace(need)
         _check(lib().simulee_check_batch(self.h, arr, T, outs, ctypes.c_void_p(reports.data_ptr()),
-                                         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)),
+                                         ctypes.c_void_p(ws.data_ptr()), need, _stream_ptr(stream)),
                "simulee_check_batch")
         torch.cuda.synchronize(self.device)
         rep_bytes = reports.cpu().numpy().tobytes()
