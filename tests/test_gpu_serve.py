@@ -42,11 +42,28 @@ def test_served_results_equal_alone_results():
     assert all(j.done >= j.arrival for j in jobs)
 
 
+def test_batches_overlap_on_the_device():
+    """A large job first (a few milliseconds of GPU work), then small jobs arriving while it runs: the
+    later jobs are launched as further batches before the first one finishes, and every result still
+    equals the result of checking the trace alone."""
+    from paper_1905_01833_gb300 import serve, simulee
+    big = tracegen.pattern(31, n_blocks=384, block_threads=256, n_epochs=32, shared_units=12288, global_units=1 << 22)
+    trs = [big] + _pool()[:6]
+    alone = [checker().check(simulee.to_device(t)) for t in trs]
+    arrivals = [0.0] + [2e-4 * (k + 1) for k in range(12)]
+    dts = [simulee.to_device(t) for t in trs]
+    jobs = [serve.Job(0, dts[0], 0.0)] + [serve.Job(k + 1, dts[1 + k % 6], a) for k, a in enumerate(arrivals[1:])]
+    stats = serve.Server(0, max_inflight=3).run(jobs)
+    assert stats["max_inflight"] >= 2, stats      # batches overlapped on the device
+    for j in jobs:
+        k = 0 if j.jid == 0 else 1 + (j.jid - 1) % 6
+        assert diff(j.result, alone[k]) == [], f"job {j.jid}"
+
+
 def test_tight_budget_still_serves_everything():
     from paper_1905_01833_gb300 import serve
     trs = _pool()[:6]
     arrivals = serve.poisson_arrivals(rate=2000.0, n=20, seed=2)
-    srv_need = None
     jobs, stats = _serve(trs, arrivals, hbm_budget=200 << 20)
     assert stats["max_reserved_bytes"] <= 200 << 20
     for j in jobs:
