@@ -1,18 +1,27 @@
 """Benchmark of the synchronization check: access records checked per second.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
-One step = one full check (all stages: validation and routing, radix sorts,
-segmented reductions with epoch adjacency, canonical race list, divergence and
-redundant-barrier lists) of one synthetic trace of the grid workload: 1024
-blocks x 256 threads, 32 barrier epochs, 12288 shared units per block and 2^26
-global units, tree-reduction and tiled-transpose blocks, ~6e7 records (~1 GB,
+Default workload (the headline line): one step = one batched check
+(simulee_check_batch: races, divergence and redundant barriers of every trace)
+of the batched workload: 4096 independent traces with lognormal sizes (median
+1e5 records, clipped to 1e3..1e7, sigma fitted so that the sizes sum to 6e8
+records), block sizes {64, 128, 256, 1024}, 4..64 barrier epochs, tree-reduction
+and tiled-transpose blocks over shared and global memory (9.6 GB of records,
 larger than L2, so no flush is needed between steps).
 
-`value` is measured with the trace resident in HBM; `e2e` times the same check
-through the C ABI with the trace in pinned host memory, including the host to
-device copy of the trace and the device to host copy of the report and lists.
-With N > 1 (torchrun) every rank checks its own trace (independent replicas;
+`value` is measured with the traces resident in HBM; `e2e` times the same
+batched check through the C ABI with the traces in pinned host memory,
+including the host-to-device copy of every record and the device-to-host copy
+of the reports and result lists. `parity` compares every trace's result with
+the CPU oracle (rank 0, one GPU), which is also the timed `cpu_baseline`
+(one oracle process per host core). The line also carries the plain
+single-trace form (`single_trace`: one check of the grid workload, 1024 blocks
+x 256 threads, 32 epochs, ~6.1e7 records) and the served form (`served`:
+Poisson arrivals of jobs of log-uniform size 1e4..1e8 records under a 120 GB
+budget, batched serving against serial checking).
+
+With N > 1 (torchrun) every rank checks its own batch (independent replicas;
 the check has no cross-GPU exchange) and the time is the max over ranks.
 """
 from __future__ import annotations
@@ -26,6 +35,7 @@ import subprocess
 import sys
 import threading
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -36,6 +46,9 @@ METRIC = "access-events checked/sec"
 UNIT = "Gev/s"
 WORKLOAD = ("grid: 1024 blocks x 256 threads, 32 epochs, 12288 shared units/block + 2^26 global units, "
             "tree-reduction / 32x32 tiled-transpose blocks, 10% blocks missing one barrier, 2% global atomics")
+BATCH_WORKLOAD = ("batch: {T} traces, lognormal sizes (median 1e5 records, sigma {sigma:.4f} fitted to a "
+                  "{total:.2g}-record total, clipped 1e3..1e7), block sizes 64/128/256/1024, 4..64 epochs, "
+                  "tree-reduction / tiled-transpose blocks; one batched check per step")
 
 
 def peaks():
@@ -206,30 +219,6 @@ def make_trace(rank: int, n_blocks: int = 1024):
     return tracegen.c2(seed=tracegen.DEFAULT_SEED + rank, n_blocks=n_blocks)
 
 
-def reference_arm(args, rank: int, world: int):
-    """The oracle as the reference: each step checks a bounded sample of the workload on the host."""
-    if rank != 0:
-        return
-    tr = make_trace(0)
-    nb = args.ref_blocks
-    for _ in range(args.warmup):
-        run_oracle_sample(tr, nb)
-    times, n = [], 0
-    for _ in range(args.steps):
-        n, dt = run_oracle_sample(tr, nb)
-        times.append(dt)
-    t = sum(times) / len(times)
-    v = n / t / 1e9
-    sample = f"records of blocks 0..{nb - 1} of the grid workload ({n} records) per step, single thread"
-    print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_events_per_step": n},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
-
-
 def job_value(events_this_rank: int, ms_this_rank: float, dist=None, device="cpu"):
     """Whole-job throughput of independent replicas: all ranks' records over the slowest rank's time.
 
@@ -266,126 +255,521 @@ def device_pool(torch, trs, dev):
     return out, (ev, cn)
 
 
-def batch_arm(args):
-    """Batched workload: 4096 independent traces (lognormal sizes, median 1e5 records, block sizes
-    64..1024, 4..64 epochs) checked by one batched call; direct launches and CUDA-graph replay."""
-    import ctypes
+def result_digest(res: dict, races_cap: int) -> str:
+    """Digest of one trace's result: status, counts and the list bytes (the race list up to races_cap,
+    the length an output of that capacity holds). An oracle result and a GPU result with that race
+    capacity have equal digests exactly when they are identical."""
+    nr = int(res["n_races"]) if "n_races" in res else len(res["races"])
+    status = int(res["status"])
+    if status == 4 and nr > races_cap:   # truncated race list: the prefix and the true count are compared
+        status = 0
+    h = hashlib.sha256()
+    h.update(np.array([status, int(res["bad_kind"]), int(res["bad_index"]), nr, len(res["divergence"]),
+                       len(res["redundant"]), len(res["grid_redundant"])], dtype=np.int64).tobytes())
+    h.update(np.ascontiguousarray(res["races"][:races_cap]).tobytes())
+    for k in ("divergence", "redundant", "grid_redundant"):
+        h.update(np.ascontiguousarray(res[k]).tobytes())
+    return h.hexdigest()
+
+
+def batch_specs(seed: int, n_traces: int):
+    """Member specs (index, records, block size, epochs, seed) of the batched workload, and its sigma."""
+    import tracegen
+    sigma = tracegen.c3_sigma(seed=seed, n_traces=n_traces)
+    sizes, bss, eps = tracegen.c3_sizes(seed=seed, n_traces=n_traces, sigma=sigma)
+    return [(i, int(n), int(b), int(e), seed) for i, (n, b, e) in enumerate(zip(sizes, bss, eps))], sigma
+
+
+def race_cap_for(n: int) -> int:
+    """Race-list capacity of a batch member in the parity call (its true count fits with room to spare)."""
+    return min(2 * n + 2, 1024 + n // 8)
+
+
+# ---- the oracle on the host cores: one spawned process per core ----------------------------------
+
+def _oracle_host(conn, barrier):
+    """One oracle process: builds batch members on request, then checks them with the oracle, timed
+    from a common start (a barrier shared by all processes) to its last member."""
+    import oracle
+    import tracegen
+    cache = {}
+    while True:
+        msg = conn.recv()
+        if msg[0] == "quit":
+            break
+        if msg[0] == "gen":
+            for spec in msg[1]:
+                i, n, bs, ep, seed = spec
+                cache[i] = tracegen.c3_trace(i, n, bs, ep, seed=seed)
+            conn.send(len(cache))
+        elif msg[0] == "run":
+            ids, want_digest = msg[1], msg[2]
+            barrier.wait()
+            t0 = time.monotonic()
+            res = []
+            for i in ids:
+                res.append(oracle.check(cache[i]))
+            t1 = time.monotonic()
+            out = []
+            for i, r in zip(ids, res):
+                assert r["status"] == 0, f"oracle status {r['status']} on member {i}"
+                out.append((i, cache[i].n_events, result_digest(r, race_cap_for(cache[i].n_events))
+                            if want_digest else None))
+            conn.send((t0, t1, out))
+        elif msg[0] == "drop":
+            cache.clear()
+            conn.send(0)
+
+
+class OracleHosts:
+    """The CPU oracle in one spawned process per host core (spawned before any GPU work)."""
+
+    def __init__(self, cores: int | None = None):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.cores = cores or len(os.sched_getaffinity(0))
+        self.barrier = ctx.Barrier(self.cores)
+        self.conns, self.procs = [], []
+        for _ in range(self.cores):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_host, args=(b, self.barrier), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        self.assign: list[list[int]] = [[] for _ in range(self.cores)]
+
+    def generate(self, specs):
+        """Spread members over the processes by records (longest first) and have them build the traces."""
+        loads = [0] * self.cores
+        parts = [[] for _ in range(self.cores)]
+        for spec in sorted(specs, key=lambda s: -s[1]):
+            w = loads.index(min(loads))
+            parts[w].append(spec)
+            loads[w] += spec[1]
+        for c, p in zip(self.conns, parts):
+            c.send(("gen", p))
+        for c in self.conns:
+            c.recv()
+        self.assign = [[s[0] for s in p] for p in parts]
+
+    def run(self, want_digest: bool):
+        """Check every member once; returns (wall seconds from common start to last finish, records,
+        {member: digest})."""
+        for c, ids in zip(self.conns, self.assign):
+            c.send(("run", ids, want_digest))
+        outs = [c.recv() for c in self.conns]
+        t0 = min(o[0] for o in outs)
+        t1 = max(o[1] for o in outs)
+        n, dig = 0, {}
+        for o in outs:
+            for i, k, d in o[2]:
+                n += k
+                dig[i] = d
+        return t1 - t0, n, dig
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(("quit",))
+            except Exception:
+                pass
+        for p in self.procs:
+            p.join(timeout=30)
+
+
+# ---- batched workload on the GPU ----------------------------------------------------------------
+
+def generate_members(specs, threads: int):
+    import tracegen
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(lambda s: tracegen.c3_trace(s[0], s[1], s[2], s[3], seed=s[4]), specs))
+
+
+def member_global_counts(trs, threads: int):
+    """Per member: global records and distinct global units (the hash path's inter-block stream and
+    signature bytes)."""
+    def one(tr):
+        ev = tr.events
+        g = ev[((ev[:, 3] >> 30) & 1) == 1, 0]
+        return int(g.size), (int(np.unique(g).size) if g.size else 0)
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(one, trs))
+
+
+def batch_key_bytes(trs) -> int:
+    """Bytes of an inter-block stream key in a batched call over these traces (8 when wider than 32 bits)."""
+    return 8 if bits(len(trs)) + bits(max(t.global_units for t in trs)) > 32 else 4
+
+
+class BatchRun:
+    """Buffers and C-ABI calls of one batched check over device-resident traces."""
+
+    def __init__(self, torch, dts, device: str, caps, compact: bool = True, **opts):
+        import ctypes
+        from paper_1905_01833_gb300 import simulee
+        self.torch, self.simulee, self.ctypes = torch, simulee, ctypes
+        self.dev = device
+        self.chk = simulee.Checker(int(device.split(":")[1]), **opts)
+        self.T = len(dts)
+        self.arr = (simulee.Trace * self.T)(*[d.c() for d in dts])
+        self.set_caps(caps)
+        self.reports = torch.zeros(self.T * simulee.REPORT_BYTES, dtype=torch.uint8, device=device)
+        self.set_workspace(compact)
+
+    def set_workspace(self, compact: bool):
+        """A compact workspace (simulee_compact_workspace_size) or the one that never runs out of room."""
+        simulee, ctypes = self.simulee, self.ctypes
+        n = ctypes.c_size_t()
+        f = simulee.lib().simulee_compact_workspace_size if compact else simulee.lib().simulee_batch_workspace_size
+        simulee._check(f(self.chk.h, self.arr, self.T, ctypes.byref(n)), "workspace size")
+        self.compact = compact
+        self.ws = None
+        self.ws = self.torch.empty(int(n.value), dtype=self.torch.uint8, device=self.dev)
+
+    def set_caps(self, caps):
+        """Output lists: per member (races, divergence, redundant, grid) capacities, packed per kind."""
+        simulee, torch = self.simulee, self.torch
+        widths = (32, 16, 8, 4)
+        self.caps = caps
+        self.offs = []
+        tot = [0, 0, 0, 0]
+        for c in caps:
+            self.offs.append(tuple(tot))
+            tot = [tot[k] + c[k] * widths[k] for k in range(4)]
+        self.bufs = [torch.empty(max(x, 16), dtype=torch.uint8, device=self.dev) for x in tot]
+        self.used = tot
+        self.outs = (simulee.Outputs * self.T)()
+        for i, c in enumerate(caps):
+            o = self.offs[i]
+            self.outs[i] = simulee.Outputs(*(v for k in range(4) for v in (self.bufs[k].data_ptr() + o[k], c[k])))
+
+    def call(self, stream, arr=None, chk=None, reports_ptr=None):
+        c = self.ctypes
+        h = (chk or self.chk).h
+        s = self.simulee.lib().simulee_check_batch(h, arr if arr is not None else self.arr, self.T, self.outs,
+                                                   c.c_void_p(reports_ptr or self.reports.data_ptr()),
+                                                   c.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                                   c.c_void_p(stream.cuda_stream))
+        if s != 0:
+            raise RuntimeError(f"simulee_check_batch failed: {self.simulee.status_str(s)}")
+
+    def stream_sizes(self, stream) -> dict:
+        """Stream counts of the last call on this run's workspace (simulee_stream_sizes)."""
+        c, torch = self.ctypes, self.torch
+        out = torch.zeros(5, dtype=torch.int32, device=self.dev)
+        self.simulee._check(self.simulee.lib().simulee_stream_sizes(
+            self.chk.h, c.c_void_p(self.ws.data_ptr()), c.c_void_p(out.data_ptr()), c.c_void_p(stream.cuda_stream)),
+            "simulee_stream_sizes")
+        v = [int(x) for x in out.cpu().tolist()]
+        return dict(n_s=v[0], n_g=v[1], n_x=v[2], n_races=v[3], x_slots=v[4])
+
+    def results(self, reports_host=None):
+        """Per member: report fields and host copies of its lists."""
+        simulee = self.simulee
+        rb = (reports_host if reports_host is not None else self.reports.cpu()).numpy().tobytes()
+        host = [b.cpu().numpy() for b in self.bufs]
+        dts = (simulee.RACE_DTYPE, simulee.DIV_DTYPE, simulee.BAR_DTYPE, np.dtype("<u4"))
+        names = ("races", "divergence", "redundant", "grid_redundant")
+        out = []
+        for i in range(self.T):
+            r = simulee.Report.from_buffer_copy(rb[i * simulee.REPORT_BYTES:(i + 1) * simulee.REPORT_BYTES])
+            res = dict(status=r.status, bad_kind=r.bad_kind, bad_index=r.bad_index, n_races=r.n_races,
+                       n_divergence=r.n_divergence, n_redundant=r.n_redundant, n_grid_redundant=r.n_grid_redundant)
+            counts = (r.n_races, r.n_divergence, r.n_redundant, r.n_grid_redundant)
+            ok = r.status in (simulee.OK, simulee.ETRUNC)
+            for k in range(4):
+                cnt = min(self.caps[i][k], counts[k]) if ok else 0
+                o = self.offs[i][k]
+                res[names[k]] = np.frombuffer(host[k][o:o + cnt * dts[k].itemsize].tobytes(), dtype=dts[k])
+            out.append(res)
+        return out
+
+
+def batch_stage_bytes(trs, gcounts, sizes, kx: int):
+    """Algorithmic DRAM bytes of the stages of one batched check (the hash path's plan).
+
+    hash: one 16-byte read of every record, the inter-block stream element (key + 8-byte payload) of
+    every global record, a read and a write of the block signature of every touched global unit.
+    sort: the inter-block filter (every slot read, every kept element written) and the radix passes of
+    the streams the library reports (elements read and written per pass). ingest: barrier counts and
+    the signature-table clear. reduce: one read of every sorted stream."""
+    n = sum(t.n_events for t in trs)
+    n_gl = sum(g for g, _ in gcounts)
+    n_gu = sum(u for _, u in gcounts)
+    n_s, n_g, n_x, n_xs = sizes["n_s"], sizes["n_g"], sizes["n_x"], sizes["x_slots"]
+    T = len(trs)
+    bb = bits(sum(t.n_blocks for t in trs))
+    bus = bits(max(t.shared_units for t in trs))
+    bug = bits(max(t.global_units for t in trs))
+    be = bits(max(t.max_barriers for t in trs) + 1)
+    ks = 8 if bb + bus + be > 32 else 4
+    kg = 8 if bb + bug + be > 32 else 4
+    np_s, np_g, np_x = -(-(bb + bus + be) // 8), -(-(bb + bug + be) // 8), -(-(bits(T) + bug) // 8)
+    sig = 4 * sum(t.global_units for t in trs)
+    return dict(
+        ingest=sum(4 * t.barrier_counts.size for t in trs) + sig,
+        hash=16 * n + n_gl * (kx + 8) + 8 * n_gu,
+        fallback=16 * (n_s + n_g) + n_s * (ks + 8) + n_g * (kg + 8),
+        sort=n_xs * (kx + 8) + n_x * (kx + 8)
+        + 2 * (n_s * np_s * (ks + 8) + n_g * np_g * (kg + 8) + n_x * np_x * (kx + 8)),
+        reduce=n_s * (ks + 8) + n_g * (kg + 8) + n_x * (kx + 8),
+        n_records=n, n_global=n_gl, n_global_units=n_gu, radix_passes=np_s + np_g + np_x)
+
+
+def headline(args, rank: int, world: int, local: int, dist):
+    """The batched workload: device time, end to end, roofline of the hash stage, oracle parity and
+    baseline; plus the single-trace and served forms on one GPU."""
     import torch
     import tracegen
     from paper_1905_01833_gb300 import simulee
-    dev = "cuda:0"
-    sizes, bss, eps = tracegen.c3_sizes(n_traces=args.batch_traces)
-    base = None if args.no_cpu_baseline else batch_oracle_baseline(sizes, bss, eps)
+    dev = f"cuda:{local}"
+    cores = len(os.sched_getaffinity(0))
+    specs, sigma = batch_specs(tracegen.DEFAULT_SEED + rank, args.batch_traces)
+    with_oracle = rank == 0 and world == 1 and not args.no_cpu_baseline
+    hosts = OracleHosts() if with_oracle else None   # spawned before the first GPU call
     t0 = time.perf_counter()
-    trs = [tracegen.c3_trace(i, int(n), int(bs), int(e)) for i, (n, bs, e) in enumerate(zip(sizes, bss, eps))]
+    trs = generate_members(specs, cores)
     gen_s = time.perf_counter() - t0
+    gcounts = member_global_counts(trs, cores)
+    oracle_line = None
+    if hosts is not None:
+        hosts.generate(specs)
+        wall, n_or, digests = hosts.run(want_digest=True)
+        hosts.close()
+        oracle_line = {"value": n_or / wall / 1e9, "unit": UNIT, "cores": hosts.cores, "kind": "oracle",
+                       "sample": f"every member of the batch ({len(specs)} traces, {n_or} records), one oracle "
+                                 f"process per host core, {wall:.1f} s wall from a common start"}
+
+    torch.cuda.set_device(local)
     dts, keep = device_pool(torch, trs, dev)
-    del trs
-    chk = simulee.Checker(0)
     T = len(dts)
-    arr = (simulee.Trace * T)(*[d.c() for d in dts])
-    caps = [(min(2 * d.n_events + 2, 1 << 16), d.n_blocks, d.n_blocks * max(d.max_barriers, 1), max(d.max_barriers, 1))
-            for d in dts]
-    widths = (32, 16, 8, 4)
-    tot = [sum(c[k] * widths[k] for c in caps) for k in range(4)]
-    bufs = [torch.empty(max(x, 16), dtype=torch.uint8, device=dev) for x in tot]
-    outs = (simulee.Outputs * T)()
-    off = [0, 0, 0, 0]
-    for i, c in enumerate(caps):
-        outs[i] = simulee.Outputs(*(v for k in range(4) for v in (bufs[k].data_ptr() + off[k], c[k])))
-        for k in range(4):
-            off[k] += c[k] * widths[k]
-    reports = torch.zeros(T * simulee.REPORT_BYTES, dtype=torch.uint8, device=dev)
-    n = ctypes.c_size_t()
-    simulee._check(simulee.lib().simulee_batch_workspace_size(chk.h, arr, T, ctypes.byref(n)), "batch ws")
-    ws = torch.empty(int(n.value), dtype=torch.uint8, device=dev)
+    n_ev = sum(d.n_events for d in dts)
     stream = torch.cuda.current_stream()
-    L = simulee.lib()
-
-    def call():
-        s_ = L.simulee_check_batch(chk.h, arr, T, outs, ctypes.c_void_p(reports.data_ptr()),
-                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.c_void_p(stream.cuda_stream))
-        if s_ != 0:
-            raise RuntimeError(simulee.status_str(s_))
-
-    for _ in range(args.warmup):
-        call()
+    # parity call: generous race capacities; its counts size the lists of the timed calls
+    run = BatchRun(torch, dts, dev, [(race_cap_for(d.n_events), d.n_blocks, d.n_blocks * max(d.max_barriers, 1),
+                                      max(d.max_barriers, 1)) for d in dts])
+    run.call(stream)
     torch.cuda.synchronize()
-    rep = np.frombuffer(reports.cpu().numpy().tobytes(), dtype=np.int32).reshape(T, -1)
-    assert (rep[:, 0] == 0).all() or (np.isin(rep[:, 0], [0, 4])).all(), "batch reported errors"
+    first = run.results()
+    if any(r["status"] == simulee.ENOMEM for r in first):   # the compact workspace ran out of room
+        run.set_workspace(compact=False)
+        run.call(stream)
+        torch.cuda.synchronize()
+        first = run.results()
+    bad = [i for i, r in enumerate(first) if r["status"] != 0]
+    if bad:
+        raise RuntimeError(f"batch member {bad[0]} reported status {first[bad[0]]['status']}")
+    parity = None
+    if hosts is not None:
+        eq = [i for i in range(T) if result_digest(first[i], race_cap_for(dts[i].n_events)) == digests[i]]
+        ne = sorted(set(range(T)) - set(eq))
+        parity = {"checked": T, "equal": len(eq), "first_mismatch": ne[0] if ne else None,
+                  "what": "every member's status, counts and race / divergence / redundant-barrier / grid lists, "
+                          "byte for byte against the CPU oracle"}
+    counts = [(r["n_races"], r["n_divergence"], r["n_redundant"], r["n_grid_redundant"]) for r in first]
+    run.set_caps([tuple(max(int(x), 1) for x in c) for c in counts])   # exact-size lists for the timed calls
+    for _ in range(args.warmup):
+        run.call(stream)
+    torch.cuda.synchronize()
+    launches = run.chk.last_launches()
+    sampler = ClockSampler(gpu_uuid(torch, local) if world == 1 else None)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        call()
+        run.call(stream)
     e1.record(stream)
     torch.cuda.synchronize()
+    clocks = sampler.stop()
     ms = e0.elapsed_time(e1) / args.steps
-    # per-stage times from further calls with the library's stage events (not part of the timed steps)
+    again = run.results()
+    for i in range(T):   # the timed calls give the parity call's results
+        if again[i]["n_races"] != counts[i][0] or again[i]["status"] != 0:
+            raise RuntimeError(f"batch member {i}: timed call differs from the parity call")
+    # per-stage times from further calls with the library's stage events (launched directly)
     nst = len(simulee.STAGES)
-    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * nst)] for _ in range(3)]
+    reps = 3
+    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * nst)] for _ in range(reps)]
     for row in sev:
         for e in row:
             e.record(stream)
     for row in sev:
-        chk.set_stage_events(row)
-        call()
+        run.chk.set_stage_events(row)
+        run.call(stream)
     torch.cuda.synchronize()
-    chk.set_stage_events(None)
-    stage_ms = {name: sum(r[2 * k].elapsed_time(r[2 * k + 1]) for r in sev) / len(sev)
+    run.chk.set_stage_events(None)
+    stage_ms = {name: sum(r[2 * k].elapsed_time(r[2 * k + 1]) for r in sev) / reps
                 for k, name in enumerate(simulee.STAGES)}
-    # the same call captured once in a CUDA graph and replayed
-    g = torch.cuda.CUDAGraph()
-    s2 = torch.cuda.Stream()
-    s2.wait_stream(stream)
-    with torch.cuda.stream(s2):
-        stream = s2
-        with torch.cuda.graph(g, stream=s2):
-            call()
-    stream = torch.cuda.current_stream()
-    g.replay()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        g.replay()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_g = e0.elapsed_time(e1) / args.steps
-    n_ev = sum(d.n_events for d in dts)
-    return {"workload": f"batch: {T} traces, lognormal sizes (median 1e5, sigma 0.87, clipped 1e3..1e7), "
-                        f"block sizes 64..1024, 4..64 epochs", "traces": T, "n_events": n_ev,
-            "value": n_ev / (ms * 1e-3) / 1e9, "ms_per_step": ms,
-            "graph_value": n_ev / (ms_g * 1e-3) / 1e9, "graph_ms_per_step": ms_g, "unit": UNIT,
-            "stages_ms": stage_ms,
-            "launches_per_step": chk.last_launches(), "workspace_bytes": ws.numel(), "gen_s": gen_s,
-            **({"cpu_baseline": base} if base else {})}
+    n_hash = run.chk.last_launches()
+    sizes = run.stream_sizes(stream)
+    value, ms = job_value(n_ev, ms, dist, dev)
 
+    # end to end: every step copies all records and counts from pinned host memory, checks the batch
+    # and reads the reports and result lists back; two device copies of the batch (the resident one
+    # and a second), the next step's upload on a copy stream while this step is checked
+    ev_h = torch.empty(keep[0].shape, dtype=torch.int32).pin_memory()
+    cn_h = torch.empty(keep[1].shape, dtype=torch.int32).pin_memory()
+    ev_h.copy_(keep[0])
+    cn_h.copy_(keep[1])
+    ev2, cn2 = torch.empty_like(keep[0]), torch.empty_like(keep[1])
+    base_e, base_c = keep[0].data_ptr(), keep[1].data_ptr()
+    arr2 = (simulee.Trace * T)()
+    for i, d in enumerate(dts):
+        c = d.c()
+        if d.n_events:
+            c.events = ev2.data_ptr() + (d.events.data_ptr() - base_e)
+        c.barrier_counts = cn2.data_ptr() + (d.barrier_counts.data_ptr() - base_c)
+        arr2[i] = c
+    arrs = [run.arr, arr2]
+    d_ev, d_cn = [keep[0], ev2], [keep[1], cn2]
+    chks = [run.chk, simulee.Checker(local)]
+    copy_s = torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    freed = [torch.cuda.Event() for _ in range(2)]
+    rep_h = torch.empty(T * simulee.REPORT_BYTES, dtype=torch.uint8).pin_memory()
+    out_h = [torch.empty(max(u, 16), dtype=torch.uint8).pin_memory() for u in run.used]
+    h2d = ev_h.numel() * 4 + cn_h.numel() * 4
+    d2h = T * simulee.REPORT_BYTES + sum(run.used)
 
-def _oracle_trace_worker(job):
-    """One batch member checked by the oracle (runs in a spawned process; generation not timed)."""
-    import oracle
-    import tracegen
-    i, n, bs, ep = job
-    tr = tracegen.c3_trace(i, n, bs, ep)
+    def issue_copy(i):
+        q = i % 2
+        if i >= 2:
+            copy_s.wait_event(freed[q])
+        with torch.cuda.stream(copy_s):
+            d_ev[q].copy_(ev_h, non_blocking=True)
+            d_cn[q].copy_(cn_h, non_blocking=True)
+        copied[q].record(copy_s)
+
+    def finish_step(i):
+        q = i % 2
+        stream.wait_event(copied[q])
+        run.call(stream, arr=arrs[q], chk=chks[q])
+        freed[q].record(stream)
+        rep_h.copy_(run.reports, non_blocking=True)
+        for k in range(4):
+            if run.used[k]:
+                out_h[k][:run.used[k]].copy_(run.bufs[k][:run.used[k]], non_blocking=True)
+        stream.synchronize()
+
+    def run_e2e(k, overlap):
+        issue_copy(0)
+        for i in range(k):
+            if overlap and i + 1 < k:
+                issue_copy(i + 1)
+            finish_step(i)
+            if not overlap and i + 1 < k:
+                issue_copy(i + 1)
+
+    run_e2e(3, True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    out = oracle.check(tr)
-    assert out["status"] == 0
-    return tr.n_events, time.perf_counter() - t0
+    run_e2e(args.e2e_steps, True)
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_value, _ = job_value(n_ev, e2e_s * 1e3, dist, dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nser = max(2, args.e2e_steps // 2)
+    run_e2e(nser, False)
+    e2e_serial, _ = job_value(n_ev, (time.perf_counter() - t0) / nser * 1e3, dist, dev)
+    chks[1].close()
+    rb = rep_h.numpy().tobytes()
+    for i in range(T):
+        r = simulee.Report.from_buffer_copy(rb[i * simulee.REPORT_BYTES:(i + 1) * simulee.REPORT_BYTES])
+        if r.status != 0 or r.n_races != counts[i][0]:
+            raise RuntimeError(f"batch member {i}: end-to-end result differs from the resident-trace check")
+    del ev2, cn2, ev_h, cn_h, out_h
+
+    # roofline of the dominant stage (the hash path's single read)
+    peak, peak_src = peaks()
+    sb = batch_stage_bytes(trs, gcounts, sizes, batch_key_bytes(trs))
+    cand = [k for k in ("ingest", "hash", "fallback", "sort", "reduce") if sb[k] > 0]
+    dom = max(cand, key=lambda k: stage_ms[k])
+    kname = {"ingest": "k_block_stats", "hash": "k_hash_blocks", "fallback": "k_ingest", "sort": "k_onesweep",
+             "reduce": "k_reduce_groups"}[dom]
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    nl = 2 if (dom == "hash" and any(d.block_threads > 256 for d in dts)
+               and sum(d.n_blocks for d in dts if d.block_threads <= 256) >= 2 * sms) else 1
+    achieved = sb[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    b_plan = sum(sb[k] for k in ("ingest", "hash", "fallback", "sort", "reduce")) / n_ev
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src, "launches": nl,
+                "bytes_per_launch": sb[dom] / nl, "launch_ms": stage_ms[dom] / nl,
+                "stage_bytes": sb[dom], "stage_ms": stage_ms[dom],
+                "bytes_per_record": sb[dom] / n_ev,
+                "traffic": kernel_traffic(kname, "batch"),
+                "plan": {"bytes_per_record": b_plan, "frac": value * 1e9 * b_plan / (peak * 1e9),
+                         "floor_frac": value * 1e9 * 16 / (peak * 1e9), "radix_passes": sb["radix_passes"]}}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD.format(T=T, sigma=sigma, total=float(n_ev)), "traces": T,
+                   "n_events": n_ev, "sigma": sigma, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (9.6 GB of records, 129 MB L2); no flush",
+                   "launch": "repeated identical batched calls replayed by the library as one CUDA graph"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "serial_value": e2e_serial,
+                "overlap": "two device copies of the batch: the next step's host-to-device copy runs on a copy "
+                           "stream while the current step is checked; serial_value = copy, check and read-back "
+                           "one after another"},
+        "gpu_launches": launches * args.steps,
+        "roofline": roofline,
+        "stages_ms": stage_ms,
+        "streams": sizes,
+        "workspace_bytes": run.ws.numel(),
+        "workspace_bytes_per_record": run.ws.numel() / n_ev,
+        "workspace": "compact" if run.compact else "full",
+        "generation_s": gen_s,
+        "results": {"n_races": int(sum(c[0] for c in counts)), "n_divergence": int(sum(c[1] for c in counts)),
+                    "n_redundant": int(sum(c[2] for c in counts)), "n_grid_redundant": int(sum(c[3] for c in counts))},
+        "clocks": clocks,
+    }
+    if oracle_line:
+        line["cpu_baseline"] = oracle_line
+    if parity:
+        line["parity"] = parity
+    del run, dts, keep, trs
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return line
 
 
-def batch_oracle_baseline(sizes, bss, eps, stride: int = 32) -> dict:
-    """The oracle over every stride-th batch member, one process per host core (spawned before any GPU work)."""
-    import multiprocessing as mp
-    cores = len(os.sched_getaffinity(0))
-    jobs = [(i, int(sizes[i]), int(bss[i]), int(eps[i])) for i in range(0, len(sizes), stride)]
-    with mp.get_context("spawn").Pool(cores) as pool:
-        pool.map(_oracle_trace_worker, jobs[:cores])        # warm-up: load the oracle in every worker
-        t0 = time.perf_counter()
-        res = pool.map(_oracle_trace_worker, jobs, chunksize=1)
-        wall = time.perf_counter() - t0
-    n = sum(r[0] for r in res)
-    return {"value": n / wall / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"every {stride}th batch member ({len(jobs)} traces, {n} records), one process per core, "
-                      f"{wall:.1f} s wall"}
+def reference_arm(args, rank: int, world: int):
+    """The oracle as the reference arm: each step checks a bounded sample of the batched workload (every
+    ref_stride-th member) with one oracle process per host core; rank 0 only."""
+    if rank != 0:
+        return
+    import tracegen
+    specs, sigma = batch_specs(tracegen.DEFAULT_SEED, args.batch_traces)
+    sample = specs[::args.ref_stride]
+    hosts = OracleHosts(min(len(os.sched_getaffinity(0)), len(sample)))
+    hosts.generate(sample)
+    for _ in range(args.warmup):
+        hosts.run(want_digest=False)
+    times, n = [], 0
+    for _ in range(args.steps):
+        wall, n, _ = hosts.run(want_digest=False)
+        times.append(wall)
+    hosts.close()
+    t = sum(times) / len(times)
+    v = n / t / 1e9
+    total = sum(s[1] for s in specs)
+    desc = (f"every {args.ref_stride}th member of the batched workload ({len(sample)} traces, {n} records) per "
+            f"step, one oracle process per host core ({hosts.cores})")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD.format(T=len(specs), sigma=sigma, total=float(total)),
+                   "traces": len(specs), "n_events": total, "sigma": sigma, "n_events_per_step": n},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": hosts.cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
 def single_trace_arm(args):
@@ -562,112 +946,20 @@ def tracegen_events(sol) -> int:
     return tracegen.model_events(model, grid, block)
 
 
-def serve_arm(args):
-    """Serving workload: Poisson arrivals of check jobs, sizes log-uniform 1e4..1e8 records from the
-    grid and barrier generators, continuous batching under a 120 GB HBM budget, against serial checking."""
-    import torch
-    import tracegen
-    from paper_1905_01833_gb300 import serve
-    rng = np.random.default_rng(7)
-    pool_sizes = np.exp(np.linspace(np.log(1e4), np.log(1e8), args.serve_pool))
-    trs = []
-    for i, sz in enumerate(pool_sizes):
-        if i % 2 == 0:   # grid family: 256-thread blocks, 32 epochs (~2e5 records per block)
-            nb = max(1, int(round(sz / 59600)))
-            tr = tracegen.pattern(100 + i, n_blocks=nb, block_threads=256, n_epochs=32, shared_units=12288,
-                                  global_units=1 << max(20, int(np.ceil(np.log2(4096 + 2 * 1024 * nb)))))
-            if tr.n_events > sz:
-                tr.events = np.ascontiguousarray(tr.events[:int(sz)])
-        else:            # barrier family: 1024-thread blocks, 64 epochs, 4 accesses (262144 records per block)
-            nb = max(1, int(round(sz / 262144)))
-            tr = tracegen.barrier(100 + i, n_blocks=nb, block_threads=1024, n_epochs=64, shared_units=8192)
-            if tr.n_events > sz:
-                tr.events = np.ascontiguousarray(tr.events[:int(sz)])
-        trs.append(tr)
-    dts, keep = device_pool(torch, trs, "cuda:0")
-    del trs
-    draws = np.exp(rng.uniform(np.log(1e4), np.log(1e8), size=args.serve_jobs))
-    pick = np.abs(np.log(draws)[:, None] - np.log(pool_sizes)[None, :]).argmin(axis=1)
-
-    def run(rate, serial):
-        arr = serve.poisson_arrivals(rate, args.serve_jobs, seed=11)
-        jobs = [serve.Job(i, dts[int(pick[i])], float(arr[i])) for i in range(args.serve_jobs)]
-        srv = serve.Server(0, hbm_budget=120 << 30, serial=serial, keep_lists=False)
-        return srv.run(jobs)
-
-    warm = serve.Server(0, keep_lists=False)
-    warm.run([serve.Job(i, dts[i % len(dts)], 0.0) for i in range(len(dts))])
-    res = {"workload": f"serve: Poisson arrivals, {args.serve_jobs} jobs, sizes log-uniform 1e4..1e8 records "
-                       f"(pool of {len(dts)} device-resident traces), 120 GB budget",
-           "unit": UNIT, "rates": {}}
-    for rate in args.serve_rates:
-        a = run(rate, serial=False)
-        b = run(rate, serial=True)
-        res["rates"][str(rate)] = {
-            "batched": {k: a[k] for k in ("p50_ms", "p99_ms", "max_ms", "batches", "max_batch", "max_inflight")}
-            | {"value": a["events_per_s"] / 1e9},
-            "serial": {k: b[k] for k in ("p50_ms", "p99_ms", "max_ms")} | {"value": b["events_per_s"] / 1e9}}
-    return res
-
-
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--path", choices=["auto", "sort"], default="auto")
-    ap.add_argument("--hash-shape", type=int, choices=[0, 1, 2], default=0,
-                    help="hash path CTAs: 0 chosen per call, 1 one 1024-thread CTA per SM, 2 two 512-thread CTAs")
-    ap.add_argument("--graph-replay", choices=["auto", "off"], default="auto",
-                    help="auto: repeated identical calls replayed by the library as one CUDA graph; off: direct launches")
-    ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--oracle-blocks", type=int, default=256)
-    ap.add_argument("--ref-blocks", type=int, default=32)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--blocks", type=int, default=1024, help="grid blocks (1024 = the benchmark workload; "
-                    "smaller values only for profiling captures)")
-    ap.add_argument("--workload", choices=["grid", "batch", "serve", "fitness", "evolve", "strided", "barrier", "warp",
-                                           "paper"],
-                    default="grid",
-                    help="grid: the benchmark line; batch / serve: the batched and served forms; fitness: Eq. 1 "
-                         "over the grid workload (separate lines)")
-    ap.add_argument("--batch-traces", type=int, default=4096)
-    ap.add_argument("--serve-jobs", type=int, default=2000)
-    ap.add_argument("--serve-pool", type=int, default=24)
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 1000.0, 4000.0])
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
-    if args.workload != "grid" and args.impl == "ours":
-        import torch
-        torch.cuda.set_device(0)
-        out = {"batch": batch_arm, "serve": serve_arm, "fitness": fitness_arm, "evolve": evolve_arm,
-               "strided": single_trace_arm, "barrier": single_trace_arm, "warp": single_trace_arm,
-               "paper": single_trace_arm}[args.workload](args)
-        print(json.dumps({"metric": METRIC, **out}))
-        return
-
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
-        reference_arm(args, rank, world)
-        return
-
+def grid_arm(args, rank: int, world: int, local: int, dist, full: bool = True):
+    """The plain single-trace form: one simulee_check of the grid workload per step, trace resident in HBM;
+    with `full`, also direct launches, end to end through the C ABI and the oracle on a sample."""
+    import ctypes
     import torch
     from paper_1905_01833_gb300 import simulee
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
-
     tr = make_trace(rank, args.blocks)
     dt = simulee.to_device(tr, f"cuda:{local}")
-    chk = simulee.Checker(local, path=simulee.PATH_SORT if args.path == "sort" else simulee.PATH_AUTO,
-                          hash_shape=args.hash_shape,
-                          graph_replay=simulee.GRAPH_OFF if args.graph_replay == "off" else simulee.GRAPH_AUTO)
-    ws = chk.workspace(chk.workspace_size(dt))
+    mode = dict(path=simulee.PATH_SORT if args.path == "sort" else simulee.PATH_AUTO, hash_shape=args.hash_shape,
+                graph_replay=simulee.GRAPH_OFF if args.graph_replay == "off" else simulee.GRAPH_AUTO)
+    chk = simulee.Checker(local, **mode)
+    ws = chk.workspace(chk.compact_workspace_size([dt]))
+    compact = True
     caps = dict(races_cap=4_000_000, div_cap=tr.n_blocks, red_cap=tr.n_blocks * tr.max_barriers,
                 grid_cap=tr.max_barriers)
     outs, bufs = chk.alloc_outputs(caps["races_cap"], caps["div_cap"], caps["red_cap"], caps["grid_cap"])
@@ -675,96 +967,112 @@ def main():
     stream = torch.cuda.current_stream()
     L = simulee.lib()
     ctrace = dt.c()
-    import ctypes
     sp = ctypes.c_void_p(stream.cuda_stream)
 
-    def step(trace_c, rep_ptr):
-        s = L.simulee_check(chk.h, ctypes.byref(trace_c), ctypes.byref(outs), ctypes.c_void_p(rep_ptr),
+    def step(c, trace_c, rep_ptr):
+        s = L.simulee_check(c.h, ctypes.byref(trace_c), ctypes.byref(outs), ctypes.c_void_p(rep_ptr),
                             ctypes.c_void_p(ws.data_ptr()), ws.numel(), sp)
         if s != 0:
             raise RuntimeError(f"simulee_check failed: {simulee.status_str(s)}")
 
+    step(chk, ctrace, report_dev.data_ptr())
+    torch.cuda.synchronize()
+    if simulee.Report.from_buffer_copy(report_dev.cpu().numpy().tobytes()).status == simulee.ENOMEM:
+        ws = None
+        ws = chk.workspace(chk.workspace_size(dt))   # the compact workspace ran out of room
+        compact = False
     for _ in range(args.warmup):
-        step(ctrace, report_dev.data_ptr())
+        step(chk, ctrace, report_dev.data_ptr())
     torch.cuda.synchronize()
     rep0 = simulee.Report.from_buffer_copy(report_dev.cpu().numpy().tobytes())
     if rep0.status != 0:
         raise RuntimeError(f"check reported status {rep0.status}")
     launches = chk.last_launches()
-
-    # stage events for every timed step
     nst = len(simulee.STAGES)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * nst)] for _ in range(args.steps)]
+    steps = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * nst)] for _ in range(steps)]
     for row in evs:
         for e in row:
             e.record(stream)
     torch.cuda.synchronize()
-
-    sampler = ClockSampler(gpu_uuid(torch, local) if world == 1 else None)
-    sampler.start()
-    time.sleep(0.3)
+    sampler = ClockSampler(gpu_uuid(torch, local) if (world == 1 and full) else None)
+    if full:
+        sampler.start()
+        time.sleep(0.3)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
-    for i in range(args.steps):
-        step(ctrace, report_dev.data_ptr())
+    for _ in range(steps):
+        step(chk, ctrace, report_dev.data_ptr())
     t_end.record(stream)
     torch.cuda.synchronize()
-    clocks = sampler.stop()
-    ms = t_start.elapsed_time(t_end) / args.steps
-    # per-stage times from a second run of the same steps with stage events (not the timed steps above,
-    # so the events add nothing to their time)
-    for i in range(args.steps):
+    clocks = sampler.stop() if full else None
+    ms = t_start.elapsed_time(t_end) / steps
+    for i in range(steps):
         chk.set_stage_events(evs[i])
-        step(ctrace, report_dev.data_ptr())
+        step(chk, ctrace, report_dev.data_ptr())
     torch.cuda.synchronize()
     chk.set_stage_events(None)
-    stage_ms = {name: sum(evs[i][2 * s].elapsed_time(evs[i][2 * s + 1]) for i in range(args.steps)) / args.steps
+    stage_ms = {name: sum(evs[i][2 * s].elapsed_time(evs[i][2 * s + 1]) for i in range(steps)) / steps
                 for s, name in enumerate(simulee.STAGES)}
-    # the same steps with graph replay off: every call issues its kernels one by one
+    rep = simulee.Report.from_buffer_copy(report_dev.cpu().numpy().tobytes())
+    assert rep.status == 0 and rep.n_races == rep0.n_races and rep.n_redundant == rep0.n_redundant
     direct = None
     if world == 1:
-        chk_d = simulee.Checker(local, path=simulee.PATH_SORT if args.path == "sort" else simulee.PATH_AUTO,
-                                hash_shape=args.hash_shape, graph_replay=simulee.GRAPH_OFF)
-
-        def step_d():
-            s = L.simulee_check(chk_d.h, ctypes.byref(ctrace), ctypes.byref(outs), ctypes.c_void_p(report_dev.data_ptr()),
-                                ctypes.c_void_p(ws.data_ptr()), ws.numel(), sp)
-            if s != 0:
-                raise RuntimeError(f"simulee_check failed: {simulee.status_str(s)}")
+        chk_d = simulee.Checker(local, **dict(mode, graph_replay=simulee.GRAPH_OFF))
         for _ in range(3):
-            step_d()
+            step(chk_d, ctrace, report_dev.data_ptr())
         torch.cuda.synchronize()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         g0.record(stream)
-        for _ in range(args.steps):
-            step_d()
+        for _ in range(steps):
+            step(chk_d, ctrace, report_dev.data_ptr())
         g1.record(stream)
         torch.cuda.synchronize()
-        ms_d = g0.elapsed_time(g1) / args.steps
+        ms_d = g0.elapsed_time(g1) / steps
         direct = {"value": tr.n_events / (ms_d * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_d,
                   "launches_per_step": chk_d.last_launches()}
         chk_d.close()
-    rep = simulee.Report.from_buffer_copy(report_dev.cpu().numpy().tobytes())
-    assert rep.status == 0 and rep.n_races == rep0.n_races and rep.n_redundant == rep0.n_redundant
-
     value, ms = job_value(tr.n_events, ms, dist, f"cuda:{local}")
 
+    sizes = chk.stream_sizes()
+    sb = stage_bytes(tr, sizes, args.path, *global_counts(tr))
+    peak, peak_src = peaks()
+    cand = [k for k in ("ingest", "hash", "fallback", "sort", "reduce") if sb[k] > 0]
+    dom = max(cand, key=lambda k: stage_ms[k])
+    kname = {"ingest": "k_ingest", "hash": "k_hash_blocks", "fallback": "k_ingest", "sort": "k_onesweep",
+             "reduce": "k_reduce_groups"}[dom]
+    nl = sb["launches"][dom]
+    achieved = sb[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src,
+                "bytes_per_launch": sb[dom] / nl, "launch_ms": stage_ms[dom] / nl,
+                "traffic": kernel_traffic(kname, "grid")}
+    b_plan = sum(sb[k] for k in ("ingest", "hash", "fallback", "sort", "reduce")) / tr.n_events
+    roofline["plan"] = {"bytes_per_record": b_plan, "frac": value * 1e9 * b_plan / (peak * 1e9),
+                        "floor_frac": value * 1e9 * 16 / (peak * 1e9), "radix_passes": sb["launches"]["sort"] - 1}
+    line = {"workload": WORKLOAD if args.blocks == 1024 else WORKLOAD.replace("1024 blocks", f"{args.blocks} blocks"),
+            "n_events": tr.n_events, "value": value, "unit": UNIT, "ms_per_step": ms, "steps": steps,
+            "launches_per_step": launches, "direct": direct, "roofline": roofline, "stages_ms": stage_ms,
+            "streams": sizes, "workspace_bytes": ws.numel(), "workspace_bytes_per_record": ws.numel() / tr.n_events,
+            "workspace": "compact" if compact else "full",
+            "results": {"n_races": rep.n_races, "n_divergence": rep.n_divergence, "n_redundant": rep.n_redundant,
+                        "n_grid_redundant": rep.n_grid_redundant}}
+    if not full:
+        return line
+    line["clocks"] = clocks
+
     # end to end through the C ABI: pinned host trace -> device, check, report and lists -> host, every
-    # step. Two device trace buffers: the next step's records go up on a copy stream while this step
-    # is checked (one context per buffer, so that each keeps its own replay graph); the same steps
-    # one after another give e2e_serial.
+    # step; two device trace buffers and two contexts, the next step's upload on a copy stream
     h_ev = torch.from_numpy(tr.events.view(np.int32)).pin_memory()
     h_cn = torch.from_numpy(tr.barrier_counts.view(np.int32)).pin_memory()
     d_ev = [torch.empty_like(dt.events) for _ in range(2)]
     d_cn = [torch.empty_like(dt.barrier_counts) for _ in range(2)]
     etr = [simulee.DeviceTrace(d_ev[q], d_cn[q], tr.n_blocks, tr.block_threads, tr.shared_units, tr.global_units,
                                tr.max_barriers).c() for q in range(2)]
-    chks = [chk, simulee.Checker(local, path=simulee.PATH_SORT if args.path == "sort" else simulee.PATH_AUTO,
-                                 hash_shape=args.hash_shape,
-                                 graph_replay=simulee.GRAPH_OFF if args.graph_replay == "off" else simulee.GRAPH_AUTO)]
+    chks = [chk, simulee.Checker(local, **mode)]
     copy_s = torch.cuda.Stream(device=f"cuda:{local}")
     copied = [torch.cuda.Event() for _ in range(2)]
     freed = [torch.cuda.Event() for _ in range(2)]
@@ -778,7 +1086,7 @@ def main():
     def issue_copy(i):
         q = i % 2
         if i >= 2:
-            copy_s.wait_event(freed[q])   # the check of step i - 2 has read this buffer
+            copy_s.wait_event(freed[q])
         with torch.cuda.stream(copy_s):
             d_ev[q].copy_(h_ev, non_blocking=True)
             d_cn[q].copy_(h_cn, non_blocking=True)
@@ -788,10 +1096,7 @@ def main():
         nonlocal d2h
         q = i % 2
         stream.wait_event(copied[q])
-        s_ = L.simulee_check(chks[q].h, ctypes.byref(etr[q]), ctypes.byref(outs), ctypes.c_void_p(rep_host.data_ptr()),
-                             ctypes.c_void_p(ws.data_ptr()), ws.numel(), sp)
-        if s_ != 0:
-            raise RuntimeError(f"simulee_check failed: {simulee.status_str(s_)}")
+        step(chks[q], etr[q], rep_host.data_ptr())
         freed[q].record(stream)
         stream.synchronize()
         r = simulee.Report.from_buffer_copy(rep_host.numpy().tobytes())
@@ -816,75 +1121,158 @@ def main():
                 issue_copy(i + 1)
 
     run_e2e(4, True)
-    if dist:
-        dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     run_e2e(args.e2e_steps, True)
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    e2e_value, _ = job_value(tr.n_events, e2e_s * 1e3, dist, f"cuda:{local}")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    run_e2e(max(2, args.e2e_steps // 2), False)
-    e2e_serial_s = (time.perf_counter() - t0) / max(2, args.e2e_steps // 2)
-    e2e_serial, _ = job_value(tr.n_events, e2e_serial_s * 1e3, dist, f"cuda:{local}")
+    nser = max(2, args.e2e_steps // 2)
+    run_e2e(nser, False)
+    e2e_serial_s = (time.perf_counter() - t0) / nser
     chks[1].close()
-    h2d = tr.events.nbytes + tr.barrier_counts.nbytes
-
-    # roofline of the dominant stage
-    sizes = chk.stream_sizes()
-    sb = stage_bytes(tr, sizes, args.path, *global_counts(tr))
-    peak, peak_src = peaks()
-    cand = [k for k in ("ingest", "hash", "fallback", "sort", "reduce") if sb[k] > 0]
-    dom = max(cand, key=lambda k: stage_ms[k])
-    kname = {"ingest": "k_ingest", "hash": "k_hash_blocks", "fallback": "k_ingest", "sort": "k_onesweep",
-             "reduce": "k_reduce_groups"}[dom]
-    nl = sb["launches"][dom]
-    achieved = sb[dom] / (stage_ms[dom] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_src,
-                "bytes_per_launch": sb[dom] / nl, "launch_ms": stage_ms[dom] / nl,
-                "traffic": kernel_traffic(kname, "grid")}
-    stage_gbs = {k: sb[k] / (stage_ms[k] * 1e-3) / 1e9 for k in cand if stage_ms[k] > 0}
-    # the whole plan: algorithmic bytes per record over every stage, and the single-read floor (16 B per record)
-    b_plan = sum(sb[k] for k in ("ingest", "hash", "fallback", "sort", "reduce")) / tr.n_events
-    roofline["plan"] = {"bytes_per_record": b_plan, "frac": value * 1e9 * b_plan / (peak * 1e9),
-                        "floor_frac": value * 1e9 * 16 / (peak * 1e9),
-                        "radix_passes": sb["launches"]["sort"] - 1}
-
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if args.blocks == 1024 else WORKLOAD.replace("1024 blocks", f"{args.blocks} blocks"),
-                   "n_events": tr.n_events, "parallelism": f"replicas{world}",
-                   "l2": "inputs larger than L2 (1 GB trace, 129 MB L2); no flush", "path": args.path},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "serial_value": e2e_serial,
-                "overlap": "two device trace buffers: the next step's host-to-device copy runs on a copy "
-                           "stream while the current step is checked; serial_value = copy, check and "
-                           "read-back one after another"},
-        "gpu_launches": launches * args.steps,
-        "launch": "repeated identical calls replayed by the library as one CUDA graph (graph_replay auto); "
-                  "'direct' times the same steps with every kernel launched by the call",
-        "direct": direct,
-        "roofline": roofline,
-        "stages_ms": stage_ms,
-        "stages_gbs": stage_gbs,
-        "streams": sizes,
-        "results": {"n_races": rep.n_races, "n_divergence": rep.n_divergence, "n_redundant": rep.n_redundant,
-                    "n_grid_redundant": rep.n_grid_redundant},
-        "clocks": clocks,
-    }
+    line["e2e"] = {"value": tr.n_events / e2e_s / 1e9, "unit": UNIT,
+                   "h2d_bytes_per_step": tr.events.nbytes + tr.barrier_counts.nbytes, "d2h_bytes_per_step": d2h,
+                   "serial_value": tr.n_events / e2e_serial_s / 1e9}
+    line["gpu_launches"] = launches * steps
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, secs = run_oracle_sample(tr, args.oracle_blocks)
         line["cpu_baseline"] = {"value": n / secs / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"records of blocks 0..{args.oracle_blocks - 1} of the same trace "
                                           f"({n} records, {secs:.1f} s, single thread)",
                                 "host_cores": len(os.sched_getaffinity(0))}
-    if rank == 0:
-        print(json.dumps(line))
+    del d_ev, d_cn, dt, ws
+    torch.cuda.empty_cache()
+    return line
+
+
+def serve_pool(torch, n_pool: int, dev: str):
+    """The served workload's device-resident traces (tracegen.c5_member: sizes log-spaced over 1e4..1e8
+    records, grid and barrier families), with each trace's plan bytes on the hash path (record read,
+    inter-block elements, signatures)."""
+    import tracegen
+    pool_sizes = tracegen.c5_pool_sizes(n_pool)
+    trs = [tracegen.c5_member(i, sz) for i, sz in enumerate(pool_sizes)]
+    plan = []
+    for tr in trs:
+        g, u = global_counts(tr)
+        kx = 8 if bits(tr.global_units) > 32 else 4
+        plan.append(16 * tr.n_events + g * (kx + 8) + 8 * u)
+    dts, keep = device_pool(torch, trs, dev)
+    return trs, dts, keep, pool_sizes, plan
+
+
+def serve_arm(args):
+    """Served workload: Poisson arrivals of check jobs (sizes log-uniform 1e4..1e8 records, picked from a
+    pool of device-resident grid- and barrier-family traces), continuous batching under a 120 GB HBM
+    budget, against serial checking; at 200 jobs/s and at a rate beyond saturation."""
+    import torch
+    from paper_1905_01833_gb300 import serve
+    trs, dts, keep, pool_sizes, plan = serve_pool(torch, args.serve_pool, "cuda:0")
+    rng = np.random.default_rng(7)
+    draws = np.exp(rng.uniform(np.log(1e4), np.log(1e8), size=args.serve_jobs))
+    pick = np.abs(np.log(draws)[:, None] - np.log(pool_sizes)[None, :]).argmin(axis=1)
+    peak, _ = peaks()
+
+    def run(rate, serial):
+        arr = serve.poisson_arrivals(rate, args.serve_jobs, seed=11)
+        jobs = [serve.Job(i, dts[int(pick[i])], float(arr[i])) for i in range(args.serve_jobs)]
+        srv = serve.Server(0, hbm_budget=120 << 30, serial=serial, keep_lists=False)
+        out = srv.run(jobs)
+        b = sum(plan[int(pick[i])] for i in range(args.serve_jobs))
+        out["plan_bytes_per_record"] = b / out["events"]
+        out["plan_frac"] = b / out["wall_s"] / (peak * 1e9)
+        del srv
+        torch.cuda.empty_cache()
+        return out
+
+    warm = serve.Server(0, keep_lists=False)
+    warm.run([serve.Job(i, dts[i % len(dts)], 0.0) for i in range(len(dts))])
+    del warm
+    torch.cuda.empty_cache()
+    keys = ("p50_ms", "p99_ms", "max_ms", "batches", "max_batch", "max_inflight", "plan_frac",
+            "plan_bytes_per_record", "jobs", "events", "wall_s")
+    res = {"workload": f"serve: Poisson arrivals, {args.serve_jobs} jobs, sizes log-uniform 1e4..1e8 records "
+                       f"(pool of {len(dts)} device-resident grid / barrier traces), 120 GB budget, up to 3 "
+                       f"batches in flight", "unit": UNIT, "rates": {}}
+    for rate in args.serve_rates:
+        a = run(rate, serial=False)
+        b = run(rate, serial=True)
+        res["rates"][str(int(rate))] = {
+            "batched": {k: a[k] for k in keys} | {"value": a["events_per_s"] / 1e9},
+            "serial": {k: b[k] for k in keys} | {"value": b["events_per_s"] / 1e9}}
+    del dts, keep
+    torch.cuda.empty_cache()
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--path", choices=["auto", "sort"], default="auto")
+    ap.add_argument("--hash-shape", type=int, choices=[0, 1, 2], default=0,
+                    help="hash path CTAs: 0 chosen per call, 1 one 1024-thread CTA per SM, 2 two 512-thread CTAs")
+    ap.add_argument("--graph-replay", choices=["auto", "off"], default="auto",
+                    help="auto: repeated identical calls replayed by the library as one CUDA graph; off: direct launches")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--oracle-blocks", type=int, default=256)
+    ap.add_argument("--ref-stride", type=int, default=64, help="reference arm: every n-th batch member per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="headline: the batched line only")
+    ap.add_argument("--blocks", type=int, default=1024, help="grid blocks (1024 = the single-trace workload; "
+                    "smaller values only for profiling captures)")
+    ap.add_argument("--workload", choices=["headline", "grid", "serve", "fitness", "evolve", "strided", "barrier",
+                                           "warp", "paper"], default="headline",
+                    help="headline: the batched workload with the single-trace and served forms; the others print "
+                         "their own line")
+    ap.add_argument("--batch-traces", type=int, default=4096)
+    ap.add_argument("--serve-jobs", type=int, default=2000)
+    ap.add_argument("--serve-pool", type=int, default=24)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 20000.0])
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    if args.workload not in ("headline", "grid"):
+        import torch
+        torch.cuda.set_device(0)
+        out = {"serve": serve_arm, "fitness": fitness_arm, "evolve": evolve_arm, "strided": single_trace_arm,
+               "barrier": single_trace_arm, "warp": single_trace_arm, "paper": single_trace_arm}[args.workload](args)
+        print(json.dumps({"metric": METRIC, **out}))
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        torch.cuda.set_device(local)
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    if args.workload == "grid":
+        line = grid_arm(args, rank, world, local, dist)
+        out = {"metric": METRIC, "value": line.pop("value"), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": line.pop("ms_per_step"), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+               "config": {"workload": line.pop("workload"), "n_events": line.pop("n_events"),
+                          "parallelism": f"replicas{world}", "path": args.path,
+                          "l2": "inputs larger than L2 (1 GB trace, 129 MB L2); no flush"}, **line}
+        if rank == 0:
+            print(json.dumps(out))
+    else:
+        line = headline(args, rank, world, local, dist)
+        if world == 1 and not args.no_extras:
+            line["single_trace"] = grid_arm(args, rank, world, local, None)
+            line["served"] = serve_arm(args)
+        if rank == 0:
+            print(json.dumps(line))
     if dist:
+        dist.barrier()
         dist.destroy_process_group()
 
 
