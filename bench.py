@@ -273,9 +273,11 @@ def result_digest(res: dict, races_cap: int) -> str:
 
 
 def batch_specs(seed: int, n_traces: int):
-    """Member specs (index, records, block size, epochs, seed) of the batched workload, and its sigma."""
+    """Member specs (index, records, block size, epochs, seed) of the batched workload, and its sigma
+    (fitted to 6e8 records for 4096 traces, in proportion for other counts)."""
     import tracegen
-    sigma = tracegen.c3_sigma(seed=seed, n_traces=n_traces)
+    total = tracegen.C3_RECORDS * n_traces // 4096
+    sigma = tracegen.c3_sigma(seed=seed, n_traces=n_traces, total=total)
     sizes, bss, eps = tracegen.c3_sizes(seed=seed, n_traces=n_traces, sigma=sigma)
     return [(i, int(n), int(b), int(e), seed) for i, (n, b, e) in enumerate(zip(sizes, bss, eps))], sigma
 
@@ -547,7 +549,8 @@ def headline(args, rank: int, world: int, local: int, dist):
     stream = torch.cuda.current_stream()
     # parity call: generous race capacities; its counts size the lists of the timed calls
     run = BatchRun(torch, dts, dev, [(race_cap_for(d.n_events), d.n_blocks, d.n_blocks * max(d.max_barriers, 1),
-                                      max(d.max_barriers, 1)) for d in dts])
+                                      max(d.max_barriers, 1)) for d in dts],
+                   graph_replay=simulee.GRAPH_OFF if args.graph_replay == "off" else simulee.GRAPH_AUTO)
     run.call(stream)
     torch.cuda.synchronize()
     first = run.results()

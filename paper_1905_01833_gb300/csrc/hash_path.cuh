@@ -37,15 +37,16 @@ namespace simk {
 
 // Two shapes: one CTA of 1024 threads per SM with 8192-entry run tables, or
 // two CTAs of 512 threads per SM with 4096-entry tables (so that one CTA's
-// barriers overlap the other's work). A run may hold up to 3/4 of a table's
-// entries in distinct units.
+// barriers overlap the other's work). A run may hold up to 7/8 of a table's
+// entries in distinct units (runs near that load are rare and only probe longer;
+// a run beyond it sends its block to the sort path).
 template <int THREADS, int SLOTS>
 struct HbShape {
     static constexpr int threads = THREADS;
     static constexpr int slots = SLOTS;
     static constexpr int ctas_per_sm = 1024 / THREADS;
     static constexpr int window = 2 * THREADS;        // records per window (two per thread)
-    static constexpr int cap = SLOTS / 4 * 3;         // distinct units per run
+    static constexpr int cap = SLOTS / 8 * 7;         // distinct units per run
     static constexpr int shift = SLOTS == 8192 ? 19 : 20;   // 32 - log2(SLOTS)
     static constexpr int pool = SLOTS / 3;            // racy units per run (24-byte summaries in 8-byte entries)
 };
@@ -235,6 +236,11 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                 const uint32_t idx = wbase + j * SH::threads + tid;
                 const bool in = idx < s1, fresh = in && idx >= vmark;
                 const uint4 e = cur[j];
+                if (!__any_sync(0xFFFFFFFFu, fresh)) {   // the warp's records here were validated before
+                    if (in && e.z == lb) pb |= 1u << j;
+                    isx[j] = false;
+                    continue;
+                }
                 const uint32_t u = e.x, vo = e.y, blk = e.z, w3 = e.w;
                 const uint32_t tt = w3 & 0xFFFFu, ep = (w3 >> 16) & 0xFFFu, act = (w3 >> 28) & 3u;
                 const uint32_t sp = (w3 >> 30) & 1u, resv = w3 >> 31;

@@ -362,15 +362,36 @@ struct Run {
     }
 };
 
-// descriptors reach the device through kernel parameters (no host staging buffer)
+// Descriptors reach the device through kernel parameters (no host staging buffer, so a captured
+// launch sequence carries them). The parameter block is read in place (__grid_constant__: no
+// per-thread copy of it), one 4-byte word per thread.
 constexpr int kDescChunk = 180;
+constexpr int kDescWords = (int)(sizeof(TraceDesc) / 4);
+static_assert(sizeof(TraceDesc) % 4 == 0, "descriptor words");
 struct DescChunk {
-    TraceDesc d[kDescChunk];
+    uint32_t w[kDescChunk * kDescWords];
 };
 static_assert(sizeof(DescChunk) + 16 < 32000, "descriptor chunk must fit the kernel parameter space");
+constexpr int kDescThreads = 256;
 
-__global__ void k_set_desc(TraceDesc *dst, DescChunk chunk, uint32_t count) {
-    if (threadIdx.x < count) dst[threadIdx.x] = chunk.d[threadIdx.x];
+__global__ void k_set_desc(uint32_t *dst, const __grid_constant__ DescChunk chunk, uint32_t words) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x)
+        dst[i] = chunk.w[i];
+}
+
+// upload descriptors [0, T) to td on `st`; returns the launches issued
+uint32_t upload_descs(TraceDesc *td, const std::vector<TraceDesc> &h, uint32_t T, cudaStream_t st) {
+    uint32_t launches = 0;
+    for (uint32_t i = 0; i < T; i += kDescChunk) {
+        DescChunk c;
+        const uint32_t cnt = std::min<uint32_t>(kDescChunk, T - i);
+        memcpy(c.w, h.data() + i, cnt * sizeof(TraceDesc));
+        const uint32_t words = cnt * kDescWords;
+        k_set_desc<<<(words + kDescThreads - 1) / kDescThreads, kDescThreads, 0, st>>>(
+            reinterpret_cast<uint32_t *>(td + i), c, words);
+        launches++;
+    }
+    return launches;
 }
 
 // schedule-rank sort input: key (trace, visit order), value = batch-wide record index
@@ -561,13 +582,7 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
     uint32_t *fbt = R.at<uint32_t>(L.off_fbt);
     uint32_t *sig = L.sig_slots ? R.at<uint32_t>(L.off_sig) : nullptr;
     if (sig && (want.races || want.red)) cudaMemsetAsync(sig, 0, L.sig_slots * 4, st);
-    for (uint32_t i = 0; i < T; i += kDescChunk) {
-        DescChunk c;
-        const uint32_t cnt = std::min<uint32_t>(kDescChunk, T - i);
-        memcpy(c.d, hdesc.data() + i, cnt * sizeof(TraceDesc));
-        k_set_desc<<<1, kDescChunk, 0, st>>>(td + i, c, cnt);
-        R.launches++;
-    }
+    R.launches += upload_descs(td, hdesc, T, st);
     k_block_trace<<<R.grid_for(L.NB, 256, 8), 256, 0, st>>>(td, L, tob);
     // 2. barrier counts
     k_block_stats<<<R.grid_for(L.NB, 8, 16), 256, 0, st>>>(td, tob, L, R.at<uint4>(L.off_stats), ts);
@@ -1023,13 +1038,7 @@ simulee_status run_fitness(simulee_ctx *ctx, const simulee_trace *traces, uint32
     std::vector<uint8_t *> no_rep(T, nullptr);
     std::vector<TraceDesc> hdesc;
     fill_descs(traces, no_out.data(), no_rep.data(), T, hdesc);
-    for (uint32_t i = 0; i < T; i += kDescChunk) {
-        DescChunk c;
-        const uint32_t cnt = std::min<uint32_t>(kDescChunk, T - i);
-        memcpy(c.d, hdesc.data() + i, cnt * sizeof(TraceDesc));
-        k_set_desc<<<1, kDescChunk, 0, st>>>(td + i, c, cnt);
-        launches++;
-    }
+    launches += upload_descs(td, hdesc, T, st);
     k_fit_init<<<grid_for(T, 256, 1), 256, 0, st>>>(acc, T);
     k_block_trace<<<grid_for(L.NB, 256, 8), 256, 0, st>>>(td, L, tob);
     k_block_stats<<<grid_for(L.NB, 8, 16), 256, 0, st>>>(td, tob, L, reinterpret_cast<uint4 *>(w + P.off_stats), ts);
