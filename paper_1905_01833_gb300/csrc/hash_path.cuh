@@ -40,18 +40,22 @@ namespace simk {
 // barriers overlap the other's work). A run may hold up to 7/8 of a table's
 // entries in distinct units (runs near that load are rare and only probe longer;
 // a run beyond it sends its block to the sort path).
-template <int THREADS, int SLOTS>
+template <int THREADS, int SLOTS, int PER, int CTAS>
 struct HbShape {
     static constexpr int threads = THREADS;
     static constexpr int slots = SLOTS;
-    static constexpr int ctas_per_sm = 1024 / THREADS;
-    static constexpr int window = 2 * THREADS;        // records per window (two per thread)
+    static constexpr int ctas_per_sm = CTAS;
+    static constexpr int per = PER;                   // records per thread per window
+    static constexpr int window = PER * THREADS;      // records per window
     static constexpr int cap = SLOTS / 8 * 7;         // distinct units per run
     static constexpr int shift = SLOTS == 8192 ? 19 : 20;   // 32 - log2(SLOTS)
     static constexpr int pool = SLOTS / 3;            // racy units per run (24-byte summaries in 8-byte entries)
 };
-using HbLarge = HbShape<1024, 8192>;
-using HbSmall = HbShape<512, 4096>;
+// Two records per thread per window: with four per thread and half the threads (the same tables and
+// windows, twice the registers per thread) the kernel ran 40% slower, 16 warps per SM hiding too little
+// of the shared-memory and global latencies.
+using HbLarge = HbShape<1024, 8192, 2, 1>;
+using HbSmall = HbShape<512, 4096, 2, 2>;
 static_assert((HbLarge::cap + HbLarge::threads - 1) / HbLarge::threads <= 32, "list entries per thread");
 static_assert((HbSmall::cap + HbSmall::threads - 1) / HbSmall::threads <= 32, "list entries per thread");
 
@@ -218,10 +222,11 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         //      starts at the run's first record; records below vmark are already validated and
         //      routed (a window that starts inside the previous one re-reads them from cache).
         uint32_t wbase = s0, vmark = s0;
-        uint4 cur[2], nxt[2];
-        auto load = [&](uint4 (&w)[2], uint32_t base) {
+        constexpr int P = SH::per;
+        uint4 cur[P], nxt[P];
+        auto load = [&](uint4 (&w)[P], uint32_t base) {
 #pragma unroll
-            for (int j = 0; j < 2; j++) {
+            for (int j = 0; j < P; j++) {
                 const uint32_t i = base + j * SH::threads + tid;
                 w[j] = i < s1 ? ev[i] : make_uint4(0, 0, 0, 0);
             }
@@ -230,9 +235,9 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         // records of this block (those to hash)
         auto activate = [&]() -> uint32_t {
             uint32_t pb = 0;
-            bool stopme = false, isx[2];
+            bool stopme = false, isx[P];
 #pragma unroll
-            for (int j = 0; j < 2; j++) {
+            for (int j = 0; j < P; j++) {
                 const uint32_t idx = wbase + j * SH::threads + tid;
                 const bool in = idx < s1, fresh = in && idx >= vmark;
                 const uint4 e = cur[j];
@@ -263,8 +268,12 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                 if (in && blk == lb && (ok || !fresh)) pb |= 1u << j;
                 isx[j] = ok && sp == 1u && ep <= maxb;
             }
-            const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, isx[0]), b1 = __ballot_sync(0xFFFFFFFFu, isx[1]);
-            const uint32_t tot = __popc(b0) + __popc(b1);
+            uint32_t bal[P], tot = 0;
+#pragma unroll
+            for (int j = 0; j < P; j++) {
+                bal[j] = __ballot_sync(0xFFFFFFFFu, isx[j]);
+                tot += __popc(bal[j]);
+            }
             if (tot) {
                 if (xpos + tot > xend) {   // warp-uniform: a fresh chunk of slots for this warp
                     hb_x_fill(xk, xv, xpos, xend, xcap, lane);
@@ -274,11 +283,14 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                     xpos = nbase;
                     xend = nbase + HB_XCH;
                 }
+                uint32_t before = 0;   // this warp's X records of the items before item j
 #pragma unroll
-                for (int j = 0; j < 2; j++) {
+                for (int j = 0; j < P; j++) {
+                    const uint32_t bj = bal[j];
+                    const uint32_t o = xpos + before + __popc(bj & lt);
+                    before += __popc(bj);
                     if (!isx[j]) continue;
                     const uint4 e = cur[j];
-                    const uint32_t o = xpos + (j ? __popc(b0) + __popc(b1 & lt) : __popc(b0 & lt));
                     const uint32_t blk = e.z, w3 = e.w, act = (w3 >> 28) & 3u;
                     const uint32_t xo = pad ? ((blk << 10) | (w3 & 0x3FFu)) : blk * bt + (w3 & 0xFFFFu);
                     if (o < xcap) {
@@ -320,7 +332,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                 if (more) load(nxt, wend);
                 uint32_t first = HB_NONE;   // the window's first record after the run
 #pragma unroll
-                for (int j = 0; j < 2; j++) {
+                for (int j = 0; j < P; j++) {
                     const uint4 r = cur[j];
                     const uint32_t idx = wbase + j * SH::threads + tid;
                     const uint32_t ep = (r.w >> 16) & 0xFFFu;
@@ -376,8 +388,8 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                 if (lane == 0 && first != HB_NONE) atomicMin(&s_first[par], first);
                 if (more) {
                     wbase = wend;
-                    cur[0] = nxt[0];
-                    cur[1] = nxt[1];
+#pragma unroll
+                    for (int j = 0; j < P; j++) cur[j] = nxt[j];
                     pend = activate();
                     continue;
                 }
