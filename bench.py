@@ -548,9 +548,20 @@ def headline(args, rank: int, world: int, local: int, dist):
     n_ev = sum(d.n_events for d in dts)
     stream = torch.cuda.current_stream()
     # parity call: generous race capacities; its counts size the lists of the timed calls
+    # launch choices (radix width and tile, hash-vs-sort cutover, CTA shapes and counts) from the autotuner
+    tune_info, tuned = None, {}
+    if not args.no_autotune:
+        from paper_1905_01833_gb300 import autotune
+        t0 = time.perf_counter()
+        tuner = autotune.Autotuner(local, cache_path=args.autotune_cache)
+        tuned = tuner.best_batch(dts, races_caps=[race_cap_for(d.n_events) for d in dts])
+        hit = tuner.cache.get(tuner.batch_key(dts), {})
+        tune_info = {"options": tuned, "bucket": tuner.batch_key(dts), "tuned_ms": hit.get("ms"),
+                     "default_ms": hit.get("default_ms"), "evaluated": hit.get("evaluated"),
+                     "seconds": time.perf_counter() - t0}
     run = BatchRun(torch, dts, dev, [(race_cap_for(d.n_events), d.n_blocks, d.n_blocks * max(d.max_barriers, 1),
                                       max(d.max_barriers, 1)) for d in dts],
-                   graph_replay=simulee.GRAPH_OFF if args.graph_replay == "off" else simulee.GRAPH_AUTO)
+                   **dict(tuned, graph_replay=simulee.GRAPH_OFF if args.graph_replay == "off" else simulee.GRAPH_AUTO))
     run.call(stream)
     torch.cuda.synchronize()
     first = run.results()
@@ -629,7 +640,7 @@ def headline(args, rank: int, world: int, local: int, dist):
         arr2[i] = c
     arrs = [run.arr, arr2]
     d_ev, d_cn = [keep[0], ev2], [keep[1], cn2]
-    chks = [run.chk, simulee.Checker(local)]
+    chks = [run.chk, simulee.Checker(local, **tuned)]
     copy_s = torch.cuda.Stream(device=dev)
     copied = [torch.cuda.Event() for _ in range(2)]
     freed = [torch.cuda.Event() for _ in range(2)]
@@ -733,6 +744,8 @@ def headline(args, rank: int, world: int, local: int, dist):
                     "n_redundant": int(sum(c[2] for c in counts)), "n_grid_redundant": int(sum(c[3] for c in counts))},
         "clocks": clocks,
     }
+    if tune_info:
+        line["autotune"] = tune_info
     if oracle_line:
         line["cpu_baseline"] = oracle_line
     if parity:
@@ -1177,10 +1190,15 @@ def serve_arm(args):
     pick = np.abs(np.log(draws)[:, None] - np.log(pool_sizes)[None, :]).argmin(axis=1)
     peak, _ = peaks()
 
+    opts = {}
+    if not args.no_autotune:
+        from paper_1905_01833_gb300 import autotune
+        opts = autotune.Autotuner(0, cache_path=args.autotune_cache).best_batch(dts)
+
     def run(rate, serial):
         arr = serve.poisson_arrivals(rate, args.serve_jobs, seed=11)
         jobs = [serve.Job(i, dts[int(pick[i])], float(arr[i])) for i in range(args.serve_jobs)]
-        srv = serve.Server(0, hbm_budget=120 << 30, serial=serial, keep_lists=False)
+        srv = serve.Server(0, hbm_budget=120 << 30, serial=serial, keep_lists=False, options=opts)
         out = srv.run(jobs)
         b = sum(plan[int(pick[i])] for i in range(args.serve_jobs))
         out["plan_bytes_per_record"] = b / out["events"]
@@ -1197,7 +1215,7 @@ def serve_arm(args):
             "plan_bytes_per_record", "jobs", "events", "wall_s")
     res = {"workload": f"serve: Poisson arrivals, {args.serve_jobs} jobs, sizes log-uniform 1e4..1e8 records "
                        f"(pool of {len(dts)} device-resident grid / barrier traces), 120 GB budget, up to 3 "
-                       f"batches in flight", "unit": UNIT, "rates": {}}
+                       f"batches in flight", "unit": UNIT, "options": opts, "rates": {}}
     for rate in args.serve_rates:
         a = run(rate, serial=False)
         b = run(rate, serial=True)
@@ -1225,6 +1243,8 @@ def main():
     ap.add_argument("--ref-stride", type=int, default=64, help="reference arm: every n-th batch member per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline: the batched line only")
+    ap.add_argument("--no-autotune", action="store_true", help="headline: the library's default launch choices")
+    ap.add_argument("--autotune-cache", default=None, help="autotuner cache file (default: the user's cache)")
     ap.add_argument("--blocks", type=int, default=1024, help="grid blocks (1024 = the single-trace workload; "
                     "smaller values only for profiling captures)")
     ap.add_argument("--workload", choices=["headline", "grid", "serve", "fitness", "evolve", "strided", "barrier",

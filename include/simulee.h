@@ -188,6 +188,14 @@ typedef struct {
                                  8192-entry run tables (up to 6144 distinct units per run), 2 = two
                                  512-thread CTAs per SM with 4096-entry tables (up to 3072) */
     uint32_t graph_replay;    /* simulee_graph_replay */
+    uint32_t sort_items;      /* radix-sort tile: 256 threads x sort_items elements; 0 = 16, or 8 */
+    uint32_t radix_bits;      /* digit width of each radix pass: 0 = 8, or 6 or 11 (those widths build
+                                 their digit histograms in one extra read of the stream's keys) */
+    uint32_t hash_cap_eighths;   /* hash path: a run may hold up to this many eighths of its table in
+                                    distinct units before its block goes to the sort path; 0 = 7, or 4..7 */
+    uint32_t hash_pool_div;   /* hash path: a run's racy units are resolved in place up to table size /
+                                 hash_pool_div of them, beyond that the run goes to the sort path;
+                                 0 = 3, or 3..64 */
 } simulee_options;
 
 /* Repeated calls. With SIMULEE_GRAPH_AUTO, a check call (simulee_check*, simulee_check_batch,

@@ -37,7 +37,10 @@ constexpr uint32_t STMT_DIVERGED = 0x80000000u;
 constexpr uint64_t EMPTY = ~0ull;
 constexpr int RADIX_BITS = 8;
 constexpr int RADIX = 1 << RADIX_BITS;
-constexpr int MAX_PASSES = 40;   // all sort passes of one call
+constexpr int MAX_PASSES = 40;   // sort passes of one call over 8-bit digits (histograms from the record reads)
+constexpr int W_PASSES = 64;     // sort passes of one call over digits of another width (own histograms)
+constexpr int W_SLOT_PASSES = 11;   // passes of one stream at the narrowest width (64-bit keys, 6 bits)
+constexpr int W_RADIX_MAX = 2048;   // digits of the widest width (11 bits)
 
 // One trace of a call (a single-trace call is a batch of one). Device array
 // in the workspace, written by the host side of the call.
@@ -84,6 +87,7 @@ struct Ctl {
     unsigned int n_rf;            // race records left by the race filter
     unsigned int px_tile;         // next tile of the visit-order scan
     unsigned int tiles[MAX_PASSES];  // onesweep tile counters, one per pass
+    unsigned int wtiles[W_PASSES];   // the same for passes over digits of another width
 };
 
 // Batch-wide dimensions, bit layouts and workspace offsets of one call (host-computed).
@@ -106,6 +110,11 @@ struct Layout {
     uint32_t words;                  // 32-bit words per block in the barrier bitmaps
     uint64_t race_cap;               // staging capacity for race records
     uint64_t status_tiles;           // tiles covered by the look-back status array
+    uint32_t sort_items;             // radix-sort tile: 256 threads x this many elements (8 or 16)
+    uint32_t radix_bits;             // digit width of the radix passes (6, 8 or 11)
+    uint32_t hb_cap_eighths;         // hash path: distinct units a run may hold, in eighths of its table
+    uint32_t hb_pool_div;            // hash path: racy units resolved in place per run, table size / this
+    size_t off_hw, off_dw;           // histograms and digit bases of passes not 8 bits wide, per stream
     size_t off_binel;                // per batch-wide block: the hash path does not apply to it
     size_t off_spill;                // per block and epoch: a run the hash path leaves to the sort path
     size_t off_tflag;                // per ingest tile: holds a spilled run

@@ -39,7 +39,9 @@ namespace simk {
 // two CTAs of 512 threads per SM with 4096-entry tables (so that one CTA's
 // barriers overlap the other's work). A run may hold up to 7/8 of a table's
 // entries in distinct units (runs near that load are rare and only probe longer;
-// a run beyond it sends its block to the sort path).
+// a run beyond it sends its block to the sort path); the options of a call may
+// lower that cutover (4/8 to 7/8) and the racy-unit pool (table / 3 down to
+// table / 64).
 template <int THREADS, int SLOTS, int PER, int CTAS>
 struct HbShape {
     static constexpr int threads = THREADS;
@@ -199,6 +201,9 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
     }
     const uint64_t xcap = L.x_cap;
     uint32_t xpos = 0, xend = 0;   // this warp's reserved inter-block slots [xpos, xend)
+    // the cutover to the sort path chosen for the call: distinct units per run, racy units per run
+    const uint32_t cap_rt = min((uint32_t)SH::cap, (uint32_t)SH::slots / 8u * L.hb_cap_eighths);
+    const uint32_t pool_rt = min((uint32_t)SH::pool, (uint32_t)SH::slots / L.hb_pool_div);
     for (;;) {
         __syncthreads();
         if (tid == 0) s_blk = atomicAdd(queue, 1u);
@@ -379,7 +384,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                         base = __shfl_sync(0xFFFFFFFFu, base, leader);
                         if (created) {
                             const uint32_t pos = base + __popc(cm & lt);
-                            if (pos < SH::cap) list[par * SH::cap + pos] = (uint16_t)s;
+                            if (pos < cap_rt) list[par * SH::cap + pos] = (uint16_t)s;
                             else s_flag = 2u;   // more distinct units than listed entries
                         }
                     }
@@ -436,7 +441,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             __syncthreads();   // B
             const uint32_t nracy = s_nracy[par];
             if (!stop && nracy > 0) {
-                if (nracy > (uint32_t)SH::pool || hi - lo >= HB_POS_LIMIT) {
+                if (nracy > pool_rt || hi - lo >= HB_POS_LIMIT) {
                     // too many racy units: the sort path computes this run's races
                     if (tid == 0) {
                         atomicOr(&spill[(uint64_t)b * L.swords + (e >> 5)], 1u << (e & 31));

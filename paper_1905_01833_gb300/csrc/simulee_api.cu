@@ -90,6 +90,9 @@ simulee_status check_trace_args(const simulee_trace *t) {
     return SIMULEE_OK;
 }
 
+// digits per tile in the look-back status array: the widest of the call's passes
+uint32_t status_digits(const Layout &L) { return std::max<uint32_t>(RADIX, 1u << L.radix_bits); }
+
 // How make_layout sizes the record streams and the race staging.
 //   FULL:    for the worst case (every record on the sort path, every group racing): never overflows.
 //   COMPACT: the query of a compact workspace: streams hold the records of traces that take the sort
@@ -101,8 +104,8 @@ enum class Sizing { FULL, COMPACT, FIT };
 // Batch-wide bit layouts, pass counts and workspace offsets (a single trace is a batch of one).
 // sort_all: every trace takes the sort path (the options force it). avail: the caller's workspace
 // bytes (Sizing::FIT).
-simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout &L, Sizing sizing = Sizing::FULL,
-                           bool sort_all = false, size_t avail = 0) {
+simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, const simulee_options &opt, Layout &L,
+                           Sizing sizing = Sizing::FULL, bool sort_all = false, size_t avail = 0) {
     memset(&L, 0, sizeof L);
     if (T == 0 || T > kMaxTraces) return SIMULEE_EINVAL;
     uint64_t n = 0, nb = 0, tiles = 0;
@@ -161,6 +164,10 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout 
     if (L.p0_q + L.np_q > MAX_PASSES || L.np_s + L.np_g + L.np_x > IN_MAXP) return SIMULEE_EINVAL;
     L.words = std::max<uint32_t>(1, (maxb + 31) / 32);
     const uint64_t n1 = std::max<uint64_t>(L.n, 1);
+    L.sort_items = opt.sort_items ? opt.sort_items : 16u;
+    L.radix_bits = opt.radix_bits ? opt.radix_bits : (uint32_t)RADIX_BITS;
+    L.hb_cap_eighths = opt.hash_cap_eighths ? opt.hash_cap_eighths : 7u;
+    L.hb_pool_div = opt.hash_pool_div ? opt.hash_pool_div : 3u;
 
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes); return r; };
@@ -175,7 +182,12 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout 
     L.swords = maxb / 32 + 1;
     L.off_spill = take((size_t)L.NB * L.swords * 4);
     L.off_tflag = take((size_t)std::max<uint64_t>(L.ntiles_in, 1) * 4);
+    // histograms of passes over digits of another width than 8 bits: one region per stream (S, G, X,
+    // races, schedule ranks)
+    const size_t w_region = (size_t)5 * W_SLOT_PASSES * W_RADIX_MAX * 4;
+    if (L.radix_bits != (uint32_t)RADIX_BITS) L.off_hw = take(w_region);
     L.zero_end = o;
+    if (L.radix_bits != (uint32_t)RADIX_BITS) L.off_dw = take(w_region);
     L.off_bstart = take((size_t)L.NB * 4);
     L.off_blist = take((size_t)L.NB * 4);
     L.off_fbt = take((size_t)std::max<uint64_t>(L.ntiles_in, 1) * 4);
@@ -227,8 +239,9 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, Layout 
         M.cap_x1 = cx;
         M.race_cap = cr;
         const uint64_t sort_max = std::max<uint64_t>(std::max<uint64_t>(cs, cx), std::max<uint64_t>(cr, uns ? n1 : 0));
-        M.status_tiles = (sort_max + OS_TILE - 1) / OS_TILE;
-        M.off_status = tk((size_t)M.status_tiles * RADIX * 8);
+        const uint64_t tile = (uint64_t)OS_THREADS * M.sort_items;
+        M.status_tiles = (sort_max + tile - 1) / tile;
+        M.off_status = tk((size_t)M.status_tiles * status_digits(M) * 8);
         for (int i = 0; i < 2; i++) {
             M.off_sk[i] = tk(cs * ks);
             M.off_sv[i] = tk(cs * 8);
@@ -332,29 +345,86 @@ struct Run {
         if (ctx->stage_on) cudaEventRecord(ctx->stage_ev[2 * stage + end], st);
     }
 
-    int sort_grid(uint64_t n_max) const {
-        const uint64_t tiles = (n_max + OS_TILE - 1) / OS_TILE;
-        const uint64_t per_sm = ctx->opt.sort_ctas_per_sm ? ctx->opt.sort_ctas_per_sm : 3u;
+    int sort_grid(uint64_t n_max, uint32_t bits) const {
+        const uint64_t tile = (uint64_t)OS_THREADS * L.sort_items;
+        const uint64_t tiles = (n_max + tile - 1) / tile;
+        // the 11-bit passes hold one CTA per SM (their per-digit shared arrays)
+        const uint64_t per_sm = bits > 8 ? 1u : (ctx->opt.sort_ctas_per_sm ? ctx->opt.sort_ctas_per_sm : 3u);
         return (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)ctx->sms * per_sm));
     }
 
-    // LSD sort of (key, value) pairs that start in buffer `start` of 0/1; returns the buffer
-    // holding the result.
-    template <class K>
-    int sort(size_t koff[2], size_t voff[2], const uint32_t *n_ptr, uint64_t n_max, uint32_t np, uint32_t p0,
-             int start = 0, uint32_t tile_cap = 0) {
-        const int grid = sort_grid(n_max);
+    uint32_t wpass = 0;   // passes issued over digits of another width (their tile counters and tags)
+
+    template <class K, int ITEMS, int BITS>
+    void pass(int grid, const K *kin, const uint64_t *vin, K *kout, uint64_t *vout, const uint32_t *n_ptr,
+              uint64_t n_max, uint32_t shift, const uint32_t *dbase, uint32_t tag, uint32_t *ctr, uint32_t tile_cap) {
+        const uint32_t wh = first_pass_done ? 0u : withhold;
+        first_pass_done = true;
+        if (!attr_done(ctx, k_onesweep<K, ITEMS, BITS>))
+            cudaFuncSetAttribute(k_onesweep<K, ITEMS, BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)onesweep_smem<K, ITEMS, BITS>());
+        k_onesweep<K, ITEMS, BITS><<<grid, OS_THREADS, onesweep_smem<K, ITEMS, BITS>(), st>>>(
+            kin, vin, kout, vout, n_ptr, n_max, shift, dbase, at<unsigned long long>(L.off_status), tag, ctr, ctl,
+            wait_ns, wh, tile_cap);
+        launches++;
+    }
+
+    // the passes of one sort over BITS-bit digits with tiles of 256 x ITEMS; 8-bit digits take their
+    // histograms from the record reads (passes p0.. of the call), other widths count them first
+    template <class K, int ITEMS, int BITS>
+    int sort_w(size_t koff[2], size_t voff[2], const uint32_t *n_ptr, uint64_t n_max, uint32_t key_bits, uint32_t p0,
+               int start, uint32_t tile_cap, uint32_t slot) {
+        const uint32_t np = (key_bits + BITS - 1) / BITS;
+        if (np == 0) return start;
+        const int grid = sort_grid(n_max, BITS);
+        const uint32_t *dbase;
+        constexpr uint32_t R = 1u << BITS;
+        if (BITS == RADIX_BITS) {
+            dbase = at<uint32_t>(L.off_dbase) + (size_t)p0 * RADIX;
+        } else {
+            uint32_t *hw = at<uint32_t>(L.off_hw) + (size_t)slot * W_SLOT_PASSES * W_RADIX_MAX;
+            uint32_t *dw = at<uint32_t>(L.off_dw) + (size_t)slot * W_SLOT_PASSES * W_RADIX_MAX;
+            k_hist_keys<K, BITS><<<grid_for(n_max, (uint64_t)OS_THREADS * 16, 4), 256, np * R * 4, st>>>(
+                at<K>(koff[start]), n_ptr, n_max, np, hw, ctl);
+            k_digit_bases_w<BITS><<<np, OS_THREADS, 0, st>>>(hw, dw);
+            launches += 2;
+            dbase = dw;
+        }
         for (uint32_t p = 0; p < np; p++) {
             const int src = (start + (int)p) & 1, dst = src ^ 1;
-            const uint32_t wh = first_pass_done ? 0u : withhold;
-            first_pass_done = true;
-            k_onesweep<K><<<grid, OS_THREADS, onesweep_smem<K>(), st>>>(
-                at<K>(koff[src]), at<uint64_t>(voff[src]), at<K>(koff[dst]), at<uint64_t>(voff[dst]), n_ptr, n_max,
-                RADIX_BITS * p, at<uint32_t>(L.off_dbase) + (size_t)(p0 + p) * RADIX,
-                at<unsigned long long>(L.off_status), p0 + p + 1, &ctl->tiles[p0 + p], ctl, wait_ns, wh, tile_cap);
-            launches++;
+            uint32_t tag, *ctr;
+            if (BITS == RADIX_BITS) {
+                tag = p0 + p + 1;
+                ctr = &ctl->tiles[p0 + p];
+            } else {
+                tag = MAX_PASSES + 1 + wpass;
+                ctr = &ctl->wtiles[wpass];
+                wpass++;
+            }
+            pass<K, ITEMS, BITS>(grid, at<K>(koff[src]), at<uint64_t>(voff[src]), at<K>(koff[dst]), at<uint64_t>(voff[dst]),
+                                 n_ptr, n_max, BITS * p, dbase + (size_t)p * R, tag, ctr, tile_cap);
         }
         return (start + (int)np) & 1;
+    }
+
+    // LSD sort of (key, value) pairs that start in buffer `start` of 0/1; returns the buffer holding the
+    // result. key_bits: the bits in use; p0: the first of the call's 8-bit passes for this stream; slot:
+    // the stream's histogram region for other digit widths.
+    template <class K>
+    int sort(size_t koff[2], size_t voff[2], const uint32_t *n_ptr, uint64_t n_max, uint32_t key_bits, uint32_t p0,
+             int start, uint32_t tile_cap, uint32_t slot) {
+        const bool small = L.sort_items == 8;
+        switch (L.radix_bits) {
+            case 6:
+                return small ? sort_w<K, 8, 6>(koff, voff, n_ptr, n_max, key_bits, p0, start, tile_cap, slot)
+                             : sort_w<K, 16, 6>(koff, voff, n_ptr, n_max, key_bits, p0, start, tile_cap, slot);
+            case 11:
+                return small ? sort_w<K, 8, 11>(koff, voff, n_ptr, n_max, key_bits, p0, start, tile_cap, slot)
+                             : sort_w<K, 16, 11>(koff, voff, n_ptr, n_max, key_bits, p0, start, tile_cap, slot);
+            default:
+                return small ? sort_w<K, 8, 8>(koff, voff, n_ptr, n_max, key_bits, p0, start, tile_cap, slot)
+                             : sort_w<K, 16, 8>(koff, voff, n_ptr, n_max, key_bits, p0, start, tile_cap, slot);
+        }
     }
 
     int grid_for(uint64_t items, uint64_t per_cta, uint64_t max_per_sm) const {
@@ -498,7 +568,8 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
     if (((uintptr_t)ws & 255u) != 0) return SIMULEE_EINVAL;
     Run R;
     R.ctx = ctx;
-    simulee_status s = make_layout(traces, T, ctx->sms, R.L, Sizing::FIT, ctx->opt.path == SIMULEE_PATH_SORT, ws_bytes);
+    simulee_status s =
+        make_layout(traces, T, ctx->sms, ctx->opt, R.L, Sizing::FIT, ctx->opt.path == SIMULEE_PATH_SORT, ws_bytes);
     if (s != SIMULEE_OK) return s;
     if (ws_bytes < R.L.total) return SIMULEE_ENOMEM;
     std::vector<TraceDesc> hdesc;
@@ -575,7 +646,7 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
     // 1. zero control state, upload descriptors
     R.mark(SIMULEE_STAGE_INGEST, 0);
     cudaMemsetAsync(R.ws, 0, L.zero_end, st);
-    cudaMemsetAsync(R.ws + L.off_status, 0, (size_t)L.status_tiles * RADIX * 8, st);
+    cudaMemsetAsync(R.ws + L.off_status, 0, (size_t)L.status_tiles * status_digits(L) * 8, st);
     uint32_t *binel = R.at<uint32_t>(L.off_binel);
     uint32_t *spill = R.at<uint32_t>(L.off_spill);
     uint32_t *tflag = R.at<uint32_t>(L.off_tflag);
@@ -618,8 +689,8 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
             k_digit_bases<<<L.np_q, RADIX, 0, st>>>(hq, dq, R.ctl);
             k_set_count<<<1, 1, 0, st>>>(&R.ctl->n_q, (unsigned int)L.n);
             R.launches += 3;
-            const int b = L.wide_q ? R.sort<uint64_t>(qk, qv, &R.ctl->n_q, L.n, L.np_q, L.p0_q)
-                                   : R.sort<uint32_t>(qk, qv, &R.ctl->n_q, L.n, L.np_q, L.p0_q);
+            const int b = L.wide_q ? R.sort<uint64_t>(qk, qv, &R.ctl->n_q, L.n, L.bits_q, L.p0_q, 0, 0, 4)
+                                   : R.sort<uint32_t>(qk, qv, &R.ctl->n_q, L.n, L.bits_q, L.p0_q, 0, 0, 4);
             if (L.wide_q)
                 k_rank_scatter<uint64_t><<<g, 256, 0, st>>>(R.at<uint64_t>(qk[b]), R.at<uint64_t>(qv[b]), L.n, rank,
                                                             pos_to_vo, R.ctl);
@@ -725,10 +796,10 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
                 k_digit_bases<<<L.p0_x, RADIX, 0, st>>>(hist, dbase, R.ctl);
                 R.launches++;
             }
-            bs = L.wide_s ? R.sort<uint64_t>(sk, sv, &R.ctl->n_s, L.cap_s, L.np_s, L.p0_s)
-                          : R.sort<uint32_t>(sk, sv, &R.ctl->n_s, L.cap_s, L.np_s, L.p0_s);
-            bg = L.wide_g ? R.sort<uint64_t>(gk, gv, &R.ctl->n_g, L.cap_s, L.np_g, L.p0_g)
-                          : R.sort<uint32_t>(gk, gv, &R.ctl->n_g, L.cap_s, L.np_g, L.p0_g);
+            bs = L.wide_s ? R.sort<uint64_t>(sk, sv, &R.ctl->n_s, L.cap_s, L.bits_s, L.p0_s, 0, 0, 0)
+                          : R.sort<uint32_t>(sk, sv, &R.ctl->n_s, L.cap_s, L.bits_s, L.p0_s, 0, 0, 0);
+            bg = L.wide_g ? R.sort<uint64_t>(gk, gv, &R.ctl->n_g, L.cap_s, L.bits_g, L.p0_g, 0, 0, 1)
+                          : R.sort<uint32_t>(gk, gv, &R.ctl->n_g, L.cap_s, L.bits_g, L.p0_g, 0, 0, 1);
             const int gp = R.grid_for(L.n, PX_TILE, 4);
             unsigned long long *stw = R.at<unsigned long long>(L.off_status);
 #define SIM_PX(KG, KX)                                                                                            \
@@ -752,8 +823,8 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
                                                         R.ctl);
                 R.launches++;
             }
-            bx = L.wide_x ? R.sort<uint64_t>(xk, xv, &R.ctl->n_xf, L.cap_x1, L.np_x, L.p0_x, 1)
-                          : R.sort<uint32_t>(xk, xv, &R.ctl->n_xf, L.cap_x1, L.np_x, L.p0_x, 1);
+            bx = L.wide_x ? R.sort<uint64_t>(xk, xv, &R.ctl->n_xf, L.cap_x1, L.bits_x, L.p0_x, 1, 0, 2)
+                          : R.sort<uint32_t>(xk, xv, &R.ctl->n_xf, L.cap_x1, L.bits_x, L.p0_x, 1, 0, 2);
         } else {
         // inter-block records of units touched by one block only are dropped before sorting;
         // the filter also builds the inter stream's digit histograms
@@ -765,12 +836,12 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
             k_digit_bases<<<L.p0_r, RADIX, 0, st>>>(hist, R.at<uint32_t>(L.off_dbase), R.ctl);
             R.launches++;
         }
-        bs = L.wide_s ? R.sort<uint64_t>(sk, sv, &R.ctl->n_s, L.cap_s, L.np_s, L.p0_s)
-                      : R.sort<uint32_t>(sk, sv, &R.ctl->n_s, L.cap_s, L.np_s, L.p0_s);
-        bg = L.wide_g ? R.sort<uint64_t>(gk, gv, &R.ctl->n_g, L.cap_s, L.np_g, L.p0_g)
-                      : R.sort<uint32_t>(gk, gv, &R.ctl->n_g, L.cap_s, L.np_g, L.p0_g);
-        bx = L.wide_x ? R.sort<uint64_t>(xk, xv, &R.ctl->n_xf, L.cap_x1, L.np_x, L.p0_x, 1)
-                      : R.sort<uint32_t>(xk, xv, &R.ctl->n_xf, L.cap_x1, L.np_x, L.p0_x, 1);
+        bs = L.wide_s ? R.sort<uint64_t>(sk, sv, &R.ctl->n_s, L.cap_s, L.bits_s, L.p0_s, 0, 0, 0)
+                      : R.sort<uint32_t>(sk, sv, &R.ctl->n_s, L.cap_s, L.bits_s, L.p0_s, 0, 0, 0);
+        bg = L.wide_g ? R.sort<uint64_t>(gk, gv, &R.ctl->n_g, L.cap_s, L.bits_g, L.p0_g, 0, 0, 1)
+                      : R.sort<uint32_t>(gk, gv, &R.ctl->n_g, L.cap_s, L.bits_g, L.p0_g, 0, 0, 1);
+        bx = L.wide_x ? R.sort<uint64_t>(xk, xv, &R.ctl->n_xf, L.cap_x1, L.bits_x, L.p0_x, 1, 0, 2)
+                      : R.sort<uint32_t>(xk, xv, &R.ctl->n_xf, L.cap_x1, L.bits_x, L.p0_x, 1, 0, 2);
         }
     }
     R.mark(SIMULEE_STAGE_SORT, 1);
@@ -803,7 +874,7 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
         R.launches += 2;
         size_t rk[2] = {L.off_rk[0], L.off_rk[1]}, rv[2] = {L.off_rv[0], L.off_rv[1]};
         // race records are few next to the record streams: at most 128 tiles keeps their look-back short
-        const int br = R.sort<uint64_t>(rk, rv, &R.ctl->n_rf, L.race_cap, L.np_r, L.p0_r, 1, 128u);
+        const int br = R.sort<uint64_t>(rk, rv, &R.ctl->n_rf, L.race_cap, L.bits_r, L.p0_r, 1, 128u, 3);
         const int gw = R.grid_for(L.race_cap, 256, 8);
         if (T > 1) {   // one trace: its races start at 0 (the per-trace state is zeroed)
             k_race_starts<<<gw, 256, 0, st>>>(R.at<uint64_t>(rk[br]), L, R.ctl, ts);
@@ -1105,6 +1176,13 @@ simulee_status simulee_create(simulee_ctx **ctx, int device, const simulee_optio
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return SIMULEE_ECUDA;
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return SIMULEE_ECUDA;
+    if (opt) {
+        if (opt->sort_items != 0 && opt->sort_items != 8 && opt->sort_items != 16) return SIMULEE_EINVAL;
+        if (opt->radix_bits != 0 && opt->radix_bits != 6 && opt->radix_bits != 8 && opt->radix_bits != 11)
+            return SIMULEE_EINVAL;
+        if (opt->hash_cap_eighths != 0 && (opt->hash_cap_eighths < 4 || opt->hash_cap_eighths > 7)) return SIMULEE_EINVAL;
+        if (opt->hash_pool_div != 0 && (opt->hash_pool_div < 3 || opt->hash_pool_div > 64)) return SIMULEE_EINVAL;
+    }
     simulee_ctx *c = new (std::nothrow) simulee_ctx();
     if (!c) return SIMULEE_ENOMEM;
     c->device = device;
@@ -1123,7 +1201,7 @@ simulee_status simulee_destroy(simulee_ctx *ctx) {
 simulee_status simulee_workspace_size(simulee_ctx *ctx, const simulee_trace *trace, size_t *bytes) {
     if (!ctx || !trace || !bytes) return SIMULEE_EINVAL;
     Layout L;
-    const simulee_status s = make_layout(trace, 1, ctx->sms, L);
+    const simulee_status s = make_layout(trace, 1, ctx->sms, ctx->opt, L);
     if (s != SIMULEE_OK) return s;
     *bytes = L.total;
     return SIMULEE_OK;
@@ -1134,7 +1212,7 @@ simulee_status simulee_compact_workspace_size(simulee_ctx *ctx, const simulee_tr
     if (!ctx || !traces || !bytes || n_traces == 0) return SIMULEE_EINVAL;
     Layout L;
     const simulee_status s =
-        make_layout(traces, n_traces, ctx->sms, L, Sizing::COMPACT, ctx->opt.path == SIMULEE_PATH_SORT);
+        make_layout(traces, n_traces, ctx->sms, ctx->opt, L, Sizing::COMPACT, ctx->opt.path == SIMULEE_PATH_SORT);
     if (s != SIMULEE_OK) return s;
     *bytes = L.total;
     return SIMULEE_OK;
@@ -1180,7 +1258,7 @@ simulee_status simulee_batch_workspace_size(simulee_ctx *ctx, const simulee_trac
                                             size_t *bytes) {
     if (!ctx || !traces || !bytes || n_traces == 0) return SIMULEE_EINVAL;
     Layout L;
-    const simulee_status s = make_layout(traces, n_traces, ctx->sms, L);
+    const simulee_status s = make_layout(traces, n_traces, ctx->sms, ctx->opt, L);
     if (s != SIMULEE_OK) return s;
     *bytes = L.total;
     return SIMULEE_OK;

@@ -31,8 +31,13 @@ __device__ __forceinline__ uint32_t st_tag(uint64_t s) { return (uint32_t)(s >> 
 __device__ __forceinline__ uint64_t st_flag(uint64_t s) { return (s >> 54) & 3ull; }
 __device__ __forceinline__ uint64_t st_count(uint64_t s) { return s & ((1ull << 54) - 1); }
 
-template <class K>
-constexpr size_t onesweep_smem() { return (size_t)OS_TILE * (sizeof(K) + sizeof(uint64_t)); }
+// Shared memory of one pass: the tile's values and keys, then per digit the global bases, per warp and
+// digit the counts (one column more for invalid lanes), per digit the tile's exclusive offsets.
+template <class K, int ITEMS = OS_ITEMS, int BITS = RADIX_BITS>
+constexpr size_t onesweep_smem() {
+    constexpr size_t R = (size_t)1 << BITS, TILE = (size_t)OS_THREADS * ITEMS;
+    return TILE * 8 + R * 8 + TILE * sizeof(K) + (size_t)OS_WARPS * (R + 1) * 4 + R * 4;
+}
 
 // Block-wide exclusive scan of one value per thread (OS_THREADS threads).
 __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *warp_sums) {
@@ -51,31 +56,37 @@ __device__ __forceinline__ uint32_t block_excl_scan_256(uint32_t v, uint32_t *wa
     return x - v + add;
 }
 
-template <class K>
-__global__ void __launch_bounds__(OS_THREADS, 3)
+// One LSD pass over digits of BITS bits (6 to 11) with tiles of OS_THREADS * ITEMS elements. Each
+// thread owns DPT consecutive digits (one when BITS <= 8) for the per-digit steps: warp offsets,
+// publication, look-back, global bases.
+template <class K, int ITEMS = OS_ITEMS, int BITS = RADIX_BITS>
+__global__ void __launch_bounds__(OS_THREADS, BITS > 8 ? 1 : 3)
 k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__restrict__ kout,
            uint64_t *__restrict__ vout, const uint32_t *n_ptr, uint64_t n_max, uint32_t shift,
            const uint32_t *__restrict__ dbase, unsigned long long *status, uint32_t tag, uint32_t *tile_ctr,
            Ctl *ctl, uint64_t wait_ns, uint32_t withhold, uint32_t tile_cap) {
+    constexpr uint32_t R = 1u << BITS;
+    constexpr int TILE = OS_THREADS * ITEMS;
+    constexpr int DPT = (int)((R + OS_THREADS - 1) / OS_THREADS);
     extern __shared__ __align__(16) uint8_t smem[];
-    K *skeys = reinterpret_cast<K *>(smem);
-    uint64_t *svals = reinterpret_cast<uint64_t *>(smem + (size_t)OS_TILE * sizeof(K));
-    __shared__ uint32_t whist[OS_WARPS][RADIX + 1];
-    __shared__ uint32_t texcl[RADIX];
-    __shared__ uint64_t gbase[RADIX];
+    uint64_t *svals = reinterpret_cast<uint64_t *>(smem);                 // [TILE]
+    uint64_t *gbase = svals + TILE;                                        // [R]
+    K *skeys = reinterpret_cast<K *>(gbase + R);                           // [TILE]
+    uint32_t *whist = reinterpret_cast<uint32_t *>(skeys + TILE);          // [OS_WARPS][R + 1]
+    uint32_t *texcl = whist + OS_WARPS * (R + 1);                          // [R]
     __shared__ uint32_t wsum[OS_WARPS];
     __shared__ uint32_t s_tile;
 
     if (must_stop(ctl)) return;
     const uint64_t n = min((uint64_t)*n_ptr, n_max);
     if (n == 0) return;   // an empty stream (e.g. nothing left the hash path): no tile, no look-back
-    // tile size: 4096 elements, or, when there would be fewer tiles than mt (the grid's CTAs, at most
+    // tile size: TILE elements, or, when there would be fewer tiles than mt (the grid's CTAs, at most
     // tile_cap when given), the smallest multiple of the CTA's threads that makes at most mt tiles
     // (the count is known on the device only; every CTA computes the same size). More, smaller tiles
     // mean less work per tile but longer look-back chains.
-    uint32_t ipt = OS_ITEMS;
+    uint32_t ipt = ITEMS;
     const uint64_t mt = tile_cap ? min((uint64_t)gridDim.x, (uint64_t)tile_cap) : (uint64_t)gridDim.x;
-    if (n < mt * OS_TILE) {
+    if (n < mt * TILE) {
         const uint64_t per = mt * OS_THREADS;
         ipt = n > per ? (uint32_t)((n + per - 1) / per) : 1u;
     }
@@ -86,7 +97,7 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
 
     for (;;) {
         if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
-        for (int i = tid; i < OS_WARPS * (RADIX + 1); i += OS_THREADS) (&whist[0][0])[i] = 0;
+        for (uint32_t i = tid; i < OS_WARPS * (R + 1); i += OS_THREADS) whist[i] = 0;
         __syncthreads();
         const uint64_t tile = s_tile;
         if (tile >= ntiles) return;
@@ -95,100 +106,124 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
 
         // element li of the tile: warp w holds li in [w * 32 * ipt, (w + 1) * 32 * ipt), item j of
         // lane l is li = w * 32 * ipt + j * 32 + l (items j >= ipt are unused)
-        K k[OS_ITEMS];
-        uint32_t rd[OS_ITEMS];   // rank within warp (low 16 bits) | digit << 16
+        K k[ITEMS];
+        uint32_t rd[ITEMS];   // rank within warp (low 16 bits) | digit << 16
 #pragma unroll
-        for (int j = 0; j < OS_ITEMS; j++) {
+        for (int j = 0; j < ITEMS; j++) {
             const uint32_t li = w * (32 * ipt) + j * 32 + lane;
             k[j] = ((uint32_t)j < ipt && li < nvalid) ? kin[base + li] : K(0);
         }
+        uint32_t *myhist = whist + w * (R + 1);
 #pragma unroll
-        for (int j = 0; j < OS_ITEMS; j++) {
+        for (int j = 0; j < ITEMS; j++) {
             if ((uint32_t)j >= ipt) break;
             const uint32_t li = w * (32 * ipt) + j * 32 + lane;
             const bool valid = li < nvalid;
-            const uint32_t d = valid ? (uint32_t)((k[j] >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
+            const uint32_t d = valid ? (uint32_t)((k[j] >> shift) & (R - 1)) : R;
             // lanes holding the same digit: one ballot per digit bit (warp multi-split)
             const uint32_t vmask = __ballot_sync(0xFFFFFFFFu, valid);
             uint32_t peers = vmask;
 #pragma unroll
-            for (int bit = 0; bit < RADIX_BITS; bit++) {
+            for (int bit = 0; bit < BITS; bit++) {
                 const uint32_t on = (d >> bit) & 1u;
                 const uint32_t m = __ballot_sync(0xFFFFFFFFu, on);
                 peers &= on ? m : ~m;
             }
             if (!valid) peers = ~vmask;
-            const uint32_t cnt = whist[w][d];
+            const uint32_t cnt = myhist[d];
             __syncwarp();
-            if ((peers & lt) == 0) whist[w][d] = cnt + __popc(peers);
+            if ((peers & lt) == 0) myhist[d] = cnt + __popc(peers);
             __syncwarp();
             rd[j] = (cnt + __popc(peers & lt)) | (d << 16);
         }
         __syncthreads();
         // per digit: exclusive offsets of the warps, tile count
-        uint32_t run = 0;
-        {
-            const int d = tid;  // OS_THREADS == RADIX
+        uint32_t run[DPT];
 #pragma unroll
-            for (int ww = 0; ww < OS_WARPS; ww++) {
-                const uint32_t c = whist[ww][d];
-                whist[ww][d] = run;
-                run += c;
+        for (int q = 0; q < DPT; q++) {
+            const uint32_t d = (uint32_t)tid * DPT + q;
+            uint32_t r = 0;
+            if (d < R) {
+#pragma unroll
+                for (int ww = 0; ww < OS_WARPS; ww++) {
+                    const uint32_t c = whist[ww * (R + 1) + d];
+                    whist[ww * (R + 1) + d] = r;
+                    r += c;
+                }
             }
+            run[q] = r;
         }
         // publish this tile's counts, then look back over earlier tiles
         const bool withheld = withhold != 0 && tile == (uint64_t)(withhold - 1);
         volatile unsigned long long *vst = status;
-        if (!withheld) vst[tile * RADIX + tid] = st_make(tag, tile == 0 ? ST_INC : ST_AGG, run);
-        uint64_t excl = 0;
-        if (tile > 0) {
-            int64_t t = (int64_t)tile - 1;
-            const uint64_t t0 = globaltimer_ns();
-            uint32_t spins = 0;
-            while (t >= 0) {
-                // four predecessors per step, their loads in flight together; consume them in order up
-                // to the first inclusive count, or up to a word not yet published (then read again)
-                uint64_t s4[OS_LOOKBACK];
 #pragma unroll
-                for (int q = 0; q < OS_LOOKBACK; q++) s4[q] = t - q >= 0 ? vst[(uint64_t)(t - q) * RADIX + tid] : 0ull;
-                int used = 0;
-                bool inc = false, blocked = false;
-#pragma unroll
-                for (int q = 0; q < OS_LOOKBACK; q++) {
-                    if (inc || blocked || t - q < 0) continue;
-                    const uint64_t s = s4[q];
-                    if (st_tag(s) != tag || st_flag(s) == 0) {
-                        blocked = true;
-                        continue;
-                    }
-                    excl += st_count(s);
-                    used = q + 1;
-                    if (st_flag(s) == ST_INC) inc = true;
-                }
-                if (inc) break;
-                t -= used;
-                if (blocked && (++spins & 63) == 0) {
-                    if (*(volatile unsigned int *)&ctl->timeout) break;
-                    if (globaltimer_ns() - t0 > wait_ns) {
-                        atomicExch(&ctl->timeout, 1u);
-                        break;
-                    }
-                }
-            }
-            if (!withheld) vst[tile * RADIX + tid] = st_make(tag, ST_INC, excl + run);
+        for (int q = 0; q < DPT; q++) {
+            const uint32_t d = (uint32_t)tid * DPT + q;
+            if (d < R && !withheld) vst[tile * R + d] = st_make(tag, tile == 0 ? ST_INC : ST_AGG, run[q]);
         }
-        gbase[tid] = (uint64_t)dbase[tid] + excl;
-        const uint32_t te = block_excl_scan_256(run, wsum);
-        texcl[tid] = te;
+#pragma unroll
+        for (int q = 0; q < DPT; q++) {
+            const uint32_t d = (uint32_t)tid * DPT + q;
+            if (d >= R) continue;
+            uint64_t excl = 0;
+            if (tile > 0) {
+                int64_t t = (int64_t)tile - 1;
+                const uint64_t t0 = globaltimer_ns();
+                uint32_t spins = 0;
+                while (t >= 0) {
+                    // four predecessors per step, their loads in flight together; consume them in order up
+                    // to the first inclusive count, or up to a word not yet published (then read again)
+                    uint64_t s4[OS_LOOKBACK];
+#pragma unroll
+                    for (int c = 0; c < OS_LOOKBACK; c++) s4[c] = t - c >= 0 ? vst[(uint64_t)(t - c) * R + d] : 0ull;
+                    int used = 0;
+                    bool inc = false, blocked = false;
+#pragma unroll
+                    for (int c = 0; c < OS_LOOKBACK; c++) {
+                        if (inc || blocked || t - c < 0) continue;
+                        const uint64_t sw = s4[c];
+                        if (st_tag(sw) != tag || st_flag(sw) == 0) {
+                            blocked = true;
+                            continue;
+                        }
+                        excl += st_count(sw);
+                        used = c + 1;
+                        if (st_flag(sw) == ST_INC) inc = true;
+                    }
+                    if (inc) break;
+                    t -= used;
+                    if (blocked && (++spins & 63) == 0) {
+                        if (*(volatile unsigned int *)&ctl->timeout) break;
+                        if (globaltimer_ns() - t0 > wait_ns) {
+                            atomicExch(&ctl->timeout, 1u);
+                            break;
+                        }
+                    }
+                }
+                if (!withheld) vst[tile * R + d] = st_make(tag, ST_INC, excl + run[q]);
+            }
+            gbase[d] = (uint64_t)dbase[d] + excl;
+        }
+        // the tile's exclusive offsets per digit, in digit order
+        uint32_t tsum = 0;
+#pragma unroll
+        for (int q = 0; q < DPT; q++) tsum += run[q];
+        uint32_t acc = block_excl_scan_256(tsum, wsum);
+#pragma unroll
+        for (int q = 0; q < DPT; q++) {
+            const uint32_t d = (uint32_t)tid * DPT + q;
+            if (d < R) texcl[d] = acc;
+            acc += run[q];
+        }
         __syncthreads();
         // stable scatter into shared memory in digit order
 #pragma unroll
-        for (int j = 0; j < OS_ITEMS; j++) {
+        for (int j = 0; j < ITEMS; j++) {
             if ((uint32_t)j >= ipt) break;
             const uint32_t li = w * (32 * ipt) + j * 32 + lane;
             if (li < nvalid) {
                 const uint32_t d = rd[j] >> 16;
-                const uint32_t pos = texcl[d] + whist[w][d] + (rd[j] & 0xFFFFu);
+                const uint32_t pos = texcl[d] + whist[w * (R + 1) + d] + (rd[j] & 0xFFFFu);
                 skeys[pos] = k[j];
                 if (vin) svals[pos] = vin[base + li];
             }
@@ -196,7 +231,7 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
         __syncthreads();
         for (uint32_t i = tid; i < nvalid; i += OS_THREADS) {
             const K kk = skeys[i];
-            const uint32_t d = (uint32_t)((kk >> shift) & (RADIX - 1));
+            const uint32_t d = (uint32_t)((kk >> shift) & (R - 1));
             const uint64_t o = gbase[d] + (i - texcl[d]);
             if (o < n) {   // always true unless a wait gave up and the offsets are unreliable
                 kout[o] = kk;
@@ -204,6 +239,49 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
             }
         }
         __syncthreads();
+    }
+}
+
+// Digit histograms of every pass of BITS-bit digits over a stream (count from the device), for the
+// passes whose width the record reads do not histogram. Shared counts: npass * 2^BITS.
+template <class K, int BITS>
+__global__ void k_hist_keys(const K *__restrict__ keys, const uint32_t *n_ptr, uint64_t n_max, uint32_t npass,
+                            uint32_t *hist, Ctl *ctl) {
+    constexpr uint32_t R = 1u << BITS;
+    extern __shared__ uint32_t hk_sh[];
+    if (must_stop(ctl)) return;
+    for (uint32_t i = threadIdx.x; i < npass * R; i += blockDim.x) hk_sh[i] = 0;
+    __syncthreads();
+    const uint64_t n = min((uint64_t)*n_ptr, n_max);
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = (uint64_t)keys[i];
+        for (uint32_t p = 0; p < npass; p++) atomicAdd(&hk_sh[p * R + ((uint32_t)(k >> (BITS * p)) & (R - 1))], 1u);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < npass * R; i += blockDim.x)
+        if (hk_sh[i]) atomicAdd(&hist[i], hk_sh[i]);
+}
+
+// Exclusive scan of each pass's 2^BITS-digit histogram into its digit bases (one CTA per pass).
+template <int BITS>
+__global__ void k_digit_bases_w(const uint32_t *hist, uint32_t *dbase) {
+    constexpr uint32_t R = 1u << BITS;
+    constexpr int DPT = (int)((R + OS_THREADS - 1) / OS_THREADS);
+    __shared__ uint32_t wsum[OS_WARPS];
+    const uint32_t p = blockIdx.x;
+    uint32_t v[DPT], tsum = 0;
+#pragma unroll
+    for (int q = 0; q < DPT; q++) {
+        const uint32_t d = threadIdx.x * DPT + q;
+        v[q] = d < R ? hist[p * R + d] : 0u;
+        tsum += v[q];
+    }
+    uint32_t acc = block_excl_scan_256(tsum, wsum);
+#pragma unroll
+    for (int q = 0; q < DPT; q++) {
+        const uint32_t d = threadIdx.x * DPT + q;
+        if (d < R) dbase[p * R + d] = acc;
+        acc += v[q];
     }
 }
 

@@ -163,12 +163,12 @@ class Server:
 
     def __init__(self, device: int = 0, hbm_budget: int = 120 << 30, max_inflight: int = 3, max_batch: int = 4096,
                  serial: bool = False, keep_lists: bool = True, races_cap: int = 1 << 20,
-                 max_batch_records: int = 1 << 30, compact: bool = True):
+                 max_batch_records: int = 1 << 30, compact: bool = True, options: dict | None = None):
         import torch
         self.torch = torch
         self.device = device
         self.dev = f"cuda:{device}"
-        self.chk = simulee.Checker(device)
+        self.chk = simulee.Checker(device, **(options or {}))   # launch choices, e.g. from the autotuner
         self.budget = hbm_budget
         self.max_inflight = 1 if serial else max_inflight
         self.max_batch = 1 if serial else max_batch
