@@ -196,6 +196,11 @@ typedef struct {
     uint32_t hash_pool_div;   /* hash path: a run's racy units are resolved in place up to table size /
                                  hash_pool_div of them, beyond that the run goes to the sort path;
                                  0 = 3, or 3..64 */
+    uint32_t hot_unit_marks;  /* hash path, block signatures of global units: 0 or 1 = a warp marks a unit
+                                 once per run of consecutive lanes that hold the same unit and block, so a
+                                 unit that every thread reads (a kernel-wide constant) costs one atomic per
+                                 run of lanes rather than one per record; 2 = every record marks (about 2%
+                                 less work per record when no unit is that hot) */
 } simulee_options;
 
 /* Repeated calls. With SIMULEE_GRAPH_AUTO, a check call (simulee_check*, simulee_check_batch,

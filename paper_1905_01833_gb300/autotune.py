@@ -11,6 +11,9 @@ knobs are launch-time choices of the library (simulee_options):
 * hash_cap_eighths / hash_pool_div: the cutover from the hash path to the sort
   path: how full a run's table may get in distinct units (4/8 to 7/8) and how
   many racy units a run resolves in place (table / 3 down to table / 64);
+* hot_unit_marks: whether a warp marks a global unit's block signature once
+  per run of lanes holding it (a guard against units every thread reads) or
+  once per record (a little less work when no unit is that hot);
 * sort_items: the radix sort's tile (256 threads x 8 or 16 elements);
 * radix_bits: the radix sort's digit width (6, 8 or 11 bits);
 * ingest_ctas_per_sm, sort_ctas_per_sm, reduce_ctas_per_sm: persistent CTAs per
@@ -37,6 +40,7 @@ KNOBS = {
     "hash_shape": (0, 1, 2),
     "hash_cap_eighths": (7, 6, 5),
     "hash_pool_div": (3, 6, 12),
+    "hot_unit_marks": (0, 2),
     "sort_items": (16, 8),
     "radix_bits": (8, 6, 11),
     "ingest_ctas_per_sm": (2, 1),
@@ -182,7 +186,7 @@ class Autotuner:
                     if v == best[k]:
                         continue
                     cand = dict(best, **{k: v})
-                    if cand["path"] == simulee.PATH_SORT and k.startswith("hash"):
+                    if cand["path"] == simulee.PATH_SORT and (k.startswith("hash") or k == "hot_unit_marks"):
                         continue   # the hash knobs do nothing on the sort path
                     ms = measure(cand)
                     log.append((cand, ms))

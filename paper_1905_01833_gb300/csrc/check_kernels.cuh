@@ -243,6 +243,10 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
             const bool isX = markX && !(d.flags & TF_PAPER_ORDER);
             const uint32_t bS = __ballot_sync(0xFFFFFFFFu, isS), bG = __ballot_sync(0xFFFFFFFFu, isG);
             const uint32_t bX = __ballot_sync(0xFFFFFFFFu, isX);
+            // a unit every thread reads (a kernel-wide constant) is marked once per run of lanes
+            const uint32_t bM = __ballot_sync(0xFFFFFFFFu, markX);
+            const uint32_t pu = __shfl_up_sync(0xFFFFFFFFu, u, 1), pblk = __shfl_up_sync(0xFFFFFFFFu, blk, 1);
+            const bool sameM = lane > 0 && ((bM >> (lane - 1)) & 1u) && pu == u && pblk == blk;
             cS += __popc(bS);
             cG += __popc(bG);
             cX += __popc(bX);
@@ -251,7 +255,7 @@ k_ingest(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ rank, La
                 const uint64_t sb = (uint64_t)d.block_off + blk;
                 if (bS) hist_add(hs, shl(sb, L.bus + L.be) | shl(u, L.be) | ep, np_s, isS, bS);
                 if (bG) hist_add(hg, shl(sb, L.bug + L.be) | shl(u, L.be) | ep, np_g, isG, bG);
-                if (markX) sig_mark(L, sig, sig_slot(L, d.sig_off, t, u), blk, (uint32_t)sb);
+                if (markX && !sameM) sig_mark(L, sig, sig_slot(L, d.sig_off, t, u), blk, (uint32_t)sb);
             }
         }
         if (MODE != IN_VALIDATE) {
@@ -527,20 +531,35 @@ __device__ __forceinline__ void mark_needed(uint32_t *nonred, const Layout &L, u
 }
 
 // ---------------------------------------------------------------------------
-// Segmented reductions over a sorted stream, one thread per group.
+// Segmented reductions over a sorted stream: the conflict scan.
 //
-// A CTA loads a tile of 2048 sorted elements into shared memory, finds the
-// group heads (key changes), and owns the groups whose head lies in its tile;
-// a group that runs past the tile end is finished from global memory by its
-// owner. Each group is reduced to its top-2 summary in registers (groups are a
-// few elements long), emits its races, and leaves a compact adjacency summary
-// in shared memory.
+// CTAs claim tiles of 2048 sorted elements in order. A tile is loaded into
+// shared memory and cut at its group heads (key changes) into segments: the
+// piece before its first head (the end of a group that began in an earlier
+// tile), the groups that begin and end inside it, and its last piece, which
+// may run on into later tiles. A segment is reduced to its top-2 summary by
+// one thread when it is short and by a warp when it is long: the lanes stride
+// over it and their summaries are merged with warp-wide min reductions (all
+// the segment's elements are accesses of one unit, so this groups same-unit
+// accesses inside a warp).
+//
+// A group is finished (races emitted, adjacency tested) by the tile that holds
+// its last element. Before it waits on anything, every tile publishes the
+// summary of its last piece and of the piece before its last head and then a
+// ready word tagged with the launch; a group that began in earlier tiles is
+// completed by looking back over those summaries until the tile holding its
+// head (256 tiles per step). Tiles are claimed in order and publish before they
+// wait, so every wait is on a tile already being processed, and waits are
+// bounded by wall time as in the radix sort. A group of millions of elements
+// is thus summarised by all the tiles it covers at once and finished by one
+// look-back over their summaries.
 //
 // Intra streams (key = block, unit, epoch with the epoch in the low bits):
-// group (b, u, e) and the group after it are epochs e and e+1 of the same unit
-// exactly when the next key is key + 1; a conflict between their summaries
-// marks barrier e of block b as needed. The owner of a tile's last group also
-// summarises the group that follows (owned by a later tile) for this test.
+// group (b, u, e) and the group before it are epochs e-1 and e of the same unit
+// exactly when the key before is key - 1 (with the paper's visit-order counters:
+// when both have the same block and unit); a conflict between their summaries
+// marks barrier e-1 of block b as needed. The finisher of the later group tests
+// the pair.
 // Inter stream (key = trace, global unit): owners are blocks; no adjacency.
 // ---------------------------------------------------------------------------
 constexpr int RG_THREADS = 256;
@@ -604,27 +623,52 @@ __device__ __forceinline__ WaItem wa_item(const TraceDesc &d, uint64_t v) {
     return WaItem{payload_act(v), (uint32_t)(v >> 32) & 0x3FFFFFFFu, d.stmt[idx], d.events[idx].y};
 }
 
-// races of group [gs, ge) and the adjacency test against the group of the next epoch, if present
+// 64-bit minimum over the warp (all lanes take part)
+__device__ __forceinline__ uint64_t warp_min64(uint64_t x) {
+    const uint32_t hi = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(x >> 32));
+    const uint32_t lo = __reduce_min_sync(0xFFFFFFFFu, (uint32_t)(x >> 32) == hi ? (uint32_t)x : 0xFFFFFFFFu);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// Races of group [gs, ge) of a warp-aware trace and the adjacency test against the group of the next epoch,
+// if present. The stream does not hold a group's elements in schedule order (the record reads place their
+// tiles in the order they finish), so every pair is examined and, per class, the lowest in schedule order
+// kept: the pair whose later access comes first, then the earliest partner (schedule order: visit order,
+// then record index). Called by one thread (lanes = 1) or by all lanes of a warp (lanes = 32), which share
+// the work.
 template <class K>
-__device__ void warp_group(const K *__restrict__ keys, const uint64_t *__restrict__ vals, uint64_t gs, uint64_t ge,
-                           uint64_t n, K kg, const TraceDesc &d, const Layout &L, const RaceStage &rs, Ctl *ctl,
-                           uint32_t *nonred, uint32_t trace, uint32_t space, uint32_t block, uint32_t epoch,
-                           uint32_t unit) {
-    // lowest pair per class: elements are in schedule order (the sort is stable over record order)
-#pragma unroll 1
-    for (int cls = 0; cls < 2; cls++) {
-        bool found = false;
-        for (uint64_t qi = gs + 1; qi < ge && !found; qi++) {
-            const WaItem q = wa_item(d, vals[qi]);
-            for (uint64_t pi = gs; pi < qi; pi++) {
-                const WaItem p = wa_item(d, vals[pi]);
-                if (!wa_conflict(p.act, p.gtid, p.stmt, q.act, q.gtid, q.stmt, d.bt)) continue;
-                if (((p.act != ACT_R && q.act != ACT_R) ? 0 : 1) != cls) continue;
-                emit_race(rs, ctl, trace, race_key(L, trace, space, 0u, block, epoch, unit, (uint32_t)cls),
-                          ((uint64_t)p.vo << 32) | p.gtid, ((uint64_t)q.vo << 32) | q.gtid);
-                found = true;
-                break;
+__device__ void wa_group(const K *__restrict__ keys, const uint64_t *__restrict__ vals, uint64_t gs, uint64_t ge,
+                         uint64_t n, K kg, const TraceDesc &d, const Layout &L, const RaceStage &rs, Ctl *ctl,
+                         uint32_t *nonred, uint32_t trace, uint32_t space, uint32_t block, uint32_t epoch,
+                         uint32_t unit, int lane, int lanes) {
+    uint64_t bq[2] = {EMPTY, EMPTY}, bp[2] = {EMPTY, EMPTY};   // (visit order << 32 | record index) of q and p
+    for (uint64_t qi = gs + lane; qi < ge; qi += lanes) {
+        const WaItem q = wa_item(d, vals[qi]);
+        const uint64_t kq = ((uint64_t)q.vo << 32) | (uint32_t)vals[qi];
+        for (uint64_t pi = gs; pi < ge; pi++) {
+            const WaItem p = wa_item(d, vals[pi]);
+            const uint64_t kp = ((uint64_t)p.vo << 32) | (uint32_t)vals[pi];
+            if (kp >= kq || !wa_conflict(p.act, p.gtid, p.stmt, q.act, q.gtid, q.stmt, d.bt)) continue;
+            const int cls = (p.act != ACT_R && q.act != ACT_R) ? 0 : 1;
+            if (kq < bq[cls] || (kq == bq[cls] && kp < bp[cls])) {
+                bq[cls] = kq;
+                bp[cls] = kp;
             }
+        }
+    }
+#pragma unroll
+    for (int cls = 0; cls < 2; cls++) {
+        if (lanes > 1) {
+            const uint64_t mq = warp_min64(bq[cls]);
+            bp[cls] = warp_min64(bq[cls] == mq ? bp[cls] : EMPTY);
+            bq[cls] = mq;
+        }
+        if (lane == 0 && bq[cls] != EMPTY) {
+            const uint32_t ip = (uint32_t)bp[cls], iq = (uint32_t)bq[cls];
+            const uint4 ep = d.events[ip], eq = d.events[iq];
+            const uint32_t gp = ep.z * d.bt + (ep.w & 0xFFFFu), gq = eq.z * d.bt + (eq.w & 0xFFFFu);
+            emit_race(rs, ctl, trace, race_key(L, trace, space, 0u, block, epoch, unit, (uint32_t)cls),
+                      ((uint64_t)ep.y << 32) | gp, ((uint64_t)eq.y << 32) | gq);
         }
     }
     // barrier `epoch` is needed when a pair across this group and the next epoch's group conflicts
@@ -632,25 +676,177 @@ __device__ void warp_group(const K *__restrict__ keys, const uint64_t *__restric
         bool needed = false;
         for (uint64_t qi = ge; qi < n && keys[qi] == kg + 1 && !needed; qi++) {
             const WaItem q = wa_item(d, vals[qi]);
-            for (uint64_t pi = gs; pi < ge && !needed; pi++) {
+            for (uint64_t pi = gs + lane; pi < ge && !needed; pi += lanes) {
                 const WaItem p = wa_item(d, vals[pi]);
                 needed = wa_conflict(p.act, p.gtid, p.stmt, q.act, q.gtid, q.stmt, d.bt);
             }
+            if (lanes > 1) needed = __any_sync(0xFFFFFFFFu, needed);
         }
-        if (needed) mark_needed(nonred, L, block, epoch);
+        if (needed && lane == 0) mark_needed(nonred, L, block, epoch);
     }
 }
+
+constexpr uint32_t RG_LONG = 32;                             // segments longer than this are reduced by a warp
+constexpr uint32_t RG_MAX_LONG = RG_TILE / (RG_LONG + 1) + 1;  // long segments a tile can hold
+constexpr uint32_t RG_HAS_HEAD = 1u, RG_PREV_HEAD = 2u;
+
+// What a tile publishes for the tiles after it.
+struct RgTile {
+    Top2 last;        // its last piece: from its last head (or, without a head, its first element) to its end
+    Top2 prev;        // the piece before its last head: from the head before that (RG_PREV_HEAD) or its start
+    uint32_t head;    // element index of its last head (RG_HAS_HEAD)
+    uint32_t flags;
+};
 
 template <class K, bool INTER>
 constexpr size_t reduce_groups_smem() {
     return (size_t)RG_TILE * (8 + sizeof(K)) + (INTER ? 0 : (RG_TILE + 1) * sizeof(Adj)) + (RG_TILE + 2) * 2;
 }
 
+// The top-2 summary of the union of the lanes' summaries, in every lane. Per category the first item is
+// the smallest first item; the second is the smallest item of another owner than the first's: a lane's
+// first item when its owner differs, else the lane's second item (which has another owner than the lane's
+// first, that is than the union's first).
+template <class Own>
+__device__ __forceinline__ void top2_warp_merge(Top2 &s, const Own &own) {
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const uint64_t a = warp_min64(s.a[c]);
+        const uint64_t cand = (s.a[c] != EMPTY && own(s.a[c]) != own(a)) ? s.a[c] : s.b[c];
+        s.b[c] = warp_min64(cand);
+        s.a[c] = a;
+    }
+}
+
+// the union of every thread's summary, in every thread (all threads of the CTA call it)
+template <class Own>
+__device__ __forceinline__ Top2 top2_cta_merge(Top2 s, const Own &own, Top2 *s_part) {
+    top2_warp_merge(s, own);
+    __syncthreads();   // s_part is free
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    Top2 r;
+    if ((threadIdx.x & 31) < RG_THREADS / 32) r = s_part[threadIdx.x & 31];
+    else r.clear();
+    top2_warp_merge(r, own);
+    return r;
+}
+
+__device__ __forceinline__ Top2 ldcg_top2(const Top2 *p) {
+    const unsigned long long *q = reinterpret_cast<const unsigned long long *>(p);
+    Top2 s;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        s.a[c] = __ldcg(q + c);
+        s.b[c] = __ldcg(q + 3 + c);
+    }
+    return s;
+}
+
+// Wait until tile j of this launch has published. False when the wait gave up (ctl->timeout is then set,
+// which stops every other waiter too).
+__device__ __forceinline__ bool rg_wait(const uint32_t *ready, uint64_t j, uint32_t tag, Ctl *ctl, uint64_t wait_ns) {
+    const volatile uint32_t *r = ready + j;
+    if (*r != tag) {
+        const uint64_t t0 = globaltimer_ns();
+        for (uint32_t i = 1; *r != tag; i++) {
+            if ((i & 63) == 0) {
+                if (*(volatile unsigned int *)&ctl->timeout) return false;
+                if (globaltimer_ns() - t0 > wait_ns) {
+                    atomicExch(&ctl->timeout, 1u);
+                    return false;
+                }
+            }
+        }
+    }
+    __threadfence();
+    return true;
+}
+
+// shared scratch of a look-back
+struct RgLook {
+    Top2 acc;
+    uint32_t head, ok, found, first[RG_THREADS / 32];
+    uint64_t htile;
+};
+
+// The summary of the group open at the end of tile j0, from its head to the end of j0: the last pieces that
+// tiles j0, j0-1, ... published, down to the first of them that has a head. All threads of the CTA call it
+// and receive the summary, the element index of the group's head and the tile holding it; false (in all
+// threads) when a wait gave up.
+template <class Own>
+__device__ bool rg_lookback(uint64_t j0, const RgTile *pub, const uint32_t *ready, uint32_t tag, Ctl *ctl,
+                            uint64_t wait_ns, const Own &own, Top2 *s_part, RgLook &lk, Top2 &S, uint32_t &head,
+                            uint64_t &htile) {
+    const int tid = threadIdx.x;
+    if (tid == 0) {   // most groups began in the tile just before
+        lk.ok = rg_wait(ready, j0, tag, ctl, wait_ns) ? 1u : 0u;
+        lk.found = 0;
+        if (lk.ok) {
+            lk.acc = ldcg_top2(&pub[j0].last);
+            if (__ldcg(&pub[j0].flags) & RG_HAS_HEAD) {
+                lk.found = 1;
+                lk.head = __ldcg(&pub[j0].head);
+                lk.htile = j0;
+            }
+        }
+    }
+    __syncthreads();
+    if (!lk.ok) return false;
+    int64_t base = (int64_t)j0 - 1;
+    while (!lk.found && base >= 0) {
+        // tiles base, base - 1, ..., base - 255: one per thread
+        const int64_t j = base - tid;
+        bool ok = true, hh = false;
+        if (j >= 0) {
+            ok = rg_wait(ready, (uint64_t)j, tag, ctl, wait_ns);
+            if (ok) hh = (__ldcg(&pub[j].flags) & RG_HAS_HEAD) != 0u;
+        }
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, hh);
+        if ((tid & 31) == 0) lk.first[tid >> 5] = bal ? (uint32_t)(tid + __ffs(bal) - 1) : (uint32_t)RG_THREADS;
+        if (__syncthreads_or(!ok)) return false;
+        uint32_t first = RG_THREADS;   // the thread of the nearest tile with a head
+#pragma unroll
+        for (int w = 0; w < RG_THREADS / 32; w++) first = min(first, lk.first[w]);
+        Top2 part;
+        part.clear();
+        if (j >= 0 && (uint32_t)tid <= first) part = ldcg_top2(&pub[j].last);
+        part = top2_cta_merge(part, own, s_part);
+        if (tid == 0) {
+            top2_merge(lk.acc, part, own);
+            if (first < (uint32_t)RG_THREADS) {
+                lk.found = 1;
+                lk.htile = (uint64_t)(base - first);
+                lk.head = __ldcg(&pub[lk.htile].head);
+            }
+        }
+        __syncthreads();
+        base -= RG_THREADS;
+    }
+    S = lk.acc;
+    head = lk.head;
+    htile = lk.htile;
+    __syncthreads();   // lk is free again
+    return true;
+}
+
+// the group before one of key kq (ended right before its head) is the same unit's previous epoch: its
+// key is kq - 1, or (the paper's visit-order counters) any key of the same block and unit
+template <class K>
+__device__ __forceinline__ bool rg_adjacent(K kp, K kq, const Layout &L, const TraceDesc *td, const uint32_t *tob,
+                                            uint32_t bu) {
+    if (kq == kp + 1) return true;
+    const uint32_t be = L.be;
+    if (((uint64_t)kq >> be) != ((uint64_t)kp >> be)) return false;
+    return (td[tob[(uint64_t)kp >> (bu + be)]].flags & TF_PAPER_ORDER) != 0;
+}
+
 template <class K, bool INTER>
 __global__ void __launch_bounds__(RG_THREADS)
 k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, const uint32_t *n_ptr, uint64_t n_max,
                 Layout L, const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob, uint32_t space,
-                uint32_t bu, Ctl *ctl, uint32_t *nonred, RaceStage rs) {
+                uint32_t bu, Ctl *ctl, uint32_t *nonred, RaceStage rs, RgTile *pub, uint32_t *ready, uint32_t tag,
+                uint32_t *tile_ctr, uint64_t wait_ns) {
     extern __shared__ __align__(16) uint8_t rg_smem[];
     uint64_t *sval = reinterpret_cast<uint64_t *>(rg_smem);
     K *skey = reinterpret_cast<K *>(rg_smem + RG_TILE * 8);
@@ -658,16 +854,73 @@ k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, c
     uint16_t *shead = reinterpret_cast<uint16_t *>(rg_smem + RG_TILE * (8 + sizeof(K)) +
                                                    (INTER ? 0 : (RG_TILE + 1) * sizeof(Adj)));
     __shared__ uint32_t wsum[RG_THREADS / 32];
-    __shared__ K s_next_key;
-    __shared__ uint32_t s_has_next;
-    if (must_stop(ctl)) return;
+    __shared__ Top2 s_part[RG_THREADS / 32];
+    __shared__ Top2 s_first, s_last, s_prev;   // segment 0, the last segment, the segment before it
+    __shared__ RgLook s_look;
+    __shared__ uint16_t s_long[RG_MAX_LONG];
+    __shared__ uint32_t s_G, s_nlong, s_ends, s_stop;
+    __shared__ uint64_t s_tile;
     const uint64_t n = min((uint64_t)*n_ptr, n_max);
     const uint64_t ntiles = (n + RG_TILE - 1) / RG_TILE;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t be = L.be;
     const uint64_t umask = (bu >= 64) ? ~0ull : ((1ull << bu) - 1);
     const OwnThread own_t;
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    auto own_of = [&](K kg) -> OwnBlock {   // inter-block owners: the blocks of the key's trace
+        const uint32_t trace = (uint32_t)((uint64_t)kg >> (L.bug + L.bxr));
+        return OwnBlock{td[trace].bt, td[trace].nb <= (1u << 20)};
+    };
+    // races of a finished group (and, intra streams, its adjacency summary), by one thread (lanes = 1) or
+    // by all lanes of a warp holding the same summary (lanes = 32)
+    auto finish = [&](K kg, uint64_t gs, uint64_t ge, const Top2 &S, Adj *adj_out, int ln, int lanes) {
+        if (INTER) {
+            if (ln != 0) return;
+            const uint32_t trace = (uint32_t)((uint64_t)kg >> (L.bug + L.bxr));
+            const OwnBlock own_b = own_of(kg);
+            const uint32_t unit = (uint32_t)((uint64_t)kg & umask);
+            // the visit order of a paper-counter trace's group (0 for other traces)
+            const uint32_t vord = (uint32_t)(((uint64_t)kg >> L.bug) & ((1ull << L.bxr) - 1));
+#pragma unroll
+            for (int cls = 0; cls < 2; cls++) {
+                uint64_t p, q;
+                if (!lowest_pair(S, cls, own_b, p, q)) continue;
+                // owner codes back to block * block_threads + tid
+                p = (p & ~0xFFFFFFFFull) | own_b.gtid((uint32_t)p);
+                q = (q & ~0xFFFFFFFFull) | own_b.gtid((uint32_t)q);
+                emit_race(rs, ctl, trace, race_key(L, trace, 1u, 1u, 0u, vord, unit, cls), p, q);
+            }
+        } else {
+            const uint32_t trace = tob[(uint64_t)kg >> (bu + be)];
+            const uint64_t sk = (uint64_t)kg >> be;
+            const uint32_t block = (uint32_t)(sk >> bu), unit = (uint32_t)(sk & umask);
+            const uint32_t epoch = (uint32_t)((uint64_t)kg & ((1ull << be) - 1));
+            const TraceDesc &d = td[trace];
+            if (d.flags & TF_WARP_AWARE) {
+                // pair by pair, with the adjacency test against the next epoch's group
+                wa_group(keys, vals, gs, ge, n, kg, d, L, rs, ctl, nonred, trace, space, block, epoch, unit, ln, lanes);
+                if (ln == 0) {
+                    Top2 none;
+                    none.clear();
+                    *adj_out = adj_of(none);
+                }
+            } else if (ln == 0) {
+                emit_group(L, rs, ctl, S, own_t, trace, space, 0u, block, epoch, unit);
+                *adj_out = adj_of(S);
+            }
+        }
+    };
+    auto warp_aware = [&](K kg) -> bool {
+        return !INTER && (td[tob[(uint64_t)kg >> (bu + be)]].flags & TF_WARP_AWARE) != 0;
+    };
+    for (;;) {
+        if (tid == 0) {
+            s_tile = atomicAdd(tile_ctr, 1u);
+            s_stop = must_stop(ctl) ? 1u : 0u;
+            s_nlong = 0;
+        }
+        __syncthreads();
+        const uint64_t tile = s_tile;
+        if (tile >= ntiles || s_stop) break;
         const uint64_t t0 = tile * RG_TILE;
         const uint32_t m = (uint32_t)min((uint64_t)RG_TILE, n - t0);
         for (uint32_t i = tid; i < m; i += RG_THREADS) {
@@ -687,117 +940,149 @@ k_reduce_groups(const K *__restrict__ keys, const uint64_t *__restrict__ vals, c
             }
         }
         const uint32_t nh = __popc(hm);
-        const uint32_t base = block_excl_scan_256(nh, wsum);
+        const uint32_t hbase = block_excl_scan_256(nh, wsum);
         {
-            uint32_t o = base;
+            uint32_t o = hbase;
 #pragma unroll
             for (int j = 0; j < RG_ITEMS; j++)
                 if ((hm >> j) & 1u) shead[o++] = (uint16_t)(tid * RG_ITEMS + j);
         }
-        if (tid == RG_THREADS - 1) wsum[0] = base + nh;   // number of groups owned by this tile
+        if (tid == RG_THREADS - 1) s_G = hbase + nh;   // heads in this tile
+        if (tid == 0) s_ends = (t0 + m >= n || keys[t0 + m] != skey[m - 1]) ? 1u : 0u;   // the last piece ends here
         __syncthreads();
-        const uint32_t G = wsum[0];
-        if (tid == 0) s_has_next = 0;
-        __syncthreads();
-        for (uint32_t g = tid; g < G; g += RG_THREADS) {
-            const uint32_t st = shead[g];
-            const K kg = skey[st];
-            uint32_t trace, bt = 1;
-            bool pad = false;
-            if (INTER) {
-                trace = (uint32_t)((uint64_t)kg >> (L.bug + L.bxr));
-                bt = td[trace].bt;
-                pad = td[trace].nb <= (1u << 20);
-            } else {
-                trace = tob[(uint64_t)kg >> (bu + be)];
+        const uint32_t G = s_G;
+        const bool ends = s_ends != 0u;
+        const uint32_t fhead = G ? shead[0] : m;
+        // Segments: 0 = [0, first head), s = 1..G = [head s-1, head s or the tile end). Segments 1..G-1 are
+        // groups inside the tile; segment G is finished here when the tile ends it; segment 0 (when not empty)
+        // ends a group that began before, finished after the look-back.
+        auto segment_done = [&](uint32_t s, uint32_t a, uint32_t e, const Top2 &S, int ln, int lanes) {
+            if (s == 0) {
+                if (ln == 0) s_first = S;
+                return;
             }
-            const OwnBlock own_b{bt, pad};
+            if (ln == 0 && s == G) s_last = S;
+            if (ln == 0 && s + 1 == G && G >= 2) s_prev = S;
+            if (s < G || ends) finish(skey[a], t0 + a, t0 + e, S, INTER ? nullptr : &sadj[s], ln, lanes);
+        };
+        for (uint32_t s = tid; s <= G; s += RG_THREADS) {
+            const uint32_t a = s == 0 ? 0u : shead[s - 1], e = s < G ? shead[s] : m;
+            if (a == e) continue;   // segment 0 of a tile that starts with a head
+            if (e - a > RG_LONG) {
+                s_long[atomicAdd(&s_nlong, 1u)] = (uint16_t)s;
+                continue;
+            }
             Top2 S;
             S.clear();
-            uint64_t cnt = 0;
-            uint64_t e;   // element index one past the group (absolute)
-            if (g + 1 < G) {
-                const uint32_t en = shead[g + 1];
-                for (uint32_t j = st; j < en; j++) {
-                    const uint64_t v = sval[j];
-                    if (INTER) top2_add(S, payload_act(v), payload_item(v), own_b);
-                    else top2_add(S, payload_act(v), payload_item(v), own_t);
-                }
-                cnt = en - st;
-                e = t0 + en;
-            } else {
-                uint64_t j = t0 + st;
-                for (; j < n; j++) {
-                    const K kj = (j < t0 + m) ? skey[j - t0] : keys[j];
-                    if (kj != kg) break;
-                    const uint64_t v = (j < t0 + m) ? sval[j - t0] : vals[j];
-                    if (INTER) top2_add(S, payload_act(v), payload_item(v), own_b);
-                    else top2_add(S, payload_act(v), payload_item(v), own_t);
-                }
-                cnt = j - (t0 + st);
-                e = j;
-            }
             if (INTER) {
-                if (cnt >= 2) {
-                    const uint32_t unit = (uint32_t)((uint64_t)kg & umask);
-                    // the visit order of a paper-counter trace's group (0 for other traces)
-                    const uint32_t vord = (uint32_t)(((uint64_t)kg >> L.bug) & ((1ull << L.bxr) - 1));
-#pragma unroll
-                    for (int cls = 0; cls < 2; cls++) {
-                        uint64_t p, q;
-                        if (!lowest_pair(S, cls, own_b, p, q)) continue;
-                        // owner codes back to block * block_threads + tid
-                        p = (p & ~0xFFFFFFFFull) | own_b.gtid((uint32_t)p);
-                        q = (q & ~0xFFFFFFFFull) | own_b.gtid((uint32_t)q);
-                        emit_race(rs, ctl, trace, race_key(L, trace, 1u, 1u, 0u, vord, unit, cls), p, q);
+                const OwnBlock own_b = own_of(skey[a]);
+                for (uint32_t j = a; j < e; j++) top2_add(S, payload_act(sval[j]), payload_item(sval[j]), own_b);
+            } else {
+                for (uint32_t j = a; j < e; j++) top2_add(S, payload_act(sval[j]), payload_item(sval[j]), own_t);
+            }
+            segment_done(s, a, e, S, 0, 1);
+        }
+        __syncthreads();
+        // long segments: a warp each, lanes striding, then a warp-wide merge
+        const uint32_t nlong = s_nlong;
+        for (uint32_t q = warp; q < nlong; q += RG_THREADS / 32) {
+            const uint32_t s = s_long[q];
+            const uint32_t a = s == 0 ? 0u : shead[s - 1], e = s < G ? shead[s] : m;
+            Top2 S;
+            S.clear();
+            if (INTER) {
+                const OwnBlock own_b = own_of(skey[a]);
+                for (uint32_t j = a + lane; j < e; j += 32) top2_add(S, payload_act(sval[j]), payload_item(sval[j]), own_b);
+                top2_warp_merge(S, own_b);
+            } else {
+                for (uint32_t j = a + lane; j < e; j += 32) top2_add(S, payload_act(sval[j]), payload_item(sval[j]), own_t);
+                top2_warp_merge(S, own_t);
+            }
+            segment_done(s, a, e, S, lane, 32);   // every lane holds the merged summary
+        }
+        __syncthreads();
+        // publish for the tiles after this one
+        if (tid == 0) {
+            RgTile &P = pub[tile];
+            Top2 prev;
+            prev.clear();
+            uint32_t flags = 0, head = 0;
+            if (G) {
+                flags |= RG_HAS_HEAD;
+                head = (uint32_t)(t0 + shead[G - 1]);
+                if (G >= 2) {
+                    prev = s_prev;
+                    flags |= RG_PREV_HEAD;
+                } else if (fhead > 0) {
+                    prev = s_first;
+                }
+            }
+            P.last = G ? s_last : s_first;
+            P.prev = prev;
+            P.head = head;
+            P.flags = flags;
+            __threadfence();
+            *(volatile uint32_t *)&ready[tile] = tag;
+        }
+        // the group that ends in segment 0 began in an earlier tile; intra streams also need the summary of
+        // the group that ended right before this tile (the predecessor of segment 1)
+        const bool fin0 = fhead > 0 && (G > 0 || ends);
+        if (tile > 0 && (fin0 || (!INTER && fhead == 0 && G > 0))) {
+            Top2 LB;
+            uint32_t lb_head = 0;
+            uint64_t lb_tile = 0;
+            const K k0 = skey[0];
+            bool ok;
+            if (INTER) ok = rg_lookback(tile - 1, pub, ready, tag, ctl, wait_ns, own_of(k0), s_part, s_look, LB, lb_head, lb_tile);
+            else ok = rg_lookback(tile - 1, pub, ready, tag, ctl, wait_ns, own_t, s_part, s_look, LB, lb_head, lb_tile);
+            if (!ok) break;
+            if (fin0) {
+                if (warp == 0) {   // the first warp finishes it (a warp-aware group's pairs are shared out)
+                    if (INTER) top2_merge(LB, s_first, own_of(k0));
+                    else top2_merge(LB, s_first, own_t);
+                    finish(k0, lb_head, t0 + fhead, LB, INTER ? nullptr : &sadj[0], lane, 32);
+                }
+                if (!INTER && lb_head > 0 && !warp_aware(k0)) {
+                    // the group before it: the piece before the last head of the head's tile, and what
+                    // came before that piece when it did not start at a head
+                    Top2 P = ldcg_top2(&pub[lb_tile].prev);
+                    const uint32_t pf = __ldcg(&pub[lb_tile].flags);
+                    if (!(pf & RG_PREV_HEAD)) {
+                        Top2 X;
+                        uint32_t xh;
+                        uint64_t xt;
+                        if (!rg_lookback(lb_tile - 1, pub, ready, tag, ctl, wait_ns, own_t, s_part, s_look, X, xh, xt)) break;
+                        top2_merge(P, X, own_t);
+                    }
+                    __syncthreads();   // sadj[0] is written
+                    if (tid == 0) {
+                        const K kp = keys[lb_head - 1];
+                        if (rg_adjacent(kp, k0, L, td, tob, bu) && adj_conflict(adj_of(P), sadj[0]))
+                            mark_needed(nonred, L, (uint32_t)(((uint64_t)kp >> be) >> bu),
+                                        (uint32_t)((uint64_t)kp & ((1ull << be) - 1)));
                     }
                 }
-            } else {
-                const uint64_t sk = (uint64_t)kg >> be;
-                const uint32_t block = (uint32_t)(sk >> bu), unit = (uint32_t)(sk & umask);
-                const uint32_t epoch = (uint32_t)((uint64_t)kg & ((1ull << be) - 1));
-                const TraceDesc &d = td[trace];
-                if (d.flags & TF_WARP_AWARE) {
-                    warp_group(keys, vals, e - cnt, e, n, kg, d, L, rs, ctl, nonred, trace, space, block, epoch, unit);
+            } else if (!INTER && tid == 0) {
+                if (warp_aware(kprev0)) {
                     Top2 none;
                     none.clear();
-                    sadj[g] = adj_of(none);   // adjacency already decided pair by pair
+                    sadj[0] = adj_of(none);
                 } else {
-                    if (cnt >= 2) emit_group(L, rs, ctl, S, own_t, trace, space, 0u, block, epoch, unit);
-                    sadj[g] = adj_of(S);
-                }
-                if (g + 1 == G && e < n) {
-                    // the following group belongs to a later tile: summarise it for the adjacency test
-                    const K kn = keys[e];
-                    Top2 T;
-                    T.clear();
-                    for (uint64_t j = e; j < n && keys[j] == kn; j++) {
-                        const uint64_t v = vals[j];
-                        top2_add(T, payload_act(v), payload_item(v), own_t);
-                    }
-                    sadj[G] = adj_of(T);
-                    s_next_key = kn;
-                    s_has_next = 1;
+                    sadj[0] = adj_of(LB);
                 }
             }
         }
         __syncthreads();
-        if (!INTER) {
-            for (uint32_t g = tid; g < G; g += RG_THREADS) {
-                const K kg = skey[shead[g]];
-                bool has = false;
-                K kn = 0;
-                if (g + 1 < G) { has = true; kn = skey[shead[g + 1]]; }
-                else if (s_has_next) { has = true; kn = s_next_key; }
-                // the next group of the same (block, unit): epoch + 1, or, with the paper's counters, the
-                // next epoch that touches the unit
-                bool next = kn == kg + 1;
-                if (has && !next && ((uint64_t)kn >> be) == ((uint64_t)kg >> be))
-                    next = (td[tob[(uint64_t)kg >> (bu + be)]].flags & TF_PAPER_ORDER) != 0;
-                if (has && next && adj_conflict(sadj[g], sadj[g + 1])) {
-                    const uint64_t sk = (uint64_t)kg >> be;
-                    mark_needed(nonred, L, (uint32_t)(sk >> bu), (uint32_t)((uint64_t)kg & ((1ull << be) - 1)));
-                }
+        // intra streams: each group finished inside the tile against the group before it
+        if (!INTER && G > 0) {
+            const uint32_t last_fin = ends ? G : G - 1;
+            for (uint32_t s = 1 + tid; s <= last_fin; s += RG_THREADS) {
+                const uint32_t a = shead[s - 1];
+                if (t0 + a == 0) continue;   // the stream's first group
+                const K kq = skey[a], kp = a > 0 ? skey[a - 1] : kprev0;
+                if (rg_adjacent(kp, kq, L, td, tob, bu) && adj_conflict(sadj[s - 1], sadj[s]))
+                    mark_needed(nonred, L, (uint32_t)(((uint64_t)kp >> be) >> bu),
+                                (uint32_t)((uint64_t)kp & ((1ull << be) - 1)));
             }
         }
         __syncthreads();

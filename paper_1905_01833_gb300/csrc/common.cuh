@@ -88,6 +88,7 @@ struct Ctl {
     unsigned int px_tile;         // next tile of the visit-order scan
     unsigned int tiles[MAX_PASSES];  // onesweep tile counters, one per pass
     unsigned int wtiles[W_PASSES];   // the same for passes over digits of another width
+    unsigned int rg_tiles[3];        // next tile of the segmented reductions (S, G, X streams)
 };
 
 // Batch-wide dimensions, bit layouts and workspace offsets of one call (host-computed).
@@ -115,6 +116,8 @@ struct Layout {
     uint32_t hb_cap_eighths;         // hash path: distinct units a run may hold, in eighths of its table
     uint32_t hb_pool_div;            // hash path: racy units resolved in place per run, table size / this
     size_t off_hw, off_dw;           // histograms and digit bases of passes not 8 bits wide, per stream
+    uint64_t rg_tiles;               // tiles of the largest stream a segmented reduction scans
+    size_t off_rgpub, off_rgready;   // the reductions' published tile summaries and their ready words
     size_t off_binel;                // per batch-wide block: the hash path does not apply to it
     size_t off_spill;                // per block and epoch: a run the hash path leaves to the sort path
     size_t off_tflag;                // per ingest tile: holds a spilled run

@@ -171,7 +171,9 @@ __device__ __forceinline__ void hb_x_fill(KX *xk, uint64_t *xv, uint32_t from, u
         }
 }
 
-template <class KX, class SH>
+// HOT: a warp marks a global unit's block signature once per run of consecutive lanes holding the same
+// unit and block (a unit that every thread reads would otherwise take one atomic per record on one word)
+template <class KX, class SH, bool HOT>
 __global__ void __launch_bounds__(SH::threads, SH::ctas_per_sm)
 k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob, const uint32_t *__restrict__ bstart,
               const uint32_t *__restrict__ blist, uint32_t lbeg, uint32_t lcnt, unsigned int *queue, Layout L, TState *ts, Ctl *ctl, uint32_t *nonred, uint32_t *binel, uint32_t *spill, uint32_t *tflag,
@@ -240,7 +242,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         // records of this block (those to hash)
         auto activate = [&]() -> uint32_t {
             uint32_t pb = 0;
-            bool stopme = false, isx[P];
+            bool stopme = false, isx[P], same[P];   // same: the lane before holds this record's unit and block
 #pragma unroll
             for (int j = 0; j < P; j++) {
                 const uint32_t idx = wbase + j * SH::threads + tid;
@@ -249,6 +251,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                 if (!__any_sync(0xFFFFFFFFu, fresh)) {   // the warp's records here were validated before
                     if (in && e.z == lb) pb |= 1u << j;
                     isx[j] = false;
+                    same[j] = false;
                     continue;
                 }
                 const uint32_t u = e.x, vo = e.y, blk = e.z, w3 = e.w;
@@ -257,6 +260,12 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                 // the record before: its visit order (strictly increasing) and, in the same block, its epoch
                 uint32_t pvo = __shfl_up_sync(0xFFFFFFFFu, vo, 1), pw = __shfl_up_sync(0xFFFFFFFFu, w3, 1);
                 uint32_t pz = __shfl_up_sync(0xFFFFFFFFu, blk, 1);
+                if (HOT) {
+                    const uint32_t pu = __shfl_up_sync(0xFFFFFFFFu, u, 1);   // every lane shuffles
+                    same[j] = lane > 0 && pz == blk && pu == u;
+                } else {
+                    same[j] = false;
+                }
                 if (lane == 0) {
                     const uint4 p = (fresh && idx > 0) ? ev[idx - 1] : make_uint4(0, 0, 0xFFFFFFFFu, 0);
                     pvo = p.y;
@@ -302,7 +311,9 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                         xk[o] = (KX)(shl(t, L.bug + L.bxr) | e.x);
                         xv[o] = make_payload(act, xo, e.y);
                     }
-                    sig_mark(L, sig_t, sig_slot(L, 0ull, t, e.x), blk, d.block_off + blk);
+                    // a unit every thread reads (a kernel-wide constant) is marked once per run of lanes
+                    if (!(same[j] && ((bj >> (lane - 1)) & 1u)))
+                        sig_mark(L, sig_t, sig_slot(L, 0ull, t, e.x), blk, d.block_off + blk);
                 }
                 xpos += tot;
             }

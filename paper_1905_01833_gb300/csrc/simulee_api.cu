@@ -242,6 +242,9 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, const s
         const uint64_t tile = (uint64_t)OS_THREADS * M.sort_items;
         M.status_tiles = (sort_max + tile - 1) / tile;
         M.off_status = tk((size_t)M.status_tiles * status_digits(M) * 8);
+        M.rg_tiles = (std::max<uint64_t>(cs, cx) + RG_TILE - 1) / RG_TILE + 1;
+        M.off_rgpub = tk((size_t)M.rg_tiles * sizeof(RgTile));
+        M.off_rgready = tk((size_t)M.rg_tiles * 4);
         for (int i = 0; i < 2; i++) {
             M.off_sk[i] = tk(cs * ks);
             M.off_sv[i] = tk(cs * 8);
@@ -307,7 +310,10 @@ void set_sort_attr() {
 
 template <class KX, class SH>
 void set_hash_attr() {
-    cudaFuncSetAttribute(k_hash_blocks<KX, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hash_blocks_smem<SH>());
+    cudaFuncSetAttribute(k_hash_blocks<KX, SH, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)hash_blocks_smem<SH>());
+    cudaFuncSetAttribute(k_hash_blocks<KX, SH, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)hash_blocks_smem<SH>());
 }
 
 template <class K, bool INTER>
@@ -647,6 +653,7 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
     R.mark(SIMULEE_STAGE_INGEST, 0);
     cudaMemsetAsync(R.ws, 0, L.zero_end, st);
     cudaMemsetAsync(R.ws + L.off_status, 0, (size_t)L.status_tiles * status_digits(L) * 8, st);
+    cudaMemsetAsync(R.ws + L.off_rgready, 0, (size_t)L.rg_tiles * 4, st);
     uint32_t *binel = R.at<uint32_t>(L.off_binel);
     uint32_t *spill = R.at<uint32_t>(L.off_spill);
     uint32_t *tflag = R.at<uint32_t>(L.off_tflag);
@@ -740,11 +747,17 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
             uint32_t *bstart = R.at<uint32_t>(L.off_bstart), *blist = R.at<uint32_t>(L.off_blist);
             k_block_ranges<<<R.grid_for(L.NB, 8, 16), 256, 0, st>>>(td, tob, L, bstart, blist);
             R.launches++;
+#define SIM_HASH2(KX, SH, HOT, BEG, CNT, Q)                                                                          \
+    k_hash_blocks<KX, SH, HOT><<<std::max(1, std::min<int>(ctx->sms * SH::ctas_per_sm, (int)(CNT))), SH::threads,  \
+                                 hash_blocks_smem<SH>(), st>>>(td, tob, bstart, blist, BEG, CNT, &R.ctl->hb_next[Q], \
+                                                               L, ts, R.ctl, nonred, binel, spill, tflag,            \
+                                                               R.at<KX>(L.off_xk[0]), R.at<uint64_t>(L.off_xv[0]),  \
+                                                               sig, rs)
 #define SIM_HASH(KX, SH, BEG, CNT, Q)                                                                               \
-    k_hash_blocks<KX, SH><<<std::max(1, std::min<int>(ctx->sms * SH::ctas_per_sm, (int)(CNT))), SH::threads,       \
-                            hash_blocks_smem<SH>(), st>>>(td, tob, bstart, blist, BEG, CNT, &R.ctl->hb_next[Q], L,  \
-                                                          ts, R.ctl, nonred, binel, spill, tflag,                   \
-                                                          R.at<KX>(L.off_xk[0]), R.at<uint64_t>(L.off_xv[0]), sig, rs)
+    do {                                                                                                            \
+        if (ctx->opt.hot_unit_marks == 2) SIM_HASH2(KX, SH, false, BEG, CNT, Q);                                    \
+        else SIM_HASH2(KX, SH, true, BEG, CNT, Q);                                                                  \
+    } while (0)
             // the first group (small CTAs when split or forced), then the second group (large CTAs)
             for (int q = 0; q < 2; q++) {
                 const uint32_t beg = q == 0 ? 0u : n_first, cnt = q == 0 ? n_first : n_second;
@@ -760,6 +773,7 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
                 R.launches++;
             }
 #undef SIM_HASH
+#undef SIM_HASH2
             R.mark(SIMULEE_STAGE_HASH, 1);
             R.mark(SIMULEE_STAGE_FALLBACK, 0);
             k_fallback_tiles<<<R.grid_for(L.ntiles_in, 256, 8), 256, 0, st>>>(td, L, ts, binel, tflag, R.ctl, fbt);
@@ -850,15 +864,17 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
     R.mark(SIMULEE_STAGE_REDUCE, 0);
     if (sorting) {
         const int gr = R.grid_for(L.n, RG_TILE, ctx->opt.reduce_ctas_per_sm ? ctx->opt.reduce_ctas_per_sm : 3u);
-#define SIM_REDUCE(K, INTER, KOFF, VOFF, NPTR, NMAX, SPACE, BU)                                                       \
+        // the three launches share the published tile summaries; their ready words carry tags 1, 2, 3
+#define SIM_REDUCE(K, INTER, KOFF, VOFF, NPTR, NMAX, SPACE, BU, SLOT)                                                 \
     k_reduce_groups<K, INTER><<<gr, RG_THREADS, reduce_groups_smem<K, INTER>(), st>>>(                                \
-        R.at<K>(KOFF), R.at<uint64_t>(VOFF), NPTR, NMAX, L, td, tob, SPACE, BU, R.ctl, nonred, rs)
-        if (L.wide_s) SIM_REDUCE(uint64_t, false, L.off_sk[bs], L.off_sv[bs], &R.ctl->n_s, L.cap_s, 0u, L.bus);
-        else SIM_REDUCE(uint32_t, false, L.off_sk[bs], L.off_sv[bs], &R.ctl->n_s, L.cap_s, 0u, L.bus);
-        if (L.wide_g) SIM_REDUCE(uint64_t, false, L.off_gk[bg], L.off_gv[bg], &R.ctl->n_g, L.cap_s, 1u, L.bug);
-        else SIM_REDUCE(uint32_t, false, L.off_gk[bg], L.off_gv[bg], &R.ctl->n_g, L.cap_s, 1u, L.bug);
-        if (L.wide_x) SIM_REDUCE(uint64_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_xf, L.cap_x1, 1u, L.bug);
-        else SIM_REDUCE(uint32_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_xf, L.cap_x1, 1u, L.bug);
+        R.at<K>(KOFF), R.at<uint64_t>(VOFF), NPTR, NMAX, L, td, tob, SPACE, BU, R.ctl, nonred, rs,                     \
+        R.at<RgTile>(L.off_rgpub), R.at<uint32_t>(L.off_rgready), SLOT + 1u, &R.ctl->rg_tiles[SLOT], R.wait_ns)
+        if (L.wide_s) SIM_REDUCE(uint64_t, false, L.off_sk[bs], L.off_sv[bs], &R.ctl->n_s, L.cap_s, 0u, L.bus, 0u);
+        else SIM_REDUCE(uint32_t, false, L.off_sk[bs], L.off_sv[bs], &R.ctl->n_s, L.cap_s, 0u, L.bus, 0u);
+        if (L.wide_g) SIM_REDUCE(uint64_t, false, L.off_gk[bg], L.off_gv[bg], &R.ctl->n_g, L.cap_s, 1u, L.bug, 1u);
+        else SIM_REDUCE(uint32_t, false, L.off_gk[bg], L.off_gv[bg], &R.ctl->n_g, L.cap_s, 1u, L.bug, 1u);
+        if (L.wide_x) SIM_REDUCE(uint64_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_xf, L.cap_x1, 1u, L.bug, 2u);
+        else SIM_REDUCE(uint32_t, true, L.off_xk[bx], L.off_xv[bx], &R.ctl->n_xf, L.cap_x1, 1u, L.bug, 2u);
 #undef SIM_REDUCE
         R.launches += 3;
     }
@@ -1181,6 +1197,7 @@ simulee_status simulee_create(simulee_ctx **ctx, int device, const simulee_optio
         if (opt->radix_bits != 0 && opt->radix_bits != 6 && opt->radix_bits != 8 && opt->radix_bits != 11)
             return SIMULEE_EINVAL;
         if (opt->hash_cap_eighths != 0 && (opt->hash_cap_eighths < 4 || opt->hash_cap_eighths > 7)) return SIMULEE_EINVAL;
+        if (opt->hot_unit_marks > 2) return SIMULEE_EINVAL;
         if (opt->hash_pool_div != 0 && (opt->hash_pool_div < 3 || opt->hash_pool_div > 64)) return SIMULEE_EINVAL;
     }
     simulee_ctx *c = new (std::nothrow) simulee_ctx();

@@ -63,7 +63,7 @@ class Options(ctypes.Structure):
                 ("ingest_ctas_per_sm", ctypes.c_uint32), ("sort_ctas_per_sm", ctypes.c_uint32),
                 ("reduce_ctas_per_sm", ctypes.c_uint32), ("hash_shape", ctypes.c_uint32), ("graph_replay", ctypes.c_uint32),
                 ("sort_items", ctypes.c_uint32), ("radix_bits", ctypes.c_uint32), ("hash_cap_eighths", ctypes.c_uint32),
-                ("hash_pool_div", ctypes.c_uint32)]
+                ("hash_pool_div", ctypes.c_uint32), ("hot_unit_marks", ctypes.c_uint32)]
 
 
 class Fitness(ctypes.Structure):
@@ -185,12 +185,13 @@ class Checker:
     def __init__(self, device: int = 0, wait_limit_us: int = 0, path: int = PATH_AUTO, test_withhold: int = 0,
                  ingest_ctas_per_sm: int = 0, sort_ctas_per_sm: int = 0, reduce_ctas_per_sm: int = 0,
                  hash_shape: int = 0, graph_replay: int = GRAPH_AUTO, sort_items: int = 0, radix_bits: int = 0,
-                 hash_cap_eighths: int = 0, hash_pool_div: int = 0):
+                 hash_cap_eighths: int = 0, hash_pool_div: int = 0, hot_unit_marks: int = 0):
         import torch
         self.device = device
         self.torch = torch
         opt = Options(wait_limit_us, path, test_withhold, ingest_ctas_per_sm, sort_ctas_per_sm, reduce_ctas_per_sm,
-                      hash_shape, graph_replay, sort_items, radix_bits, hash_cap_eighths, hash_pool_div)
+                      hash_shape, graph_replay, sort_items, radix_bits, hash_cap_eighths, hash_pool_div,
+                      hot_unit_marks)
         h = ctypes.c_void_p()
         _check(lib().simulee_create(ctypes.byref(h), device, ctypes.byref(opt)), "simulee_create")
         self.h = h

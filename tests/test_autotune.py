@@ -16,9 +16,9 @@ def test_buckets_and_knobs():
     assert autotune.batch_bucket([T, T]) == "batch-t1-n27-s4"
     # every knob's first value is the library's default (0 in simulee_options selects it)
     assert autotune.DEFAULTS == {"path": 0, "hash_shape": 0, "hash_cap_eighths": 7, "hash_pool_div": 3,
-                                 "sort_items": 16, "radix_bits": 8, "ingest_ctas_per_sm": 2,
+                                 "hot_unit_marks": 0, "sort_items": 16, "radix_bits": 8, "ingest_ctas_per_sm": 2,
                                  "sort_ctas_per_sm": 3, "reduce_ctas_per_sm": 3}
-    for k in ("sort_items", "radix_bits", "hash_cap_eighths", "hash_pool_div"):
+    for k in ("sort_items", "radix_bits", "hash_cap_eighths", "hash_pool_div", "hot_unit_marks"):
         assert len(autotune.KNOBS[k]) >= 2
 
 
@@ -67,7 +67,7 @@ def test_tuned_batch_equals_oracle(tmp_path):
 @pytest.mark.gpu
 @pytest.mark.parametrize("opts", [dict(radix_bits=6), dict(radix_bits=11), dict(sort_items=8),
                                   dict(radix_bits=11, sort_items=8, path=1), dict(radix_bits=6, path=1),
-                                  dict(hash_cap_eighths=4, hash_pool_div=64)])
+                                  dict(hash_cap_eighths=4, hash_pool_div=64), dict(hot_unit_marks=2)])
 def test_every_knob_value_equals_oracle(opts):
     """Each sort width and tile, and the tightest hash cutover, on traces that send records through every stream
     (unsorted and warp-aware traces, a spilling grid trace) in one batch."""

@@ -326,6 +326,55 @@ def random_grouped(seed: int, **kw) -> Trace:
     return tr
 
 
+def broadcast(seed: int = DEFAULT_SEED, n_blocks: int = 64, block_threads: int = 256, n_epochs: int = 8,
+              reads: int = 1, global_const: bool = True, writers: bool = True) -> Trace:
+    """Kernels whose threads share hot units: per epoch every thread reads the epoch's shared broadcast unit
+    `reads` times (e mod 4; thread 0 writes it in the epoch before when that epoch is even), adds into one of 32 shared histogram bins
+    (eight consecutive threads per bin; a plain write instead of an atomic in every fourth epoch), writes a
+    private shared unit and, with `global_const`, reads one global unit that every thread of the grid reads
+    (a kernel-wide constant). With `writers`, one thread per block also writes the broadcast unit in epochs
+    e = 1 mod 3 and thread 0 of each block writes the global constant in epochs e = 2 mod 5, so the hot
+    units' groups hold races. Emission order: block, epoch, slot, thread; visit order = position. Global
+    writes of thread t go to its own unit b * block_threads + t (no conflicts)."""
+    bt, E = block_threads, n_epochs
+    gconst = (1 << 24) - 1
+    t = np.arange(bt, dtype=np.int64)
+    rng = np.random.default_rng(seed)
+    wtid = rng.integers(1, bt, size=n_blocks)   # the block's extra writer of the broadcast unit
+    units, blocks, tids, epochs, acts, spaces = [], [], [], [], [], []
+
+    def put(u, b, th, e, a, sp):
+        n = len(th)
+        units.append(np.broadcast_to(np.asarray(u, dtype=np.int64), (n,)))
+        blocks.append(np.full(n, b, dtype=np.int64))
+        tids.append(np.asarray(th, dtype=np.int64))
+        epochs.append(np.full(n, e, dtype=np.int64))
+        acts.append(np.broadcast_to(np.asarray(a, dtype=np.int64), (n,)))
+        spaces.append(np.full(n, sp, dtype=np.int64))
+
+    for b in range(n_blocks):
+        for e in range(E):
+            for _ in range(reads):
+                put(e % 4, b, t, e, READ, SHARED)
+            if writers and e % 3 == 1:
+                put(e % 4, b, [int(wtid[b])], e, WRITE, SHARED)
+            put(8 + (t // 8 + e) % 32, b, t, e, WRITE if e % 4 == 3 else ATOMIC, SHARED)
+            put(64 + t, b, t, e, WRITE, SHARED)
+            if global_const:
+                put(gconst, b, t, e, READ, GLOBAL)
+            if writers and e % 5 == 2:
+                put(gconst, b, [0], e, WRITE, GLOBAL)
+            put((b * bt + t) % gconst, b, t, e, WRITE, GLOBAL)
+            if e % 2 == 0:
+                put((e + 1) % 4, b, [0], e, WRITE, SHARED)
+    u = np.concatenate(units)
+    ev = pack(u, np.arange(len(u)), np.concatenate(blocks), np.concatenate(tids), np.concatenate(epochs),
+              np.concatenate(acts), np.concatenate(spaces))
+    counts = np.full(n_blocks * bt, E - 1, dtype=np.uint32)
+    return Trace(ev, counts, n_blocks, bt, 4096, 1 << 24, E - 1,
+                 meta=dict(kind="broadcast", seed=seed, reads=reads, global_const=global_const, writers=writers))
+
+
 class Builder:
     """Hand-built traces: records are appended in schedule order (visit order = serial)."""
 
