@@ -121,6 +121,7 @@ struct Layout {
     size_t off_binel;                // per batch-wide block: the hash path does not apply to it
     size_t off_spill;                // per block and epoch: a run the hash path leaves to the sort path
     size_t off_tflag;                // per ingest tile: holds a spilled run
+    size_t off_bbins;                // hash-path block sizes: histogram and placement cursors per launch group
     size_t off_bstart;               // per batch-wide block of a hash-path trace: its first record
     size_t off_blist;                // hash-path blocks, grouped by the CTA shape that takes them
     size_t off_fbt;                  // tiles for the fallback read

@@ -182,6 +182,7 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, const s
     L.swords = maxb / 32 + 1;
     L.off_spill = take((size_t)L.NB * L.swords * 4);
     L.off_tflag = take((size_t)std::max<uint64_t>(L.ntiles_in, 1) * 4);
+    L.off_bbins = take((size_t)2 * 2 * HB_BINS * 4);
     // histograms of passes over digits of another width than 8 bits: one region per stream (S, G, X,
     // races, schedule ranks)
     const size_t w_region = (size_t)5 * W_SLOT_PASSES * W_RADIX_MAX * 4;
@@ -745,8 +746,12 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
         R.mark(SIMULEE_STAGE_HASH, 0);
         if (route && any_hash) {
             uint32_t *bstart = R.at<uint32_t>(L.off_bstart), *blist = R.at<uint32_t>(L.off_blist);
-            k_block_ranges<<<R.grid_for(L.NB, 8, 16), 256, 0, st>>>(td, tob, L, bstart, blist);
-            R.launches++;
+            uint32_t *bbins = R.at<uint32_t>(L.off_bbins);
+            // block ranges and sizes, then each launch's list with its largest blocks first
+            k_block_ranges<<<R.grid_for(L.NB, 8, 16), 256, 0, st>>>(td, tob, L, n_first, bstart, bbins);
+            k_block_order<<<R.grid_for(L.NB, 256, 4), 256, 0, st>>>(td, tob, bstart, L, n_first, bbins,
+                                                                    bbins + 2 * HB_BINS, blist);
+            R.launches += 2;
 #define SIM_HASH2(KX, SH, HOT, BEG, CNT, Q)                                                                          \
     k_hash_blocks<KX, SH, HOT><<<std::max(1, std::min<int>(ctx->sms * SH::ctas_per_sm, (int)(CNT))), SH::threads,  \
                                  hash_blocks_smem<SH>(), st>>>(td, tob, bstart, blist, BEG, CNT, &R.ctl->hb_next[Q], \
