@@ -455,6 +455,16 @@ class BatchRun:
         if s != 0:
             raise RuntimeError(f"simulee_check_batch failed: {self.simulee.status_str(s)}")
 
+    def hash_groups(self, stream) -> dict:
+        """Blocks per hash-path launch group in the last call on this run's workspace (simulee_hash_groups)."""
+        c, torch = self.ctypes, self.torch
+        out = torch.zeros(5, dtype=torch.int32, device=self.dev)
+        self.simulee._check(self.simulee.lib().simulee_hash_groups(
+            self.chk.h, c.c_void_p(self.ws.data_ptr()), c.c_void_p(out.data_ptr()), c.c_void_p(stream.cuda_stream)),
+            "simulee_hash_groups")
+        v = [int(x) for x in out.cpu().tolist()]
+        return dict(zip(("quarter", "half", "small", "large"), (v[i + 1] - v[i] for i in range(4))))
+
     def stream_sizes(self, stream) -> dict:
         """Stream counts of the last call on this run's workspace (simulee_stream_sizes)."""
         c, torch = self.ctypes, self.torch
@@ -620,6 +630,7 @@ def headline(args, rank: int, world: int, local: int, dist):
                 for k, name in enumerate(simulee.STAGES)}
     n_hash = run.chk.last_launches()
     sizes = run.stream_sizes(stream)
+    hgroups = run.hash_groups(stream)
     value, ms = job_value(n_ev, ms, dist, dev)
 
     # end to end: every step copies all records and counts from pinned host memory, checks the batch
@@ -706,13 +717,13 @@ def headline(args, rank: int, world: int, local: int, dist):
     dom = max(cand, key=lambda k: stage_ms[k])
     kname = {"ingest": "k_block_stats", "hash": "k_hash_blocks", "fallback": "k_ingest", "sort": "k_onesweep",
              "reduce": "k_reduce_groups"}[dom]
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    nl = 2 if (dom == "hash" and any(d.block_threads > 256 for d in dts)
-               and sum(d.n_blocks for d in dts if d.block_threads <= 256) >= 2 * sms) else 1
+    # the hash kernel runs one launch per launch group that holds blocks (thread groups of 128 or 256
+    # threads in the smaller CTAs, whole smaller CTAs, larger CTAs)
+    nl = max(1, sum(1 for v in hgroups.values() if v > 0)) if dom == "hash" else 1
     achieved = sb[dom] / (stage_ms[dom] * 1e-3) / 1e9
     b_plan = sum(sb[k] for k in ("ingest", "hash", "fallback", "sort", "reduce")) / n_ev
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_src, "launches": nl,
+                "frac": achieved / peak, "peak_source": peak_src, "launches": nl, "hash_groups": hgroups,
                 "bytes_per_launch": sb[dom] / nl, "launch_ms": stage_ms[dom] / nl,
                 "stage_bytes": sb[dom], "stage_ms": stage_ms[dom],
                 "bytes_per_record": sb[dom] / n_ev,
@@ -1054,7 +1065,9 @@ def grid_arm(args, rank: int, world: int, local: int, dist, full: bool = True):
     value, ms = job_value(tr.n_events, ms, dist, f"cuda:{local}")
 
     sizes = chk.stream_sizes()
+    hgroups = chk.hash_groups()
     sb = stage_bytes(tr, sizes, args.path, *global_counts(tr))
+    sb["launches"]["hash"] = max(1, sum(1 for v in hgroups.values() if v > 0))
     peak, peak_src = peaks()
     cand = [k for k in ("ingest", "hash", "fallback", "sort", "reduce") if sb[k] > 0]
     dom = max(cand, key=lambda k: stage_ms[k])
@@ -1064,8 +1077,8 @@ def grid_arm(args, rank: int, world: int, local: int, dist, full: bool = True):
     achieved = sb[dom] / (stage_ms[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
-                "bytes_per_launch": sb[dom] / nl, "launch_ms": stage_ms[dom] / nl,
-                "traffic": kernel_traffic(kname, "grid")}
+                "bytes_per_launch": sb[dom] / nl, "launch_ms": stage_ms[dom] / nl, "launches": nl,
+                "hash_groups": hgroups, "traffic": kernel_traffic(kname, "grid")}
     b_plan = sum(sb[k] for k in ("ingest", "hash", "fallback", "sort", "reduce")) / tr.n_events
     roofline["plan"] = {"bytes_per_record": b_plan, "frac": value * 1e9 * b_plan / (peak * 1e9),
                         "floor_frac": value * 1e9 * 16 / (peak * 1e9), "radix_passes": sb["launches"]["sort"] - 1}

@@ -201,6 +201,11 @@ typedef struct {
                                  unit that every thread reads (a kernel-wide constant) costs one atomic per
                                  run of lanes rather than one per record; 2 = every record marks (about 2%
                                  less work per record when no unit is that hot) */
+    uint32_t hash_groups;     /* hash path, CTAs of the smaller shape (512 threads, 4096-entry tables):
+                                 0 = a block whose runs are short (at most 512 or 1024 records per epoch on
+                                 average) is checked by a group of 128 or 256 of the CTA's threads with a
+                                 quarter or half of its tables, so that a CTA checks four or two such blocks
+                                 at once; 1 = every block by a whole CTA */
 } simulee_options;
 
 /* Repeated calls. With SIMULEE_GRAPH_AUTO, a check call (simulee_check*, simulee_check_batch,
@@ -416,6 +421,13 @@ uint32_t simulee_last_replayed(const simulee_ctx *ctx);
    inter-block stream slots written before the inter-block filter (every global record, plus slots
    the hash path reserved and left unused). For measuring algorithmic bytes. */
 simulee_status simulee_stream_sizes(simulee_ctx *ctx, const void *ws, uint32_t *dev_out, void *stream);
+/* Queues on `stream` a copy of five uint32 into dev_out (device memory), for the last check that
+   used workspace `ws`: how the hash path split its blocks into launches. Entries 0..3 are the first
+   position of each launch group in the hash path's block list (blocks checked by 128-thread groups
+   of the smaller CTAs, by 256-thread groups, by whole smaller CTAs, by the larger CTAs), entry 4 the
+   number of blocks listed; group i has entry i+1 - entry i blocks. All zero when no trace took the
+   hash path. For measurement and tests. */
+simulee_status simulee_hash_groups(simulee_ctx *ctx, const void *ws, uint32_t *dev_out, void *stream);
 simulee_status simulee_set_stage_events(simulee_ctx *ctx, void *const *events, uint32_t n_events);
 
 /* Static description of a status code. */

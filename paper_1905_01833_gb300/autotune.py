@@ -11,6 +11,9 @@ knobs are launch-time choices of the library (simulee_options):
 * hash_cap_eighths / hash_pool_div: the cutover from the hash path to the sort
   path: how full a run's table may get in distinct units (4/8 to 7/8) and how
   many racy units a run resolves in place (table / 3 down to table / 64);
+* hash_groups: whether the smaller CTAs check blocks with short runs in thread
+  groups of 128 or 256 threads (four or two blocks per CTA at once) or each
+  block with the whole CTA;
 * hot_unit_marks: whether a warp marks a global unit's block signature once
   per run of lanes holding it (a guard against units every thread reads) or
   once per record (a little less work when no unit is that hot);
@@ -41,6 +44,7 @@ KNOBS = {
     "hash_cap_eighths": (7, 6, 5),
     "hash_pool_div": (3, 6, 12),
     "hot_unit_marks": (0, 2),
+    "hash_groups": (0, 1),
     "sort_items": (16, 8),
     "radix_bits": (8, 6, 11),
     "ingest_ctas_per_sm": (2, 1),

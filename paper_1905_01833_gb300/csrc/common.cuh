@@ -83,12 +83,13 @@ struct Ctl {
     unsigned int n_div, n_red;    // divergent blocks / redundant barriers (all traces)
     unsigned int n_q;             // records in the schedule-rank sort (unsorted traces)
     unsigned int n_fb;            // tiles listed for the fallback read
-    unsigned int hb_next[2];      // next list entry for the hash path's CTAs, per launch
+    unsigned int hb_next[4];      // next list entry for the hash path's CTAs, per launch group
     unsigned int n_rf;            // race records left by the race filter
     unsigned int px_tile;         // next tile of the visit-order scan
     unsigned int tiles[MAX_PASSES];  // onesweep tile counters, one per pass
     unsigned int wtiles[W_PASSES];   // the same for passes over digits of another width
     unsigned int rg_tiles[3];        // next tile of the segmented reductions (S, G, X streams)
+    unsigned int hb_gbeg[5];         // hash path: first list entry of each launch group, then all entries
 };
 
 // Batch-wide dimensions, bit layouts and workspace offsets of one call (host-computed).
@@ -124,6 +125,7 @@ struct Layout {
     size_t off_bbins;                // hash-path block sizes: histogram and placement cursors per launch group
     size_t off_bstart;               // per batch-wide block of a hash-path trace: its first record
     size_t off_blist;                // hash-path blocks, grouped by the CTA shape that takes them
+    size_t off_bgroup;               // per batch-wide block of a hash-path trace: its launch group (u8)
     size_t off_fbt;                  // tiles for the fallback read
     size_t off_sig;                  // block signature per global unit (or unit hash)
     uint64_t sig_slots;              // entries of the signature table (0: no global memory)

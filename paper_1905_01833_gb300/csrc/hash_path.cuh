@@ -35,31 +35,67 @@
 
 namespace simk {
 
-// Two shapes: one CTA of 1024 threads per SM with 8192-entry run tables, or
+// CTA shapes: one CTA of 1024 threads per SM with 8192-entry run tables, or
 // two CTAs of 512 threads per SM with 4096-entry tables (so that one CTA's
-// barriers overlap the other's work). A run may hold up to 7/8 of a table's
-// entries in distinct units (runs near that load are rare and only probe longer;
-// a run beyond it sends its block to the sort path); the options of a call may
-// lower that cutover (4/8 to 7/8) and the racy-unit pool (table / 3 down to
-// table / 64).
-template <int THREADS, int SLOTS, int PER, int CTAS>
+// barriers overlap the other's work). A CTA of the smaller shape may also be
+// split into 2 or 4 thread groups, each with its own quarter or half of the
+// tables and its own named barrier, checking one block each: blocks whose runs
+// are short (a few hundred records) then fill their windows, and a run's
+// barriers and finalisation involve only its group's threads.
+// A run may hold up to 7/8 of its group's table in distinct units (runs near
+// that load are rare and only probe longer; a run beyond it sends its block to
+// the sort path); the options of a call may lower that cutover (4/8 to 7/8)
+// and the racy-unit pool (table / 3 down to table / 64).
+__host__ __device__ constexpr int hb_log2(int x) { return x <= 1 ? 0 : 1 + hb_log2(x / 2); }
+template <int THREADS, int SLOTS, int PER, int CTAS, int GROUPS = 1>
 struct HbShape {
-    static constexpr int threads = THREADS;
-    static constexpr int slots = SLOTS;
+    static constexpr int threads = THREADS;           // threads of the CTA
+    static constexpr int slots = SLOTS;               // table entries of the CTA, all groups
     static constexpr int ctas_per_sm = CTAS;
+    static constexpr int groups = GROUPS;             // blocks checked at once by one CTA
+    static constexpr int gthreads = THREADS / GROUPS; // threads of a group
+    static constexpr int gslots = SLOTS / GROUPS;     // table entries of a group
     static constexpr int per = PER;                   // records per thread per window
-    static constexpr int window = PER * THREADS;      // records per window
-    static constexpr int cap = SLOTS / 8 * 7;         // distinct units per run
-    static constexpr int shift = SLOTS == 8192 ? 19 : 20;   // 32 - log2(SLOTS)
-    static constexpr int pool = SLOTS / 3;            // racy units per run (24-byte summaries in 8-byte entries)
+    static constexpr int window = PER * gthreads;     // records per window of a group
+    static constexpr int cap = gslots / 8 * 7;        // distinct units per run
+    static constexpr int shift = 32 - hb_log2(gslots);
+    static constexpr int pool = gslots / 3;           // racy units per run (24-byte summaries in 8-byte entries)
+    static_assert(THREADS % (32 * GROUPS) == 0 && (gslots & (gslots - 1)) == 0 && GROUPS <= 4, "group shape");
+    static_assert((cap + gthreads - 1) / gthreads <= 32, "list entries per thread");
 };
 // Two records per thread per window: with four per thread and half the threads (the same tables and
 // windows, twice the registers per thread) the kernel ran 40% slower, 16 warps per SM hiding too little
 // of the shared-memory and global latencies.
 using HbLarge = HbShape<1024, 8192, 2, 1>;
 using HbSmall = HbShape<512, 4096, 2, 2>;
-static_assert((HbLarge::cap + HbLarge::threads - 1) / HbLarge::threads <= 32, "list entries per thread");
-static_assert((HbSmall::cap + HbSmall::threads - 1) / HbSmall::threads <= 32, "list entries per thread");
+// Thread groups take one record per thread per window: with two, the extra registers of a group's
+// addressing spill (64 registers per thread at two 512-thread CTAs per SM) and the batched workload's
+// hash stage was 0.7% slower.
+using HbHalf = HbShape<512, 4096, 1, 2, 2>;      // two groups of 256 threads, 2048-entry tables
+using HbQuarter = HbShape<512, 4096, 1, 2, 4>;   // four groups of 128 threads, 1024-entry tables
+
+// a group's barrier: the CTA barrier for one group, else named barrier 1 + g over the group's warps
+// (immediate barrier ids, so that the kernel reserves only the barriers it uses)
+template <class SH>
+__device__ __forceinline__ void hb_sync() {
+    if constexpr (SH::groups == 1) {
+        __syncthreads();
+    } else {
+        switch (threadIdx.x >> hb_log2(SH::gthreads)) {
+        case 0: asm volatile("bar.sync 1, %0;" ::"n"(SH::gthreads) : "memory"); break;
+        case 1: asm volatile("bar.sync 2, %0;" ::"n"(SH::gthreads) : "memory"); break;
+        case 2: asm volatile("bar.sync 3, %0;" ::"n"(SH::gthreads) : "memory"); break;
+        default: asm volatile("bar.sync 4, %0;" ::"n"(SH::gthreads) : "memory"); break;
+        }
+    }
+}
+
+// per-group scalars; the per-run ones are indexed by the run's table parity: the finalisation of one
+// run clears the next run's set, so a run needs no barrier between its finalisation and the next
+// run's inserts
+struct HbGroupState {
+    uint32_t blk, flag, ridx, cnt[2], first[2], nracy[2], needed[2];
+};
 
 constexpr uint32_t HB_EMPTY = 0xFFFFFFFFu;
 constexpr uint32_t HB_NONE = 0xFFFFFFFFu;           // no epoch
@@ -67,10 +103,15 @@ constexpr uint32_t HB_POS_LIMIT = 1u << 22;         // run positions in a pool i
 constexpr uint32_t HB_XCH = 256;                    // inter-block slots a warp reserves at a time
 constexpr int HB_RM = 4;                            // run records per thread held across the two pool passes
 
-// shared memory: owner summaries and keys of two run tables and the creation lists of both
+// Shared memory, one region per thread group: owner summaries [2][gslots] (u64), keys [2][gslots] (u32),
+// creation lists [2][cap] (u16), the group's scalars. A group addresses everything from one base.
+template <class SH>
+__host__ __device__ constexpr size_t hb_group_bytes() {
+    return ((size_t)SH::gslots * 24 + (size_t)SH::cap * 4 + sizeof(HbGroupState) + 15) / 16 * 16;
+}
 template <class SH>
 constexpr size_t hash_blocks_smem() {
-    return (size_t)SH::slots * 8 * 2 + (size_t)SH::slots * 4 * 2 + (size_t)SH::cap * 2 * 2;
+    return (size_t)SH::groups * hb_group_bytes<SH>();
 }
 
 // owner summary field of category c: OR(tid) | OR(~tid) << 10
@@ -167,40 +208,83 @@ __device__ __forceinline__ uint64_t hb_lower_bound(const TraceDesc &d, uint32_t 
     return min(lo, hi);
 }
 
-// bstart of every hash-path block, and the size histogram of each launch group (the first group holds
-// list entries [0, n_first), the second the rest); hist is zeroed by the call
+// Launch groups of the hash path, in list order: blocks of the smaller CTA shape checked by groups of
+// 128 threads (HB_LG_QUARTER), of 256 threads (HB_LG_HALF) or by whole CTAs (HB_LG_SMALL), then the
+// blocks of the larger shape (HB_LG_LARGE). The host puts each trace's blocks in the smaller or the
+// larger class (list entries below or above small_end). Inside the smaller class a block goes to the
+// smallest group whose table holds each of its runs, found by sampling the epochs of its records every
+// `stride` records (a quarter of the distinct units a quarter table may hold): records are in epoch
+// order inside a block, and any 4 * stride consecutive records contain four samples, so a run of
+// 4 * stride records or more holds two samples three apart, and one of 8 * stride or more two samples
+// seven apart. No equal samples three apart: every run is shorter than a quarter table's capacity;
+// none seven apart: shorter than a half table's. (A run's distinct units are at most its records.)
+// Runs up to 3 * stride (7 * stride) records never show such a pair.
+constexpr int HB_LG_QUARTER = 0, HB_LG_HALF = 1, HB_LG_SMALL = 2, HB_LG_LARGE = 3, HB_LGROUPS = 4;
+
+// launch group of a block of the smaller class whose records are [lo, hi), by one warp (all lanes
+// return it)
+__device__ __forceinline__ uint32_t hb_sampled_group(const uint4 *ev, uint64_t lo, uint64_t hi, uint32_t stride,
+                                                     int lane) {
+    uint32_t prev = 0x20000u + lane;   // this lane's sample of the previous chunk (none yet: unique)
+    bool near3 = false, near7 = false;  // two samples three / seven strides apart in one epoch
+    for (uint64_t base = lo; base < hi && !near7; base += 32ull * stride) {
+        const uint64_t p = base + (uint64_t)lane * stride;
+        const uint32_t ep = p < hi ? (ev[p].w >> 16) & 0xFFFu : 0x10000u + lane;   // past the end: unique
+        const uint32_t up3 = __shfl_up_sync(0xFFFFFFFFu, ep, 3), up7 = __shfl_up_sync(0xFFFFFFFFu, ep, 7);
+        const uint32_t pc3 = __shfl_sync(0xFFFFFFFFu, prev, (lane + 29) & 31);   // previous chunk, lane + 29
+        const uint32_t pc7 = __shfl_sync(0xFFFFFFFFu, prev, (lane + 25) & 31);   // previous chunk, lane + 25
+        near3 |= __any_sync(0xFFFFFFFFu, ep == (lane >= 3 ? up3 : pc3));
+        near7 |= __any_sync(0xFFFFFFFFu, ep == (lane >= 7 ? up7 : pc7));
+        prev = ep;
+    }
+    return !near3 ? HB_LG_QUARTER : (!near7 ? HB_LG_HALF : HB_LG_SMALL);
+}
+
+// bstart and launch group of every hash-path block, and the size histogram of each launch group; hist
+// (HB_LGROUPS x HB_BINS) is zeroed by the call
 __global__ void k_block_ranges(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob, Layout L,
-                               uint32_t n_first, uint32_t *bstart, uint32_t *hist) {
+                               uint32_t small_end, uint32_t groups_on, uint32_t *bstart, uint8_t *bgroup,
+                               uint32_t *hist) {
     const int lane = threadIdx.x & 31;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    // a quarter of a quarter table's distinct units at the call's cutover (1024 / 8 * eighths / 4)
+    const uint32_t stride = 32u * L.hb_cap_eighths;
     for (uint64_t b = warp; b < L.NB; b += nwarps) {
         const TraceDesc &d = td[tob[b]];
         if (!d.hash_ok) continue;
         const uint32_t lb = (uint32_t)(b - d.block_off);
         const uint64_t lo = hb_lower_bound(d, lb, lane);
         const uint64_t hi = lb + 1 < d.nb ? hb_lower_bound(d, lb + 1, lane) : d.n;
+        const uint32_t entry = d.hlist + lb;
+        const uint32_t q = entry >= small_end ? (uint32_t)HB_LG_LARGE
+                           : !groups_on       ? (uint32_t)HB_LG_SMALL
+                                              : hb_sampled_group(d.events, lo, hi, stride, lane);
         if (lane == 0) {
             bstart[b] = (uint32_t)lo;
-            const uint32_t g = d.hlist + lb >= n_first ? 1u : 0u;
-            atomicAdd(&hist[g * HB_BINS + hb_size_bin((uint32_t)(hi - lo))], 1u);
+            bgroup[b] = (uint8_t)q;
+            atomicAdd(&hist[q * HB_BINS + hb_size_bin((uint32_t)(hi - lo))], 1u);
         }
     }
 }
 
-// each launch group's list in order of decreasing block size (bins from the largest down; the order
-// inside a bin is the order of the placing atomics); hist as k_block_ranges left it, cursor zeroed
+// Each launch group's list in order of decreasing block size (bins from the largest down; the order
+// inside a bin is the order of the placing atomics). hist and bgroup as k_block_ranges left them;
+// cursor zeroed; gbeg[q] = first list entry of launch group q (gbeg[HB_LGROUPS] = all entries).
 __global__ void k_block_order(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob,
-                              const uint32_t *__restrict__ bstart, Layout L, uint32_t n_first,
-                              const uint32_t *__restrict__ hist, uint32_t *cursor, uint32_t *blist) {
-    __shared__ uint32_t base[2 * HB_BINS];   // first list entry of each (group, bin)
-    if (threadIdx.x < 2) {
-        const uint32_t g = threadIdx.x;
-        uint32_t acc = g ? n_first : 0u;
-        for (int k = HB_BINS - 1; k >= 0; k--) {
-            base[g * HB_BINS + k] = acc;
-            acc += hist[g * HB_BINS + k];
+                              const uint32_t *__restrict__ bstart, const uint8_t *__restrict__ bgroup, Layout L,
+                              const uint32_t *__restrict__ hist, uint32_t *cursor, uint32_t *gbeg, uint32_t *blist) {
+    __shared__ uint32_t base[HB_LGROUPS * HB_BINS];   // first list entry of each (group, bin)
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int q = 0; q < HB_LGROUPS; q++) {
+            if (blockIdx.x == 0) gbeg[q] = acc;
+            for (int k = HB_BINS - 1; k >= 0; k--) {
+                base[q * HB_BINS + k] = acc;
+                acc += hist[q * HB_BINS + k];
+            }
         }
+        if (blockIdx.x == 0) gbeg[HB_LGROUPS] = acc;
     }
     __syncthreads();
     for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < L.NB; b += (uint64_t)gridDim.x * blockDim.x) {
@@ -208,8 +292,7 @@ __global__ void k_block_order(const TraceDesc *__restrict__ td, const uint32_t *
         if (!d.hash_ok) continue;
         const uint32_t lb = (uint32_t)(b - d.block_off);
         const uint32_t s0 = bstart[b], s1 = lb + 1 < d.nb ? bstart[b + 1] : (uint32_t)d.n;
-        const uint32_t g = d.hlist + lb >= n_first ? 1u : 0u;
-        const uint32_t bin = g * HB_BINS + hb_size_bin(s1 - s0);
+        const uint32_t bin = bgroup[b] * HB_BINS + hb_size_bin(s1 - s0);
         blist[base[bin] + atomicAdd(&cursor[bin], 1u)] = (uint32_t)b;
     }
 }
@@ -229,42 +312,47 @@ __device__ __forceinline__ void hb_x_fill(KX *xk, uint64_t *xv, uint32_t from, u
 template <class KX, class SH, bool HOT>
 __global__ void __launch_bounds__(SH::threads, SH::ctas_per_sm)
 k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob, const uint32_t *__restrict__ bstart,
-              const uint32_t *__restrict__ blist, uint32_t lbeg, uint32_t lcnt, unsigned int *queue, Layout L, TState *ts, Ctl *ctl, uint32_t *nonred, uint32_t *binel, uint32_t *spill, uint32_t *tflag,
+              const uint32_t *__restrict__ blist, const uint32_t *__restrict__ gbeg, int lgroup,
+              const uint4 *__restrict__ stats, unsigned int *queue, Layout L, TState *ts, Ctl *ctl, uint32_t *nonred, uint32_t *binel, uint32_t *spill, uint32_t *tflag,
               KX *xk, uint64_t *xv, uint32_t *sig, RaceStage rs) {
+    // this launch's blocks: list entries lbeg .. lbeg + lcnt - 1
+    const uint32_t lbeg = gbeg[lgroup], lcnt = gbeg[lgroup + 1] - lbeg;
+    if (lcnt == 0) return;
     extern __shared__ __align__(16) uint64_t hb_smem[];
-    uint64_t *own = hb_smem;                                               // [2][SH::slots]
-    uint32_t *key = reinterpret_cast<uint32_t *>(own + 2 * SH::slots);      // [2][SH::slots]
-    uint16_t *list = reinterpret_cast<uint16_t *>(key + 2 * SH::slots);     // [2][SH::cap]
-    // per-run scalars are indexed by the run's table parity: the finalisation of one run clears the
-    // next run's set, so a run needs no barrier between its finalisation and the next run's inserts
-    __shared__ uint32_t s_blk, s_flag, s_ridx, s_cnt[2], s_first[2], s_nracy[2], s_needed[2];
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int g = SH::groups == 1 ? 0 : (int)(threadIdx.x >> hb_log2(SH::gthreads));
+    const int tid = SH::groups == 1 ? (int)threadIdx.x : (int)(threadIdx.x & (SH::gthreads - 1));
+    const int lane = threadIdx.x & 31;
+    uint8_t *const greg = reinterpret_cast<uint8_t *>(hb_smem) + (size_t)g * hb_group_bytes<SH>();
+    uint64_t *own = reinterpret_cast<uint64_t *>(greg);                            // [2][gslots]
+    uint32_t *key = reinterpret_cast<uint32_t *>(greg + 16 * SH::gslots);          // [2][gslots]
+    uint16_t *list = reinterpret_cast<uint16_t *>(greg + 24 * SH::gslots);         // [2][cap]
+    HbGroupState &S = *reinterpret_cast<HbGroupState *>(greg + 24 * SH::gslots + 4 * SH::cap);
     const uint32_t lt = lanemask_lt();
-    for (int i = tid; i < 2 * SH::slots; i += SH::threads) {
+    for (int i = tid; i < 2 * SH::gslots; i += SH::gthreads) {
         own[i] = 0ull;
         key[i] = HB_EMPTY;
     }
     if (tid == 0) {
-        s_flag = 0;
-        s_ridx = 0;
+        S.flag = 0;
+        S.ridx = 0;
         for (int q = 0; q < 2; q++) {
-            s_cnt[q] = 0;
-            s_first[q] = HB_NONE;
-            s_nracy[q] = 0;
-            s_needed[q] = 0;
+            S.cnt[q] = 0;
+            S.first[q] = HB_NONE;
+            S.nracy[q] = 0;
+            S.needed[q] = 0;
         }
     }
     const uint64_t xcap = L.x_cap;
     uint32_t xpos = 0, xend = 0;   // this warp's reserved inter-block slots [xpos, xend)
     // the cutover to the sort path chosen for the call: distinct units per run, racy units per run
-    const uint32_t cap_rt = min((uint32_t)SH::cap, (uint32_t)SH::slots / 8u * L.hb_cap_eighths);
-    const uint32_t pool_rt = min((uint32_t)SH::pool, (uint32_t)SH::slots / L.hb_pool_div);
+    const uint32_t cap_rt = min((uint32_t)SH::cap, (uint32_t)SH::gslots / 8u * L.hb_cap_eighths);
+    const uint32_t pool_rt = min((uint32_t)SH::pool, (uint32_t)SH::gslots / L.hb_pool_div);
     for (;;) {
-        __syncthreads();
-        if (tid == 0) s_blk = atomicAdd(queue, 1u);
-        __syncthreads();
-        if (s_blk >= lcnt) break;
-        const uint32_t b = blist[lbeg + s_blk];   // this launch's blocks: list entries lbeg .. lbeg + lcnt - 1
+        hb_sync<SH>();
+        if (tid == 0) S.blk = atomicAdd(queue, 1u);
+        hb_sync<SH>();
+        if (S.blk >= lcnt) break;
+        const uint32_t b = blist[lbeg + S.blk];
         const uint32_t t = tob[b];
         const TraceDesc &d = td[t];
         // uniform: only hash-path traces whose barrier counts are valid (otherwise nothing is reported)
@@ -274,11 +362,14 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         if (s0 >= s1) continue;   // a block without records: no runs
         const uint4 *ev = d.events;
         const uint32_t *cnts = d.counts;
+        // the block's smallest barrier count: a record of this block at an epoch up to it is within its
+        // thread's count, so only later epochs (diverged threads) need the thread's count
+        const uint32_t bmin = stats[b].x;
         const uint32_t nb = d.nb, bt = d.bt, su = d.su, gu = d.gu, maxb = d.maxb;
         const bool pad = nb <= (1u << 20);
         uint32_t *const sig_t = L.sig_direct ? sig + d.sig_off : sig;   // this trace's stretch of a direct table
 
-        // ---- windows: records wbase + j * SH::threads + tid, j = 0, 1. A run's first window
+        // ---- windows: records wbase + j * SH::gthreads + tid, j = 0, 1. A run's first window
         //      starts at the run's first record; records below vmark are already validated and
         //      routed (a window that starts inside the previous one re-reads them from cache).
         uint32_t wbase = s0, vmark = s0;
@@ -287,7 +378,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         auto load = [&](uint4 (&w)[P], uint32_t base) {
 #pragma unroll
             for (int j = 0; j < P; j++) {
-                const uint32_t i = base + j * SH::threads + tid;
+                const uint32_t i = base + j * SH::gthreads + tid;
                 w[j] = i < s1 ? ev[i] : make_uint4(0, 0, 0, 0);
             }
         };
@@ -298,7 +389,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             bool stopme = false, isx[P], same[P];   // same: the lane before holds this record's unit and block
 #pragma unroll
             for (int j = 0; j < P; j++) {
-                const uint32_t idx = wbase + j * SH::threads + tid;
+                const uint32_t idx = wbase + j * SH::gthreads + tid;
                 const bool in = idx < s1, fresh = in && idx >= vmark;
                 const uint4 e = cur[j];
                 if (!__any_sync(0xFFFFFFFFu, fresh)) {   // the warp's records here were validated before
@@ -326,7 +417,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                     pz = p.z;
                 }
                 bool ok = fresh && blk < nb && tt < bt && act != 3u && resv == 0u && (sp ? u < gu : u < su);
-                if (ok && ep > cnts[blk * bt + tt]) ok = false;
+                if (ok && (blk != lb || ep > bmin) && ep > cnts[blk * bt + tt]) ok = false;
                 if (fresh && idx > 0 && vo <= pvo) ok = false;
                 if (fresh && !ok) atomicMax(&ts[t].bad_rec, ~(unsigned long long)idx);
                 if (ok && blk != lb) atomicOr(&ts[t].inel, 1u);   // the trace is not block-contiguous
@@ -370,7 +461,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                 }
                 xpos += tot;
             }
-            if (stopme) s_flag = 1u;
+            if (stopme) S.flag = 1u;
             vmark = max(vmark, min(wbase + (uint32_t)SH::window, s1));
             return pb;
         };
@@ -381,12 +472,12 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         uint32_t prev_e = HB_NONE, par = 0, cnt_prev = 0, run_start = s0;
         bool hashing = true, full_reset = false;
         for (;;) {
-            uint32_t *kt = key + par * SH::slots;
-            uint64_t *ot = own + par * SH::slots;
-            const uint32_t *pkt = key + (par ^ 1u) * SH::slots;   // the previous run's table
-            const uint64_t *pot = own + (par ^ 1u) * SH::slots;
+            uint32_t *kt = key + par * SH::gslots;
+            uint64_t *ot = own + par * SH::gslots;
+            const uint32_t *pkt = key + (par ^ 1u) * SH::gslots;   // the previous run's table
+            const uint64_t *pot = own + (par ^ 1u) * SH::gslots;
             const bool adj = prev_e != HB_NONE && prev_e + 1 == e;
-            volatile uint32_t *needed_flag = &s_needed[par];
+            volatile uint32_t *needed_flag = &S.needed[par];
             // ---- 1. insert run e: its records in this window and, while it goes on, the next windows.
             //      Adjacency (barrier e-1 needed) is tested record by record against the previous run's
             //      table: a conflict between epoch e-1 and the epoch-e records exists exactly when one
@@ -403,7 +494,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
 #pragma unroll
                 for (int j = 0; j < P; j++) {
                     const uint4 r = cur[j];
-                    const uint32_t idx = wbase + j * SH::threads + tid;
+                    const uint32_t idx = wbase + j * SH::gthreads + tid;
                     const uint32_t ep = (r.w >> 16) & 0xFFFu;
                     const bool mine = ((pend >> j) & 1u) && ep == e;
                     uint32_t s = HB_EMPTY;
@@ -413,28 +504,28 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                         uint32_t h = hb_hash<SH>(k);
                         // linear probing; each probe is a claim attempt (most records bring a new unit,
                         // so the compare-and-swap replaces a plain read rather than following one)
-                        for (int probe = 0; probe < SH::slots; probe++) {
+                        for (int probe = 0; probe < SH::gslots; probe++) {
                             const uint32_t old = atomicCAS(&kt[h], HB_EMPTY, k);
                             if (old == HB_EMPTY) { s = h; created = true; break; }
                             if (old == k) { s = h; break; }
-                            h = (h + 1) & (SH::slots - 1);
+                            h = (h + 1) & (SH::gslots - 1);
                         }
                         const uint64_t qb = hb_own_bits((r.w >> 28) & 3u, r.w & 0x3FFu);
                         if (s == HB_EMPTY) {
-                            s_flag = 2u;   // table full
+                            S.flag = 2u;   // table full
                         } else {
                             atomicOr(reinterpret_cast<unsigned long long *>(&ot[s]), (unsigned long long)qb);
                         }
                         if (adj && !*needed_flag) {
                             uint32_t ph = hb_hash<SH>(k);
-                            for (int probe = 0; probe < SH::slots; probe++) {
+                            for (int probe = 0; probe < SH::gslots; probe++) {
                                 const uint32_t c = pkt[ph];
                                 if (c == HB_EMPTY) break;
                                 if (c == k) {
                                     if (hb_cross(pot[ph], qb)) *needed_flag = 1u;
                                     break;
                                 }
-                                ph = (ph + 1) & (SH::slots - 1);
+                                ph = (ph + 1) & (SH::gslots - 1);
                             }
                         }
                     } else if (idx < s1) {
@@ -444,17 +535,17 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                     if (cm) {
                         const int leader = __ffs(cm) - 1;
                         uint32_t base = 0;
-                        if (lane == leader) base = atomicAdd(&s_cnt[par], (uint32_t)__popc(cm));
+                        if (lane == leader) base = atomicAdd(&S.cnt[par], (uint32_t)__popc(cm));
                         base = __shfl_sync(0xFFFFFFFFu, base, leader);
                         if (created) {
                             const uint32_t pos = base + __popc(cm & lt);
                             if (pos < cap_rt) list[par * SH::cap + pos] = (uint16_t)s;
-                            else s_flag = 2u;   // more distinct units than listed entries
+                            else S.flag = 2u;   // more distinct units than listed entries
                         }
                     }
                 }
                 first = __reduce_min_sync(0xFFFFFFFFu, first);
-                if (lane == 0 && first != HB_NONE) atomicMin(&s_first[par], first);
+                if (lane == 0 && first != HB_NONE) atomicMin(&S.first[par], first);
                 if (more) {
                     wbase = wend;
 #pragma unroll
@@ -466,9 +557,9 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
             }
 
             // ---- 2. finalise run e
-            __syncthreads();   // A: the run's inserts are complete
-            const uint32_t flag = s_flag, first = s_first[par];
-            const uint32_t cnt = min(s_cnt[par], (uint32_t)SH::cap);
+            hb_sync<SH>();   // A: the run's inserts are complete
+            const uint32_t flag = S.flag, first = S.first[par];
+            const uint32_t cnt = min(S.cnt[par], (uint32_t)SH::cap);
             const uint32_t lo = run_start, hi = (first != HB_NONE ? first : min(wbase + (uint32_t)SH::window, s1)) - 1;
             const uint32_t next_start = hi + 1;
             const bool stop = flag != 0u;
@@ -479,31 +570,31 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                 next_e = (ev[next_start].w >> 16) & 0xFFFu;
             }
             if (!stop && tid == 0 && *needed_flag) mark_needed(nonred, L, b, e - 1);
-            uint32_t rmask = 0;   // bit m: this thread's list entry tid + m * SH::threads is racy
+            uint32_t rmask = 0;   // bit m: this thread's list entry tid + m * SH::gthreads is racy
             if (!stop) {
 #pragma unroll 1
-                for (uint32_t i = tid, m = 0; i < cnt; i += SH::threads, m++) {
+                for (uint32_t i = tid, m = 0; i < cnt; i += SH::gthreads, m++) {
                     if (hb_racy(ot[list[par * SH::cap + i]])) {
                         rmask |= 1u << m;
-                        atomicAdd(&s_nracy[par], 1u);
+                        atomicAdd(&S.nracy[par], 1u);
                     }
                 }
                 // the previous run's table is no longer read: release it for the next run
                 const uint32_t pp = par ^ 1u;
-                for (uint32_t i = tid; i < cnt_prev; i += SH::threads) {
+                for (uint32_t i = tid; i < cnt_prev; i += SH::gthreads) {
                     const uint32_t sl = list[pp * SH::cap + i];
-                    key[pp * SH::slots + sl] = HB_EMPTY;
-                    own[pp * SH::slots + sl] = 0ull;
+                    key[pp * SH::gslots + sl] = HB_EMPTY;
+                    own[pp * SH::gslots + sl] = 0ull;
                 }
             }
             if (tid == 0) {   // the next run's scalars
-                s_cnt[par ^ 1u] = 0;
-                s_first[par ^ 1u] = HB_NONE;
-                s_nracy[par ^ 1u] = 0;
-                s_needed[par ^ 1u] = 0;
+                S.cnt[par ^ 1u] = 0;
+                S.first[par ^ 1u] = HB_NONE;
+                S.nracy[par ^ 1u] = 0;
+                S.needed[par ^ 1u] = 0;
             }
-            __syncthreads();   // B
-            const uint32_t nracy = s_nracy[par];
+            hb_sync<SH>();   // B
+            const uint32_t nracy = S.nracy[par];
             if (!stop && nracy > 0) {
                 if (nracy > pool_rt || hi - lo >= HB_POS_LIMIT) {
                     // too many racy units: the sort path computes this run's races
@@ -517,13 +608,13 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                     // its keys are all HB_EMPTY (every 16-bit half 0xFFFF) and its owner summaries all 0:
                     // the keys become a map slot -> racy index, the summaries the pool of 6 items per
                     // racy unit, and only what the racy units used is put back afterwards.
-                    uint16_t *rmap = reinterpret_cast<uint16_t *>(key + (par ^ 1u) * SH::slots);
-                    uint32_t *pool = reinterpret_cast<uint32_t *>(own + (par ^ 1u) * SH::slots);
-                    for (uint32_t i = tid; i < nracy * 6; i += SH::threads) pool[i] = HB_EMPTY;
+                    uint16_t *rmap = reinterpret_cast<uint16_t *>(key + (par ^ 1u) * SH::gslots);
+                    uint32_t *pool = reinterpret_cast<uint32_t *>(own + (par ^ 1u) * SH::gslots);
+                    for (uint32_t i = tid; i < nracy * 6; i += SH::gthreads) pool[i] = HB_EMPTY;
                     for (uint32_t m = 0; rmask >> m; m++)
                         if ((rmask >> m) & 1u)
-                            rmap[list[par * SH::cap + tid + m * SH::threads]] = (uint16_t)atomicAdd(&s_ridx, 1u);
-                    __syncthreads();
+                            rmap[list[par * SH::cap + tid + m * SH::gthreads]] = (uint16_t)atomicAdd(&S.ridx, 1u);
+                    hb_sync<SH>();
                     // a record of a racy unit of this run: racy index | category << 16 in the high word,
                     // run position << 10 | tid in the low word; ~0 for any other record
                     auto racy_item = [&](const uint4 &r, uint32_t i) -> uint64_t {
@@ -533,11 +624,11 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                         const uint32_t k = (r.x << 1) | ((r.w >> 30) & 1u);
                         uint32_t h = hb_hash<SH>(k);
                         bool found = false;
-                        for (int probe = 0; probe < SH::slots; probe++) {
+                        for (int probe = 0; probe < SH::gslots; probe++) {
                             const uint32_t kk = kt[h];
                             if (kk == k) { found = true; break; }
                             if (kk == HB_EMPTY) break;
-                            h = (h + 1) & (SH::slots - 1);
+                            h = (h + 1) & (SH::gslots - 1);
                         }
                         if (!found) return ~0ull;
                         const uint32_t ri = rmap[h];
@@ -556,33 +647,33 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                         if ((pe[hw >> 16] & 0x3FFu) != (item & 0x3FFu)) atomicMin(&pe[3 + (hw >> 16)], item);
                     };
                     const uint32_t nrec = hi - lo + 1;
-                    if (nrec <= (uint32_t)(SH::threads * HB_RM)) {
+                    if (nrec <= (uint32_t)(SH::gthreads * HB_RM)) {
                         // the run's records, HB_RM per thread, looked up once: both passes use the items
                         uint4 rr[HB_RM];
 #pragma unroll
                         for (int m = 0; m < HB_RM; m++) {
-                            const uint32_t i = lo + tid + m * SH::threads;
+                            const uint32_t i = lo + tid + m * SH::gthreads;
                             rr[m] = i <= hi ? ev[i] : make_uint4(0, 0, 0xFFFFFFFFu, 0);
                         }
                         uint64_t it[HB_RM];
 #pragma unroll
                         for (int m = 0; m < HB_RM; m++) {
-                            it[m] = racy_item(rr[m], lo + tid + m * SH::threads);
+                            it[m] = racy_item(rr[m], lo + tid + m * SH::gthreads);
                             first_pass(it[m]);
                         }
-                        __syncthreads();
+                        hb_sync<SH>();
 #pragma unroll
                         for (int m = 0; m < HB_RM; m++) second_pass(it[m]);
-                        __syncthreads();
+                        hb_sync<SH>();
                     } else {
 #pragma unroll 1
                         for (int pass = 0; pass < 2; pass++) {
-                            for (uint32_t i = lo + tid; i <= hi; i += SH::threads) {
+                            for (uint32_t i = lo + tid; i <= hi; i += SH::gthreads) {
                                 const uint64_t x = racy_item(ev[i], i);
                                 if (pass == 0) first_pass(x);
                                 else second_pass(x);
                             }
-                            __syncthreads();
+                            hb_sync<SH>();
                         }
                     }
                     // emission; each racy unit's map entry and pool items are read by its own thread only,
@@ -590,7 +681,7 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                     const OwnThread ownt;
                     for (uint32_t m = 0; rmask >> m; m++) {
                         if (!((rmask >> m) & 1u)) continue;
-                        const uint32_t sl = list[par * SH::cap + tid + m * SH::threads];
+                        const uint32_t sl = list[par * SH::cap + tid + m * SH::gthreads];
                         const uint32_t k = kt[sl];
                         uint32_t *pe = pool + rmap[sl] * 6;
                         Top2 S;
@@ -612,8 +703,8 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                             emit_race(rs, ctl, t, race_key(L, t, k & 1u, 0u, b, e, k >> 1, cls), pi, qi, true);
                         }
                     }
-                    if (tid == 0) s_ridx = 0;
-                    __syncthreads();   // the map and the pool are clean again before the next run inserts there
+                    if (tid == 0) S.ridx = 0;
+                    hb_sync<SH>();   // the map and the pool are clean again before the next run inserts there
                 }
             }
             if (stop) {
@@ -640,26 +731,26 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
         }
         // clean tables for the next block
         if (full_reset) {
-            __syncthreads();
-            for (int i = tid; i < 2 * SH::slots; i += SH::threads) {
+            hb_sync<SH>();
+            for (int i = tid; i < 2 * SH::gslots; i += SH::gthreads) {
                 own[i] = 0ull;
                 key[i] = HB_EMPTY;
             }
-            if (tid == 0) s_flag = 0;
+            if (tid == 0) S.flag = 0;
         } else if (hashing) {
             const uint32_t pp = par ^ 1u;   // the last run's table
-            for (uint32_t i = tid; i < cnt_prev; i += SH::threads) {
+            for (uint32_t i = tid; i < cnt_prev; i += SH::gthreads) {
                 const uint32_t sl = list[pp * SH::cap + i];
-                key[pp * SH::slots + sl] = HB_EMPTY;
-                own[pp * SH::slots + sl] = 0ull;
+                key[pp * SH::gslots + sl] = HB_EMPTY;
+                own[pp * SH::gslots + sl] = 0ull;
             }
         }
         if (tid == 0)
             for (int q = 0; q < 2; q++) {
-                s_cnt[q] = 0;
-                s_first[q] = HB_NONE;
-                s_nracy[q] = 0;
-                s_needed[q] = 0;
+                S.cnt[q] = 0;
+                S.first[q] = HB_NONE;
+                S.nracy[q] = 0;
+                S.needed[q] = 0;
             }
     }
     hb_x_fill(xk, xv, xpos, xend, xcap, lane);   // the unused tail of this warp's last chunk

@@ -182,7 +182,7 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, const s
     L.swords = maxb / 32 + 1;
     L.off_spill = take((size_t)L.NB * L.swords * 4);
     L.off_tflag = take((size_t)std::max<uint64_t>(L.ntiles_in, 1) * 4);
-    L.off_bbins = take((size_t)2 * 2 * HB_BINS * 4);
+    L.off_bbins = take((size_t)2 * HB_LGROUPS * HB_BINS * 4);
     // histograms of passes over digits of another width than 8 bits: one region per stream (S, G, X,
     // races, schedule ranks)
     const size_t w_region = (size_t)5 * W_SLOT_PASSES * W_RADIX_MAX * 4;
@@ -191,6 +191,7 @@ simulee_status make_layout(const simulee_trace *tr, uint32_t T, int sms, const s
     if (L.radix_bits != (uint32_t)RADIX_BITS) L.off_dw = take(w_region);
     L.off_bstart = take((size_t)L.NB * 4);
     L.off_blist = take((size_t)L.NB * 4);
+    L.off_bgroup = take((size_t)L.NB);
     L.off_fbt = take((size_t)std::max<uint64_t>(L.ntiles_in, 1) * 4);
     // block signatures of global units: indexed directly (each trace's units after the previous
     // traces' ones) when all traces' global units together fit 2^28 slots, else by a hash of
@@ -636,6 +637,10 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
         set_hash_attr<uint64_t, HbLarge>();
         set_hash_attr<uint32_t, HbSmall>();
         set_hash_attr<uint64_t, HbSmall>();
+        set_hash_attr<uint32_t, HbHalf>();
+        set_hash_attr<uint64_t, HbHalf>();
+        set_hash_attr<uint32_t, HbQuarter>();
+        set_hash_attr<uint64_t, HbQuarter>();
         ctx->attrs_set = true;
     }
     R.st = (cudaStream_t)stream;
@@ -746,37 +751,51 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
         R.mark(SIMULEE_STAGE_HASH, 0);
         if (route && any_hash) {
             uint32_t *bstart = R.at<uint32_t>(L.off_bstart), *blist = R.at<uint32_t>(L.off_blist);
-            uint32_t *bbins = R.at<uint32_t>(L.off_bbins);
-            // block ranges and sizes, then each launch's list with its largest blocks first
-            k_block_ranges<<<R.grid_for(L.NB, 8, 16), 256, 0, st>>>(td, tob, L, n_first, bstart, bbins);
-            k_block_order<<<R.grid_for(L.NB, 256, 4), 256, 0, st>>>(td, tob, bstart, L, n_first, bbins,
-                                                                    bbins + 2 * HB_BINS, blist);
+            uint32_t *bbins = R.at<uint32_t>(L.off_bbins), *gbeg = R.ctl->hb_gbeg;
+            uint8_t *bgroup = R.at<uint8_t>(L.off_bgroup);
+            // thread groups inside the smaller shape's CTAs for blocks with short runs
+            const uint32_t groups_on = first_small && ctx->opt.hash_groups != 1 ? 1u : 0u;
+            // list entries below small_end are blocks of the smaller shape, the rest of the larger
+            const uint32_t small_end = first_small ? n_first : 0u, n_listed = n_first + n_second;
+            // block ranges, launch group and size of each block, then each group's list with its
+            // largest blocks first
+            k_block_ranges<<<R.grid_for(L.NB, 8, 16), 256, 0, st>>>(td, tob, L, small_end, groups_on, bstart, bgroup,
+                                                                    bbins);
+            k_block_order<<<R.grid_for(L.NB, 256, 4), 256, 0, st>>>(td, tob, bstart, bgroup, L, bbins,
+                                                                    bbins + HB_LGROUPS * HB_BINS, gbeg, blist);
             R.launches += 2;
-#define SIM_HASH2(KX, SH, HOT, BEG, CNT, Q)                                                                          \
-    k_hash_blocks<KX, SH, HOT><<<std::max(1, std::min<int>(ctx->sms * SH::ctas_per_sm, (int)(CNT))), SH::threads,  \
-                                 hash_blocks_smem<SH>(), st>>>(td, tob, bstart, blist, BEG, CNT, &R.ctl->hb_next[Q], \
-                                                               L, ts, R.ctl, nonred, binel, spill, tflag,            \
-                                                               R.at<KX>(L.off_xk[0]), R.at<uint64_t>(L.off_xv[0]),  \
-                                                               sig, rs)
-#define SIM_HASH(KX, SH, BEG, CNT, Q)                                                                               \
+#define SIM_HASH2(KX, SH, HOT, CNT, Q)                                                                               \
+    k_hash_blocks<KX, SH, HOT><<<std::max(1, std::min<int>(ctx->sms * SH::ctas_per_sm,                              \
+                                                           (int)(((CNT) + SH::groups - 1) / SH::groups))),           \
+                                 SH::threads, hash_blocks_smem<SH>(), st>>>(                                         \
+        td, tob, bstart, blist, gbeg, Q, R.at<uint4>(L.off_stats), &R.ctl->hb_next[Q], L, ts, R.ctl, nonred, binel,  \
+        spill, tflag,                                                                                               \
+        R.at<KX>(L.off_xk[0]), R.at<uint64_t>(L.off_xv[0]), sig, rs)
+#define SIM_HASH(KX, SH, CNT, Q)                                                                                    \
     do {                                                                                                            \
-        if (ctx->opt.hot_unit_marks == 2) SIM_HASH2(KX, SH, false, BEG, CNT, Q);                                    \
-        else SIM_HASH2(KX, SH, true, BEG, CNT, Q);                                                                  \
+        if (ctx->opt.hot_unit_marks == 2) SIM_HASH2(KX, SH, false, CNT, Q);                                         \
+        else SIM_HASH2(KX, SH, true, CNT, Q);                                                                       \
     } while (0)
-            // the first group (small CTAs when split or forced), then the second group (large CTAs)
-            for (int q = 0; q < 2; q++) {
-                const uint32_t beg = q == 0 ? 0u : n_first, cnt = q == 0 ? n_first : n_second;
+#define SIM_HASH_Q(KX, Q, CNT)                                                                                      \
+    do {                                                                                                            \
+        if ((Q) == HB_LG_QUARTER) SIM_HASH(KX, HbQuarter, CNT, Q);                                                  \
+        else if ((Q) == HB_LG_HALF) SIM_HASH(KX, HbHalf, CNT, Q);                                                   \
+        else if ((Q) == HB_LG_SMALL) SIM_HASH(KX, HbSmall, CNT, Q);                                                 \
+        else SIM_HASH(KX, HbLarge, CNT, Q);                                                                         \
+    } while (0)
+            // launch groups in list order; the smaller class (small_end blocks) is split on the device
+            // between the thread-group shapes and whole smaller CTAs, so each of those launches is
+            // sized for the whole class and its CTAs read the group's true count
+            for (int q = 0; q < HB_LGROUPS; q++) {
+                const bool small_class = q != HB_LG_LARGE;
+                const uint32_t cnt = small_class ? small_end : n_listed - small_end;
                 if (cnt == 0) continue;
-                const bool small = q == 0 && first_small;
-                if (L.wide_x) {
-                    if (small) SIM_HASH(uint64_t, HbSmall, beg, cnt, q);
-                    else SIM_HASH(uint64_t, HbLarge, beg, cnt, q);
-                } else {
-                    if (small) SIM_HASH(uint32_t, HbSmall, beg, cnt, q);
-                    else SIM_HASH(uint32_t, HbLarge, beg, cnt, q);
-                }
+                if (small_class && !groups_on && q != HB_LG_SMALL) continue;
+                if (L.wide_x) SIM_HASH_Q(uint64_t, q, cnt);
+                else SIM_HASH_Q(uint32_t, q, cnt);
                 R.launches++;
             }
+#undef SIM_HASH_Q
 #undef SIM_HASH
 #undef SIM_HASH2
             R.mark(SIMULEE_STAGE_HASH, 1);
@@ -1203,6 +1222,7 @@ simulee_status simulee_create(simulee_ctx **ctx, int device, const simulee_optio
             return SIMULEE_EINVAL;
         if (opt->hash_cap_eighths != 0 && (opt->hash_cap_eighths < 4 || opt->hash_cap_eighths > 7)) return SIMULEE_EINVAL;
         if (opt->hot_unit_marks > 2) return SIMULEE_EINVAL;
+        if (opt->hash_groups > 1) return SIMULEE_EINVAL;
         if (opt->hash_pool_div != 0 && (opt->hash_pool_div < 3 || opt->hash_pool_div > 64)) return SIMULEE_EINVAL;
     }
     simulee_ctx *c = new (std::nothrow) simulee_ctx();
@@ -1336,6 +1356,13 @@ simulee_status simulee_stream_sizes(simulee_ctx *ctx, const void *ws, uint32_t *
     if (!ctx || !ws || !dev_out) return SIMULEE_EINVAL;
     static_assert(offsetof(Ctl, n_x) == offsetof(Ctl, n_s) + 16, "stream counters are contiguous");
     const cudaError_t e = cudaMemcpyAsync(dev_out, (const uint8_t *)ws + offsetof(Ctl, n_s), 20,
+                                          cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIMULEE_OK : SIMULEE_ECUDA;
+}
+
+simulee_status simulee_hash_groups(simulee_ctx *ctx, const void *ws, uint32_t *dev_out, void *stream) {
+    if (!ctx || !ws || !dev_out) return SIMULEE_EINVAL;
+    const cudaError_t e = cudaMemcpyAsync(dev_out, (const uint8_t *)ws + offsetof(Ctl, hb_gbeg), sizeof(Ctl::hb_gbeg),
                                           cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
     return e == cudaSuccess ? SIMULEE_OK : SIMULEE_ECUDA;
 }

@@ -63,7 +63,8 @@ class Options(ctypes.Structure):
                 ("ingest_ctas_per_sm", ctypes.c_uint32), ("sort_ctas_per_sm", ctypes.c_uint32),
                 ("reduce_ctas_per_sm", ctypes.c_uint32), ("hash_shape", ctypes.c_uint32), ("graph_replay", ctypes.c_uint32),
                 ("sort_items", ctypes.c_uint32), ("radix_bits", ctypes.c_uint32), ("hash_cap_eighths", ctypes.c_uint32),
-                ("hash_pool_div", ctypes.c_uint32), ("hot_unit_marks", ctypes.c_uint32)]
+                ("hash_pool_div", ctypes.c_uint32), ("hot_unit_marks", ctypes.c_uint32),
+                ("hash_groups", ctypes.c_uint32)]
 
 
 class Fitness(ctypes.Structure):
@@ -112,6 +113,7 @@ def lib():
         sigs["simulee_compact_workspace_size"] = [vp, P(Trace), u32, P(ctypes.c_size_t)]
         sigs["simulee_check_noalloc"] = [vp, P(Trace), P(Outputs), vp, vp]
         sigs["simulee_stream_sizes"] = [vp, vp, vp, vp]
+        sigs["simulee_hash_groups"] = [vp, vp, vp, vp]
         sigs["simulee_fitness_workspace_size"] = [vp, P(Trace), u32, P(ctypes.c_size_t)]
         sigs["simulee_fitness_batch"] = [vp, P(Trace), u32, vp, vp, ctypes.c_size_t, vp]
         sigs["simulee_model_traces"] = [vp, vp, u32, vp, u64, vp, u64, vp]
@@ -185,13 +187,13 @@ class Checker:
     def __init__(self, device: int = 0, wait_limit_us: int = 0, path: int = PATH_AUTO, test_withhold: int = 0,
                  ingest_ctas_per_sm: int = 0, sort_ctas_per_sm: int = 0, reduce_ctas_per_sm: int = 0,
                  hash_shape: int = 0, graph_replay: int = GRAPH_AUTO, sort_items: int = 0, radix_bits: int = 0,
-                 hash_cap_eighths: int = 0, hash_pool_div: int = 0, hot_unit_marks: int = 0):
+                 hash_cap_eighths: int = 0, hash_pool_div: int = 0, hot_unit_marks: int = 0, hash_groups: int = 0):
         import torch
         self.device = device
         self.torch = torch
         opt = Options(wait_limit_us, path, test_withhold, ingest_ctas_per_sm, sort_ctas_per_sm, reduce_ctas_per_sm,
                       hash_shape, graph_replay, sort_items, radix_bits, hash_cap_eighths, hash_pool_div,
-                      hot_unit_marks)
+                      hot_unit_marks, hash_groups)
         h = ctypes.c_void_p()
         _check(lib().simulee_create(ctypes.byref(h), device, ctypes.byref(opt)), "simulee_create")
         self.h = h
@@ -233,6 +235,15 @@ class Checker:
         v = [int(x) for x in out.cpu().tolist()]
         # x_slots: inter-block stream slots written (global records, plus unused reserved slots on the hash path)
         return dict(n_s=v[0], n_g=v[1], n_x=v[2], n_races=v[3], x_slots=v[4])
+
+    def hash_groups(self, stream=None) -> dict:
+        """Blocks per hash-path launch group in the last check on this checker's workspace: checked by
+        128-thread groups (quarter), 256-thread groups (half), whole smaller CTAs (small), larger CTAs (large)."""
+        out = self.torch.zeros(5, dtype=self.torch.int32, device=f"cuda:{self.device}")
+        _check(lib().simulee_hash_groups(self.h, ctypes.c_void_p(self._ws.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                         _stream_ptr(stream)), "simulee_hash_groups")
+        v = [int(x) for x in out.cpu().tolist()]
+        return dict(zip(("quarter", "half", "small", "large"), (v[i + 1] - v[i] for i in range(4))))
 
     def workspace_size(self, dt: DeviceTrace) -> int:
         n = ctypes.c_size_t()

@@ -16,9 +16,9 @@ def test_buckets_and_knobs():
     assert autotune.batch_bucket([T, T]) == "batch-t1-n27-s4"
     # every knob's first value is the library's default (0 in simulee_options selects it)
     assert autotune.DEFAULTS == {"path": 0, "hash_shape": 0, "hash_cap_eighths": 7, "hash_pool_div": 3,
-                                 "hot_unit_marks": 0, "sort_items": 16, "radix_bits": 8, "ingest_ctas_per_sm": 2,
+                                 "hot_unit_marks": 0, "hash_groups": 0, "sort_items": 16, "radix_bits": 8, "ingest_ctas_per_sm": 2,
                                  "sort_ctas_per_sm": 3, "reduce_ctas_per_sm": 3}
-    for k in ("sort_items", "radix_bits", "hash_cap_eighths", "hash_pool_div", "hot_unit_marks"):
+    for k in ("sort_items", "radix_bits", "hash_cap_eighths", "hash_pool_div", "hot_unit_marks", "hash_groups"):
         assert len(autotune.KNOBS[k]) >= 2
 
 
