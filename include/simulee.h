@@ -184,7 +184,7 @@ typedef struct {
     uint32_t sort_ctas_per_sm;     /* persistent CTAs per SM of each radix pass; 0 = 3 */
     uint32_t reduce_ctas_per_sm;   /* persistent CTAs per SM of the segmented reductions; 0 = 3 */
     uint32_t hash_shape;      /* hash path CTAs: 0 = chosen per call (the smaller shape when blocks have at
-                                 most 256 threads and there are at least two blocks per SM), 1 = one 1024-thread CTA per SM with
+                                 most 256 threads and there are at least two blocks per SM), 1 = one 768-thread CTA per SM with
                                  8192-entry run tables (up to 6144 distinct units per run), 2 = two
                                  512-thread CTAs per SM with 4096-entry tables (up to 3072) */
     uint32_t graph_replay;    /* simulee_graph_replay */

@@ -6,7 +6,7 @@ record count, and the share of records in blocks of at most 256 threads). The
 knobs are launch-time choices of the library (simulee_options):
 
 * path: the hash path where it applies, or the radix-sort path for everything;
-* hash_shape: the hash path's CTAs (one 1024-thread CTA per SM with 8192-entry
+* hash_shape: the hash path's CTAs (one 768-thread CTA per SM with 8192-entry
   run tables, two 512-thread CTAs with 4096-entry tables, or chosen per call);
 * hash_cap_eighths / hash_pool_div: the cutover from the hash path to the sort
   path: how full a run's table may get in distinct units (4/8 to 7/8) and how

@@ -594,7 +594,7 @@ simulee_status issue_check(simulee_ctx *ctx, const simulee_trace *traces, uint32
     // hash-path CTA shapes: blocks of at most 256 threads go to two 512-thread CTAs per SM with
     // 4096-entry tables when there are at least two such blocks per SM (their runs hold fewer distinct
     // units than that table; one CTA's barriers overlap the other's work), the others to one
-    // 1024-thread CTA per SM with 8192-entry tables. The block list holds the first group, then the
+    // 768-thread CTA per SM with 8192-entry tables. The block list holds the first group, then the
     // second; each group is one launch.
     uint32_t nb_small = 0, nb_large = 0;
     for (uint32_t i = 0; i < T; i++)

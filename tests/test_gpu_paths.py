@@ -18,7 +18,7 @@ from gpu_util import diff, gpu_check
 pytestmark = pytest.mark.gpu
 
 PATHS = {"auto": 0, "sort": 1}
-SHAPES = [1, 2]   # hash path: one 1024-thread CTA per SM (8192-entry tables), two 512-thread CTAs (4096)
+SHAPES = [1, 2]   # hash path: one 768-thread CTA per SM (8192-entry tables), two 512-thread CTAs (4096)
 
 
 @pytest.mark.parametrize("path", sorted(PATHS))
