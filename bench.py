@@ -864,7 +864,7 @@ def single_trace_arm(args):
 
 def fitness_arm(args):
     """Fitness of Eq. 1 (distinct addresses / distinct address-thread pairs) over the grid workload: records
-    per second through simulee_fitness_batch, with the radix plan's algorithmic bytes against the HBM peak."""
+    per second through simulee_fitness_batch, with the plan's algorithmic bytes against the HBM peak."""
     import ctypes
     import torch
     import tracegen
@@ -897,11 +897,14 @@ def fitness_arm(args):
     ms = a.elapsed_time(b) / steps
     f = simulee.Fitness.from_buffer_copy(out.cpu().numpy().tobytes())
     assert f.status == 0
-    # key bits: gtid + unit + block + space (one trace): radix passes of 8 bits, 8-byte keys when wider than 32 bits
+    # key bits of the radix sort that takes what the single read leaves (here: nothing; every block's
+    # distinct pairs fit its table): gtid + unit + block + space
     kb = bits(tr.n_blocks * tr.block_threads) + bits(max(tr.shared_units, tr.global_units)) + bits(tr.n_blocks) + 1
-    npass, kw = -(-kb // 8), (8 if kb > 32 else 4)
+    npass = -(-kb // 8)
     n = tr.n_events
-    algo = n * (16 + kw + 2 * npass * kw + kw) + 4 * tr.barrier_counts.size   # read, key write, passes, count
+    # HBM bytes: the validation read and the single read of every record, the barrier counts; the block
+    # tables (512 KB per CTA) and the global-unit bitmap stay in L2
+    algo = n * (16 + 16) + 4 * tr.barrier_counts.size
     peak, peak_src = peaks()
     line = {"workload": f"fitness (Eq. 1) over the grid workload ({tr.n_blocks} blocks, {n} records)",
             "unit": UNIT, "value": n / (ms * 1e-3) / 1e9, "ms_per_step": ms, "steps": steps,

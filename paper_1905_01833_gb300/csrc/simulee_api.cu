@@ -1059,18 +1059,28 @@ struct FitPlan {
     FitKeys fk;
     bool wide;
     uint64_t status_tiles;
+    bool single;           // the single read applies (the bitmap of all traces' global units is small enough)
+    uint32_t fb_ctas;      // CTAs of the single read, one table each
+    uint64_t gbit_words;   // 32-bit words of the global-unit bitmap
     size_t off_ctl, off_ts, off_acc, off_hist, off_td, off_tob, off_stats, off_dbase, off_status, off_k[2];
+    size_t off_fb, off_gbits, off_bstart, off_tabs;
     size_t zero_end, total;
 };
 
-simulee_status fit_plan(const simulee_trace *tr, uint32_t T, FitPlan &P) {
+// The single read's global-unit bitmap holds every trace's global units (one bit each) up to this many
+// bits (1 GiB); a batch with more is counted from sorted keys.
+constexpr uint64_t kFitMaxGlobalBits = 1ull << 33;
+
+simulee_status fit_plan(const simulee_trace *tr, uint32_t T, int sms, FitPlan &P) {
     memset(&P, 0, sizeof P);
     if (!tr || T == 0 || T > kMaxTraces) return SIMULEE_EINVAL;
     uint64_t n = 0, nb = 0, tiles = 0, maxthreads = 0;
     uint32_t maxb = 0, maxnb = 0, units = 0;
+    uint64_t gbits = 0;
     for (uint32_t i = 0; i < T; i++) {
         const simulee_status s = check_trace_args(&tr[i]);
         if (s != SIMULEE_OK) return s;
+        gbits += tr[i].global_units;
         n += tr[i].n_events;
         nb += tr[i].n_blocks;
         tiles += (tr[i].n_events + IN_TILE - 1) / IN_TILE;
@@ -1100,10 +1110,17 @@ simulee_status fit_plan(const simulee_trace *tr, uint32_t T, FitPlan &P) {
     P.status_tiles = (n1 + OS_TILE - 1) / OS_TILE;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes); return r; };
+    P.single = n > 0 && gbits <= kFitMaxGlobalBits;
+    P.gbit_words = P.single ? (gbits + 31) / 32 : 0;
+    P.fb_ctas = P.single ? (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(nb, (uint64_t)sms)) : 0;
     P.off_ctl = take(sizeof(Ctl));
     P.off_ts = take((size_t)T * sizeof(TState));
     P.off_hist = take((size_t)8 * RADIX * 4);
+    P.off_fb = take((size_t)nb * 4);
+    P.off_gbits = take((size_t)P.gbit_words * 4);
     P.zero_end = o;
+    P.off_bstart = take((size_t)nb * 4);
+    P.off_tabs = take((size_t)P.fb_ctas * FB_SLOTS * 8);
     P.off_acc = take((size_t)T * sizeof(FitAcc));
     P.off_td = take((size_t)T * sizeof(TraceDesc));
     P.off_tob = take((size_t)nb * 4);
@@ -1120,7 +1137,7 @@ simulee_status run_fitness(simulee_ctx *ctx, const simulee_trace *traces, uint32
     if (!ctx || !traces || !out || !ws || T == 0) return SIMULEE_EINVAL;
     if (((uintptr_t)ws & 255u) != 0) return SIMULEE_EINVAL;
     FitPlan P;
-    simulee_status s = fit_plan(traces, T, P);
+    simulee_status s = fit_plan(traces, T, ctx->sms, P);
     if (s != SIMULEE_OK) return s;
     if (ws_bytes < P.total) return SIMULEE_ENOMEM;
     int prev_dev = -1;
@@ -1149,8 +1166,13 @@ simulee_status run_fitness(simulee_ctx *ctx, const simulee_trace *traces, uint32
     std::vector<uint8_t *> no_rep(T, nullptr);
     std::vector<TraceDesc> hdesc;
     fill_descs(traces, no_out.data(), no_rep.data(), T, hdesc);
+    // traces counted by the single read (sig_off: the bit of the trace's global unit 0 in the bitmap):
+    // those with at least 1024 records per block on average; a 1024-thread CTA per block would idle on
+    // smaller blocks, which the sort takes in bulk
+    for (uint32_t i = 0; i < T; i++)
+        hdesc[i].hash_ok = P.single && hdesc[i].n > 0 && hdesc[i].n >= 1024ull * hdesc[i].nb ? 1u : 0u;
     launches += upload_descs(td, hdesc, T, st);
-    k_fit_init<<<grid_for(T, 256, 1), 256, 0, st>>>(acc, T);
+    k_fit_init<<<grid_for(T, 256, 1), 256, 0, st>>>(td, acc, T);
     k_block_trace<<<grid_for(L.NB, 256, 8), 256, 0, st>>>(td, L, tob);
     k_block_stats<<<grid_for(L.NB, 8, 16), 256, 0, st>>>(td, tob, L, reinterpret_cast<uint4 *>(w + P.off_stats), ts);
     launches += 3;
@@ -1163,16 +1185,26 @@ simulee_status run_fitness(simulee_ctx *ctx, const simulee_trace *traces, uint32
         k_ingest<uint32_t, uint32_t, uint32_t, IN_VALIDATE><<<gi, IN_THREADS, ingest_smem(), st>>>(
             td, nullptr, L, ts, ctl, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, hist, nullptr, nullptr,
             nullptr, nullptr, wait_ns);
-        k_set_count<<<1, 1, 0, st>>>(&ctl->n_q, (unsigned int)L.n);
+        launches++;
+        // the single read: block ranges, then one CTA per block with a table of its own
+        uint32_t *fb = reinterpret_cast<uint32_t *>(w + P.off_fb);
+        if (P.single) {
+            uint32_t *bstart = reinterpret_cast<uint32_t *>(w + P.off_bstart);
+            k_fit_ranges<<<grid_for(L.NB, 8, 16), 256, 0, st>>>(td, tob, L, bstart);
+            k_fit_blocks<<<P.fb_ctas, FB_THREADS, 0, st>>>(
+                td, tob, bstart, L, ts, &ctl->hb_next[0], reinterpret_cast<unsigned long long *>(w + P.off_tabs),
+                reinterpret_cast<uint32_t *>(w + P.off_gbits), acc, fb);
+            launches += 2;
+        }
+        // what the single read left (ctl->n_q records) through the radix sort
         const int gk = grid_for(L.ntiles_in, 1, 8);
         const int gs = grid_for(L.n, OS_TILE, 3);
-        launches += 2;
 #define SIM_FIT(K)                                                                                                 \
     do {                                                                                                           \
         if (!attr_done(ctx, k_onesweep<K>))                                                                        \
             cudaFuncSetAttribute(k_onesweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)onesweep_smem<K>()); \
         K *k0 = reinterpret_cast<K *>(w + P.off_k[0]), *k1 = reinterpret_cast<K *>(w + P.off_k[1]);                 \
-        k_fit_keys<K><<<gk, FK_THREADS, 0, st>>>(td, L, P.fk, k0, hist, acc);                                      \
+        k_fit_keys<K><<<gk, FK_THREADS, 0, st>>>(td, L, P.fk, fb, k0, hist, acc, ctl);                            \
         k_digit_bases<<<P.fk.np, RADIX, 0, st>>>(hist, dbase, ctl);                                                \
         launches += 2;                                                                                             \
         K *bufs[2] = {k0, k1};                                                                                     \
@@ -1319,7 +1351,7 @@ simulee_status simulee_fitness_workspace_size(simulee_ctx *ctx, const simulee_tr
                                               size_t *bytes) {
     if (!ctx || !traces || !bytes) return SIMULEE_EINVAL;
     FitPlan P;
-    const simulee_status s = fit_plan(traces, n_traces, P);
+    const simulee_status s = fit_plan(traces, n_traces, ctx->sms, P);
     if (s != SIMULEE_OK) return s;
     *bytes = P.total;
     return SIMULEE_OK;

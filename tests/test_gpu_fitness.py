@@ -4,6 +4,14 @@ Integer sums and ranges: the tolerance is zero. Every field of every trace's
 result is compared, for single traces and batches (each trace's result must
 equal the oracle's for that trace alone), valid and bad traces, sorted and
 unsorted, empty ones, and key widths that need 64-bit keys.
+
+The library counts traces whose blocks are contiguous in record order and hold
+at least 1024 records on average with one read per block (a table per CTA, a
+bitmap of global units; the grid-family traces here) and sends to its
+radix sort the records of a block with more distinct (unit, thread) pairs than
+that table takes (49,152 entries at most) and every record of a trace whose blocks are
+not contiguous (the unsorted random traces); both hand-offs are tested here,
+alone and mixed in one batch.
 """
 import numpy as np
 import pytest
@@ -88,3 +96,56 @@ def test_full_size_grid_workload():
     want = oracle.fitness(tr)
     assert _diff(got, want) == []
     assert 0 < got["n_addresses"] <= got["n_pairs"]
+
+
+def _one_big_block(seed: int) -> tracegen.Trace:
+    """Three 1024-thread blocks in record order; block 1 makes 64 distinct shared-unit pairs and 8 global-unit
+    pairs per thread (73,728 pairs, more than a block table takes), shared with its neighbours' units."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for b in range(3):
+        per = 72 if b == 1 else 3
+        for k in range(per):
+            t = np.arange(1024)
+            glob = k % 9 == 8
+            unit = (t * 64 + k + rng.integers(0, 3)) % (1 << 16) if not glob else (b * 7919 + t * 8 + k) % (1 << 18)
+            rows.append((unit, b, t, 0, rng.integers(0, 3, size=1024), 1 if glob else 0))
+    u = np.concatenate([r[0] for r in rows])
+    blk = np.concatenate([np.full(1024, r[1]) for r in rows])
+    tid = np.concatenate([r[2] for r in rows])
+    act = np.concatenate([r[4] for r in rows])
+    sp = np.concatenate([np.full(1024, r[5]) for r in rows])
+    ev = tracegen.pack(u, np.arange(len(u)), blk, tid, 0, act, sp)
+    return tracegen.Trace(ev, np.zeros(3 * 1024, dtype=np.uint32), 3, 1024, 1 << 16, 1 << 18, 0)
+
+
+def test_block_with_more_pairs_than_its_table():
+    tr = _one_big_block(3)
+    want = oracle.fitness(tr)
+    assert want["n_pairs"] > 49152
+    assert _diff(_gpu([tr])[0], want) == []
+
+
+def test_batch_mixing_single_read_and_sorted_traces():
+    trs = [_one_big_block(4), tracegen.random_tiny(31, unsorted=True), tracegen.random_grouped(32, n_events=3000),
+           tracegen.pattern(9, n_blocks=5, block_threads=256, n_epochs=10, shared_units=12288, global_units=1 << 20),
+           cases.bad_count()[0], tracegen.random_tiny(33, n_events=2000, n_blocks=7)]
+    got = _gpu(trs)
+    for i, tr in enumerate(trs):
+        assert _diff(got[i], oracle.fitness(tr)) == [], f"trace {i}"
+
+
+
+def test_blocks_out_of_order_fall_back_to_the_sort():
+    """Large blocks whose records come block by block but not in block order: the single read finds a record
+    of another block in a block's range and the whole trace is counted from sorted keys."""
+    tr = tracegen.pattern(12, n_blocks=6, block_threads=256, n_epochs=8, shared_units=12288, global_units=1 << 20)
+    ev = tr.events
+    order = np.concatenate([np.nonzero(ev[:, 2] == b)[0] for b in (3, 1, 0, 5, 2, 4)])
+    ev = np.ascontiguousarray(ev[order])
+    ev[:, 1] = np.arange(len(ev), dtype=np.uint32)   # visit orders in the new record order
+    tr2 = tracegen.Trace(ev, tr.barrier_counts, tr.n_blocks, tr.block_threads, tr.shared_units, tr.global_units,
+                         tr.max_barriers)
+    want = oracle.fitness(tr2)
+    assert want["n_addresses"] == oracle.fitness(tr)["n_addresses"]
+    assert _diff(_gpu([tr2])[0], want) == []
