@@ -823,7 +823,12 @@ def single_trace_arm(args):
         tr, name = tracegen.c4(), "barrier: 1024 blocks x 1024 threads, 64 epochs, 4 accesses per thread per epoch"
         sample_blocks = 8
     dt = simulee.to_device(tr)
-    chk = simulee.Checker(0)
+    # launch choices (radix width and tile, hash-vs-sort cutover, CTA shapes and counts) from the autotuner
+    opts = {}
+    if not args.no_autotune:
+        from paper_1905_01833_gb300 import autotune
+        opts = autotune.Autotuner(0, cache_path=args.autotune_cache).best(dt)
+    chk = simulee.Checker(0, **opts)
     races_cap = min(2 * tr.n_events + 2, 1 << 22)
     ws = chk.workspace(chk.workspace_size(dt))
     outs, bufs = chk.alloc_outputs(races_cap, tr.n_blocks, tr.n_blocks * max(tr.max_barriers, 1),
@@ -853,6 +858,7 @@ def single_trace_arm(args):
     r = simulee.Report.from_buffer_copy(rep.cpu().numpy().tobytes())
     line = {"workload": name, "n_events": tr.n_events, "value": tr.n_events / (ms * 1e-3) / 1e9, "unit": UNIT,
             "ms_per_step": ms, "steps": steps, "launches_per_step": chk.last_launches(),
+            "options": opts or "library defaults",
             "results": {"status": r.status, "n_races": r.n_races, "n_divergence": r.n_divergence,
                         "n_redundant": r.n_redundant, "n_grid_redundant": r.n_grid_redundant}}
     if not args.no_cpu_baseline:
@@ -1259,7 +1265,7 @@ def main():
     ap.add_argument("--ref-stride", type=int, default=64, help="reference arm: every n-th batch member per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline: the batched line only")
-    ap.add_argument("--no-autotune", action="store_true", help="headline: the library's default launch choices")
+    ap.add_argument("--no-autotune", action="store_true", help="the library's default launch choices (headline and single-trace arms)")
     ap.add_argument("--autotune-cache", default=None, help="autotuner cache file (default: the user's cache)")
     ap.add_argument("--blocks", type=int, default=1024, help="grid blocks (1024 = the single-trace workload; "
                     "smaller values only for profiling captures)")

@@ -1,7 +1,7 @@
 """Autotuner for the check's launch choices, with a persistent JSON cache.
 
 Tuned per GPU model and shape bucket (single traces: log2 of the record count,
-the block count and the epoch count; batches: log2 of the trace count and of the
+the block count and the epoch count, and the trace flags; batches: log2 of the trace count and of the
 record count, and the share of records in blocks of at most 256 threads). The
 knobs are launch-time choices of the library (simulee_options):
 
@@ -60,8 +60,11 @@ def _lg(x) -> int:
 
 
 def bucket(dt) -> str:
-    """Shape bucket of a trace: log2 ceilings of records, blocks and epochs."""
-    return f"n{_lg(dt.n_events)}-b{_lg(dt.n_blocks)}-e{_lg(dt.max_barriers + 1)}"
+    """Shape bucket of a trace: log2 ceilings of records, blocks and epochs, and the trace flags that change
+    the path (unsorted, warp-aware and paper-order traces take the radix sort)."""
+    b = f"n{_lg(dt.n_events)}-b{_lg(dt.n_blocks)}-e{_lg(dt.max_barriers + 1)}"
+    flags = int(getattr(dt, "flags", 0) or 0)
+    return f"{b}-f{flags}" if flags else b
 
 
 def batch_bucket(dts) -> str:

@@ -13,6 +13,10 @@ def test_buckets_and_knobs():
     class T:
         n_events, n_blocks, max_barriers, block_threads = 61_000_000, 1024, 31, 256
     assert autotune.bucket(T) == "n26-b10-e5"
+
+    class W(T):
+        flags = tracegen.WARP_AWARE
+    assert autotune.bucket(W) == "n26-b10-e5-f2"   # warp-aware traces take the sort: a bucket of their own
     assert autotune.batch_bucket([T, T]) == "batch-t1-n27-s4"
     # every knob's first value is the library's default (0 in simulee_options selects it)
     assert autotune.DEFAULTS == {"path": 0, "hash_shape": 0, "hash_cap_eighths": 7, "hash_pool_div": 3,
