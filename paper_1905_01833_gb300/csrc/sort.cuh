@@ -31,12 +31,14 @@ __device__ __forceinline__ uint32_t st_tag(uint64_t s) { return (uint32_t)(s >> 
 __device__ __forceinline__ uint64_t st_flag(uint64_t s) { return (s >> 54) & 3ull; }
 __device__ __forceinline__ uint64_t st_count(uint64_t s) { return s & ((1ull << 54) - 1); }
 
-// Shared memory of one pass: the tile's values and keys, then per digit the global bases, per warp and
-// digit the counts (one column more for invalid lanes), per digit the tile's exclusive offsets.
+// Shared memory of one pass: the tile's values and keys, then per digit the global bases, per digit the
+// tile's exclusive offsets, per warp and digit the counts (16 bits: a tile holds at most 4096 elements; one
+// column more for invalid lanes). With 16-bit counts a pass over 64-bit keys fits three CTAs per SM (72.7
+// KB each; with 32-bit counts, 76.8 KB, only two).
 template <class K, int ITEMS = OS_ITEMS, int BITS = RADIX_BITS>
 constexpr size_t onesweep_smem() {
     constexpr size_t R = (size_t)1 << BITS, TILE = (size_t)OS_THREADS * ITEMS;
-    return TILE * 8 + R * 8 + TILE * sizeof(K) + (size_t)OS_WARPS * (R + 1) * 4 + R * 4;
+    return TILE * 8 + R * 8 + TILE * sizeof(K) + R * 4 + ((size_t)OS_WARPS * (R + 1) * 2 + 3) / 4 * 4;
 }
 
 // Block-wide exclusive scan of one value per thread (OS_THREADS threads).
@@ -72,8 +74,9 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
     uint64_t *svals = reinterpret_cast<uint64_t *>(smem);                 // [TILE]
     uint64_t *gbase = svals + TILE;                                        // [R]
     K *skeys = reinterpret_cast<K *>(gbase + R);                           // [TILE]
-    uint32_t *whist = reinterpret_cast<uint32_t *>(skeys + TILE);          // [OS_WARPS][R + 1]
-    uint32_t *texcl = whist + OS_WARPS * (R + 1);                          // [R]
+    uint32_t *texcl = reinterpret_cast<uint32_t *>(skeys + TILE);          // [R]
+    uint16_t *whist = reinterpret_cast<uint16_t *>(texcl + R);              // [OS_WARPS][R + 1]
+    static_assert(OS_THREADS * ITEMS <= 65535, "16-bit digit counts");
     __shared__ uint32_t wsum[OS_WARPS];
     __shared__ uint32_t s_tile;
 
@@ -113,7 +116,7 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
             const uint32_t li = w * (32 * ipt) + j * 32 + lane;
             k[j] = ((uint32_t)j < ipt && li < nvalid) ? kin[base + li] : K(0);
         }
-        uint32_t *myhist = whist + w * (R + 1);
+        uint16_t *myhist = whist + w * (R + 1);
 #pragma unroll
         for (int j = 0; j < ITEMS; j++) {
             if ((uint32_t)j >= ipt) break;
@@ -132,7 +135,7 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
             if (!valid) peers = ~vmask;
             const uint32_t cnt = myhist[d];
             __syncwarp();
-            if ((peers & lt) == 0) myhist[d] = cnt + __popc(peers);
+            if ((peers & lt) == 0) myhist[d] = (uint16_t)(cnt + __popc(peers));
             __syncwarp();
             rd[j] = (cnt + __popc(peers & lt)) | (d << 16);
         }
@@ -147,7 +150,7 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
 #pragma unroll
                 for (int ww = 0; ww < OS_WARPS; ww++) {
                     const uint32_t c = whist[ww * (R + 1) + d];
-                    whist[ww * (R + 1) + d] = r;
+                    whist[ww * (R + 1) + d] = (uint16_t)r;
                     r += c;
                 }
             }
