@@ -76,7 +76,7 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
     K *skeys = reinterpret_cast<K *>(gbase + R);                           // [TILE]
     uint32_t *texcl = reinterpret_cast<uint32_t *>(skeys + TILE);          // [R]
     uint16_t *whist = reinterpret_cast<uint16_t *>(texcl + R);              // [OS_WARPS][R + 1]
-    static_assert(OS_THREADS * ITEMS <= 65535, "16-bit digit counts");
+    static_assert(OS_THREADS * ITEMS <= 65535 && ITEMS % 4 == 0, "16-bit digit counts, values loaded four at a time");
     __shared__ uint32_t wsum[OS_WARPS];
     __shared__ uint32_t s_tile;
 
@@ -219,16 +219,29 @@ k_onesweep(const K *__restrict__ kin, const uint64_t *__restrict__ vin, K *__res
             acc += run[q];
         }
         __syncthreads();
-        // stable scatter into shared memory in digit order
+        // stable scatter into shared memory in digit order. The values are loaded four at a time, their
+        // loads in flight together (one item at a time behind the item's bounds test, each load waited out
+        // its whole latency: the pass was 18% slower)
+        constexpr int VB = 4;
 #pragma unroll
-        for (int j = 0; j < ITEMS; j++) {
-            if ((uint32_t)j >= ipt) break;
-            const uint32_t li = w * (32 * ipt) + j * 32 + lane;
-            if (li < nvalid) {
-                const uint32_t d = rd[j] >> 16;
-                const uint32_t pos = texcl[d] + whist[w * (R + 1) + d] + (rd[j] & 0xFFFFu);
-                skeys[pos] = k[j];
-                if (vin) svals[pos] = vin[base + li];
+        for (int j0 = 0; j0 < ITEMS; j0 += VB) {
+            uint64_t vv[VB];
+#pragma unroll
+            for (int jj = 0; jj < VB; jj++) {
+                const int j = j0 + jj;
+                const uint32_t li = w * (32 * ipt) + j * 32 + lane;
+                vv[jj] = (vin && (uint32_t)j < ipt && li < nvalid) ? vin[base + li] : 0ull;
+            }
+#pragma unroll
+            for (int jj = 0; jj < VB; jj++) {
+                const int j = j0 + jj;
+                const uint32_t li = w * (32 * ipt) + j * 32 + lane;
+                if ((uint32_t)j < ipt && li < nvalid) {
+                    const uint32_t d = rd[j] >> 16;
+                    const uint32_t pos = texcl[d] + whist[w * (R + 1) + d] + (rd[j] & 0xFFFFu);
+                    skeys[pos] = k[j];
+                    if (vin) svals[pos] = vv[jj];
+                }
             }
         }
         __syncthreads();
