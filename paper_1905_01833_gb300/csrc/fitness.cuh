@@ -78,17 +78,29 @@ __device__ __forceinline__ unsigned long long fb_key(uint32_t addr, uint32_t sp,
            ((unsigned long long)(unit & 0x7FFFFFFFu) << 10) | (tid & 0x3FFu);
 }
 
-// insert k into a table of 2^lg entries: 1 new, 0 present, -1 no free slot
-__device__ __forceinline__ int fb_insert(unsigned long long *tab, unsigned long long k, uint32_t lg) {
+__device__ __forceinline__ uint32_t fb_hash(unsigned long long k, uint32_t lg) {
+    return (uint32_t)((k * 0x9E3779B97F4A7C15ull) >> (64u - lg));   // Fibonacci hashing, top lg bits
+}
+
+// insert k into a table of 2^lg entries, probing from slot h on: 1 new, 0 present, -1 no free slot
+__device__ __forceinline__ int fb_insert_from(unsigned long long *tab, unsigned long long k, uint32_t lg, uint32_t h,
+                                              uint32_t probes) {
     const uint32_t mask = (1u << lg) - 1u;
-    uint32_t h = (uint32_t)((k * 0x9E3779B97F4A7C15ull) >> (64u - lg));   // Fibonacci hashing, top lg bits
-    for (uint32_t p = 0; p <= mask; p++) {
+    for (uint32_t p = 0; p < probes; p++) {
         const unsigned long long old = atomicCAS(&tab[h], FB_EMPTY, k);
         if (old == FB_EMPTY) return 1;
         if (old == k) return 0;
         h = (h + 1) & mask;
     }
     return -1;
+}
+
+// the result of a first claim attempt `old` at k's home slot, probing on when another key holds it
+__device__ __forceinline__ int fb_resolve(unsigned long long *tab, unsigned long long k, uint32_t lg,
+                                          unsigned long long old) {
+    if (old == FB_EMPTY) return 1;
+    if (old == k) return 0;
+    return fb_insert_from(tab, k, lg, (fb_hash(k, lg) + 1) & ((1u << lg) - 1u), (1u << lg) - 1u);
 }
 
 // first record of every block (blocks of traces that take the single read)
@@ -147,49 +159,80 @@ k_fit_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob,
         __syncthreads();
         uint32_t lo0 = 0xFFFFFFFFu, hi0 = 0, lo1 = 0xFFFFFFFFu, hi1 = 0;
         uint32_t pairs = 0, addrs = 0, gaddrs = 0;
-        for (uint32_t base = s0; base < s1; base += 2 * FB_THREADS) {
+        // four records per thread per round, their first claim attempts (then the shared units' and the
+        // bitmap's atomics) in flight together: the table lives in L2, so each atomic waits out an L2 round
+        // trip (two records per round, one after the other: 7% slower)
+        constexpr int FR = 4;
+        for (uint32_t base = s0; base < s1; base += FR * FB_THREADS) {
             const bool over = *(volatile uint32_t *)&s_over != 0u;
-            uint4 e[2];
+            uint4 e[FR];
 #pragma unroll
-            for (int j = 0; j < 2; j++) {
+            for (int j = 0; j < FR; j++) {
                 const uint32_t i = base + j * FB_THREADS + tid;
                 e[j] = i < s1 ? __ldcs(&d.events[i]) : make_uint4(0, 0, 0xFFFFFFFFu, 0);
             }
-            uint32_t made = 0;   // table entries this thread made in this round
+            uint32_t live = 0;   // bit j: record j is this block's and in range
 #pragma unroll
-            for (int j = 0; j < 2; j++) {
+            for (int j = 0; j < FR; j++) {
                 const uint32_t i = base + j * FB_THREADS + tid;
                 if (i >= s1) continue;
                 if (e[j].z != lb) {   // the trace's blocks are not contiguous: count it from sorted keys
                     atomicOr(&acc[t].whole, 1u);
                     continue;
                 }
-                const uint32_t u = e[j].x, sp = (e[j].w >> 30) & 1u, tt = e[j].w & 0xFFFFu;
-                if (sp) { lo1 = min(lo1, u); hi1 = max(hi1, u); }
+                live |= 1u << j;
+                const uint32_t u = e[j].x;
+                if ((e[j].w >> 30) & 1u) { lo1 = min(lo1, u); hi1 = max(hi1, u); }
                 else { lo0 = min(lo0, u); hi0 = max(hi0, u); }
-                bool fresh = over;   // a global unit to mark: every one once the table is given up
-                if (!over) {
-                    const int r = fb_insert(tab, fb_key(0u, sp, u, tt), lg);
+            }
+            uint32_t made = 0, fresh = over ? live : 0u, newsh = 0;
+            if (!over) {
+                unsigned long long kk[FR], old[FR];
+#pragma unroll
+                for (int j = 0; j < FR; j++) {
+                    kk[j] = fb_key(0u, (e[j].w >> 30) & 1u, e[j].x, e[j].w & 0xFFFFu);
+                    old[j] = ((live >> j) & 1u) ? atomicCAS(&tab[fb_hash(kk[j], lg)], FB_EMPTY, kk[j]) : 0ull;
+                }
+#pragma unroll
+                for (int j = 0; j < FR; j++) {
+                    if (!((live >> j) & 1u)) continue;
+                    const int r = fb_resolve(tab, kk[j], lg, old[j]);
                     if (r < 0) {
                         s_over = 1u;
-                        fresh = true;
+                        fresh |= 1u << j;
                     } else if (r > 0) {
                         made++;
                         pairs++;
-                        fresh = true;
-                        if (!sp) {
-                            const int ra = fb_insert(tab, fb_key(1u, 0u, u, 0u), lg);
-                            if (ra < 0) s_over = 1u;
-                            else if (ra > 0) { made++; addrs++; }
-                        }
+                        fresh |= 1u << j;
+                        if (!((e[j].w >> 30) & 1u)) newsh |= 1u << j;
                     }
                 }
-                if (sp && fresh) {
-                    const uint64_t bit = d.sig_off + u;
-                    const uint32_t m = 1u << (bit & 31u);
-                    if (!(atomicOr(&gbits[bit >> 5], m) & m)) gaddrs++;
+                // the shared unit of each new shared pair, first claim attempts together
+#pragma unroll
+                for (int j = 0; j < FR; j++) {
+                    kk[j] = fb_key(1u, 0u, e[j].x, 0u);
+                    old[j] = ((newsh >> j) & 1u) ? atomicCAS(&tab[fb_hash(kk[j], lg)], FB_EMPTY, kk[j]) : 0ull;
+                }
+#pragma unroll
+                for (int j = 0; j < FR; j++) {
+                    if (!((newsh >> j) & 1u)) continue;
+                    const int ra = fb_resolve(tab, kk[j], lg, old[j]);
+                    if (ra < 0) s_over = 1u;
+                    else if (ra > 0) { made++; addrs++; }
                 }
             }
+            // global units of new pairs (of every global record once the table is given up), together
+            uint32_t was[FR], mbit[FR];
+#pragma unroll
+            for (int j = 0; j < FR; j++) {
+                const bool g = ((fresh >> j) & 1u) && ((e[j].w >> 30) & 1u);
+                const uint64_t bit = d.sig_off + e[j].x;
+                mbit[j] = g ? 1u << (bit & 31u) : 0u;
+                was[j] = g ? atomicOr(&gbits[bit >> 5], mbit[j]) : ~0u;
+            }
+#pragma unroll
+            for (int j = 0; j < FR; j++)
+                if (mbit[j] && !(was[j] & mbit[j])) gaddrs++;
             made = __reduce_add_sync(0xFFFFFFFFu, made);
             if (lane == 0 && made && atomicAdd(&s_ins, made) + made > cap) s_over = 1u;
         }
