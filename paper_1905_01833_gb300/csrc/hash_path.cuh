@@ -403,28 +403,20 @@ k_hash_blocks(const TraceDesc *__restrict__ td, const uint32_t *__restrict__ tob
                 const uint32_t u = e.x, vo = e.y, blk = e.z, w3 = e.w;
                 const uint32_t tt = w3 & 0xFFFFu, ep = (w3 >> 16) & 0xFFFu, act = (w3 >> 28) & 3u;
                 const uint32_t sp = (w3 >> 30) & 1u, resv = w3 >> 31;
-                // the record before: its visit order (strictly increasing) and, in the same block, its epoch
-                uint32_t pvo = __shfl_up_sync(0xFFFFFFFFu, vo, 1), pw = __shfl_up_sync(0xFFFFFFFFu, w3, 1);
-                uint32_t pz = __shfl_up_sync(0xFFFFFFFFu, blk, 1);
-                if (HOT) {
-                    const uint32_t pu = __shfl_up_sync(0xFFFFFFFFu, u, 1);   // every lane shuffles
-                    same[j] = lane > 0 && pz == blk && pu == u;
-                } else {
-                    same[j] = false;
-                }
-                if (lane == 0) {
-                    const uint4 p = (fresh && idx > 0) ? ev[idx - 1] : make_uint4(0, 0, 0xFFFFFFFFu, 0);
-                    pvo = p.y;
-                    pw = p.w;
-                    pz = p.z;
-                }
-                bool ok = fresh && blk < nb && tt < bt && act != 3u && resv == 0u && (sp ? u < gu : u < su);
+                // the record before, loaded by each lane (a coalesced load of the window shifted by one record,
+                // mostly from cache): its visit order (strictly increasing) and, in the same block, its epoch
+                const uint4 pr = (fresh && idx > 0) ? ev[idx - 1] : make_uint4(0, 0, 0xFFFFFFFFu, 0);
+                same[j] = HOT && lane > 0 && pr.z == blk && pr.x == u;
+                bool ok = fresh & (blk < nb) & (tt < bt) & (act != 3u) & (resv == 0u) & (u < (sp ? gu : su)) &
+                          (idx == 0 || vo > pr.y);
                 if (ok && (blk != lb || ep > bmin) && ep > cnts[blk * bt + tt]) ok = false;
-                if (fresh && idx > 0 && vo <= pvo) ok = false;
-                if (fresh && !ok) atomicMax(&ts[t].bad_rec, ~(unsigned long long)idx);
-                if (ok && blk != lb) atomicOr(&ts[t].inel, 1u);   // the trace is not block-contiguous
-                if (fresh && (!ok || blk != lb)) stopme = true;
-                if (ok && pz == blk && ((pw >> 16) & 0xFFFu) > ep) stopme = true;   // epochs go back
+                const bool bad = fresh && (!ok || blk != lb);
+                const bool back = ok && pr.z == blk && ((pr.w >> 16) & 0xFFFu) > ep;   // epochs go back
+                if (__any_sync(0xFFFFFFFFu, bad || back)) {   // rare: a bad record, another block's, epochs going back
+                    if (fresh && !ok) atomicMax(&ts[t].bad_rec, ~(unsigned long long)idx);
+                    if (ok && blk != lb) atomicOr(&ts[t].inel, 1u);   // the trace is not block-contiguous
+                    if (bad || back) stopme = true;
+                }
                 if (in && blk == lb && (ok || !fresh)) pb |= 1u << j;
                 isx[j] = ok && sp == 1u && ep <= maxb;
             }
