@@ -110,7 +110,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "sm_min_mhz": min(sm) if sm else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def gpu_uuid(torch, dev: int) -> str | None:
@@ -690,6 +690,9 @@ def headline(args, rank: int, world: int, local: int, dist):
                 issue_copy(i + 1)
 
     run_e2e(3, True)
+    e2e_sampler = ClockSampler(gpu_uuid(torch, local) if world == 1 else None)
+    e2e_sampler.start()
+    time.sleep(0.3)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -702,6 +705,19 @@ def headline(args, rank: int, world: int, local: int, dist):
     nser = max(2, args.e2e_steps // 2)
     run_e2e(nser, False)
     e2e_serial, _ = job_value(n_ev, (time.perf_counter() - t0) / nser * 1e3, dist, dev)
+    e2e_clocks = e2e_sampler.stop()
+    # the upload alone (device time on the copy stream): the host link's bound on the end-to-end figure
+    u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    u0.record(copy_s)
+    for _ in range(3):
+        with torch.cuda.stream(copy_s):
+            d_ev[1].copy_(ev_h, non_blocking=True)
+            d_cn[1].copy_(cn_h, non_blocking=True)
+    u1.record(copy_s)
+    torch.cuda.synchronize()
+    upload_ms = u0.elapsed_time(u1) / 3
+    link_value, _ = job_value(n_ev, upload_ms, dist, dev)
     chks[1].close()
     rb = rep_h.numpy().tobytes()
     for i in range(T):
@@ -742,7 +758,12 @@ def headline(args, rank: int, world: int, local: int, dist):
                 "serial_value": e2e_serial,
                 "overlap": "two device copies of the batch: the next step's host-to-device copy runs on a copy "
                            "stream while the current step is checked; serial_value = copy, check and read-back "
-                           "one after another"},
+                           "one after another",
+                "link": {"upload_ms": upload_ms, "h2d_gbs": h2d / (upload_ms * 1e-3) / 1e9, "bound_value": link_value,
+                         "what": "the step's upload alone from pinned host memory (CUDA events on the copy "
+                                 "stream, 3 copies); bound_value = records per second that link carries, the "
+                                 "ceiling of value when the check overlaps the upload"},
+                "clocks": e2e_clocks},
         "gpu_launches": launches * args.steps,
         "roofline": roofline,
         "stages_ms": stage_ms,
