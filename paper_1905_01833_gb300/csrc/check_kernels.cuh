@@ -648,23 +648,56 @@ __device__ __forceinline__ uint64_t warp_min64(uint64_t x) {
 // kept: the pair whose later access comes first, then the earliest partner (schedule order: visit order,
 // then record index). Called by one thread (lanes = 1) or by all lanes of a warp (lanes = 32), which share
 // the work.
+// Groups of up to WA_CACHE elements searched by one thread keep their items in registers: each item is
+// gathered through its record index once, not once per pair (most groups hold 2-4 accesses). Item
+// words: action << 30 | thread, statement word, visit order, record index.
+constexpr uint32_t WA_CACHE = 3;
+
 template <class K>
 __device__ void wa_group(const K *__restrict__ keys, const uint64_t *__restrict__ vals, uint64_t gs, uint64_t ge,
                          uint64_t n, K kg, const TraceDesc &d, const Layout &L, const RaceStage &rs, Ctl *ctl,
                          uint32_t *nonred, uint32_t trace, uint32_t space, uint32_t block, uint32_t epoch,
                          uint32_t unit, int lane, int lanes) {
     uint64_t bq[2] = {EMPTY, EMPTY}, bp[2] = {EMPTY, EMPTY};   // (visit order << 32 | record index) of q and p
-    for (uint64_t qi = gs + lane; qi < ge; qi += lanes) {
-        const WaItem q = wa_item(d, vals[qi]);
-        const uint64_t kq = ((uint64_t)q.vo << 32) | (uint32_t)vals[qi];
-        for (uint64_t pi = gs; pi < ge; pi++) {
-            const WaItem p = wa_item(d, vals[pi]);
-            const uint64_t kp = ((uint64_t)p.vo << 32) | (uint32_t)vals[pi];
-            if (kp >= kq || !wa_conflict(p.act, p.gtid, p.stmt, q.act, q.gtid, q.stmt, d.bt)) continue;
-            const int cls = (p.act != ACT_R && q.act != ACT_R) ? 0 : 1;
-            if (kq < bq[cls] || (kq == bq[cls] && kp < bp[cls])) {
-                bq[cls] = kq;
-                bp[cls] = kp;
+    // keep the pair (p, q) when it conflicts and is lower in its class than the one kept
+    auto consider = [&](const WaItem &p, uint64_t kp, const WaItem &q, uint64_t kq) {
+        if (kp >= kq || !wa_conflict(p.act, p.gtid, p.stmt, q.act, q.gtid, q.stmt, d.bt)) return;
+        const int cls = (p.act != ACT_R && q.act != ACT_R) ? 0 : 1;
+        if (kq < bq[cls] || (kq == bq[cls] && kp < bp[cls])) {
+            bq[cls] = kq;
+            bp[cls] = kp;
+        }
+    };
+    const uint32_t g = (uint32_t)min(ge - gs, (uint64_t)WA_CACHE + 1u);
+    const bool cached = lanes == 1 && g <= WA_CACHE;
+    uint32_t c_ag[WA_CACHE], c_st[WA_CACHE], c_vo[WA_CACHE], c_ix[WA_CACHE];
+    auto c_item = [&](int i) { return WaItem{c_ag[i] >> 30, c_ag[i] & 0x3FFFFFFFu, c_st[i], c_vo[i]}; };
+    auto c_key = [&](int i) { return ((uint64_t)c_vo[i] << 32) | c_ix[i]; };
+    if (cached) {
+#pragma unroll
+        for (int i = 0; i < (int)WA_CACHE; i++) {
+            c_ag[i] = c_st[i] = c_vo[i] = c_ix[i] = 0u;
+            if ((uint32_t)i < g) {
+                const uint64_t v = vals[gs + i];
+                const WaItem it = wa_item(d, v);
+                c_ag[i] = (it.act << 30) | it.gtid;
+                c_st[i] = it.stmt;
+                c_vo[i] = it.vo;
+                c_ix[i] = (uint32_t)v;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < (int)WA_CACHE; a++)
+#pragma unroll
+            for (int b = 0; b < (int)WA_CACHE; b++)
+                if ((uint32_t)a < g && (uint32_t)b < g) consider(c_item(b), c_key(b), c_item(a), c_key(a));
+    } else {
+        for (uint64_t qi = gs + lane; qi < ge; qi += lanes) {
+            const WaItem q = wa_item(d, vals[qi]);
+            const uint64_t kq = ((uint64_t)q.vo << 32) | (uint32_t)vals[qi];
+            for (uint64_t pi = gs; pi < ge; pi++) {
+                const WaItem p = wa_item(d, vals[pi]);
+                consider(p, ((uint64_t)p.vo << 32) | (uint32_t)vals[pi], q, kq);
             }
         }
     }
@@ -688,9 +721,18 @@ __device__ void wa_group(const K *__restrict__ keys, const uint64_t *__restrict_
         bool needed = false;
         for (uint64_t qi = ge; qi < n && keys[qi] == kg + 1 && !needed; qi++) {
             const WaItem q = wa_item(d, vals[qi]);
-            for (uint64_t pi = gs + lane; pi < ge && !needed; pi += lanes) {
-                const WaItem p = wa_item(d, vals[pi]);
-                needed = wa_conflict(p.act, p.gtid, p.stmt, q.act, q.gtid, q.stmt, d.bt);
+            if (cached) {
+#pragma unroll
+                for (int b = 0; b < (int)WA_CACHE; b++)
+                    if ((uint32_t)b < g && !needed) {
+                        const WaItem p = c_item(b);
+                        needed = wa_conflict(p.act, p.gtid, p.stmt, q.act, q.gtid, q.stmt, d.bt);
+                    }
+            } else {
+                for (uint64_t pi = gs + lane; pi < ge && !needed; pi += lanes) {
+                    const WaItem p = wa_item(d, vals[pi]);
+                    needed = wa_conflict(p.act, p.gtid, p.stmt, q.act, q.gtid, q.stmt, d.bt);
+                }
             }
             if (lanes > 1) needed = __any_sync(0xFFFFFFFFu, needed);
         }
