@@ -670,7 +670,7 @@ __device__ void wa_group(const K *__restrict__ keys, const uint64_t *__restrict_
     };
     const uint32_t g = (uint32_t)min(ge - gs, (uint64_t)WA_CACHE + 1u);
     const bool cached = lanes == 1 && g <= WA_CACHE;
-    uint32_t c_ag[WA_CACHE], c_st[WA_CACHE], c_vo[WA_CACHE], c_ix[WA_CACHE];
+    uint32_t c_ag[WA_CACHE] = {}, c_st[WA_CACHE] = {}, c_vo[WA_CACHE] = {}, c_ix[WA_CACHE] = {};
     auto c_item = [&](int i) { return WaItem{c_ag[i] >> 30, c_ag[i] & 0x3FFFFFFFu, c_st[i], c_vo[i]}; };
     auto c_key = [&](int i) { return ((uint64_t)c_vo[i] << 32) | c_ix[i]; };
     if (cached) {
